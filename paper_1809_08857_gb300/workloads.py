@@ -1,0 +1,111 @@
+"""Seeded synthetic inputs for the elliptic solves (shared by the oracle tests
+and the CUDA path).  This module holds no solver arithmetic: it only draws
+charge densities, permittivities, sources and electrode masks, as numpy
+arrays of shape (nz, ny, nx) on the unit cube with h = 1/n.
+
+The shapes follow the paper's geometries (rod-plane and needle-plane gaps with
+a live top face and a grounded bottom face, Secs. 3 and 4) and the charged
+filaments of a propagating streamer; the kinetic data and Perlin table the
+paper uses are not available, so these synthetic fields stand in for them.
+"""
+import numpy as np
+
+EPS0 = 8.8541878128e-12  # F/m, CODATA 2018
+
+# Boundary conditions of the gap: Neumann on the four sides, phi = 0 at z = 0
+# (grounded plane) and phi = 1 at z = 1 (live face).  Faces -x,+x,-y,+y,-z,+z;
+# kind 0 = Dirichlet, 1 = Neumann.
+GAP_BC_KIND = (1, 1, 1, 1, 0, 0)
+GAP_BC_VALUE = (0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+
+
+def centres(n):
+    """Cell-centre coordinates (i + 1/2) h of an n-cell axis on [0, 1]."""
+    return (np.arange(n, dtype=np.float64) + 0.5) / n
+
+
+def gaussian_blobs(n, seed, nblobs=4, width=0.05):
+    """Space charge rho (C/m^3) = eps0 * sum_k a_k exp(-|x - c_k|^2 / (2 w^2)),
+    centres uniform in [0.2, 0.8]^3, amplitudes a_k ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0.2, 0.8, size=(nblobs, 3))
+    a = rng.standard_normal(nblobs)
+    x = centres(n)
+    rho = np.zeros((n, n, n))
+    for k in range(nblobs):
+        ex = np.exp(-((x - c[k, 0]) ** 2) / (2 * width**2))
+        ey = np.exp(-((x - c[k, 1]) ** 2) / (2 * width**2))
+        ez = np.exp(-((x - c[k, 2]) ** 2) / (2 * width**2))
+        rho += a[k] * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
+    return rho * EPS0
+
+
+def dielectric_slab(n, z_top=0.2, eps_slab=4.0):
+    """Relative permittivity eps_slab for cell centres with z < z_top, else 1."""
+    z = centres(n)
+    eps = np.ones((n, n, n))
+    eps[z < z_top] = eps_slab
+    return eps
+
+
+def _shell_distance_slab(x, y, z, axis_xy, z0, z1, radius):
+    """Distance from points of one z plane to the open capsule surface: a
+    cylinder of the given radius from z0 to z1 along z, closed by a
+    hemispherical head at z1, open at z0."""
+    r = np.sqrt((x[None, :] - axis_xy[0]) ** 2 + (y[:, None] - axis_xy[1]) ** 2)
+    if z > z1:
+        return np.abs(np.sqrt(r**2 + (z - z1) ** 2) - radius)
+    if z >= z0:
+        return np.abs(r - radius)
+    return np.sqrt((r - radius) ** 2 + (z0 - z) ** 2)
+
+
+def streamer_shell(n, seed, radius=0.02, z0=0.4, z1=0.8, axis_xy=(0.5, 0.5),
+                   amplitude=1e-3, noise=0.1):
+    """Charged shell of a streamer channel: cells within h of the surface of a
+    cylinder (radius, from z0 to z1 on the axis) with a hemispherical head.
+    Density amplitude * eps0 / h^2 times a lognormal factor exp(noise * xi),
+    xi ~ N(0, 1) per shell cell (drawn in index order)."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n
+    x = centres(n)
+    shell = np.zeros((n, n, n), dtype=bool)
+    for k in range(n):
+        d = _shell_distance_slab(x, x, x[k], axis_xy, z0, z1, radius)
+        shell[k] = d <= h
+    rho = np.zeros((n, n, n))
+    cnt = int(shell.sum())
+    rho[shell] = amplitude / h**2 * np.exp(noise * rng.standard_normal(cnt))
+    return rho * EPS0
+
+
+def ionization_source(n, seed, sigma_cells=2.0):
+    """Non-negative photo-emission source S for the radiative-transfer solves:
+    the magnitude of the streamer-shell charge (in units of eps0), smoothed by
+    a Gaussian of width sigma_cells cells."""
+    from scipy.ndimage import gaussian_filter
+
+    shell = np.abs(streamer_shell(n, seed)) / EPS0
+    s = gaussian_filter(shell, sigma=sigma_cells, mode="constant", truncate=4.0)
+    return np.maximum(s, 0.0)
+
+
+def needle_mask(n, tip_z=0.8, tip_radius_cells=5.0, half_angle_deg=10.0, axis_xy=(0.5, 0.5)):
+    """Electrode cells of a needle from the top face down to a hyperboloid tip:
+    r^2 <= 2 R d + d^2 tan^2(theta), d = z - tip_z >= 0, R = tip radius."""
+    h = 1.0 / n
+    R = tip_radius_cells * h
+    t2 = np.tan(np.deg2rad(half_angle_deg)) ** 2
+    x = centres(n)
+    r2 = (x[None, :] - axis_xy[0]) ** 2 + (x[:, None] - axis_xy[1]) ** 2
+    mask = np.zeros((n, n, n), dtype=np.uint8)
+    for k in range(n):
+        d = x[k] - tip_z
+        if d >= 0:
+            mask[k] = r2 <= 2 * R * d + d * d * t2
+    return mask
+
+
+def helmholtz_kappas():
+    """Inverse absorption lengths of the three photon groups, kappa L = 10, 100, 1000."""
+    return (10.0, 100.0, 1000.0)
