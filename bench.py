@@ -1,0 +1,387 @@
+"""Benchmark: Poisson + 3 x screened-Helmholtz solves to 1e-10 relative
+residual at 512^3 on one GB300 (per rank), through libmg's C ABI.
+
+One step = one solve set: the variable-permittivity Poisson problem (dielectric
+slab eps_r = 4 below z = 0.2, streamer-shell charge, phi = 0 / 1 on the bottom
+/ top faces, Neumann sides) plus the three radiative-transfer Helmholtz
+problems (kappa L = 10, 100, 1000, Gaussian-smoothed ionisation source), each
+from a zero initial guess, mixed precision (FP32 V-cycles inside FP64
+iterative refinement).  Inputs are seeded synthetic fields generated on the
+host and resident in HBM before timing; every array is 1 GiB, far larger than
+the 129 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank solves its own replica (weak scaling, no collective on
+the data path); the time is the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson+3×Helmholtz solves/s to 1e-10 rel. residual at 512³; % HBM roofline"
+UNIT = "solve sets/s (1 set = 1 Poisson + 3 Helmholtz)"
+TOL = 1e-10
+KAPPAS = (10.0, 100.0, 1000.0)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--inner-cycles", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload(n):
+    from paper_1809_08857_gb300 import workloads as W
+
+    return {"rho": W.streamer_shell(n, 0), "eps": W.dielectric_slab(n),
+            "S": W.ionization_source(n, 0)}
+
+
+def config(args):
+    return {"workload": f"poisson_slab_shell_{args.n}^3 + 3x helmholtz_{args.n}^3 (kappa L = 10, 100, 1000)",
+            "grid": [args.n] * 3, "tol": TOL, "precision": args.precision,
+            "inner_cycles": args.inner_cycles, "smoother": "red-black Gauss-Seidel V(2,2)",
+            "l2": "inputs larger than L2 (1 GiB per array), no flush"}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+
+def oracle_sample(inputs, n, cycles_per_problem):
+    """Time the FP64 CPU oracle on the host cores: per problem, a solve
+    capped at 0 cycles (setup, norms) and at 1 cycle; the difference is the
+    cost of one V(2,2)-cycle.  The set time is the per-cycle cost times the
+    cycles each problem needs (the V-cycle counts the GPU solver reported for
+    the same problems)."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    h = 1.0 / n
+    probs = [(oracle.poisson((n, n, n), h, eps_r=inputs["eps"]), inputs["rho"] / oracle.EPS0)]
+    probs += [(oracle.helmholtz((n, n, n), h, k), inputs["S"]) for k in KAPPAS]
+    t_set = 0.0
+    per = []
+    t0 = time.perf_counter()
+    for q, (p, f) in enumerate(probs):
+        if q == 0 or q == 1:  # Poisson and one Helmholtz measured; the others share the cost
+            ta = time.perf_counter()
+            p.solve(f, tol=0.0, max_cycles=0)
+            tb = time.perf_counter()
+            p.solve(f, tol=0.0, max_cycles=1)
+            tc = time.perf_counter()
+            tcyc = max((tc - tb) - (tb - ta), 1e-9)
+        per.append(tcyc)
+        t_set += tcyc * cycles_per_problem[q]
+    wall = time.perf_counter() - t0
+    return {"value": 1.0 / t_set, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 C oracle (OpenMP, {cores} threads) at {n}^3: one V(2,2)-cycle of the "
+                       f"Poisson and of a Helmholtz problem timed (cap 1 minus cap 0), "
+                       f"{[round(x, 2) for x in per]} s/cycle, times the V-cycle counts "
+                       f"{list(cycles_per_problem)} needed for 1e-10; {wall:.0f} s of CPU work"),
+            "seconds_per_set": t_set}
+
+
+# ---------------------------------------------------------------- clocks
+
+
+class Clocks:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "smooth": ["paper_1809_08857_gb300/csrc/mg_split32.cu"],
+    "restrict": ["paper_1809_08857_gb300/csrc/mg_split32.cu"],
+    "prolong": ["paper_1809_08857_gb300/csrc/mg_split32.cu"],
+    "resid64": ["paper_1809_08857_gb300/csrc/mg_ir.cu"],
+}
+
+
+def traffic_for(cls, launches_bytes):
+    """DRAM bytes per launch of the class from the committed ncu summary, or
+    None when there is none or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = t.get(cls)
+    if not ent or ent.get("source_hash") != source_hash(KERNEL_SOURCES.get(cls, [])):
+        return None
+    # scale a small-case capture to this launch size by cells processed
+    return ent["dram_bytes_per_cell"] * ent.get("cells_scale", 1.0) * launches_bytes
+
+
+def roofline(prof, n):
+    pk, src = peaks()
+    fine = {k: v for k, v in prof.items() if k != "coarse" and v["ms"] > 0}
+    if not fine:
+        return None
+    dom = max(fine, key=lambda k: fine[k]["ms"])
+    d = fine[dom]
+    avg_ms = d["ms"] / d["launches"]
+    avg_bytes = d["bytes"] / d["launches"]
+    gbs = avg_bytes / (avg_ms * 1e-3) / 1e9
+    peak = float(pk["hbm_gbs"])
+    total_ms = sum(v["ms"] for v in prof.values())
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(gbs / peak, 4), "traffic": traffic_for(dom, n),
+            "kernel": dom, "avg_launch_ms": round(avg_ms, 4),
+            "algorithmic_bytes_per_launch": avg_bytes, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
+            "class_share": {k: round(v["ms"] / total_ms, 4) for k, v in prof.items() if total_ms > 0},
+            "class_gbs": {k: round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) for k, v in fine.items()}}
+
+
+# ---------------------------------------------------------------- arms
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    inputs = workload(args.n)
+    cyc = (14, 10, 9, 5)
+    res = None
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        res = oracle_sample(inputs, args.n, cyc)
+    wall = time.perf_counter() - t0
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / res["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded streamer shell, dielectric slab, smoothed ionisation source)",
+            "config": config(args), "impl": "reference",
+            "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_1809_08857_gb300 import build, mg
+
+    build.build()
+    mg.load()
+    n = args.n
+    h = 1.0 / n
+    inputs = workload(n)
+    rho = torch.from_numpy(inputs["rho"]).to(dev)
+    eps = torch.from_numpy(inputs["eps"]).to(dev)
+    S = torch.from_numpy(inputs["S"]).to(dev)
+    prec = mg.MG_PREC_MIXED if args.precision == "mixed" else mg.MG_PREC_FP64
+    solver = mg.Solver((n, n, n), h, eps_r=eps, precision=prec, inner_cycles=args.inner_cycles)
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
+    psi = [torch.zeros_like(phi) for _ in range(3)]
+    cycles = [0, 0, 0, 0]
+
+    def step():
+        phi.zero_()
+        for p in psi:
+            p.zero_()
+        sp = solver.solve_poisson(rho, phi, TOL)
+        sh = solver.solve_helmholtz_batch(S, psi, KAPPAS, TOL)
+        cycles[:] = [sp["cycles"]] + [s["cycles"] for s in sh]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    solver.profile(True)
+    l0 = mg.launch_count()
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = mg.launch_count() - l0
+    prof = solver.profile_read(reset=True)
+    solver.profile(False)
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * 1e3 / ms_per_step
+
+    # end to end through host buffers (pinned), copies inside the timed region
+    rho_h = torch.from_numpy(inputs["rho"]).pin_memory()
+    S_h = torch.from_numpy(inputs["S"]).pin_memory()
+    out_h = [torch.empty((n, n, n), dtype=torch.float64).pin_memory() for _ in range(4)]
+    rho_d, S_d = torch.empty_like(rho), torch.empty_like(S)
+
+    def e2e_step():
+        rho_d.copy_(rho_h, non_blocking=True)
+        S_d.copy_(S_h, non_blocking=True)
+        phi.zero_()
+        for p in psi:
+            p.zero_()
+        solver.solve_poisson(rho_d, phi, TOL)
+        solver.solve_helmholtz_batch(S_d, psi, KAPPAS, TOL)
+        for o, d in zip(out_h, [phi] + psi):
+            o.copy_(d, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    cells = n ** 3
+    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * cells,
+           "d2h_bytes_per_step": 4 * 8 * cells}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (FP32 V-cycles in FP64 refinement)" if prec else "f64",
+            "data": "synthetic (seeded streamer shell, dielectric slab, smoothed ionisation source)",
+            "config": config(args), "clocks": clk.summary(), "e2e": e2e,
+            "gpu_launches": launches, "cycles_per_problem": cycles,
+            "roofline": roofline(prof, n), "kernel_profile": prof}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = oracle_sample(inputs, n, cycles)
+        line["cpu_baseline"] = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

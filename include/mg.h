@@ -1,0 +1,207 @@
+/*
+ * mg.h -- C ABI of libmg.so: GB300 (sm_103a) geometric multigrid for the two
+ * elliptic equations of Marskar, "Adaptive multiscale methods for 3D streamer
+ * discharges in air" (arXiv:1809.08857):
+ *
+ *   Poisson (Sec. 2, Eq. 2, with a cell-wise relative permittivity eps_r):
+ *       -div(eps_r grad phi) = rho / eps0
+ *   Radiative transfer in the Helmholtz form of Eq. 3, one photon group j:
+ *       (kappa_j^2 - lap) Psi_j = S
+ *
+ * discretised with the second-order cell-centred finite-volume scheme of
+ * Sec. 2, items (ii)-(iii), and solved with geometric multigrid and red-black
+ * Gauss-Seidel smoothing (Sec. 2, item (ii)).
+ *
+ * Conventions shared by every entry point
+ *  - Grid: nx*ny*nz cells of side h; arrays are contiguous, x fastest:
+ *    index (k*ny + j)*nx + i.  Faces are numbered -x,+x,-y,+y,-z,+z.
+ *  - Array arguments are DEVICE pointers owned by the caller, FP64, unless the
+ *    comment says otherwise.  The library never frees them and keeps none of
+ *    them after the call returns, except that mg_create copies eps_r, mask and
+ *    mask_value into its own storage.
+ *  - Work is enqueued on the context's CUDA stream (mg_create / mg_set_stream).
+ *    A solve synchronises that stream because its convergence test reads the
+ *    residual norm on the host; on return the outputs are complete.
+ *  - Discretisation readings (the paper leaves these open):
+ *      face between two free cells: harmonic mean of eps_r;
+ *      face towards an electrode (masked) cell: the free cell's eps_r, with
+ *        the electrode value held at the masked cell's centre;
+ *      Dirichlet domain face with value g: ghost value 2g - u (distance h/2);
+ *      Neumann domain face: homogeneous (zero flux).
+ *  - Convergence: relative residual ||b - A u||_2 / ||b||_2 over free cells,
+ *    where b holds rho/eps0 plus the boundary and electrode lifts, i.e. ||b||
+ *    is the residual norm of the zero guess.
+ *  - Every function returns an mg_status; no C++ exception crosses the ABI.
+ *    On error, mg_last_error() gives a message for the calling thread.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx; /* opaque, library-owned */
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = 1,   /* bad pointer, size, option or boundary spec */
+  MG_ERR_CUDA = 2,          /* a CUDA runtime call failed (see mg_last_error) */
+  MG_ERR_OOM = 3,           /* device allocation failed */
+  MG_ERR_NOT_CONVERGED = 4, /* max_cycles reached; outputs hold the last iterate */
+  MG_ERR_NONFINITE = 5,     /* NaN/Inf in the input or the residual */
+  MG_ERR_UNSUPPORTED = 6    /* valid request this build does not implement */
+} mg_status;
+
+typedef enum { MG_BC_DIRICHLET = 0, MG_BC_NEUMANN = 1 } mg_bc_kind;
+
+/* Uniform box: nx*ny*nz cells of side h, lower corner at origin. */
+typedef struct {
+  int nx, ny, nz;
+  double h;
+  double origin[3];
+} mg_grid;
+
+/* Boundary conditions of the Poisson problem, per face (-x,+x,-y,+y,-z,+z):
+ * kind[f] is an mg_bc_kind; value[f] is the Dirichlet potential (ignored for
+ * Neumann, which is homogeneous).  The Helmholtz problems always use
+ * homogeneous Dirichlet on every face and on electrode cells (free-space
+ * absorption; the paper leaves their boundary conditions open, Sec. 2 (iii)). */
+typedef struct {
+  int kind[6];
+  double value[6];
+} mg_bc;
+
+typedef enum { MG_PREC_FP64 = 0, MG_PREC_MIXED = 1 } mg_precision;
+
+/* Solver options.  Zero-initialised fields take the defaults shown. */
+typedef struct {
+  int nu1;          /* pre-smoothing red-black sweeps per level (2) */
+  int nu2;          /* post-smoothing sweeps (2) */
+  int max_cycles;   /* cap on V-cycles (FP64) or outer refinement steps (100) */
+  int precision;    /* mg_precision: FP64 V-cycles, or FP32 V-cycles inside
+                       FP64 iterative refinement (MG_PREC_FP64 = 0) */
+  int inner_cycles; /* FP32 V-cycles per refinement step in mixed mode (1) */
+  int reserved[3];  /* must be zero */
+} mg_options;
+
+/* Per-solve statistics.  hist[c] is the relative residual after c cycles
+ * (hist[0] = initial guess), for c < 64. */
+typedef struct {
+  int cycles;       /* V-cycles (FP64) or refinement steps (mixed) taken */
+  int converged;    /* 1 if rel_resid <= tol */
+  double rel_resid; /* final ||b - A u|| / ||b||, evaluated in FP64 */
+  double time_ms;   /* device time of the solve (CUDA events) */
+  double hist[64];
+} mg_stats;
+
+/* Fill *opt with the defaults. */
+void mg_default_options(mg_options* opt);
+
+/*
+ * mg_create -- build the multigrid hierarchy for one grid.
+ *   grid       box description (h > 0, every n >= 1).
+ *   eps_r      device, nx*ny*nz FP64 relative permittivity (> 0) of each
+ *              cell, or NULL for 1 everywhere.  Copied.
+ *   mask       device, nx*ny*nz uint8: nonzero marks an electrode cell whose
+ *              potential is fixed (Dirichlet at its centre), or NULL.  Copied.
+ *   mask_value device, nx*ny*nz FP64 potential of each electrode cell (read
+ *              where mask != 0), or NULL for 0.  Copied.
+ *   bc         Poisson boundary conditions (see mg_bc).  At least one
+ *              Dirichlet face or electrode cell is required for the Poisson
+ *              problem to be nonsingular.
+ *   opt        options, or NULL for defaults.
+ *   cuda_stream  cudaStream_t to enqueue on (NULL = legacy default stream).
+ *   out        receives the context; free it with mg_destroy.
+ * Setup is the operator assembly of Sec. 2 items (ii)-(iii) (face
+ * coefficients, coarse grids by 2x coarsening, coarsest-grid inverse).
+ */
+mg_status mg_create(const mg_grid* grid, const double* eps_r, const uint8_t* mask,
+                    const double* mask_value, const mg_bc* bc, const mg_options* opt,
+                    void* cuda_stream, mg_ctx** out);
+
+/*
+ * mg_solve_poisson -- solve Eq. 2: -div(eps_r grad phi) = rho/eps0.
+ *   rho  device, nx*ny*nz FP64 space charge density (C/m^3).
+ *   phi  device, nx*ny*nz FP64; in: initial guess, out: solution.  Electrode
+ *        cells are overwritten with their mask values.
+ *   tol  stop when the relative residual <= tol (e.g. 1e-10).
+ *   stats  nullable; receives cycles, residual history and device time.
+ * Returns MG_ERR_NOT_CONVERGED (phi holds the last iterate) if max_cycles is
+ * reached, MG_ERR_NONFINITE if the residual is NaN/Inf.
+ */
+mg_status mg_solve_poisson(mg_ctx* ctx, const double* rho, double* phi, double tol,
+                           mg_stats* stats);
+
+/*
+ * mg_solve_helmholtz_batch -- the three radiative-transfer solves of Eq. 3 in
+ * Helmholtz form, (kappa_j^2 - lap) Psi_j = S for j = 0, 1, 2, with Psi = 0 on
+ * every domain face and on electrode cells.  The paper's form
+ * kappa Psi - div(grad Psi / (3 kappa)) = eta/c maps onto it by multiplying by
+ * 3 kappa (kappa_j here = sqrt(3) kappa_paper, S = 3 kappa eta / c).
+ *   S      device, nx*ny*nz FP64 source shared by the three groups.
+ *   psi    three device pointers, nx*ny*nz FP64 each; in: guess, out: solution.
+ *   kappa  host, three inverse absorption lengths (1/length, > 0).
+ *   tol    relative residual target per group.
+ *   stats  nullable, host array of three.
+ */
+mg_status mg_solve_helmholtz_batch(mg_ctx* ctx, const double* S, double* const psi[3],
+                                   const double kappa[3], double tol, mg_stats stats[3]);
+
+/* ---- instrumentation ------------------------------------------------------
+ * Kernel classes of the fine (finest-level) launches: red-black smoothing,
+ * fused residual + restriction, prolongation + correction, the FP64
+ * refinement residual (with the solution update), and everything on coarser
+ * levels (coarse).  With profiling enabled every fine-level launch is
+ * bracketed by CUDA events on the context's stream; `bytes` accumulates the
+ * algorithmic bytes of each launch (each operand read once, each result
+ * written once).  This is instrumentation of the solver, not part of the
+ * method. */
+typedef enum {
+  MG_KCLASS_SMOOTH = 0,
+  MG_KCLASS_RESTRICT = 1,
+  MG_KCLASS_PROLONG = 2,
+  MG_KCLASS_RESID64 = 3,
+  MG_KCLASS_COARSE = 4,
+  MG_KCLASS_COUNT = 5
+} mg_kclass;
+
+typedef struct {
+  long long launches; /* kernel launches of this class */
+  double ms;          /* summed event-timed duration (fine-level classes) */
+  double bytes;       /* summed algorithmic bytes (fine-level classes) */
+} mg_kprof;
+
+/* Turn per-launch event timing on (1) or off (0); resets the counters. */
+mg_status mg_profile_enable(mg_ctx* ctx, int enable);
+
+/* Copy the per-class counters (MG_KCLASS_COUNT entries) into out; reset them
+ * if reset != 0. */
+mg_status mg_profile_read(mg_ctx* ctx, mg_kprof* out, int reset);
+
+/* Process-wide number of kernel launches issued by libmg so far. */
+long long mg_launch_count(void);
+
+/* Rebind the context to another CUDA stream (cudaStream_t, NULL = legacy). */
+mg_status mg_set_stream(mg_ctx* ctx, void* cuda_stream);
+
+/* Number of multigrid levels and the dimensions of level l (for tests). */
+mg_status mg_level_info(const mg_ctx* ctx, int level, int* nlevels, int dims[3]);
+
+/* Free the context and all library-owned device memory.  NULL is a no-op. */
+void mg_destroy(mg_ctx* ctx);
+
+/* Static description of a status code. */
+const char* mg_error_string(mg_status status);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char* mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H */

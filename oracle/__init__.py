@@ -146,7 +146,7 @@ class Problem:
         return lib.or_rhs_norm(ctypes.byref(self.g), self.alpha, _p(self.beta), _p(self.mask),
                                _p(_f64(f)), _p(_f64(u)))
 
-    def solve(self, f, u0=None, tol=1e-13, max_cycles=200, nu1=2, nu2=2):
+    def solve(self, f, u0=None, tol=1e-13, max_cycles=1000, nu1=2, nu2=2):
         """Multigrid V(nu1,nu2) solve to ``tol`` or to the round-off floor.
 
         Returns (u, cycles, final relative residual, history)."""

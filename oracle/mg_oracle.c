@@ -397,10 +397,10 @@ int or_solve(const or_grid* g, double alpha, const double* beta, const uint8_t* 
     ++cyc;
     double nrel = sqrt(or_residual(g, alpha, beta, mask, f, u, NULL, 0)) / bnorm;
     if (hist) hist[cyc] = nrel;
-    /* round-off floor: the residual no longer drops by a useful factor */
-    stalls = nrel > 0.5 * rel ? stalls + 1 : 0;
+    /* round-off floor: three cycles in a row without a 1% reduction */
+    stalls = nrel > 0.99 * rel ? stalls + 1 : 0;
     rel = nrel;
-    if (stalls >= 2) break;
+    if (stalls >= 3) break;
   }
   if (rel_out) *rel_out = rel;
   mg_free(&M);

@@ -1,0 +1,142 @@
+// Internal declarations of libmg: operator views handed to the kernels and
+// the launch wrappers.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mg {
+
+// Process-wide count of kernel launches issued by the launch wrappers.
+long long launch_count();
+void add_launches(long long k);
+
+// Face order -x,+x,-y,+y,-z,+z.
+struct Box {
+  int nx, ny, nz;
+  __host__ __device__ long long n() const { return (long long)nx * ny * nz; }
+};
+
+// Small fixed arrays passed to kernels by value.
+struct Dir6 {
+  uint8_t d[6];
+};
+struct Val6 {
+  double v[6];
+};
+
+// FP64 view of the level operator
+//   (A u)_c = (alpha + D_c) u_c - sum_{free in-box nb} w_f u_nb
+// with w_f already divided by h^2.  cx[c] holds the weight of the face
+// between c and c - e_x (likewise cy, cz); D_c is the sum of all six face
+// weights of c, including Dirichlet domain faces (2 beta_c / h^2) and faces
+// towards electrode cells (beta_c / h^2); D_c < 0 marks an electrode cell.
+// With cx == nullptr the operator has beta = 1: interior weights ih2, domain
+// Dirichlet faces 2 ih2, and electrode cells come from `mask`.
+struct Op64 {
+  const double* cx;
+  const double* cy;
+  const double* cz;
+  const double* D;
+  const uint8_t* mask;
+  Box b;
+  double ih2;
+  uint8_t dir[6];  // 1 = Dirichlet domain face
+};
+
+// FP32 view of a level in red/black split storage: colour c = (i+j+k)&1,
+// packed row width W = (nx+1)/2, cell (i,j,k) at ((k*ny + j)*W + (i>>1)) of
+// colour c.  beta[c] (nullable => beta = 1 everywhere, no electrode cells)
+// holds the cell coefficient, with beta < 0 marking an electrode cell.
+struct Split32 {
+  const float* beta[2];
+  Box b;
+  int W;
+  float ih2;
+  uint8_t dir[6];
+};
+
+struct Ptr2 {
+  const float* p[2];
+};
+struct MPtr2 {
+  float* p[2];
+};
+
+// Arguments of the fused FP64 refinement step (see mg_ir.cu).
+struct IrArgs {
+  Op64 op;
+  double alpha;
+  const double* rhs;   // b = rhs * rhs_scale + lifts
+  double rhs_scale;
+  int lift;            // add Dirichlet-face lifts 2 beta_c g / h^2
+  const double* beta0; // natural FP64 beta for the lifts (nullable = 1)
+  Val6 bval;           // Dirichlet face values
+  const double* u_in;  // natural FP64 iterate
+  double* u_out;       // u_in + e (nullable: not written)
+  const float* e[2];   // split FP32 correction (nullable: zero)
+  float* r[2];         // split FP32 residual out (nullable)
+  int W;               // packed row width of e and r
+  double* partial;     // per-CTA sums of r^2
+  int zchunk;          // set by the launcher
+};
+
+// ---- setup ---------------------------------------------------------------
+void launch_faces64(const double* beta, const uint8_t* mask, Box b, double ih2,
+                    const uint8_t dir[6], double* cx, double* cy, double* cz, double* D,
+                    cudaStream_t s);
+void launch_coarsen(const double* beta_f, const uint8_t* mask_f, Box fb, double* beta_c,
+                    uint8_t* mask_c, cudaStream_t s);
+void launch_assemble_dense(Op64 op, double alpha, double* M, cudaStream_t s);
+void launch_gj_invert(double* M, int n, double* rowp, double* colp, cudaStream_t s);
+
+// ---- solve ---------------------------------------------------------------
+// b = f * scale + Dirichlet-face lifts (2 beta_c g / h^2); 0 on electrode cells.
+void launch_rhs64(const double* f, double scale, const double* beta, const uint8_t* mask,
+                  Box b, double ih2, const uint8_t dir[6], const double bval[6], double* out,
+                  cudaStream_t s);
+// u[c] = value[c] (or 0 if value == nullptr) on electrode cells.
+void launch_set_masked(const uint8_t* mask, const double* value, long long n, double* u,
+                       cudaStream_t s);
+// Red-black Gauss-Seidel half-sweep of colour (i+j+k)&1 == color.
+void launch_rbgs64(const Op64& op, double alpha, const double* f, double* u, int color,
+                   cudaStream_t s);
+
+// r = f - A u averaged over 8 children into fc; uc (nullable) zeroed.
+void launch_resid_restrict64(const Op64& op, double alpha, const double* f, const double* u,
+                             double* fc, double* uc, cudaStream_t s);
+
+// uf += trilinear prolongation of ec (coarse box = fine/2); electrode fine
+// cells untouched.  dir[] selects the reflection sign of coarse ghosts.
+void launch_prolong64(const Op64& fop, const double* ec, double* uf, cudaStream_t s);
+
+// Residual r = f - A u of the level (no restriction); returns nothing.
+void launch_resid64(const Op64& op, double alpha, const double* f, const double* u, double* r,
+                    cudaStream_t s);
+
+// u += Minv r over all n cells of the coarsest level (Minv FP64, rows of
+// electrode cells zero).
+void launch_dense_apply64(const double* Minv, int n, const double* r, double* u, cudaStream_t s);
+
+
+// sum of partial[0..n) into *out (single block, fixed order).
+void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s);
+
+// ---- FP32 split-storage inner V-cycle (mg_split32.cu) -----------------------
+void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
+                         const float* uo, bool zero_other, cudaStream_t s);
+void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
+                              MPtr2 fc, MPtr2 uc, cudaStream_t s);
+void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s);
+void launch_resid32s(const Split32& op, float alpha, Ptr2 f, Ptr2 u, MPtr2 r, cudaStream_t s);
+void launch_dense_apply32s(const Split32& op, const double* Minv, Ptr2 r, MPtr2 u,
+                           cudaStream_t s);
+void launch_split_beta(const double* beta, const uint8_t* mask, const Split32& op, MPtr2 out,
+                       cudaStream_t s);
+
+// ---- fused FP64 refinement step (mg_ir.cu) ---------------------------------
+// zero_free: norm of b (free cells of u read as 0).
+void launch_ir_fused(const IrArgs& a, bool zero_free, cudaStream_t s);
+int ir_partials(const Box& b);
+
+}  // namespace mg

@@ -1,0 +1,162 @@
+// FP64 iterative-refinement step of the mixed-precision solve:
+//
+//     u_new = u + e            (FP32 correction from the inner V-cycle)
+//     r     = b - A u_new      (FP64, b = rhs * scale + Dirichlet lifts)
+//     r32   = (float) r        (right-hand side of the next inner V-cycle)
+//     ||r||^2 partial sums per CTA
+//
+// in one pass.  The operator and lifts follow Sec. 2 items (ii)-(iii) of
+// arXiv:1809.08857 (second-order cell-centred finite volumes for Eqs. 2-3).
+//
+// On GB300 the FP64 pipe issues about 1/57 of the FP32 rate, so this kernel
+// is bounded by FP64 arithmetic, not by HBM.  It therefore forms u + e once
+// per cell: each CTA marches along z through a 32 x 8 (x, y) tile, keeping
+// three planes of u + e (with a one-cell halo) in shared memory, and every
+// stencil neighbour is read from there.
+#include "mg_internal.h"
+
+namespace mg {
+
+namespace {
+
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int PX = TX + 2, PY = TY + 2, PN = PX * PY;
+
+__device__ __forceinline__ bool masked64(const Op64& op, long long c) {
+  if (op.D) return op.D[c] < 0.0;
+  return op.mask != nullptr && op.mask[c] != 0;
+}
+
+template <bool HasE, bool ZeroFree>
+__device__ __forceinline__ double load_cell(const IrArgs& a, int i, int j, int k) {
+  if (i < 0 || j < 0 || k < 0 || i >= a.op.b.nx || j >= a.op.b.ny || k >= a.op.b.nz) return 0.0;
+  const long long c = ((long long)k * a.op.b.ny + j) * a.op.b.nx + i;
+  if (ZeroFree) return masked64(a.op, c) ? a.u_in[c] : 0.0;
+  double v = a.u_in[c];
+  if (HasE) {
+    const long long t = ((long long)k * a.op.b.ny + j) * a.W + (i >> 1);
+    v += (double)(((i + j + k) & 1) ? a.e[1][t] : a.e[0][t]);
+  }
+  return v;
+}
+
+template <bool HasE, bool ZeroFree>
+__global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
+  __shared__ double pl[3][PN];
+  __shared__ double red[NT / 32];
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = blockIdx.z * a.zchunk;
+  const int z1 = min(a.op.b.nz, z0 + a.zchunk);
+  const int nx = a.op.b.nx, ny = a.op.b.ny, nz = a.op.b.nz;
+  const long long sy = nx, sz = (long long)nx * ny;
+  const int i = x0 + tx, j = y0 + ty;
+  const bool own = i < nx && j < ny;
+
+  auto load_plane = [&](int buf, int k) {
+    for (int q = threadIdx.x; q < PN; q += NT) {
+      const int lx = q % PX, ly = q / PX;
+      pl[buf][q] = load_cell<HasE, ZeroFree>(a, x0 + lx - 1, y0 + ly - 1, k);
+    }
+  };
+  load_plane(0, z0 - 1);
+  load_plane(1, z0);
+  int b0 = 0, b1 = 1, b2 = 2;
+  double ss = 0.0;
+  for (int k = z0; k < z1; ++k) {
+    load_plane(b2, k + 1);
+    __syncthreads();
+    if (own) {
+      const long long c = ((long long)k * ny + j) * nx + i;
+      const int q = (ty + 1) * PX + (tx + 1);
+      double r = 0.0;
+      const double uc = pl[b1][q];
+      if (!masked64(a.op, c)) {
+        double b = a.rhs[c] * a.rhs_scale;
+        if (a.lift) {
+          const double bc = a.beta0 ? a.beta0[c] : 1.0;
+          const double l = 2.0 * bc * a.op.ih2;
+          if (i == 0 && a.op.dir[0]) b += l * a.bval.v[0];
+          if (i == nx - 1 && a.op.dir[1]) b += l * a.bval.v[1];
+          if (j == 0 && a.op.dir[2]) b += l * a.bval.v[2];
+          if (j == ny - 1 && a.op.dir[3]) b += l * a.bval.v[3];
+          if (k == 0 && a.op.dir[4]) b += l * a.bval.v[4];
+          if (k == nz - 1 && a.op.dir[5]) b += l * a.bval.v[5];
+        }
+        double diag, off;
+        if (a.op.cx) {
+          double o = 0.0;
+          if (i > 0) o += a.op.cx[c] * pl[b1][q - 1];
+          if (i < nx - 1) o += a.op.cx[c + 1] * pl[b1][q + 1];
+          if (j > 0) o += a.op.cy[c] * pl[b1][q - PX];
+          if (j < ny - 1) o += a.op.cy[c + sy] * pl[b1][q + PX];
+          if (k > 0) o += a.op.cz[c] * pl[b0][q];
+          if (k < nz - 1) o += a.op.cz[c + sz] * pl[b2][q];
+          diag = a.op.D[c];
+          off = o;
+        } else {
+          // beta = 1: the off-diagonal sum is a plain neighbour sum
+          double o = 0.0, d = 0.0;
+          if (i > 0) { d += 1.0; o += pl[b1][q - 1]; } else if (a.op.dir[0]) d += 2.0;
+          if (i < nx - 1) { d += 1.0; o += pl[b1][q + 1]; } else if (a.op.dir[1]) d += 2.0;
+          if (j > 0) { d += 1.0; o += pl[b1][q - PX]; } else if (a.op.dir[2]) d += 2.0;
+          if (j < ny - 1) { d += 1.0; o += pl[b1][q + PX]; } else if (a.op.dir[3]) d += 2.0;
+          if (k > 0) { d += 1.0; o += pl[b0][q]; } else if (a.op.dir[4]) d += 2.0;
+          if (k < nz - 1) { d += 1.0; o += pl[b2][q]; } else if (a.op.dir[5]) d += 2.0;
+          diag = d * a.op.ih2;
+          off = o * a.op.ih2;
+        }
+        r = ZeroFree ? b + off : b - ((diag + a.alpha) * uc - off);
+      }
+      if (a.u_out) a.u_out[c] = uc;
+      if (a.r[0]) (((i + j + k) & 1) ? a.r[1] : a.r[0])[((long long)k * ny + j) * a.W + (i >> 1)] = (float)r;
+      ss += r * r;
+    }
+    __syncthreads();
+    const int t = b0;
+    b0 = b1;
+    b1 = b2;
+    b2 = t;
+  }
+  // CTA sum of r^2
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0)
+      a.partial[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+}  // namespace
+
+static dim3 ir_grid(const Box& b, int* zchunk) {
+  const int gx = (b.nx + TX - 1) / TX, gy = (b.ny + TY - 1) / TY;
+  // enough CTAs for every SM (152 on GB300) several times over, long z runs
+  int zc = b.nz;
+  while (zc > 16 && (long long)gx * gy * ((b.nz + zc - 1) / zc) < 4 * 152 * 4) zc = (zc + 1) / 2;
+  *zchunk = zc;
+  return dim3(gx, gy, (b.nz + zc - 1) / zc);
+}
+
+int ir_partials(const Box& b) {
+  int zc;
+  dim3 g = ir_grid(b, &zc);
+  return (int)(g.x * g.y * g.z);
+}
+
+void launch_ir_fused(const IrArgs& args, bool zero_free, cudaStream_t s) {
+  IrArgs a = args;
+  dim3 g = ir_grid(a.op.b, &a.zchunk);
+  const bool has_e = a.e[0] != nullptr;
+  if (zero_free) k_ir_fused<false, true><<<g, NT, 0, s>>>(a);
+  else if (has_e) k_ir_fused<true, false><<<g, NT, 0, s>>>(a);
+  else k_ir_fused<false, false><<<g, NT, 0, s>>>(a);
+  add_launches(1);
+}
+
+}  // namespace mg

@@ -1,0 +1,263 @@
+"""ctypes binding of libmg.so (include/mg.h).
+
+Argument marshalling only: torch tensors are passed as raw device pointers and
+the current torch CUDA stream is handed to the library.  Every step of the
+solve runs in libmg's CUDA kernels; there is no CPU fallback, and loading
+fails loudly when libmg.so is missing.
+"""
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmg.so")
+
+MG_OK = 0
+MG_ERR_INVALID_ARG = 1
+MG_ERR_CUDA = 2
+MG_ERR_OOM = 3
+MG_ERR_NOT_CONVERGED = 4
+MG_ERR_NONFINITE = 5
+MG_ERR_UNSUPPORTED = 6
+
+MG_BC_DIRICHLET = 0
+MG_BC_NEUMANN = 1
+MG_PREC_FP64 = 0
+MG_PREC_MIXED = 1
+
+EXPORTS = [
+    "mg_default_options", "mg_create", "mg_solve_poisson", "mg_solve_helmholtz_batch",
+    "mg_set_stream", "mg_level_info", "mg_destroy", "mg_error_string", "mg_last_error",
+    "mg_profile_enable", "mg_profile_read", "mg_launch_count",
+]
+
+KCLASSES = ["smooth", "restrict", "prolong", "resid64", "coarse"]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("h", ctypes.c_double), ("origin", ctypes.c_double * 3)]
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int * 6), ("value", ctypes.c_double * 6)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
+                ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_resid", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("hist", ctypes.c_double * 64)]
+
+    def as_dict(self):
+        n = min(self.cycles + 1, 64)
+        return {"cycles": self.cycles, "converged": bool(self.converged),
+                "rel_resid": self.rel_resid, "time_ms": self.time_ms,
+                "hist": list(self.hist[:n])}
+
+
+class KProf(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class MGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libmg status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libmg.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libmg.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    lib.mg_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.mg_default_options.restype = None
+    lib.mg_create.argtypes = [ctypes.POINTER(Grid), P, P, P, ctypes.POINTER(BC),
+                              ctypes.POINTER(Options), P, ctypes.POINTER(P)]
+    lib.mg_create.restype = ctypes.c_int
+    lib.mg_solve_poisson.argtypes = [P, P, P, ctypes.c_double, ctypes.POINTER(Stats)]
+    lib.mg_solve_poisson.restype = ctypes.c_int
+    lib.mg_solve_helmholtz_batch.argtypes = [P, P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.c_double, ctypes.POINTER(Stats)]
+    lib.mg_solve_helmholtz_batch.restype = ctypes.c_int
+    lib.mg_set_stream.argtypes = [P, P]
+    lib.mg_set_stream.restype = ctypes.c_int
+    lib.mg_level_info.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]
+    lib.mg_level_info.restype = ctypes.c_int
+    lib.mg_destroy.argtypes = [P]
+    lib.mg_destroy.restype = None
+    lib.mg_error_string.argtypes = [ctypes.c_int]
+    lib.mg_error_string.restype = ctypes.c_char_p
+    lib.mg_last_error.argtypes = []
+    lib.mg_last_error.restype = ctypes.c_char_p
+    lib.mg_profile_enable.argtypes = [P, ctypes.c_int]
+    lib.mg_profile_enable.restype = ctypes.c_int
+    lib.mg_profile_read.argtypes = [P, ctypes.POINTER(KProf), ctypes.c_int]
+    lib.mg_profile_read.restype = ctypes.c_int
+    lib.mg_launch_count.argtypes = []
+    lib.mg_launch_count.restype = ctypes.c_longlong
+    _lib = lib
+    return lib
+
+
+def _check(status, allow=()):
+    if status == MG_OK or status in allow:
+        return status
+    lib = load()
+    raise MGError(status, f"{lib.mg_error_string(status).decode()}: {lib.mg_last_error().decode()}")
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def launch_count():
+    """Process-wide number of kernel launches issued by libmg."""
+    return load().mg_launch_count()
+
+
+def default_options():
+    opt = Options()
+    load().mg_default_options(ctypes.byref(opt))
+    return opt
+
+
+class Solver:
+    """One grid with its multigrid hierarchy (mg_create).
+
+    shape: (nz, ny, nx); h: cell size; eps_r, mask, mask_value: CUDA tensors
+    of that shape (float64, uint8, float64) or None; bc_kind/bc_value: the
+    Poisson boundary conditions per face (-x,+x,-y,+y,-z,+z).
+    """
+
+    def __init__(self, shape, h, eps_r=None, mask=None, mask_value=None,
+                 bc_kind=(1, 1, 1, 1, 0, 0), bc_value=(0, 0, 0, 0, 0, 1),
+                 precision=MG_PREC_FP64, nu1=2, nu2=2, max_cycles=100, inner_cycles=1,
+                 stream=None):
+        lib = load()
+        nz, ny, nx = (int(s) for s in shape)
+        self.shape = (nz, ny, nx)
+        g = Grid(nx, ny, nz, float(h), (ctypes.c_double * 3)(0.0, 0.0, 0.0))
+        bc = BC((ctypes.c_int * 6)(*[int(k) for k in bc_kind]),
+                (ctypes.c_double * 6)(*[float(v) for v in bc_value]))
+        opt = Options(nu1, nu2, max_cycles, precision, inner_cycles, (ctypes.c_int * 3)(0, 0, 0))
+        for t in (eps_r, mask, mask_value):
+            if t is not None and tuple(t.shape) != self.shape:
+                raise ValueError("coefficient shape mismatch")
+        ctx = ctypes.c_void_p()
+        st = lib.mg_create(ctypes.byref(g), _ptr(eps_r, torch.float64), _ptr(mask, torch.uint8),
+                           _ptr(mask_value, torch.float64), ctypes.byref(bc), ctypes.byref(opt),
+                           _stream_handle(stream), ctypes.byref(ctx))
+        _check(st)
+        self._ctx = ctx
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.mg_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream=None):
+        _check(self._lib.mg_set_stream(self._ctx, _stream_handle(stream)))
+
+    def levels(self):
+        n = ctypes.c_int()
+        out = []
+        _check(self._lib.mg_level_info(self._ctx, 0, ctypes.byref(n), None))
+        for l in range(n.value):
+            d = (ctypes.c_int * 3)()
+            _check(self._lib.mg_level_info(self._ctx, l, None, d))
+            out.append((d[2], d[1], d[0]))
+        return out
+
+    def profile(self, enable=True):
+        """Bracket every fine-level kernel launch with CUDA events (instrumentation)."""
+        _check(self._lib.mg_profile_enable(self._ctx, 1 if enable else 0))
+
+    def profile_read(self, reset=False):
+        """Per kernel class: launches, event-timed ms, algorithmic bytes."""
+        arr = (KProf * len(KCLASSES))()
+        _check(self._lib.mg_profile_read(self._ctx, arr, 1 if reset else 0))
+        return {k: {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
+                for i, k in enumerate(KCLASSES)}
+
+    def _check_field(self, t):
+        if tuple(t.shape) != self.shape:
+            raise ValueError(f"field shape {tuple(t.shape)} != grid {self.shape}")
+
+    def solve_poisson(self, rho, phi, tol=1e-10, raise_on_nonconvergence=True):
+        """Solve Eq. 2 in place on phi (CUDA float64).  Returns stats dict."""
+        self._check_field(rho)
+        self._check_field(phi)
+        self.set_stream()
+        st = Stats()
+        status = self._lib.mg_solve_poisson(self._ctx, _ptr(rho, torch.float64),
+                                            _ptr(phi, torch.float64), float(tol), ctypes.byref(st))
+        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        d = st.as_dict()
+        d["status"] = status
+        return d
+
+    def solve_helmholtz_batch(self, S, psi, kappa, tol=1e-10, raise_on_nonconvergence=True):
+        """Solve the three Helmholtz problems of Eq. 3 in place on psi[0..2]."""
+        self._check_field(S)
+        if len(psi) != 3 or len(kappa) != 3:
+            raise ValueError("need three psi arrays and three kappas")
+        for p in psi:
+            self._check_field(p)
+        self.set_stream()
+        ptrs = (ctypes.c_void_p * 3)(*[p.data_ptr() for p in psi])
+        for p in psi:
+            _ptr(p, torch.float64)
+        kap = (ctypes.c_double * 3)(*[float(k) for k in kappa])
+        st = (Stats * 3)()
+        status = self._lib.mg_solve_helmholtz_batch(self._ctx, _ptr(S, torch.float64), ptrs, kap,
+                                                    float(tol), st)
+        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        return [s.as_dict() for s in st]
+
+    # ---- host-buffer convenience (end-to-end path) -------------------------
+
+    def solve_poisson_host(self, rho_host, phi_host, tol=1e-10):
+        """Host (pinned) buffers in and out: H2D copy, device solve, D2H copy."""
+        dev = torch.device("cuda")
+        rho = rho_host.to(dev, non_blocking=True)
+        phi = phi_host.to(dev, non_blocking=True)
+        st = self.solve_poisson(rho, phi, tol)
+        phi_host.copy_(phi, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return st

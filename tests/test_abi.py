@@ -1,0 +1,80 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads
+and exports every function include/mg.h declares, and argument validation
+rejects bad input before any device work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1809_08857_gb300 import build, mg
+
+    build.build()
+    return mg.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "mg_create" in names and "mg_solve_poisson" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_lists_every_export():
+    from paper_1809_08857_gb300 import mg
+
+    assert sorted(mg.EXPORTS) == sorted(n for n in declared_functions())
+
+
+def test_create_rejects_bad_arguments_without_gpu(lib):
+    from paper_1809_08857_gb300 import mg
+
+    ctx = ctypes.c_void_p()
+    bc = mg.BC((ctypes.c_int * 6)(1, 1, 1, 1, 0, 0), (ctypes.c_double * 6)(0, 0, 0, 0, 0, 1))
+    bad = mg.Grid(0, 8, 8, 0.1, (ctypes.c_double * 3)())
+    assert lib.mg_create(ctypes.byref(bad), None, None, None, ctypes.byref(bc), None, None,
+                         ctypes.byref(ctx)) == mg.MG_ERR_INVALID_ARG
+    assert b"sizes" in lib.mg_last_error()
+    good = mg.Grid(8, 8, 8, -1.0, (ctypes.c_double * 3)())
+    assert lib.mg_create(ctypes.byref(good), None, None, None, ctypes.byref(bc), None, None,
+                         ctypes.byref(ctx)) == mg.MG_ERR_INVALID_ARG
+    badbc = mg.BC((ctypes.c_int * 6)(1, 1, 7, 1, 0, 0), (ctypes.c_double * 6)())
+    good = mg.Grid(8, 8, 8, 0.1, (ctypes.c_double * 3)())
+    assert lib.mg_create(ctypes.byref(good), None, None, None, ctypes.byref(badbc), None, None,
+                         ctypes.byref(ctx)) == mg.MG_ERR_INVALID_ARG
+    opt = mg.Options(2, 2, 10, 9, 1, (ctypes.c_int * 3)())
+    assert lib.mg_create(ctypes.byref(good), None, None, None, ctypes.byref(bc), ctypes.byref(opt),
+                         None, ctypes.byref(ctx)) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_create(None, None, None, None, None, None, None, None) == mg.MG_ERR_INVALID_ARG
+
+
+def test_solve_rejects_null_context(lib):
+    from paper_1809_08857_gb300 import mg
+
+    assert lib.mg_solve_poisson(None, None, None, 1e-10, None) == mg.MG_ERR_INVALID_ARG
+    assert lib.mg_solve_helmholtz_batch(None, None, None, None, 1e-10, None) == mg.MG_ERR_INVALID_ARG
+    lib.mg_destroy(None)
+    assert lib.mg_error_string(mg.MG_ERR_NOT_CONVERGED) == b"not converged within max_cycles"
+
+
+def test_default_options(lib):
+    from paper_1809_08857_gb300 import mg
+
+    o = mg.default_options()
+    assert (o.nu1, o.nu2, o.max_cycles, o.precision, o.inner_cycles) == (2, 2, 100, 0, 1)
