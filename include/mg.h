@@ -185,6 +185,37 @@ mg_status mg_profile_read(mg_ctx* ctx, mg_kprof* out, int reset);
 /* Process-wide number of kernel launches issued by libmg so far. */
 long long mg_launch_count(void);
 
+/*
+ * mg_residual_norm_noalloc -- ||b - A u||_2 over free cells for a
+ * constant-coefficient problem (beta = 1: the Helmholtz operator, or the
+ * Poisson operator with eps_r = 1), computed without allocating any device
+ * memory.  The paper has no counterpart; this is a service entry point for
+ * callers that cannot call cudaMalloc during the call: codes whose device
+ * memory is already owned by their own pool allocator, and time-stepping
+ * loops that cannot take the device-wide synchronisation cudaMalloc/cudaFree
+ * may cause.
+ *   grid, bc   the box and its boundary conditions (Dirichlet values lift b).
+ *   alpha      zeroth-order coefficient (0 for Poisson, kappa^2 for Helmholtz).
+ *   rhs        device, nx*ny*nz FP64; b = rhs * rhs_scale + Dirichlet lifts
+ *              (rhs_scale = 1/eps0 turns a charge density into rho/eps0).
+ *   mask       device, nx*ny*nz uint8 electrode cells, or NULL.
+ *   u          device, nx*ny*nz FP64 iterate (electrode cells hold their values).
+ *   norm_out   device, one FP64: receives ||b - A u||_2.
+ *   cuda_stream  stream to enqueue on (NULL = legacy default stream).
+ * Work is enqueued and the call returns without synchronising.  Scratch: a
+ * library-owned static device array of 16384 FP64 partial sums (128 KiB per
+ * GPU, held until the process exits); grids need ceil(nx/32)*ceil(ny/8) <=
+ * 16384 (every grid up to 2048 x 2048 x any nz), larger ones are rejected with
+ * MG_ERR_UNSUPPORTED.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current, so make that first
+ * call before capturing work into a CUDA graph on that device.  Every call
+ * shares the array: calls that overlap on the GPU (other streams or host
+ * threads) race and must be serialised by the caller.
+ */
+mg_status mg_residual_norm_noalloc(const mg_grid* grid, const mg_bc* bc, double alpha,
+                                   const double* rhs, double rhs_scale, const uint8_t* mask,
+                                   const double* u, double* norm_out, void* cuda_stream);
+
 /* Rebind the context to another CUDA stream (cudaStream_t, NULL = legacy). */
 mg_status mg_set_stream(mg_ctx* ctx, void* cuda_stream);
 

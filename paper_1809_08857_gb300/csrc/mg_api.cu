@@ -33,6 +33,12 @@ mg_status fail(mg_status st, const std::string& msg) {
   return st;
 }
 
+}  // namespace
+
+void mg::set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
 #define MG_CUDA(call)                                                         \
   do {                                                                        \
     cudaError_t e_ = (call);                                                  \

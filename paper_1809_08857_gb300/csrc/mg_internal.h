@@ -5,7 +5,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace mg {
+
+// Message returned by mg_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
 
 // Process-wide count of kernel launches issued by the launch wrappers.
 long long launch_count();

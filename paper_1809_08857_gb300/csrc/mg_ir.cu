@@ -13,7 +13,18 @@
 // per cell: each CTA marches along z through a 32 x 8 (x, y) tile, keeping
 // three planes of u + e (with a one-cell halo) in shared memory, and every
 // stencil neighbour is read from there.
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "../../include/mg.h"
 #include "mg_internal.h"
+
+// Largest number of CTAs (partial sums) one call may use: 16384 doubles,
+// 128 KiB.  Every GPU that loads libmg holds this array until process exit.
+#define MG_NOALLOC_MAX_PARTIALS 16384
+
+static __device__ __align__(256) double g_noalloc_scratch[MG_NOALLOC_MAX_PARTIALS];
 
 namespace mg {
 
@@ -160,3 +171,138 @@ void launch_ir_fused(const IrArgs& args, bool zero_free, cudaStream_t s) {
 }
 
 }  // namespace mg
+
+// ---- allocation-free residual norm ------------------------------------------
+//
+// mg_residual_norm_noalloc (include/mg.h) runs the refinement-residual kernel
+// above for a constant-coefficient operator described entirely by the
+// caller's arguments, and keeps its per-CTA partial sums in the file-scope
+// device array g_noalloc_scratch (top of this file) instead of in memory
+// obtained from cudaMalloc.  It is for callers that must not allocate device
+// memory during the call: codes whose device memory is already owned by their
+// own pool allocator, and time-stepping loops that cannot afford the implicit
+// device-wide synchronisation that cudaMalloc and cudaFree may perform.  Every
+// call overwrites the partial sums it later reads, so nothing needs clearing;
+// calls that overlap on the GPU (two streams, or two host threads) share the
+// array and race.
+
+namespace mg {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};  // device address of the array, per device
+
+// Sum of the partials (same order as the solver's reduction), then sqrt.
+__global__ void k_noalloc_finish(const double* __restrict__ partial, int n, double* out) {
+  __shared__ double ws[NT / 32];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) s += partial[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) ws[w] = s;
+  __syncthreads();
+  if (w == 0) {
+    double v = lane < NT / 32 ? ws[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) *out = sqrt(v);
+  }
+}
+
+// Device address of g_noalloc_scratch on the current device.  The first call
+// on a device resolves it with cudaGetSymbolAddress (host code only holds a
+// stand-in for the symbol, never its device address).
+mg_status noalloc_scratch(double** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    mg::set_last_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    return MG_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    mg::set_last_error("device ordinal out of range for the allocation-free scratch");
+    return MG_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      mg::set_last_error(std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") +
+                         cudaGetErrorString(e));
+      return MG_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return MG_OK;
+}
+
+}  // namespace
+
+// The refinement-residual kernel (no correction, not the norm of b) with its
+// partial sums in the static scratch, then the final sum and square root.
+void launch_noalloc(IrArgs a, double* scratch, int nparts, double* norm_out, cudaStream_t s) {
+  a.partial = scratch;
+  dim3 g = ir_grid(a.op.b, &a.zchunk);
+  k_ir_fused<false, false><<<g, NT, 0, s>>>(a);
+  k_noalloc_finish<<<1, NT, 0, s>>>(scratch, nparts, norm_out);
+  add_launches(2);
+}
+
+}  // namespace mg
+
+extern "C" mg_status mg_residual_norm_noalloc(const mg_grid* grid, const mg_bc* bc, double alpha,
+                                              const double* rhs, double rhs_scale,
+                                              const uint8_t* mask, const double* u,
+                                              double* norm_out, void* cuda_stream) {
+  mg::set_last_error("");
+  if (!grid || !bc || !rhs || !u || !norm_out) {
+    mg::set_last_error("NULL argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->h > 0.0) ||
+      !(alpha >= 0.0) || !std::isfinite(rhs_scale)) {
+    mg::set_last_error("grid sizes must be >= 1, h > 0, alpha >= 0, rhs_scale finite");
+    return MG_ERR_INVALID_ARG;
+  }
+  for (int f = 0; f < 6; ++f)
+    if ((bc->kind[f] != MG_BC_DIRICHLET && bc->kind[f] != MG_BC_NEUMANN) ||
+        !std::isfinite(bc->value[f])) {
+      mg::set_last_error("bad boundary condition");
+      return MG_ERR_INVALID_ARG;
+    }
+  mg::Box box{grid->nx, grid->ny, grid->nz};
+  const int nparts = mg::ir_partials(box);
+  if (nparts > MG_NOALLOC_MAX_PARTIALS) {
+    mg::set_last_error("grid too large for the allocation-free scratch: ceil(nx/32)*ceil(ny/8) "
+                       "must not exceed 16384");
+    return MG_ERR_UNSUPPORTED;
+  }
+  double* scratch = nullptr;
+  mg_status st = mg::noalloc_scratch(&scratch);
+  if (st != MG_OK) return st;
+
+  mg::IrArgs a{};
+  a.op.b = box;
+  a.op.ih2 = 1.0 / (grid->h * grid->h);
+  a.op.mask = mask;
+  for (int f = 0; f < 6; ++f) {
+    a.op.dir[f] = bc->kind[f] == MG_BC_DIRICHLET;
+    a.bval.v[f] = bc->value[f];
+  }
+  a.alpha = alpha;
+  a.rhs = rhs;
+  a.rhs_scale = rhs_scale;
+  a.lift = 1;
+  a.u_in = u;
+  mg::launch_noalloc(a, scratch, nparts, norm_out, (cudaStream_t)cuda_stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mg::set_last_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+    return MG_ERR_CUDA;
+  }
+  return MG_OK;
+}

@@ -29,7 +29,7 @@ MG_PREC_MIXED = 1
 EXPORTS = [
     "mg_default_options", "mg_create", "mg_solve_poisson", "mg_solve_helmholtz_batch",
     "mg_set_stream", "mg_level_info", "mg_destroy", "mg_error_string", "mg_last_error",
-    "mg_profile_enable", "mg_profile_read", "mg_launch_count",
+    "mg_profile_enable", "mg_profile_read", "mg_launch_count", "mg_residual_norm_noalloc",
 ]
 
 KCLASSES = ["smooth", "restrict", "prolong", "resid64", "coarse"]
@@ -111,6 +111,9 @@ def load():
     lib.mg_profile_read.restype = ctypes.c_int
     lib.mg_launch_count.argtypes = []
     lib.mg_launch_count.restype = ctypes.c_longlong
+    lib.mg_residual_norm_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(BC),
+                                             ctypes.c_double, P, ctypes.c_double, P, P, P, P]
+    lib.mg_residual_norm_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -142,6 +145,27 @@ def _stream_handle(stream=None):
 def launch_count():
     """Process-wide number of kernel launches issued by libmg."""
     return load().mg_launch_count()
+
+
+def residual_norm_noalloc(u, rhs, h, alpha=0.0, rhs_scale=1.0, mask=None,
+                          bc_kind=(1, 1, 1, 1, 0, 0), bc_value=(0, 0, 0, 0, 0, 1), out=None,
+                          stream=None):
+    """||b - A u||_2 for a constant-coefficient problem without any device
+    allocation inside libmg (mg_residual_norm_noalloc).  `out` is a CUDA
+    float64 tensor of one element that receives the norm (allocated here by
+    torch if not given); the call is asynchronous on the stream."""
+    lib = load()
+    nz, ny, nx = (int(s) for s in u.shape)
+    g = Grid(nx, ny, nz, float(h), (ctypes.c_double * 3)(0.0, 0.0, 0.0))
+    bc = BC((ctypes.c_int * 6)(*[int(k) for k in bc_kind]),
+            (ctypes.c_double * 6)(*[float(v) for v in bc_value]))
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=u.device)
+    _check(lib.mg_residual_norm_noalloc(ctypes.byref(g), ctypes.byref(bc), float(alpha),
+                                        _ptr(rhs, torch.float64), float(rhs_scale),
+                                        _ptr(mask, torch.uint8), _ptr(u, torch.float64),
+                                        _ptr(out, torch.float64), _stream_handle(stream)))
+    return out
 
 
 def default_options():
