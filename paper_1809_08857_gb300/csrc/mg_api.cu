@@ -309,7 +309,8 @@ mg_status vcycle32(mg_ctx* c, Kind kind, double alpha, int l, bool first_zero) {
         const bool zo = zero && q == 0 && col == 0;
         // other colour (unless known zero) + own rhs + own write + coefficients
         Scope sc(c, cls_s, n * ((zo ? 0.0 : 2.0) + 2.0 + 2.0 + fb));
-        mg::launch_half_sweep32(op, a32, col, L.f32[col], L.u32[col], L.u32[col ^ 1], zo, s);
+        mg::launch_half_sweep32(op, a32, col, L.f32[col], L.u32[col], L.u32[col ^ 1], zo,
+                                L.mask != nullptr, s);
       }
   };
   smooth(c->opt.nu1, first_zero);
@@ -607,8 +608,9 @@ mg_status mg_solve_poisson(mg_ctx* c, const double* rho, double* phi, double tol
     Scope sc(c, MG_KCLASS_COARSE, 0);
     mg::launch_set_masked(L0.mask, c->mask_value, n, phi, s);
   }
-  const Rhs rhs{rho, 1.0 / kEps0, true};
-  if (c->opt.precision == MG_PREC_FP64) {
+  // b = rho / eps0 + Dirichlet lifts, formed once per solve
+  const Rhs rhs{c->b64, 1.0, false};
+  {
     uint8_t dir[6];
     for (int f = 0; f < 6; ++f) dir[f] = poisson_dir(c, f);
     Scope sc(c, MG_KCLASS_COARSE, 0);

@@ -84,6 +84,8 @@ struct IrArgs {
   int W;               // packed row width of e and r
   double* partial;     // per-CTA sums of r^2
   int zchunk;          // set by the launcher
+  double dint;         // interior diagonal 6/h^2 + alpha (beta = 1), set by the launcher
+  int has_alpha;       // alpha != 0, set by the launcher
 };
 
 // ---- setup ---------------------------------------------------------------
@@ -129,7 +131,7 @@ void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t
 
 // ---- FP32 split-storage inner V-cycle (mg_split32.cu) -----------------------
 void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
-                         const float* uo, bool zero_other, cudaStream_t s);
+                         const float* uo, bool zero_other, bool has_mask, cudaStream_t s);
 void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
                               MPtr2 fc, MPtr2 uc, cudaStream_t s);
 void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s);

@@ -30,11 +30,45 @@ namespace mg {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int TX = 32, TY = 16, NT = TX * TY;
 constexpr int PX = TX + 2, PY = TY + 2, PN = PX * PY;
 
+// IEEE-754 binary32 -> binary64 by re-biasing the exponent (1023 - 127 = 896)
+// and widening the fraction, on the integer pipe (the FP64 pipe is the
+// bottleneck of this kernel).  Zeros and binary32 subnormals (< 1.2e-38,
+// never reached by a correction of a physical field) map to a signed zero;
+// infinities and NaNs keep their class.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
+  const unsigned ex = (b >> 23) & 0xffu;
+  const unsigned long long man = (unsigned long long)(b & 0x7fffffu) << 29;
+  const unsigned long long e64 = ex == 0xffu ? 0x7ffull : (unsigned long long)ex + 896ull;
+  const unsigned long long bits = ex == 0u ? sgn : (sgn | (e64 << 52) | man);
+  return __longlong_as_double((long long)bits);
+}
+
+// binary64 -> binary32 by truncation (round toward zero: at most one FP32
+// ulp, harmless for the right-hand side of the FP32 inner cycle), integer
+// pipe.  Values below the binary32 normal range flush to zero, values above
+// it become infinity, NaN stays NaN.
+__device__ __forceinline__ float narrow(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sgn = (unsigned)(b >> 63) << 31;
+  const int ex = (int)((b >> 52) & 0x7ffull);
+  const unsigned man = (unsigned)((b >> 29) & 0x7fffffull);
+  const int e32 = ex - 896;
+  unsigned bits;
+  if (ex == 0x7ff) bits = sgn | 0x7f800000u | (man ? 0x400000u : 0u);
+  else if (e32 >= 255) bits = sgn | 0x7f800000u;
+  else if (e32 <= 0) bits = sgn;
+  else bits = sgn | ((unsigned)e32 << 23) | man;
+  return __uint_as_float(bits);
+}
+
+// electrode test on the integer pipe: D < 0 marks an electrode cell
 __device__ __forceinline__ bool masked64(const Op64& op, long long c) {
-  if (op.D) return op.D[c] < 0.0;
+  if (op.D) return __double_as_longlong(op.D[c]) < 0;
   return op.mask != nullptr && op.mask[c] != 0;
 }
 
@@ -46,15 +80,18 @@ __device__ __forceinline__ double load_cell(const IrArgs& a, int i, int j, int k
   double v = a.u_in[c];
   if (HasE) {
     const long long t = ((long long)k * a.op.b.ny + j) * a.W + (i >> 1);
-    v += (double)(((i + j + k) & 1) ? a.e[1][t] : a.e[0][t]);
+    v += widen(((i + j + k) & 1) ? a.e[1][t] : a.e[0][t]);
   }
   return v;
 }
 
-template <bool HasE, bool ZeroFree>
+// Faces: variable-coefficient operator (face arrays); otherwise beta = 1.
+// OnTheFlyB: b = rhs * rhs_scale + Dirichlet lifts formed here; otherwise b
+// is read as given (the solver precomputes it once per solve).
+template <bool Faces, bool HasE, bool ZeroFree, bool OnTheFlyB>
 __global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
   __shared__ double pl[3][PN];
-  __shared__ double red[NT / 32];
+  __shared__ float red[NT / 32];
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * a.zchunk;
@@ -63,6 +100,16 @@ __global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
   const long long sy = nx, sz = (long long)nx * ny;
   const int i = x0 + tx, j = y0 + ty;
   const bool own = i < nx && j < ny;
+  // beta = 1: the diagonal is (in-box faces + 2 per Dirichlet face) / h^2 +
+  // alpha; interior cells use the precomputed 6/h^2 + alpha
+  int dxy = 0;
+  if (!Faces) {
+    dxy += i > 0 ? 1 : (a.op.dir[0] ? 2 : 0);
+    dxy += i < nx - 1 ? 1 : (a.op.dir[1] ? 2 : 0);
+    dxy += j > 0 ? 1 : (a.op.dir[2] ? 2 : 0);
+    dxy += j < ny - 1 ? 1 : (a.op.dir[3] ? 2 : 0);
+  }
+  const bool xy_inner = i > 0 && i < nx - 1 && j > 0 && j < ny - 1;
 
   auto load_plane = [&](int buf, int k) {
     for (int q = threadIdx.x; q < PN; q += NT) {
@@ -73,7 +120,7 @@ __global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
   load_plane(0, z0 - 1);
   load_plane(1, z0);
   int b0 = 0, b1 = 1, b2 = 2;
-  double ss = 0.0;
+  float ss = 0.0f;
   for (int k = z0; k < z1; ++k) {
     load_plane(b2, k + 1);
     __syncthreads();
@@ -83,45 +130,58 @@ __global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
       double r = 0.0;
       const double uc = pl[b1][q];
       if (!masked64(a.op, c)) {
-        double b = a.rhs[c] * a.rhs_scale;
-        if (a.lift) {
-          const double bc = a.beta0 ? a.beta0[c] : 1.0;
-          const double l = 2.0 * bc * a.op.ih2;
-          if (i == 0 && a.op.dir[0]) b += l * a.bval.v[0];
-          if (i == nx - 1 && a.op.dir[1]) b += l * a.bval.v[1];
-          if (j == 0 && a.op.dir[2]) b += l * a.bval.v[2];
-          if (j == ny - 1 && a.op.dir[3]) b += l * a.bval.v[3];
-          if (k == 0 && a.op.dir[4]) b += l * a.bval.v[4];
-          if (k == nz - 1 && a.op.dir[5]) b += l * a.bval.v[5];
-        }
-        double diag, off;
-        if (a.op.cx) {
-          double o = 0.0;
-          if (i > 0) o += a.op.cx[c] * pl[b1][q - 1];
-          if (i < nx - 1) o += a.op.cx[c + 1] * pl[b1][q + 1];
-          if (j > 0) o += a.op.cy[c] * pl[b1][q - PX];
-          if (j < ny - 1) o += a.op.cy[c + sy] * pl[b1][q + PX];
-          if (k > 0) o += a.op.cz[c] * pl[b0][q];
-          if (k < nz - 1) o += a.op.cz[c + sz] * pl[b2][q];
-          diag = a.op.D[c];
-          off = o;
+        double b;
+        if (OnTheFlyB) {
+          b = a.rhs[c] * a.rhs_scale;
+          const bool edge = i == 0 || i == nx - 1 || j == 0 || j == ny - 1 || k == 0 || k == nz - 1;
+          if (a.lift && edge) {
+            const double l = 2.0 * (a.beta0 ? a.beta0[c] : 1.0) * a.op.ih2;
+            if (i == 0 && a.op.dir[0]) b += l * a.bval.v[0];
+            if (i == nx - 1 && a.op.dir[1]) b += l * a.bval.v[1];
+            if (j == 0 && a.op.dir[2]) b += l * a.bval.v[2];
+            if (j == ny - 1 && a.op.dir[3]) b += l * a.bval.v[3];
+            if (k == 0 && a.op.dir[4]) b += l * a.bval.v[4];
+            if (k == nz - 1 && a.op.dir[5]) b += l * a.bval.v[5];
+          }
         } else {
-          // beta = 1: the off-diagonal sum is a plain neighbour sum
-          double o = 0.0, d = 0.0;
-          if (i > 0) { d += 1.0; o += pl[b1][q - 1]; } else if (a.op.dir[0]) d += 2.0;
-          if (i < nx - 1) { d += 1.0; o += pl[b1][q + 1]; } else if (a.op.dir[1]) d += 2.0;
-          if (j > 0) { d += 1.0; o += pl[b1][q - PX]; } else if (a.op.dir[2]) d += 2.0;
-          if (j < ny - 1) { d += 1.0; o += pl[b1][q + PX]; } else if (a.op.dir[3]) d += 2.0;
-          if (k > 0) { d += 1.0; o += pl[b0][q]; } else if (a.op.dir[4]) d += 2.0;
-          if (k < nz - 1) { d += 1.0; o += pl[b2][q]; } else if (a.op.dir[5]) d += 2.0;
-          diag = d * a.op.ih2;
-          off = o * a.op.ih2;
+          b = a.rhs[c];
         }
-        r = ZeroFree ? b + off : b - ((diag + a.alpha) * uc - off);
+        if (Faces) {
+          // r = b - D u_c + sum_f w_f u_nb, as one FMA chain
+          double t = b;
+          if (!ZeroFree) t = fma(-(a.has_alpha ? a.op.D[c] + a.alpha : a.op.D[c]), uc, b);
+          if (i > 0) t = fma(a.op.cx[c], pl[b1][q - 1], t);
+          if (i < nx - 1) t = fma(a.op.cx[c + 1], pl[b1][q + 1], t);
+          if (j > 0) t = fma(a.op.cy[c], pl[b1][q - PX], t);
+          if (j < ny - 1) t = fma(a.op.cy[c + sy], pl[b1][q + PX], t);
+          if (k > 0) t = fma(a.op.cz[c], pl[b0][q], t);
+          if (k < nz - 1) t = fma(a.op.cz[c + sz], pl[b2][q], t);
+          r = t;
+        } else {
+          double o = 0.0;
+          if (i > 0) o += pl[b1][q - 1];
+          if (i < nx - 1) o += pl[b1][q + 1];
+          if (j > 0) o += pl[b1][q - PX];
+          if (j < ny - 1) o += pl[b1][q + PX];
+          if (k > 0) o += pl[b0][q];
+          if (k < nz - 1) o += pl[b2][q];
+          if (ZeroFree) {
+            r = fma(a.op.ih2, o, b);
+          } else {
+            double diag = a.dint;
+            if (!(xy_inner && k > 0 && k < nz - 1)) {
+              const int d = dxy + (k > 0 ? 1 : (a.op.dir[4] ? 2 : 0)) +
+                            (k < nz - 1 ? 1 : (a.op.dir[5] ? 2 : 0));
+              diag = fma((double)d, a.op.ih2, a.alpha);
+            }
+            r = fma(a.op.ih2, o, fma(-diag, uc, b));
+          }
+        }
       }
       if (a.u_out) a.u_out[c] = uc;
-      if (a.r[0]) (((i + j + k) & 1) ? a.r[1] : a.r[0])[((long long)k * ny + j) * a.W + (i >> 1)] = (float)r;
-      ss += r * r;
+      const float r32 = narrow(r);
+      if (a.r[0]) (((i + j + k) & 1) ? a.r[1] : a.r[0])[((long long)k * ny + j) * a.W + (i >> 1)] = r32;
+      ss = fmaf(r32, r32, ss);
     }
     __syncthreads();
     const int t = b0;
@@ -129,13 +189,14 @@ __global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
     b1 = b2;
     b2 = t;
   }
-  // CTA sum of r^2
+  // CTA sum of r^2 (FP32 is ample for a stopping test; the partials and the
+  // final sum are accumulated in FP64)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double v = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+    double v = threadIdx.x < NT / 32 ? (double)red[threadIdx.x] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (threadIdx.x == 0)
@@ -147,9 +208,9 @@ __global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
 
 static dim3 ir_grid(const Box& b, int* zchunk) {
   const int gx = (b.nx + TX - 1) / TX, gy = (b.ny + TY - 1) / TY;
-  // enough CTAs for every SM (152 on GB300) several times over, long z runs
+  // enough CTAs to fill every SM (152 on GB300) a few times, long z runs
   int zc = b.nz;
-  while (zc > 16 && (long long)gx * gy * ((b.nz + zc - 1) / zc) < 4 * 152 * 4) zc = (zc + 1) / 2;
+  while (zc > 16 && (long long)gx * gy * ((b.nz + zc - 1) / zc) < 4 * 152 * 2) zc = (zc + 1) / 2;
   *zchunk = zc;
   return dim3(gx, gy, (b.nz + zc - 1) / zc);
 }
@@ -160,13 +221,35 @@ int ir_partials(const Box& b) {
   return (int)(g.x * g.y * g.z);
 }
 
+template <bool F, bool E, bool Z, bool O>
+static void go(const IrArgs& a, dim3 g, cudaStream_t s) {
+  k_ir_fused<F, E, Z, O><<<g, NT, 0, s>>>(a);
+}
+
+static void dispatch(const IrArgs& a, dim3 g, bool zero_free, bool on_the_fly, cudaStream_t s) {
+  const bool faces = a.op.cx != nullptr;
+  const bool has_e = a.e[0] != nullptr && !zero_free;
+  if (on_the_fly) {
+    if (faces) go<true, false, false, true>(a, g, s);
+    else go<false, false, false, true>(a, g, s);
+  } else if (zero_free) {
+    if (faces) go<true, false, true, false>(a, g, s);
+    else go<false, false, true, false>(a, g, s);
+  } else if (has_e) {
+    if (faces) go<true, true, false, false>(a, g, s);
+    else go<false, true, false, false>(a, g, s);
+  } else {
+    if (faces) go<true, false, false, false>(a, g, s);
+    else go<false, false, false, false>(a, g, s);
+  }
+}
+
 void launch_ir_fused(const IrArgs& args, bool zero_free, cudaStream_t s) {
   IrArgs a = args;
   dim3 g = ir_grid(a.op.b, &a.zchunk);
-  const bool has_e = a.e[0] != nullptr;
-  if (zero_free) k_ir_fused<false, true><<<g, NT, 0, s>>>(a);
-  else if (has_e) k_ir_fused<true, false><<<g, NT, 0, s>>>(a);
-  else k_ir_fused<false, false><<<g, NT, 0, s>>>(a);
+  a.dint = 6.0 * a.op.ih2 + a.alpha;
+  a.has_alpha = a.alpha != 0.0;
+  dispatch(a, g, zero_free, false, s);
   add_launches(1);
 }
 
@@ -247,7 +330,9 @@ mg_status noalloc_scratch(double** out) {
 void launch_noalloc(IrArgs a, double* scratch, int nparts, double* norm_out, cudaStream_t s) {
   a.partial = scratch;
   dim3 g = ir_grid(a.op.b, &a.zchunk);
-  k_ir_fused<false, false><<<g, NT, 0, s>>>(a);
+  a.dint = 6.0 * a.op.ih2 + a.alpha;
+  a.has_alpha = a.alpha != 0.0;
+  dispatch(a, g, false, true, s);
   k_noalloc_finish<<<1, NT, 0, s>>>(scratch, nparts, norm_out);
   add_launches(2);
 }

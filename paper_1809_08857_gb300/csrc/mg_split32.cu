@@ -100,30 +100,121 @@ __device__ __forceinline__ void row32(const Split32& op, int col, long long t, i
 }
 
 // One colour of a red-black sweep: u_own <- (f + off) / (alpha + diag).
-// zero_other: the other colour is known to be zero (first half-sweep from a
-// zero guess), so it is not read.
+// ZeroOther: the other colour is known to be zero (first half-sweep from a
+// zero guess), so it is not read.  Block (32, 8) over (packed x, y), one z
+// plane per blockIdx.z: no integer division in the index math.
 template <bool VB, bool ZeroOther>
 __global__ void __launch_bounds__(kT) k_half_sweep(Split32 op, float alpha, int col,
                                                    const float* __restrict__ f,
                                                    float* __restrict__ u,
                                                    const float* __restrict__ uo) {
-  const long long t = (long long)blockIdx.x * kT + threadIdx.x;
-  const int W = op.W;
-  if (t >= (long long)W * op.b.ny * op.b.nz) return;
-  const int p = (int)(t % W);
-  const long long jk = t / W;
-  const int j = (int)(jk % op.b.ny), k = (int)(jk / op.b.ny);
+  const int p = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  if (p >= op.W || j >= op.b.ny) return;
   const int i = 2 * p + ((j + k + col) & 1);
   if (i >= op.b.nx) return;
+  const long long t = ((long long)k * op.b.ny + j) * op.W + p;
   if (VB && bsel(op, col)[t] < 0.0f) return;
   float diag, off;
-  if (ZeroOther) {
-    row32<VB>(op, col, t, i, j, k, uo, diag, off);  // off unused
-    u[t] = __fdividef(f[t], diag + alpha);
-  } else {
-    row32<VB>(op, col, t, i, j, k, uo, diag, off);
-    u[t] = __fdividef(f[t] + off, diag + alpha);
+  row32<VB>(op, col, t, i, j, k, uo, diag, off);
+  u[t] = __fdividef(ZeroOther ? f[t] : f[t] + off, diag + alpha);
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ float el(const float4& v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+// Vectorised half-sweep: four packed cells per thread (float4 loads and
+// store), x-neighbours across quad edges exchanged by warp shuffles.  Needs
+// nx % 8 == 0 (W % 4 == 0, no padding).  Block (32, 8): a warp covers 128
+// packed cells of one row.  Grid (ceil(W/128), ceil(ny/8), nz).
+template <bool VB, bool ZeroOther, bool HasMask>
+__global__ void __launch_bounds__(kT) k_half_sweep_v4(Split32 op, float alpha, int col,
+                                                      const float* __restrict__ f,
+                                                      float* __restrict__ u,
+                                                      const float* __restrict__ uo) {
+  const unsigned FULL = 0xffffffffu;
+  const int W = op.W, ny = op.b.ny, nz = op.b.nz;
+  const int lane = threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  const int p0 = 4 * (blockIdx.x * 32 + lane);
+  const bool active = j < ny && p0 < W;
+  const int jj = min(j, ny - 1);
+  const int pp = min(p0, W - 4);
+  const long long t0 = ((long long)k * ny + jj) * W + pp;
+  const long long sz = (long long)W * ny;
+  const int s = (jj + k + col) & 1;
+  const float* bo = bsel(op, col);
+  const float* bt = bsel(op, col ^ 1);
+  const float4 one = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+  const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float4 F = ld4(f + t0);
+  const float4 BO = VB ? ld4(bo + t0) : one;
+  const float4 BT = VB ? ld4(bt + t0) : one;
+  const float4 UO = ZeroOther ? zero : ld4(uo + t0);
+  const bool ym = jj > 0, yp = jj < ny - 1, zm = k > 0, zp = k < nz - 1;
+  const float4 UYm = (!ZeroOther && ym) ? ld4(uo + t0 - W) : zero;
+  const float4 UYp = (!ZeroOther && yp) ? ld4(uo + t0 + W) : zero;
+  const float4 UZm = (!ZeroOther && zm) ? ld4(uo + t0 - sz) : zero;
+  const float4 UZp = (!ZeroOther && zp) ? ld4(uo + t0 + sz) : zero;
+  const float4 BYm = (VB && ym) ? ld4(bt + t0 - W) : one;
+  const float4 BYp = (VB && yp) ? ld4(bt + t0 + W) : one;
+  const float4 BZm = (VB && zm) ? ld4(bt + t0 - sz) : one;
+  const float4 BZp = (VB && zp) ? ld4(bt + t0 + sz) : one;
+  float uprev = __shfl_up_sync(FULL, UO.w, 1), unext = __shfl_down_sync(FULL, UO.x, 1);
+  float bprev = __shfl_up_sync(FULL, BT.w, 1), bnext = __shfl_down_sync(FULL, BT.x, 1);
+  if (lane == 0 && pp > 0) {
+    if (!ZeroOther) uprev = uo[t0 - 1];
+    if (VB) bprev = bt[t0 - 1];
   }
+  if (lane == 31 && pp + 4 < W) {
+    if (!ZeroOther) unext = uo[t0 + 4];
+    if (VB) bnext = bt[t0 + 4];
+  }
+  float4 U = zero;
+  if (HasMask) U = ld4(u + t0);
+  // other-colour values at packed pp-1 .. pp+4
+  const float ux[6] = {uprev, UO.x, UO.y, UO.z, UO.w, unext};
+  const float bx[6] = {bprev, BT.x, BT.y, BT.z, BT.w, bnext};
+  float out[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int p = pp + e;
+    const float bc = el(BO, e);
+    float d = 0.0f, o = 0.0f, w;
+    // x: left neighbour at packed p - 1 + s, right at p + s
+    if (!(p == 0 && s == 0)) {
+      const float un = s ? ux[e + 1] : ux[e], bn = s ? bx[e + 1] : bx[e];
+      w = VB ? wface(bc, bn) : 1.0f;
+      d += w;
+      o += w * un;
+    } else if (op.dir[0]) {
+      d += 2.0f * bc;
+    }
+    if (!(p == W - 1 && s == 1)) {
+      const float un = s ? ux[e + 2] : ux[e + 1], bn = s ? bx[e + 2] : bx[e + 1];
+      w = VB ? wface(bc, bn) : 1.0f;
+      d += w;
+      o += w * un;
+    } else if (op.dir[1]) {
+      d += 2.0f * bc;
+    }
+    if (ym) { w = VB ? wface(bc, el(BYm, e)) : 1.0f; d += w; o += w * el(UYm, e); }
+    else if (op.dir[2]) d += 2.0f * bc;
+    if (yp) { w = VB ? wface(bc, el(BYp, e)) : 1.0f; d += w; o += w * el(UYp, e); }
+    else if (op.dir[3]) d += 2.0f * bc;
+    if (zm) { w = VB ? wface(bc, el(BZm, e)) : 1.0f; d += w; o += w * el(UZm, e); }
+    else if (op.dir[4]) d += 2.0f * bc;
+    if (zp) { w = VB ? wface(bc, el(BZp, e)) : 1.0f; d += w; o += w * el(UZp, e); }
+    else if (op.dir[5]) d += 2.0f * bc;
+    float v = __fdividef(ZeroOther ? el(F, e) : fmaf(o, op.ih2, el(F, e)), fmaf(d, op.ih2, alpha));
+    if (HasMask && bc < 0.0f) v = el(U, e);
+    out[e] = v;
+  }
+  if (active) *reinterpret_cast<float4*>(u + t0) = make_float4(out[0], out[1], out[2], out[3]);
 }
 
 __device__ __forceinline__ long long spos(const Split32& op, int i, int j, int k) {
@@ -136,11 +227,9 @@ __device__ __forceinline__ long long spos(const Split32& op, int i, int j, int k
 template <bool VB>
 __global__ void __launch_bounds__(kT) k_resid_restrict(Split32 op, Split32 cop, float alpha,
                                                        Ptr2 f, Ptr2 u, MPtr2 fc, MPtr2 uc) {
-  const long long C = (long long)blockIdx.x * kT + threadIdx.x;
-  if (C >= cop.b.n()) return;
-  const int I = (int)(C % cop.b.nx);
-  const long long JK = C / cop.b.nx;
-  const int J = (int)(JK % cop.b.ny), K = (int)(JK / cop.b.ny);
+  const int I = blockIdx.x * 32 + threadIdx.x;
+  const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
+  if (I >= cop.b.nx || J >= cop.b.ny) return;
   float sum = 0.0f;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -173,33 +262,34 @@ __device__ __forceinline__ float cval(const Split32& cop, const Ptr2& ec, int I,
 }
 
 // u_fine += trilinear (27, 9, 3, 1)/64 interpolation of the coarse
-// correction; electrode cells untouched.  blockIdx.y = fine colour.
+// correction; electrode cells untouched.  One thread per fine x-pair
+// (2p, 2p+1): both cells sit at packed index p (one in each colour) and share
+// the coarse parent I = p, so the 8-point stencils of the pair need 12
+// coarse values.  Block (32, 8) over (p, j), blockIdx.z = k.
 template <bool VB>
 __global__ void __launch_bounds__(kT) k_prolong(Split32 op, Split32 cop, Ptr2 ec, MPtr2 u) {
-  const int col = blockIdx.y;
-  const long long t = (long long)blockIdx.x * kT + threadIdx.x;
-  const int W = op.W;
-  if (t >= (long long)W * op.b.ny * op.b.nz) return;
-  const int p = (int)(t % W);
-  const long long jk = t / W;
-  const int j = (int)(jk % op.b.ny), k = (int)(jk / op.b.ny);
-  const int i = 2 * p + ((j + k + col) & 1);
-  if (i >= op.b.nx) return;
-  if (VB && bsel(op, col)[t] < 0.0f) return;
-  const int I = i >> 1, J = j >> 1, K = k >> 1;
-  const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
-  const float c000 = cval(cop, ec, I, J, K);
-  const float c100 = cval(cop, ec, I + si, J, K);
-  const float c010 = cval(cop, ec, I, J + sj, K);
-  const float c110 = cval(cop, ec, I + si, J + sj, K);
-  const float c001 = cval(cop, ec, I, J, K + sk);
-  const float c101 = cval(cop, ec, I + si, J, K + sk);
-  const float c011 = cval(cop, ec, I, J + sj, K + sk);
-  const float c111 = cval(cop, ec, I + si, J + sj, K + sk);
-  const float v = (27.0f * c000 + 9.0f * (c100 + c010 + c001) + 3.0f * (c110 + c101 + c011) +
-                   c111) *
-                  (1.0f / 64.0f);
-  sel(u, col)[t] += v;
+  const int p = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  if (p >= op.W || j >= op.b.ny) return;
+  const long long t = ((long long)k * op.b.ny + j) * op.W + p;
+  const int c0 = (j + k) & 1;  // colour of cell 2p
+  const int I = p, J = j >> 1, K = k >> 1;
+  const int sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
+  float x0 = 0.0f, x1 = 0.0f;  // y-z weighted x-interpolants of cells 2p and 2p+1
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int b = q & 1, c = q >> 1;
+    const float wyz = (b ? 0.25f : 0.75f) * (c ? 0.25f : 0.75f);
+    const float A = cval(cop, ec, I - 1, J + b * sj, K + c * sk);
+    const float B = cval(cop, ec, I, J + b * sj, K + c * sk);
+    const float C = cval(cop, ec, I + 1, J + b * sj, K + c * sk);
+    x0 = fmaf(wyz, fmaf(0.75f, B, 0.25f * A), x0);
+    x1 = fmaf(wyz, fmaf(0.75f, B, 0.25f * C), x1);
+  }
+  float* u0 = sel(u, c0);
+  float* u1 = sel(u, c0 ^ 1);
+  if (!(VB && bsel(op, c0)[t] < 0.0f)) u0[t] += x0;
+  if (2 * p + 1 < op.b.nx && !(VB && bsel(op, c0 ^ 1)[t] < 0.0f)) u1[t] += x1;
 }
 
 // r = f - A u at every cell of the level (electrode and padding cells: 0).
@@ -256,31 +346,44 @@ __global__ void k_split_beta(const double* beta, const uint8_t* mask, Split32 op
 }  // namespace
 
 void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
-                         const float* uo, bool zero_other, cudaStream_t s) {
-  const long long t = (long long)op.W * op.b.ny * op.b.nz;
+                         const float* uo, bool zero_other, bool has_mask, cudaStream_t s) {
   const bool vb = op.beta[0] != nullptr;
-  if (vb) {
-    if (zero_other) k_half_sweep<true, true><<<nblk(t), kT, 0, s>>>(op, alpha, col, f, u, uo);
-    else k_half_sweep<true, false><<<nblk(t), kT, 0, s>>>(op, alpha, col, f, u, uo);
+  dim3 blk(32, 8);
+  if (op.b.nx % 8 == 0) {
+    dim3 g((op.W / 4 + 31) / 32, (op.b.ny + 7) / 8, op.b.nz);
+#define HS4(A, B, C) k_half_sweep_v4<A, B, C><<<g, blk, 0, s>>>(op, alpha, col, f, u, uo)
+    if (vb) {
+      if (has_mask) { if (zero_other) HS4(true, true, true); else HS4(true, false, true); }
+      else { if (zero_other) HS4(true, true, false); else HS4(true, false, false); }
+    } else {
+      if (zero_other) HS4(false, true, false); else HS4(false, false, false);
+    }
+#undef HS4
   } else {
-    if (zero_other) k_half_sweep<false, true><<<nblk(t), kT, 0, s>>>(op, alpha, col, f, u, uo);
-    else k_half_sweep<false, false><<<nblk(t), kT, 0, s>>>(op, alpha, col, f, u, uo);
+    dim3 g((op.W + 31) / 32, (op.b.ny + 7) / 8, op.b.nz);
+    if (vb) {
+      if (zero_other) k_half_sweep<true, true><<<g, blk, 0, s>>>(op, alpha, col, f, u, uo);
+      else k_half_sweep<true, false><<<g, blk, 0, s>>>(op, alpha, col, f, u, uo);
+    } else {
+      if (zero_other) k_half_sweep<false, true><<<g, blk, 0, s>>>(op, alpha, col, f, u, uo);
+      else k_half_sweep<false, false><<<g, blk, 0, s>>>(op, alpha, col, f, u, uo);
+    }
   }
   add_launches(1);
 }
 
 void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
                               MPtr2 fc, MPtr2 uc, cudaStream_t s) {
-  if (op.beta[0]) k_resid_restrict<true><<<nblk(cop.b.n()), kT, 0, s>>>(op, cop, alpha, f, u, fc, uc);
-  else k_resid_restrict<false><<<nblk(cop.b.n()), kT, 0, s>>>(op, cop, alpha, f, u, fc, uc);
+  dim3 blk(32, 8), g((cop.b.nx + 31) / 32, (cop.b.ny + 7) / 8, cop.b.nz);
+  if (op.beta[0]) k_resid_restrict<true><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
+  else k_resid_restrict<false><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
   add_launches(1);
 }
 
 void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s) {
-  const long long t = (long long)op.W * op.b.ny * op.b.nz;
-  dim3 g(nblk(t), 2);
-  if (op.beta[0]) k_prolong<true><<<g, kT, 0, s>>>(op, cop, ec, u);
-  else k_prolong<false><<<g, kT, 0, s>>>(op, cop, ec, u);
+  dim3 blk(32, 8), g((op.W + 31) / 32, (op.b.ny + 7) / 8, op.b.nz);
+  if (op.beta[0]) k_prolong<true><<<g, blk, 0, s>>>(op, cop, ec, u);
+  else k_prolong<false><<<g, blk, 0, s>>>(op, cop, ec, u);
   add_launches(1);
 }
 
