@@ -317,13 +317,20 @@ mg_status vcycle32(mg_ctx* c, Kind kind, double alpha, int l, bool first_zero) {
   Level& C = c->lv[l + 1];
   mg::Split32 cop = sop(c, l + 1, kind);
   {
-    Scope sc(c, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE, n * (8.0 + fb + 1.0));
-    mg::launch_resid_restrict32s(op, cop, a32, cp(L.f32), cp(L.u32), mp(C.f32), mp(C.u32), s);
+    const bool red_only = c->opt.nu1 > 0;
+    // u both colours, f (red only if red_only), beta both colours, coarse f and u
+    Scope sc(c, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE,
+             n * (4.0 + (red_only ? 2.0 : 4.0) + fb + 1.0));
+    mg::launch_resid_restrict32s(op, cop, a32, cp(L.f32), cp(L.u32), mp(C.f32), mp(C.u32),
+                                 red_only, s);
   }
   MG_TRY(vcycle32(c, kind, alpha, l + 1, true));
   {
-    Scope sc(c, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE, n * (8.0 + 0.5 + fb));
-    mg::launch_prolong32s(op, cop, cp(C.u32), mp(L.u32), s);
+    const bool black_only = c->opt.nu2 > 0;
+    // fine u read + write (black only if black_only), coarse e, beta for the electrode test
+    Scope sc(c, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE,
+             n * ((black_only ? 4.0 : 8.0) + 0.5 + (black_only ? fb / 2 : fb)));
+    mg::launch_prolong32s(op, cop, cp(C.u32), mp(L.u32), black_only, s);
   }
   smooth(c->opt.nu2, false);
   return check_launch();

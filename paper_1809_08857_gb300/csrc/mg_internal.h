@@ -132,9 +132,12 @@ void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t
 // ---- FP32 split-storage inner V-cycle (mg_split32.cu) -----------------------
 void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
                          const float* uo, bool zero_other, bool has_mask, cudaStream_t s);
+// red_only: the pre-smoothing ended with a black half-sweep (black residuals are 0).
 void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
-                              MPtr2 fc, MPtr2 uc, cudaStream_t s);
-void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s);
+                              MPtr2 fc, MPtr2 uc, bool red_only, cudaStream_t s);
+// black_only: post-smoothing starts with a red half-sweep (red cells are overwritten).
+void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, bool black_only,
+                       cudaStream_t s);
 void launch_resid32s(const Split32& op, float alpha, Ptr2 f, Ptr2 u, MPtr2 r, cudaStream_t s);
 void launch_dense_apply32s(const Split32& op, const double* Minv, Ptr2 r, MPtr2 u,
                            cudaStream_t s);

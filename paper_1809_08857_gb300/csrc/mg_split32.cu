@@ -10,7 +10,11 @@
 //
 // Operator (Sec. 2 items (ii)-(iii)): (A u)_c = alpha u_c + sum_f w_f (u_c -
 // u_nb)/h^2 with w_f the harmonic mean of the two cells' beta, beta_c towards
-// an electrode cell (beta < 0 marks one) and 2 beta_c on a Dirichlet face.
+// an electrode cell and 2 beta_c on a Dirichlet face.  Each level stores
+// hb = 1/(2 beta) per cell (hb < 0 marks an electrode cell), so the harmonic
+// mean 2 b_c b_n / (b_c + b_n) is one add and one reciprocal:
+// w = 1 / (hb_c + hb_n); towards an electrode w = 1 / (2 hb_c); on a
+// Dirichlet face w = 1 / hb_c.
 #include "mg_internal.h"
 
 namespace mg {
@@ -29,9 +33,12 @@ __device__ __forceinline__ const float* bsel(const Split32& op, int c) {
   return c ? op.beta[1] : op.beta[0];
 }
 
-__device__ __forceinline__ float wface(float bc, float bn) {
-  return bn < 0.0f ? bc : __fdividef(2.0f * bc * bn, bc + bn);
+// face weight between a free cell (hb = hc) and an in-box neighbour (hn)
+__device__ __forceinline__ float wface(float hc, float hn) {
+  return __fdividef(1.0f, hn < 0.0f ? hc + hc : hc + hn);
 }
+// Dirichlet domain face: 2 beta_c
+__device__ __forceinline__ float wdir(float hc) { return __fdividef(1.0f, hc); }
 
 // Row of the operator at a cell of colour `col`, packed position t (row
 // offset + p), coordinates (i, j, k), s = i & 1.  Returns the residual
@@ -44,7 +51,8 @@ __device__ __forceinline__ void row32(const Split32& op, int col, long long t, i
   const long long rowo = t - (i >> 1);
   const int s = i & 1;
   const float* bt = bsel(op, col ^ 1);
-  const float bc = VB ? bsel(op, col)[t] : 1.0f;
+  const float bc = VB ? bsel(op, col)[t] : 0.5f;  // hb of the cell
+  const float wd = VB ? wdir(bc) : 2.0f;           // Dirichlet face weight
   float d = 0.0f, o = 0.0f, w;
   if (i > 0) {
     const long long q = rowo + (i >> 1) - 1 + s;
@@ -52,7 +60,7 @@ __device__ __forceinline__ void row32(const Split32& op, int col, long long t, i
     d += w;
     o += w * uo[q];
   } else if (op.dir[0]) {
-    d += 2.0f * bc;
+    d += wd;
   }
   if (i + 1 < op.b.nx) {
     const long long q = rowo + (i >> 1) + s;
@@ -60,7 +68,7 @@ __device__ __forceinline__ void row32(const Split32& op, int col, long long t, i
     d += w;
     o += w * uo[q];
   } else if (op.dir[1]) {
-    d += 2.0f * bc;
+    d += wd;
   }
   if (j > 0) {
     const long long q = t - W;
@@ -68,7 +76,7 @@ __device__ __forceinline__ void row32(const Split32& op, int col, long long t, i
     d += w;
     o += w * uo[q];
   } else if (op.dir[2]) {
-    d += 2.0f * bc;
+    d += wd;
   }
   if (j + 1 < op.b.ny) {
     const long long q = t + W;
@@ -76,7 +84,7 @@ __device__ __forceinline__ void row32(const Split32& op, int col, long long t, i
     d += w;
     o += w * uo[q];
   } else if (op.dir[3]) {
-    d += 2.0f * bc;
+    d += wd;
   }
   const long long sz = (long long)W * op.b.ny;
   if (k > 0) {
@@ -85,7 +93,7 @@ __device__ __forceinline__ void row32(const Split32& op, int col, long long t, i
     d += w;
     o += w * uo[q];
   } else if (op.dir[4]) {
-    d += 2.0f * bc;
+    d += wd;
   }
   if (k + 1 < op.b.nz) {
     const long long q = t + sz;
@@ -93,7 +101,7 @@ __device__ __forceinline__ void row32(const Split32& op, int col, long long t, i
     d += w;
     o += w * uo[q];
   } else if (op.dir[5]) {
-    d += 2.0f * bc;
+    d += wd;
   }
   diag = d * op.ih2;
   off = o * op.ih2;
@@ -130,12 +138,55 @@ __device__ __forceinline__ float el(const float4& v, int e) {
 // Vectorised half-sweep: four packed cells per thread (float4 loads and
 // store), x-neighbours across quad edges exchanged by warp shuffles.  Needs
 // nx % 8 == 0 (W % 4 == 0, no padding).  Block (32, 8): a warp covers 128
-// packed cells of one row.  Grid (ceil(W/128), ceil(ny/8), nz).
+// packed cells of one row, so the row parity S (which decides whether a
+// cell's x-neighbours in the other colour sit at packed p-1, p or p, p+1) is
+// warp-uniform and the quad update is compiled once per parity.
+struct Quad {
+  float4 F, BO, U;                   // own rhs, own hb, own old value (electrodes)
+  float ux[6], bx[6];                // other colour at packed pp-1 .. pp+4
+  float4 UYm, UYp, UZm, UZp;         // other colour, y/z neighbours
+  float4 BYm, BYp, BZm, BZp;
+};
+
+template <bool VB, bool ZeroOther, bool HasMask, int S>
+__device__ __forceinline__ float4 quad_update(const Split32& op, float alpha, const Quad& q,
+                                              int pp, bool ym, bool yp, bool zm, bool zp) {
+  float out[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int p = pp + e;
+    const float hc = VB ? el(q.BO, e) : 0.5f;
+    float d = 0.0f, o = 0.0f;
+    auto face = [&](float hn, float un) {
+      float w = 1.0f;
+      if (VB) w = HasMask ? wface(hc, hn) : __fdividef(1.0f, hc + hn);
+      d += w;
+      if (!ZeroOther) o = fmaf(w, un, o);
+    };
+    auto dface = [&](bool dir) {
+      if (dir) d += VB ? wdir(hc) : 2.0f;
+    };
+    // x: other-colour neighbours at packed p - 1 + S and p + S
+    if (!(S == 0 && p == 0)) face(q.bx[e + S], q.ux[e + S]);
+    else dface(op.dir[0]);
+    if (!(S == 1 && p == op.W - 1)) face(q.bx[e + S + 1], q.ux[e + S + 1]);
+    else dface(op.dir[1]);
+    if (ym) face(el(q.BYm, e), el(q.UYm, e)); else dface(op.dir[2]);
+    if (yp) face(el(q.BYp, e), el(q.UYp, e)); else dface(op.dir[3]);
+    if (zm) face(el(q.BZm, e), el(q.UZm, e)); else dface(op.dir[4]);
+    if (zp) face(el(q.BZp, e), el(q.UZp, e)); else dface(op.dir[5]);
+    float v = __fdividef(fmaf(o, op.ih2, el(q.F, e)), fmaf(d, op.ih2, alpha));
+    if (HasMask && hc < 0.0f) v = el(q.U, e);
+    out[e] = v;
+  }
+  return make_float4(out[0], out[1], out[2], out[3]);
+}
+
 template <bool VB, bool ZeroOther, bool HasMask>
-__global__ void __launch_bounds__(kT) k_half_sweep_v4(Split32 op, float alpha, int col,
-                                                      const float* __restrict__ f,
-                                                      float* __restrict__ u,
-                                                      const float* __restrict__ uo) {
+__global__ void __launch_bounds__(kT, 4) k_half_sweep_v4(Split32 op, float alpha, int col,
+                                                         const float* __restrict__ f,
+                                                         float* __restrict__ u,
+                                                         const float* __restrict__ uo) {
   const unsigned FULL = 0xffffffffu;
   const int W = op.W, ny = op.b.ny, nz = op.b.nz;
   const int lane = threadIdx.x;
@@ -146,24 +197,25 @@ __global__ void __launch_bounds__(kT) k_half_sweep_v4(Split32 op, float alpha, i
   const int pp = min(p0, W - 4);
   const long long t0 = ((long long)k * ny + jj) * W + pp;
   const long long sz = (long long)W * ny;
-  const int s = (jj + k + col) & 1;
   const float* bo = bsel(op, col);
   const float* bt = bsel(op, col ^ 1);
-  const float4 one = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+  const float4 half = make_float4(0.5f, 0.5f, 0.5f, 0.5f);
   const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  const float4 F = ld4(f + t0);
-  const float4 BO = VB ? ld4(bo + t0) : one;
-  const float4 BT = VB ? ld4(bt + t0) : one;
-  const float4 UO = ZeroOther ? zero : ld4(uo + t0);
   const bool ym = jj > 0, yp = jj < ny - 1, zm = k > 0, zp = k < nz - 1;
-  const float4 UYm = (!ZeroOther && ym) ? ld4(uo + t0 - W) : zero;
-  const float4 UYp = (!ZeroOther && yp) ? ld4(uo + t0 + W) : zero;
-  const float4 UZm = (!ZeroOther && zm) ? ld4(uo + t0 - sz) : zero;
-  const float4 UZp = (!ZeroOther && zp) ? ld4(uo + t0 + sz) : zero;
-  const float4 BYm = (VB && ym) ? ld4(bt + t0 - W) : one;
-  const float4 BYp = (VB && yp) ? ld4(bt + t0 + W) : one;
-  const float4 BZm = (VB && zm) ? ld4(bt + t0 - sz) : one;
-  const float4 BZp = (VB && zp) ? ld4(bt + t0 + sz) : one;
+  Quad q;
+  q.F = ld4(f + t0);
+  q.BO = VB ? ld4(bo + t0) : half;
+  const float4 UO = ZeroOther ? zero : ld4(uo + t0);
+  const float4 BT = VB ? ld4(bt + t0) : half;
+  q.UYm = (!ZeroOther && ym) ? ld4(uo + t0 - W) : zero;
+  q.UYp = (!ZeroOther && yp) ? ld4(uo + t0 + W) : zero;
+  q.UZm = (!ZeroOther && zm) ? ld4(uo + t0 - sz) : zero;
+  q.UZp = (!ZeroOther && zp) ? ld4(uo + t0 + sz) : zero;
+  q.BYm = (VB && ym) ? ld4(bt + t0 - W) : half;
+  q.BYp = (VB && yp) ? ld4(bt + t0 + W) : half;
+  q.BZm = (VB && zm) ? ld4(bt + t0 - sz) : half;
+  q.BZp = (VB && zp) ? ld4(bt + t0 + sz) : half;
+  q.U = HasMask ? ld4(u + t0) : zero;
   float uprev = __shfl_up_sync(FULL, UO.w, 1), unext = __shfl_down_sync(FULL, UO.x, 1);
   float bprev = __shfl_up_sync(FULL, BT.w, 1), bnext = __shfl_down_sync(FULL, BT.x, 1);
   if (lane == 0 && pp > 0) {
@@ -174,47 +226,12 @@ __global__ void __launch_bounds__(kT) k_half_sweep_v4(Split32 op, float alpha, i
     if (!ZeroOther) unext = uo[t0 + 4];
     if (VB) bnext = bt[t0 + 4];
   }
-  float4 U = zero;
-  if (HasMask) U = ld4(u + t0);
-  // other-colour values at packed pp-1 .. pp+4
-  const float ux[6] = {uprev, UO.x, UO.y, UO.z, UO.w, unext};
-  const float bx[6] = {bprev, BT.x, BT.y, BT.z, BT.w, bnext};
-  float out[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int p = pp + e;
-    const float bc = el(BO, e);
-    float d = 0.0f, o = 0.0f, w;
-    // x: left neighbour at packed p - 1 + s, right at p + s
-    if (!(p == 0 && s == 0)) {
-      const float un = s ? ux[e + 1] : ux[e], bn = s ? bx[e + 1] : bx[e];
-      w = VB ? wface(bc, bn) : 1.0f;
-      d += w;
-      o += w * un;
-    } else if (op.dir[0]) {
-      d += 2.0f * bc;
-    }
-    if (!(p == W - 1 && s == 1)) {
-      const float un = s ? ux[e + 2] : ux[e + 1], bn = s ? bx[e + 2] : bx[e + 1];
-      w = VB ? wface(bc, bn) : 1.0f;
-      d += w;
-      o += w * un;
-    } else if (op.dir[1]) {
-      d += 2.0f * bc;
-    }
-    if (ym) { w = VB ? wface(bc, el(BYm, e)) : 1.0f; d += w; o += w * el(UYm, e); }
-    else if (op.dir[2]) d += 2.0f * bc;
-    if (yp) { w = VB ? wface(bc, el(BYp, e)) : 1.0f; d += w; o += w * el(UYp, e); }
-    else if (op.dir[3]) d += 2.0f * bc;
-    if (zm) { w = VB ? wface(bc, el(BZm, e)) : 1.0f; d += w; o += w * el(UZm, e); }
-    else if (op.dir[4]) d += 2.0f * bc;
-    if (zp) { w = VB ? wface(bc, el(BZp, e)) : 1.0f; d += w; o += w * el(UZp, e); }
-    else if (op.dir[5]) d += 2.0f * bc;
-    float v = __fdividef(ZeroOther ? el(F, e) : fmaf(o, op.ih2, el(F, e)), fmaf(d, op.ih2, alpha));
-    if (HasMask && bc < 0.0f) v = el(U, e);
-    out[e] = v;
-  }
-  if (active) *reinterpret_cast<float4*>(u + t0) = make_float4(out[0], out[1], out[2], out[3]);
+  q.ux[0] = uprev; q.ux[1] = UO.x; q.ux[2] = UO.y; q.ux[3] = UO.z; q.ux[4] = UO.w; q.ux[5] = unext;
+  q.bx[0] = bprev; q.bx[1] = BT.x; q.bx[2] = BT.y; q.bx[3] = BT.z; q.bx[4] = BT.w; q.bx[5] = bnext;
+  const int s = (jj + k + col) & 1;  // warp-uniform
+  const float4 v = s ? quad_update<VB, ZeroOther, HasMask, 1>(op, alpha, q, pp, ym, yp, zm, zp)
+                     : quad_update<VB, ZeroOther, HasMask, 0>(op, alpha, q, pp, ym, yp, zm, zp);
+  if (active) *reinterpret_cast<float4*>(u + t0) = v;
 }
 
 __device__ __forceinline__ long long spos(const Split32& op, int i, int j, int k) {
@@ -224,7 +241,10 @@ __device__ __forceinline__ long long spos(const Split32& op, int i, int j, int k
 // Residual of the 8 fine children of each coarse cell, averaged into the
 // coarse right-hand side; the coarse unknown is zeroed.  Children of coarse
 // cell (I,J,K) sit at packed index I of fine rows (2J+b, 2K+c).
-template <bool VB>
+// RedOnly: the pre-smoothing ended with a black half-sweep, after which every
+// black cell satisfies its own equation (Gauss-Seidel), so only the four red
+// children carry a residual.
+template <bool VB, bool RedOnly>
 __global__ void __launch_bounds__(kT) k_resid_restrict(Split32 op, Split32 cop, float alpha,
                                                        Ptr2 f, Ptr2 u, MPtr2 fc, MPtr2 uc) {
   const int I = blockIdx.x * 32 + threadIdx.x;
@@ -236,6 +256,7 @@ __global__ void __launch_bounds__(kT) k_resid_restrict(Split32 op, Split32 cop, 
     const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
     const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
     const int col = (a + b + c) & 1;
+    if (RedOnly && col == 1) continue;
     const long long t = spos(op, i, j, k);
     if (VB && bsel(op, col)[t] < 0.0f) continue;
     float diag, off;
@@ -248,48 +269,61 @@ __global__ void __launch_bounds__(kT) k_resid_restrict(Split32 op, Split32 cop, 
   sel(uc, ccol)[ct] = 0.0f;
 }
 
-// coarse correction at a possibly out-of-box coarse index (homogeneous
-// reflection: -1 across Dirichlet faces, +1 across Neumann faces)
-__device__ __forceinline__ float cval(const Split32& cop, const Ptr2& ec, int I, int J, int K) {
-  float s = 1.0f;
-  if (I < 0) { I = 0; if (cop.dir[0]) s = -s; }
-  if (I >= cop.b.nx) { I = cop.b.nx - 1; if (cop.dir[1]) s = -s; }
-  if (J < 0) { J = 0; if (cop.dir[2]) s = -s; }
-  if (J >= cop.b.ny) { J = cop.b.ny - 1; if (cop.dir[3]) s = -s; }
-  if (K < 0) { K = 0; if (cop.dir[4]) s = -s; }
-  if (K >= cop.b.nz) { K = cop.b.nz - 1; if (cop.dir[5]) s = -s; }
-  return s * sel(ec, (I + J + K) & 1)[spos(cop, I, J, K)];
-}
 
 // u_fine += trilinear (27, 9, 3, 1)/64 interpolation of the coarse
 // correction; electrode cells untouched.  One thread per fine x-pair
 // (2p, 2p+1): both cells sit at packed index p (one in each colour) and share
 // the coarse parent I = p, so the 8-point stencils of the pair need 12
 // coarse values.  Block (32, 8) over (p, j), blockIdx.z = k.
-template <bool VB>
+// BlackOnly: post-smoothing starts with a red half-sweep, which overwrites
+// every red cell without reading it, so only black cells are corrected.
+template <bool VB, bool BlackOnly>
 __global__ void __launch_bounds__(kT) k_prolong(Split32 op, Split32 cop, Ptr2 ec, MPtr2 u) {
   const int p = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
   if (p >= op.W || j >= op.b.ny) return;
   const long long t = ((long long)k * op.b.ny + j) * op.W + p;
   const int c0 = (j + k) & 1;  // colour of cell 2p
+  const bool do0 = !BlackOnly || c0 == 1;
+  const bool do1 = (!BlackOnly || c0 == 0) && 2 * p + 1 < op.b.nx;
+  const int cnx = cop.b.nx, cny = cop.b.ny, cnz = cop.b.nz, cW = cop.W;
+  // coarse x positions I-1, I, I+1 (I = p) and the two y / z rows, reflected
+  // at domain faces (sign -1 across Dirichlet faces, +1 across Neumann)
   const int I = p, J = j >> 1, K = k >> 1;
-  const int sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
-  float x0 = 0.0f, x1 = 0.0f;  // y-z weighted x-interpolants of cells 2p and 2p+1
+  const int Jn = J + ((j & 1) ? 1 : -1), Kn = K + ((k & 1) ? 1 : -1);
+  int xi[3] = {I - 1, I, I + 1};
+  float xs[3] = {1.0f, 1.0f, 1.0f};
+  if (xi[0] < 0) { xi[0] = 0; xs[0] = cop.dir[0] ? -1.0f : 1.0f; }
+  if (xi[2] >= cnx) { xi[2] = cnx - 1; xs[2] = cop.dir[1] ? -1.0f : 1.0f; }
+  int yj[2] = {J, Jn};
+  float ys = 1.0f;
+  if (Jn < 0) { yj[1] = 0; ys = cop.dir[2] ? -1.0f : 1.0f; }
+  if (Jn >= cny) { yj[1] = cny - 1; ys = cop.dir[3] ? -1.0f : 1.0f; }
+  int zk[2] = {K, Kn};
+  float zs = 1.0f;
+  if (Kn < 0) { zk[1] = 0; zs = cop.dir[4] ? -1.0f : 1.0f; }
+  if (Kn >= cnz) { zk[1] = cnz - 1; zs = cop.dir[5] ? -1.0f : 1.0f; }
+  float x0 = 0.0f, x1 = 0.0f;  // interpolants of cells 2p and 2p+1
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int b = q & 1, c = q >> 1;
-    const float wyz = (b ? 0.25f : 0.75f) * (c ? 0.25f : 0.75f);
-    const float A = cval(cop, ec, I - 1, J + b * sj, K + c * sk);
-    const float B = cval(cop, ec, I, J + b * sj, K + c * sk);
-    const float C = cval(cop, ec, I + 1, J + b * sj, K + c * sk);
-    x0 = fmaf(wyz, fmaf(0.75f, B, 0.25f * A), x0);
-    x1 = fmaf(wyz, fmaf(0.75f, B, 0.25f * C), x1);
+    const float wyz = (b ? 0.25f * ys : 0.75f) * (c ? 0.25f * zs : 0.75f);
+    const int JJ = yj[b], KK = zk[c];
+    const long long row = ((long long)KK * cny + JJ) * cW;
+    const int par = (JJ + KK) & 1;
+    // coarse cell (X, JJ, KK) has colour (X + JJ + KK) & 1, packed X >> 1
+    const float B = sel(ec, (xi[1] + par) & 1)[row + (xi[1] >> 1)];
+    if (do0) {
+      const float A = xs[0] * sel(ec, (xi[0] + par) & 1)[row + (xi[0] >> 1)];
+      x0 = fmaf(wyz, fmaf(0.75f, B, 0.25f * A), x0);
+    }
+    if (do1) {
+      const float C = xs[2] * sel(ec, (xi[2] + par) & 1)[row + (xi[2] >> 1)];
+      x1 = fmaf(wyz, fmaf(0.75f, B, 0.25f * C), x1);
+    }
   }
-  float* u0 = sel(u, c0);
-  float* u1 = sel(u, c0 ^ 1);
-  if (!(VB && bsel(op, c0)[t] < 0.0f)) u0[t] += x0;
-  if (2 * p + 1 < op.b.nx && !(VB && bsel(op, c0 ^ 1)[t] < 0.0f)) u1[t] += x1;
+  if (do0 && !(VB && bsel(op, c0)[t] < 0.0f)) sel(u, c0)[t] += x0;
+  if (do1 && !(VB && bsel(op, c0 ^ 1)[t] < 0.0f)) sel(u, c0 ^ 1)[t] += x1;
 }
 
 // r = f - A u at every cell of the level (electrode and padding cells: 0).
@@ -331,15 +365,15 @@ __global__ void k_dense_apply(Split32 op, const double* __restrict__ Minv, Ptr2 
   }
 }
 
-// FP32 split beta of one level from the natural FP64 beta (nullable = 1) and
-// mask (nullable): electrode cells get -1.
+// FP32 split coefficient hb = 1/(2 beta) of one level from the natural FP64
+// beta (nullable = 1) and mask (nullable): electrode cells get -1.
 __global__ void k_split_beta(const double* beta, const uint8_t* mask, Split32 op, MPtr2 out) {
   const long long c = (long long)blockIdx.x * kT + threadIdx.x;
   if (c >= op.b.n()) return;
   const int i = (int)(c % op.b.nx);
   const long long jk = c / op.b.nx;
   const int j = (int)(jk % op.b.ny), k = (int)(jk / op.b.ny);
-  const float v = (mask && mask[c]) ? -1.0f : (beta ? (float)beta[c] : 1.0f);
+  const float v = (mask && mask[c]) ? -1.0f : (beta ? (float)(0.5 / beta[c]) : 0.5f);
   sel(out, (i + j + k) & 1)[spos(op, i, j, k)] = v;
 }
 
@@ -373,17 +407,28 @@ void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f
 }
 
 void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
-                              MPtr2 fc, MPtr2 uc, cudaStream_t s) {
+                              MPtr2 fc, MPtr2 uc, bool red_only, cudaStream_t s) {
   dim3 blk(32, 8), g((cop.b.nx + 31) / 32, (cop.b.ny + 7) / 8, cop.b.nz);
-  if (op.beta[0]) k_resid_restrict<true><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
-  else k_resid_restrict<false><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
+  if (op.beta[0]) {
+    if (red_only) k_resid_restrict<true, true><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
+    else k_resid_restrict<true, false><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
+  } else {
+    if (red_only) k_resid_restrict<false, true><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
+    else k_resid_restrict<false, false><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
+  }
   add_launches(1);
 }
 
-void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s) {
+void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, bool black_only,
+                       cudaStream_t s) {
   dim3 blk(32, 8), g((op.W + 31) / 32, (op.b.ny + 7) / 8, op.b.nz);
-  if (op.beta[0]) k_prolong<true><<<g, blk, 0, s>>>(op, cop, ec, u);
-  else k_prolong<false><<<g, blk, 0, s>>>(op, cop, ec, u);
+  if (op.beta[0]) {
+    if (black_only) k_prolong<true, true><<<g, blk, 0, s>>>(op, cop, ec, u);
+    else k_prolong<true, false><<<g, blk, 0, s>>>(op, cop, ec, u);
+  } else {
+    if (black_only) k_prolong<false, true><<<g, blk, 0, s>>>(op, cop, ec, u);
+    else k_prolong<false, false><<<g, blk, 0, s>>>(op, cop, ec, u);
+  }
   add_launches(1);
 }
 
