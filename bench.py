@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--inner-cycles", type=int, default=1)
+    ap.add_argument("--inner-cycles", type=int, default=3)
+    ap.add_argument("--concurrency", type=int, default=4)
+    ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -62,7 +64,8 @@ def workload(n):
 def config(args):
     return {"workload": f"poisson_slab_shell_{args.n}^3 + 3x helmholtz_{args.n}^3 (kappa L = 10, 100, 1000)",
             "grid": [args.n] * 3, "tol": TOL, "precision": args.precision,
-            "inner_cycles": args.inner_cycles, "smoother": "red-black Gauss-Seidel V(2,2)",
+            "inner_cycles": args.inner_cycles, "concurrency": args.concurrency,
+            "graphs": not args.no_graphs, "smoother": "red-black Gauss-Seidel V(2,2)",
             "l2": "inputs larger than L2 (1 GiB per array), no flush"}
 
 
@@ -202,7 +205,7 @@ def traffic_for(cls, launches_bytes):
     return ent["dram_bytes_per_cell"] * ent.get("cells_scale", 1.0) * launches_bytes
 
 
-def roofline(prof, n):
+def roofline(prof, n, wall_ms=None):
     pk, src = peaks()
     fine = {k: v for k, v in prof.items() if k != "coarse" and v["ms"] > 0}
     if not fine:
@@ -214,12 +217,15 @@ def roofline(prof, n):
     gbs = avg_bytes / (avg_ms * 1e-3) / 1e9
     peak = float(pk["hbm_gbs"])
     total_ms = sum(v["ms"] for v in prof.values())
+    step_bytes = sum(v["bytes"] for v in fine.values())
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
             "frac": round(gbs / peak, 4), "traffic": traffic_for(dom, n),
             "kernel": dom, "avg_launch_ms": round(avg_ms, 4),
             "algorithmic_bytes_per_launch": avg_bytes, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
             "class_share": {k: round(v["ms"] / total_ms, 4) for k, v in prof.items() if total_ms > 0},
-            "class_gbs": {k: round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) for k, v in fine.items()}}
+            "class_gbs": {k: round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) for k, v in fine.items()},
+            "fine_level_bytes_per_wall_s_gbs": (round(step_bytes / (wall_ms * 1e-3) / 1e9, 1)
+                                                if wall_ms else None)}
 
 
 # ---------------------------------------------------------------- arms
@@ -271,7 +277,8 @@ def run_ours(args):
     eps = torch.from_numpy(inputs["eps"]).to(dev)
     S = torch.from_numpy(inputs["S"]).to(dev)
     prec = mg.MG_PREC_MIXED if args.precision == "mixed" else mg.MG_PREC_FP64
-    solver = mg.Solver((n, n, n), h, eps_r=eps, precision=prec, inner_cycles=args.inner_cycles)
+    solver = mg.Solver((n, n, n), h, eps_r=eps, precision=prec, inner_cycles=args.inner_cycles,
+                       concurrency=args.concurrency, graphs=not args.no_graphs)
     phi = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
     psi = [torch.zeros_like(phi) for _ in range(3)]
     cycles = [0, 0, 0, 0]
@@ -280,9 +287,8 @@ def run_ours(args):
         phi.zero_()
         for p in psi:
             p.zero_()
-        sp = solver.solve_poisson(rho, phi, TOL)
-        sh = solver.solve_helmholtz_batch(S, psi, KAPPAS, TOL)
-        cycles[:] = [sp["cycles"]] + [s["cycles"] for s in sh]
+        st = solver.solve_set(rho, phi, S, psi, KAPPAS, TOL)
+        cycles[:] = [s["cycles"] for s in st]
 
     def barrier():
         if world > 1:
@@ -332,8 +338,7 @@ def run_ours(args):
         phi.zero_()
         for p in psi:
             p.zero_()
-        solver.solve_poisson(rho_d, phi, TOL)
-        solver.solve_helmholtz_batch(S_d, psi, KAPPAS, TOL)
+        solver.solve_set(rho_d, phi, S_d, psi, KAPPAS, TOL)
         for o, d in zip(out_h, [phi] + psi):
             o.copy_(d, non_blocking=True)
 
@@ -362,7 +367,7 @@ def run_ours(args):
             "data": "synthetic (seeded streamer shell, dielectric slab, smoothed ionisation source)",
             "config": config(args), "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": launches, "cycles_per_problem": cycles,
-            "roofline": roofline(prof, n), "kernel_profile": prof}
+            "roofline": roofline(prof, n, ms), "kernel_profile": prof}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_sample(inputs, n, cycles)
         line["cpu_baseline"] = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -85,7 +85,11 @@ typedef struct {
   int precision;    /* mg_precision: FP64 V-cycles, or FP32 V-cycles inside
                        FP64 iterative refinement (MG_PREC_FP64 = 0) */
   int inner_cycles; /* FP32 V-cycles per refinement step in mixed mode (1) */
-  int reserved[3];  /* must be zero */
+  int concurrency;  /* mixed mode: problems of one call solved concurrently,
+                       each on a library stream with its own work arrays (4, max 4) */
+  int no_graphs;    /* mixed mode: 1 = launch kernels directly instead of
+                       replaying each refinement step as a CUDA graph (0) */
+  int reserved;     /* must be zero */
 } mg_options;
 
 /* Per-solve statistics.  hist[c] is the relative residual after c cycles
@@ -150,6 +154,20 @@ mg_status mg_solve_poisson(mg_ctx* ctx, const double* rho, double* phi, double t
  */
 mg_status mg_solve_helmholtz_batch(mg_ctx* ctx, const double* S, double* const psi[3],
                                    const double kappa[3], double tol, mg_stats stats[3]);
+
+/*
+ * mg_solve_set -- the elliptic solves of one time step of the paper's scheme
+ * (Sec. 2.2: the field update followed by the radiative-transfer update):
+ * the Poisson problem of mg_solve_poisson and the three Helmholtz problems of
+ * mg_solve_helmholtz_batch, in one call.  In mixed precision the four solves
+ * run concurrently on library-owned streams (see mg_options.concurrency), so
+ * the FP64-bound refinement steps of one problem overlap with the
+ * memory-bound FP32 V-cycles of the others.  Arguments as in the two calls
+ * above; stats (nullable) is an array of four: Poisson, then j = 0, 1, 2.
+ */
+mg_status mg_solve_set(mg_ctx* ctx, const double* rho, double* phi, const double* S,
+                       double* const psi[3], const double kappa[3], double tol,
+                       mg_stats stats[4]);
 
 /* ---- instrumentation ------------------------------------------------------
  * Kernel classes of the fine (finest-level) launches: red-black smoothing,

@@ -1,6 +1,7 @@
 // Host side of libmg: context and level hierarchy, V-cycle schedules, FP64
-// iterative refinement around FP32 V-cycles, instrumentation, and the
-// extern "C" entry points declared in include/mg.h.
+// iterative refinement around FP32 V-cycles, the concurrent multi-problem
+// driver with CUDA-graph steps, instrumentation, and the extern "C" entry
+// points declared in include/mg.h.
 //
 // Method: geometric multigrid with red-black Gauss-Seidel smoothing for the
 // second-order cell-centred discretisations of Eqs. 2 and 3 (Sec. 2 of
@@ -8,14 +9,24 @@
 // is replaced by an exact dense inverse of the small coarsest grid.
 //
 // Two precision modes:
-//  - FP64: V(nu1,nu2)-cycles in FP64 on natural-layout arrays.
+//  - FP64: V(nu1,nu2)-cycles in FP64 on natural-layout arrays, one problem
+//    after the other on the context's stream.
 //  - mixed: FP64 iterative refinement.  Each step forms r = b - A u in FP64
 //    (fused kernel, mg_ir.cu), runs FP32 V-cycles on A e = r in red/black
 //    split storage (mg_split32.cu) and adds e to u in the next fused step.
+//    Several problems (the Poisson solve and the three radiative-transfer
+//    solves of a time step) run concurrently, each on its own stream with its
+//    own work arrays, so the FP64-bound refinement kernels of one problem
+//    overlap with the HBM-bound V-cycles of the others.  Each refinement step
+//    (inner V-cycles + FP64 step + norm read-back) is captured once as a CUDA
+//    graph and replayed.
+#include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/mg.h"
@@ -25,6 +36,8 @@ namespace {
 
 constexpr double kEps0 = 8.8541878128e-12;  // F/m (CODATA 2018)
 constexpr int kDenseMax = 4096;             // largest coarsest grid inverted densely
+constexpr int kMaxWork = 4;                 // concurrent problems per context
+constexpr int kMaxGraphs = 8;               // cached step graphs per work slot
 
 thread_local std::string g_last_error;
 
@@ -56,24 +69,21 @@ namespace {
 
 enum Kind { kPoisson = 0, kHelmholtz = 1 };
 
+// Operator data of one level, shared by every problem of the context.
 struct Level {
   mg::Box b{};
   double h = 0, ih2 = 0;
-  int W = 0;             // packed row width of the split arrays
-  long long ns = 0;      // entries per colour array
+  int W = 0;                // packed row width of the split arrays
+  long long ns = 0;         // entries per colour array
   uint8_t* mask = nullptr;  // null when there are no electrode cells
   // Poisson FP64 coefficients (null when eps_r == 1 everywhere)
   double* beta64 = nullptr;
   double *cx = nullptr, *cy = nullptr, *cz = nullptr, *D = nullptr;
-  // FP32 split coefficients: Poisson (eps or mask), Helmholtz (mask only)
+  // FP32 split coefficients 1/(2 beta): Poisson (eps or mask), Helmholtz (mask only)
   float* bp[2] = {nullptr, nullptr};
   float* bh[2] = {nullptr, nullptr};
-  // FP64 correction arrays (levels >= 1) and coarsest residual
+  // FP64-mode correction arrays (levels >= 1) and coarsest residual
   double *u64 = nullptr, *f64 = nullptr, *r64 = nullptr;
-  // FP32 split work arrays
-  float* u32[2] = {nullptr, nullptr};
-  float* f32[2] = {nullptr, nullptr};
-  float* r32[2] = {nullptr, nullptr};
 };
 
 struct Coarse {
@@ -88,6 +98,40 @@ struct ProfRec {
   cudaEvent_t a, b;
 };
 
+// FP32 arrays of one level for one problem
+struct LevelWork {
+  float* u32[2] = {nullptr, nullptr};
+  float* f32[2] = {nullptr, nullptr};
+  float* r32[2] = {nullptr, nullptr};
+};
+
+// One captured refinement step.
+struct StepGraph {
+  int kind = 0;
+  double alpha = 0;
+  int ic = 0;
+  bool prof = false;
+  const double* b = nullptr;
+  const double* u_in = nullptr;
+  double* u_out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+  std::vector<ProfRec> recs;  // event pairs baked into the graph (profiling)
+  unsigned long long stamp = 0;
+};
+
+// Everything one problem needs to run concurrently with the others.
+struct Work {
+  cudaStream_t s = nullptr;
+  std::vector<LevelWork> lw;
+  double* phi_tmp = nullptr;  // ping-pong partner of the caller's iterate
+  double* partial = nullptr;
+  double* norm_dev = nullptr;   // [2]
+  double* norm_host = nullptr;  // [2], pinned
+  cudaEvent_t ev = nullptr, t0 = nullptr, t1 = nullptr;
+  std::vector<StepGraph> graphs;
+};
+
 }  // namespace
 
 struct mg_ctx {
@@ -97,20 +141,20 @@ struct mg_ctx {
   cudaStream_t stream = nullptr;
   std::vector<Level> lv;
   double* mask_value = nullptr;
-  double* b64 = nullptr;      // FP64-mode Poisson right-hand side with lifts
-  double* phi_tmp = nullptr;  // ping-pong partner of the caller's iterate
-  double* partial = nullptr;
+  double* b64 = nullptr;  // Poisson right-hand side with lifts
   int npartial = 0;
-  double* norm_dev = nullptr;
-  double* norm_host = nullptr;  // pinned
   double *gj_row = nullptr, *gj_col = nullptr;
   std::vector<Coarse> coarse;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<Work*> work;
+  cudaEvent_t fork = nullptr;
   std::vector<void*> allocs;
+  std::vector<void*> host_allocs;
+  unsigned long long clock = 0;
   // instrumentation
   bool prof = false;
   std::vector<ProfRec> pending;
   std::vector<cudaEvent_t> pool;
+  std::vector<ProfRec>* capture = nullptr;  // event pairs go into a graph
   mg_kprof acc[MG_KCLASS_COUNT] = {};
 
   template <class T>
@@ -128,35 +172,49 @@ namespace {
 
 // ---- instrumentation --------------------------------------------------------
 
+cudaEvent_t take_event(mg_ctx* c) {
+  if (c->pool.empty()) {
+    for (int q = 0; q < 16; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) == cudaSuccess) c->pool.push_back(e);
+    }
+  }
+  if (c->pool.empty()) return nullptr;
+  cudaEvent_t e = c->pool.back();
+  c->pool.pop_back();
+  return e;
+}
+
+// Brackets one launch: counts it and, with profiling on, times it with an
+// event pair on the launching stream (inside a graph capture the pair
+// becomes two event-record nodes of the graph).
 struct Scope {
   mg_ctx* c;
+  cudaStream_t s;
   int cls;
   double bytes;
   cudaEvent_t a = nullptr;
-  Scope(mg_ctx* ctx, int k, double by) : c(ctx), cls(k), bytes(by) {
-    c->acc[cls].launches += 1;
+  Scope(mg_ctx* ctx, cudaStream_t st, int k, double by) : c(ctx), s(st), cls(k), bytes(by) {
+    if (!c->capture) c->acc[cls].launches += 1;
     if (!c->prof) return;
-    if (c->pool.size() < 2) {
-      for (int q = 0; q < 16; ++q) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) == cudaSuccess) c->pool.push_back(e);
-      }
-    }
-    if (c->pool.size() < 2) return;
-    a = c->pool.back();
-    c->pool.pop_back();
-    cudaEventRecord(a, c->stream);
+    a = take_event(c);
+    if (a) record(a);
+  }
+  // inside a capture, an external record makes a real event-record node
+  void record(cudaEvent_t e) {
+    if (c->capture) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else cudaEventRecord(e, s);
   }
   ~Scope() {
     if (!a) return;
-    cudaEvent_t b = c->pool.back();
-    c->pool.pop_back();
-    cudaEventRecord(b, c->stream);
-    c->pending.push_back({cls, bytes, a, b});
+    cudaEvent_t b = take_event(c);
+    if (!b) return;
+    record(b);
+    (c->capture ? *c->capture : c->pending).push_back({cls, bytes, a, b});
   }
 };
 
-// After a stream synchronisation: fold the finished event pairs in.
+// Fold finished event pairs in (after the stream they ran on completed).
 void harvest(mg_ctx* c) {
   for (const ProfRec& r : c->pending) {
     float ms = 0.0f;
@@ -168,6 +226,17 @@ void harvest(mg_ctx* c) {
     c->pool.push_back(r.b);
   }
   c->pending.clear();
+}
+
+void harvest_graph(mg_ctx* c, const StepGraph& g) {
+  for (const ProfRec& r : g.recs) {
+    float ms = 0.0f;
+    c->acc[r.cls].launches += 1;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->acc[r.cls].ms += ms;
+      c->acc[r.cls].bytes += r.bytes;
+    }
+  }
 }
 
 uint8_t poisson_dir(const mg_ctx* c, int f) { return c->bc.kind[f] == MG_BC_DIRICHLET; }
@@ -213,13 +282,15 @@ mg_status check_launch() {
   return MG_OK;
 }
 
-// Dense inverse of the coarsest operator for (kind, alpha), built on first use.
+// Dense inverse of the coarsest operator for (kind, alpha), built on first
+// use on the context's stream (never during a graph capture).
 mg_status coarse_inverse(mg_ctx* c, Kind kind, double alpha, const double** out) {
   for (const Coarse& q : c->coarse)
     if (q.kind == kind && q.alpha == alpha) {
       *out = q.Minv;
       return MG_OK;
     }
+  if (c->capture) return fail(MG_ERR_CUDA, "coarsest inverse requested during a graph capture");
   const int l = (int)c->lv.size() - 1;
   const long long n = c->lv[l].b.n();
   if (n > kDenseMax) return fail(MG_ERR_UNSUPPORTED, "coarsest grid too large for a dense inverse");
@@ -230,6 +301,37 @@ mg_status coarse_inverse(mg_ctx* c, Kind kind, double alpha, const double** out)
   MG_TRY(check_launch());
   c->coarse.push_back({kind, alpha, M});
   *out = M;
+  return MG_OK;
+}
+
+// Work slot q (allocated on first use).
+mg_status get_work(mg_ctx* c, int q, Work** out) {
+  while ((int)c->work.size() <= q) {
+    Work* w = new (std::nothrow) Work;
+    if (!w) return fail(MG_ERR_OOM, "host allocation failed");
+    c->work.push_back(w);
+    MG_CUDA(cudaStreamCreateWithFlags(&w->s, cudaStreamNonBlocking));
+    MG_CUDA(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming));
+    MG_CUDA(cudaEventCreate(&w->t0));
+    MG_CUDA(cudaEventCreate(&w->t1));
+    const int nlev = (int)c->lv.size();
+    w->lw.resize(nlev);
+    for (int l = 0; l < nlev; ++l)
+      for (int col = 0; col < 2; ++col) {
+        const size_t ns = (size_t)c->lv[l].ns;
+        MG_TRY(c->alloc(&w->lw[l].u32[col], ns, true));
+        MG_TRY(c->alloc(&w->lw[l].f32[col], ns, true));
+        if (l == nlev - 1) MG_TRY(c->alloc(&w->lw[l].r32[col], ns, true));
+      }
+    MG_TRY(c->alloc(&w->phi_tmp, (size_t)c->lv[0].b.n()));
+    MG_TRY(c->alloc(&w->partial, (size_t)c->npartial));
+    MG_TRY(c->alloc(&w->norm_dev, 2));
+    MG_CUDA(cudaMallocHost((void**)&w->norm_host, 2 * sizeof(double)));
+    c->host_allocs.push_back(w->norm_host);
+    // the zero fills above ran on the context's stream
+    MG_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  *out = c->work[q];
   return MG_OK;
 }
 
@@ -246,11 +348,11 @@ mg_status vcycle64(mg_ctx* c, Kind kind, double alpha, int l, const double* f, d
     const double* Minv;
     MG_TRY(coarse_inverse(c, kind, alpha, &Minv));
     {
-      Scope sc(c, MG_KCLASS_COARSE, 0);
+      Scope sc(c, s, MG_KCLASS_COARSE, 0);
       mg::launch_resid64(op, alpha, f, u, c->lv[l].r64, s);
     }
     {
-      Scope sc(c, MG_KCLASS_COARSE, 0);
+      Scope sc(c, s, MG_KCLASS_COARSE, 0);
       mg::launch_dense_apply64(Minv, (int)c->lv[l].b.n(), c->lv[l].r64, u, s);
     }
     return check_launch();
@@ -258,19 +360,19 @@ mg_status vcycle64(mg_ctx* c, Kind kind, double alpha, int l, const double* f, d
   auto smooth = [&](int sweeps) {
     for (int q = 0; q < sweeps; ++q)
       for (int col = 0; col < 2; ++col) {
-        Scope sc(c, cls_s, n * (8.0 + 4.0 + 4.0 + fb));
+        Scope sc(c, s, cls_s, n * (8.0 + 4.0 + 4.0 + fb));
         mg::launch_rbgs64(op, alpha, f, u, col, s);
       }
   };
   smooth(c->opt.nu1);
   Level& C = c->lv[l + 1];
   {
-    Scope sc(c, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE, n * (16.0 + fb + 2.0));
+    Scope sc(c, s, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE, n * (16.0 + fb + 2.0));
     mg::launch_resid_restrict64(op, alpha, f, u, C.f64, C.u64, s);
   }
   MG_TRY(vcycle64(c, kind, alpha, l + 1, C.f64, C.u64));
   {
-    Scope sc(c, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE, n * (16.0 + 1.0 + fb));
+    Scope sc(c, s, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE, n * (16.0 + 1.0 + fb));
     mg::launch_prolong64(op, C.u64, u, s);
   }
   smooth(c->opt.nu2);
@@ -281,10 +383,11 @@ mg_status vcycle64(mg_ctx* c, Kind kind, double alpha, int l, const double* f, d
 
 // first_zero: the level's unknown is zero on entry (the first half-sweep
 // need not read the other colour).
-mg_status vcycle32(mg_ctx* c, Kind kind, double alpha, int l, bool first_zero) {
-  cudaStream_t s = c->stream;
+mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool first_zero) {
+  cudaStream_t s = w->s;
   const int Lc = (int)c->lv.size() - 1;
   Level& L = c->lv[l];
+  LevelWork& X = w->lw[l];
   mg::Split32 op = sop(c, l, kind);
   const float a32 = (float)alpha;
   const double n = (double)L.b.n();
@@ -293,12 +396,12 @@ mg_status vcycle32(mg_ctx* c, Kind kind, double alpha, int l, bool first_zero) {
     const double* Minv;
     MG_TRY(coarse_inverse(c, kind, alpha, &Minv));
     {
-      Scope sc(c, MG_KCLASS_COARSE, 0);
-      mg::launch_resid32s(op, a32, cp(L.f32), cp(L.u32), mp(L.r32), s);
+      Scope sc(c, s, MG_KCLASS_COARSE, 0);
+      mg::launch_resid32s(op, a32, cp(X.f32), cp(X.u32), mp(X.r32), s);
     }
     {
-      Scope sc(c, MG_KCLASS_COARSE, 0);
-      mg::launch_dense_apply32s(op, Minv, cp(L.r32), mp(L.u32), s);
+      Scope sc(c, s, MG_KCLASS_COARSE, 0);
+      mg::launch_dense_apply32s(op, Minv, cp(X.r32), mp(X.u32), s);
     }
     return check_launch();
   }
@@ -308,29 +411,29 @@ mg_status vcycle32(mg_ctx* c, Kind kind, double alpha, int l, bool first_zero) {
       for (int col = 0; col < 2; ++col) {
         const bool zo = zero && q == 0 && col == 0;
         // other colour (unless known zero) + own rhs + own write + coefficients
-        Scope sc(c, cls_s, n * ((zo ? 0.0 : 2.0) + 2.0 + 2.0 + fb));
-        mg::launch_half_sweep32(op, a32, col, L.f32[col], L.u32[col], L.u32[col ^ 1], zo,
+        Scope sc(c, s, cls_s, n * ((zo ? 0.0 : 2.0) + 2.0 + 2.0 + fb));
+        mg::launch_half_sweep32(op, a32, col, X.f32[col], X.u32[col], X.u32[col ^ 1], zo,
                                 L.mask != nullptr, s);
       }
   };
   smooth(c->opt.nu1, first_zero);
-  Level& C = c->lv[l + 1];
+  LevelWork& Y = w->lw[l + 1];
   mg::Split32 cop = sop(c, l + 1, kind);
   {
     const bool red_only = c->opt.nu1 > 0;
     // u both colours, f (red only if red_only), beta both colours, coarse f and u
-    Scope sc(c, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE,
+    Scope sc(c, s, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE,
              n * (4.0 + (red_only ? 2.0 : 4.0) + fb + 1.0));
-    mg::launch_resid_restrict32s(op, cop, a32, cp(L.f32), cp(L.u32), mp(C.f32), mp(C.u32),
+    mg::launch_resid_restrict32s(op, cop, a32, cp(X.f32), cp(X.u32), mp(Y.f32), mp(Y.u32),
                                  red_only, s);
   }
-  MG_TRY(vcycle32(c, kind, alpha, l + 1, true));
+  MG_TRY(vcycle32(c, w, kind, alpha, l + 1, true));
   {
     const bool black_only = c->opt.nu2 > 0;
     // fine u read + write (black only if black_only), coarse e, beta for the electrode test
-    Scope sc(c, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE,
+    Scope sc(c, s, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE,
              n * ((black_only ? 4.0 : 8.0) + 0.5 + (black_only ? fb / 2 : fb)));
-    mg::launch_prolong32s(op, cop, cp(C.u32), mp(L.u32), black_only, s);
+    mg::launch_prolong32s(op, cop, cp(Y.u32), mp(X.u32), black_only, s);
   }
   smooth(c->opt.nu2, false);
   return check_launch();
@@ -338,122 +441,357 @@ mg_status vcycle32(mg_ctx* c, Kind kind, double alpha, int l, bool first_zero) {
 
 // ---- FP64 refinement step / residual norm ----------------------------------
 
-struct Rhs {
-  const double* p;
-  double scale;
-  bool lift;
-};
-
-// One fused FP64 pass on level 0 (see mg_ir.cu); returns ||r||_2 (syncs).
-mg_status ir_step(mg_ctx* c, Kind kind, double alpha, const Rhs& rhs, const double* u_in,
-                  double* u_out, bool with_e, bool store_r, bool zero_free, double* norm) {
+// Enqueue one fused FP64 pass on level 0 and the read-back of ||r||^2 into
+// w->norm_host[slot] (asynchronous).
+mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha,
+                     const double* b, const double* u_in, double* u_out, bool with_e,
+                     bool store_r, bool zero_free, int slot) {
   Level& L0 = c->lv[0];
+  LevelWork& X = w->lw[0];
   mg::IrArgs a{};
   a.op = op64(c, 0, kind);
   a.alpha = alpha;
-  a.rhs = rhs.p;
-  a.rhs_scale = rhs.scale;
-  a.lift = rhs.lift ? 1 : 0;
+  a.rhs = b;
+  a.rhs_scale = 1.0;
+  a.lift = 0;
   a.beta0 = L0.beta64;
-  for (int f = 0; f < 6; ++f) a.bval.v[f] = kind == kPoisson ? c->bc.value[f] : 0.0;
   a.u_in = u_in;
   a.u_out = u_out;
-  a.e[0] = with_e ? L0.u32[0] : nullptr;
-  a.e[1] = with_e ? L0.u32[1] : nullptr;
-  a.r[0] = store_r ? L0.f32[0] : nullptr;
-  a.r[1] = store_r ? L0.f32[1] : nullptr;
+  a.e[0] = with_e ? X.u32[0] : nullptr;
+  a.e[1] = with_e ? X.u32[1] : nullptr;
+  a.r[0] = store_r ? X.f32[0] : nullptr;
+  a.r[1] = store_r ? X.f32[1] : nullptr;
   a.W = L0.W;
-  a.partial = c->partial;
+  a.partial = w->partial;
   const double n = (double)L0.b.n();
   const double bytes = n * (8.0 + 8.0 + (a.op.cx ? 32.0 : (a.op.mask ? 1.0 : 0.0)) +
                             (with_e ? 4.0 : 0.0) + (u_out ? 8.0 : 0.0) + (store_r ? 4.0 : 0.0));
   {
-    Scope sc(c, MG_KCLASS_RESID64, bytes);
-    mg::launch_ir_fused(a, zero_free, c->stream);
+    Scope sc(c, s, MG_KCLASS_RESID64, bytes);
+    mg::launch_ir_fused(a, zero_free, s);
   }
   {
-    Scope sc(c, MG_KCLASS_COARSE, 0);
-    mg::launch_sum_partials(c->partial, c->npartial, c->norm_dev, c->stream);
+    Scope sc(c, s, MG_KCLASS_COARSE, 0);
+    mg::launch_sum_partials(w->partial, c->npartial, w->norm_dev + slot, s);
   }
   MG_TRY(check_launch());
-  MG_CUDA(cudaMemcpyAsync(c->norm_host, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost,
-                          c->stream));
-  MG_CUDA(cudaStreamSynchronize(c->stream));
-  harvest(c);
-  *norm = std::sqrt(*c->norm_host);
+  MG_CUDA(cudaMemcpyAsync(w->norm_host + slot, w->norm_dev + slot, sizeof(double),
+                          cudaMemcpyDeviceToHost, s));
   return MG_OK;
 }
 
-// Solve A u = b on level 0 for one problem.  Electrode cells of u already
-// hold their values.  b64 (FP64 mode only) is b with the lifts.
-mg_status solve_one(mg_ctx* c, Kind kind, double alpha, const Rhs& rhs, const double* b64,
-                    double* u, double tol, mg_stats* st) {
-  if (st) {
-    std::memset(st, 0, sizeof(*st));
-    MG_CUDA(cudaEventRecord(c->ev0, c->stream));
-  }
-  const bool mixed = c->opt.precision == MG_PREC_MIXED;
-  double bnorm, rnorm;
-  MG_TRY(ir_step(c, kind, alpha, rhs, u, nullptr, false, false, true, &bnorm));
-  if (!std::isfinite(bnorm)) return fail(MG_ERR_NONFINITE, "non-finite right-hand side");
-  if (bnorm == 0.0) bnorm = 1.0;
-  MG_TRY(ir_step(c, kind, alpha, rhs, u, nullptr, false, mixed, false, &rnorm));
-  double rel = rnorm / bnorm;
+// One problem of a (possibly concurrent) solve.
+struct Prob {
+  Kind kind;
+  double alpha;
+  const double* b;  // right-hand side with lifts
+  double* u;        // caller's iterate (electrode values already set)
+  double tol;
+  mg_stats* st;
+  Work* w = nullptr;
+  double* cur = nullptr;
+  double* other = nullptr;
   int cyc = 0;
-  if (st) st->hist[0] = rel;
-  double* cur = u;
-  double* other = c->phi_tmp;
-  while (std::isfinite(rel) && rel > tol && cyc < c->opt.max_cycles) {
-    if (mixed) {
-      for (int q = 0; q < c->opt.inner_cycles; ++q) MG_TRY(vcycle32(c, kind, alpha, 0, q == 0));
-      MG_TRY(ir_step(c, kind, alpha, rhs, cur, other, true, true, false, &rnorm));
-      std::swap(cur, other);
-    } else {
-      MG_TRY(vcycle64(c, kind, alpha, 0, b64, u));
-      MG_TRY(ir_step(c, kind, alpha, rhs, u, nullptr, false, false, false, &rnorm));
+  double bnorm = 1.0, rel = 0.0;
+  int phase = 0;
+  bool done = false;
+  mg_status status = MG_OK;
+  const StepGraph* g = nullptr;
+};
+
+Prob make_prob(Kind kind, double alpha, const double* b, double* u, double tol, mg_stats* st) {
+  Prob p;
+  p.kind = kind;
+  p.alpha = alpha;
+  p.b = b;
+  p.u = u;
+  p.tol = tol;
+  p.st = st;
+  return p;
+}
+
+// The refinement step of p: inner V-cycles on A e = r, then the fused FP64
+// step u_out = u_in + e, r = b - A u_out, ||r||^2 -> host slot 1.
+mg_status enqueue_step_direct(mg_ctx* c, Prob& p) {
+  for (int q = 0; q < c->opt.inner_cycles; ++q)
+    MG_TRY(vcycle32(c, p.w, p.kind, p.alpha, 0, q == 0));
+  return enqueue_ir(c, p.w, p.w->s, p.kind, p.alpha, p.b, p.cur, p.other, true, true, false, 1);
+}
+
+// Cached graph of the step for p's current (u_in, u_out) parity.
+mg_status step_graph(mg_ctx* c, Prob& p, const StepGraph** out) {
+  Work* w = p.w;
+  const int ic = c->opt.inner_cycles;
+  for (StepGraph& g : w->graphs)
+    if (g.kind == p.kind && g.alpha == p.alpha && g.ic == ic && g.prof == c->prof && g.b == p.b &&
+        g.u_in == p.cur && g.u_out == p.other) {
+      g.stamp = ++c->clock;
+      *out = &g;
+      return MG_OK;
     }
-    rel = rnorm / bnorm;
-    ++cyc;
-    if (st && cyc < 64) st->hist[cyc] = rel;
+  const double* Minv;
+  MG_TRY(coarse_inverse(c, p.kind, p.alpha, &Minv));  // never inside the capture
+  if ((int)w->graphs.size() >= kMaxGraphs) {         // evict the least recently used
+    size_t old = 0;
+    for (size_t q = 1; q < w->graphs.size(); ++q)
+      if (w->graphs[q].stamp < w->graphs[old].stamp) old = q;
+    cudaGraphExecDestroy(w->graphs[old].exec);
+    for (const ProfRec& r : w->graphs[old].recs) {
+      c->pool.push_back(r.a);
+      c->pool.push_back(r.b);
+    }
+    w->graphs.erase(w->graphs.begin() + old);
   }
-  if (cur != u) {
-    MG_CUDA(cudaMemcpyAsync(u, cur, sizeof(double) * c->lv[0].b.n(), cudaMemcpyDeviceToDevice,
-                            c->stream));
+  StepGraph g;
+  g.kind = p.kind;
+  g.alpha = p.alpha;
+  g.ic = ic;
+  g.prof = c->prof;
+  g.b = p.b;
+  g.u_in = p.cur;
+  g.u_out = p.other;
+  // the event pool must not need to grow inside the capture
+  if (c->prof)
+    while (c->pool.size() < 1024) {
+      cudaEvent_t e;
+      MG_CUDA(cudaEventCreate(&e));
+      c->pool.push_back(e);
+    }
+  const long long l0 = mg::launch_count();
+  MG_CUDA(cudaStreamBeginCapture(w->s, cudaStreamCaptureModeThreadLocal));
+  c->capture = &g.recs;
+  mg_status st = enqueue_step_direct(c, p);
+  c->capture = nullptr;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(w->s, &graph);
+  if (st != MG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
   }
-  if (st) {
-    MG_CUDA(cudaEventRecord(c->ev1, c->stream));
-    MG_CUDA(cudaEventSynchronize(c->ev1));
-    float ms = 0;
-    MG_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-    st->cycles = cyc;
-    st->rel_resid = rel;
-    st->converged = rel <= tol;
-    st->time_ms = ms;
+  if (ec != cudaSuccess)
+    return fail(MG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess)
+    return fail(MG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+  g.launches = mg::launch_count() - l0;
+  mg::add_launches(-g.launches);  // counted again at every replay
+  g.stamp = ++c->clock;
+  w->graphs.push_back(std::move(g));
+  *out = &w->graphs.back();
+  return MG_OK;
+}
+
+mg_status enqueue_step(mg_ctx* c, Prob& p) {
+  p.g = nullptr;
+  if (c->opt.no_graphs) {
+    MG_TRY(enqueue_step_direct(c, p));
   } else {
-    MG_CUDA(cudaStreamSynchronize(c->stream));
+    const StepGraph* g;
+    MG_TRY(step_graph(c, p, &g));
+    MG_CUDA(cudaGraphLaunch(g->exec, p.w->s));
+    mg::add_launches(g->launches);
+    p.g = g;
+  }
+  MG_CUDA(cudaEventRecord(p.w->ev, p.w->s));
+  return MG_OK;
+}
+
+mg_status finish(mg_ctx* c, Prob& p) {
+  if (p.cur != p.u)
+    MG_CUDA(cudaMemcpyAsync(p.u, p.cur, sizeof(double) * c->lv[0].b.n(), cudaMemcpyDeviceToDevice,
+                            p.w->s));
+  if (p.st) MG_CUDA(cudaEventRecord(p.w->t1, p.w->s));
+  p.done = true;
+  if (!std::isfinite(p.rel)) {
+    p.status = MG_ERR_NONFINITE;
+    g_last_error = "non-finite value in input or residual";
+  } else if (p.rel > p.tol) {
+    p.status = MG_ERR_NOT_CONVERGED;
+    char msg[128];
+    std::snprintf(msg, sizeof msg, "not converged: rel. residual %.3e after %d steps", p.rel, p.cyc);
+    g_last_error = msg;
+  }
+  return MG_OK;
+}
+
+// Host side of one finished step of p.
+mg_status advance(mg_ctx* c, Prob& p) {
+  const double* h = p.w->norm_host;
+  if (p.g) harvest_graph(c, *p.g);
+  if (p.phase == 0) {
+    p.bnorm = std::sqrt(h[0]);
+    if (!std::isfinite(p.bnorm)) {
+      p.rel = p.bnorm;
+      return finish(c, p);
+    }
+    if (p.bnorm == 0.0) p.bnorm = 1.0;
+    p.phase = 1;
+  } else {
+    std::swap(p.cur, p.other);
+    ++p.cyc;
+  }
+  p.rel = std::sqrt(h[1]) / p.bnorm;
+  if (p.st && p.cyc < 64) p.st->hist[p.cyc] = p.rel;
+  if (!std::isfinite(p.rel) || p.rel <= p.tol || p.cyc >= c->opt.max_cycles) return finish(c, p);
+  return enqueue_step(c, p);
+}
+
+// Mixed-precision solve of several problems concurrently (one work slot and
+// stream each).  Returns the worst status; outputs are complete on return.
+mg_status solve_mixed(mg_ctx* c, std::vector<Prob>& P) {
+  for (size_t q = 0; q < P.size(); ++q) {
+    MG_TRY(get_work(c, (int)q, &P[q].w));
+    const double* Minv;
+    MG_TRY(coarse_inverse(c, P[q].kind, P[q].alpha, &Minv));
+  }
+  MG_CUDA(cudaEventRecord(c->fork, c->stream));
+  for (Prob& p : P) {
+    Work* w = p.w;
+    MG_CUDA(cudaStreamWaitEvent(w->s, c->fork, 0));
+    if (p.st) {
+      std::memset(p.st, 0, sizeof(*p.st));
+      MG_CUDA(cudaEventRecord(w->t0, w->s));
+    }
+    p.cur = p.u;
+    p.other = w->phi_tmp;
+    // ||b|| (slot 0) and the residual of the initial guess (slot 1, r -> FP32)
+    MG_TRY(enqueue_ir(c, w, w->s, p.kind, p.alpha, p.b, p.u, nullptr, false, false, true, 0));
+    MG_TRY(enqueue_ir(c, w, w->s, p.kind, p.alpha, p.b, p.u, nullptr, false, true, false, 1));
+    MG_CUDA(cudaEventRecord(w->ev, w->s));
+  }
+  size_t left = P.size();
+  while (left) {
+    bool progress = false;
+    for (Prob& p : P) {
+      if (p.done) continue;
+      const cudaError_t q = cudaEventQuery(p.w->ev);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return fail(MG_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(q));
+      progress = true;
+      MG_TRY(advance(c, p));
+      if (p.done) --left;
+    }
+    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  mg_status worst = MG_OK;
+  for (Prob& p : P) {
+    MG_CUDA(cudaStreamSynchronize(p.w->s));
+    if (p.st) {
+      float ms = 0;
+      MG_CUDA(cudaEventElapsedTime(&ms, p.w->t0, p.w->t1));
+      p.st->cycles = p.cyc;
+      p.st->rel_resid = p.rel;
+      p.st->converged = p.rel <= p.tol;
+      p.st->time_ms = ms;
+    }
+    if (p.status == MG_ERR_NONFINITE || (p.status != MG_OK && worst == MG_OK)) worst = p.status;
   }
   harvest(c);
-  if (!std::isfinite(rel)) return fail(MG_ERR_NONFINITE, "non-finite residual");
-  if (rel > tol) {
+  if (worst == MG_ERR_NONFINITE) g_last_error = "non-finite value in input or residual";
+  return worst;
+}
+
+// FP64-mode solve of one problem on the context's stream.
+mg_status solve_fp64(mg_ctx* c, Prob& p) {
+  Work* w;
+  MG_TRY(get_work(c, 0, &w));
+  cudaStream_t s = c->stream;
+  if (p.st) {
+    std::memset(p.st, 0, sizeof(*p.st));
+    MG_CUDA(cudaEventRecord(w->t0, s));
+  }
+  auto norms = [&](bool with_b) -> mg_status {
+    if (with_b) MG_TRY(enqueue_ir(c, w, s, p.kind, p.alpha, p.b, p.u, nullptr, false, false, true, 0));
+    MG_TRY(enqueue_ir(c, w, s, p.kind, p.alpha, p.b, p.u, nullptr, false, false, false, 1));
+    MG_CUDA(cudaStreamSynchronize(s));
+    harvest(c);
+    return MG_OK;
+  };
+  MG_TRY(norms(true));
+  p.bnorm = std::sqrt(w->norm_host[0]);
+  if (!std::isfinite(p.bnorm)) return fail(MG_ERR_NONFINITE, "non-finite right-hand side");
+  if (p.bnorm == 0.0) p.bnorm = 1.0;
+  p.rel = std::sqrt(w->norm_host[1]) / p.bnorm;
+  if (p.st) p.st->hist[0] = p.rel;
+  while (std::isfinite(p.rel) && p.rel > p.tol && p.cyc < c->opt.max_cycles) {
+    MG_TRY(vcycle64(c, p.kind, p.alpha, 0, p.b, p.u));
+    MG_TRY(norms(false));
+    p.rel = std::sqrt(w->norm_host[1]) / p.bnorm;
+    ++p.cyc;
+    if (p.st && p.cyc < 64) p.st->hist[p.cyc] = p.rel;
+  }
+  if (p.st) {
+    MG_CUDA(cudaEventRecord(w->t1, s));
+    MG_CUDA(cudaEventSynchronize(w->t1));
+    float ms = 0;
+    MG_CUDA(cudaEventElapsedTime(&ms, w->t0, w->t1));
+    p.st->cycles = p.cyc;
+    p.st->rel_resid = p.rel;
+    p.st->converged = p.rel <= p.tol;
+    p.st->time_ms = ms;
+  }
+  if (!std::isfinite(p.rel)) return fail(MG_ERR_NONFINITE, "non-finite residual");
+  if (p.rel > p.tol) {
     char msg[128];
-    std::snprintf(msg, sizeof msg, "not converged: rel. residual %.3e after %d cycles", rel, cyc);
+    std::snprintf(msg, sizeof msg, "not converged: rel. residual %.3e after %d cycles", p.rel, p.cyc);
     return fail(MG_ERR_NOT_CONVERGED, msg);
   }
   return MG_OK;
 }
 
+bool hard_error(mg_status st) {
+  return st == MG_ERR_CUDA || st == MG_ERR_OOM || st == MG_ERR_UNSUPPORTED ||
+         st == MG_ERR_INVALID_ARG;
+}
+
+mg_status solve(mg_ctx* c, std::vector<Prob>& P) {
+  mg_status worst = MG_OK;
+  if (c->opt.precision == MG_PREC_MIXED) {
+    // at most kMaxWork (and opt.concurrency) problems at a time
+    const size_t width = (size_t)std::max(1, std::min(c->opt.concurrency, kMaxWork));
+    for (size_t q0 = 0; q0 < P.size(); q0 += width) {
+      std::vector<Prob> part(P.begin() + q0, P.begin() + std::min(P.size(), q0 + width));
+      const mg_status st = solve_mixed(c, part);
+      if (hard_error(st)) return st;
+      if (st == MG_ERR_NONFINITE || (st != MG_OK && worst == MG_OK)) worst = st;
+    }
+    return worst;
+  }
+  for (Prob& p : P) {
+    const mg_status st = solve_fp64(c, p);
+    if (hard_error(st)) return st;
+    if (st == MG_ERR_NONFINITE || (st != MG_OK && worst == MG_OK)) worst = st;
+  }
+  return worst;
+}
+
 void destroy(mg_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (Work* w : c->work) {
+    if (w->s) cudaStreamSynchronize(w->s);
+    for (StepGraph& g : w->graphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      for (const ProfRec& r : g.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+      }
+    }
+    if (w->s) cudaStreamDestroy(w->s);
+    if (w->ev) cudaEventDestroy(w->ev);
+    if (w->t0) cudaEventDestroy(w->t0);
+    if (w->t1) cudaEventDestroy(w->t1);
+    delete w;
+  }
   for (const ProfRec& r : c->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
-  if (c->norm_host) cudaFreeHost(c->norm_host);
-  if (c->ev0) cudaEventDestroy(c->ev0);
-  if (c->ev1) cudaEventDestroy(c->ev1);
+  for (void* p : c->host_allocs) cudaFreeHost(p);
+  if (c->fork) cudaEventDestroy(c->fork);
   delete c;
 }
 
@@ -475,6 +813,9 @@ mg_status build(mg_ctx* c, const double* eps_r, const uint8_t* mask, const doubl
     h *= 2.0;
   }
   const int nlev = (int)c->lv.size();
+  const long long nc = c->lv.back().b.n();
+  if (nc > kDenseMax)
+    return fail(MG_ERR_UNSUPPORTED, "grid does not coarsen to <= 4096 cells (need even sizes)");
   for (int l = 0; l < nlev; ++l) {
     Level& L = c->lv[l];
     const size_t n = (size_t)L.b.n();
@@ -489,15 +830,14 @@ mg_status build(mg_ctx* c, const double* eps_r, const uint8_t* mask, const doubl
     for (int col = 0; col < 2; ++col) {
       if (eps_r || mask) MG_TRY(c->alloc(&L.bp[col], (size_t)L.ns, true));
       if (mask) MG_TRY(c->alloc(&L.bh[col], (size_t)L.ns, true));
-      MG_TRY(c->alloc(&L.u32[col], (size_t)L.ns, true));
-      MG_TRY(c->alloc(&L.f32[col], (size_t)L.ns, true));
-      if (l == nlev - 1) MG_TRY(c->alloc(&L.r32[col], (size_t)L.ns, true));
     }
-    if (l > 0) {
-      MG_TRY(c->alloc(&L.u64, n));
-      MG_TRY(c->alloc(&L.f64, n));
+    if (c->opt.precision == MG_PREC_FP64) {
+      if (l > 0) {
+        MG_TRY(c->alloc(&L.u64, n));
+        MG_TRY(c->alloc(&L.f64, n));
+      }
+      if (l == nlev - 1) MG_TRY(c->alloc(&L.r64, n));
     }
-    if (l == nlev - 1) MG_TRY(c->alloc(&L.r64, n));
   }
   Level& L0 = c->lv[0];
   const size_t n0 = (size_t)L0.b.n();
@@ -522,39 +862,71 @@ mg_status build(mg_ctx* c, const double* eps_r, const uint8_t* mask, const doubl
     if (mask) mg::launch_split_beta(nullptr, L.mask, sop(c, l, kHelmholtz), mp(L.bh), s);
   }
   MG_TRY(c->alloc(&c->b64, n0));
-  MG_TRY(c->alloc(&c->phi_tmp, n0));
   c->npartial = mg::ir_partials(L0.b);
-  MG_TRY(c->alloc(&c->partial, (size_t)c->npartial));
-  MG_TRY(c->alloc(&c->norm_dev, 1));
-  const long long nc = c->lv.back().b.n();
-  if (nc <= kDenseMax) {
-    MG_TRY(c->alloc(&c->gj_row, (size_t)nc));
-    MG_TRY(c->alloc(&c->gj_col, (size_t)nc));
-  }
-  MG_CUDA(cudaMallocHost((void**)&c->norm_host, sizeof(double)));
-  MG_CUDA(cudaEventCreate(&c->ev0));
-  MG_CUDA(cudaEventCreate(&c->ev1));
+  MG_TRY(c->alloc(&c->gj_row, (size_t)nc));
+  MG_TRY(c->alloc(&c->gj_col, (size_t)nc));
+  MG_CUDA(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
   MG_TRY(check_launch());
   MG_CUDA(cudaStreamSynchronize(s));
-  if (nc > kDenseMax)
-    return fail(MG_ERR_UNSUPPORTED, "grid does not coarsen to <= 4096 cells (need even sizes)");
   return MG_OK;
 }
 
 mg_status normalise_options(const mg_options* in, mg_options* out) {
   mg_default_options(out);
   if (!in) return MG_OK;
-  if (in->nu1 < 0 || in->nu2 < 0 || in->max_cycles < 0 || in->inner_cycles < 0)
+  if (in->nu1 < 0 || in->nu2 < 0 || in->max_cycles < 0 || in->inner_cycles < 0 ||
+      in->concurrency < 0)
     return fail(MG_ERR_INVALID_ARG, "negative option");
   if (in->precision != MG_PREC_FP64 && in->precision != MG_PREC_MIXED)
     return fail(MG_ERR_INVALID_ARG, "unknown precision");
-  for (int q = 0; q < 3; ++q)
-    if (in->reserved[q] != 0) return fail(MG_ERR_INVALID_ARG, "reserved option fields must be 0");
+  if (in->no_graphs != 0 && in->no_graphs != 1)
+    return fail(MG_ERR_INVALID_ARG, "no_graphs must be 0 or 1");
+  if (in->reserved != 0) return fail(MG_ERR_INVALID_ARG, "reserved option field must be 0");
   if (in->nu1) out->nu1 = in->nu1;
   if (in->nu2) out->nu2 = in->nu2;
   if (in->max_cycles) out->max_cycles = in->max_cycles;
   if (in->inner_cycles) out->inner_cycles = in->inner_cycles;
+  if (in->concurrency) out->concurrency = in->concurrency;
   out->precision = in->precision;
+  out->no_graphs = in->no_graphs;
+  return MG_OK;
+}
+
+mg_status check_ctx_tol(const mg_ctx* c, double tol) {
+  if (!c) return fail(MG_ERR_INVALID_ARG, "ctx is NULL");
+  if (!(tol >= 0.0)) return fail(MG_ERR_INVALID_ARG, "tol must be >= 0");
+  return MG_OK;
+}
+
+// Poisson right-hand side b = rho/eps0 + lifts into c->b64; electrode values into phi.
+void prepare_poisson(mg_ctx* c, const double* rho, double* phi) {
+  Level& L0 = c->lv[0];
+  cudaStream_t s = c->stream;
+  if (L0.mask) {
+    Scope sc(c, s, MG_KCLASS_COARSE, 0);
+    mg::launch_set_masked(L0.mask, c->mask_value, L0.b.n(), phi, s);
+  }
+  uint8_t dir[6];
+  for (int f = 0; f < 6; ++f) dir[f] = poisson_dir(c, f);
+  Scope sc(c, s, MG_KCLASS_COARSE, 0);
+  mg::launch_rhs64(rho, 1.0 / kEps0, L0.beta64, L0.mask, L0.b, L0.ih2, dir, c->bc.value, c->b64, s);
+}
+
+void prepare_helmholtz(mg_ctx* c, double* psi) {
+  Level& L0 = c->lv[0];
+  if (L0.mask) {
+    Scope sc(c, c->stream, MG_KCLASS_COARSE, 0);
+    mg::launch_set_masked(L0.mask, nullptr, L0.b.n(), psi, c->stream);
+  }
+}
+
+mg_status check_helmholtz_args(const double* S, double* const psi[3], const double kappa[3]) {
+  if (!S || !psi || !kappa) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  for (int j = 0; j < 3; ++j) {
+    if (!psi[j]) return fail(MG_ERR_INVALID_ARG, "psi[j] is NULL");
+    if (!(kappa[j] > 0.0) || !std::isfinite(kappa[j]))
+      return fail(MG_ERR_INVALID_ARG, "kappa must be finite and > 0");
+  }
   return MG_OK;
 }
 
@@ -570,6 +942,8 @@ void mg_default_options(mg_options* opt) {
   opt->max_cycles = 100;
   opt->precision = MG_PREC_FP64;
   opt->inner_cycles = 1;
+  opt->concurrency = 4;
+  opt->no_graphs = 0;
 }
 
 mg_status mg_create(const mg_grid* grid, const double* eps_r, const uint8_t* mask,
@@ -606,57 +980,53 @@ mg_status mg_create(const mg_grid* grid, const double* eps_r, const uint8_t* mas
 mg_status mg_solve_poisson(mg_ctx* c, const double* rho, double* phi, double tol,
                            mg_stats* stats) {
   g_last_error.clear();
-  if (!c || !rho || !phi) return fail(MG_ERR_INVALID_ARG, "NULL argument");
-  if (!(tol >= 0.0)) return fail(MG_ERR_INVALID_ARG, "tol must be >= 0");
-  Level& L0 = c->lv[0];
-  const long long n = L0.b.n();
-  cudaStream_t s = c->stream;
-  if (L0.mask) {
-    Scope sc(c, MG_KCLASS_COARSE, 0);
-    mg::launch_set_masked(L0.mask, c->mask_value, n, phi, s);
-  }
-  // b = rho / eps0 + Dirichlet lifts, formed once per solve
-  const Rhs rhs{c->b64, 1.0, false};
-  {
-    uint8_t dir[6];
-    for (int f = 0; f < 6; ++f) dir[f] = poisson_dir(c, f);
-    Scope sc(c, MG_KCLASS_COARSE, 0);
-    mg::launch_rhs64(rho, 1.0 / kEps0, L0.beta64, L0.mask, L0.b, L0.ih2, dir, c->bc.value,
-                     c->b64, s);
-  }
+  MG_TRY(check_ctx_tol(c, tol));
+  if (!rho || !phi) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  prepare_poisson(c, rho, phi);
   MG_TRY(check_launch());
-  return solve_one(c, kPoisson, 0.0, rhs, c->b64, phi, tol, stats);
+  std::vector<Prob> P;
+  P.push_back(make_prob(kPoisson, 0.0, c->b64, phi, tol, stats));
+  return solve(c, P);
 }
 
 mg_status mg_solve_helmholtz_batch(mg_ctx* c, const double* S, double* const psi[3],
                                    const double kappa[3], double tol, mg_stats stats[3]) {
   g_last_error.clear();
-  if (!c || !S || !psi || !kappa) return fail(MG_ERR_INVALID_ARG, "NULL argument");
-  if (!(tol >= 0.0)) return fail(MG_ERR_INVALID_ARG, "tol must be >= 0");
+  MG_TRY(check_ctx_tol(c, tol));
+  MG_TRY(check_helmholtz_args(S, psi, kappa));
+  std::vector<Prob> P;
   for (int j = 0; j < 3; ++j) {
-    if (!psi[j]) return fail(MG_ERR_INVALID_ARG, "psi[j] is NULL");
-    if (!(kappa[j] > 0.0) || !std::isfinite(kappa[j]))
-      return fail(MG_ERR_INVALID_ARG, "kappa must be finite and > 0");
+    prepare_helmholtz(c, psi[j]);
+    P.push_back(make_prob(kHelmholtz, kappa[j] * kappa[j], S, psi[j], tol,
+                          stats ? &stats[j] : nullptr));
   }
-  Level& L0 = c->lv[0];
-  mg_status worst = MG_OK;
-  const Rhs rhs{S, 1.0, false};
+  MG_TRY(check_launch());
+  return solve(c, P);
+}
+
+mg_status mg_solve_set(mg_ctx* c, const double* rho, double* phi, const double* S,
+                       double* const psi[3], const double kappa[3], double tol,
+                       mg_stats stats[4]) {
+  g_last_error.clear();
+  MG_TRY(check_ctx_tol(c, tol));
+  if (!rho || !phi) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  MG_TRY(check_helmholtz_args(S, psi, kappa));
+  prepare_poisson(c, rho, phi);
+  std::vector<Prob> P;
+  P.push_back(make_prob(kPoisson, 0.0, c->b64, phi, tol, stats ? &stats[0] : nullptr));
   for (int j = 0; j < 3; ++j) {
-    if (L0.mask) {
-      Scope sc(c, MG_KCLASS_COARSE, 0);
-      mg::launch_set_masked(L0.mask, nullptr, L0.b.n(), psi[j], c->stream);
-    }
-    mg_status st = solve_one(c, kHelmholtz, kappa[j] * kappa[j], rhs, S, psi[j], tol,
-                             stats ? &stats[j] : nullptr);
-    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
-    if (st != MG_OK) worst = st;
+    prepare_helmholtz(c, psi[j]);
+    P.push_back(make_prob(kHelmholtz, kappa[j] * kappa[j], S, psi[j], tol,
+                          stats ? &stats[1 + j] : nullptr));
   }
-  return worst;
+  MG_TRY(check_launch());
+  return solve(c, P);
 }
 
 mg_status mg_profile_enable(mg_ctx* c, int enable) {
   if (!c) return fail(MG_ERR_INVALID_ARG, "ctx is NULL");
   MG_CUDA(cudaStreamSynchronize(c->stream));
+  for (Work* w : c->work) MG_CUDA(cudaStreamSynchronize(w->s));
   harvest(c);
   c->prof = enable != 0;
   std::memset(c->acc, 0, sizeof(c->acc));
@@ -666,6 +1036,7 @@ mg_status mg_profile_enable(mg_ctx* c, int enable) {
 mg_status mg_profile_read(mg_ctx* c, mg_kprof* out, int reset) {
   if (!c || !out) return fail(MG_ERR_INVALID_ARG, "NULL argument");
   MG_CUDA(cudaStreamSynchronize(c->stream));
+  for (Work* w : c->work) MG_CUDA(cudaStreamSynchronize(w->s));
   harvest(c);
   std::memcpy(out, c->acc, sizeof(c->acc));
   if (reset) std::memset(c->acc, 0, sizeof(c->acc));

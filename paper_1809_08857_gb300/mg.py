@@ -28,6 +28,7 @@ MG_PREC_MIXED = 1
 
 EXPORTS = [
     "mg_default_options", "mg_create", "mg_solve_poisson", "mg_solve_helmholtz_batch",
+    "mg_solve_set",
     "mg_set_stream", "mg_level_info", "mg_destroy", "mg_error_string", "mg_last_error",
     "mg_profile_enable", "mg_profile_read", "mg_launch_count", "mg_residual_norm_noalloc",
 ]
@@ -47,7 +48,8 @@ class BC(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("concurrency", ctypes.c_int), ("no_graphs", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -94,6 +96,9 @@ def load():
     lib.mg_solve_helmholtz_batch.argtypes = [P, P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_double),
                                              ctypes.c_double, ctypes.POINTER(Stats)]
     lib.mg_solve_helmholtz_batch.restype = ctypes.c_int
+    lib.mg_solve_set.argtypes = [P, P, P, P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.c_double, ctypes.POINTER(Stats)]
+    lib.mg_solve_set.restype = ctypes.c_int
     lib.mg_set_stream.argtypes = [P, P]
     lib.mg_set_stream.restype = ctypes.c_int
     lib.mg_level_info.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -185,14 +190,15 @@ class Solver:
     def __init__(self, shape, h, eps_r=None, mask=None, mask_value=None,
                  bc_kind=(1, 1, 1, 1, 0, 0), bc_value=(0, 0, 0, 0, 0, 1),
                  precision=MG_PREC_FP64, nu1=2, nu2=2, max_cycles=100, inner_cycles=1,
-                 stream=None):
+                 concurrency=4, graphs=True, stream=None):
         lib = load()
         nz, ny, nx = (int(s) for s in shape)
         self.shape = (nz, ny, nx)
         g = Grid(nx, ny, nz, float(h), (ctypes.c_double * 3)(0.0, 0.0, 0.0))
         bc = BC((ctypes.c_int * 6)(*[int(k) for k in bc_kind]),
                 (ctypes.c_double * 6)(*[float(v) for v in bc_value]))
-        opt = Options(nu1, nu2, max_cycles, precision, inner_cycles, (ctypes.c_int * 3)(0, 0, 0))
+        opt = Options(nu1, nu2, max_cycles, precision, inner_cycles, concurrency,
+                      0 if graphs else 1, 0)
         for t in (eps_r, mask, mask_value):
             if t is not None and tuple(t.shape) != self.shape:
                 raise ValueError("coefficient shape mismatch")
@@ -271,6 +277,24 @@ class Solver:
         st = (Stats * 3)()
         status = self._lib.mg_solve_helmholtz_batch(self._ctx, _ptr(S, torch.float64), ptrs, kap,
                                                     float(tol), st)
+        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        return [s.as_dict() for s in st]
+
+    def solve_set(self, rho, phi, S, psi, kappa, tol=1e-10, raise_on_nonconvergence=True):
+        """Poisson (in place on phi) and the three Helmholtz problems (in place
+        on psi[0..2]) of one time step in one call (mg_solve_set)."""
+        for t in (rho, phi, S, *psi):
+            self._check_field(t)
+        if len(psi) != 3 or len(kappa) != 3:
+            raise ValueError("need three psi arrays and three kappas")
+        self.set_stream()
+        ptrs = (ctypes.c_void_p * 3)(*[p.data_ptr() for p in psi])
+        for p in psi:
+            _ptr(p, torch.float64)
+        kap = (ctypes.c_double * 3)(*[float(k) for k in kappa])
+        st = (Stats * 4)()
+        status = self._lib.mg_solve_set(self._ctx, _ptr(rho, torch.float64), _ptr(phi, torch.float64),
+                                        _ptr(S, torch.float64), ptrs, kap, float(tol), st)
         _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
         return [s.as_dict() for s in st]
 

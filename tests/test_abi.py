@@ -58,7 +58,7 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
     good = mg.Grid(8, 8, 8, 0.1, (ctypes.c_double * 3)())
     assert lib.mg_create(ctypes.byref(good), None, None, None, ctypes.byref(badbc), None, None,
                          ctypes.byref(ctx)) == mg.MG_ERR_INVALID_ARG
-    opt = mg.Options(2, 2, 10, 9, 1, (ctypes.c_int * 3)())
+    opt = mg.Options(2, 2, 10, 9, 1, 4, 0, 0)
     assert lib.mg_create(ctypes.byref(good), None, None, None, ctypes.byref(bc), ctypes.byref(opt),
                          None, ctypes.byref(ctx)) == mg.MG_ERR_INVALID_ARG
     assert lib.mg_create(None, None, None, None, None, None, None, None) == mg.MG_ERR_INVALID_ARG
@@ -77,4 +77,5 @@ def test_default_options(lib):
     from paper_1809_08857_gb300 import mg
 
     o = mg.default_options()
-    assert (o.nu1, o.nu2, o.max_cycles, o.precision, o.inner_cycles) == (2, 2, 100, 0, 1)
+    assert (o.nu1, o.nu2, o.max_cycles, o.precision, o.inner_cycles, o.concurrency,
+            o.no_graphs) == (2, 2, 100, 0, 1, 4, 0)
