@@ -38,6 +38,7 @@ class _Grid(ctypes.Structure):
         ("h", ctypes.c_double),
         ("bc_kind", ctypes.c_int * 6),
         ("bc_value", ctypes.c_double * 6),
+        ("face_data", ctypes.c_void_p),
     ]
 
 
@@ -70,15 +71,26 @@ def _load():
     return _lib
 
 
-def grid(shape, h, bc_kind=(0,) * 6, bc_value=(0.0,) * 6):
-    """Build the C grid descriptor for an array of shape (nz, ny, nx)."""
+def grid(shape, h, bc_kind=(0,) * 6, bc_value=(0.0,) * 6, face_data=None):
+    """Build the C grid descriptor for an array of shape (nz, ny, nx).
+    face_data (optional, numpy float64, packed per face as in ``face_count``)
+    gives the Dirichlet value at every boundary face centre; the caller keeps
+    the array alive."""
     nz, ny, nx = shape
     g = _Grid()
     g.nx, g.ny, g.nz, g.h = int(nx), int(ny), int(nz), float(h)
     for d in range(6):
         g.bc_kind[d] = int(bc_kind[d])
         g.bc_value[d] = float(bc_value[d])
+    g.face_data = None if face_data is None else face_data.ctypes.data
     return g
+
+
+def face_count(shape):
+    """Length of the packed face data: faces -x, +x (ny*nz, index k*ny + j),
+    -y, +y (nx*nz, index k*nx + i), -z, +z (nx*ny, index j*nx + i)."""
+    nz, ny, nx = shape
+    return 2 * (ny * nz + nx * nz + nx * ny)
 
 
 def _p(a):
@@ -103,7 +115,7 @@ class Problem:
     """
 
     def __init__(self, shape, h, alpha=0.0, beta=None, mask=None,
-                 bc_kind=(0,) * 6, bc_value=(0.0,) * 6):
+                 bc_kind=(0,) * 6, bc_value=(0.0,) * 6, face_data=None):
         self.shape = tuple(int(s) for s in shape)
         self.h = float(h)
         self.alpha = float(alpha)
@@ -111,7 +123,10 @@ class Problem:
         self.mask = _u8(mask)
         self.bc_kind = tuple(bc_kind)
         self.bc_value = tuple(bc_value)
-        self.g = grid(self.shape, h, bc_kind, bc_value)
+        self.face_data = None if face_data is None else _f64(face_data)
+        if self.face_data is not None and self.face_data.size != face_count(self.shape):
+            raise ValueError("face_data has the wrong length")
+        self.g = grid(self.shape, h, bc_kind, bc_value, self.face_data)
 
     def residual(self, f, u, homog=False):
         """r = f - L(u) on free cells (0 on electrode cells); returns (r, ||r||_2)."""

@@ -38,6 +38,10 @@ typedef struct {
   double h;
   int bc_kind[6];
   double bc_value[6];
+  /* optional per-face-cell Dirichlet values, packed: faces -x, +x (ny*nz,
+   * index k*ny + j), -y, +y (nx*nz, index k*nx + i), -z, +z (nx*ny, index
+   * j*nx + i); NULL means bc_value[face] on the whole face */
+  const double* face_data;
 } or_grid;
 
 #define OR_MAX_LEVELS 24
@@ -45,6 +49,24 @@ typedef struct {
 static long ncell(const or_grid* g) { return (long)g->nx * g->ny * g->nz; }
 static long idx(const or_grid* g, int i, int j, int k) {
   return ((long)k * g->ny + j) * g->nx + i;
+}
+
+/* Dirichlet value of domain face d next to cell (i,j,k) */
+static double face_value(const or_grid* g, int d, int i, int j, int k) {
+  if (!g->face_data) return g->bc_value[d];
+  const long ax = (long)g->ny * g->nz, ay = (long)g->nx * g->nz;
+  long base, q;
+  if (d < 2) {
+    base = d * ax;
+    q = (long)k * g->ny + j;
+  } else if (d < 4) {
+    base = 2 * ax + (d - 2) * ay;
+    q = (long)k * g->nx + i;
+  } else {
+    base = 2 * ax + 2 * ay + (long)(d - 4) * g->nx * g->ny;
+    q = (long)j * g->nx + i;
+  }
+  return g->face_data[base + q];
 }
 
 static const int DI[6] = {-1, 1, 0, 0, 0, 0};
@@ -78,7 +100,7 @@ static void row(const or_grid* g, double alpha, const double* beta,
     } else if (g->bc_kind[d] == 0) {
       double w = 2.0 * bc; /* ghost = 2 g - u_c */
       diag += w * ih2;
-      if (!homog) off += w * ih2 * g->bc_value[d];
+      if (!homog) off += w * ih2 * face_value(g, d, i, j, k);
     }
   }
   *diag_out = diag;
@@ -315,6 +337,7 @@ static int mg_build(or_mg* M, const or_grid* g, double alpha, const double* beta
     cg.nx /= 2; cg.ny /= 2; cg.nz /= 2;
     cg.h *= 2.0;
     for (int d = 0; d < 6; ++d) cg.bc_value[d] = 0.0;
+    cg.face_data = NULL;
     long nc = ncell(&cg);
     M->g[l + 1] = cg;
     M->beta[l + 1] = (double*)malloc(sizeof(double) * nc);
