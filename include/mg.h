@@ -169,6 +169,56 @@ mg_status mg_solve_set(mg_ctx* ctx, const double* rho, double* phi, const double
                        double* const psi[3], const double kappa[3], double tol,
                        mg_stats stats[4]);
 
+/* ---- batches of problems and refined sub-boxes -----------------------------
+ *
+ * Packed Dirichlet face data of an nx*ny*nz box: faces -x, +x (ny*nz values
+ * each, index k*ny + j), then -y, +y (nx*nz, index k*nx + i), then -z, +z
+ * (nx*ny, index j*nx + i): mg_face_count() = 2 (ny nz + nx nz + nx ny) FP64.
+ * A value is the potential (or Psi) at the centre of that boundary face.
+ */
+long long mg_face_count(int nx, int ny, int nz);
+
+typedef enum { MG_PROBLEM_POISSON = 0, MG_PROBLEM_HELMHOLTZ = 1 } mg_problem_kind;
+
+typedef struct {
+  mg_ctx* ctx;          /* grid, coefficients and work arrays of this problem */
+  int kind;             /* mg_problem_kind */
+  double kappa;         /* Helmholtz only: inverse absorption length (> 0) */
+  const double* rhs;    /* device: rho (Poisson, C/m^3) or S (Helmholtz) */
+  const double* faces;  /* device packed Dirichlet face data (values on the
+                           Dirichlet faces of the Poisson bc; every face for
+                           Helmholtz), or NULL: the ctx's bc values (Poisson),
+                           zero (Helmholtz) */
+  double* u;            /* device in/out iterate; distinct for every problem */
+} mg_problem;
+
+/*
+ * mg_solve_batch -- solve a batch of problems, possibly on different grids
+ * (for instance the uneven refined sub-boxes of an AMR level, which stand in
+ * for the paper's patch-based hierarchy of Sec. 4).  Every context must use
+ * the same precision mode.  In mixed precision up to 16 problems run
+ * concurrently (at most mg_options.concurrency per context, each on a library
+ * stream with its own work arrays); FP64 mode solves them one after the
+ * other.  stats (nullable) has nprob entries.  Returns the worst status.
+ */
+mg_status mg_solve_batch(const mg_problem* probs, int nprob, double tol, mg_stats* stats);
+
+/*
+ * mg_subbox_bc -- Dirichlet data for a refined sub-box (refinement ratio 2)
+ * from the parent solution: trilinear interpolation of the parent's
+ * cell-centred values at the centres of the sub-box's boundary faces.
+ *   parent     context of the parent grid.
+ *   parent_u   device, parent solution (parent grid size).
+ *   origin     parent cell index of the sub-box's lower corner (x, y, z);
+ *              the sub-box covers parent cells [origin, origin + dims/2).
+ *   dims       sub-box size in fine cells (x, y, z), each even; the box must
+ *              stay at least one parent cell away from every parent face.
+ *   faces      device, mg_face_count(dims) FP64 values (output, packed).
+ * Enqueued on the parent's stream.
+ */
+mg_status mg_subbox_bc(const mg_ctx* parent, const double* parent_u, const int origin[3],
+                       const int dims[3], double* faces);
+
 /* ---- instrumentation ------------------------------------------------------
  * Kernel classes of the fine (finest-level) launches: red-black smoothing,
  * fused residual + restriction, prolongation + correction, the FP64

@@ -125,6 +125,7 @@ struct Work {
   cudaStream_t s = nullptr;
   std::vector<LevelWork> lw;
   double* phi_tmp = nullptr;  // ping-pong partner of the caller's iterate
+  double* b64 = nullptr;      // right-hand side with lifts (allocated when needed)
   double* partial = nullptr;
   double* norm_dev = nullptr;   // [2]
   double* norm_host = nullptr;  // [2], pinned
@@ -141,7 +142,6 @@ struct mg_ctx {
   cudaStream_t stream = nullptr;
   std::vector<Level> lv;
   double* mask_value = nullptr;
-  double* b64 = nullptr;  // Poisson right-hand side with lifts
   int npartial = 0;
   double *gj_row = nullptr, *gj_col = nullptr;
   std::vector<Coarse> coarse;
@@ -482,13 +482,16 @@ mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha
 
 // One problem of a (possibly concurrent) solve.
 struct Prob {
+  mg_ctx* c;
   Kind kind;
   double alpha;
-  const double* b;  // right-hand side with lifts
-  double* u;        // caller's iterate (electrode values already set)
+  const double* rhs;    // rho (Poisson, C/m^3) or S (Helmholtz)
+  const double* faces;  // packed Dirichlet face data, or null
+  double* u;            // caller's iterate
   double tol;
   mg_stats* st;
   Work* w = nullptr;
+  const double* b = nullptr;  // right-hand side with lifts
   double* cur = nullptr;
   double* other = nullptr;
   int cyc = 0;
@@ -499,27 +502,62 @@ struct Prob {
   const StepGraph* g = nullptr;
 };
 
-Prob make_prob(Kind kind, double alpha, const double* b, double* u, double tol, mg_stats* st) {
+Prob make_prob(mg_ctx* c, Kind kind, double alpha, const double* rhs, const double* faces,
+               double* u, double tol, mg_stats* st) {
   Prob p;
+  p.c = c;
   p.kind = kind;
   p.alpha = alpha;
-  p.b = b;
+  p.rhs = rhs;
+  p.faces = faces;
   p.u = u;
   p.tol = tol;
   p.st = st;
   return p;
 }
 
+// Electrode values into u and the right-hand side with lifts, on stream s:
+// Poisson b = rho/eps0 + lifts; Helmholtz b = S (+ lifts of face data).
+mg_status prepare(Prob& p, cudaStream_t s) {
+  mg_ctx* c = p.c;
+  Level& L0 = c->lv[0];
+  if (L0.mask) {
+    Scope sc(c, s, MG_KCLASS_COARSE, 0);
+    mg::launch_set_masked(L0.mask, p.kind == kPoisson ? c->mask_value : nullptr, L0.b.n(), p.u, s);
+  }
+  if (p.kind == kHelmholtz && !p.faces) {
+    p.b = p.rhs;
+    return check_launch();
+  }
+  if (!p.w->b64) MG_TRY(c->alloc(&p.w->b64, (size_t)L0.b.n()));
+  uint8_t dir[6];
+  double zero[6] = {0, 0, 0, 0, 0, 0};
+  for (int f = 0; f < 6; ++f) dir[f] = p.kind == kPoisson ? poisson_dir(c, f) : 1;
+  {
+    Scope sc(c, s, MG_KCLASS_COARSE, 0);
+    if (p.kind == kPoisson)
+      mg::launch_rhs64(p.rhs, 1.0 / kEps0, L0.beta64, L0.mask, L0.b, L0.ih2, dir, c->bc.value,
+                       p.faces, p.w->b64, s);
+    else
+      mg::launch_rhs64(p.rhs, 1.0, nullptr, L0.mask, L0.b, L0.ih2, dir, zero, p.faces, p.w->b64,
+                       s);
+  }
+  p.b = p.w->b64;
+  return check_launch();
+}
+
 // The refinement step of p: inner V-cycles on A e = r, then the fused FP64
 // step u_out = u_in + e, r = b - A u_out, ||r||^2 -> host slot 1.
-mg_status enqueue_step_direct(mg_ctx* c, Prob& p) {
+mg_status enqueue_step_direct(Prob& p) {
+  mg_ctx* c = p.c;
   for (int q = 0; q < c->opt.inner_cycles; ++q)
     MG_TRY(vcycle32(c, p.w, p.kind, p.alpha, 0, q == 0));
   return enqueue_ir(c, p.w, p.w->s, p.kind, p.alpha, p.b, p.cur, p.other, true, true, false, 1);
 }
 
 // Cached graph of the step for p's current (u_in, u_out) parity.
-mg_status step_graph(mg_ctx* c, Prob& p, const StepGraph** out) {
+mg_status step_graph(Prob& p, const StepGraph** out) {
+  mg_ctx* c = p.c;
   Work* w = p.w;
   const int ic = c->opt.inner_cycles;
   for (StepGraph& g : w->graphs)
@@ -560,7 +598,7 @@ mg_status step_graph(mg_ctx* c, Prob& p, const StepGraph** out) {
   const long long l0 = mg::launch_count();
   MG_CUDA(cudaStreamBeginCapture(w->s, cudaStreamCaptureModeThreadLocal));
   c->capture = &g.recs;
-  mg_status st = enqueue_step_direct(c, p);
+  mg_status st = enqueue_step_direct(p);
   c->capture = nullptr;
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(w->s, &graph);
@@ -582,13 +620,13 @@ mg_status step_graph(mg_ctx* c, Prob& p, const StepGraph** out) {
   return MG_OK;
 }
 
-mg_status enqueue_step(mg_ctx* c, Prob& p) {
+mg_status enqueue_step(Prob& p) {
   p.g = nullptr;
-  if (c->opt.no_graphs) {
-    MG_TRY(enqueue_step_direct(c, p));
+  if (p.c->opt.no_graphs) {
+    MG_TRY(enqueue_step_direct(p));
   } else {
     const StepGraph* g;
-    MG_TRY(step_graph(c, p, &g));
+    MG_TRY(step_graph(p, &g));
     MG_CUDA(cudaGraphLaunch(g->exec, p.w->s));
     mg::add_launches(g->launches);
     p.g = g;
@@ -597,10 +635,10 @@ mg_status enqueue_step(mg_ctx* c, Prob& p) {
   return MG_OK;
 }
 
-mg_status finish(mg_ctx* c, Prob& p) {
+mg_status finish(Prob& p) {
   if (p.cur != p.u)
-    MG_CUDA(cudaMemcpyAsync(p.u, p.cur, sizeof(double) * c->lv[0].b.n(), cudaMemcpyDeviceToDevice,
-                            p.w->s));
+    MG_CUDA(cudaMemcpyAsync(p.u, p.cur, sizeof(double) * p.c->lv[0].b.n(),
+                            cudaMemcpyDeviceToDevice, p.w->s));
   if (p.st) MG_CUDA(cudaEventRecord(p.w->t1, p.w->s));
   p.done = true;
   if (!std::isfinite(p.rel)) {
@@ -616,14 +654,14 @@ mg_status finish(mg_ctx* c, Prob& p) {
 }
 
 // Host side of one finished step of p.
-mg_status advance(mg_ctx* c, Prob& p) {
+mg_status advance(Prob& p) {
   const double* h = p.w->norm_host;
-  if (p.g) harvest_graph(c, *p.g);
+  if (p.g) harvest_graph(p.c, *p.g);
   if (p.phase == 0) {
     p.bnorm = std::sqrt(h[0]);
     if (!std::isfinite(p.bnorm)) {
       p.rel = p.bnorm;
-      return finish(c, p);
+      return finish(p);
     }
     if (p.bnorm == 0.0) p.bnorm = 1.0;
     p.phase = 1;
@@ -633,31 +671,40 @@ mg_status advance(mg_ctx* c, Prob& p) {
   }
   p.rel = std::sqrt(h[1]) / p.bnorm;
   if (p.st && p.cyc < 64) p.st->hist[p.cyc] = p.rel;
-  if (!std::isfinite(p.rel) || p.rel <= p.tol || p.cyc >= c->opt.max_cycles) return finish(c, p);
-  return enqueue_step(c, p);
+  if (!std::isfinite(p.rel) || p.rel <= p.tol || p.cyc >= p.c->opt.max_cycles) return finish(p);
+  return enqueue_step(p);
 }
 
-// Mixed-precision solve of several problems concurrently (one work slot and
-// stream each).  Returns the worst status; outputs are complete on return.
-mg_status solve_mixed(mg_ctx* c, std::vector<Prob>& P) {
-  for (size_t q = 0; q < P.size(); ++q) {
-    MG_TRY(get_work(c, (int)q, &P[q].w));
+// Mixed-precision solve of problems concurrently: every problem gets a work
+// slot (its own stream and arrays) of its context.  Returns the worst
+// status; outputs are complete on return.
+mg_status solve_mixed(std::vector<Prob>& P) {
+  std::vector<mg_ctx*> ctxs;
+  for (Prob& p : P) {
+    int slot = 0;
+    for (Prob& o : P) {
+      if (&o == &p) break;
+      if (o.c == p.c) ++slot;
+    }
+    MG_TRY(get_work(p.c, slot, &p.w));
     const double* Minv;
-    MG_TRY(coarse_inverse(c, P[q].kind, P[q].alpha, &Minv));
+    MG_TRY(coarse_inverse(p.c, p.kind, p.alpha, &Minv));
+    if (std::find(ctxs.begin(), ctxs.end(), p.c) == ctxs.end()) ctxs.push_back(p.c);
   }
-  MG_CUDA(cudaEventRecord(c->fork, c->stream));
+  for (mg_ctx* c : ctxs) MG_CUDA(cudaEventRecord(c->fork, c->stream));
   for (Prob& p : P) {
     Work* w = p.w;
-    MG_CUDA(cudaStreamWaitEvent(w->s, c->fork, 0));
+    MG_CUDA(cudaStreamWaitEvent(w->s, p.c->fork, 0));
     if (p.st) {
       std::memset(p.st, 0, sizeof(*p.st));
       MG_CUDA(cudaEventRecord(w->t0, w->s));
     }
+    MG_TRY(prepare(p, w->s));
     p.cur = p.u;
     p.other = w->phi_tmp;
     // ||b|| (slot 0) and the residual of the initial guess (slot 1, r -> FP32)
-    MG_TRY(enqueue_ir(c, w, w->s, p.kind, p.alpha, p.b, p.u, nullptr, false, false, true, 0));
-    MG_TRY(enqueue_ir(c, w, w->s, p.kind, p.alpha, p.b, p.u, nullptr, false, true, false, 1));
+    MG_TRY(enqueue_ir(p.c, w, w->s, p.kind, p.alpha, p.b, p.u, nullptr, false, false, true, 0));
+    MG_TRY(enqueue_ir(p.c, w, w->s, p.kind, p.alpha, p.b, p.u, nullptr, false, true, false, 1));
     MG_CUDA(cudaEventRecord(w->ev, w->s));
   }
   size_t left = P.size();
@@ -669,7 +716,7 @@ mg_status solve_mixed(mg_ctx* c, std::vector<Prob>& P) {
       if (q == cudaErrorNotReady) continue;
       if (q != cudaSuccess) return fail(MG_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(q));
       progress = true;
-      MG_TRY(advance(c, p));
+      MG_TRY(advance(p));
       if (p.done) --left;
     }
     if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -687,20 +734,23 @@ mg_status solve_mixed(mg_ctx* c, std::vector<Prob>& P) {
     }
     if (p.status == MG_ERR_NONFINITE || (p.status != MG_OK && worst == MG_OK)) worst = p.status;
   }
-  harvest(c);
+  for (mg_ctx* c : ctxs) harvest(c);
   if (worst == MG_ERR_NONFINITE) g_last_error = "non-finite value in input or residual";
   return worst;
 }
 
-// FP64-mode solve of one problem on the context's stream.
-mg_status solve_fp64(mg_ctx* c, Prob& p) {
+// FP64-mode solve of one problem on its context's stream.
+mg_status solve_fp64(Prob& p) {
+  mg_ctx* c = p.c;
   Work* w;
   MG_TRY(get_work(c, 0, &w));
+  p.w = w;
   cudaStream_t s = c->stream;
   if (p.st) {
     std::memset(p.st, 0, sizeof(*p.st));
     MG_CUDA(cudaEventRecord(w->t0, s));
   }
+  MG_TRY(prepare(p, s));
   auto norms = [&](bool with_b) -> mg_status {
     if (with_b) MG_TRY(enqueue_ir(c, w, s, p.kind, p.alpha, p.b, p.u, nullptr, false, false, true, 0));
     MG_TRY(enqueue_ir(c, w, s, p.kind, p.alpha, p.b, p.u, nullptr, false, false, false, 1));
@@ -745,21 +795,36 @@ bool hard_error(mg_status st) {
          st == MG_ERR_INVALID_ARG;
 }
 
-mg_status solve(mg_ctx* c, std::vector<Prob>& P) {
+constexpr int kMaxConcurrent = 16;  // problems in flight across contexts
+
+mg_status solve(std::vector<Prob>& P) {
   mg_status worst = MG_OK;
-  if (c->opt.precision == MG_PREC_MIXED) {
-    // at most kMaxWork (and opt.concurrency) problems at a time
-    const size_t width = (size_t)std::max(1, std::min(c->opt.concurrency, kMaxWork));
-    for (size_t q0 = 0; q0 < P.size(); q0 += width) {
-      std::vector<Prob> part(P.begin() + q0, P.begin() + std::min(P.size(), q0 + width));
-      const mg_status st = solve_mixed(c, part);
+  if (P.empty()) return MG_OK;
+  if (P[0].c->opt.precision == MG_PREC_MIXED) {
+    // waves of at most kMaxConcurrent problems, at most concurrency (<= 4) per context
+    size_t q0 = 0;
+    while (q0 < P.size()) {
+      std::vector<Prob> part;
+      std::vector<std::pair<mg_ctx*, int>> per;
+      size_t q = q0;
+      for (; q < P.size() && (int)part.size() < kMaxConcurrent; ++q) {
+        mg_ctx* c = P[q].c;
+        auto it = std::find_if(per.begin(), per.end(), [&](auto& e) { return e.first == c; });
+        const int cap = std::max(1, std::min(c->opt.concurrency, kMaxWork));
+        if (it != per.end() && it->second >= cap) break;
+        if (it == per.end()) per.push_back({c, 1});
+        else ++it->second;
+        part.push_back(P[q]);
+      }
+      const mg_status st = solve_mixed(part);
       if (hard_error(st)) return st;
       if (st == MG_ERR_NONFINITE || (st != MG_OK && worst == MG_OK)) worst = st;
+      q0 = q;
     }
     return worst;
   }
   for (Prob& p : P) {
-    const mg_status st = solve_fp64(c, p);
+    const mg_status st = solve_fp64(p);
     if (hard_error(st)) return st;
     if (st == MG_ERR_NONFINITE || (st != MG_OK && worst == MG_OK)) worst = st;
   }
@@ -861,7 +926,6 @@ mg_status build(mg_ctx* c, const double* eps_r, const uint8_t* mask, const doubl
     if (eps_r || mask) mg::launch_split_beta(L.beta64, L.mask, sop(c, l, kPoisson), mp(L.bp), s);
     if (mask) mg::launch_split_beta(nullptr, L.mask, sop(c, l, kHelmholtz), mp(L.bh), s);
   }
-  MG_TRY(c->alloc(&c->b64, n0));
   c->npartial = mg::ir_partials(L0.b);
   MG_TRY(c->alloc(&c->gj_row, (size_t)nc));
   MG_TRY(c->alloc(&c->gj_col, (size_t)nc));
@@ -896,28 +960,6 @@ mg_status check_ctx_tol(const mg_ctx* c, double tol) {
   if (!c) return fail(MG_ERR_INVALID_ARG, "ctx is NULL");
   if (!(tol >= 0.0)) return fail(MG_ERR_INVALID_ARG, "tol must be >= 0");
   return MG_OK;
-}
-
-// Poisson right-hand side b = rho/eps0 + lifts into c->b64; electrode values into phi.
-void prepare_poisson(mg_ctx* c, const double* rho, double* phi) {
-  Level& L0 = c->lv[0];
-  cudaStream_t s = c->stream;
-  if (L0.mask) {
-    Scope sc(c, s, MG_KCLASS_COARSE, 0);
-    mg::launch_set_masked(L0.mask, c->mask_value, L0.b.n(), phi, s);
-  }
-  uint8_t dir[6];
-  for (int f = 0; f < 6; ++f) dir[f] = poisson_dir(c, f);
-  Scope sc(c, s, MG_KCLASS_COARSE, 0);
-  mg::launch_rhs64(rho, 1.0 / kEps0, L0.beta64, L0.mask, L0.b, L0.ih2, dir, c->bc.value, c->b64, s);
-}
-
-void prepare_helmholtz(mg_ctx* c, double* psi) {
-  Level& L0 = c->lv[0];
-  if (L0.mask) {
-    Scope sc(c, c->stream, MG_KCLASS_COARSE, 0);
-    mg::launch_set_masked(L0.mask, nullptr, L0.b.n(), psi, c->stream);
-  }
 }
 
 mg_status check_helmholtz_args(const double* S, double* const psi[3], const double kappa[3]) {
@@ -982,11 +1024,9 @@ mg_status mg_solve_poisson(mg_ctx* c, const double* rho, double* phi, double tol
   g_last_error.clear();
   MG_TRY(check_ctx_tol(c, tol));
   if (!rho || !phi) return fail(MG_ERR_INVALID_ARG, "NULL argument");
-  prepare_poisson(c, rho, phi);
-  MG_TRY(check_launch());
   std::vector<Prob> P;
-  P.push_back(make_prob(kPoisson, 0.0, c->b64, phi, tol, stats));
-  return solve(c, P);
+  P.push_back(make_prob(c, kPoisson, 0.0, rho, nullptr, phi, tol, stats));
+  return solve(P);
 }
 
 mg_status mg_solve_helmholtz_batch(mg_ctx* c, const double* S, double* const psi[3],
@@ -995,13 +1035,10 @@ mg_status mg_solve_helmholtz_batch(mg_ctx* c, const double* S, double* const psi
   MG_TRY(check_ctx_tol(c, tol));
   MG_TRY(check_helmholtz_args(S, psi, kappa));
   std::vector<Prob> P;
-  for (int j = 0; j < 3; ++j) {
-    prepare_helmholtz(c, psi[j]);
-    P.push_back(make_prob(kHelmholtz, kappa[j] * kappa[j], S, psi[j], tol,
+  for (int j = 0; j < 3; ++j)
+    P.push_back(make_prob(c, kHelmholtz, kappa[j] * kappa[j], S, nullptr, psi[j], tol,
                           stats ? &stats[j] : nullptr));
-  }
-  MG_TRY(check_launch());
-  return solve(c, P);
+  return solve(P);
 }
 
 mg_status mg_solve_set(mg_ctx* c, const double* rho, double* phi, const double* S,
@@ -1011,16 +1048,63 @@ mg_status mg_solve_set(mg_ctx* c, const double* rho, double* phi, const double* 
   MG_TRY(check_ctx_tol(c, tol));
   if (!rho || !phi) return fail(MG_ERR_INVALID_ARG, "NULL argument");
   MG_TRY(check_helmholtz_args(S, psi, kappa));
-  prepare_poisson(c, rho, phi);
   std::vector<Prob> P;
-  P.push_back(make_prob(kPoisson, 0.0, c->b64, phi, tol, stats ? &stats[0] : nullptr));
-  for (int j = 0; j < 3; ++j) {
-    prepare_helmholtz(c, psi[j]);
-    P.push_back(make_prob(kHelmholtz, kappa[j] * kappa[j], S, psi[j], tol,
+  P.push_back(make_prob(c, kPoisson, 0.0, rho, nullptr, phi, tol, stats ? &stats[0] : nullptr));
+  for (int j = 0; j < 3; ++j)
+    P.push_back(make_prob(c, kHelmholtz, kappa[j] * kappa[j], S, nullptr, psi[j], tol,
                           stats ? &stats[1 + j] : nullptr));
+  return solve(P);
+}
+
+mg_status mg_solve_batch(const mg_problem* probs, int nprob, double tol, mg_stats* stats) {
+  g_last_error.clear();
+  if (nprob < 0 || (nprob > 0 && !probs)) return fail(MG_ERR_INVALID_ARG, "bad problem list");
+  if (!(tol >= 0.0)) return fail(MG_ERR_INVALID_ARG, "tol must be >= 0");
+  std::vector<Prob> P;
+  for (int q = 0; q < nprob; ++q) {
+    const mg_problem& pr = probs[q];
+    if (!pr.ctx || !pr.rhs || !pr.u) return fail(MG_ERR_INVALID_ARG, "NULL ctx, rhs or u");
+    if (pr.ctx->opt.precision != probs[0].ctx->opt.precision)
+      return fail(MG_ERR_INVALID_ARG, "all contexts of a batch need the same precision mode");
+    for (int o = 0; o < q; ++o)
+      if (probs[o].u == pr.u) return fail(MG_ERR_INVALID_ARG, "two problems share one u array");
+    if (pr.kind == MG_PROBLEM_POISSON) {
+      P.push_back(make_prob(pr.ctx, kPoisson, 0.0, pr.rhs, pr.faces, pr.u, tol,
+                            stats ? &stats[q] : nullptr));
+    } else if (pr.kind == MG_PROBLEM_HELMHOLTZ) {
+      if (!(pr.kappa > 0.0) || !std::isfinite(pr.kappa))
+        return fail(MG_ERR_INVALID_ARG, "kappa must be finite and > 0");
+      P.push_back(make_prob(pr.ctx, kHelmholtz, pr.kappa * pr.kappa, pr.rhs, pr.faces, pr.u, tol,
+                            stats ? &stats[q] : nullptr));
+    } else {
+      return fail(MG_ERR_INVALID_ARG, "unknown problem kind");
+    }
   }
+  return solve(P);
+}
+
+mg_status mg_subbox_bc(const mg_ctx* parent, const double* parent_u, const int origin[3],
+                       const int dims[3], double* faces) {
+  g_last_error.clear();
+  if (!parent || !parent_u || !origin || !dims || !faces)
+    return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  const mg::Box pb = parent->lv[0].b;
+  const int pn[3] = {pb.nx, pb.ny, pb.nz};
+  for (int a = 0; a < 3; ++a) {
+    if (dims[a] < 2 || dims[a] % 2) return fail(MG_ERR_INVALID_ARG, "sub-box sizes must be even, >= 2");
+    // the interpolation stencil needs one parent cell outside each face
+    if (origin[a] < 1 || origin[a] + dims[a] / 2 > pn[a] - 1)
+      return fail(MG_ERR_INVALID_ARG, "sub-box must lie at least one parent cell inside the parent");
+  }
+  mg::launch_subbox_bc(parent_u, pb, origin[0], origin[1], origin[2],
+                       mg::Box{dims[0], dims[1], dims[2]}, faces, parent->stream);
   MG_TRY(check_launch());
-  return solve(c, P);
+  return MG_OK;
+}
+
+long long mg_face_count(int nx, int ny, int nz) {
+  if (nx < 1 || ny < 1 || nz < 1) return 0;
+  return mg::face_count(mg::Box{nx, ny, nz});
 }
 
 mg_status mg_profile_enable(mg_ctx* c, int enable) {

@@ -99,9 +99,16 @@ void launch_gj_invert(double* M, int n, double* rowp, double* colp, cudaStream_t
 
 // ---- solve ---------------------------------------------------------------
 // b = f * scale + Dirichlet-face lifts (2 beta_c g / h^2); 0 on electrode cells.
+// g = bval[face], or the packed per-face-cell values when faces != nullptr.
 void launch_rhs64(const double* f, double scale, const double* beta, const uint8_t* mask,
-                  Box b, double ih2, const uint8_t dir[6], const double bval[6], double* out,
-                  cudaStream_t s);
+                  Box b, double ih2, const uint8_t dir[6], const double bval[6],
+                  const double* faces, double* out, cudaStream_t s);
+// Entries of the packed face data of a box (2 (ny nz + nx nz + nx ny)).
+long long face_count(const Box& b);
+// Dirichlet face data of a ratio-2 sub-box at parent cell offset (ox,oy,oz)
+// by trilinear interpolation of the parent solution.
+void launch_subbox_bc(const double* parent_u, Box pb, int ox, int oy, int oz, Box sb,
+                      double* faces, cudaStream_t s);
 // u[c] = value[c] (or 0 if value == nullptr) on electrode cells.
 void launch_set_masked(const uint8_t* mask, const double* value, long long n, double* u,
                        cudaStream_t s);

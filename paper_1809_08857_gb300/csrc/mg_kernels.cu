@@ -174,8 +174,20 @@ __global__ void k_gj_elim(double* M, int n, int p, const double* rowp, const dou
 
 // ---- solve kernels --------------------------------------------------------
 
+// Packed Dirichlet face data: faces -x, +x (ny*nz each, index k*ny + j),
+// -y, +y (nx*nz, index k*nx + i), -z, +z (nx*ny, index j*nx + i).
+__host__ __device__ inline long long face_offset(const Box& b, int f) {
+  const long long ax = (long long)b.ny * b.nz, ay = (long long)b.nx * b.nz,
+                  az = (long long)b.nx * b.ny;
+  const long long off[6] = {0, ax, 2 * ax, 2 * ax + ay, 2 * ax + 2 * ay, 2 * ax + 2 * ay + az};
+  return off[f];
+}
+
+// b = f * scale + Dirichlet lifts 2 beta_c g / h^2, with g = bval[face] or,
+// when faces != nullptr, the packed per-face-cell values.
 __global__ void k_rhs64(const double* f, double scale, const double* beta, const uint8_t* mask,
-                        Box b, double ih2, Dir6 dir, Val6 bval, double* out) {
+                        Box b, double ih2, Dir6 dir, Val6 bval, const double* faces,
+                        double* out) {
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= b.n()) return;
   if (mask && mask[c]) { out[c] = 0.0; return; }
@@ -184,13 +196,65 @@ __global__ void k_rhs64(const double* f, double scale, const double* beta, const
   const int j = (int)(jk % b.ny), k = (int)(jk / b.ny);
   double v = f[c] * scale;
   const double bc = beta ? beta[c] : 1.0;
-  if (i == 0 && dir.d[0]) v += 2.0 * bc * ih2 * bval.v[0];
-  if (i == b.nx - 1 && dir.d[1]) v += 2.0 * bc * ih2 * bval.v[1];
-  if (j == 0 && dir.d[2]) v += 2.0 * bc * ih2 * bval.v[2];
-  if (j == b.ny - 1 && dir.d[3]) v += 2.0 * bc * ih2 * bval.v[3];
-  if (k == 0 && dir.d[4]) v += 2.0 * bc * ih2 * bval.v[4];
-  if (k == b.nz - 1 && dir.d[5]) v += 2.0 * bc * ih2 * bval.v[5];
+  auto g = [&](int face) -> double {
+    if (!faces) return bval.v[face];
+    long long q;
+    if (face < 2) q = (long long)k * b.ny + j;
+    else if (face < 4) q = (long long)k * b.nx + i;
+    else q = (long long)j * b.nx + i;
+    return faces[face_offset(b, face) + q];
+  };
+  if (i == 0 && dir.d[0]) v += 2.0 * bc * ih2 * g(0);
+  if (i == b.nx - 1 && dir.d[1]) v += 2.0 * bc * ih2 * g(1);
+  if (j == 0 && dir.d[2]) v += 2.0 * bc * ih2 * g(2);
+  if (j == b.ny - 1 && dir.d[3]) v += 2.0 * bc * ih2 * g(3);
+  if (k == 0 && dir.d[4]) v += 2.0 * bc * ih2 * g(4);
+  if (k == b.nz - 1 && dir.d[5]) v += 2.0 * bc * ih2 * g(5);
   out[c] = v;
+}
+
+// Dirichlet data of a refined sub-box (ratio 2) from the parent solution:
+// trilinear interpolation of the parent's cell-centred values at the fine
+// face centres of the sub-box boundary.  The sub-box covers parent cells
+// [o, o + n/2) per axis; one thread per face point.
+__global__ void k_subbox_bc(const double* __restrict__ pu, Box pb, int ox, int oy, int oz,
+                            Box sb, double* faces) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = face_offset(sb, 5) + (long long)sb.nx * sb.ny;
+  if (t >= total) return;
+  int f = 0;
+  while (f < 5 && t >= face_offset(sb, f + 1)) ++f;
+  const long long q = t - face_offset(sb, f);
+  // parent-grid coordinates (in parent cells, cell centres at integers + 1/2)
+  // of the face point; fine cell (i,j,k) centre = o + (i + 1/2)/2
+  double px, py, pz;
+  if (f < 2) {
+    const int j = (int)(q % sb.ny), k = (int)(q / sb.ny);
+    px = ox + (f == 0 ? 0.0 : 0.5 * sb.nx);
+    py = oy + 0.5 * (j + 0.5);
+    pz = oz + 0.5 * (k + 0.5);
+  } else if (f < 4) {
+    const int i = (int)(q % sb.nx), k = (int)(q / sb.nx);
+    px = ox + 0.5 * (i + 0.5);
+    py = oy + (f == 2 ? 0.0 : 0.5 * sb.ny);
+    pz = oz + 0.5 * (k + 0.5);
+  } else {
+    const int i = (int)(q % sb.nx), j = (int)(q / sb.nx);
+    px = ox + 0.5 * (i + 0.5);
+    py = oy + 0.5 * (j + 0.5);
+    pz = oz + (f == 4 ? 0.0 : 0.5 * sb.nz);
+  }
+  // lower parent cell index and weight along each axis
+  const double sx = px - 0.5, sy = py - 0.5, sz = pz - 0.5;
+  const int I = (int)floor(sx), J = (int)floor(sy), K = (int)floor(sz);
+  const double wx = sx - I, wy = sy - J, wz = sz - K;
+  double v = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    const int a = c & 1, bb = (c >> 1) & 1, cc = c >> 2;
+    const double w = (a ? wx : 1.0 - wx) * (bb ? wy : 1.0 - wy) * (cc ? wz : 1.0 - wz);
+    v += w * pu[cidx(pb, I + a, J + bb, K + cc)];
+  }
+  faces[t] = v;
 }
 
 __global__ void k_set_masked(const uint8_t* mask, const double* value, long long n, double* u) {
@@ -372,12 +436,21 @@ void launch_gj_invert(double* M, int n, double* rowp, double* colp, cudaStream_t
 }
 
 void launch_rhs64(const double* f, double scale, const double* beta, const uint8_t* mask,
-                  Box b, double ih2, const uint8_t dir[6], const double bval[6], double* out,
-                  cudaStream_t s) {
+                  Box b, double ih2, const uint8_t dir[6], const double bval[6],
+                  const double* faces, double* out, cudaStream_t s) {
   Val6 v;
   for (int q = 0; q < 6; ++q) v.v[q] = bval[q];
   k_rhs64<<<blocks_for(b.n()), kThreads, 0, s>>>(f, scale, beta, mask, b, ih2, to_dir(dir), v,
-                                                  out);
+                                                  faces, out);
+  add_launches(1);
+}
+
+long long face_count(const Box& b) { return face_offset(b, 5) + (long long)b.nx * b.ny; }
+
+void launch_subbox_bc(const double* parent_u, Box pb, int ox, int oy, int oz, Box sb,
+                      double* faces, cudaStream_t s) {
+  k_subbox_bc<<<blocks_for(face_count(sb)), kThreads, 0, s>>>(parent_u, pb, ox, oy, oz, sb,
+                                                               faces);
   add_launches(1);
 }
 

@@ -31,7 +31,11 @@ EXPORTS = [
     "mg_solve_set",
     "mg_set_stream", "mg_level_info", "mg_destroy", "mg_error_string", "mg_last_error",
     "mg_profile_enable", "mg_profile_read", "mg_launch_count", "mg_residual_norm_noalloc",
+    "mg_face_count", "mg_solve_batch", "mg_subbox_bc",
 ]
+
+MG_PROBLEM_POISSON = 0
+MG_PROBLEM_HELMHOLTZ = 1
 
 KCLASSES = ["smooth", "restrict", "prolong", "resid64", "coarse"]
 
@@ -62,6 +66,11 @@ class Stats(ctypes.Structure):
         return {"cycles": self.cycles, "converged": bool(self.converged),
                 "rel_resid": self.rel_resid, "time_ms": self.time_ms,
                 "hist": list(self.hist[:n])}
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("kind", ctypes.c_int), ("kappa", ctypes.c_double),
+                ("rhs", ctypes.c_void_p), ("faces", ctypes.c_void_p), ("u", ctypes.c_void_p)]
 
 
 class KProf(ctypes.Structure):
@@ -119,6 +128,13 @@ def load():
     lib.mg_residual_norm_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(BC),
                                              ctypes.c_double, P, ctypes.c_double, P, P, P, P]
     lib.mg_residual_norm_noalloc.restype = ctypes.c_int
+    lib.mg_face_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.mg_face_count.restype = ctypes.c_longlong
+    lib.mg_solve_batch.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double,
+                                   ctypes.POINTER(Stats)]
+    lib.mg_solve_batch.restype = ctypes.c_int
+    lib.mg_subbox_bc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), P]
+    lib.mg_subbox_bc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -171,6 +187,37 @@ def residual_norm_noalloc(u, rhs, h, alpha=0.0, rhs_scale=1.0, mask=None,
                                         _ptr(mask, torch.uint8), _ptr(u, torch.float64),
                                         _ptr(out, torch.float64), _stream_handle(stream)))
     return out
+
+
+def face_count(shape):
+    """Entries of the packed Dirichlet face data of a (nz, ny, nx) box."""
+    nz, ny, nx = shape
+    return load().mg_face_count(int(nx), int(ny), int(nz))
+
+
+def solve_batch(problems, tol=1e-10, raise_on_nonconvergence=True):
+    """Solve a list of problems, possibly on different Solvers (grids):
+    each item is a dict with keys solver, kind ("poisson"/"helmholtz"), rhs,
+    u, and optionally kappa and faces (packed Dirichlet data, CUDA float64)."""
+    lib = load()
+    arr = (Problem * len(problems))()
+    for q, pr in enumerate(problems):
+        sv = pr["solver"]
+        sv._check_field(pr["rhs"])
+        sv._check_field(pr["u"])
+        sv.set_stream()
+        faces = pr.get("faces")
+        if faces is not None and faces.numel() != face_count(sv.shape):
+            raise ValueError("faces has the wrong length")
+        arr[q] = Problem(sv._ctx.value, MG_PROBLEM_POISSON if pr["kind"] == "poisson"
+                         else MG_PROBLEM_HELMHOLTZ, float(pr.get("kappa", 0.0)),
+                         _ptr(pr["rhs"], torch.float64).value,
+                         None if faces is None else _ptr(faces, torch.float64).value,
+                         _ptr(pr["u"], torch.float64).value)
+    st = (Stats * max(1, len(problems)))()
+    status = lib.mg_solve_batch(arr, len(problems), float(tol), st)
+    _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+    return [st[q].as_dict() for q in range(len(problems))]
 
 
 def default_options():
@@ -244,6 +291,21 @@ class Solver:
         _check(self._lib.mg_profile_read(self._ctx, arr, 1 if reset else 0))
         return {k: {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
                 for i, k in enumerate(KCLASSES)}
+
+    def subbox_bc(self, parent_u, origin, dims, out=None):
+        """Dirichlet face data of a ratio-2 sub-box: origin = parent cell index
+        (x, y, z) of its lower corner, dims = sub-box size in fine cells
+        (x, y, z).  Returns the packed face array (CUDA float64)."""
+        self._check_field(parent_u)
+        nx, ny, nz = (int(d) for d in dims)
+        if out is None:
+            out = torch.empty(face_count((nz, ny, nx)), dtype=torch.float64, device=parent_u.device)
+        self.set_stream()
+        o = (ctypes.c_int * 3)(*[int(v) for v in origin])
+        d = (ctypes.c_int * 3)(nx, ny, nz)
+        _check(self._lib.mg_subbox_bc(self._ctx, _ptr(parent_u, torch.float64), o, d,
+                                      _ptr(out, torch.float64)))
+        return out
 
     def _check_field(self, t):
         if tuple(t.shape) != self.shape:

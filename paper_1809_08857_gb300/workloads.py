@@ -42,8 +42,14 @@ def gaussian_blobs(n, seed, nblobs=4, width=0.05):
 
 def dielectric_slab(n, z_top=0.2, eps_slab=4.0):
     """Relative permittivity eps_slab for cell centres with z < z_top, else 1."""
-    z = centres(n)
-    eps = np.ones((n, n, n))
+    return dielectric_slab_box((n, n, n), 1.0 / n, (0.0, 0.0, 0.0), z_top, eps_slab)
+
+
+def dielectric_slab_box(shape, h, origin, z_top=0.2, eps_slab=4.0):
+    """The dielectric slab sampled on a box (shape (nz, ny, nx), cell size h,
+    lower corner origin (x, y, z))."""
+    z = origin[2] + (np.arange(shape[0]) + 0.5) * h
+    eps = np.ones(shape)
     eps[z < z_top] = eps_slab
     return eps
 
@@ -66,14 +72,25 @@ def streamer_shell(n, seed, radius=0.02, z0=0.4, z1=0.8, axis_xy=(0.5, 0.5),
     cylinder (radius, from z0 to z1 on the axis) with a hemispherical head.
     Density amplitude * eps0 / h^2 times a lognormal factor exp(noise * xi),
     xi ~ N(0, 1) per shell cell (drawn in index order)."""
+    return streamer_shell_box((n, n, n), 1.0 / n, (0.0, 0.0, 0.0), seed, radius, z0, z1,
+                              axis_xy, amplitude, noise)
+
+
+def streamer_shell_box(shape, h, origin, seed, radius=0.02, z0=0.4, z1=0.8, axis_xy=(0.5, 0.5),
+                       amplitude=1e-3, noise=0.1):
+    """The streamer shell sampled on a box of the given shape (nz, ny, nx),
+    cell size h and lower corner origin (x, y, z): cells within h of the
+    surface carry amplitude * eps0 / h^2 * exp(noise * xi)."""
     rng = np.random.default_rng(seed)
-    h = 1.0 / n
-    x = centres(n)
-    shell = np.zeros((n, n, n), dtype=bool)
-    for k in range(n):
-        d = _shell_distance_slab(x, x, x[k], axis_xy, z0, z1, radius)
+    nz, ny, nx = shape
+    x = origin[0] + (np.arange(nx) + 0.5) * h
+    y = origin[1] + (np.arange(ny) + 0.5) * h
+    z = origin[2] + (np.arange(nz) + 0.5) * h
+    shell = np.zeros(shape, dtype=bool)
+    for k in range(nz):
+        d = _shell_distance_slab(x, y, z[k], axis_xy, z0, z1, radius)
         shell[k] = d <= h
-    rho = np.zeros((n, n, n))
+    rho = np.zeros(shape)
     cnt = int(shell.sum())
     rho[shell] = amplitude / h**2 * np.exp(noise * rng.standard_normal(cnt))
     return rho * EPS0
@@ -88,6 +105,24 @@ def ionization_source(n, seed, sigma_cells=2.0):
     shell = np.abs(streamer_shell(n, seed)) / EPS0
     s = gaussian_filter(shell, sigma=sigma_cells, mode="constant", truncate=4.0)
     return np.maximum(s, 0.0)
+
+
+def subbox_layout(n_parent, count, seed, sizes=(32, 48, 64, 96, 128), lo=0.1, hi=0.9):
+    """Refined sub-boxes (ratio 2) of a parent grid of n_parent^3 cells on the
+    unit cube: sizes (fine cells per side) drawn from `sizes`, lower corners
+    uniform so that each box lies inside [lo, hi]^3, aligned to parent cells.
+    Returns a list of (origin (x, y, z) in parent cells, dims (x, y, z) in fine
+    cells)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(rng.choice(sizes))
+        half = m // 2
+        lo_c = int(np.ceil(lo * n_parent))
+        hi_c = int(np.floor(hi * n_parent)) - half
+        o = rng.integers(lo_c, hi_c + 1, size=3)
+        out.append(((int(o[0]), int(o[1]), int(o[2])), (m, m, m)))
+    return out
 
 
 def needle_mask(n, tip_z=0.8, tip_radius_cells=5.0, half_angle_deg=10.0, axis_xy=(0.5, 0.5)):
