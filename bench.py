@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--inner-cycles", type=int, default=3)
     ap.add_argument("--concurrency", type=int, default=4)
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep --inner-cycles and V(2,2) instead of the autotuned choice")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -279,6 +281,15 @@ def run_ours(args):
     prec = mg.MG_PREC_MIXED if args.precision == "mixed" else mg.MG_PREC_FP64
     solver = mg.Solver((n, n, n), h, eps_r=eps, precision=prec, inner_cycles=args.inner_cycles,
                        concurrency=args.concurrency, graphs=not args.no_graphs)
+    tuned = None
+    if not args.no_autotune:
+        import tempfile as _tf
+
+        from paper_1809_08857_gb300 import autotune
+
+        cache = os.path.join(_tf.gettempdir(), f"mg_autotune_rank{rank}.json")
+        tuned, _ = autotune.tuned(solver, rho, S, KAPPAS, TOL, has_eps=True, precision=prec,
+                                  cache_path=cache)
     phi = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
     psi = [torch.zeros_like(phi) for _ in range(3)]
     cycles = [0, 0, 0, 0]
@@ -365,7 +376,9 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 (FP32 V-cycles in FP64 refinement)" if prec else "f64",
             "data": "synthetic (seeded streamer shell, dielectric slab, smoothed ionisation source)",
-            "config": config(args), "clocks": clk.summary(), "e2e": e2e,
+            "config": dict(config(args), autotuned=tuned, nu1=solver.options.nu1,
+                           nu2=solver.options.nu2, inner_cycles=solver.options.inner_cycles),
+            "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": launches, "cycles_per_problem": cycles,
             "roofline": roofline(prof, n, ms), "kernel_profile": prof}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -219,6 +219,21 @@ mg_status mg_solve_batch(const mg_problem* probs, int nprob, double tol, mg_stat
 mg_status mg_subbox_bc(const mg_ctx* parent, const double* parent_u, const int origin[3],
                        const int dims[3], double* faces);
 
+/* Replace the solver options of a context (precision is fixed at create). */
+mg_status mg_set_options(mg_ctx* ctx, const mg_options* opt);
+
+/*
+ * mg_autotune -- pick the smoother sweeps (nu1, nu2) in {(1,1), (2,1), (2,2),
+ * (3,3)} and, in mixed precision, the inner V-cycles per refinement step in
+ * {1..4} by timing mg_solve_set on the caller's problem (each candidate run
+ * twice from a zero guess, the faster counts; candidates that do not reach
+ * tol are rejected).  The fastest is installed in the context and returned in
+ * *best (*best_ms, nullable: its device time).  Allocates four scratch fields
+ * for the duration of the call.  Arguments as in mg_solve_set.
+ */
+mg_status mg_autotune(mg_ctx* ctx, const double* rho, const double* S, const double kappa[3],
+                      double tol, mg_options* best, double* best_ms);
+
 /* ---- instrumentation ------------------------------------------------------
  * Kernel classes of the fine (finest-level) launches: red-black smoothing,
  * fused residual + restriction, prolongation + correction, the FP64

@@ -109,7 +109,7 @@ struct LevelWork {
 struct StepGraph {
   int kind = 0;
   double alpha = 0;
-  int ic = 0;
+  int ic = 0, nu1 = 0, nu2 = 0;
   bool prof = false;
   const double* b = nullptr;
   const double* u_in = nullptr;
@@ -561,8 +561,9 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
   Work* w = p.w;
   const int ic = c->opt.inner_cycles;
   for (StepGraph& g : w->graphs)
-    if (g.kind == p.kind && g.alpha == p.alpha && g.ic == ic && g.prof == c->prof && g.b == p.b &&
-        g.u_in == p.cur && g.u_out == p.other) {
+    if (g.kind == p.kind && g.alpha == p.alpha && g.ic == ic && g.nu1 == c->opt.nu1 &&
+        g.nu2 == c->opt.nu2 && g.prof == c->prof && g.b == p.b && g.u_in == p.cur &&
+        g.u_out == p.other) {
       g.stamp = ++c->clock;
       *out = &g;
       return MG_OK;
@@ -584,6 +585,8 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
   g.kind = p.kind;
   g.alpha = p.alpha;
   g.ic = ic;
+  g.nu1 = c->opt.nu1;
+  g.nu2 = c->opt.nu2;
   g.prof = c->prof;
   g.b = p.b;
   g.u_in = p.cur;
@@ -1105,6 +1108,80 @@ mg_status mg_subbox_bc(const mg_ctx* parent, const double* parent_u, const int o
 long long mg_face_count(int nx, int ny, int nz) {
   if (nx < 1 || ny < 1 || nz < 1) return 0;
   return mg::face_count(mg::Box{nx, ny, nz});
+}
+
+mg_status mg_set_options(mg_ctx* c, const mg_options* opt) {
+  g_last_error.clear();
+  if (!c || !opt) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  mg_options o;
+  MG_TRY(normalise_options(opt, &o));
+  if (o.precision != c->opt.precision)
+    return fail(MG_ERR_INVALID_ARG, "the precision mode is fixed at mg_create");
+  c->opt = o;
+  return MG_OK;
+}
+
+mg_status mg_autotune(mg_ctx* c, const double* rho, const double* S, const double kappa[3],
+                      double tol, mg_options* best, double* best_ms) {
+  g_last_error.clear();
+  MG_TRY(check_ctx_tol(c, tol));
+  if (!rho || !S || !kappa || !best) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  const size_t n = (size_t)c->lv[0].b.n();
+  double* scratch = nullptr;
+  MG_CUDA(cudaMalloc((void**)&scratch, 4 * n * sizeof(double)));
+  double* phi = scratch;
+  double* psi[3] = {scratch + n, scratch + 2 * n, scratch + 3 * n};
+  const mg_options keep = c->opt;
+  const int sweeps[4][2] = {{1, 1}, {2, 1}, {2, 2}, {3, 3}};
+  const int inner_mixed[4] = {1, 2, 3, 4};
+  const int n_inner = c->opt.precision == MG_PREC_MIXED ? 4 : 1;
+  double best_t = 1e300;
+  mg_options best_o = keep;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  mg_status st = MG_OK;
+  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+    st = fail(MG_ERR_CUDA, "cudaEventCreate failed");
+  for (int a = 0; a < 4 && st == MG_OK; ++a)
+    for (int b = 0; b < n_inner && st == MG_OK; ++b) {
+      mg_options o = keep;
+      o.nu1 = sweeps[a][0];
+      o.nu2 = sweeps[a][1];
+      o.inner_cycles = c->opt.precision == MG_PREC_MIXED ? inner_mixed[b] : 1;
+      c->opt = o;
+      double t_min = 1e300;
+      for (int rep = 0; rep < 2 && st == MG_OK; ++rep) {  // first run builds graphs
+        if (cudaMemsetAsync(scratch, 0, 4 * n * sizeof(double), c->stream) != cudaSuccess ||
+            cudaEventRecord(t0, c->stream) != cudaSuccess) {
+          st = fail(MG_ERR_CUDA, "autotune launch failed");
+          break;
+        }
+        const mg_status sv = mg_solve_set(c, rho, phi, S, psi, kappa, tol, nullptr);
+        cudaEventRecord(t1, c->stream);
+        cudaEventSynchronize(t1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (sv == MG_ERR_NOT_CONVERGED) break;  // candidate rejected
+        if (sv != MG_OK) {
+          st = sv;
+          break;
+        }
+        t_min = std::min(t_min, (double)ms);
+      }
+      if (st == MG_OK && t_min < best_t) {
+        best_t = t_min;
+        best_o = o;
+      }
+    }
+  c->opt = st == MG_OK ? best_o : keep;
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(scratch);
+  if (st != MG_OK) return st;
+  if (best_t >= 1e300) return fail(MG_ERR_NOT_CONVERGED, "no candidate converged");
+  *best = best_o;
+  if (best_ms) *best_ms = best_t;
+  return MG_OK;
 }
 
 mg_status mg_profile_enable(mg_ctx* c, int enable) {

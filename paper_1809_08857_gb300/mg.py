@@ -31,7 +31,7 @@ EXPORTS = [
     "mg_solve_set",
     "mg_set_stream", "mg_level_info", "mg_destroy", "mg_error_string", "mg_last_error",
     "mg_profile_enable", "mg_profile_read", "mg_launch_count", "mg_residual_norm_noalloc",
-    "mg_face_count", "mg_solve_batch", "mg_subbox_bc",
+    "mg_face_count", "mg_solve_batch", "mg_subbox_bc", "mg_set_options", "mg_autotune",
 ]
 
 MG_PROBLEM_POISSON = 0
@@ -135,6 +135,11 @@ def load():
     lib.mg_solve_batch.restype = ctypes.c_int
     lib.mg_subbox_bc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), P]
     lib.mg_subbox_bc.restype = ctypes.c_int
+    lib.mg_set_options.argtypes = [P, ctypes.POINTER(Options)]
+    lib.mg_set_options.restype = ctypes.c_int
+    lib.mg_autotune.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_double)]
+    lib.mg_autotune.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -256,6 +261,7 @@ class Solver:
         _check(st)
         self._ctx = ctx
         self._lib = lib
+        self.options = opt
 
     def close(self):
         if getattr(self, "_ctx", None):
@@ -291,6 +297,29 @@ class Solver:
         _check(self._lib.mg_profile_read(self._ctx, arr, 1 if reset else 0))
         return {k: {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
                 for i, k in enumerate(KCLASSES)}
+
+    def set_options(self, **kw):
+        """Change nu1, nu2, max_cycles, inner_cycles, concurrency or graphs."""
+        o = Options.from_buffer_copy(self.options)
+        for k, v in kw.items():
+            if k == "graphs":
+                o.no_graphs = 0 if v else 1
+            else:
+                setattr(o, k, int(v))
+        _check(self._lib.mg_set_options(self._ctx, ctypes.byref(o)))
+        self.options = o
+
+    def autotune(self, rho, S, kappa, tol=1e-10):
+        """Time the sweep / inner-cycle candidates on this problem (mg_autotune)
+        and install the fastest.  Returns (options dict, device ms)."""
+        self.set_stream()
+        best = Options()
+        ms = ctypes.c_double()
+        kap = (ctypes.c_double * 3)(*[float(k) for k in kappa])
+        _check(self._lib.mg_autotune(self._ctx, _ptr(rho, torch.float64), _ptr(S, torch.float64),
+                                     kap, float(tol), ctypes.byref(best), ctypes.byref(ms)))
+        self.options = best
+        return ({"nu1": best.nu1, "nu2": best.nu2, "inner_cycles": best.inner_cycles}, ms.value)
 
     def subbox_bc(self, parent_u, origin, dims, out=None):
         """Dirichlet face data of a ratio-2 sub-box: origin = parent cell index

@@ -250,3 +250,32 @@ def test_repeated_solves_reuse_graphs(mg):
     s.close()
     assert res[0][0] == res[1][0] == res[2][0]
     assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[1][1], res[2][1])
+
+
+def test_autotune_picks_a_converging_configuration(mg, tmp_path):
+    """mg_autotune on a small solve set returns a candidate from its grid that
+    converges; the cache then reinstalls it without searching."""
+    from paper_1809_08857_gb300 import autotune
+
+    n = 32
+    h = 1.0 / n
+    rho, eps, S = W.streamer_shell(n, 1), W.dielectric_slab(n), W.ionization_source(n, 1)
+    s = mg.Solver((n, n, n), h, eps_r=cuda(eps), precision=1)
+    path = str(tmp_path / "tune.json")
+    entry, hit = autotune.tuned(s, cuda(rho), cuda(S), W.helmholtz_kappas(), TOL, has_eps=True,
+                                cache_path=path)
+    assert not hit
+    assert (entry["nu1"], entry["nu2"]) in [(1, 1), (2, 1), (2, 2), (3, 3)]
+    assert 1 <= entry["inner_cycles"] <= 4
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    psi = [torch.zeros_like(phi) for _ in range(3)]
+    st = s.solve_set(cuda(rho), phi, cuda(S), psi, W.helmholtz_kappas(), TOL)
+    assert all(x["converged"] for x in st)
+    ref, _ = oracle_poisson((n, n, n), h, rho, eps)
+    assert oracle.rel_l2(phi.cpu().numpy(), ref) <= PARITY
+    s2 = mg.Solver((n, n, n), h, eps_r=cuda(eps), precision=1)
+    _, hit2 = autotune.tuned(s2, cuda(rho), cuda(S), W.helmholtz_kappas(), TOL, has_eps=True,
+                             cache_path=path)
+    assert hit2 and s2.options.inner_cycles == entry["inner_cycles"]
+    s.close()
+    s2.close()
