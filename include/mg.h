@@ -234,6 +234,81 @@ mg_status mg_set_options(mg_ctx* ctx, const mg_options* opt);
 mg_status mg_autotune(mg_ctx* ctx, const double* rho, const double* S, const double kappa[3],
                       double tol, mg_options* best, double* best_ms);
 
+/* ---- learned warm start ----------------------------------------------------
+ *
+ * A 3D U-Net (4 levels with 16/32/48/64 channels, two 3x3x3 convolutions
+ * with ReLU per level, 2x average pooling, nearest 2x upsampling followed by a
+ * 3x3x3 convolution, skip connections by concatenation, 1x1x1 head) predicts
+ * the change of the potential between two time steps of the paper's scheme,
+ * whose elliptic solves are re-done only every coarse step (Sec. 2.2), from
+ * the new charge and the previous potential:
+ *     phi_guess = phi_prev + U(rho_n * s_rho, phi_prev * s_phi) / s_out.
+ * Activations and weights are BF16 with FP32 accumulation on the tensor
+ * cores (mma.sync); FP32 master weights are trained with Adam.  The paper has
+ * no network: this is the warm start of the solver, and multigrid corrects
+ * its guess to the same tolerance, so it cannot change the answer.
+ * Field arguments are device FP64 [n][d][h][w] (x fastest), d, h, w
+ * multiples of 8.
+ */
+typedef struct mg_unet mg_unet;
+
+/* New network with He-normal weights from the seed (the head starts at 0,
+ * so an untrained network predicts phi_prev). */
+mg_status mg_unet_create(unsigned long long seed, mg_unet** out);
+void mg_unet_destroy(mg_unet* net);
+/* Input / output scales (all > 0). */
+mg_status mg_unet_set_scales(mg_unet* net, double s_rho, double s_phi, double s_out);
+mg_status mg_unet_get_scales(const mg_unet* net, double scales[3]);
+/* One training step on a batch of n crops: forward, MSE loss against
+ * (phi - phi_prev) * s_out, backward, Adam (lr, beta = 0.9/0.999).  loss
+ * (host, nullable) receives the batch loss before the update (synchronises). */
+mg_status mg_unet_train_step(mg_unet* net, const double* rho, const double* phi_prev,
+                             const double* phi, int n, int d, int h, int w, float lr, float* loss,
+                             void* cuda_stream);
+/* phi_guess = phi_prev + U(...) / s_out (asynchronous on the stream). */
+mg_status mg_unet_predict(mg_unet* net, const double* rho, const double* phi_prev,
+                          double* phi_guess, int n, int d, int h, int w, void* cuda_stream);
+/* Loss and FP32 gradients of every parameter (no update), for checking;
+ * host_grads has mg_unet_num_params entries in mg_unet_get_params order. */
+mg_status mg_unet_grads(mg_unet* net, const double* rho, const double* phi_prev,
+                        const double* phi, int n, int d, int h, int w, float* host_grads,
+                        float* loss);
+mg_status mg_unet_num_params(const mg_unet* net, long long* n);
+/* FP32 master parameters to / from host memory, in a fixed order: every
+ * conv's weights [Cout][27][Cin] then bias, in the order enc0a, enc0b, enc1a,
+ * enc1b, enc2a, enc2b, enc3a, enc3b, then per level l = 0, 1, 2: up_l, dec_l_a,
+ * dec_l_b; then the head's 16 weights and bias. */
+mg_status mg_unet_get_params(const mg_unet* net, float* host);
+mg_status mg_unet_set_params(mg_unet* net, const float* host);
+/* Weights and scales to / from a versioned binary file. */
+mg_status mg_unet_save(const mg_unet* net, const char* path);
+mg_status mg_unet_load(mg_unet* net, const char* path);
+
+/* Single 3x3x3 convolution (zero padding) on channels-last BF16 tensors, the
+ * network's kernel exposed for tests: y = relu?(conv(concat(x1, x2)) + bias),
+ * weights [cout][27][c1 + c2] BF16, c1, c2 multiples of 16, cout in
+ * {16, 32, 48, 64, 96}; bias (FP32, nullable). */
+mg_status mg_nn_conv3d(const void* x1, int c1, const void* x2, int c2, const void* w,
+                       const float* bias, int relu, int cout, int n, int d, int h, int w_,
+                       void* y, void* cuda_stream);
+/* Its weight gradient dW[co][t][ci] = sum_v dy[v][co] x[v + off(t)][ci] (FP32, overwritten). */
+mg_status mg_nn_conv3d_wgrad(const void* dy, int cout, const void* x1, int c1, const void* x2,
+                             int c2, int n, int d, int h, int w, float* dw, void* cuda_stream);
+
+/* Attach a network to a context (not owned; NULL detaches), or load one from
+ * a file (owned by the context). */
+mg_status mg_warmstart_attach(mg_ctx* ctx, mg_unet* net);
+mg_status mg_warmstart_load(mg_ctx* ctx, const char* weights_path);
+/*
+ * mg_warmstart_predict -- guess for the Poisson solve of rho from the
+ * previous potential: the network's prediction, unless its FP64 residual
+ * ||b - A phi|| is larger than that of phi_prev, in which case phi_prev is
+ * used (plain multigrid judges the network).  *used_net (nullable) tells
+ * which.  Synchronises the context's stream.
+ */
+mg_status mg_warmstart_predict(mg_ctx* ctx, const double* rho, const double* phi_prev,
+                               double* phi_guess, int* used_net);
+
 /* ---- instrumentation ------------------------------------------------------
  * Kernel classes of the fine (finest-level) launches: red-black smoothing,
  * fused residual + restriction, prolongation + correction, the FP64

@@ -150,6 +150,8 @@ struct mg_ctx {
   std::vector<void*> allocs;
   std::vector<void*> host_allocs;
   unsigned long long clock = 0;
+  mg_unet* net = nullptr;  // warm-start network
+  bool own_net = false;
   // instrumentation
   bool prof = false;
   std::vector<ProfRec> pending;
@@ -860,6 +862,7 @@ void destroy(mg_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   for (void* p : c->host_allocs) cudaFreeHost(p);
   if (c->fork) cudaEventDestroy(c->fork);
+  if (c->own_net) mg_unet_destroy(c->net);
   delete c;
 }
 
@@ -1181,6 +1184,53 @@ mg_status mg_autotune(mg_ctx* c, const double* rho, const double* S, const doubl
   if (best_t >= 1e300) return fail(MG_ERR_NOT_CONVERGED, "no candidate converged");
   *best = best_o;
   if (best_ms) *best_ms = best_t;
+  return MG_OK;
+}
+
+mg_status mg_warmstart_attach(mg_ctx* c, mg_unet* net) {
+  if (!c) return fail(MG_ERR_INVALID_ARG, "ctx is NULL");
+  if (c->own_net) mg_unet_destroy(c->net);
+  c->net = net;
+  c->own_net = false;
+  return MG_OK;
+}
+
+mg_status mg_warmstart_load(mg_ctx* c, const char* path) {
+  if (!c || !path) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  mg_unet* net = nullptr;
+  MG_TRY(mg_unet_create(0, &net));
+  const mg_status st = mg_unet_load(net, path);
+  if (st != MG_OK) {
+    mg_unet_destroy(net);
+    return st;
+  }
+  if (c->own_net) mg_unet_destroy(c->net);
+  c->net = net;
+  c->own_net = true;
+  return MG_OK;
+}
+
+mg_status mg_warmstart_predict(mg_ctx* c, const double* rho, const double* phi_prev,
+                               double* phi_guess, int* used_net) {
+  g_last_error.clear();
+  if (!c || !rho || !phi_prev || !phi_guess) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  if (!c->net) return fail(MG_ERR_INVALID_ARG, "no warm-start network attached");
+  const mg::Box b = c->lv[0].b;
+  cudaStream_t s = c->stream;
+  MG_TRY(mg_unet_predict(c->net, rho, phi_prev, phi_guess, 1, b.nz, b.ny, b.nx, s));
+  // plain multigrid judges the guess: FP64 residual of both candidates
+  Prob p = make_prob(c, kPoisson, 0.0, rho, nullptr, phi_guess, 0.0, nullptr);
+  MG_TRY(get_work(c, 0, &p.w));
+  MG_TRY(prepare(p, s));
+  MG_TRY(enqueue_ir(c, p.w, s, kPoisson, 0.0, p.b, phi_guess, nullptr, false, false, false, 0));
+  MG_TRY(enqueue_ir(c, p.w, s, kPoisson, 0.0, p.b, phi_prev, nullptr, false, false, false, 1));
+  MG_CUDA(cudaStreamSynchronize(s));
+  const double r_net = p.w->norm_host[0], r_prev = p.w->norm_host[1];
+  const bool use = std::isfinite(r_net) && r_net <= r_prev;
+  if (!use)
+    MG_CUDA(cudaMemcpyAsync(phi_guess, phi_prev, sizeof(double) * b.n(), cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(cudaStreamSynchronize(s));
+  if (used_net) *used_net = use ? 1 : 0;
   return MG_OK;
 }
 

@@ -32,6 +32,10 @@ EXPORTS = [
     "mg_set_stream", "mg_level_info", "mg_destroy", "mg_error_string", "mg_last_error",
     "mg_profile_enable", "mg_profile_read", "mg_launch_count", "mg_residual_norm_noalloc",
     "mg_face_count", "mg_solve_batch", "mg_subbox_bc", "mg_set_options", "mg_autotune",
+    "mg_unet_create", "mg_unet_destroy", "mg_unet_set_scales", "mg_unet_get_scales",
+    "mg_unet_train_step", "mg_unet_predict", "mg_unet_grads", "mg_unet_num_params",
+    "mg_unet_get_params", "mg_unet_set_params", "mg_unet_save", "mg_unet_load", "mg_nn_conv3d",
+    "mg_nn_conv3d_wgrad", "mg_warmstart_attach", "mg_warmstart_load", "mg_warmstart_predict",
 ]
 
 MG_PROBLEM_POISSON = 0
@@ -140,6 +144,32 @@ def load():
     lib.mg_autotune.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                                 ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_double)]
     lib.mg_autotune.restype = ctypes.c_int
+    I, D, F = ctypes.c_int, ctypes.c_double, ctypes.c_float
+    FP = ctypes.POINTER(ctypes.c_float)
+    lib.mg_unet_create.argtypes = [ctypes.c_ulonglong, ctypes.POINTER(P)]
+    lib.mg_unet_destroy.argtypes = [P]
+    lib.mg_unet_destroy.restype = None
+    lib.mg_unet_set_scales.argtypes = [P, D, D, D]
+    lib.mg_unet_get_scales.argtypes = [P, ctypes.POINTER(D)]
+    lib.mg_unet_train_step.argtypes = [P, P, P, P, I, I, I, I, F, FP, P]
+    lib.mg_unet_predict.argtypes = [P, P, P, P, I, I, I, I, P]
+    lib.mg_unet_grads.argtypes = [P, P, P, P, I, I, I, I, FP, FP]
+    lib.mg_unet_num_params.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.mg_unet_get_params.argtypes = [P, FP]
+    lib.mg_unet_set_params.argtypes = [P, FP]
+    lib.mg_unet_save.argtypes = [P, ctypes.c_char_p]
+    lib.mg_unet_load.argtypes = [P, ctypes.c_char_p]
+    lib.mg_nn_conv3d.argtypes = [P, I, P, I, P, P, I, I, I, I, I, I, P, P]
+    lib.mg_nn_conv3d_wgrad.argtypes = [P, I, P, I, P, I, I, I, I, I, P, P]
+    lib.mg_warmstart_attach.argtypes = [P, P]
+    lib.mg_warmstart_load.argtypes = [P, ctypes.c_char_p]
+    lib.mg_warmstart_predict.argtypes = [P, P, P, P, ctypes.POINTER(I)]
+    for name in ("mg_unet_create", "mg_unet_set_scales", "mg_unet_get_scales",
+                 "mg_unet_train_step", "mg_unet_predict", "mg_unet_grads", "mg_unet_num_params",
+                 "mg_unet_get_params", "mg_unet_set_params", "mg_unet_save", "mg_unet_load",
+                 "mg_nn_conv3d", "mg_nn_conv3d_wgrad", "mg_warmstart_attach",
+                 "mg_warmstart_load", "mg_warmstart_predict"):
+        getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -321,6 +351,24 @@ class Solver:
         self.options = best
         return ({"nu1": best.nu1, "nu2": best.nu2, "inner_cycles": best.inner_cycles}, ms.value)
 
+    def warmstart_attach(self, net):
+        """Use a UNet for mg_warmstart_predict (None detaches)."""
+        self._net = net
+        _check(self._lib.mg_warmstart_attach(self._ctx, None if net is None else net._p))
+
+    def warmstart_predict(self, rho, phi_prev, out=None):
+        """Judged network guess for the Poisson solve; returns (guess, used_net)."""
+        self._check_field(rho)
+        self._check_field(phi_prev)
+        if out is None:
+            out = torch.empty_like(phi_prev)
+        self.set_stream()
+        used = ctypes.c_int()
+        _check(self._lib.mg_warmstart_predict(self._ctx, _ptr(rho, torch.float64),
+                                              _ptr(phi_prev, torch.float64),
+                                              _ptr(out, torch.float64), ctypes.byref(used)))
+        return out, bool(used.value)
+
     def subbox_bc(self, parent_u, origin, dims, out=None):
         """Dirichlet face data of a ratio-2 sub-box: origin = parent cell index
         (x, y, z) of its lower corner, dims = sub-box size in fine cells
@@ -400,3 +448,123 @@ class Solver:
         phi_host.copy_(phi, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return st
+
+
+class UNet:
+    """The warm-start U-Net of libmg (mg_unet_*): fields are CUDA float64
+    tensors of shape (n, d, h, w) or (d, h, w) with d, h, w multiples of 8."""
+
+    def __init__(self, seed=0):
+        self._lib = load()
+        p = ctypes.c_void_p()
+        _check(self._lib.mg_unet_create(int(seed), ctypes.byref(p)))
+        self._p = p
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self._lib.mg_unet_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _dims(t):
+        if t.dim() == 3:
+            return (1,) + tuple(t.shape)
+        if t.dim() == 4:
+            return tuple(t.shape)
+        raise ValueError("expected (d, h, w) or (n, d, h, w)")
+
+    def set_scales(self, s_rho, s_phi, s_out):
+        _check(self._lib.mg_unet_set_scales(self._p, float(s_rho), float(s_phi), float(s_out)))
+
+    def scales(self):
+        out = (ctypes.c_double * 3)()
+        _check(self._lib.mg_unet_get_scales(self._p, out))
+        return tuple(out)
+
+    def train_step(self, rho, prev, phi, lr=1e-3, stream=None):
+        n, d, h, w = self._dims(rho)
+        loss = ctypes.c_float()
+        _check(self._lib.mg_unet_train_step(self._p, _ptr(rho, torch.float64),
+                                            _ptr(prev, torch.float64), _ptr(phi, torch.float64),
+                                            n, d, h, w, float(lr), ctypes.byref(loss),
+                                            _stream_handle(stream)))
+        return loss.value
+
+    def predict(self, rho, prev, out=None, stream=None):
+        n, d, h, w = self._dims(rho)
+        if out is None:
+            out = torch.empty_like(prev)
+        _check(self._lib.mg_unet_predict(self._p, _ptr(rho, torch.float64),
+                                         _ptr(prev, torch.float64), _ptr(out, torch.float64),
+                                         n, d, h, w, _stream_handle(stream)))
+        return out
+
+    def num_params(self):
+        n = ctypes.c_longlong()
+        _check(self._lib.mg_unet_num_params(self._p, ctypes.byref(n)))
+        return n.value
+
+    def get_params(self):
+        import numpy as np
+
+        a = np.empty(self.num_params(), dtype=np.float32)
+        _check(self._lib.mg_unet_get_params(self._p, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return a
+
+    def set_params(self, a):
+        import numpy as np
+
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        if a.size != self.num_params():
+            raise ValueError("parameter count mismatch")
+        _check(self._lib.mg_unet_set_params(self._p, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def grads(self, rho, prev, phi):
+        import numpy as np
+
+        n, d, h, w = self._dims(rho)
+        g = np.empty(self.num_params(), dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(self._lib.mg_unet_grads(self._p, _ptr(rho, torch.float64), _ptr(prev, torch.float64),
+                                       _ptr(phi, torch.float64), n, d, h, w,
+                                       g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                       ctypes.byref(loss)))
+        return g, loss.value
+
+    def save(self, path):
+        _check(self._lib.mg_unet_save(self._p, str(path).encode()))
+
+    def load_file(self, path):
+        _check(self._lib.mg_unet_load(self._p, str(path).encode()))
+
+
+def conv3d(x1, w, bias=None, x2=None, relu=False, stream=None):
+    """One network convolution (mg_nn_conv3d): x1/x2 channels-last bfloat16
+    CUDA tensors (n, d, h, w, c), w bfloat16 (cout, 27, c1 + c2), bias float32."""
+    n, d, h, ww, c1 = x1.shape
+    c2 = 0 if x2 is None else x2.shape[-1]
+    cout = w.shape[0]
+    y = torch.empty((n, d, h, ww, cout), dtype=torch.bfloat16, device=x1.device)
+    _check(load().mg_nn_conv3d(_ptr(x1, torch.bfloat16), c1, None if x2 is None else _ptr(x2, torch.bfloat16),
+                               c2, _ptr(w, torch.bfloat16), None if bias is None else _ptr(bias, torch.float32),
+                               1 if relu else 0, cout, n, d, h, ww, _ptr(y, torch.bfloat16),
+                               _stream_handle(stream)))
+    return y
+
+
+def conv3d_wgrad(dy, x1, x2=None, stream=None):
+    """Weight gradient (mg_nn_conv3d_wgrad) as float32 (cout, 27, c1 + c2)."""
+    n, d, h, ww, cout = dy.shape
+    c1 = x1.shape[-1]
+    c2 = 0 if x2 is None else x2.shape[-1]
+    dw = torch.empty((cout, 27, c1 + c2), dtype=torch.float32, device=dy.device)
+    _check(load().mg_nn_conv3d_wgrad(_ptr(dy, torch.bfloat16), cout, _ptr(x1, torch.bfloat16), c1,
+                                     None if x2 is None else _ptr(x2, torch.bfloat16), c2, n, d, h,
+                                     ww, _ptr(dw, torch.float32), _stream_handle(stream)))
+    return dw

@@ -1,0 +1,140 @@
+"""GPU tests of the warm-start U-Net kernels and network against the numpy
+oracle (oracle/unet.py), which runs in FP64 on the same BF16 weights and,
+for the whole network, rounds stored activations to BF16 as the GPU does."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_08857_gb300 import build, mg as _mg
+
+    build.build()
+    _mg.load()
+    return _mg
+
+
+def bf(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).cuda()
+
+
+@pytest.mark.parametrize("shape,c1,c2,cout,relu", [
+    ((2, 3, 5, 19), 16, 0, 16, True),     # ragged against the 16 x 4 x 2 tile
+    ((1, 4, 8, 16), 32, 0, 48, True),
+    ((1, 5, 6, 7), 48, 48, 48, True),     # concatenated input
+    ((1, 4, 4, 20), 16, 16, 96, False),   # widest output (input gradient of a concat layer)
+    ((1, 2, 9, 33), 64, 0, 64, False),
+])
+def test_conv3d_matches_oracle(mg, shape, c1, c2, cout, relu):
+    rng = np.random.default_rng(c1 + c2 + cout)
+    n, d, h, w = shape
+    x1 = U.to_bf16(rng.standard_normal((n, d, h, w, c1)))
+    x2 = U.to_bf16(rng.standard_normal((n, d, h, w, c2))) if c2 else None
+    wt = U.to_bf16(rng.standard_normal((cout, 27, c1 + c2)) * 0.1)
+    b = rng.standard_normal(cout).astype(np.float32)
+    y = mg.conv3d(bf(x1), bf(wt), torch.from_numpy(b).cuda(), None if x2 is None else bf(x2), relu)
+    torch.cuda.synchronize()
+    got = y.float().cpu().numpy().astype(np.float64)
+    xin = x1 if x2 is None else np.concatenate([x1, x2], axis=-1)
+    ref = U.conv3d(xin, wt, b.astype(np.float64))
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    # output rounded to bfloat16 (relative 2^-8), FP32 accumulation
+    assert np.all(np.abs(got - ref) <= 2.0**-8 * np.abs(ref) + 1e-4 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("cout,c1,c2", [(16, 16, 0), (48, 48, 48), (64, 64, 0), (32, 16, 0)])
+def test_wgrad_matches_oracle(mg, cout, c1, c2):
+    rng = np.random.default_rng(cout * 7 + c1)
+    n, d, h, w = 2, 4, 6, 9
+    x1 = U.to_bf16(rng.standard_normal((n, d, h, w, c1)))
+    x2 = U.to_bf16(rng.standard_normal((n, d, h, w, c2))) if c2 else None
+    dy = U.to_bf16(rng.standard_normal((n, d, h, w, cout)))
+    dw = mg.conv3d_wgrad(bf(dy), bf(x1), None if x2 is None else bf(x2)).cpu().numpy()
+    xin = x1 if x2 is None else np.concatenate([x1, x2], axis=-1)
+    _, ref, _ = U.conv3d_backward(xin, np.zeros((cout, 27, c1 + c2)), dy)
+    assert np.abs(dw - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def _batch(rng, n, s):
+    rho = rng.standard_normal((n, s, s, s))
+    prev = np.cumsum(rng.standard_normal((n, s, s, s)), axis=1) * 0.1
+    phi = prev + 0.05 * rng.standard_normal((n, s, s, s)) + 0.02 * rho
+    return rho, prev, phi
+
+
+def _cuda64(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_network_gradients_match_oracle(mg):
+    """Loss and every layer's weight gradient of the whole U-Net (n = 2,
+    16^3) against the oracle with BF16 storage emulated."""
+    rng = np.random.default_rng(5)
+    net = mg.UNet(seed=3)
+    params = net.get_params()
+    params[-17:-1] = 0.3 * rng.standard_normal(16)  # non-zero head so every layer gets gradient
+    params[-1] = 0.05
+    net.set_params(params)
+    net.set_scales(0.8, 1.2, 4.0)
+    rho, prev, phi = _batch(rng, 2, 16)
+    g, loss = net.grads(_cuda64(rho), _cuda64(prev), _cuda64(phi))
+    p = U.unpack(params.astype(np.float64))
+    ref_loss, G = U.loss_and_grads(p, rho, prev, phi, (0.8, 1.2, 4.0), bf16=True)
+    assert abs(loss - ref_loss) <= 1e-2 * ref_loss
+    gd = U.unpack(g.astype(np.float64))
+    for name, co, ci in U.layer_shapes() + [("head", 1, 16)]:
+        for part in (".w", ".b"):
+            a, b = gd[name + part].ravel(), G[name + part].ravel()
+            err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+            assert err <= 0.05, (name + part, err)
+    net.close()
+
+
+def test_training_reduces_loss_and_save_load_roundtrip(mg, tmp_path):
+    rng = np.random.default_rng(6)
+    net = mg.UNet(seed=1)
+    net.set_scales(1.0, 1.0, 5.0)
+    rho_np, prev_np, _ = _batch(rng, 2, 16)
+    phi_np = prev_np + 0.05 * rho_np  # a learnable change
+    rho, prev, phi = _cuda64(rho_np), _cuda64(prev_np), _cuda64(phi_np)
+    losses = [net.train_step(rho, prev, phi, lr=2e-3) for _ in range(60)]
+    assert losses[-1] < 0.3 * losses[0]
+    path = tmp_path / "w.bin"
+    net.save(path)
+    g1 = net.predict(rho, prev)
+    net2 = mg.UNet(seed=99)
+    net2.load_file(path)
+    assert net2.scales() == (1.0, 1.0, 5.0)
+    g2 = net2.predict(rho, prev)
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2)
+    net.close()
+    net2.close()
+
+
+def test_untrained_network_predicts_previous_potential(mg):
+    """The head starts at zero: the guess is phi_prev exactly, and the
+    judged warm start accepts it (equal residual)."""
+    n = 32
+    rng = np.random.default_rng(7)
+    from paper_1809_08857_gb300 import workloads as W
+
+    rho = _cuda64(W.gaussian_blobs(n, 1))
+    prev = _cuda64(rng.standard_normal((n, n, n)))
+    net = mg.UNet(seed=2)
+    s = mg.Solver((n, n, n), 1.0 / n, precision=1)
+    s.warmstart_attach(net)
+    guess, used = s.warmstart_predict(rho, prev)
+    torch.cuda.synchronize()
+    assert torch.equal(guess, prev) and used
+    s.close()
+    net.close()
