@@ -299,9 +299,17 @@ mg_status mg_nn_conv3d_wgrad(const void* dy, int cout, const void* x1, int c1, c
  * a file (owned by the context). */
 mg_status mg_warmstart_attach(mg_ctx* ctx, mg_unet* net);
 mg_status mg_warmstart_load(mg_ctx* ctx, const char* weights_path);
+/* r = b - A phi (FP64, device arrays of the grid) for the Poisson problem of
+ * rho (C/m^3): b = rho/eps0 + boundary lifts.  Electrode cells of phi are set
+ * to their values first.  Enqueued on the context's stream. */
+mg_status mg_poisson_residual(mg_ctx* ctx, const double* rho, double* phi, double* r);
+
 /*
  * mg_warmstart_predict -- guess for the Poisson solve of rho from the
- * previous potential: the network's prediction, unless its FP64 residual
+ * previous potential.  The network is applied to the residual of the
+ * previous potential, r = b_n - A phi_prev = A (phi_n - phi_prev) (its first
+ * input channel), and phi_prev (second channel); the guess is
+ * phi_prev + U(r s_rho, phi_prev s_phi) / s_out, unless its FP64 residual
  * ||b - A phi|| is larger than that of phi_prev, in which case phi_prev is
  * used (plain multigrid judges the network).  *used_net (nullable) tells
  * which.  Synchronises the context's stream.

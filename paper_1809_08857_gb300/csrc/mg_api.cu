@@ -1210,6 +1210,28 @@ mg_status mg_warmstart_load(mg_ctx* c, const char* path) {
   return MG_OK;
 }
 
+// r = b - A phi in FP64 (natural layout) for the Poisson problem of rho, via
+// work slot 0 (b formed there); electrode cells of phi are set first.
+mg_status poisson_residual(mg_ctx* c, const double* rho, double* phi, double* r, Prob* pout) {
+  cudaStream_t s = c->stream;
+  Prob p = make_prob(c, kPoisson, 0.0, rho, nullptr, phi, 0.0, nullptr);
+  MG_TRY(get_work(c, 0, &p.w));
+  MG_TRY(prepare(p, s));
+  if (r) {
+    Scope sc(c, s, MG_KCLASS_COARSE, 0);
+    mg::launch_resid64(op64(c, 0, kPoisson), 0.0, p.b, phi, r, s);
+  }
+  MG_TRY(check_launch());
+  if (pout) *pout = p;
+  return MG_OK;
+}
+
+mg_status mg_poisson_residual(mg_ctx* c, const double* rho, double* phi, double* r) {
+  g_last_error.clear();
+  if (!c || !rho || !phi || !r) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  return poisson_residual(c, rho, phi, r, nullptr);
+}
+
 mg_status mg_warmstart_predict(mg_ctx* c, const double* rho, const double* phi_prev,
                                double* phi_guess, int* used_net) {
   g_last_error.clear();
@@ -1217,11 +1239,14 @@ mg_status mg_warmstart_predict(mg_ctx* c, const double* rho, const double* phi_p
   if (!c->net) return fail(MG_ERR_INVALID_ARG, "no warm-start network attached");
   const mg::Box b = c->lv[0].b;
   cudaStream_t s = c->stream;
-  MG_TRY(mg_unet_predict(c->net, rho, phi_prev, phi_guess, 1, b.nz, b.ny, b.nx, s));
-  // plain multigrid judges the guess: FP64 residual of both candidates
-  Prob p = make_prob(c, kPoisson, 0.0, rho, nullptr, phi_guess, 0.0, nullptr);
+  // the network sees the residual of the previous potential, r = A (phi_n - phi_prev)
+  MG_CUDA(cudaMemcpyAsync(phi_guess, phi_prev, sizeof(double) * b.n(), cudaMemcpyDeviceToDevice, s));
+  Prob p;
   MG_TRY(get_work(c, 0, &p.w));
-  MG_TRY(prepare(p, s));
+  double* r = p.w->phi_tmp;
+  MG_TRY(poisson_residual(c, rho, phi_guess, r, &p));
+  MG_TRY(mg_unet_predict(c->net, r, phi_guess, phi_guess, 1, b.nz, b.ny, b.nx, s));
+  // plain multigrid judges the guess: FP64 residual of both candidates
   MG_TRY(enqueue_ir(c, p.w, s, kPoisson, 0.0, p.b, phi_guess, nullptr, false, false, false, 0));
   MG_TRY(enqueue_ir(c, p.w, s, kPoisson, 0.0, p.b, phi_prev, nullptr, false, false, false, 1));
   MG_CUDA(cudaStreamSynchronize(s));

@@ -36,6 +36,7 @@ EXPORTS = [
     "mg_unet_train_step", "mg_unet_predict", "mg_unet_grads", "mg_unet_num_params",
     "mg_unet_get_params", "mg_unet_set_params", "mg_unet_save", "mg_unet_load", "mg_nn_conv3d",
     "mg_nn_conv3d_wgrad", "mg_warmstart_attach", "mg_warmstart_load", "mg_warmstart_predict",
+    "mg_poisson_residual",
 ]
 
 MG_PROBLEM_POISSON = 0
@@ -164,6 +165,8 @@ def load():
     lib.mg_warmstart_attach.argtypes = [P, P]
     lib.mg_warmstart_load.argtypes = [P, ctypes.c_char_p]
     lib.mg_warmstart_predict.argtypes = [P, P, P, P, ctypes.POINTER(I)]
+    lib.mg_poisson_residual.argtypes = [P, P, P, P]
+    lib.mg_poisson_residual.restype = ctypes.c_int
     for name in ("mg_unet_create", "mg_unet_set_scales", "mg_unet_get_scales",
                  "mg_unet_train_step", "mg_unet_predict", "mg_unet_grads", "mg_unet_num_params",
                  "mg_unet_get_params", "mg_unet_set_params", "mg_unet_save", "mg_unet_load",
@@ -350,6 +353,17 @@ class Solver:
                                      kap, float(tol), ctypes.byref(best), ctypes.byref(ms)))
         self.options = best
         return ({"nu1": best.nu1, "nu2": best.nu2, "inner_cycles": best.inner_cycles}, ms.value)
+
+    def poisson_residual(self, rho, phi, out=None):
+        """r = b - A phi in FP64 (electrode cells of phi are set first)."""
+        self._check_field(rho)
+        self._check_field(phi)
+        if out is None:
+            out = torch.empty_like(phi)
+        self.set_stream()
+        _check(self._lib.mg_poisson_residual(self._ctx, _ptr(rho, torch.float64),
+                                             _ptr(phi, torch.float64), _ptr(out, torch.float64)))
+        return out
 
     def warmstart_attach(self, net):
         """Use a UNet for mg_warmstart_predict (None detaches)."""

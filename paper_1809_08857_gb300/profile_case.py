@@ -1,0 +1,54 @@
+"""Small, fixed workloads for profiling single kernels under ncu.
+
+  python -m paper_1809_08857_gb300.profile_case --case solve256
+      one mixed-precision Poisson + 3 Helmholtz set at 256^3 (arrays of
+      128 MiB each, larger than the 129 MB L2), concurrency 1, no graphs, so
+      kernel launches are individually visible;
+  python -m paper_1809_08857_gb300.profile_case --case unet64
+      one U-Net training step on a batch of 2 crops of 64^3.
+"""
+import argparse
+import os
+import sys
+
+import numpy as np
+import torch
+
+from . import mg, workloads as W
+
+
+def solve256():
+    n = 256
+    h = 1.0 / n
+    rho = torch.from_numpy(W.streamer_shell(n, 0)).cuda()
+    eps = torch.from_numpy(W.dielectric_slab(n)).cuda()
+    S = torch.from_numpy(W.ionization_source(n, 0)).cuda()
+    s = mg.Solver((n, n, n), h, eps_r=eps, precision=mg.MG_PREC_MIXED, inner_cycles=3,
+                  concurrency=1, graphs=False)
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    psi = [torch.zeros_like(phi) for _ in range(3)]
+    st = s.solve_set(rho, phi, S, psi, W.helmholtz_kappas(), 1e-10)
+    torch.cuda.synchronize()
+    print("steps", [x["cycles"] for x in st])
+    s.close()
+
+
+def unet64():
+    rng = np.random.default_rng(0)
+    net = mg.UNet(seed=0)
+    shape = (2, 64, 64, 64)
+    a = [torch.from_numpy(rng.standard_normal(shape)).cuda() for _ in range(3)]
+    print("loss", net.train_step(a[0], a[1], a[2], lr=1e-4))
+    torch.cuda.synchronize()
+    net.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", choices=["solve256", "unet64"], required=True)
+    args = ap.parse_args()
+    {"solve256": solve256, "unet64": unet64}[args.case]()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -20,8 +20,9 @@ from . import mg, workloads as W
 
 def episode(n, seed, steps, z_start=0.9, z_channel=0.1, eps_slab=True, tol=1e-10, solver=None):
     """Generate one advancing-head sequence on an n^3 gap (dielectric slab,
-    phi = 0 / 1 on the bottom / top faces): yields (rho_k, phi_k) as CUDA
-    float64 tensors, phi_k solved from phi_{k-1} by the plain solver."""
+    phi = 0 / 1 on the bottom / top faces): a list of (rho_k, phi_k, r_k) as
+    CUDA float64 tensors, phi_k solved from phi_{k-1} by the plain solver and
+    r_k = b_k - A phi_{k-1} (the network's input; r_0 = b_0)."""
     rng = np.random.default_rng(seed)
     h = 1.0 / n
     radius = rng.uniform(0.015, 0.03)
@@ -32,6 +33,7 @@ def episode(n, seed, steps, z_start=0.9, z_channel=0.1, eps_slab=True, tol=1e-10
         solver = mg.Solver((n, n, n), h, eps_r=eps, precision=mg.MG_PREC_MIXED, inner_cycles=3)
     phi = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
     out = []
+    r = torch.empty_like(phi)
     for k in range(steps):
         axis = axis + rng.normal(0.0, 0.25 * h, size=2)
         z1 = z_start - k * h
@@ -40,16 +42,18 @@ def episode(n, seed, steps, z_start=0.9, z_channel=0.1, eps_slab=True, tol=1e-10
                                                     z0=z_channel, z1=z1,
                                                     axis_xy=tuple(axis))).cuda()
         phi = phi.clone()
+        r = solver.poisson_residual(rho, phi, torch.empty_like(phi))
         solver.solve_poisson(rho, phi, tol)
-        out.append((rho, phi))
+        out.append((rho, phi, r))
     if own:
         solver.close()
     return out
 
 
 def scales(episodes):
-    """Input/output scales: inverse RMS of rho, phi and of the step change."""
-    r = np.sqrt(np.mean([float((e[k][0] ** 2).mean()) for e in episodes for k in range(len(e))]))
+    """Input/output scales: inverse RMS of the residual input, of phi and of
+    the step change."""
+    r = np.sqrt(np.mean([float((e[k][2] ** 2).mean()) for e in episodes for k in range(1, len(e))]))
     p = np.sqrt(np.mean([float((e[k][1] ** 2).mean()) for e in episodes for k in range(len(e))]))
     d = np.sqrt(np.mean([float(((e[k][1] - e[k - 1][1]) ** 2).mean())
                          for e in episodes for k in range(1, len(e))]))
@@ -57,7 +61,7 @@ def scales(episodes):
 
 
 def train(net, episodes, iters, crop=32, batch=4, lr=1e-3, seed=0, log_every=0):
-    """Adam on random crops (rho_k, phi_{k-1}) -> phi_k; returns the loss history."""
+    """Adam on random crops (r_k, phi_{k-1}) -> phi_k; returns the loss history."""
     rng = np.random.default_rng(seed)
     n = episodes[0][0][0].shape[0]
     losses = []
@@ -68,7 +72,7 @@ def train(net, episodes, iters, crop=32, batch=4, lr=1e-3, seed=0, log_every=0):
             k = int(rng.integers(1, len(e)))
             o = rng.integers(0, n - crop + 1, size=3)
             sl = (slice(o[0], o[0] + crop), slice(o[1], o[1] + crop), slice(o[2], o[2] + crop))
-            rs.append(e[k][0][sl])
+            rs.append(e[k][2][sl])
             ps.append(e[k - 1][1][sl])
             ts.append(e[k][1][sl])
         rho = torch.stack(rs).contiguous()
@@ -104,7 +108,7 @@ def evaluate(net, ep, n, tol=1e-10, eps_slab=True):
         sync()
         t_plain += time.perf_counter() - t0
         t0 = time.perf_counter()
-        g = net.predict(rho, prev)
+        g = net.predict(ep[k][2], prev)
         g0 = g.clone()
         acc["steps_net"].append(s.solve_poisson(rho, g, tol)["cycles"])
         sync()

@@ -51,7 +51,7 @@ def test_trained_warm_start_gain(mg):
     # the trained network's guess is closer to the answer than phi_{n-1}
     assert res["err_net"] < res["err_plain"]
     # the held-out answer meets parity with the oracle on the last step
-    rho, phi = held[-1]
+    rho, phi, _ = held[-1]
     ref, _, _, _ = oracle.poisson((n, n, n), 1.0 / n, eps_r=W.dielectric_slab(n)).solve(
         rho.cpu().numpy() / oracle.EPS0)
     assert oracle.rel_l2(phi.cpu().numpy(), ref) <= 1e-9
