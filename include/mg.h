@@ -79,8 +79,8 @@ typedef enum { MG_PREC_FP64 = 0, MG_PREC_MIXED = 1 } mg_precision;
 
 /* Solver options.  Zero-initialised fields take the defaults shown. */
 typedef struct {
-  int nu1;          /* pre-smoothing red-black sweeps per level (2) */
-  int nu2;          /* post-smoothing sweeps (2) */
+  int nu1;          /* pre-smoothing red-black sweeps per level, >= 1 (0: default 2) */
+  int nu2;          /* post-smoothing sweeps, >= 1 (0: default 2) */
   int max_cycles;   /* cap on V-cycles (FP64) or outer refinement steps (100) */
   int precision;    /* mg_precision: FP64 V-cycles, or FP32 V-cycles inside
                        FP64 iterative refinement (MG_PREC_FP64 = 0) */

@@ -79,6 +79,8 @@ struct Level {
   // Poisson FP64 coefficients (null when eps_r == 1 everywhere)
   double* beta64 = nullptr;
   double *cx = nullptr, *cy = nullptr, *cz = nullptr, *D = nullptr;
+  // level 0 only: the same as double-floats for the refinement step
+  float2 *cxd = nullptr, *cyd = nullptr, *czd = nullptr, *Dd = nullptr;
   // FP32 split coefficients 1/(2 beta): Poisson (eps or mask), Helmholtz (mask only)
   float* bp[2] = {nullptr, nullptr};
   float* bh[2] = {nullptr, nullptr};
@@ -254,6 +256,10 @@ mg::Op64 op64(const mg_ctx* c, int l, Kind kind) {
     op.cy = L.cy;
     op.cz = L.cz;
     op.D = L.D;
+    op.cxd = L.cxd;
+    op.cyd = L.cyd;
+    op.czd = L.czd;
+    op.Dd = L.Dd;
   }
   for (int f = 0; f < 6; ++f) op.dir[f] = kind == kPoisson ? poisson_dir(c, f) : 1;
   return op;
@@ -422,20 +428,19 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
   LevelWork& Y = w->lw[l + 1];
   mg::Split32 cop = sop(c, l + 1, kind);
   {
-    const bool red_only = c->opt.nu1 > 0;
-    // u both colours, f (red only if red_only), beta both colours, coarse f and u
-    Scope sc(c, s, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE,
-             n * (4.0 + (red_only ? 2.0 : 4.0) + fb + 1.0));
-    mg::launch_resid_restrict32s(op, cop, a32, cp(X.f32), cp(X.u32), mp(Y.f32), mp(Y.u32),
-                                 red_only, s);
+    // nu1 >= 1: the pre-smoothing ends with a black half-sweep, so only red
+    // cells carry a residual.  u both colours, f red, beta both colours,
+    // coarse f and u
+    Scope sc(c, s, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE, n * (4.0 + 2.0 + fb + 1.0));
+    mg::launch_resid_restrict32s(op, cop, a32, cp(X.f32), cp(X.u32), mp(Y.f32), mp(Y.u32), s);
   }
   MG_TRY(vcycle32(c, w, kind, alpha, l + 1, true));
   {
-    const bool black_only = c->opt.nu2 > 0;
-    // fine u read + write (black only if black_only), coarse e, beta for the electrode test
-    Scope sc(c, s, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE,
-             n * ((black_only ? 4.0 : 8.0) + 0.5 + (black_only ? fb / 2 : fb)));
-    mg::launch_prolong32s(op, cop, cp(Y.u32), mp(X.u32), black_only, s);
+    // nu2 >= 1: the post-smoothing starts with a red half-sweep, so only
+    // black cells take the correction.  Fine black u read + write, coarse
+    // e, black beta for the electrode test
+    Scope sc(c, s, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE, n * (4.0 + 0.5 + fb / 2));
+    mg::launch_prolong32s(op, cop, cp(Y.u32), mp(X.u32), s);
   }
   smooth(c->opt.nu2, false);
   return check_launch();
@@ -897,6 +902,12 @@ mg_status build(mg_ctx* c, const double* eps_r, const uint8_t* mask, const doubl
       MG_TRY(c->alloc(&L.cy, n));
       MG_TRY(c->alloc(&L.cz, n));
       MG_TRY(c->alloc(&L.D, n));
+      if (l == 0) {
+        MG_TRY(c->alloc(&L.cxd, n));
+        MG_TRY(c->alloc(&L.cyd, n));
+        MG_TRY(c->alloc(&L.czd, n));
+        MG_TRY(c->alloc(&L.Dd, n));
+      }
     }
     for (int col = 0; col < 2; ++col) {
       if (eps_r || mask) MG_TRY(c->alloc(&L.bp[col], (size_t)L.ns, true));
@@ -929,6 +940,11 @@ mg_status build(mg_ctx* c, const double* eps_r, const uint8_t* mask, const doubl
   for (int l = 0; l < nlev; ++l) {
     Level& L = c->lv[l];
     if (eps_r) mg::launch_faces64(L.beta64, L.mask, L.b, L.ih2, dir, L.cx, L.cy, L.cz, L.D, s);
+    if (eps_r && l == 0) {
+      const double* src[4] = {L.cx, L.cy, L.cz, L.D};
+      float2* dst[4] = {L.cxd, L.cyd, L.czd, L.Dd};
+      for (int q = 0; q < 4; ++q) mg::launch_split_df(src[q], dst[q], L.b.n(), s);
+    }
     if (eps_r || mask) mg::launch_split_beta(L.beta64, L.mask, sop(c, l, kPoisson), mp(L.bp), s);
     if (mask) mg::launch_split_beta(nullptr, L.mask, sop(c, l, kHelmholtz), mp(L.bh), s);
   }

@@ -43,6 +43,12 @@ struct Op64 {
   const double* cy;
   const double* cz;
   const double* D;
+  // the same four level-0 arrays as double-floats (hi, lo) for the
+  // refinement step (nullable: beta = 1)
+  const float2* cxd;
+  const float2* cyd;
+  const float2* czd;
+  const float2* Dd;
   const uint8_t* mask;
   Box b;
   double ih2;
@@ -84,11 +90,15 @@ struct IrArgs {
   int W;               // packed row width of e and r
   double* partial;     // per-CTA sums of r^2
   int zchunk;          // set by the launcher
-  double dint;         // interior diagonal 6/h^2 + alpha (beta = 1), set by the launcher
-  int has_alpha;       // alpha != 0, set by the launcher
+  // set by the launcher: 1/h^2, -alpha and the beta = 1 diagonals
+  // d/h^2 + alpha (d = 0..12) as double-floats; alpha != 0
+  float2 ih2d, nalpha, diag[13];
+  int has_alpha;
 };
 
 // ---- setup ---------------------------------------------------------------
+// out = in as double-floats (hi = in rounded to FP32, lo = in - hi rounded)
+void launch_split_df(const double* in, float2* out, long long n, cudaStream_t s);
 void launch_faces64(const double* beta, const uint8_t* mask, Box b, double ih2,
                     const uint8_t dir[6], double* cx, double* cy, double* cz, double* D,
                     cudaStream_t s);
@@ -139,12 +149,11 @@ void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t
 // ---- FP32 split-storage inner V-cycle (mg_split32.cu) -----------------------
 void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
                          const float* uo, bool zero_other, bool has_mask, cudaStream_t s);
-// red_only: the pre-smoothing ended with a black half-sweep (black residuals are 0).
+// Residual of the red cells only (needs nu1 >= 1: black residuals are 0).
 void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
-                              MPtr2 fc, MPtr2 uc, bool red_only, cudaStream_t s);
-// black_only: post-smoothing starts with a red half-sweep (red cells are overwritten).
-void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, bool black_only,
-                       cudaStream_t s);
+                              MPtr2 fc, MPtr2 uc, cudaStream_t s);
+// Corrects black cells only (needs nu2 >= 1: red cells are overwritten next).
+void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s);
 void launch_resid32s(const Split32& op, float alpha, Ptr2 f, Ptr2 u, MPtr2 r, cudaStream_t s);
 void launch_dense_apply32s(const Split32& op, const double* Minv, Ptr2 r, MPtr2 u,
                            cudaStream_t s);

@@ -1,18 +1,20 @@
-// FP64 iterative-refinement step of the mixed-precision solve:
+// Iterative-refinement step of the mixed-precision solve:
 //
 //     u_new = u + e            (FP32 correction from the inner V-cycle)
-//     r     = b - A u_new      (FP64, b = rhs * scale + Dirichlet lifts)
+//     r     = b - A u_new      (b = rhs * scale + Dirichlet lifts)
 //     r32   = (float) r        (right-hand side of the next inner V-cycle)
 //     ||r||^2 partial sums per CTA
 //
 // in one pass.  The operator and lifts follow Sec. 2 items (ii)-(iii) of
 // arXiv:1809.08857 (second-order cell-centred finite volumes for Eqs. 2-3).
 //
-// On GB300 the FP64 pipe issues about 1/57 of the FP32 rate, so this kernel
-// is bounded by FP64 arithmetic, not by HBM.  It therefore forms u + e once
-// per cell: each CTA marches along z through a 32 x 8 (x, y) tile, keeping
-// three planes of u + e (with a one-cell halo) in shared memory, and every
-// stencil neighbour is read from there.
+// u, b and the operator are FP64 data, but the arithmetic of r is done in
+// double-float (pairs of FP32 numbers, 48 significant bits): on GB300 the
+// FP64 pipe issues about 1/57 of the FP32 rate, and an FP64 stencil of about
+// ten operations per cell left this pass at 20 % of the HBM bandwidth.  The
+// only FP64 instruction left per cell is u + e.  Each CTA marches along z
+// through a 32 x 16 (x, y) tile, keeping three planes of u + e (with a
+// one-cell halo) in shared memory as double-floats.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -68,29 +70,76 @@ __device__ __forceinline__ float narrow(double x) {
 
 // electrode test on the integer pipe: D < 0 marks an electrode cell
 __device__ __forceinline__ bool masked64(const Op64& op, long long c) {
-  if (op.D) return __double_as_longlong(op.D[c]) < 0;
+  if (op.Dd) return op.Dd[c].x < 0.0f;
   return op.mask != nullptr && op.mask[c] != 0;
 }
 
+// ---- double-float arithmetic ------------------------------------------------
+//
+// A double-float is an unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi): 48 significant bits, enough for a residual whose stopping
+// test sits at 1e-10 of ||b||.  Products and sums are made exact with the
+// classical error-free transformations (Dekker's product via FMA, Knuth's
+// two-sum); the _rn intrinsics keep the compiler from contracting or
+// reassociating them.
+
+// binary64 -> double-float without an FP64 instruction: hi = x truncated to
+// 24 significant bits (integer pipe), lo = the remaining 29 bits rounded to
+// FP32 (one integer -> float conversion and a power-of-two scale).  For
+// |x| < 2^-74 lo is dropped; below the FP32 normal range x flushes to 0.
+__device__ __forceinline__ float2 split_df(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const float hi = narrow(x);
+  const int se = (int)((b >> 52) & 0x7ffull) - 948;  // FP32 exponent field of 2^(ex - 1075)
+  const float scale = (se >= 1 && se <= 254) ? __uint_as_float((unsigned)se << 23) : 0.0f;
+  const float lo = __fmul_rn(__uint2float_rn((unsigned)(b & 0x1fffffffull)), scale);
+  return make_float2(hi, (b >> 63) ? -lo : lo);
+}
+
+// Running sum s + e of double-float products.  add(c, u): s + e += c * u.
+// The product's rounding error (FMA) and its cross terms, and the two-sum
+// error of s, go into e; e itself is a plain FP32 sum of terms 2^-24 below
+// the leading ones, so the total error stays near 2^-48 of the largest term.
+struct DfAcc {
+  float s, e;
+  __device__ __forceinline__ void add(float2 c, float2 u) {
+    const float p = __fmul_rn(c.x, u.x);
+    float q = fmaf(c.x, u.x, -p);
+    q = fmaf(c.x, u.y, q);
+    q = fmaf(c.y, u.x, q);
+    const float t = __fadd_rn(s, p);
+    const float v = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, v)), __fsub_rn(p, v));
+    s = t;
+    e = __fadd_rn(e, __fadd_rn(err, q));
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(s, e); }
+};
+
+// u + e at cell (i, j, k) as a double-float (0 outside the box).  The one FP64
+// instruction per cell is the add of the FP32 correction; own cells (not
+// the halo of the tile) also store it to u_out.
 template <bool HasE, bool ZeroFree>
-__device__ __forceinline__ double load_cell(const IrArgs& a, int i, int j, int k) {
-  if (i < 0 || j < 0 || k < 0 || i >= a.op.b.nx || j >= a.op.b.ny || k >= a.op.b.nz) return 0.0;
+__device__ __forceinline__ float2 load_cell(const IrArgs& a, int i, int j, int k, bool own) {
+  if (i < 0 || j < 0 || k < 0 || i >= a.op.b.nx || j >= a.op.b.ny || k >= a.op.b.nz)
+    return make_float2(0.0f, 0.0f);
   const long long c = ((long long)k * a.op.b.ny + j) * a.op.b.nx + i;
-  if (ZeroFree) return masked64(a.op, c) ? a.u_in[c] : 0.0;
+  if (ZeroFree) return masked64(a.op, c) ? split_df(a.u_in[c]) : make_float2(0.0f, 0.0f);
   double v = a.u_in[c];
   if (HasE) {
     const long long t = ((long long)k * a.op.b.ny + j) * a.W + (i >> 1);
     v += widen(((i + j + k) & 1) ? a.e[1][t] : a.e[0][t]);
   }
-  return v;
+  if (own && a.u_out) a.u_out[c] = v;
+  return split_df(v);
 }
 
 // Faces: variable-coefficient operator (face arrays); otherwise beta = 1.
-// OnTheFlyB: b = rhs * rhs_scale + Dirichlet lifts formed here; otherwise b
-// is read as given (the solver precomputes it once per solve).
+// OnTheFlyB: b = rhs * rhs_scale + Dirichlet lifts formed here (FP64);
+// otherwise b is read as given (the solver precomputes it once per solve).
 template <bool Faces, bool HasE, bool ZeroFree, bool OnTheFlyB>
-__global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
-  __shared__ double pl[3][PN];
+__global__ void __launch_bounds__(NT) k_ir_df(IrArgs a) {
+  __shared__ float2 pl[3][PN];
   __shared__ float red[NT / 32];
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -100,8 +149,7 @@ __global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
   const long long sy = nx, sz = (long long)nx * ny;
   const int i = x0 + tx, j = y0 + ty;
   const bool own = i < nx && j < ny;
-  // beta = 1: the diagonal is (in-box faces + 2 per Dirichlet face) / h^2 +
-  // alpha; interior cells use the precomputed 6/h^2 + alpha
+  // beta = 1: diagonal (in-box faces + 2 per Dirichlet face) / h^2 + alpha
   int dxy = 0;
   if (!Faces) {
     dxy += i > 0 ? 1 : (a.op.dir[0] ? 2 : 0);
@@ -109,12 +157,13 @@ __global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
     dxy += j > 0 ? 1 : (a.op.dir[2] ? 2 : 0);
     dxy += j < ny - 1 ? 1 : (a.op.dir[3] ? 2 : 0);
   }
-  const bool xy_inner = i > 0 && i < nx - 1 && j > 0 && j < ny - 1;
 
   auto load_plane = [&](int buf, int k) {
+    const bool kown = k >= z0 && k < z1;
     for (int q = threadIdx.x; q < PN; q += NT) {
       const int lx = q % PX, ly = q / PX;
-      pl[buf][q] = load_cell<HasE, ZeroFree>(a, x0 + lx - 1, y0 + ly - 1, k);
+      const bool own_cell = kown && lx >= 1 && lx <= TX && ly >= 1 && ly <= TY;
+      pl[buf][q] = load_cell<HasE, ZeroFree>(a, x0 + lx - 1, y0 + ly - 1, k, own_cell);
     }
   };
   load_plane(0, z0 - 1);
@@ -127,61 +176,60 @@ __global__ void __launch_bounds__(NT) k_ir_fused(IrArgs a) {
     if (own) {
       const long long c = ((long long)k * ny + j) * nx + i;
       const int q = (ty + 1) * PX + (tx + 1);
-      double r = 0.0;
-      const double uc = pl[b1][q];
+      float r = 0.0f;
       if (!masked64(a.op, c)) {
-        double b;
+        double bd;
         if (OnTheFlyB) {
-          b = a.rhs[c] * a.rhs_scale;
+          bd = a.rhs[c] * a.rhs_scale;
           const bool edge = i == 0 || i == nx - 1 || j == 0 || j == ny - 1 || k == 0 || k == nz - 1;
           if (a.lift && edge) {
             const double l = 2.0 * (a.beta0 ? a.beta0[c] : 1.0) * a.op.ih2;
-            if (i == 0 && a.op.dir[0]) b += l * a.bval.v[0];
-            if (i == nx - 1 && a.op.dir[1]) b += l * a.bval.v[1];
-            if (j == 0 && a.op.dir[2]) b += l * a.bval.v[2];
-            if (j == ny - 1 && a.op.dir[3]) b += l * a.bval.v[3];
-            if (k == 0 && a.op.dir[4]) b += l * a.bval.v[4];
-            if (k == nz - 1 && a.op.dir[5]) b += l * a.bval.v[5];
+            if (i == 0 && a.op.dir[0]) bd += l * a.bval.v[0];
+            if (i == nx - 1 && a.op.dir[1]) bd += l * a.bval.v[1];
+            if (j == 0 && a.op.dir[2]) bd += l * a.bval.v[2];
+            if (j == ny - 1 && a.op.dir[3]) bd += l * a.bval.v[3];
+            if (k == 0 && a.op.dir[4]) bd += l * a.bval.v[4];
+            if (k == nz - 1 && a.op.dir[5]) bd += l * a.bval.v[5];
           }
         } else {
-          b = a.rhs[c];
+          bd = a.rhs[c];
+        }
+        const float2 bb = split_df(bd);
+        DfAcc acc{bb.x, bb.y};
+        // r = b - diag u_c + sum_f w_f u_nb
+        if (!ZeroFree) {
+          const float2 uc = pl[b1][q];
+          float2 dg;
+          if (Faces) {
+            dg = a.op.Dd[c];
+            if (a.has_alpha) acc.add(a.nalpha, uc);
+          } else {
+            const int d = dxy + (k > 0 ? 1 : (a.op.dir[4] ? 2 : 0)) +
+                          (k < nz - 1 ? 1 : (a.op.dir[5] ? 2 : 0));
+            dg = a.diag[d];
+          }
+          acc.add(make_float2(-dg.x, -dg.y), uc);
         }
         if (Faces) {
-          // r = b - D u_c + sum_f w_f u_nb, as one FMA chain
-          double t = b;
-          if (!ZeroFree) t = fma(-(a.has_alpha ? a.op.D[c] + a.alpha : a.op.D[c]), uc, b);
-          if (i > 0) t = fma(a.op.cx[c], pl[b1][q - 1], t);
-          if (i < nx - 1) t = fma(a.op.cx[c + 1], pl[b1][q + 1], t);
-          if (j > 0) t = fma(a.op.cy[c], pl[b1][q - PX], t);
-          if (j < ny - 1) t = fma(a.op.cy[c + sy], pl[b1][q + PX], t);
-          if (k > 0) t = fma(a.op.cz[c], pl[b0][q], t);
-          if (k < nz - 1) t = fma(a.op.cz[c + sz], pl[b2][q], t);
-          r = t;
+          if (i > 0) acc.add(a.op.cxd[c], pl[b1][q - 1]);
+          if (i < nx - 1) acc.add(a.op.cxd[c + 1], pl[b1][q + 1]);
+          if (j > 0) acc.add(a.op.cyd[c], pl[b1][q - PX]);
+          if (j < ny - 1) acc.add(a.op.cyd[c + sy], pl[b1][q + PX]);
+          if (k > 0) acc.add(a.op.czd[c], pl[b0][q]);
+          if (k < nz - 1) acc.add(a.op.czd[c + sz], pl[b2][q]);
         } else {
-          double o = 0.0;
-          if (i > 0) o += pl[b1][q - 1];
-          if (i < nx - 1) o += pl[b1][q + 1];
-          if (j > 0) o += pl[b1][q - PX];
-          if (j < ny - 1) o += pl[b1][q + PX];
-          if (k > 0) o += pl[b0][q];
-          if (k < nz - 1) o += pl[b2][q];
-          if (ZeroFree) {
-            r = fma(a.op.ih2, o, b);
-          } else {
-            double diag = a.dint;
-            if (!(xy_inner && k > 0 && k < nz - 1)) {
-              const int d = dxy + (k > 0 ? 1 : (a.op.dir[4] ? 2 : 0)) +
-                            (k < nz - 1 ? 1 : (a.op.dir[5] ? 2 : 0));
-              diag = fma((double)d, a.op.ih2, a.alpha);
-            }
-            r = fma(a.op.ih2, o, fma(-diag, uc, b));
-          }
+          const float2 w = a.ih2d;
+          if (i > 0) acc.add(w, pl[b1][q - 1]);
+          if (i < nx - 1) acc.add(w, pl[b1][q + 1]);
+          if (j > 0) acc.add(w, pl[b1][q - PX]);
+          if (j < ny - 1) acc.add(w, pl[b1][q + PX]);
+          if (k > 0) acc.add(w, pl[b0][q]);
+          if (k < nz - 1) acc.add(w, pl[b2][q]);
         }
+        r = acc.value();
       }
-      if (a.u_out) a.u_out[c] = uc;
-      const float r32 = narrow(r);
-      if (a.r[0]) (((i + j + k) & 1) ? a.r[1] : a.r[0])[((long long)k * ny + j) * a.W + (i >> 1)] = r32;
-      ss = fmaf(r32, r32, ss);
+      if (a.r[0]) (((i + j + k) & 1) ? a.r[1] : a.r[0])[((long long)k * ny + j) * a.W + (i >> 1)] = r;
+      ss = fmaf(r, r, ss);
     }
     __syncthreads();
     const int t = b0;
@@ -223,11 +271,26 @@ int ir_partials(const Box& b) {
 
 template <bool F, bool E, bool Z, bool O>
 static void go(const IrArgs& a, dim3 g, cudaStream_t s) {
-  k_ir_fused<F, E, Z, O><<<g, NT, 0, s>>>(a);
+  k_ir_df<F, E, Z, O><<<g, NT, 0, s>>>(a);
+}
+
+// double-float of a host double
+static float2 df_host(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+// Launch constants: 1/h^2, -alpha and the beta = 1 diagonals d/h^2 + alpha
+// (d = in-box faces + 2 per Dirichlet face, 0..12) as double-floats.
+static void ir_constants(IrArgs& a) {
+  a.ih2d = df_host(a.op.ih2);
+  a.nalpha = df_host(-a.alpha);
+  for (int d = 0; d <= 12; ++d) a.diag[d] = df_host(d * a.op.ih2 + a.alpha);
+  a.has_alpha = a.alpha != 0.0;
 }
 
 static void dispatch(const IrArgs& a, dim3 g, bool zero_free, bool on_the_fly, cudaStream_t s) {
-  const bool faces = a.op.cx != nullptr;
+  const bool faces = a.op.cxd != nullptr;
   const bool has_e = a.e[0] != nullptr && !zero_free;
   if (on_the_fly) {
     if (faces) go<true, false, false, true>(a, g, s);
@@ -247,8 +310,7 @@ static void dispatch(const IrArgs& a, dim3 g, bool zero_free, bool on_the_fly, c
 void launch_ir_fused(const IrArgs& args, bool zero_free, cudaStream_t s) {
   IrArgs a = args;
   dim3 g = ir_grid(a.op.b, &a.zchunk);
-  a.dint = 6.0 * a.op.ih2 + a.alpha;
-  a.has_alpha = a.alpha != 0.0;
+  ir_constants(a);
   dispatch(a, g, zero_free, false, s);
   add_launches(1);
 }
@@ -330,8 +392,7 @@ mg_status noalloc_scratch(double** out) {
 void launch_noalloc(IrArgs a, double* scratch, int nparts, double* norm_out, cudaStream_t s) {
   a.partial = scratch;
   dim3 g = ir_grid(a.op.b, &a.zchunk);
-  a.dint = 6.0 * a.op.ih2 + a.alpha;
-  a.has_alpha = a.alpha != 0.0;
+  ir_constants(a);
   dispatch(a, g, false, true, s);
   k_noalloc_finish<<<1, NT, 0, s>>>(scratch, nparts, norm_out);
   add_launches(2);

@@ -100,6 +100,14 @@ __global__ void k_faces64(const double* beta, const uint8_t* mask, Box b, double
             : wxm * ih2 + wxp * ih2 + wym * ih2 + wyp * ih2 + wzm * ih2 + wzp * ih2;
 }
 
+__global__ void k_split_df(const double* __restrict__ in, float2* __restrict__ out, long long n) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const double v = in[c];
+  const float hi = __double2float_rn(v);
+  out[c] = make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
 // coarse cell masked iff all 8 children are; beta = mean of free children
 __global__ void k_coarsen(const double* bf, const uint8_t* mf, Box fb, double* bcoarse,
                           uint8_t* mcoarse) {
@@ -409,6 +417,11 @@ void launch_faces64(const double* beta, const uint8_t* mask, Box b, double ih2,
                     cudaStream_t s) {
   k_faces64<<<blocks_for(b.n()), kThreads, 0, s>>>(beta, mask, b, ih2, to_dir(dir), cx, cy, cz,
                                                     D);
+  add_launches(1);
+}
+
+void launch_split_df(const double* in, float2* out, long long n, cudaStream_t s) {
+  k_split_df<<<blocks_for(n), kThreads, 0, s>>>(in, out, n);
   add_launches(1);
 }
 

@@ -238,92 +238,278 @@ __device__ __forceinline__ long long spos(const Split32& op, int i, int j, int k
   return ((long long)k * op.b.ny + j) * op.W + (i >> 1);
 }
 
-// Residual of the 8 fine children of each coarse cell, averaged into the
-// coarse right-hand side; the coarse unknown is zeroed.  Children of coarse
-// cell (I,J,K) sit at packed index I of fine rows (2J+b, 2K+c).
-// RedOnly: the pre-smoothing ended with a black half-sweep, after which every
-// black cell satisfies its own equation (Gauss-Seidel), so only the four red
-// children carry a residual.
-template <bool VB, bool RedOnly>
-__global__ void __launch_bounds__(kT) k_resid_restrict(Split32 op, Split32 cop, float alpha,
-                                                       Ptr2 f, Ptr2 u, MPtr2 fc, MPtr2 uc) {
-  const int I = blockIdx.x * 32 + threadIdx.x;
+// Two adjacent packed entries of a colour array: one float2 when the packed
+// width is even (8-byte aligned pair), else two scalars (the second only if
+// it exists).
+template <bool Vec2>
+__device__ __forceinline__ float2 ld2(const float* __restrict__ a, long long t, bool has1) {
+  if (Vec2) return *reinterpret_cast<const float2*>(a + t);
+  return make_float2(a[t], has1 ? a[t + 1] : 0.0f);
+}
+
+// Residual of the fine children of each coarse cell, averaged (1/8) into the
+// coarse right-hand side; the coarse unknown is zeroed.
+// One thread per coarse packed pair P of a coarse row (J, K): the coarse
+// cells X = 2P and 2P+1 (one of each colour, packed index P) have the fine
+// children i = 4P..4P+3 in the fine rows (2J+b, 2K+c), which sit at packed
+// positions 2P, 2P+1 of both fine colours.  For the cells of colour col the
+// thread loads the other colour over the 4 x 4 window of fine rows (j, k) in
+// 2J-1..2J+2 x 2K-1..2K+2 without its corners: the x-neighbours come from
+// the four own rows, the y- and z-neighbours from the same packed positions
+// of the adjacent rows.  x-neighbours outside the pair come from the
+// neighbouring lanes (lanes 0 and 31 load them).  Block (32, 8) over (P, J),
+// blockIdx.z = K.
+// Only the red children carry a residual: the pre-smoothing (at least one
+// sweep) ended with a black half-sweep, after which every black cell
+// satisfies its own equation (Gauss-Seidel).
+template <bool VB, bool Vec2>
+__global__ void __launch_bounds__(kT, 2) k_resid_restrict(Split32 op, Split32 cop, float alpha,
+                                                          Ptr2 f, Ptr2 u, MPtr2 fc, MPtr2 uc) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x;
   const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
-  if (I >= cop.b.nx || J >= cop.b.ny) return;
-  float sum = 0.0f;
+  const int cny = cop.b.ny, cnx = cop.b.nx, cW = cop.W;
+  if (J >= cny) return;  // whole warp
+  const int Pl = blockIdx.x * 32 + lane;
+  const bool live = Pl < cW;
+  const int P = live ? Pl : cW - 1;  // idle lanes read a valid pair
+  const bool has1 = 2 * P + 1 < cnx;
+  const int nx = op.b.nx, ny = op.b.ny, nz = op.b.nz, W = op.W;
+  const float half = 0.5f;
+  float acc0 = 0.0f, acc1 = 0.0f;  // coarse X = 2P, 2P+1
+  {
+    constexpr int col = 0;  // red cells; black neighbours
+    const float* uo = u.p[1];
+    const float* bo = op.beta[1];
+    // other colour over the row window: R[jj][kk] for j = 2J-1+jj,
+    // k = 2K-1+kk (corners unused); rows outside the box are never read
+    float2 UO[4][4], BO[4][4];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
-    const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
-    const int col = (a + b + c) & 1;
-    if (RedOnly && col == 1) continue;
-    const long long t = spos(op, i, j, k);
-    if (VB && bsel(op, col)[t] < 0.0f) continue;
-    float diag, off;
-    row32<VB>(op, col, t, i, j, k, sel(u, col ^ 1), diag, off);
-    sum += sel(f, col)[t] - ((diag + alpha) * sel(u, col)[t] - off);
+    for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const bool inner_j = jj == 1 || jj == 2, inner_k = kk == 1 || kk == 2;
+        if (!inner_j && !inner_k) continue;
+        const int j = 2 * J - 1 + jj, k = 2 * K - 1 + kk;
+        const bool in = j >= 0 && j < ny && k >= 0 && k < nz;
+        const long long t = ((long long)k * ny + j) * W + 2 * P;
+        UO[jj][kk] = in ? ld2<Vec2>(uo, t, has1) : make_float2(0.0f, 0.0f);
+        BO[jj][kk] = (VB && in) ? ld2<Vec2>(bo, t, has1) : make_float2(half, half);
+      }
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int j = 2 * J + b, k = 2 * K + c;
+        const int s = col ^ ((b + c) & 1);  // own cells at i = 4P+s, 4P+2+s
+        const long long t = ((long long)k * ny + j) * W + 2 * P;
+        const float2 F = ld2<Vec2>(sel(f, col), t, has1);
+        const float2 U = ld2<Vec2>(sel(u, col), t, has1);
+        const float2 HC = VB ? ld2<Vec2>(bsel(op, col), t, has1) : make_float2(half, half);
+        const float2 ur = UO[b + 1][c + 1], br = BO[b + 1][c + 1];
+        // other colour at packed 2P-1 (s = 0) or 2P+2 (s = 1)
+        float uh = s ? __shfl_down_sync(FULL, ur.x, 1) : __shfl_up_sync(FULL, ur.y, 1);
+        float bh = VB ? (s ? __shfl_down_sync(FULL, br.x, 1) : __shfl_up_sync(FULL, br.y, 1))
+                      : half;
+        if (s == 0 && lane == 0 && P > 0) {
+          uh = uo[t - 1];
+          if (VB) bh = bo[t - 1];
+        }
+        if (s == 1 && lane == 31 && 2 * P + 2 < W) {
+          uh = uo[t + 2];
+          if (VB) bh = bo[t + 2];
+        }
+        // x-neighbour packed positions of own cell e (0, 1): 2P+e-1+s, 2P+e+s
+        const float ux[4] = {s ? ur.x : uh, s ? ur.y : ur.x, s ? uh : ur.y, 0.0f};
+        const float bx[4] = {s ? br.x : bh, s ? br.y : br.x, s ? bh : br.y, 0.0f};
+        const float2 yn[2] = {UO[b][c + 1], UO[b + 2][c + 1]};
+        const float2 yb[2] = {BO[b][c + 1], BO[b + 2][c + 1]};
+        const float2 zn[2] = {UO[b + 1][c], UO[b + 1][c + 2]};
+        const float2 zb[2] = {BO[b + 1][c], BO[b + 1][c + 2]};
+        const bool ym = j > 0, yp = j < ny - 1, zm = k > 0, zp = k < nz - 1;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int i = 4 * P + 2 * e + s;
+          const float hc = e ? HC.y : HC.x;
+          float d = 0.0f, o = 0.0f;
+          auto face = [&](float hn, float un) {
+            const float w = VB ? wface(hc, hn) : 1.0f;
+            d += w;
+            o = fmaf(w, un, o);
+          };
+          auto dface = [&](bool dir) {
+            if (dir) d += VB ? wdir(hc) : 2.0f;
+          };
+          if (i > 0) face(bx[e], ux[e]); else dface(op.dir[0]);
+          if (i < nx - 1) face(bx[e + 1], ux[e + 1]); else dface(op.dir[1]);
+          if (ym) face(e ? yb[0].y : yb[0].x, e ? yn[0].y : yn[0].x); else dface(op.dir[2]);
+          if (yp) face(e ? yb[1].y : yb[1].x, e ? yn[1].y : yn[1].x); else dface(op.dir[3]);
+          if (zm) face(e ? zb[0].y : zb[0].x, e ? zn[0].y : zn[0].x); else dface(op.dir[4]);
+          if (zp) face(e ? zb[1].y : zb[1].x, e ? zn[1].y : zn[1].x); else dface(op.dir[5]);
+          const float uc0 = e ? U.y : U.x, fc0 = e ? F.y : F.x;
+          float r = fc0 - fmaf(fmaf(d, op.ih2, alpha), uc0, -o * op.ih2);
+          if ((VB && hc < 0.0f) || (e == 1 && !has1)) r = 0.0f;
+          if (e == 0) acc0 += r; else acc1 += r;
+        }
+      }
   }
-  const int ccol = (I + J + K) & 1;
-  const long long ct = spos(cop, I, J, K);
-  sel(fc, ccol)[ct] = 0.125f * sum;
-  sel(uc, ccol)[ct] = 0.0f;
+  if (!live) return;
+  const int cpar = (J + K) & 1;  // colour of coarse X = 2P
+  const long long ct = ((long long)K * cny + J) * cW + P;
+  sel(fc, cpar)[ct] = 0.125f * acc0;
+  sel(uc, cpar)[ct] = 0.0f;
+  if (has1) {
+    sel(fc, cpar ^ 1)[ct] = 0.125f * acc1;
+    sel(uc, cpar ^ 1)[ct] = 0.0f;
+  }
 }
 
 
 // u_fine += trilinear (27, 9, 3, 1)/64 interpolation of the coarse
-// correction; electrode cells untouched.  One thread per fine x-pair
-// (2p, 2p+1): both cells sit at packed index p (one in each colour) and share
-// the coarse parent I = p, so the 8-point stencils of the pair need 12
-// coarse values.  Block (32, 8) over (p, j), blockIdx.z = k.
-// BlackOnly: post-smoothing starts with a red half-sweep, which overwrites
-// every red cell without reading it, so only black cells are corrected.
-template <bool VB, bool BlackOnly>
+// correction; electrode cells untouched.  The interpolation is separable:
+// each fine row (2J+b, 2K+c) first blends the coarse rows J, J +- 1 and
+// planes K, K +- 1 into a line L(X) (weights 3/4 and 1/4 per axis), then
+// fine cell 2X+s takes 3/4 L(X) + 1/4 L(X -+ 1).  Across a domain face the
+// coarse neighbour is the reflected cell, with sign -1 for Dirichlet (the
+// correction vanishes on the face) and +1 for Neumann.
+//
+// One thread per coarse packed pair P of a coarse row (J, K): the coarse
+// cells X = 2P and 2P+1 sit at packed index P of the two colour arrays, so
+// each of the 9 coarse rows costs one coalesced load per colour.  The thread
+// writes fine cells i = 4P..4P+3 of the four fine rows of (J, K), at packed
+// positions 2P and 2P+1 of both fine colours.  L(2P-1) and L(2P+2) come from
+// the neighbouring lanes; lanes 0 and 31 load that coarse column themselves.
+// Block (32, 8) over (P, J), blockIdx.z = K.
+// Only black cells are corrected: the post-smoothing (at least one sweep)
+// starts with a red half-sweep, which overwrites every red cell without
+// reading it.
+// Vec2: the fine packed width is even, so the pair (2P, 2P+1) is one float2.
+template <bool VB, bool Vec2>
 __global__ void __launch_bounds__(kT) k_prolong(Split32 op, Split32 cop, Ptr2 ec, MPtr2 u) {
-  const int p = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-  if (p >= op.W || j >= op.b.ny) return;
-  const long long t = ((long long)k * op.b.ny + j) * op.W + p;
-  const int c0 = (j + k) & 1;  // colour of cell 2p
-  const bool do0 = !BlackOnly || c0 == 1;
-  const bool do1 = (!BlackOnly || c0 == 0) && 2 * p + 1 < op.b.nx;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x;
+  const int P = blockIdx.x * 32 + lane;
+  const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
   const int cnx = cop.b.nx, cny = cop.b.ny, cnz = cop.b.nz, cW = cop.W;
-  // coarse x positions I-1, I, I+1 (I = p) and the two y / z rows, reflected
-  // at domain faces (sign -1 across Dirichlet faces, +1 across Neumann)
-  const int I = p, J = j >> 1, K = k >> 1;
-  const int Jn = J + ((j & 1) ? 1 : -1), Kn = K + ((k & 1) ? 1 : -1);
-  int xi[3] = {I - 1, I, I + 1};
-  float xs[3] = {1.0f, 1.0f, 1.0f};
-  if (xi[0] < 0) { xi[0] = 0; xs[0] = cop.dir[0] ? -1.0f : 1.0f; }
-  if (xi[2] >= cnx) { xi[2] = cnx - 1; xs[2] = cop.dir[1] ? -1.0f : 1.0f; }
-  int yj[2] = {J, Jn};
-  float ys = 1.0f;
-  if (Jn < 0) { yj[1] = 0; ys = cop.dir[2] ? -1.0f : 1.0f; }
-  if (Jn >= cny) { yj[1] = cny - 1; ys = cop.dir[3] ? -1.0f : 1.0f; }
-  int zk[2] = {K, Kn};
-  float zs = 1.0f;
-  if (Kn < 0) { zk[1] = 0; zs = cop.dir[4] ? -1.0f : 1.0f; }
-  if (Kn >= cnz) { zk[1] = cnz - 1; zs = cop.dir[5] ? -1.0f : 1.0f; }
-  float x0 = 0.0f, x1 = 0.0f;  // interpolants of cells 2p and 2p+1
+  if (J >= cny) return;  // whole warp
+  const bool live = P < cW;
+  const bool has1 = 2 * P + 1 < cnx;
+  // coarse rows J-1, J, J+1 and planes K-1, K, K+1 (reflected at the faces)
+  const int Jr[3] = {J > 0 ? J - 1 : J, J, J < cny - 1 ? J + 1 : J};
+  const int Kr[3] = {K > 0 ? K - 1 : K, K, K < cnz - 1 ? K + 1 : K};
+  const float wJm = 0.25f * (J > 0 ? 1.0f : (cop.dir[2] ? -1.0f : 1.0f));
+  const float wJp = 0.25f * (J < cny - 1 ? 1.0f : (cop.dir[3] ? -1.0f : 1.0f));
+  const float wKm = 0.25f * (K > 0 ? 1.0f : (cop.dir[4] ? -1.0f : 1.0f));
+  const float wKp = 0.25f * (K < cnz - 1 ? 1.0f : (cop.dir[5] ? -1.0f : 1.0f));
+  const float sXm = cop.dir[0] ? -1.0f : 1.0f, sXp = cop.dir[1] ? -1.0f : 1.0f;
+
+  // z blend of the three rows: Z[c][y] for c = 0 (towards K-1), 1 (K+1);
+  // x = 0: coarse X = 2P, x = 1: X = 2P+1
+  float Z[2][2][3];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int b = q & 1, c = q >> 1;
-    const float wyz = (b ? 0.25f * ys : 0.75f) * (c ? 0.25f * zs : 0.75f);
-    const int JJ = yj[b], KK = zk[c];
-    const long long row = ((long long)KK * cny + JJ) * cW;
-    const int par = (JJ + KK) & 1;
-    // coarse cell (X, JJ, KK) has colour (X + JJ + KK) & 1, packed X >> 1
-    const float B = sel(ec, (xi[1] + par) & 1)[row + (xi[1] >> 1)];
-    if (do0) {
-      const float A = xs[0] * sel(ec, (xi[0] + par) & 1)[row + (xi[0] >> 1)];
-      x0 = fmaf(wyz, fmaf(0.75f, B, 0.25f * A), x0);
+  for (int y = 0; y < 3; ++y) {
+    float e[3][2];
+#pragma unroll
+    for (int z = 0; z < 3; ++z) {
+      const int par = (Jr[y] + Kr[z]) & 1;  // colour of coarse X = 2P
+      const long long row = ((long long)Kr[z] * cny + Jr[y]) * cW + P;
+      e[z][0] = live ? sel(ec, par)[row] : 0.0f;
+      e[z][1] = (live && has1) ? sel(ec, par ^ 1)[row] : 0.0f;
     }
-    if (do1) {
-      const float C = xs[2] * sel(ec, (xi[2] + par) & 1)[row + (xi[2] >> 1)];
-      x1 = fmaf(wyz, fmaf(0.75f, B, 0.25f * C), x1);
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      const float m = 0.75f * e[1][x];
+      Z[0][x][y] = fmaf(wKm, e[0][x], m);
+      Z[1][x][y] = fmaf(wKp, e[2][x], m);
     }
   }
-  if (do0 && !(VB && bsel(op, c0)[t] < 0.0f)) sel(u, c0)[t] += x0;
-  if (do1 && !(VB && bsel(op, c0 ^ 1)[t] < 0.0f)) sel(u, c0 ^ 1)[t] += x1;
+  // lines L[b][c][x] of the four fine rows (2J+b, 2K+c)
+  float L[2][2][2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      const float m = 0.75f * Z[c][x][1];
+      L[0][c][x] = fmaf(wJm, Z[c][x][0], m);
+      L[1][c][x] = fmaf(wJp, Z[c][x][2], m);
+    }
+  // L at X = 2P-1 (previous lane's X = 2P+1) and X = 2P+2 (next lane's 2P)
+  float Lm[2][2], Lp[2][2];
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      Lm[b][c] = __shfl_up_sync(FULL, L[b][c][1], 1);
+      Lp[b][c] = __shfl_down_sync(FULL, L[b][c][0], 1);
+    }
+  const bool halo_m = lane == 0 && live && P > 0;
+  const bool halo_p = lane == 31 && live && 2 * P + 2 < cnx;
+  if (halo_m || halo_p) {
+    // the coarse column X = 2P-1 (colour of X = 2P flipped, packed P-1) or
+    // X = 2P+2 (colour of X = 2P, packed P+1), blended like the others
+    const int dp = halo_m ? -1 : 1;
+    const int flip = halo_m ? 1 : 0;
+    float Zh[2][3];
+#pragma unroll
+    for (int y = 0; y < 3; ++y) {
+      float e[3];
+#pragma unroll
+      for (int z = 0; z < 3; ++z) {
+        const int par = ((Jr[y] + Kr[z]) & 1) ^ flip;
+        e[z] = sel(ec, par)[((long long)Kr[z] * cny + Jr[y]) * cW + P + dp];
+      }
+      const float m = 0.75f * e[1];
+      Zh[0][y] = fmaf(wKm, e[0], m);
+      Zh[1][y] = fmaf(wKp, e[2], m);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float m = 0.75f * Zh[c][1];
+      const float h0 = fmaf(wJm, Zh[c][0], m), h1 = fmaf(wJp, Zh[c][2], m);
+      if (halo_m) { Lm[0][c] = h0; Lm[1][c] = h1; }
+      else { Lp[0][c] = h0; Lp[1][c] = h1; }
+    }
+  }
+  if (!live) return;
+  const int ny = op.b.ny, W = op.W;
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float L0 = L[b][c][0], L1 = L[b][c][1];
+      const float lm = P == 0 ? sXm * L0 : Lm[b][c];           // L(2P-1)
+      const float lx = has1 ? L1 : sXp * L0;                    // L(2P+1)
+      const float lp = 2 * P + 2 >= cnx ? sXp * L1 : Lp[b][c];  // L(2P+2)
+      const float v0 = fmaf(0.25f, lm, 0.75f * L0);  // fine i = 4P
+      const float v1 = fmaf(0.25f, lx, 0.75f * L0);  // 4P+1
+      const float v2 = fmaf(0.25f, L0, 0.75f * L1);  // 4P+2
+      const float v3 = fmaf(0.25f, lp, 0.75f * L1);  // 4P+3
+      const int pi = (b + c) & 1;  // colour of fine cell 4P in this row
+      const long long t = ((long long)(2 * K + c) * ny + (2 * J + b)) * W + 2 * P;
+      // colour pi holds cells 4P, 4P+2; colour pi^1 holds 4P+1, 4P+3
+      {
+        constexpr int col = 1;
+        const bool even = col == pi;  // black holds 4P and 4P+2
+        const float a0 = even ? v0 : v1, a1 = even ? v2 : v3;
+        float* uu = sel(u, col);
+        const float* hb = bsel(op, col);
+        if (Vec2) {
+          float2 w = *reinterpret_cast<const float2*>(uu + t);
+          if (VB) {
+            const float2 g = *reinterpret_cast<const float2*>(hb + t);
+            if (g.x >= 0.0f) w.x += a0;
+            if (g.y >= 0.0f) w.y += a1;
+          } else {
+            w.x += a0;
+            w.y += a1;
+          }
+          *reinterpret_cast<float2*>(uu + t) = w;
+        } else {
+          if (!(VB && hb[t] < 0.0f)) uu[t] += a0;
+          if (has1 && !(VB && hb[t + 1] < 0.0f)) uu[t + 1] += a1;
+        }
+      }
+    }
 }
 
 // r = f - A u at every cell of the level (electrode and padding cells: 0).
@@ -407,28 +593,23 @@ void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f
 }
 
 void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
-                              MPtr2 fc, MPtr2 uc, bool red_only, cudaStream_t s) {
-  dim3 blk(32, 8), g((cop.b.nx + 31) / 32, (cop.b.ny + 7) / 8, cop.b.nz);
-  if (op.beta[0]) {
-    if (red_only) k_resid_restrict<true, true><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
-    else k_resid_restrict<true, false><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
-  } else {
-    if (red_only) k_resid_restrict<false, true><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
-    else k_resid_restrict<false, false><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc);
-  }
+                              MPtr2 fc, MPtr2 uc, cudaStream_t s) {
+  dim3 blk(32, 8), g((cop.W + 31) / 32, (cop.b.ny + 7) / 8, cop.b.nz);
+  const bool vec2 = op.W % 2 == 0;
+#define RR(A, B) k_resid_restrict<A, B><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc)
+  if (op.beta[0]) { if (vec2) RR(true, true); else RR(true, false); }
+  else { if (vec2) RR(false, true); else RR(false, false); }
+#undef RR
   add_launches(1);
 }
 
-void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, bool black_only,
-                       cudaStream_t s) {
-  dim3 blk(32, 8), g((op.W + 31) / 32, (op.b.ny + 7) / 8, op.b.nz);
-  if (op.beta[0]) {
-    if (black_only) k_prolong<true, true><<<g, blk, 0, s>>>(op, cop, ec, u);
-    else k_prolong<true, false><<<g, blk, 0, s>>>(op, cop, ec, u);
-  } else {
-    if (black_only) k_prolong<false, true><<<g, blk, 0, s>>>(op, cop, ec, u);
-    else k_prolong<false, false><<<g, blk, 0, s>>>(op, cop, ec, u);
-  }
+void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s) {
+  dim3 blk(32, 8), g((cop.W + 31) / 32, (cop.b.ny + 7) / 8, cop.b.nz);
+  const bool vec2 = op.W % 2 == 0;
+#define PRO(A, B) k_prolong<A, B><<<g, blk, 0, s>>>(op, cop, ec, u)
+  if (op.beta[0]) { if (vec2) PRO(true, true); else PRO(true, false); }
+  else { if (vec2) PRO(false, true); else PRO(false, false); }
+#undef PRO
   add_launches(1);
 }
 

@@ -1,0 +1,153 @@
+"""One multigrid cycle on the GPU against one cycle of the oracle.
+
+A converged solve only shows that the answer is right; inside the mixed
+path the FP32 V-cycle is a preconditioner, so a wrong weight in a smoother,
+restriction or prolongation kernel would only slow convergence down.  These
+tests stop both sides after exactly one cycle from a zero guess (tol = 0,
+max_cycles = 1, one inner cycle), where the GPU iterate is the V-cycle's
+output itself:
+
+  * FP64 path: the same V(nu1, nu2) cycle as the oracle (Sec. 2's red-black
+    Gauss-Seidel, 8-child restriction, trilinear prolongation, exact coarsest
+    solve), equal to rounding;
+  * mixed path: the FP32 V-cycle applied to the FP64 residual, equal to the
+    oracle's FP64 cycle to FP32 rounding (the tolerance below; a dropped or
+    misplaced stencil weight moves the result by 1e-3 or more).
+
+Several (nu1, nu2) pairs (both >= 1: an option value of 0 selects the
+default, 2) and shapes that reach odd coarse extents (a coarse level of
+5 x 6 x 4 cells under an even one, hence odd packed widths).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_08857_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FP64_TOL = 1e-12
+FP32_TOL = 2e-5
+NUS = [(2, 2), (1, 1), (3, 1), (1, 3)]
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_08857_gb300 import build, mg as _mg
+
+    build.build()
+    _mg.load()
+    return _mg
+
+
+def cuda(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def blobs(shape, seed):
+    """Smooth random charge on a box of the given (nz, ny, nx) shape."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    z, y, x = [(np.arange(m) + 0.5) / m for m in (nz, ny, nx)]
+    rho = np.zeros(shape)
+    for _ in range(4):
+        c = rng.uniform(0.2, 0.8, 3)
+        a = rng.standard_normal()
+        rho += a * np.exp(-((z[:, None, None] - c[2]) ** 2 + (y[None, :, None] - c[1]) ** 2
+                            + (x[None, None, :] - c[0]) ** 2) / (2 * 0.08**2))
+    return rho * W.EPS0
+
+
+def one_cycle_gpu(mg, prec, shape, h, nu, rho=None, eps=None, mask=None, mask_value=None,
+                  kappa=None, S=None, bc_kind=W.GAP_BC_KIND, bc_value=W.GAP_BC_VALUE):
+    s = mg.Solver(shape, h, eps_r=cuda(eps), mask=cuda(mask), mask_value=cuda(mask_value),
+                  bc_kind=bc_kind, bc_value=bc_value, precision=prec, nu1=nu[0], nu2=nu[1],
+                  max_cycles=1, inner_cycles=1)
+    try:
+        if kappa is None:
+            u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+            st = s.solve_poisson(cuda(rho), u, 0.0, raise_on_nonconvergence=False)
+            assert st["cycles"] == 1
+            return u.cpu().numpy()
+        psi = [torch.zeros(shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+        st = s.solve_helmholtz_batch(cuda(S), psi, kappa, 0.0, raise_on_nonconvergence=False)
+        assert all(x["cycles"] == 1 for x in st)
+        return [p.cpu().numpy() for p in psi]
+    finally:
+        s.close()
+
+
+def one_cycle_oracle(prob, f, nu, u0=None):
+    u, cyc, _, _ = prob.solve(f, u0=u0, tol=0.0, max_cycles=1, nu1=nu[0], nu2=nu[1])
+    assert cyc == 1
+    return u
+
+
+def check(got, ref, prec):
+    err = oracle.rel_l2(got, ref)
+    assert err <= (FP64_TOL if prec == 0 else FP32_TOL), err
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nu", NUS)
+def test_one_cycle_poisson_slab(mg, prec, nu):
+    """Variable permittivity, gap boundary conditions, a non-cubic box whose
+    hierarchy is 32x48x40 -> 16x24x20 -> 8x12x10 -> 4x6x5 (x, y, z)."""
+    shape = (40, 48, 32)
+    h = 1.0 / 48
+    rho = blobs(shape, 3)
+    eps = W.dielectric_slab_box(shape, h, (0.0, 0.0, 0.0), z_top=0.3)
+    got = one_cycle_gpu(mg, prec, shape, h, nu, rho=rho, eps=eps)
+    p = oracle.Problem(shape, h, 0.0, eps, None, W.GAP_BC_KIND, W.GAP_BC_VALUE)
+    check(got, one_cycle_oracle(p, rho / oracle.EPS0, nu), prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nu", [(2, 2), (3, 1)])
+def test_one_cycle_odd_coarse_width(mg, prec, nu):
+    """40 x 48 x 32 (x, y, z): the coarsest level has 5 cells along x, so the
+    level above it has an odd packed width (5 per colour and row)."""
+    shape = (32, 48, 40)
+    h = 1.0 / 48
+    rho = blobs(shape, 4)
+    eps = W.dielectric_slab_box(shape, h, (0.0, 0.0, 0.0), z_top=0.25)
+    bc_kind = (0, 1, 1, 0, 0, 0)
+    bc_value = (0.2, 0.0, 0.0, -0.3, 0.0, 1.0)
+    got = one_cycle_gpu(mg, prec, shape, h, nu, rho=rho, eps=eps, bc_kind=bc_kind,
+                        bc_value=bc_value)
+    p = oracle.Problem(shape, h, 0.0, eps, None, bc_kind, bc_value)
+    check(got, one_cycle_oracle(p, rho / oracle.EPS0, nu), prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nu", [(2, 2), (1, 3)])
+def test_one_cycle_electrode(mg, prec, nu):
+    """Needle electrode at potential 1 (masked cells) in the gap."""
+    n = 32
+    h = 1.0 / n
+    mask = W.needle_mask(n, tip_z=0.6, tip_radius_cells=3.0)
+    mv = mask.astype(np.float64)
+    rho = blobs((n, n, n), 5)
+    eps = W.dielectric_slab(n)
+    got = one_cycle_gpu(mg, prec, (n, n, n), h, nu, rho=rho, eps=eps, mask=mask, mask_value=mv)
+    p = oracle.Problem((n, n, n), h, 0.0, eps, mask, W.GAP_BC_KIND, W.GAP_BC_VALUE)
+    u0 = np.where(mask != 0, mv, 0.0)
+    check(got, one_cycle_oracle(p, rho / oracle.EPS0, nu, u0=u0), prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nu", [(2, 2), (1, 1), (3, 1)])
+def test_one_cycle_helmholtz(mg, prec, nu):
+    """Constant-coefficient screened Poisson (all-Dirichlet, zero data), the
+    three photon groups of one source."""
+    shape = (32, 24, 40)
+    h = 1.0 / 40
+    S = np.abs(blobs(shape, 6)) / W.EPS0
+    kap = W.helmholtz_kappas()
+    got = one_cycle_gpu(mg, prec, shape, h, nu, kappa=kap, S=S)
+    for g, k in zip(got, kap):
+        check(g, one_cycle_oracle(oracle.helmholtz(shape, h, k), S, nu), prec)

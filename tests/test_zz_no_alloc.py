@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-NORM_RTOL = 1e-12  # the two paths run the same FP64 kernel and reduction order
+NORM_RTOL = 1e-12  # the two paths run the same kernel and reduction order
 
 
 @pytest.fixture(scope="module")
