@@ -67,30 +67,42 @@ def config(args):
     return {"workload": f"poisson_slab_shell_{args.n}^3 + 3x helmholtz_{args.n}^3 (kappa L = 10, 100, 1000)",
             "grid": [args.n] * 3, "tol": TOL, "precision": args.precision,
             "inner_cycles": args.inner_cycles, "concurrency": args.concurrency,
-            "graphs": not args.no_graphs, "smoother": "red-black Gauss-Seidel V(2,2)",
+            "graphs": not args.no_graphs, "smoother": "red-black Gauss-Seidel V(nu1, nu2)",
             "l2": "inputs larger than L2 (1 GiB per array), no flush"}
 
 
 # ---------------------------------------------------------------- CPU oracle
 
 
-def oracle_sample(inputs, n, cycles_per_problem):
-    """Time the FP64 CPU oracle on the host cores: per problem, a solve
-    capped at 0 cycles (setup, norms) and at 1 cycle; the difference is the
-    cost of one V(2,2)-cycle.  The set time is the per-cycle cost times the
-    cycles each problem needs (the V-cycle counts the GPU solver reported for
-    the same problems)."""
+def oracle_problems(n, inputs=None):
     import oracle
 
-    cores = os.cpu_count() or 1
+    if inputs is None:
+        inputs = workload(n)
     h = 1.0 / n
     probs = [(oracle.poisson((n, n, n), h, eps_r=inputs["eps"]), inputs["rho"] / oracle.EPS0)]
     probs += [(oracle.helmholtz((n, n, n), h, k), inputs["S"]) for k in KAPPAS]
+    return probs
+
+
+def oracle_sample(inputs, n, count_n=256):
+    """Time the FP64 CPU oracle on the host cores, on a bounded sample of the
+    set: per problem kind, a solve capped at 0 cycles (setup, norms) and at 1
+    cycle at n^3; the difference is the cost of one V(2,2)-cycle.  The set
+    time is that cost times the cycles the oracle itself needs to reach 1e-10
+    on the same workload, counted by full oracle solves at count_n^3 (the
+    V-cycle count of multigrid hardly depends on the grid size)."""
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    counts = []
+    for p, f in oracle_problems(count_n):
+        _, cyc, rel, _ = p.solve(f, tol=TOL, max_cycles=200)
+        counts.append(cyc)
+    probs = oracle_problems(n, inputs)
     t_set = 0.0
     per = []
-    t0 = time.perf_counter()
     for q, (p, f) in enumerate(probs):
-        if q == 0 or q == 1:  # Poisson and one Helmholtz measured; the others share the cost
+        if q <= 1:  # the Poisson and one Helmholtz problem; the others cost the same per cycle
             ta = time.perf_counter()
             p.solve(f, tol=0.0, max_cycles=0)
             tb = time.perf_counter()
@@ -98,13 +110,14 @@ def oracle_sample(inputs, n, cycles_per_problem):
             tc = time.perf_counter()
             tcyc = max((tc - tb) - (tb - ta), 1e-9)
         per.append(tcyc)
-        t_set += tcyc * cycles_per_problem[q]
+        t_set += tcyc * counts[q]
     wall = time.perf_counter() - t0
     return {"value": 1.0 / t_set, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"FP64 C oracle (OpenMP, {cores} threads) at {n}^3: one V(2,2)-cycle of the "
-                       f"Poisson and of a Helmholtz problem timed (cap 1 minus cap 0), "
-                       f"{[round(x, 2) for x in per]} s/cycle, times the V-cycle counts "
-                       f"{list(cycles_per_problem)} needed for 1e-10; {wall:.0f} s of CPU work"),
+            "sample": (f"FP64 C oracle (OpenMP, {cores} threads): one V(2,2)-cycle at {n}^3 timed "
+                       f"for the Poisson and a Helmholtz problem (cap 1 minus cap 0), "
+                       f"{[round(x, 2) for x in per]} s/cycle, times the oracle's own V-cycle "
+                       f"counts to 1e-10 {counts} (full solves at {count_n}^3); "
+                       f"{wall:.0f} s of CPU work"),
             "seconds_per_set": t_set}
 
 
@@ -191,9 +204,10 @@ KERNEL_SOURCES = {
 }
 
 
-def traffic_for(cls, launches_bytes):
-    """DRAM bytes per launch of the class from the committed ncu summary, or
-    None when there is none or the kernel source changed since."""
+def traffic_for(cls, cells):
+    """DRAM bytes per launch of the class's level-0 kernel from the committed
+    ncu summary (bytes per cell of the captured launch times the cells of
+    this grid), or None when there is none or the kernel source changed."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -203,13 +217,23 @@ def traffic_for(cls, launches_bytes):
     ent = t.get(cls)
     if not ent or ent.get("source_hash") != source_hash(KERNEL_SOURCES.get(cls, [])):
         return None
-    # scale a small-case capture to this launch size by cells processed
-    return ent["dram_bytes_per_cell"] * ent.get("cells_scale", 1.0) * launches_bytes
+    return ent["dram_bytes_per_cell"] * cells
 
 
-def roofline(prof, n, wall_ms=None):
+def classes(prof):
+    total = sum(v["ms"] for v in prof.values())
+    return ({k: round(v["ms"] / total, 4) for k, v in prof.items()} if total > 0 else {},
+            {k: round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)
+             for k, v in prof.items() if k != "coarse" and v["ms"] > 0})
+
+
+def roofline(prof_serial, prof_overlap, n):
+    """Dominant fine-level kernel class of a profiled step run one problem at
+    a time (launches do not overlap, so an event pair brackets one kernel):
+    algorithmic bytes per launch / average launch time, against the measured
+    copy bandwidth."""
     pk, src = peaks()
-    fine = {k: v for k, v in prof.items() if k != "coarse" and v["ms"] > 0}
+    fine = {k: v for k, v in prof_serial.items() if k != "coarse" and v["ms"] > 0}
     if not fine:
         return None
     dom = max(fine, key=lambda k: fine[k]["ms"])
@@ -218,16 +242,20 @@ def roofline(prof, n, wall_ms=None):
     avg_bytes = d["bytes"] / d["launches"]
     gbs = avg_bytes / (avg_ms * 1e-3) / 1e9
     peak = float(pk["hbm_gbs"])
-    total_ms = sum(v["ms"] for v in prof.values())
-    step_bytes = sum(v["bytes"] for v in fine.values())
+    share_s, gbs_s = classes(prof_serial)
+    share_o, gbs_o = classes(prof_overlap)
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(gbs / peak, 4), "traffic": traffic_for(dom, n),
+            "frac": round(gbs / peak, 4), "traffic": traffic_for(dom, n ** 3),
             "kernel": dom, "avg_launch_ms": round(avg_ms, 4),
-            "algorithmic_bytes_per_launch": avg_bytes, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
-            "class_share": {k: round(v["ms"] / total_ms, 4) for k, v in prof.items() if total_ms > 0},
-            "class_gbs": {k: round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) for k, v in fine.items()},
-            "fine_level_bytes_per_wall_s_gbs": (round(step_bytes / (wall_ms * 1e-3) / 1e9, 1)
-                                                if wall_ms else None)}
+            "algorithmic_bytes_per_launch": avg_bytes,
+            "peak_source": (f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
+                            else "fallback 6.8 TB/s"),
+            "timing": "CUDA events around every fine-level launch on its stream, in one "
+                      "profiled solve set run one problem at a time after the timed steps",
+            "class_share": share_s, "class_gbs": gbs_s,
+            "overlapped": {"note": "the same set at the timed concurrency: event pairs "
+                                   "include the kernels of other problems running meanwhile",
+                           "class_share": share_o, "class_gbs": gbs_o}}
 
 
 # ---------------------------------------------------------------- arms
@@ -238,11 +266,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     inputs = workload(args.n)
-    cyc = (14, 10, 9, 5)
     res = None
     t0 = time.perf_counter()
     for _ in range(max(1, args.steps)):
-        res = oracle_sample(inputs, args.n, cyc)
+        res = oracle_sample(inputs, args.n)
     wall = time.perf_counter() - t0
     line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / res["value"],
@@ -311,7 +338,6 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    solver.profile(True)
     l0 = mg.launch_count()
     with Clocks(local) as clk:
         barrier()
@@ -325,8 +351,6 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
     launches = mg.launch_count() - l0
-    prof = solver.profile_read(reset=True)
-    solver.profile(False)
     ms = e0.elapsed_time(e1)
     if world > 1:
         import torch.distributed as dist
@@ -371,6 +395,20 @@ def run_ours(args):
     e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * cells,
            "d2h_bytes_per_step": 4 * 8 * cells}
 
+    # kernel profile (outside the timed region): one set at the timed
+    # concurrency, then one set with the problems run one after another
+    solver.profile(True)
+    step()
+    torch.cuda.synchronize()
+    prof_overlap = solver.profile_read(reset=True)
+    conc = solver.options.concurrency
+    solver.set_options(concurrency=1)
+    step()
+    torch.cuda.synchronize()
+    prof_serial = solver.profile_read(reset=True)
+    solver.set_options(concurrency=conc)
+    solver.profile(False)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -380,9 +418,9 @@ def run_ours(args):
                            nu2=solver.options.nu2, inner_cycles=solver.options.inner_cycles),
             "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": launches, "cycles_per_problem": cycles,
-            "roofline": roofline(prof, n, ms), "kernel_profile": prof}
+            "roofline": roofline(prof_serial, prof_overlap, n), "kernel_profile": prof_serial}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res = oracle_sample(inputs, n, cycles)
+        res = oracle_sample(inputs, n)
         line["cpu_baseline"] = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:
         print(json.dumps(line), flush=True)
