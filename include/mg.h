@@ -83,7 +83,9 @@ typedef struct {
   int nu2;          /* post-smoothing sweeps, >= 1 (0: default 2) */
   int max_cycles;   /* cap on V-cycles (FP64) or outer refinement steps (100) */
   int precision;    /* mg_precision: FP64 V-cycles, or FP32 V-cycles inside
-                       FP64 iterative refinement (MG_PREC_FP64 = 0) */
+                       iterative refinement whose residual b - A u is formed
+                       from the FP64 data in double-float arithmetic (pairs
+                       of FP32, 48 significant bits) (MG_PREC_FP64 = 0) */
   int inner_cycles; /* FP32 V-cycles per refinement step in mixed mode (1) */
   int concurrency;  /* mixed mode: problems of one call solved concurrently,
                        each on a library stream with its own work arrays (4, max 4) */
@@ -97,7 +99,9 @@ typedef struct {
 typedef struct {
   int cycles;       /* V-cycles (FP64) or refinement steps (mixed) taken */
   int converged;    /* 1 if rel_resid <= tol */
-  double rel_resid; /* final ||b - A u|| / ||b||, evaluated in FP64 */
+  double rel_resid; /* final ||b - A u|| / ||b||: r in double-float (48-bit)
+                       arithmetic from FP64 data; r^2 summed per thread in
+                       FP32, across thread blocks in FP64 */
   double time_ms;   /* device time of the solve (CUDA events) */
   double hist[64];
 } mg_stats;

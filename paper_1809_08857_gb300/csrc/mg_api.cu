@@ -113,9 +113,9 @@ struct StepGraph {
   double alpha = 0;
   int ic = 0, nu1 = 0, nu2 = 0;
   bool prof = false;
-  const double* b = nullptr;
-  const double* u_in = nullptr;
-  double* u_out = nullptr;
+  const float2* b = nullptr;
+  const float2* u_in = nullptr;
+  float2* u_out = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long launches = 0;
   std::vector<ProfRec> recs;  // event pairs baked into the graph (profiling)
@@ -126,8 +126,12 @@ struct StepGraph {
 struct Work {
   cudaStream_t s = nullptr;
   std::vector<LevelWork> lw;
-  double* phi_tmp = nullptr;  // ping-pong partner of the caller's iterate
+  double* phi_tmp = nullptr;  // FP64 scratch field (warm start; allocated when needed)
   double* b64 = nullptr;      // right-hand side with lifts (allocated when needed)
+  // mixed precision: the iterate as double-floats (ping-pong) and b as
+  // double-floats (allocated on the first mixed-precision solve)
+  float2* udf[2] = {nullptr, nullptr};
+  float2* bdf = nullptr;
   double* partial = nullptr;
   double* norm_dev = nullptr;   // [2]
   double* norm_host = nullptr;  // [2], pinned
@@ -331,8 +335,7 @@ mg_status get_work(mg_ctx* c, int q, Work** out) {
         MG_TRY(c->alloc(&w->lw[l].f32[col], ns, true));
         if (l == nlev - 1) MG_TRY(c->alloc(&w->lw[l].r32[col], ns, true));
       }
-    MG_TRY(c->alloc(&w->phi_tmp, (size_t)c->lv[0].b.n()));
-    MG_TRY(c->alloc(&w->partial, (size_t)c->npartial));
+    MG_TRY(c->alloc(&w->partial, 2 * (size_t)c->npartial));
     MG_TRY(c->alloc(&w->norm_dev, 2));
     MG_CUDA(cudaMallocHost((void**)&w->norm_host, 2 * sizeof(double)));
     c->host_allocs.push_back(w->norm_host);
@@ -448,41 +451,68 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
 
 // ---- FP64 refinement step / residual norm ----------------------------------
 
-// Enqueue one fused FP64 pass on level 0 and the read-back of ||r||^2 into
-// w->norm_host[slot] (asynchronous).
-mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha,
-                     const double* b, const double* u_in, double* u_out, bool with_e,
-                     bool store_r, bool zero_free, int slot) {
+// Operands of one refinement pass: b as double-floats (bdf) or FP64 (b64,
+// then optionally written back as double-floats to bdf_out); the iterate as
+// double-floats (udf_in, with the correction e of work slot w when with_e)
+// or FP64 (u64); u + e written as double-floats to udf_out (nullable).
+// znorm (FP64 iterate only): the same pass also sums ||b||^2, the squared
+// residual of the guess that is 0 on free cells, into norm slot 0.
+struct IrIo {
+  const float2* bdf = nullptr;
+  const double* b64 = nullptr;
+  float2* bdf_out = nullptr;
+  const float2* udf_in = nullptr;
+  const double* u64 = nullptr;
+  float2* udf_out = nullptr;
+  bool with_e = false;
+  bool store_r = false;
+  bool znorm = false;
+};
+
+// Enqueue one fused refinement pass on level 0 and the read-back of ||r||^2
+// into w->norm_host[slot] (and of ||b||^2 into norm_host[0] with znorm;
+// then slot must be 1) (asynchronous).
+mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha, const IrIo& io,
+                     int slot) {
   Level& L0 = c->lv[0];
   LevelWork& X = w->lw[0];
   mg::IrArgs a{};
   a.op = op64(c, 0, kind);
   a.alpha = alpha;
-  a.rhs = b;
+  a.bdf = io.bdf;
+  a.rhs = io.b64;
   a.rhs_scale = 1.0;
   a.lift = 0;
   a.beta0 = L0.beta64;
-  a.u_in = u_in;
-  a.u_out = u_out;
-  a.e[0] = with_e ? X.u32[0] : nullptr;
-  a.e[1] = with_e ? X.u32[1] : nullptr;
-  a.r[0] = store_r ? X.f32[0] : nullptr;
-  a.r[1] = store_r ? X.f32[1] : nullptr;
+  a.bdf_out = io.bdf_out;
+  a.udf_in = io.udf_in;
+  a.u_in = io.u64;
+  a.udf_out = io.udf_out;
+  a.e[0] = io.with_e ? X.u32[0] : nullptr;
+  a.e[1] = io.with_e ? X.u32[1] : nullptr;
+  a.r[0] = io.store_r ? X.f32[0] : nullptr;
+  a.r[1] = io.store_r ? X.f32[1] : nullptr;
   a.W = L0.W;
   a.partial = w->partial;
+  a.partial_z = io.znorm ? w->partial + c->npartial : nullptr;
   const double n = (double)L0.b.n();
-  const double bytes = n * (8.0 + 8.0 + (a.op.cx ? 32.0 : (a.op.mask ? 1.0 : 0.0)) +
-                            (with_e ? 4.0 : 0.0) + (u_out ? 8.0 : 0.0) + (store_r ? 4.0 : 0.0));
+  // u and b read, face arrays (or the electrode mask), e, u + e and b
+  // written back, r
+  const double bytes = n * (8.0 + 8.0 + (a.op.cxd ? 32.0 : (a.op.mask ? 1.0 : 0.0)) +
+                            (io.with_e ? 4.0 : 0.0) + (io.udf_out ? 8.0 : 0.0) +
+                            (io.bdf_out ? 8.0 : 0.0) + (io.store_r ? 4.0 : 0.0));
   {
     Scope sc(c, s, MG_KCLASS_RESID64, bytes);
-    mg::launch_ir_fused(a, zero_free, s);
+    mg::launch_ir_fused(a, s);
   }
   {
     Scope sc(c, s, MG_KCLASS_COARSE, 0);
     mg::launch_sum_partials(w->partial, c->npartial, w->norm_dev + slot, s);
+    if (io.znorm) mg::launch_sum_partials(a.partial_z, c->npartial, w->norm_dev, s);
   }
   MG_TRY(check_launch());
-  MG_CUDA(cudaMemcpyAsync(w->norm_host + slot, w->norm_dev + slot, sizeof(double),
+  const int lo = io.znorm ? 0 : slot;
+  MG_CUDA(cudaMemcpyAsync(w->norm_host + lo, w->norm_dev + lo, sizeof(double) * (slot - lo + 1),
                           cudaMemcpyDeviceToHost, s));
   return MG_OK;
 }
@@ -499,8 +529,8 @@ struct Prob {
   mg_stats* st;
   Work* w = nullptr;
   const double* b = nullptr;  // right-hand side with lifts
-  double* cur = nullptr;
-  double* other = nullptr;
+  float2* cur = nullptr;      // double-float iterate (mixed precision)
+  float2* other = nullptr;
   int cyc = 0;
   double bnorm = 1.0, rel = 0.0;
   int phase = 0;
@@ -559,7 +589,13 @@ mg_status enqueue_step_direct(Prob& p) {
   mg_ctx* c = p.c;
   for (int q = 0; q < c->opt.inner_cycles; ++q)
     MG_TRY(vcycle32(c, p.w, p.kind, p.alpha, 0, q == 0));
-  return enqueue_ir(c, p.w, p.w->s, p.kind, p.alpha, p.b, p.cur, p.other, true, true, false, 1);
+  IrIo io;
+  io.bdf = p.w->bdf;
+  io.udf_in = p.cur;
+  io.udf_out = p.other;
+  io.with_e = true;
+  io.store_r = true;
+  return enqueue_ir(c, p.w, p.w->s, p.kind, p.alpha, io, 1);
 }
 
 // Cached graph of the step for p's current (u_in, u_out) parity.
@@ -569,7 +605,7 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
   const int ic = c->opt.inner_cycles;
   for (StepGraph& g : w->graphs)
     if (g.kind == p.kind && g.alpha == p.alpha && g.ic == ic && g.nu1 == c->opt.nu1 &&
-        g.nu2 == c->opt.nu2 && g.prof == c->prof && g.b == p.b && g.u_in == p.cur &&
+        g.nu2 == c->opt.nu2 && g.prof == c->prof && g.b == w->bdf && g.u_in == p.cur &&
         g.u_out == p.other) {
       g.stamp = ++c->clock;
       *out = &g;
@@ -595,7 +631,7 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
   g.nu1 = c->opt.nu1;
   g.nu2 = c->opt.nu2;
   g.prof = c->prof;
-  g.b = p.b;
+  g.b = w->bdf;
   g.u_in = p.cur;
   g.u_out = p.other;
   // the event pool must not need to grow inside the capture
@@ -646,9 +682,12 @@ mg_status enqueue_step(Prob& p) {
 }
 
 mg_status finish(Prob& p) {
-  if (p.cur != p.u)
-    MG_CUDA(cudaMemcpyAsync(p.u, p.cur, sizeof(double) * p.c->lv[0].b.n(),
-                            cudaMemcpyDeviceToDevice, p.w->s));
+  // the iterate back to FP64 (electrode cells keep their values); without a
+  // step the caller's guess stays as it was
+  if (p.cyc > 0) {
+    Scope sc(p.c, p.w->s, MG_KCLASS_COARSE, 0);
+    mg::launch_df_to_f64(p.cur, p.c->lv[0].mask, p.u, p.c->lv[0].b.n(), p.w->s);
+  }
   if (p.st) MG_CUDA(cudaEventRecord(p.w->t1, p.w->s));
   p.done = true;
   if (!std::isfinite(p.rel)) {
@@ -697,6 +736,12 @@ mg_status solve_mixed(std::vector<Prob>& P) {
       if (o.c == p.c) ++slot;
     }
     MG_TRY(get_work(p.c, slot, &p.w));
+    const size_t n = (size_t)p.c->lv[0].b.n();
+    if (!p.w->bdf) {
+      MG_TRY(p.c->alloc(&p.w->udf[0], n));
+      MG_TRY(p.c->alloc(&p.w->udf[1], n));
+      MG_TRY(p.c->alloc(&p.w->bdf, n));
+    }
     const double* Minv;
     MG_TRY(coarse_inverse(p.c, p.kind, p.alpha, &Minv));
     if (std::find(ctxs.begin(), ctxs.end(), p.c) == ctxs.end()) ctxs.push_back(p.c);
@@ -710,11 +755,19 @@ mg_status solve_mixed(std::vector<Prob>& P) {
       MG_CUDA(cudaEventRecord(w->t0, w->s));
     }
     MG_TRY(prepare(p, w->s));
-    p.cur = p.u;
-    p.other = w->phi_tmp;
+    p.cur = w->udf[0];
+    p.other = w->udf[1];
     // ||b|| (slot 0) and the residual of the initial guess (slot 1, r -> FP32)
-    MG_TRY(enqueue_ir(p.c, w, w->s, p.kind, p.alpha, p.b, p.u, nullptr, false, false, true, 0));
-    MG_TRY(enqueue_ir(p.c, w, w->s, p.kind, p.alpha, p.b, p.u, nullptr, false, true, false, 1));
+    // ||b|| (slot 0) and the residual of the guess (slot 1) in one pass;
+    // b and the guess become double-floats on the way
+    IrIo r0;
+    r0.b64 = p.b;
+    r0.bdf_out = w->bdf;
+    r0.u64 = p.u;
+    r0.udf_out = p.cur;
+    r0.store_r = true;
+    r0.znorm = true;
+    MG_TRY(enqueue_ir(p.c, w, w->s, p.kind, p.alpha, r0, 1));
     MG_CUDA(cudaEventRecord(w->ev, w->s));
   }
   size_t left = P.size();
@@ -762,8 +815,11 @@ mg_status solve_fp64(Prob& p) {
   }
   MG_TRY(prepare(p, s));
   auto norms = [&](bool with_b) -> mg_status {
-    if (with_b) MG_TRY(enqueue_ir(c, w, s, p.kind, p.alpha, p.b, p.u, nullptr, false, false, true, 0));
-    MG_TRY(enqueue_ir(c, w, s, p.kind, p.alpha, p.b, p.u, nullptr, false, false, false, 1));
+    IrIo io;
+    io.b64 = p.b;
+    io.u64 = p.u;
+    io.znorm = with_b;
+    MG_TRY(enqueue_ir(c, w, s, p.kind, p.alpha, io, 1));
     MG_CUDA(cudaStreamSynchronize(s));
     harvest(c);
     return MG_OK;
@@ -1259,12 +1315,17 @@ mg_status mg_warmstart_predict(mg_ctx* c, const double* rho, const double* phi_p
   MG_CUDA(cudaMemcpyAsync(phi_guess, phi_prev, sizeof(double) * b.n(), cudaMemcpyDeviceToDevice, s));
   Prob p;
   MG_TRY(get_work(c, 0, &p.w));
+  if (!p.w->phi_tmp) MG_TRY(c->alloc(&p.w->phi_tmp, (size_t)b.n()));
   double* r = p.w->phi_tmp;
   MG_TRY(poisson_residual(c, rho, phi_guess, r, &p));
   MG_TRY(mg_unet_predict(c->net, r, phi_guess, phi_guess, 1, b.nz, b.ny, b.nx, s));
   // plain multigrid judges the guess: FP64 residual of both candidates
-  MG_TRY(enqueue_ir(c, p.w, s, kPoisson, 0.0, p.b, phi_guess, nullptr, false, false, false, 0));
-  MG_TRY(enqueue_ir(c, p.w, s, kPoisson, 0.0, p.b, phi_prev, nullptr, false, false, false, 1));
+  IrIo io;
+  io.b64 = p.b;
+  io.u64 = phi_guess;
+  MG_TRY(enqueue_ir(c, p.w, s, kPoisson, 0.0, io, 0));
+  io.u64 = phi_prev;
+  MG_TRY(enqueue_ir(c, p.w, s, kPoisson, 0.0, io, 1));
   MG_CUDA(cudaStreamSynchronize(s));
   const double r_net = p.w->norm_host[0], r_prev = p.w->norm_host[1];
   const bool use = std::isfinite(r_net) && r_net <= r_prev;

@@ -74,21 +74,30 @@ struct MPtr2 {
   float* p[2];
 };
 
-// Arguments of the fused FP64 refinement step (see mg_ir.cu).
+// Arguments of the fused refinement step (see mg_ir.cu).  The right-hand
+// side comes as a double-float array (bdf), an FP64 array (rhs) or is formed
+// on the fly from rhs * rhs_scale + lifts; the iterate comes as a
+// double-float array (udf_in, plus the FP32 correction e) or as an FP64 array
+// (u_in, split on load).
 struct IrArgs {
   Op64 op;
   double alpha;
-  const double* rhs;   // b = rhs * rhs_scale + lifts
+  const float2* bdf;   // b as double-floats (used when non-null)
+  const double* rhs;   // b (lift == 0) or rhs with the lifts added here
   double rhs_scale;
   int lift;            // add Dirichlet-face lifts 2 beta_c g / h^2
   const double* beta0; // natural FP64 beta for the lifts (nullable = 1)
   Val6 bval;           // Dirichlet face values
-  const double* u_in;  // natural FP64 iterate
-  double* u_out;       // u_in + e (nullable: not written)
+  float2* bdf_out;     // b written as double-floats (nullable)
+  const float2* udf_in;  // double-float iterate (used when non-null)
+  const double* u_in;    // FP64 iterate otherwise
+  float2* udf_out;     // u + e as double-floats (nullable: not written)
   const float* e[2];   // split FP32 correction (nullable: zero)
   float* r[2];         // split FP32 residual out (nullable)
   int W;               // packed row width of e and r
   double* partial;     // per-CTA sums of r^2
+  double* partial_z;   // nullable: per-CTA sums of the squared residual of
+                       // the guess that is 0 on free cells (FP64 guess only)
   int zchunk;          // set by the launcher
   // set by the launcher: 1/h^2, -alpha and the beta = 1 diagonals
   // d/h^2 + alpha (d = 0..12) as double-floats; alpha != 0
@@ -160,9 +169,14 @@ void launch_dense_apply32s(const Split32& op, const double* Minv, Ptr2 r, MPtr2 
 void launch_split_beta(const double* beta, const uint8_t* mask, const Split32& op, MPtr2 out,
                        cudaStream_t s);
 
-// ---- fused FP64 refinement step (mg_ir.cu) ---------------------------------
-// zero_free: norm of b (free cells of u read as 0).
-void launch_ir_fused(const IrArgs& a, bool zero_free, cudaStream_t s);
+// ---- fused refinement step (mg_ir.cu) --------------------------------------
+// One pass: (u + e), r = b - A u, r -> FP32, per-CTA sums of r^2 (and of the
+// squared residual of the zero guess when a.partial_z is set).
+void launch_ir_fused(const IrArgs& a, cudaStream_t s);
+// out = hi + lo in FP64 (the final iterate of a mixed-precision solve);
+// electrode cells (mask nonzero, nullable) are left as they are
+void launch_df_to_f64(const float2* in, const uint8_t* mask, double* out, long long n,
+                      cudaStream_t s);
 int ir_partials(const Box& b);
 
 }  // namespace mg

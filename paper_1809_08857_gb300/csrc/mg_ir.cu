@@ -12,9 +12,10 @@
 // double-float (pairs of FP32 numbers, 48 significant bits): on GB300 the
 // FP64 pipe issues about 1/57 of the FP32 rate, and an FP64 stencil of about
 // ten operations per cell left this pass at 20 % of the HBM bandwidth.  The
-// only FP64 instruction left per cell is u + e.  Each CTA marches along z
-// through a 32 x 16 (x, y) tile, keeping three planes of u + e (with a
-// one-cell halo) in shared memory as double-floats.
+// iterate itself is kept as double-floats during a solve, so no FP64
+// instruction is left per cell.  Each CTA marches along z through a 32 x 16
+// (x, y) tile, keeping three planes of u + e (with a one-cell halo) in
+// shared memory as double-floats.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -68,12 +69,6 @@ __device__ __forceinline__ float narrow(double x) {
   return __uint_as_float(bits);
 }
 
-// electrode test on the integer pipe: D < 0 marks an electrode cell
-__device__ __forceinline__ bool masked64(const Op64& op, long long c) {
-  if (op.Dd) return op.Dd[c].x < 0.0f;
-  return op.mask != nullptr && op.mask[c] != 0;
-}
-
 // ---- double-float arithmetic ------------------------------------------------
 //
 // A double-float is an unevaluated sum hi + lo of two FP32 numbers with
@@ -116,39 +111,50 @@ struct DfAcc {
   __device__ __forceinline__ float value() const { return __fadd_rn(s, e); }
 };
 
-// u + e at cell (i, j, k) as a double-float (0 outside the box).  The one FP64
-// instruction per cell is the add of the FP32 correction; own cells (not
-// the halo of the tile) also store it to u_out.
-template <bool HasE, bool ZeroFree>
-__device__ __forceinline__ float2 load_cell(const IrArgs& a, int i, int j, int k, bool own) {
-  if (i < 0 || j < 0 || k < 0 || i >= a.op.b.nx || j >= a.op.b.ny || k >= a.op.b.nz)
-    return make_float2(0.0f, 0.0f);
-  const long long c = ((long long)k * a.op.b.ny + j) * a.op.b.nx + i;
-  if (ZeroFree) return masked64(a.op, c) ? split_df(a.u_in[c]) : make_float2(0.0f, 0.0f);
-  double v = a.u_in[c];
-  if (HasE) {
-    const long long t = ((long long)k * a.op.b.ny + j) * a.W + (i >> 1);
-    v += widen(((i + j + k) & 1) ? a.e[1][t] : a.e[0][t]);
-  }
-  if (own && a.u_out) a.u_out[c] = v;
-  return split_df(v);
+// a + b (double-float plus FP32) renormalised: two-sum of the leading parts,
+// then the fast two-sum of the result with the low parts.
+__device__ __forceinline__ float2 df_add(float2 a, float b) {
+  const float s = __fadd_rn(a.x, b);
+  const float v = __fsub_rn(s, a.x);
+  const float t = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b, v));
+  const float lo = __fadd_rn(t, a.y);
+  const float hi = __fadd_rn(s, lo);
+  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
 }
 
-// Faces: variable-coefficient operator (face arrays); otherwise beta = 1.
-// OnTheFlyB: b = rhs * rhs_scale + Dirichlet lifts formed here (FP64);
-// otherwise b is read as given (the solver precomputes it once per solve).
-template <bool Faces, bool HasE, bool ZeroFree, bool OnTheFlyB>
-__global__ void __launch_bounds__(NT) k_ir_df(IrArgs a) {
-  __shared__ float2 pl[3][PN];
-  __shared__ float red[NT / 32];
+// Template arguments:
+//   Faces   variable-coefficient operator (double-float face arrays);
+//           otherwise beta = 1
+//   HasE    the iterate is udf_in + e (a refinement step)
+//   U64     the iterate is the FP64 array u_in (split on load); otherwise
+//           the double-float array udf_in
+//   BIn     0: b = bdf (double-float); 1: b = rhs (FP64); 2: b = rhs *
+//           rhs_scale + Dirichlet lifts, formed here in FP64
+//   ZNorm   also the norm of the residual of the guess that is 0 on free
+//           cells and u on electrode cells (||b|| of the stopping test),
+//           into partial_z
+// Software pipeline along z with four plane buffers: while plane k is
+// computed, plane k+2 is stored to shared memory from registers and the
+// loads of plane k+3 and of the own cells' b and coefficients of plane k+1
+// are in flight; one barrier per plane.
+template <bool Faces, bool HasE, bool U64, int BIn, bool ZNorm>
+__global__ void __launch_bounds__(NT, 2) k_ir_df(IrArgs a) {
+  __shared__ float2 pl[4][PN];
+  __shared__ unsigned char mk[ZNorm ? 4 : 1][ZNorm ? PN : 1];  // electrode flags
+  __shared__ float red[2][NT / 32];
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * a.zchunk;
-  const int z1 = min(a.op.b.nz, z0 + a.zchunk);
   const int nx = a.op.b.nx, ny = a.op.b.ny, nz = a.op.b.nz;
-  const long long sy = nx, sz = (long long)nx * ny;
+  const int z1 = min(nz, z0 + a.zchunk);
+  const int W = a.W;
+  const int sy = nx;
+  const long long sz = (long long)nx * ny, szW = (long long)W * ny;
   const int i = x0 + tx, j = y0 + ty;
   const bool own = i < nx && j < ny;
+  const int ooff = j * nx + i;        // in-plane offset of the own cell
+  const int oeoff = j * W + (i >> 1);  // and of its packed (split) position
+  const bool zmask = ZNorm && a.op.mask != nullptr;
   // beta = 1: diagonal (in-box faces + 2 per Dirichlet face) / h^2 + alpha
   int dxy = 0;
   if (!Faces) {
@@ -157,32 +163,124 @@ __global__ void __launch_bounds__(NT) k_ir_df(IrArgs a) {
     dxy += j > 0 ? 1 : (a.op.dir[2] ? 2 : 0);
     dxy += j < ny - 1 ? 1 : (a.op.dir[3] ? 2 : 0);
   }
+  // the (at most two) tile cells this thread loads per plane
+  constexpr int NS = (PN + NT - 1) / NT;
+  int qoff[NS], qeoff[NS], qpar[NS];
+  bool qin[NS], qown[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int q = threadIdx.x + s * NT;
+    const int lx = q % PX, ly = q / PX;
+    const int gi = x0 + lx - 1, gj = y0 + ly - 1;
+    qin[s] = q < PN && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+    qown[s] = qin[s] && lx >= 1 && lx <= TX && ly >= 1 && ly <= TY;
+    qoff[s] = gj * nx + gi;
+    qeoff[s] = gj * W + (gi >> 1);
+    qpar[s] = (gi + gj) & 1;
+  }
 
-  auto load_plane = [&](int buf, int k) {
-    const bool kown = k >= z0 && k < z1;
-    for (int q = threadIdx.x; q < PN; q += NT) {
-      const int lx = q % PX, ly = q / PX;
-      const bool own_cell = kown && lx >= 1 && lx <= TX && ly >= 1 && ly <= TY;
-      pl[buf][q] = load_cell<HasE, ZeroFree>(a, x0 + lx - 1, y0 + ly - 1, k, own_cell);
+  // ---- tile planes: raw loads (fetch) and their use one iteration later (commit)
+  double rd[NS];         // FP64 iterate
+  float2 ru[NS];         // double-float iterate
+  float re[NS];          // correction
+  unsigned char rm[NS];  // electrode flag
+  auto fetch = [&](int k) {
+    const bool kin = k >= 0 && k < nz;
+    const long long pb = (long long)k * sz, pe = (long long)k * szW;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (!(kin && qin[s])) continue;
+      const long long c = pb + qoff[s];
+      if (zmask) rm[s] = a.op.mask[c];
+      if (U64) {
+        rd[s] = a.u_in[c];
+      } else {
+        ru[s] = a.udf_in[c];
+        if (HasE) {
+          const long long t = pe + qeoff[s];
+          re[s] = ((qpar[s] + k) & 1) ? a.e[1][t] : a.e[0][t];
+        }
+      }
     }
   };
-  load_plane(0, z0 - 1);
-  load_plane(1, z0);
-  int b0 = 0, b1 = 1, b2 = 2;
-  float ss = 0.0f;
+  auto commit = [&](int buf, int k) {
+    const bool kin = k >= 0 && k < nz, kown = k >= z0 && k < z1;
+    const long long pb = (long long)k * sz;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int q = threadIdx.x + s * NT;
+      if (NS * NT > PN && q >= PN) break;
+      float2 v = make_float2(0.0f, 0.0f);
+      unsigned char m = 0;
+      if (kin && qin[s]) {
+        if (U64) v = split_df(rd[s]);
+        else v = HasE ? df_add(ru[s], re[s]) : ru[s];
+        if (kown && qown[s] && a.udf_out) a.udf_out[pb + qoff[s]] = v;
+        if (zmask) m = rm[s];
+      }
+      pl[buf][q] = v;
+      if (ZNorm) mk[buf][q] = m;
+    }
+  };
+
+  // ---- own cell of a plane: b, electrode flag, coefficients
+  struct Cell {
+    double bd;
+    float2 bb, dg, cxm, cxp, cym, cyp, czm, czp;
+    bool m;
+  };
+  auto cell_fetch = [&](int k, Cell& C) {
+    if (!own || k >= z1) return;
+    const long long c = (long long)k * sz + ooff;
+    if (Faces) {
+      C.dg = a.op.Dd[c];
+      const float2* cx = a.op.cxd + c;
+      const float2* cy = a.op.cyd + c;
+      const float2* cz = a.op.czd + c;
+      C.cxm = cx[0];
+      if (i < nx - 1) C.cxp = cx[1];
+      C.cym = cy[0];
+      if (j < ny - 1) C.cyp = cy[sy];
+      C.czm = cz[0];
+      if (k < nz - 1) C.czp = cz[sz];
+    } else {
+      C.m = a.op.mask && a.op.mask[c];
+    }
+    if (BIn == 0) C.bb = a.bdf[c];
+    else C.bd = a.rhs[c];
+  };
+
+  fetch(z0 - 1);
+  commit(0, z0 - 1);
+  fetch(z0);
+  commit(1, z0);
+  fetch(z0 + 1);
+  commit(2, z0 + 1);
+  if (z0 + 2 <= z1) fetch(z0 + 2);
+  Cell C{}, Cn{};
+  cell_fetch(z0, C);
+  __syncthreads();
+  float ss = 0.0f, sz2 = 0.0f;
   for (int k = z0; k < z1; ++k) {
-    load_plane(b2, k + 1);
-    __syncthreads();
+    // plane p sits in buffer (p - z0 + 1) & 3
+    const int b0 = (k - z0) & 3, bm = (k - z0 + 1) & 3, bp = (k - z0 + 2) & 3;
+    if (k + 2 <= z1) commit((k - z0 + 3) & 3, k + 2);
+    if (k + 3 <= z1) fetch(k + 3);
+    cell_fetch(k + 1, Cn);
     if (own) {
-      const long long c = ((long long)k * ny + j) * nx + i;
+      const long long c = (long long)k * sz + ooff;
       const int q = (ty + 1) * PX + (tx + 1);
-      float r = 0.0f;
-      if (!masked64(a.op, c)) {
-        double bd;
-        if (OnTheFlyB) {
-          bd = a.rhs[c] * a.rhs_scale;
+      float r = 0.0f, rz = 0.0f;
+      const bool m = Faces ? C.dg.x < 0.0f : C.m;
+      float2 bb;
+      if (BIn == 0) {
+        bb = C.bb;
+      } else {
+        double bd = C.bd;
+        if (BIn == 2) {
+          bd *= a.rhs_scale;
           const bool edge = i == 0 || i == nx - 1 || j == 0 || j == ny - 1 || k == 0 || k == nz - 1;
-          if (a.lift && edge) {
+          if (a.lift && edge && !m) {
             const double l = 2.0 * (a.beta0 ? a.beta0[c] : 1.0) * a.op.ih2;
             if (i == 0 && a.op.dir[0]) bd += l * a.bval.v[0];
             if (i == nx - 1 && a.op.dir[1]) bd += l * a.bval.v[1];
@@ -191,65 +289,89 @@ __global__ void __launch_bounds__(NT) k_ir_df(IrArgs a) {
             if (k == 0 && a.op.dir[4]) bd += l * a.bval.v[4];
             if (k == nz - 1 && a.op.dir[5]) bd += l * a.bval.v[5];
           }
-        } else {
-          bd = a.rhs[c];
         }
-        const float2 bb = split_df(bd);
+        bb = split_df(bd);
+        if (a.bdf_out) a.bdf_out[c] = bb;
+      }
+      if (!m) {
         DfAcc acc{bb.x, bb.y};
+        DfAcc az{bb.x, bb.y};  // zero guess: only electrode neighbours contribute
         // r = b - diag u_c + sum_f w_f u_nb
-        if (!ZeroFree) {
-          const float2 uc = pl[b1][q];
-          float2 dg;
-          if (Faces) {
-            dg = a.op.Dd[c];
-            if (a.has_alpha) acc.add(a.nalpha, uc);
-          } else {
-            const int d = dxy + (k > 0 ? 1 : (a.op.dir[4] ? 2 : 0)) +
-                          (k < nz - 1 ? 1 : (a.op.dir[5] ? 2 : 0));
-            dg = a.diag[d];
-          }
-          acc.add(make_float2(-dg.x, -dg.y), uc);
-        }
+        const float2 uc = pl[bm][q];
+        float2 dg;
         if (Faces) {
-          if (i > 0) acc.add(a.op.cxd[c], pl[b1][q - 1]);
-          if (i < nx - 1) acc.add(a.op.cxd[c + 1], pl[b1][q + 1]);
-          if (j > 0) acc.add(a.op.cyd[c], pl[b1][q - PX]);
-          if (j < ny - 1) acc.add(a.op.cyd[c + sy], pl[b1][q + PX]);
-          if (k > 0) acc.add(a.op.czd[c], pl[b0][q]);
-          if (k < nz - 1) acc.add(a.op.czd[c + sz], pl[b2][q]);
+          dg = C.dg;
+          if (a.has_alpha) acc.add(a.nalpha, uc);
+        } else {
+          const int d = dxy + (k > 0 ? 1 : (a.op.dir[4] ? 2 : 0)) +
+                        (k < nz - 1 ? 1 : (a.op.dir[5] ? 2 : 0));
+          dg = a.diag[d];
+        }
+        acc.add(make_float2(-dg.x, -dg.y), uc);
+        auto nb = [&](bool in, float2 w, int buf, int qq) {
+          if (!in) return;
+          const float2 un = pl[buf][qq];
+          acc.add(w, un);
+          if (zmask && mk[buf][qq]) az.add(w, un);
+        };
+        if (Faces) {
+          nb(i > 0, C.cxm, bm, q - 1);
+          nb(i < nx - 1, C.cxp, bm, q + 1);
+          nb(j > 0, C.cym, bm, q - PX);
+          nb(j < ny - 1, C.cyp, bm, q + PX);
+          nb(k > 0, C.czm, b0, q);
+          nb(k < nz - 1, C.czp, bp, q);
         } else {
           const float2 w = a.ih2d;
-          if (i > 0) acc.add(w, pl[b1][q - 1]);
-          if (i < nx - 1) acc.add(w, pl[b1][q + 1]);
-          if (j > 0) acc.add(w, pl[b1][q - PX]);
-          if (j < ny - 1) acc.add(w, pl[b1][q + PX]);
-          if (k > 0) acc.add(w, pl[b0][q]);
-          if (k < nz - 1) acc.add(w, pl[b2][q]);
+          nb(i > 0, w, bm, q - 1);
+          nb(i < nx - 1, w, bm, q + 1);
+          nb(j > 0, w, bm, q - PX);
+          nb(j < ny - 1, w, bm, q + PX);
+          nb(k > 0, w, b0, q);
+          nb(k < nz - 1, w, bp, q);
         }
         r = acc.value();
+        rz = az.value();
       }
-      if (a.r[0]) (((i + j + k) & 1) ? a.r[1] : a.r[0])[((long long)k * ny + j) * a.W + (i >> 1)] = r;
+      if (a.r[0]) (((i + j + k) & 1) ? a.r[1] : a.r[0])[(long long)k * szW + oeoff] = r;
       ss = fmaf(r, r, ss);
+      if (ZNorm) sz2 = fmaf(rz, rz, sz2);
     }
+    C = Cn;
     __syncthreads();
-    const int t = b0;
-    b0 = b1;
-    b1 = b2;
-    b2 = t;
   }
-  // CTA sum of r^2 (FP32 is ample for a stopping test; the partials and the
+  // CTA sums of r^2 (FP32 is ample for a stopping test; the partials and the
   // final sum are accumulated in FP64)
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (ZNorm) sz2 += __shfl_xor_sync(0xffffffffu, sz2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = ss;
+    if (ZNorm) red[1][threadIdx.x >> 5] = sz2;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
-    double v = threadIdx.x < NT / 32 ? (double)red[threadIdx.x] : 0.0;
+    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0)
-      a.partial[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = v;
+    for (int h = 0; h < (ZNorm ? 2 : 1); ++h) {
+      double v = threadIdx.x < NT / 32 ? (double)red[h][threadIdx.x] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (threadIdx.x == 0) (h ? a.partial_z : a.partial)[cta] = v;
+    }
   }
+}
+
+// FP64 result of a double-float iterate: exact widening of both parts on
+// the integer pipe, one FP64 add.  Electrode cells keep the caller's value.
+__global__ void k_df_to_f64(const float2* __restrict__ in, const uint8_t* __restrict__ mask,
+                            double* __restrict__ out, long long n) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n || (mask && mask[c])) return;
+  const float2 v = in[c];
+  out[c] = widen(v.x) + widen(v.y);
 }
 
 }  // namespace
@@ -269,9 +391,32 @@ int ir_partials(const Box& b) {
   return (int)(g.x * g.y * g.z);
 }
 
-template <bool F, bool E, bool Z, bool O>
+template <bool F, bool E, bool U, int B, bool Z>
 static void go(const IrArgs& a, dim3 g, cudaStream_t s) {
-  k_ir_df<F, E, Z, O><<<g, NT, 0, s>>>(a);
+  k_ir_df<F, E, U, B, Z><<<g, NT, 0, s>>>(a);
+}
+
+template <bool F>
+static void dispatch_f(const IrArgs& a, dim3 g, cudaStream_t s) {
+  const int bin = a.bdf ? 0 : (a.lift || a.rhs_scale != 1.0 ? 2 : 1);
+  if (a.udf_in) {  // double-float iterate (+ correction)
+    if (a.e[0]) go<F, true, false, 0, false>(a, g, s);
+    else go<F, false, false, 0, false>(a, g, s);
+  } else if (a.partial_z) {  // FP64 guess, both norms
+    if (bin == 0) go<F, false, true, 0, true>(a, g, s);
+    else go<F, false, true, 1, true>(a, g, s);
+  } else if (bin == 0) {
+    go<F, false, true, 0, false>(a, g, s);
+  } else if (bin == 1) {
+    go<F, false, true, 1, false>(a, g, s);
+  } else {
+    go<F, false, true, 2, false>(a, g, s);
+  }
+}
+
+static void dispatch(const IrArgs& a, dim3 g, cudaStream_t s) {
+  if (a.op.cxd) dispatch_f<true>(a, g, s);
+  else dispatch_f<false>(a, g, s);
 }
 
 // double-float of a host double
@@ -289,29 +434,17 @@ static void ir_constants(IrArgs& a) {
   a.has_alpha = a.alpha != 0.0;
 }
 
-static void dispatch(const IrArgs& a, dim3 g, bool zero_free, bool on_the_fly, cudaStream_t s) {
-  const bool faces = a.op.cxd != nullptr;
-  const bool has_e = a.e[0] != nullptr && !zero_free;
-  if (on_the_fly) {
-    if (faces) go<true, false, false, true>(a, g, s);
-    else go<false, false, false, true>(a, g, s);
-  } else if (zero_free) {
-    if (faces) go<true, false, true, false>(a, g, s);
-    else go<false, false, true, false>(a, g, s);
-  } else if (has_e) {
-    if (faces) go<true, true, false, false>(a, g, s);
-    else go<false, true, false, false>(a, g, s);
-  } else {
-    if (faces) go<true, false, false, false>(a, g, s);
-    else go<false, false, false, false>(a, g, s);
-  }
-}
-
-void launch_ir_fused(const IrArgs& args, bool zero_free, cudaStream_t s) {
+void launch_ir_fused(const IrArgs& args, cudaStream_t s) {
   IrArgs a = args;
   dim3 g = ir_grid(a.op.b, &a.zchunk);
   ir_constants(a);
-  dispatch(a, g, zero_free, false, s);
+  dispatch(a, g, s);
+  add_launches(1);
+}
+
+void launch_df_to_f64(const float2* in, const uint8_t* mask, double* out, long long n,
+                      cudaStream_t s) {
+  k_df_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, mask, out, n);
   add_launches(1);
 }
 
@@ -393,7 +526,7 @@ void launch_noalloc(IrArgs a, double* scratch, int nparts, double* norm_out, cud
   a.partial = scratch;
   dim3 g = ir_grid(a.op.b, &a.zchunk);
   ir_constants(a);
-  dispatch(a, g, false, true, s);
+  dispatch(a, g, s);
   k_noalloc_finish<<<1, NT, 0, s>>>(scratch, nparts, norm_out);
   add_launches(2);
 }

@@ -472,6 +472,25 @@ __global__ void __launch_bounds__(kT) k_prolong(Split32 op, Split32 cop, Ptr2 ec
   }
   if (!live) return;
   const int ny = op.b.ny, W = op.W;
+  float* ub = u.p[1];           // black cells only
+  const float* hb = op.beta[1];
+  // the four fine rows' black pairs (and their hb) are all read before any
+  // is written, so the four read-modify-writes overlap
+  long long t[2][2];
+  float2 w[2][2], g[2][2];
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      t[b][c] = ((long long)(2 * K + c) * ny + (2 * J + b)) * W + 2 * P;
+      if (Vec2) {
+        w[b][c] = *reinterpret_cast<const float2*>(ub + t[b][c]);
+        if (VB) g[b][c] = *reinterpret_cast<const float2*>(hb + t[b][c]);
+      } else {
+        w[b][c] = make_float2(ub[t[b][c]], has1 ? ub[t[b][c] + 1] : 0.0f);
+        if (VB) g[b][c] = make_float2(hb[t[b][c]], has1 ? hb[t[b][c] + 1] : 0.0f);
+      }
+    }
 #pragma unroll
   for (int b = 0; b < 2; ++b)
 #pragma unroll
@@ -480,34 +499,19 @@ __global__ void __launch_bounds__(kT) k_prolong(Split32 op, Split32 cop, Ptr2 ec
       const float lm = P == 0 ? sXm * L0 : Lm[b][c];           // L(2P-1)
       const float lx = has1 ? L1 : sXp * L0;                    // L(2P+1)
       const float lp = 2 * P + 2 >= cnx ? sXp * L1 : Lp[b][c];  // L(2P+2)
-      const float v0 = fmaf(0.25f, lm, 0.75f * L0);  // fine i = 4P
-      const float v1 = fmaf(0.25f, lx, 0.75f * L0);  // 4P+1
-      const float v2 = fmaf(0.25f, L0, 0.75f * L1);  // 4P+2
-      const float v3 = fmaf(0.25f, lp, 0.75f * L1);  // 4P+3
-      const int pi = (b + c) & 1;  // colour of fine cell 4P in this row
-      const long long t = ((long long)(2 * K + c) * ny + (2 * J + b)) * W + 2 * P;
-      // colour pi holds cells 4P, 4P+2; colour pi^1 holds 4P+1, 4P+3
-      {
-        constexpr int col = 1;
-        const bool even = col == pi;  // black holds 4P and 4P+2
-        const float a0 = even ? v0 : v1, a1 = even ? v2 : v3;
-        float* uu = sel(u, col);
-        const float* hb = bsel(op, col);
-        if (Vec2) {
-          float2 w = *reinterpret_cast<const float2*>(uu + t);
-          if (VB) {
-            const float2 g = *reinterpret_cast<const float2*>(hb + t);
-            if (g.x >= 0.0f) w.x += a0;
-            if (g.y >= 0.0f) w.y += a1;
-          } else {
-            w.x += a0;
-            w.y += a1;
-          }
-          *reinterpret_cast<float2*>(uu + t) = w;
-        } else {
-          if (!(VB && hb[t] < 0.0f)) uu[t] += a0;
-          if (has1 && !(VB && hb[t + 1] < 0.0f)) uu[t + 1] += a1;
-        }
+      // colour pi = (b + c) & 1 holds fine cells 4P, 4P+2 of this row and
+      // colour pi^1 holds 4P+1, 4P+3
+      const bool even = ((b + c) & 1) == 1;  // black holds 4P and 4P+2
+      const float a0 = even ? fmaf(0.25f, lm, 0.75f * L0) : fmaf(0.25f, lx, 0.75f * L0);
+      const float a1 = even ? fmaf(0.25f, L0, 0.75f * L1) : fmaf(0.25f, lp, 0.75f * L1);
+      float2 v = w[b][c];
+      if (!(VB && g[b][c].x < 0.0f)) v.x += a0;
+      if (!(VB && g[b][c].y < 0.0f)) v.y += a1;
+      if (Vec2) {
+        *reinterpret_cast<float2*>(ub + t[b][c]) = v;
+      } else {
+        ub[t[b][c]] = v.x;
+        if (has1) ub[t[b][c] + 1] = v.y;
       }
     }
 }
