@@ -145,6 +145,24 @@ mg_status mg_solve_poisson(mg_ctx* ctx, const double* rho, double* phi, double t
                            mg_stats* stats);
 
 /*
+ * mg_solve_screened -- solve alpha u - div(beta grad u) = f with the
+ * context's cell coefficient beta (the eps_r array given to mg_create, 1
+ * where it was NULL), its electrode cells (u held at mask_value) and its
+ * boundary conditions (Dirichlet values lifted into b, Neumann homogeneous),
+ * discretised like Eq. 2 (Sec. 2 items (ii)-(iii)).  One factor
+ * (I - mu L) n = g of the semi-implicit diffusion advance of Sec. 2.2 is
+ * this problem with alpha = 1/mu, f = g/mu and beta the diffusion
+ * coefficient; the TGA step of that section takes two of them.
+ *   alpha  >= 0; with alpha = 0 the problem needs a Dirichlet face or an
+ *          electrode cell to be nonsingular.
+ *   f      device, nx*ny*nz FP64 right-hand side.
+ *   u      device, nx*ny*nz FP64; in: guess, out: solution.
+ *   tol, stats  as in mg_solve_poisson.
+ */
+mg_status mg_solve_screened(mg_ctx* ctx, double alpha, const double* f, double* u, double tol,
+                            mg_stats* stats);
+
+/*
  * mg_solve_helmholtz_batch -- the three radiative-transfer solves of Eq. 3 in
  * Helmholtz form, (kappa_j^2 - lap) Psi_j = S for j = 0, 1, 2, with Psi = 0 on
  * every domain face and on electrode cells.  The paper's form
@@ -173,6 +191,27 @@ mg_status mg_solve_set(mg_ctx* ctx, const double* rho, double* phi, const double
                        double* const psi[3], const double kappa[3], double tol,
                        mg_stats stats[4]);
 
+/*
+ * mg_efield -- the electric field E = -grad phi at cell centres and the
+ * dielectric relaxation time Delta t_E = eps0 |E| / |J| (the time scale of
+ * Sec. 1 that sets the coarse step of the scheme, Sec. 3), minimised over
+ * the free cells.
+ *   phi  device, nx*ny*nz FP64 potential (electrode cells at their values,
+ *        as mg_solve_poisson leaves them).
+ *   J    device, 3*nx*ny*nz FP64 current density (A/m^2): the x, y and z
+ *        components one after the other, each x fastest; NULL if dt is NULL.
+ *   E    device, 3*nx*ny*nz FP64 output in the same layout (V per unit of h),
+ *        or NULL.  Centred differences (phi(c-1) - phi(c+1)) / (2h) per axis;
+ *        outside the box the face ghost of the context's bc (Dirichlet
+ *        2g - phi_c, Neumann phi_c); a masked neighbour contributes its
+ *        electrode value; electrode cells get E = 0.
+ *   dt   host, receives min eps0 |E| / |J| in seconds over free cells with
+ *        |J| > 0 (+inf if there is none), formed in FP32 (a time step needs
+ *        no more); NULL to skip.  The call then synchronises the stream.
+ * Enqueued on the context's stream.
+ */
+mg_status mg_efield(mg_ctx* ctx, const double* phi, const double* J, double* E, double* dt);
+
 /* ---- batches of problems and refined sub-boxes -----------------------------
  *
  * Packed Dirichlet face data of an nx*ny*nz box: faces -x, +x (ny*nz values
@@ -182,18 +221,25 @@ mg_status mg_solve_set(mg_ctx* ctx, const double* rho, double* phi, const double
  */
 long long mg_face_count(int nx, int ny, int nz);
 
-typedef enum { MG_PROBLEM_POISSON = 0, MG_PROBLEM_HELMHOLTZ = 1 } mg_problem_kind;
+typedef enum {
+  MG_PROBLEM_POISSON = 0,   /* Eq. 2 on the ctx's coefficients and bc */
+  MG_PROBLEM_HELMHOLTZ = 1, /* Eq. 3, one group (kappa) */
+  MG_PROBLEM_SCREENED = 2   /* mg_solve_screened (alpha) */
+} mg_problem_kind;
 
 typedef struct {
   mg_ctx* ctx;          /* grid, coefficients and work arrays of this problem */
   int kind;             /* mg_problem_kind */
   double kappa;         /* Helmholtz only: inverse absorption length (> 0) */
-  const double* rhs;    /* device: rho (Poisson, C/m^3) or S (Helmholtz) */
+  const double* rhs;    /* device: rho (Poisson, C/m^3), S (Helmholtz) or f
+                           (screened) */
   const double* faces;  /* device packed Dirichlet face data (values on the
-                           Dirichlet faces of the Poisson bc; every face for
-                           Helmholtz), or NULL: the ctx's bc values (Poisson),
-                           zero (Helmholtz) */
+                           Dirichlet faces of the ctx's bc for Poisson and
+                           screened; every face for Helmholtz), or NULL: the
+                           ctx's bc values (Poisson, screened), zero
+                           (Helmholtz) */
   double* u;            /* device in/out iterate; distinct for every problem */
+  double alpha;         /* MG_PROBLEM_SCREENED only: alpha >= 0 */
 } mg_problem;
 
 /*

@@ -156,6 +156,8 @@ struct mg_ctx {
   std::vector<void*> allocs;
   std::vector<void*> host_allocs;
   unsigned long long clock = 0;
+  float* efield_partial = nullptr;  // mg_efield scratch (allocated on first use)
+  double* efield_dt = nullptr;
   mg_unet* net = nullptr;  // warm-start network
   bool own_net = false;
   // instrumentation
@@ -528,6 +530,7 @@ struct Prob {
   double tol;
   mg_stats* st;
   Work* w = nullptr;
+  double rhs_scale = 1.0;     // operator of kind Poisson: b = rhs * rhs_scale + lifts
   const double* b = nullptr;  // right-hand side with lifts
   float2* cur = nullptr;      // double-float iterate (mixed precision)
   float2* other = nullptr;
@@ -539,12 +542,16 @@ struct Prob {
   const StepGraph* g = nullptr;
 };
 
+// kind Poisson with alpha = 0 is Eq. 2 (b = rho / eps0 + lifts); with
+// rhs_scale = 1 and any alpha >= 0 it is the screened variable-coefficient
+// problem alpha u - div(beta grad u) = f of mg_solve_screened.
 Prob make_prob(mg_ctx* c, Kind kind, double alpha, const double* rhs, const double* faces,
-               double* u, double tol, mg_stats* st) {
+               double* u, double tol, mg_stats* st, double rhs_scale = 1.0 / kEps0) {
   Prob p;
   p.c = c;
   p.kind = kind;
   p.alpha = alpha;
+  p.rhs_scale = kind == kPoisson ? rhs_scale : 1.0;
   p.rhs = rhs;
   p.faces = faces;
   p.u = u;
@@ -554,7 +561,8 @@ Prob make_prob(mg_ctx* c, Kind kind, double alpha, const double* rhs, const doub
 }
 
 // Electrode values into u and the right-hand side with lifts, on stream s:
-// Poisson b = rho/eps0 + lifts; Helmholtz b = S (+ lifts of face data).
+// Poisson b = rho/eps0 + lifts (screened: f + lifts); Helmholtz b = S (+
+// lifts of face data).
 mg_status prepare(Prob& p, cudaStream_t s) {
   mg_ctx* c = p.c;
   Level& L0 = c->lv[0];
@@ -573,7 +581,7 @@ mg_status prepare(Prob& p, cudaStream_t s) {
   {
     Scope sc(c, s, MG_KCLASS_COARSE, 0);
     if (p.kind == kPoisson)
-      mg::launch_rhs64(p.rhs, 1.0 / kEps0, L0.beta64, L0.mask, L0.b, L0.ih2, dir, c->bc.value,
+      mg::launch_rhs64(p.rhs, p.rhs_scale, L0.beta64, L0.mask, L0.b, L0.ih2, dir, c->bc.value,
                        p.faces, p.w->b64, s);
     else
       mg::launch_rhs64(p.rhs, 1.0, nullptr, L0.mask, L0.b, L0.ih2, dir, zero, p.faces, p.w->b64,
@@ -1107,6 +1115,39 @@ mg_status mg_solve_poisson(mg_ctx* c, const double* rho, double* phi, double tol
   return solve(P);
 }
 
+mg_status mg_efield(mg_ctx* c, const double* phi, const double* J, double* E, double* dt) {
+  g_last_error.clear();
+  if (!c || !phi) return fail(MG_ERR_INVALID_ARG, "NULL ctx or phi");
+  if (dt && !J) return fail(MG_ERR_INVALID_ARG, "dt needs J");
+  const Level& L0 = c->lv[0];
+  if (!c->efield_partial) {
+    MG_TRY(c->alloc(&c->efield_partial, (size_t)mg::efield_partials(L0.b)));
+    MG_TRY(c->alloc(&c->efield_dt, 1));
+  }
+  uint8_t dir[6];
+  for (int f = 0; f < 6; ++f) dir[f] = poisson_dir(c, f);
+  mg::launch_efield(phi, L0.mask, L0.b, L0.h, dir, c->bc.value, J, E, kEps0, c->efield_partial,
+                    dt ? c->efield_dt : nullptr, c->stream);
+  MG_TRY(check_launch());
+  if (dt) {
+    MG_CUDA(cudaMemcpyAsync(dt, c->efield_dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return MG_OK;
+}
+
+mg_status mg_solve_screened(mg_ctx* c, double alpha, const double* f, double* u, double tol,
+                            mg_stats* stats) {
+  g_last_error.clear();
+  MG_TRY(check_ctx_tol(c, tol));
+  if (!f || !u) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  if (!(alpha >= 0.0) || !std::isfinite(alpha))
+    return fail(MG_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+  std::vector<Prob> P;
+  P.push_back(make_prob(c, kPoisson, alpha, f, nullptr, u, tol, stats, 1.0));
+  return solve(P);
+}
+
 mg_status mg_solve_helmholtz_batch(mg_ctx* c, const double* S, double* const psi[3],
                                    const double kappa[3], double tol, mg_stats stats[3]) {
   g_last_error.clear();
@@ -1154,6 +1195,11 @@ mg_status mg_solve_batch(const mg_problem* probs, int nprob, double tol, mg_stat
         return fail(MG_ERR_INVALID_ARG, "kappa must be finite and > 0");
       P.push_back(make_prob(pr.ctx, kHelmholtz, pr.kappa * pr.kappa, pr.rhs, pr.faces, pr.u, tol,
                             stats ? &stats[q] : nullptr));
+    } else if (pr.kind == MG_PROBLEM_SCREENED) {
+      if (!(pr.alpha >= 0.0) || !std::isfinite(pr.alpha))
+        return fail(MG_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+      P.push_back(make_prob(pr.ctx, kPoisson, pr.alpha, pr.rhs, pr.faces, pr.u, tol,
+                            stats ? &stats[q] : nullptr, 1.0));
     } else {
       return fail(MG_ERR_INVALID_ARG, "unknown problem kind");
     }

@@ -36,11 +36,14 @@ EXPORTS = [
     "mg_unet_train_step", "mg_unet_predict", "mg_unet_grads", "mg_unet_num_params",
     "mg_unet_get_params", "mg_unet_set_params", "mg_unet_save", "mg_unet_load", "mg_nn_conv3d",
     "mg_nn_conv3d_wgrad", "mg_warmstart_attach", "mg_warmstart_load", "mg_warmstart_predict",
-    "mg_poisson_residual",
+    "mg_poisson_residual", "mg_solve_screened", "mg_efield",
 ]
 
 MG_PROBLEM_POISSON = 0
 MG_PROBLEM_HELMHOLTZ = 1
+MG_PROBLEM_SCREENED = 2
+_KINDS = {"poisson": MG_PROBLEM_POISSON, "helmholtz": MG_PROBLEM_HELMHOLTZ,
+          "screened": MG_PROBLEM_SCREENED}
 
 KCLASSES = ["smooth", "restrict", "prolong", "resid64", "coarse"]
 
@@ -75,7 +78,8 @@ class Stats(ctypes.Structure):
 
 class Problem(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("kind", ctypes.c_int), ("kappa", ctypes.c_double),
-                ("rhs", ctypes.c_void_p), ("faces", ctypes.c_void_p), ("u", ctypes.c_void_p)]
+                ("rhs", ctypes.c_void_p), ("faces", ctypes.c_void_p), ("u", ctypes.c_void_p),
+                ("alpha", ctypes.c_double)]
 
 
 class KProf(ctypes.Structure):
@@ -107,6 +111,11 @@ def load():
     lib.mg_create.restype = ctypes.c_int
     lib.mg_solve_poisson.argtypes = [P, P, P, ctypes.c_double, ctypes.POINTER(Stats)]
     lib.mg_solve_poisson.restype = ctypes.c_int
+    lib.mg_solve_screened.argtypes = [P, ctypes.c_double, P, P, ctypes.c_double,
+                                      ctypes.POINTER(Stats)]
+    lib.mg_solve_screened.restype = ctypes.c_int
+    lib.mg_efield.argtypes = [P, P, P, P, ctypes.POINTER(ctypes.c_double)]
+    lib.mg_efield.restype = ctypes.c_int
     lib.mg_solve_helmholtz_batch.argtypes = [P, P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_double),
                                              ctypes.c_double, ctypes.POINTER(Stats)]
     lib.mg_solve_helmholtz_batch.restype = ctypes.c_int
@@ -235,8 +244,9 @@ def face_count(shape):
 
 def solve_batch(problems, tol=1e-10, raise_on_nonconvergence=True):
     """Solve a list of problems, possibly on different Solvers (grids):
-    each item is a dict with keys solver, kind ("poisson"/"helmholtz"), rhs,
-    u, and optionally kappa and faces (packed Dirichlet data, CUDA float64)."""
+    each item is a dict with keys solver, kind ("poisson", "helmholtz" or
+    "screened"), rhs, u, and optionally kappa (helmholtz), alpha (screened)
+    and faces (packed Dirichlet data, CUDA float64)."""
     lib = load()
     arr = (Problem * len(problems))()
     for q, pr in enumerate(problems):
@@ -247,11 +257,10 @@ def solve_batch(problems, tol=1e-10, raise_on_nonconvergence=True):
         faces = pr.get("faces")
         if faces is not None and faces.numel() != face_count(sv.shape):
             raise ValueError("faces has the wrong length")
-        arr[q] = Problem(sv._ctx.value, MG_PROBLEM_POISSON if pr["kind"] == "poisson"
-                         else MG_PROBLEM_HELMHOLTZ, float(pr.get("kappa", 0.0)),
+        arr[q] = Problem(sv._ctx.value, _KINDS[pr["kind"]], float(pr.get("kappa", 0.0)),
                          _ptr(pr["rhs"], torch.float64).value,
                          None if faces is None else _ptr(faces, torch.float64).value,
-                         _ptr(pr["u"], torch.float64).value)
+                         _ptr(pr["u"], torch.float64).value, float(pr.get("alpha", 0.0)))
     st = (Stats * max(1, len(problems)))()
     status = lib.mg_solve_batch(arr, len(problems), float(tol), st)
     _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
@@ -410,6 +419,36 @@ class Solver:
         st = Stats()
         status = self._lib.mg_solve_poisson(self._ctx, _ptr(rho, torch.float64),
                                             _ptr(phi, torch.float64), float(tol), ctypes.byref(st))
+        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        d = st.as_dict()
+        d["status"] = status
+        return d
+
+    def efield(self, phi, J=None, E=None):
+        """E = -grad phi at cell centres into E (CUDA float64 (3, nz, ny, nx),
+        optional) and, with J (same layout), the relaxation time
+        min eps0 |E| / |J| over free cells (mg_efield); returns it or None."""
+        self._check_field(phi)
+        for t in (J, E):
+            if t is not None and (tuple(t.shape) != (3,) + self.shape or not t.is_contiguous()):
+                raise ValueError("J and E must be contiguous (3, nz, ny, nx)")
+        self.set_stream()
+        dt = ctypes.c_double()
+        _check(self._lib.mg_efield(self._ctx, _ptr(phi, torch.float64), _ptr(J, torch.float64),
+                                   _ptr(E, torch.float64),
+                                   ctypes.byref(dt) if J is not None else None))
+        return dt.value if J is not None else None
+
+    def solve_screened(self, alpha, f, u, tol=1e-10, raise_on_nonconvergence=True):
+        """alpha u - div(beta grad u) = f in place on u, beta = this Solver's
+        eps_r (mg_solve_screened)."""
+        self._check_field(f)
+        self._check_field(u)
+        self.set_stream()
+        st = Stats()
+        status = self._lib.mg_solve_screened(self._ctx, ctypes.c_double(float(alpha)),
+                                             _ptr(f, torch.float64), _ptr(u, torch.float64),
+                                             ctypes.c_double(float(tol)), ctypes.byref(st))
         _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
         d = st.as_dict()
         d["status"] = status

@@ -63,11 +63,17 @@ def blobs(shape, seed):
 
 
 def one_cycle_gpu(mg, prec, shape, h, nu, rho=None, eps=None, mask=None, mask_value=None,
-                  kappa=None, S=None, bc_kind=W.GAP_BC_KIND, bc_value=W.GAP_BC_VALUE):
+                  kappa=None, S=None, bc_kind=W.GAP_BC_KIND, bc_value=W.GAP_BC_VALUE,
+                  alpha=None):
     s = mg.Solver(shape, h, eps_r=cuda(eps), mask=cuda(mask), mask_value=cuda(mask_value),
                   bc_kind=bc_kind, bc_value=bc_value, precision=prec, nu1=nu[0], nu2=nu[1],
                   max_cycles=1, inner_cycles=1)
     try:
+        if alpha is not None:
+            u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+            st = s.solve_screened(alpha, cuda(rho), u, 0.0, raise_on_nonconvergence=False)
+            assert st["cycles"] == 1
+            return u.cpu().numpy()
         if kappa is None:
             u = torch.zeros(shape, dtype=torch.float64, device="cuda")
             st = s.solve_poisson(cuda(rho), u, 0.0, raise_on_nonconvergence=False)
@@ -151,3 +157,18 @@ def test_one_cycle_helmholtz(mg, prec, nu):
     got = one_cycle_gpu(mg, prec, shape, h, nu, kappa=kap, S=S)
     for g, k in zip(got, kap):
         check(g, one_cycle_oracle(oracle.helmholtz(shape, h, k), S, nu), prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nu", [(2, 2), (1, 3)])
+def test_one_cycle_screened(mg, prec, nu):
+    """Variable coefficient and alpha > 0 together (mg_solve_screened), Neumann
+    on the sides and Dirichlet data on z."""
+    shape = (24, 32, 40)
+    h = 1.0 / 40
+    f = blobs(shape, 7) / W.EPS0
+    beta = W.dielectric_slab_box(shape, h, (0.0, 0.0, 0.0), z_top=0.3) * (
+        1.0 + 0.5 * np.random.default_rng(8).random(shape))
+    got = one_cycle_gpu(mg, prec, shape, h, nu, rho=f, eps=beta, alpha=400.0)
+    p = oracle.Problem(shape, h, 400.0, beta, None, W.GAP_BC_KIND, W.GAP_BC_VALUE)
+    check(got, one_cycle_oracle(p, f, nu), prec)

@@ -421,3 +421,55 @@ def test_face_data_reproduces_linear_potential(alpha, eps):
     p = oracle.Problem(shape, h, alpha=alpha, beta=np.full(shape, eps), face_data=fd)
     u, _, rel, _ = p.solve(alpha * exact)
     np.testing.assert_allclose(u, exact, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- screened operator
+
+
+def test_screened_operator_is_alpha_plus_poisson():
+    """alpha u - div(beta grad u): alpha enters as alpha * I only (not weighted
+    by beta or by the boundary terms), on top of the variable-coefficient
+    operator pinned above; checked on a random field, random beta, mixed BCs
+    and an electrode block."""
+    rng = np.random.default_rng(21)
+    shape = (6, 7, 8)
+    h = 0.11
+    beta = rng.uniform(0.5, 5.0, shape)
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[2:4, 3:5, 1:3] = 1
+    kinds = (0, 1, 1, 0, 0, 1)
+    u = rng.standard_normal(shape)
+    a0 = oracle.Problem(shape, h, 0.0, beta, mask, kinds).apply(u, homog=True)
+    a1 = oracle.Problem(shape, h, 7.5, beta, mask, kinds).apply(u, homog=True)
+    free = mask == 0
+    np.testing.assert_allclose((a1 - a0)[free], 7.5 * u[free], rtol=1e-12, atol=1e-9)
+
+
+def test_screened_constant_solutions():
+    """Neumann on every face: constant u = f / alpha whatever beta is (no flux
+    through any face).  Dirichlet value g on every face and f = alpha g: u = g
+    (the ghost 2g - u equals u)."""
+    rng = np.random.default_rng(22)
+    shape = (8, 10, 12)
+    h = 1.0 / 12
+    beta = rng.uniform(0.2, 8.0, shape)
+    alpha = 3.7
+    p = oracle.Problem(shape, h, alpha, beta, None, (1,) * 6)
+    u, _, _, _ = p.solve(np.full(shape, alpha * 2.5))
+    np.testing.assert_allclose(u, 2.5, rtol=1e-12)
+    p = oracle.Problem(shape, h, alpha, beta, None, (0,) * 6, (-1.25,) * 6)
+    u, _, _, _ = p.solve(np.full(shape, alpha * -1.25))
+    np.testing.assert_allclose(u, -1.25, rtol=1e-12)
+
+
+def test_screened_neumann_conserves():
+    """Neumann on every face: the sum over cells of (alpha u - div(beta grad
+    u)) equals alpha times the sum of u for any u (interior face fluxes
+    cancel pairwise), so a diffusion factor (I - mu L) keeps the total."""
+    rng = np.random.default_rng(23)
+    shape = (9, 8, 7)
+    h = 0.2
+    beta = rng.uniform(0.1, 3.0, shape)
+    u = rng.standard_normal(shape)
+    au = oracle.Problem(shape, h, 2.0, beta, None, (1,) * 6).apply(u)
+    assert abs(au.sum() - 2.0 * u.sum()) <= 1e-10 * np.abs(au).sum()
