@@ -13,7 +13,7 @@ stands for the exact discrete solution.
 
 Arrays are numpy, shape (nz, ny, nx), x fastest.  Faces are ordered
 -x, +x, -y, +y, -z, +z; ``bc_kind`` 0 = Dirichlet (value in ``bc_value``),
-1 = homogeneous Neumann.
+1 = homogeneous Neumann, 2 = Robin n.grad u + a u = 0 (a in ``bc_value``).
 
 Parity status: every function here is pinned by tests in
 ``tests/test_oracle_pins.py`` (closed-form eigenmode solves, layered-dielectric
@@ -225,9 +225,22 @@ def poisson(shape, h, eps_r=None, mask=None, bc_kind=(1, 1, 1, 1, 0, 0),
     return Problem(shape, h, 0.0, eps_r, mask, bc_kind, bc_value)
 
 
-def helmholtz(shape, h, kappa, mask=None):
-    """Screened Helmholtz (kappa^2 - lap) Psi = S with Psi = 0 on all faces
-    and on electrode cells (Eq. 3 in the form kappa^2 Psi - lap Psi = S)."""
+def marshak_coefficient(kappa):
+    """Robin coefficient a of the Marshak condition n.grad Psi + a Psi = 0 for
+    the Helmholtz form (kappa^2 - lap) Psi = S: the paper's Eq. 3 with the
+    Eddington closure has n.grad Psi + (3 kappa_p / 2) Psi = 0, and
+    kappa = sqrt(3) kappa_p, so a = (sqrt(3)/2) kappa."""
+    return 0.5 * np.sqrt(3.0) * float(kappa)
+
+
+def helmholtz(shape, h, kappa, mask=None, marshak=False):
+    """Screened Helmholtz (kappa^2 - lap) Psi = S (Eq. 3 in the form
+    kappa^2 Psi - lap Psi = S), Psi = 0 on electrode cells; on every domain
+    face Psi = 0, or with marshak=True the Robin condition of
+    marshak_coefficient(kappa)."""
+    if marshak:
+        a = marshak_coefficient(kappa)
+        return Problem(shape, h, float(kappa) ** 2, None, mask, (2,) * 6, (a,) * 6)
     return Problem(shape, h, float(kappa) ** 2, None, mask, (0,) * 6, (0.0,) * 6)
 
 

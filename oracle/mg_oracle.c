@@ -26,7 +26,14 @@
  * grid reaches the same discrete answer.
  *
  * Layout: x fastest, index (k*ny + j)*nx + i.  Faces are ordered
- * -x, +x, -y, +y, -z, +z.  bc_kind 0 = Dirichlet, 1 = Neumann.
+ * -x, +x, -y, +y, -z, +z.  bc_kind 0 = Dirichlet, 1 = Neumann, 2 = Robin
+ * n.grad u + a u = 0 with a = bc_value (outward normal n; the Marshak
+ * condition of the radiative-transfer equations):
+ *   face value (u_c + u_g)/2 and normal derivative (u_g - u_c)/h give the
+ *   ghost u_g = u_c (1 - a h/2)/(1 + a h/2), so the face adds
+ *   2 beta_c rho / h^2 to the diagonal with rho = (a h/2)/(1 + a h/2)
+ *   (rho = 1: homogeneous Dirichlet, rho = 0: Neumann).  Coarse grids use
+ *   their own h.
  */
 #include <math.h>
 #include <stdint.h>
@@ -69,6 +76,12 @@ static double face_value(const or_grid* g, int d, int i, int j, int k) {
   return g->face_data[base + q];
 }
 
+/* Robin face of grid g: weight factor rho (diagonal 2 beta_c rho / h^2) */
+static double robin_rho(const or_grid* g, int d) {
+  const double ah2 = 0.5 * g->bc_value[d] * g->h;
+  return ah2 / (1.0 + ah2);
+}
+
 static const int DI[6] = {-1, 1, 0, 0, 0, 0};
 static const int DJ[6] = {0, 0, -1, 1, 0, 0};
 static const int DK[6] = {0, 0, 0, 0, -1, 1};
@@ -101,6 +114,8 @@ static void row(const or_grid* g, double alpha, const double* beta,
       double w = 2.0 * bc; /* ghost = 2 g - u_c */
       diag += w * ih2;
       if (!homog) off += w * ih2 * face_value(g, d, i, j, k);
+    } else if (g->bc_kind[d] == 2) {
+      diag += 2.0 * bc * robin_rho(g, d) * ih2; /* ghost = u_c (1 - ah/2)/(1 + ah/2) */
     }
   }
   *diag_out = diag;
@@ -159,18 +174,26 @@ void or_restrict(const or_grid* fg, const double* rf, const or_grid* cg, double*
       }
 }
 
-/* Coarse correction value at a possibly out-of-box coarse index: reflected
- * through the domain face with sign -1 (homogeneous Dirichlet) or +1
- * (Neumann); masked coarse cells hold a zero correction. */
+/* Ghost factor of the homogeneous face condition of grid g: u_g = s u_c
+ * with s = -1 (Dirichlet), +1 (Neumann), (1 - ah/2)/(1 + ah/2) (Robin). */
+static double ghost_factor(const or_grid* g, int d) {
+  if (g->bc_kind[d] == 0) return -1.0;
+  if (g->bc_kind[d] == 1) return 1.0;
+  return 1.0 - 2.0 * robin_rho(g, d);
+}
+
+/* Coarse correction value at a possibly out-of-box coarse index: the ghost
+ * of the homogeneous face condition (ghost_factor times the cell inside);
+ * masked coarse cells hold a zero correction. */
 static double coarse_val(const or_grid* cg, const uint8_t* cmask, const double* ec,
                          int I, int J, int K) {
   double s = 1.0;
-  if (I < 0) { I = 0; s *= cg->bc_kind[0] == 0 ? -1.0 : 1.0; }
-  if (I >= cg->nx) { I = cg->nx - 1; s *= cg->bc_kind[1] == 0 ? -1.0 : 1.0; }
-  if (J < 0) { J = 0; s *= cg->bc_kind[2] == 0 ? -1.0 : 1.0; }
-  if (J >= cg->ny) { J = cg->ny - 1; s *= cg->bc_kind[3] == 0 ? -1.0 : 1.0; }
-  if (K < 0) { K = 0; s *= cg->bc_kind[4] == 0 ? -1.0 : 1.0; }
-  if (K >= cg->nz) { K = cg->nz - 1; s *= cg->bc_kind[5] == 0 ? -1.0 : 1.0; }
+  if (I < 0) { I = 0; s *= ghost_factor(cg, 0); }
+  if (I >= cg->nx) { I = cg->nx - 1; s *= ghost_factor(cg, 1); }
+  if (J < 0) { J = 0; s *= ghost_factor(cg, 2); }
+  if (J >= cg->ny) { J = cg->ny - 1; s *= ghost_factor(cg, 3); }
+  if (K < 0) { K = 0; s *= ghost_factor(cg, 4); }
+  if (K >= cg->nz) { K = cg->nz - 1; s *= ghost_factor(cg, 5); }
   long c = idx(cg, I, J, K);
   if (cmask && cmask[c]) return 0.0;
   return s * ec[c];
@@ -336,7 +359,10 @@ static int mg_build(or_mg* M, const or_grid* g, double alpha, const double* beta
     or_grid cg = M->g[l];
     cg.nx /= 2; cg.ny /= 2; cg.nz /= 2;
     cg.h *= 2.0;
-    for (int d = 0; d < 6; ++d) cg.bc_value[d] = 0.0;
+    /* corrections are homogeneous: Dirichlet values 0; a Robin face keeps
+     * its coefficient */
+    for (int d = 0; d < 6; ++d)
+      if (cg.bc_kind[d] != 2) cg.bc_value[d] = 0.0;
     cg.face_data = NULL;
     long nc = ncell(&cg);
     M->g[l + 1] = cg;

@@ -473,3 +473,64 @@ def test_screened_neumann_conserves():
     u = rng.standard_normal(shape)
     au = oracle.Problem(shape, h, 2.0, beta, None, (1,) * 6).apply(u)
     assert abs(au.sum() - 2.0 * u.sum()) <= 1e-10 * np.abs(au).sum()
+
+
+# ---------------------------------------------------------------- Robin (Marshak) faces
+
+
+def robin_mode(n, h, a):
+    """Lowest discrete eigenvector of the 1D cell-centred second difference
+    with the Robin ghost u_g = g u_c, g = (1 - ah/2)/(1 + ah/2), on both ends:
+    u_i = cos(theta (i + 1/2) + phi), found from the two end conditions
+    (tan phi = -(ah/2) cot(theta/2) from the low end, a scalar root for theta
+    from the high end).  Returns (u, lambda) with lambda = (2 - 2 cos theta)/h^2."""
+    from scipy.optimize import brentq
+
+    gam = (1 - a * h / 2) / (1 + a * h / 2)
+    phi_of = lambda t: np.arctan(-(a * h / 2) / np.tan(t / 2))
+    F = lambda t: (np.cos(t * (n + 0.5) + phi_of(t)) - gam * np.cos(t * (n - 0.5) + phi_of(t)))
+    t = brentq(F, 1e-9, np.pi / n - 1e-12)
+    u = np.cos(t * (np.arange(n) + 0.5) + phi_of(t))
+    # the low-end condition holds by construction; check the high end too
+    assert abs(np.cos(t * (n + 0.5) + phi_of(t)) - gam * u[-1]) < 1e-10
+    return u, (2 - 2 * np.cos(t)) / h**2
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("a", [0.5, 7.0, 60.0])
+def test_robin_eigenmode(axis, a):
+    """A mode along one axis with Robin faces on that axis (Neumann on the
+    others) is an eigenvector of the discrete operator with eigenvalue
+    alpha + lambda; solving with f = (alpha + lambda) u returns u."""
+    n = 16
+    h = 1.0 / n
+    u1, lam1 = robin_mode(n, h, a)
+    shape = [6, 7, 8]
+    shape[2 - axis] = n
+    shape = tuple(shape)
+    kinds = [1] * 6
+    vals = [0.0] * 6
+    kinds[2 * axis] = kinds[2 * axis + 1] = 2
+    vals[2 * axis] = vals[2 * axis + 1] = a
+    bshape = [1, 1, 1]
+    bshape[2 - axis] = n
+    u = np.broadcast_to(u1.reshape(bshape), shape).copy()
+    alpha = 3.0
+    p = oracle.Problem(shape, h, alpha, None, None, kinds, vals)
+    got, _, rel, _ = p.solve((alpha + lam1) * u)
+    np.testing.assert_allclose(got, u, rtol=0, atol=1e-11)
+
+
+def test_robin_limits():
+    """a = 0 is the Neumann face; a very large a is the homogeneous Dirichlet
+    face (the ghost factor tends to -1)."""
+    rng = np.random.default_rng(31)
+    shape = (8, 8, 8)
+    h = 1.0 / 8
+    f = rng.standard_normal(shape)
+    ref_n, _, _, _ = oracle.Problem(shape, h, 2.0, None, None, (1,) * 6).solve(f)
+    got, _, _, _ = oracle.Problem(shape, h, 2.0, None, None, (2,) * 6, (0.0,) * 6).solve(f)
+    np.testing.assert_allclose(got, ref_n, rtol=0, atol=1e-12)
+    ref_d, _, _, _ = oracle.Problem(shape, h, 2.0, None, None, (0,) * 6).solve(f)
+    got, _, _, _ = oracle.Problem(shape, h, 2.0, None, None, (2,) * 6, (1e14,) * 6).solve(f)
+    assert oracle.rel_l2(got, ref_d) < 1e-11
