@@ -67,15 +67,26 @@ typedef struct {
 
 /* Boundary conditions of the Poisson problem, per face (-x,+x,-y,+y,-z,+z):
  * kind[f] is an mg_bc_kind; value[f] is the Dirichlet potential (ignored for
- * Neumann, which is homogeneous).  The Helmholtz problems always use
- * homogeneous Dirichlet on every face and on electrode cells (free-space
- * absorption; the paper leaves their boundary conditions open, Sec. 2 (iii)). */
+ * Neumann, which is homogeneous).  The Helmholtz problems use Psi = 0 on
+ * electrode cells and, on every domain face, the condition chosen by
+ * mg_options.rte_bc (the paper leaves it open, Sec. 2 (iii)). */
 typedef struct {
   int kind[6];
   double value[6];
 } mg_bc;
 
 typedef enum { MG_PREC_FP64 = 0, MG_PREC_MIXED = 1 } mg_precision;
+
+/* Boundary condition of the radiative-transfer (Helmholtz) problems on the
+ * domain faces; the paper leaves it open (Sec. 2 item (iii)).
+ *   MG_RTE_BC_DIRICHLET  Psi = 0 (free-space absorption).
+ *   MG_RTE_BC_MARSHAK    the Marshak condition of the Eddington closure,
+ *                        n.grad Psi + (3 kappa_p / 2) Psi = 0 for Eq. 3's
+ *                        kappa_p, i.e. n.grad Psi + (sqrt(3)/2) kappa Psi = 0
+ *                        in the Helmholtz form (kappa = sqrt(3) kappa_p);
+ *                        discretised with the face value (u_c + u_g)/2 and
+ *                        the normal derivative (u_g - u_c)/h. */
+typedef enum { MG_RTE_BC_DIRICHLET = 0, MG_RTE_BC_MARSHAK = 1 } mg_rte_bc;
 
 /* Solver options.  Zero-initialised fields take the defaults shown. */
 typedef struct {
@@ -91,7 +102,8 @@ typedef struct {
                        each on a library stream with its own work arrays (4, max 4) */
   int no_graphs;    /* mixed mode: 1 = launch kernels directly instead of
                        replaying each refinement step as a CUDA graph (0) */
-  int reserved;     /* must be zero */
+  int rte_bc;       /* mg_rte_bc: domain faces of the Helmholtz problems
+                       (MG_RTE_BC_DIRICHLET = 0); fixed at mg_create */
 } mg_options;
 
 /* Per-solve statistics.  hist[c] is the relative residual after c cycles

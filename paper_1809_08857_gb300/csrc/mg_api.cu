@@ -251,7 +251,20 @@ void harvest_graph(mg_ctx* c, const StepGraph& g) {
 
 uint8_t poisson_dir(const mg_ctx* c, int f) { return c->bc.kind[f] == MG_BC_DIRICHLET; }
 
-mg::Op64 op64(const mg_ctx* c, int l, Kind kind) {
+// Face factor rho of face f on a level of cell size h (see Op64): Poisson
+// and screened problems use the context's Dirichlet/Neumann faces; the
+// Helmholtz problems Psi = 0 (rho = 1) or the Marshak condition
+// n.grad Psi + a Psi = 0 with a = (sqrt(3)/2) kappa, kappa = sqrt(alpha)
+// (the Eddington closure of Eq. 3, whose coefficient is 3 kappa_p / 2, in
+// the Helmholtz scaling kappa = sqrt(3) kappa_p), rho = (ah/2)/(1 + ah/2).
+double face_rho(const mg_ctx* c, Kind kind, double alpha, int f, double h) {
+  if (kind == kPoisson) return poisson_dir(c, f) ? 1.0 : 0.0;
+  if (c->opt.rte_bc == MG_RTE_BC_DIRICHLET) return 1.0;
+  const double ah2 = 0.5 * (0.5 * std::sqrt(3.0) * std::sqrt(alpha)) * h;
+  return ah2 / (1.0 + ah2);
+}
+
+mg::Op64 op64(const mg_ctx* c, int l, Kind kind, double alpha) {
   const Level& L = c->lv[l];
   mg::Op64 op{};
   op.b = L.b;
@@ -267,11 +280,11 @@ mg::Op64 op64(const mg_ctx* c, int l, Kind kind) {
     op.czd = L.czd;
     op.Dd = L.Dd;
   }
-  for (int f = 0; f < 6; ++f) op.dir[f] = kind == kPoisson ? poisson_dir(c, f) : 1;
+  for (int f = 0; f < 6; ++f) op.rho[f] = face_rho(c, kind, alpha, f, L.h);
   return op;
 }
 
-mg::Split32 sop(const mg_ctx* c, int l, Kind kind) {
+mg::Split32 sop(const mg_ctx* c, int l, Kind kind, double alpha) {
   const Level& L = c->lv[l];
   mg::Split32 op{};
   op.b = L.b;
@@ -280,7 +293,7 @@ mg::Split32 sop(const mg_ctx* c, int l, Kind kind) {
   float* const* beta = kind == kPoisson ? L.bp : L.bh;
   op.beta[0] = beta[0];
   op.beta[1] = beta[1];
-  for (int f = 0; f < 6; ++f) op.dir[f] = kind == kPoisson ? poisson_dir(c, f) : 1;
+  for (int f = 0; f < 6; ++f) op.rho[f] = (float)face_rho(c, kind, alpha, f, L.h);
   return op;
 }
 
@@ -310,7 +323,7 @@ mg_status coarse_inverse(mg_ctx* c, Kind kind, double alpha, const double** out)
   if (n > kDenseMax) return fail(MG_ERR_UNSUPPORTED, "coarsest grid too large for a dense inverse");
   double* M = nullptr;
   MG_TRY(c->alloc(&M, (size_t)n * n));
-  mg::launch_assemble_dense(op64(c, l, kind), alpha, M, c->stream);
+  mg::launch_assemble_dense(op64(c, l, kind, alpha), alpha, M, c->stream);
   mg::launch_gj_invert(M, (int)n, c->gj_row, c->gj_col, c->stream);
   MG_TRY(check_launch());
   c->coarse.push_back({kind, alpha, M});
@@ -353,7 +366,7 @@ mg_status get_work(mg_ctx* c, int q, Work** out) {
 mg_status vcycle64(mg_ctx* c, Kind kind, double alpha, int l, const double* f, double* u) {
   cudaStream_t s = c->stream;
   const int Lc = (int)c->lv.size() - 1;
-  mg::Op64 op = op64(c, l, kind);
+  mg::Op64 op = op64(c, l, kind, alpha);
   const double n = (double)op.b.n();
   const double fb = op.cx ? 32.0 : (op.mask ? 1.0 : 0.0);  // coefficient bytes per cell
   const int cls_s = l == 0 ? MG_KCLASS_SMOOTH : MG_KCLASS_COARSE;
@@ -386,7 +399,7 @@ mg_status vcycle64(mg_ctx* c, Kind kind, double alpha, int l, const double* f, d
   MG_TRY(vcycle64(c, kind, alpha, l + 1, C.f64, C.u64));
   {
     Scope sc(c, s, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE, n * (16.0 + 1.0 + fb));
-    mg::launch_prolong64(op, C.u64, u, s);
+    mg::launch_prolong64(op, op64(c, l + 1, kind, alpha), C.u64, u, s);
   }
   smooth(c->opt.nu2);
   return check_launch();
@@ -401,7 +414,7 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
   const int Lc = (int)c->lv.size() - 1;
   Level& L = c->lv[l];
   LevelWork& X = w->lw[l];
-  mg::Split32 op = sop(c, l, kind);
+  mg::Split32 op = sop(c, l, kind, alpha);
   const float a32 = (float)alpha;
   const double n = (double)L.b.n();
   const double fb = op.beta[0] ? 4.0 : 0.0;
@@ -431,7 +444,7 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
   };
   smooth(c->opt.nu1, first_zero);
   LevelWork& Y = w->lw[l + 1];
-  mg::Split32 cop = sop(c, l + 1, kind);
+  mg::Split32 cop = sop(c, l + 1, kind, alpha);
   {
     // nu1 >= 1: the pre-smoothing ends with a black half-sweep, so only red
     // cells carry a residual.  u both colours, f red, beta both colours,
@@ -479,7 +492,7 @@ mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha
   Level& L0 = c->lv[0];
   LevelWork& X = w->lw[0];
   mg::IrArgs a{};
-  a.op = op64(c, 0, kind);
+  a.op = op64(c, 0, kind, alpha);
   a.alpha = alpha;
   a.bdf = io.bdf;
   a.rhs = io.b64;
@@ -577,7 +590,8 @@ mg_status prepare(Prob& p, cudaStream_t s) {
   if (!p.w->b64) MG_TRY(c->alloc(&p.w->b64, (size_t)L0.b.n()));
   uint8_t dir[6];
   double zero[6] = {0, 0, 0, 0, 0, 0};
-  for (int f = 0; f < 6; ++f) dir[f] = p.kind == kPoisson ? poisson_dir(c, f) : 1;
+  for (int f = 0; f < 6; ++f)
+    dir[f] = p.kind == kPoisson ? poisson_dir(c, f) : c->opt.rte_bc == MG_RTE_BC_DIRICHLET;
   {
     Scope sc(c, s, MG_KCLASS_COARSE, 0);
     if (p.kind == kPoisson)
@@ -1009,8 +1023,8 @@ mg_status build(mg_ctx* c, const double* eps_r, const uint8_t* mask, const doubl
       float2* dst[4] = {L.cxd, L.cyd, L.czd, L.Dd};
       for (int q = 0; q < 4; ++q) mg::launch_split_df(src[q], dst[q], L.b.n(), s);
     }
-    if (eps_r || mask) mg::launch_split_beta(L.beta64, L.mask, sop(c, l, kPoisson), mp(L.bp), s);
-    if (mask) mg::launch_split_beta(nullptr, L.mask, sop(c, l, kHelmholtz), mp(L.bh), s);
+    if (eps_r || mask) mg::launch_split_beta(L.beta64, L.mask, sop(c, l, kPoisson, 0.0), mp(L.bp), s);
+    if (mask) mg::launch_split_beta(nullptr, L.mask, sop(c, l, kHelmholtz, 0.0), mp(L.bh), s);
   }
   c->npartial = mg::ir_partials(L0.b);
   MG_TRY(c->alloc(&c->gj_row, (size_t)nc));
@@ -1031,7 +1045,8 @@ mg_status normalise_options(const mg_options* in, mg_options* out) {
     return fail(MG_ERR_INVALID_ARG, "unknown precision");
   if (in->no_graphs != 0 && in->no_graphs != 1)
     return fail(MG_ERR_INVALID_ARG, "no_graphs must be 0 or 1");
-  if (in->reserved != 0) return fail(MG_ERR_INVALID_ARG, "reserved option field must be 0");
+  if (in->rte_bc != MG_RTE_BC_DIRICHLET && in->rte_bc != MG_RTE_BC_MARSHAK)
+    return fail(MG_ERR_INVALID_ARG, "rte_bc must be MG_RTE_BC_DIRICHLET or MG_RTE_BC_MARSHAK");
   if (in->nu1) out->nu1 = in->nu1;
   if (in->nu2) out->nu2 = in->nu2;
   if (in->max_cycles) out->max_cycles = in->max_cycles;
@@ -1039,6 +1054,7 @@ mg_status normalise_options(const mg_options* in, mg_options* out) {
   if (in->concurrency) out->concurrency = in->concurrency;
   out->precision = in->precision;
   out->no_graphs = in->no_graphs;
+  out->rte_bc = in->rte_bc;
   return MG_OK;
 }
 
@@ -1193,6 +1209,8 @@ mg_status mg_solve_batch(const mg_problem* probs, int nprob, double tol, mg_stat
     } else if (pr.kind == MG_PROBLEM_HELMHOLTZ) {
       if (!(pr.kappa > 0.0) || !std::isfinite(pr.kappa))
         return fail(MG_ERR_INVALID_ARG, "kappa must be finite and > 0");
+      if (pr.faces && pr.ctx->opt.rte_bc == MG_RTE_BC_MARSHAK)
+        return fail(MG_ERR_INVALID_ARG, "face data needs Dirichlet faces (rte_bc is Marshak)");
       P.push_back(make_prob(pr.ctx, kHelmholtz, pr.kappa * pr.kappa, pr.rhs, pr.faces, pr.u, tol,
                             stats ? &stats[q] : nullptr));
     } else if (pr.kind == MG_PROBLEM_SCREENED) {
@@ -1238,6 +1256,8 @@ mg_status mg_set_options(mg_ctx* c, const mg_options* opt) {
   MG_TRY(normalise_options(opt, &o));
   if (o.precision != c->opt.precision)
     return fail(MG_ERR_INVALID_ARG, "the precision mode is fixed at mg_create");
+  if (o.rte_bc != c->opt.rte_bc)
+    return fail(MG_ERR_INVALID_ARG, "rte_bc is fixed at mg_create");
   c->opt = o;
   return MG_OK;
 }
@@ -1337,7 +1357,7 @@ mg_status poisson_residual(mg_ctx* c, const double* rho, double* phi, double* r,
   MG_TRY(prepare(p, s));
   if (r) {
     Scope sc(c, s, MG_KCLASS_COARSE, 0);
-    mg::launch_resid64(op64(c, 0, kPoisson), 0.0, p.b, phi, r, s);
+    mg::launch_resid64(op64(c, 0, kPoisson, 0.0), 0.0, p.b, phi, r, s);
   }
   MG_TRY(check_launch());
   if (pout) *pout = p;

@@ -52,7 +52,10 @@ struct Op64 {
   const uint8_t* mask;
   Box b;
   double ih2;
-  uint8_t dir[6];  // 1 = Dirichlet domain face
+  // per domain face (-x,+x,-y,+y,-z,+z): the face adds 2 beta_c rho / h^2 to
+  // the diagonal and its homogeneous ghost is (1 - 2 rho) u_c: rho = 1
+  // Dirichlet, 0 Neumann, (ah/2)/(1 + ah/2) Robin n.grad u + a u = 0
+  double rho[6];
 };
 
 // FP32 view of a level in red/black split storage: colour c = (i+j+k)&1,
@@ -64,7 +67,7 @@ struct Split32 {
   Box b;
   int W;
   float ih2;
-  uint8_t dir[6];
+  float rho[6];  // face factors as in Op64 (this level's h)
 };
 
 struct Ptr2 {
@@ -99,9 +102,9 @@ struct IrArgs {
   double* partial_z;   // nullable: per-CTA sums of the squared residual of
                        // the guess that is 0 on free cells (FP64 guess only)
   int zchunk;          // set by the launcher
-  // set by the launcher: 1/h^2, -alpha and the beta = 1 diagonals
-  // d/h^2 + alpha (d = 0..12) as double-floats; alpha != 0
-  float2 ih2d, nalpha, diag[13];
+  // set by the launcher: 1/h^2, -alpha and the interior beta = 1 diagonal
+  // 6/h^2 + alpha as double-floats; alpha != 0
+  float2 ih2d, nalpha, dint;
   int has_alpha;
 };
 
@@ -140,8 +143,9 @@ void launch_resid_restrict64(const Op64& op, double alpha, const double* f, cons
                              double* fc, double* uc, cudaStream_t s);
 
 // uf += trilinear prolongation of ec (coarse box = fine/2); electrode fine
-// cells untouched.  dir[] selects the reflection sign of coarse ghosts.
-void launch_prolong64(const Op64& fop, const double* ec, double* uf, cudaStream_t s);
+// cells untouched.  Coarse ghosts: (1 - 2 cop.rho) times the cell inside.
+void launch_prolong64(const Op64& fop, const Op64& cop, const double* ec, double* uf,
+                      cudaStream_t s);
 
 // Residual r = f - A u of the level (no restriction); returns nothing.
 void launch_resid64(const Op64& op, double alpha, const double* f, const double* u, double* r,

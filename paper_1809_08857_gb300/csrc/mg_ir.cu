@@ -155,13 +155,17 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df(IrArgs a) {
   const int ooff = j * nx + i;        // in-plane offset of the own cell
   const int oeoff = j * W + (i >> 1);  // and of its packed (split) position
   const bool zmask = ZNorm && a.op.mask != nullptr;
-  // beta = 1: diagonal (in-box faces + 2 per Dirichlet face) / h^2 + alpha
-  int dxy = 0;
+  // beta = 1: diagonal (in-box faces + 2 rho per domain face) / h^2 +
+  // alpha; interior cells use the launcher's double-float 6/h^2 + alpha,
+  // boundary cells form theirs in FP64 (a few cells per plane)
+  double dxy = 0.0;
+  bool xy_in = true;
   if (!Faces) {
-    dxy += i > 0 ? 1 : (a.op.dir[0] ? 2 : 0);
-    dxy += i < nx - 1 ? 1 : (a.op.dir[1] ? 2 : 0);
-    dxy += j > 0 ? 1 : (a.op.dir[2] ? 2 : 0);
-    dxy += j < ny - 1 ? 1 : (a.op.dir[3] ? 2 : 0);
+    dxy += i > 0 ? 1.0 : 2.0 * a.op.rho[0];
+    dxy += i < nx - 1 ? 1.0 : 2.0 * a.op.rho[1];
+    dxy += j > 0 ? 1.0 : 2.0 * a.op.rho[2];
+    dxy += j < ny - 1 ? 1.0 : 2.0 * a.op.rho[3];
+    xy_in = i > 0 && i < nx - 1 && j > 0 && j < ny - 1;
   }
   // the (at most two) tile cells this thread loads per plane
   constexpr int NS = (PN + NT - 1) / NT;
@@ -282,12 +286,12 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df(IrArgs a) {
           const bool edge = i == 0 || i == nx - 1 || j == 0 || j == ny - 1 || k == 0 || k == nz - 1;
           if (a.lift && edge && !m) {
             const double l = 2.0 * (a.beta0 ? a.beta0[c] : 1.0) * a.op.ih2;
-            if (i == 0 && a.op.dir[0]) bd += l * a.bval.v[0];
-            if (i == nx - 1 && a.op.dir[1]) bd += l * a.bval.v[1];
-            if (j == 0 && a.op.dir[2]) bd += l * a.bval.v[2];
-            if (j == ny - 1 && a.op.dir[3]) bd += l * a.bval.v[3];
-            if (k == 0 && a.op.dir[4]) bd += l * a.bval.v[4];
-            if (k == nz - 1 && a.op.dir[5]) bd += l * a.bval.v[5];
+            if (i == 0 && a.op.rho[0] == 1.0) bd += l * a.bval.v[0];
+            if (i == nx - 1 && a.op.rho[1] == 1.0) bd += l * a.bval.v[1];
+            if (j == 0 && a.op.rho[2] == 1.0) bd += l * a.bval.v[2];
+            if (j == ny - 1 && a.op.rho[3] == 1.0) bd += l * a.bval.v[3];
+            if (k == 0 && a.op.rho[4] == 1.0) bd += l * a.bval.v[4];
+            if (k == nz - 1 && a.op.rho[5] == 1.0) bd += l * a.bval.v[5];
           }
         }
         bb = split_df(bd);
@@ -303,9 +307,13 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df(IrArgs a) {
           dg = C.dg;
           if (a.has_alpha) acc.add(a.nalpha, uc);
         } else {
-          const int d = dxy + (k > 0 ? 1 : (a.op.dir[4] ? 2 : 0)) +
-                        (k < nz - 1 ? 1 : (a.op.dir[5] ? 2 : 0));
-          dg = a.diag[d];
+          if (xy_in && k > 0 && k < nz - 1) {
+            dg = a.dint;
+          } else {
+            const double d = dxy + (k > 0 ? 1.0 : 2.0 * a.op.rho[4]) +
+                             (k < nz - 1 ? 1.0 : 2.0 * a.op.rho[5]);
+            dg = split_df(fma(d, a.op.ih2, a.alpha));
+          }
         }
         acc.add(make_float2(-dg.x, -dg.y), uc);
         auto nb = [&](bool in, float2 w, int buf, int qq) {
@@ -425,12 +433,12 @@ static float2 df_host(double v) {
   return make_float2(hi, (float)(v - (double)hi));
 }
 
-// Launch constants: 1/h^2, -alpha and the beta = 1 diagonals d/h^2 + alpha
-// (d = in-box faces + 2 per Dirichlet face, 0..12) as double-floats.
+// Launch constants: 1/h^2, -alpha and the interior beta = 1 diagonal
+// 6/h^2 + alpha as double-floats.
 static void ir_constants(IrArgs& a) {
   a.ih2d = df_host(a.op.ih2);
   a.nalpha = df_host(-a.alpha);
-  for (int d = 0; d <= 12; ++d) a.diag[d] = df_host(d * a.op.ih2 + a.alpha);
+  a.dint = df_host(6.0 * a.op.ih2 + a.alpha);
   a.has_alpha = a.alpha != 0.0;
 }
 
@@ -569,7 +577,7 @@ extern "C" mg_status mg_residual_norm_noalloc(const mg_grid* grid, const mg_bc* 
   a.op.ih2 = 1.0 / (grid->h * grid->h);
   a.op.mask = mask;
   for (int f = 0; f < 6; ++f) {
-    a.op.dir[f] = bc->kind[f] == MG_BC_DIRICHLET;
+    a.op.rho[f] = bc->kind[f] == MG_BC_DIRICHLET ? 1.0 : 0.0;
     a.bval.v[f] = bc->value[f];
   }
   a.alpha = alpha;

@@ -47,12 +47,12 @@ __device__ __forceinline__ void row(const Op64& op, int i, int j, int k, long lo
     off = o;
   } else {
     double o = 0.0, d = 0.0;
-    if (i > 0) { d += 1.0; o += ld(c - 1); } else if (op.dir[0]) d += 2.0;
-    if (i < nx - 1) { d += 1.0; o += ld(c + 1); } else if (op.dir[1]) d += 2.0;
-    if (j > 0) { d += 1.0; o += ld(c - sy); } else if (op.dir[2]) d += 2.0;
-    if (j < ny - 1) { d += 1.0; o += ld(c + sy); } else if (op.dir[3]) d += 2.0;
-    if (k > 0) { d += 1.0; o += ld(c - sz); } else if (op.dir[4]) d += 2.0;
-    if (k < nz - 1) { d += 1.0; o += ld(c + sz); } else if (op.dir[5]) d += 2.0;
+    if (i > 0) { d += 1.0; o += ld(c - 1); } else d += 2.0 * op.rho[0];
+    if (i < nx - 1) { d += 1.0; o += ld(c + 1); } else d += 2.0 * op.rho[1];
+    if (j > 0) { d += 1.0; o += ld(c - sy); } else d += 2.0 * op.rho[2];
+    if (j < ny - 1) { d += 1.0; o += ld(c + sy); } else d += 2.0 * op.rho[3];
+    if (k > 0) { d += 1.0; o += ld(c - sz); } else d += 2.0 * op.rho[4];
+    if (k < nz - 1) { d += 1.0; o += ld(c + sz); } else d += 2.0 * op.rho[5];
     diag = d * op.ih2;
     off = o * op.ih2;
   }
@@ -324,22 +324,23 @@ __global__ void k_resid(Op op, T alpha, const T* __restrict__ f, const T* __rest
   r[c] = f[c] - ((diag + alpha) * u[c] - off);
 }
 
-// coarse value with homogeneous-BC reflection across domain faces
+// coarse value with the homogeneous face ghost (1 - 2 rho) across domain
+// faces (rho of the coarse level)
 template <class T>
-__device__ __forceinline__ T cval(const T* ec, const Box& cb, const uint8_t* dir, int I, int J,
+__device__ __forceinline__ T cval(const T* ec, const Box& cb, const double* rho, int I, int J,
                                   int K) {
   T s = 1;
-  if (I < 0) { I = 0; if (dir[0]) s = -s; }
-  if (I >= cb.nx) { I = cb.nx - 1; if (dir[1]) s = -s; }
-  if (J < 0) { J = 0; if (dir[2]) s = -s; }
-  if (J >= cb.ny) { J = cb.ny - 1; if (dir[3]) s = -s; }
-  if (K < 0) { K = 0; if (dir[4]) s = -s; }
-  if (K >= cb.nz) { K = cb.nz - 1; if (dir[5]) s = -s; }
+  if (I < 0) { I = 0; s *= (T)(1.0 - 2.0 * rho[0]); }
+  if (I >= cb.nx) { I = cb.nx - 1; s *= (T)(1.0 - 2.0 * rho[1]); }
+  if (J < 0) { J = 0; s *= (T)(1.0 - 2.0 * rho[2]); }
+  if (J >= cb.ny) { J = cb.ny - 1; s *= (T)(1.0 - 2.0 * rho[3]); }
+  if (K < 0) { K = 0; s *= (T)(1.0 - 2.0 * rho[4]); }
+  if (K >= cb.nz) { K = cb.nz - 1; s *= (T)(1.0 - 2.0 * rho[5]); }
   return s * ec[cidx(cb, I, J, K)];
 }
 
 template <class Op, class T>
-__global__ void k_prolong(Op op, const T* __restrict__ ec, T* uf) {
+__global__ void k_prolong(Op op, Op cop, const T* __restrict__ ec, T* uf) {
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= op.b.n()) return;
   if (masked(op, c)) return;
@@ -354,7 +355,7 @@ __global__ void k_prolong(Op op, const T* __restrict__ ec, T* uf) {
   for (int q = 0; q < 8; ++q) {
     const int a = q & 1, bb = (q >> 1) & 1, cc = q >> 2;
     const T w = (a ? (T)0.25 : (T)0.75) * (bb ? (T)0.25 : (T)0.75) * (cc ? (T)0.25 : (T)0.75);
-    v += w * cval(ec, cb, op.dir, I + a * si, J + bb * sj, K + cc * sk);
+    v += w * cval(ec, cb, cop.rho, I + a * si, J + bb * sj, K + cc * sk);
   }
   uf[c] += v;
 }
@@ -487,8 +488,9 @@ void launch_resid_restrict64(const Op64& op, double alpha, const double* f, cons
   add_launches(1);
 }
 
-void launch_prolong64(const Op64& fop, const double* ec, double* uf, cudaStream_t s) {
-  k_prolong<Op64, double><<<blocks_for(fop.b.n()), kThreads, 0, s>>>(fop, ec, uf);
+void launch_prolong64(const Op64& fop, const Op64& cop, const double* ec, double* uf,
+                      cudaStream_t s) {
+  k_prolong<Op64, double><<<blocks_for(fop.b.n()), kThreads, 0, s>>>(fop, cop, ec, uf);
   add_launches(1);
 }
 

@@ -10,11 +10,12 @@
 //
 // Operator (Sec. 2 items (ii)-(iii)): (A u)_c = alpha u_c + sum_f w_f (u_c -
 // u_nb)/h^2 with w_f the harmonic mean of the two cells' beta, beta_c towards
-// an electrode cell and 2 beta_c on a Dirichlet face.  Each level stores
-// hb = 1/(2 beta) per cell (hb < 0 marks an electrode cell), so the harmonic
-// mean 2 b_c b_n / (b_c + b_n) is one add and one reciprocal:
-// w = 1 / (hb_c + hb_n); towards an electrode w = 1 / (2 hb_c); on a
-// Dirichlet face w = 1 / hb_c.
+// an electrode cell and 2 beta_c rho_f on a domain face (rho_f = 1 Dirichlet,
+// 0 Neumann, (ah/2)/(1 + ah/2) Robin).  Each level stores hb = 1/(2 beta)
+// per cell (hb < 0 marks an electrode cell), so the harmonic mean
+// 2 b_c b_n / (b_c + b_n) is one add and one reciprocal: w = 1 / (hb_c +
+// hb_n); towards an electrode w = 1 / (2 hb_c); on a domain face
+// rho_f / hb_c.
 #include "mg_internal.h"
 
 namespace mg {
@@ -52,39 +53,39 @@ __device__ __forceinline__ void row32(const Split32& op, int col, long long t, i
   const int s = i & 1;
   const float* bt = bsel(op, col ^ 1);
   const float bc = VB ? bsel(op, col)[t] : 0.5f;  // hb of the cell
-  const float wd = VB ? wdir(bc) : 2.0f;           // Dirichlet face weight
+  const float wd = VB ? wdir(bc) : 2.0f;           // Dirichlet face weight (rho = 1)
   float d = 0.0f, o = 0.0f, w;
   if (i > 0) {
     const long long q = rowo + (i >> 1) - 1 + s;
     w = VB ? wface(bc, bt[q]) : 1.0f;
     d += w;
     o += w * uo[q];
-  } else if (op.dir[0]) {
-    d += wd;
+  } else {
+    d = fmaf(wd, op.rho[0], d);
   }
   if (i + 1 < op.b.nx) {
     const long long q = rowo + (i >> 1) + s;
     w = VB ? wface(bc, bt[q]) : 1.0f;
     d += w;
     o += w * uo[q];
-  } else if (op.dir[1]) {
-    d += wd;
+  } else {
+    d = fmaf(wd, op.rho[1], d);
   }
   if (j > 0) {
     const long long q = t - W;
     w = VB ? wface(bc, bt[q]) : 1.0f;
     d += w;
     o += w * uo[q];
-  } else if (op.dir[2]) {
-    d += wd;
+  } else {
+    d = fmaf(wd, op.rho[2], d);
   }
   if (j + 1 < op.b.ny) {
     const long long q = t + W;
     w = VB ? wface(bc, bt[q]) : 1.0f;
     d += w;
     o += w * uo[q];
-  } else if (op.dir[3]) {
-    d += wd;
+  } else {
+    d = fmaf(wd, op.rho[3], d);
   }
   const long long sz = (long long)W * op.b.ny;
   if (k > 0) {
@@ -92,16 +93,16 @@ __device__ __forceinline__ void row32(const Split32& op, int col, long long t, i
     w = VB ? wface(bc, bt[q]) : 1.0f;
     d += w;
     o += w * uo[q];
-  } else if (op.dir[4]) {
-    d += wd;
+  } else {
+    d = fmaf(wd, op.rho[4], d);
   }
   if (k + 1 < op.b.nz) {
     const long long q = t + sz;
     w = VB ? wface(bc, bt[q]) : 1.0f;
     d += w;
     o += w * uo[q];
-  } else if (op.dir[5]) {
-    d += wd;
+  } else {
+    d = fmaf(wd, op.rho[5], d);
   }
   diag = d * op.ih2;
   off = o * op.ih2;
@@ -163,18 +164,16 @@ __device__ __forceinline__ float4 quad_update(const Split32& op, float alpha, co
       d += w;
       if (!ZeroOther) o = fmaf(w, un, o);
     };
-    auto dface = [&](bool dir) {
-      if (dir) d += VB ? wdir(hc) : 2.0f;
-    };
+    auto dface = [&](float r) { d = fmaf(VB ? wdir(hc) : 2.0f, r, d); };
     // x: other-colour neighbours at packed p - 1 + S and p + S
     if (!(S == 0 && p == 0)) face(q.bx[e + S], q.ux[e + S]);
-    else dface(op.dir[0]);
+    else dface(op.rho[0]);
     if (!(S == 1 && p == op.W - 1)) face(q.bx[e + S + 1], q.ux[e + S + 1]);
-    else dface(op.dir[1]);
-    if (ym) face(el(q.BYm, e), el(q.UYm, e)); else dface(op.dir[2]);
-    if (yp) face(el(q.BYp, e), el(q.UYp, e)); else dface(op.dir[3]);
-    if (zm) face(el(q.BZm, e), el(q.UZm, e)); else dface(op.dir[4]);
-    if (zp) face(el(q.BZp, e), el(q.UZp, e)); else dface(op.dir[5]);
+    else dface(op.rho[1]);
+    if (ym) face(el(q.BYm, e), el(q.UYm, e)); else dface(op.rho[2]);
+    if (yp) face(el(q.BYp, e), el(q.UYp, e)); else dface(op.rho[3]);
+    if (zm) face(el(q.BZm, e), el(q.UZm, e)); else dface(op.rho[4]);
+    if (zp) face(el(q.BZp, e), el(q.UZp, e)); else dface(op.rho[5]);
     float v = __fdividef(fmaf(o, op.ih2, el(q.F, e)), fmaf(d, op.ih2, alpha));
     if (HasMask && hc < 0.0f) v = el(q.U, e);
     out[e] = v;
@@ -337,15 +336,13 @@ __global__ void __launch_bounds__(kT, 2) k_resid_restrict(Split32 op, Split32 co
             d += w;
             o = fmaf(w, un, o);
           };
-          auto dface = [&](bool dir) {
-            if (dir) d += VB ? wdir(hc) : 2.0f;
-          };
-          if (i > 0) face(bx[e], ux[e]); else dface(op.dir[0]);
-          if (i < nx - 1) face(bx[e + 1], ux[e + 1]); else dface(op.dir[1]);
-          if (ym) face(e ? yb[0].y : yb[0].x, e ? yn[0].y : yn[0].x); else dface(op.dir[2]);
-          if (yp) face(e ? yb[1].y : yb[1].x, e ? yn[1].y : yn[1].x); else dface(op.dir[3]);
-          if (zm) face(e ? zb[0].y : zb[0].x, e ? zn[0].y : zn[0].x); else dface(op.dir[4]);
-          if (zp) face(e ? zb[1].y : zb[1].x, e ? zn[1].y : zn[1].x); else dface(op.dir[5]);
+          auto dface = [&](float r) { d = fmaf(VB ? wdir(hc) : 2.0f, r, d); };
+          if (i > 0) face(bx[e], ux[e]); else dface(op.rho[0]);
+          if (i < nx - 1) face(bx[e + 1], ux[e + 1]); else dface(op.rho[1]);
+          if (ym) face(e ? yb[0].y : yb[0].x, e ? yn[0].y : yn[0].x); else dface(op.rho[2]);
+          if (yp) face(e ? yb[1].y : yb[1].x, e ? yn[1].y : yn[1].x); else dface(op.rho[3]);
+          if (zm) face(e ? zb[0].y : zb[0].x, e ? zn[0].y : zn[0].x); else dface(op.rho[4]);
+          if (zp) face(e ? zb[1].y : zb[1].x, e ? zn[1].y : zn[1].x); else dface(op.rho[5]);
           const float uc0 = e ? U.y : U.x, fc0 = e ? F.y : F.x;
           float r = fc0 - fmaf(fmaf(d, op.ih2, alpha), uc0, -o * op.ih2);
           if ((VB && hc < 0.0f) || (e == 1 && !has1)) r = 0.0f;
@@ -370,8 +367,9 @@ __global__ void __launch_bounds__(kT, 2) k_resid_restrict(Split32 op, Split32 co
 // each fine row (2J+b, 2K+c) first blends the coarse rows J, J +- 1 and
 // planes K, K +- 1 into a line L(X) (weights 3/4 and 1/4 per axis), then
 // fine cell 2X+s takes 3/4 L(X) + 1/4 L(X -+ 1).  Across a domain face the
-// coarse neighbour is the reflected cell, with sign -1 for Dirichlet (the
-// correction vanishes on the face) and +1 for Neumann.
+// coarse neighbour is the ghost of the homogeneous face condition, the cell
+// inside times 1 - 2 rho: -1 for Dirichlet (the correction vanishes on the
+// face), +1 for Neumann, (1 - ah/2)/(1 + ah/2) for Robin.
 //
 // One thread per coarse packed pair P of a coarse row (J, K): the coarse
 // cells X = 2P and 2P+1 sit at packed index P of the two colour arrays, so
@@ -397,11 +395,12 @@ __global__ void __launch_bounds__(kT) k_prolong(Split32 op, Split32 cop, Ptr2 ec
   // coarse rows J-1, J, J+1 and planes K-1, K, K+1 (reflected at the faces)
   const int Jr[3] = {J > 0 ? J - 1 : J, J, J < cny - 1 ? J + 1 : J};
   const int Kr[3] = {K > 0 ? K - 1 : K, K, K < cnz - 1 ? K + 1 : K};
-  const float wJm = 0.25f * (J > 0 ? 1.0f : (cop.dir[2] ? -1.0f : 1.0f));
-  const float wJp = 0.25f * (J < cny - 1 ? 1.0f : (cop.dir[3] ? -1.0f : 1.0f));
-  const float wKm = 0.25f * (K > 0 ? 1.0f : (cop.dir[4] ? -1.0f : 1.0f));
-  const float wKp = 0.25f * (K < cnz - 1 ? 1.0f : (cop.dir[5] ? -1.0f : 1.0f));
-  const float sXm = cop.dir[0] ? -1.0f : 1.0f, sXp = cop.dir[1] ? -1.0f : 1.0f;
+  // ghost factors 1 - 2 rho of the coarse level's faces
+  const float wJm = 0.25f * (J > 0 ? 1.0f : 1.0f - 2.0f * cop.rho[2]);
+  const float wJp = 0.25f * (J < cny - 1 ? 1.0f : 1.0f - 2.0f * cop.rho[3]);
+  const float wKm = 0.25f * (K > 0 ? 1.0f : 1.0f - 2.0f * cop.rho[4]);
+  const float wKp = 0.25f * (K < cnz - 1 ? 1.0f : 1.0f - 2.0f * cop.rho[5]);
+  const float sXm = 1.0f - 2.0f * cop.rho[0], sXp = 1.0f - 2.0f * cop.rho[1];
 
   // z blend of the three rows: Z[c][y] for c = 0 (towards K-1), 1 (K+1);
   // x = 0: coarse X = 2P, x = 1: X = 2P+1

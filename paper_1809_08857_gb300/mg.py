@@ -25,6 +25,8 @@ MG_BC_DIRICHLET = 0
 MG_BC_NEUMANN = 1
 MG_PREC_FP64 = 0
 MG_PREC_MIXED = 1
+MG_RTE_BC_DIRICHLET = 0
+MG_RTE_BC_MARSHAK = 1
 
 EXPORTS = [
     "mg_default_options", "mg_create", "mg_solve_poisson", "mg_solve_helmholtz_batch",
@@ -61,7 +63,7 @@ class Options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("concurrency", ctypes.c_int), ("no_graphs", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("rte_bc", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -278,13 +280,14 @@ class Solver:
 
     shape: (nz, ny, nx); h: cell size; eps_r, mask, mask_value: CUDA tensors
     of that shape (float64, uint8, float64) or None; bc_kind/bc_value: the
-    Poisson boundary conditions per face (-x,+x,-y,+y,-z,+z).
+    Poisson boundary conditions per face (-x,+x,-y,+y,-z,+z); rte_bc: domain
+    faces of the Helmholtz problems (Psi = 0 or the Marshak condition).
     """
 
     def __init__(self, shape, h, eps_r=None, mask=None, mask_value=None,
                  bc_kind=(1, 1, 1, 1, 0, 0), bc_value=(0, 0, 0, 0, 0, 1),
                  precision=MG_PREC_FP64, nu1=2, nu2=2, max_cycles=100, inner_cycles=1,
-                 concurrency=4, graphs=True, stream=None):
+                 concurrency=4, graphs=True, stream=None, rte_bc=MG_RTE_BC_DIRICHLET):
         lib = load()
         nz, ny, nx = (int(s) for s in shape)
         self.shape = (nz, ny, nx)
@@ -292,7 +295,7 @@ class Solver:
         bc = BC((ctypes.c_int * 6)(*[int(k) for k in bc_kind]),
                 (ctypes.c_double * 6)(*[float(v) for v in bc_value]))
         opt = Options(nu1, nu2, max_cycles, precision, inner_cycles, concurrency,
-                      0 if graphs else 1, 0)
+                      0 if graphs else 1, rte_bc)
         for t in (eps_r, mask, mask_value):
             if t is not None and tuple(t.shape) != self.shape:
                 raise ValueError("coefficient shape mismatch")

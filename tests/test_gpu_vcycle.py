@@ -64,10 +64,10 @@ def blobs(shape, seed):
 
 def one_cycle_gpu(mg, prec, shape, h, nu, rho=None, eps=None, mask=None, mask_value=None,
                   kappa=None, S=None, bc_kind=W.GAP_BC_KIND, bc_value=W.GAP_BC_VALUE,
-                  alpha=None):
+                  alpha=None, rte_bc=0):
     s = mg.Solver(shape, h, eps_r=cuda(eps), mask=cuda(mask), mask_value=cuda(mask_value),
                   bc_kind=bc_kind, bc_value=bc_value, precision=prec, nu1=nu[0], nu2=nu[1],
-                  max_cycles=1, inner_cycles=1)
+                  max_cycles=1, inner_cycles=1, rte_bc=rte_bc)
     try:
         if alpha is not None:
             u = torch.zeros(shape, dtype=torch.float64, device="cuda")
@@ -172,3 +172,17 @@ def test_one_cycle_screened(mg, prec, nu):
     got = one_cycle_gpu(mg, prec, shape, h, nu, rho=f, eps=beta, alpha=400.0)
     p = oracle.Problem(shape, h, 400.0, beta, None, W.GAP_BC_KIND, W.GAP_BC_VALUE)
     check(got, one_cycle_oracle(p, f, nu), prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nu", [(2, 2), (1, 1)])
+def test_one_cycle_marshak(mg, prec, nu):
+    """Robin (Marshak) faces on every level: the face factor and the
+    prolongation ghost follow each level's h."""
+    shape = (32, 24, 40)
+    h = 1.0 / 40
+    S = np.abs(blobs(shape, 9)) / W.EPS0
+    kap = W.helmholtz_kappas()
+    got = one_cycle_gpu(mg, prec, shape, h, nu, kappa=kap, S=S, rte_bc=1)
+    for g, k in zip(got, kap):
+        check(g, one_cycle_oracle(oracle.helmholtz(shape, h, k, marshak=True), S, nu), prec)
