@@ -10,10 +10,13 @@
 // ghost value of the domain face outside the box (Dirichlet value g: 2g -
 // phi_c, Neumann: phi_c) and the electrode value at the centre of a masked
 // neighbour (the same values the operator of Eq. 2 uses).  Electrode cells
-// get E = 0.  E is FP64 (one add and one multiply per component); the ratio
-// that only selects a time step is formed in FP32.
+// get E = 0.  E is FP64 (one FP64 add and multiply per component, the same
+// arithmetic as the definition); the ratio that only selects a time step is
+// formed in FP32 from E and J narrowed on the integer pipe, which keeps the
+// FP64 pipe of GB300 (about 1/57 of the FP32 rate) at six operations per cell.
 #include <cfloat>
 
+#include "df.cuh"
 #include "mg_internal.h"
 
 namespace mg {
@@ -45,6 +48,7 @@ __global__ void __launch_bounds__(kT) k_efield(const double* __restrict__ phi,
                                                const double* __restrict__ J,
                                                double* __restrict__ E, float eps0,
                                                float* __restrict__ partial) {
+  using namespace df;
   const long long n = b.n();
   const long long sy = b.nx, sz = (long long)b.nx * b.ny;
   const long long rows = (long long)b.ny * b.nz;
@@ -73,8 +77,8 @@ __global__ void __launch_bounds__(kT) k_efield(const double* __restrict__ phi,
       E[2 * n + c] = ez;
     }
     if (J && !m) {
-      const float jx = (float)J[c], jy = (float)J[n + c], jz = (float)J[2 * n + c];
-      const float fx = (float)ex, fy = (float)ey, fz = (float)ez;
+      const float jx = narrow(J[c]), jy = narrow(J[n + c]), jz = narrow(J[2 * n + c]);
+      const float fx = narrow(ex), fy = narrow(ey), fz = narrow(ez);
       const float j2 = fmaf(jx, jx, fmaf(jy, jy, jz * jz));
       const float e2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
       if (j2 > 0.0f) best = fminf(best, eps0 * sqrtf(e2) * rsqrtf(j2));

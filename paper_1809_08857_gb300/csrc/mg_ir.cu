@@ -21,6 +21,7 @@
 #include <string>
 
 #include "../../include/mg.h"
+#include "df.cuh"
 #include "mg_internal.h"
 
 // Largest number of CTAs (partial sums) one call may use: 16384 doubles,
@@ -33,94 +34,10 @@ namespace mg {
 
 namespace {
 
+using namespace df;
+
 constexpr int TX = 32, TY = 16, NT = TX * TY;
 constexpr int PX = TX + 2, PY = TY + 2, PN = PX * PY;
-
-// IEEE-754 binary32 -> binary64 by re-biasing the exponent (1023 - 127 = 896)
-// and widening the fraction, on the integer pipe (the FP64 pipe is the
-// bottleneck of this kernel).  Zeros and binary32 subnormals (< 1.2e-38,
-// never reached by a correction of a physical field) map to a signed zero;
-// infinities and NaNs keep their class.
-__device__ __forceinline__ double widen(float x) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
-  const unsigned ex = (b >> 23) & 0xffu;
-  const unsigned long long man = (unsigned long long)(b & 0x7fffffu) << 29;
-  const unsigned long long e64 = ex == 0xffu ? 0x7ffull : (unsigned long long)ex + 896ull;
-  const unsigned long long bits = ex == 0u ? sgn : (sgn | (e64 << 52) | man);
-  return __longlong_as_double((long long)bits);
-}
-
-// binary64 -> binary32 by truncation (round toward zero: at most one FP32
-// ulp, harmless for the right-hand side of the FP32 inner cycle), integer
-// pipe.  Values below the binary32 normal range flush to zero, values above
-// it become infinity, NaN stays NaN.
-__device__ __forceinline__ float narrow(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sgn = (unsigned)(b >> 63) << 31;
-  const int ex = (int)((b >> 52) & 0x7ffull);
-  const unsigned man = (unsigned)((b >> 29) & 0x7fffffull);
-  const int e32 = ex - 896;
-  unsigned bits;
-  if (ex == 0x7ff) bits = sgn | 0x7f800000u | (man ? 0x400000u : 0u);
-  else if (e32 >= 255) bits = sgn | 0x7f800000u;
-  else if (e32 <= 0) bits = sgn;
-  else bits = sgn | ((unsigned)e32 << 23) | man;
-  return __uint_as_float(bits);
-}
-
-// ---- double-float arithmetic ------------------------------------------------
-//
-// A double-float is an unevaluated sum hi + lo of two FP32 numbers with
-// |lo| <= ulp(hi): 48 significant bits, enough for a residual whose stopping
-// test sits at 1e-10 of ||b||.  Products and sums are made exact with the
-// classical error-free transformations (Dekker's product via FMA, Knuth's
-// two-sum); the _rn intrinsics keep the compiler from contracting or
-// reassociating them.
-
-// binary64 -> double-float without an FP64 instruction: hi = x truncated to
-// 24 significant bits (integer pipe), lo = the remaining 29 bits rounded to
-// FP32 (one integer -> float conversion and a power-of-two scale).  For
-// |x| < 2^-74 lo is dropped; below the FP32 normal range x flushes to 0.
-__device__ __forceinline__ float2 split_df(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const float hi = narrow(x);
-  const int se = (int)((b >> 52) & 0x7ffull) - 948;  // FP32 exponent field of 2^(ex - 1075)
-  const float scale = (se >= 1 && se <= 254) ? __uint_as_float((unsigned)se << 23) : 0.0f;
-  const float lo = __fmul_rn(__uint2float_rn((unsigned)(b & 0x1fffffffull)), scale);
-  return make_float2(hi, (b >> 63) ? -lo : lo);
-}
-
-// Running sum s + e of double-float products.  add(c, u): s + e += c * u.
-// The product's rounding error (FMA) and its cross terms, and the two-sum
-// error of s, go into e; e itself is a plain FP32 sum of terms 2^-24 below
-// the leading ones, so the total error stays near 2^-48 of the largest term.
-struct DfAcc {
-  float s, e;
-  __device__ __forceinline__ void add(float2 c, float2 u) {
-    const float p = __fmul_rn(c.x, u.x);
-    float q = fmaf(c.x, u.x, -p);
-    q = fmaf(c.x, u.y, q);
-    q = fmaf(c.y, u.x, q);
-    const float t = __fadd_rn(s, p);
-    const float v = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, v)), __fsub_rn(p, v));
-    s = t;
-    e = __fadd_rn(e, __fadd_rn(err, q));
-  }
-  __device__ __forceinline__ float value() const { return __fadd_rn(s, e); }
-};
-
-// a + b (double-float plus FP32) renormalised: two-sum of the leading parts,
-// then the fast two-sum of the result with the low parts.
-__device__ __forceinline__ float2 df_add(float2 a, float b) {
-  const float s = __fadd_rn(a.x, b);
-  const float v = __fsub_rn(s, a.x);
-  const float t = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b, v));
-  const float lo = __fadd_rn(t, a.y);
-  const float hi = __fadd_rn(s, lo);
-  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
-}
 
 // Template arguments:
 //   Faces   variable-coefficient operator (double-float face arrays);
