@@ -156,7 +156,7 @@ struct mg_ctx {
   std::vector<void*> allocs;
   std::vector<void*> host_allocs;
   unsigned long long clock = 0;
-  float* efield_partial = nullptr;  // mg_efield scratch (allocated on first use)
+  unsigned* efield_min = nullptr;  // mg_efield scratch (allocated on first use)
   double* efield_dt = nullptr;
   mg_unet* net = nullptr;  // warm-start network
   bool own_net = false;
@@ -1136,13 +1136,15 @@ mg_status mg_efield(mg_ctx* c, const double* phi, const double* J, double* E, do
   if (!c || !phi) return fail(MG_ERR_INVALID_ARG, "NULL ctx or phi");
   if (dt && !J) return fail(MG_ERR_INVALID_ARG, "dt needs J");
   const Level& L0 = c->lv[0];
-  if (!c->efield_partial) {
-    MG_TRY(c->alloc(&c->efield_partial, (size_t)mg::efield_partials(L0.b)));
+  if (L0.b.ny > 65535 || L0.b.nz > 65535)
+    return fail(MG_ERR_UNSUPPORTED, "mg_efield needs ny, nz <= 65535");
+  if (!c->efield_min) {
+    MG_TRY(c->alloc(&c->efield_min, 1));
     MG_TRY(c->alloc(&c->efield_dt, 1));
   }
   uint8_t dir[6];
   for (int f = 0; f < 6; ++f) dir[f] = poisson_dir(c, f);
-  mg::launch_efield(phi, L0.mask, L0.b, L0.h, dir, c->bc.value, J, E, kEps0, c->efield_partial,
+  mg::launch_efield(phi, L0.mask, L0.b, L0.h, dir, c->bc.value, J, E, kEps0, c->efield_min,
                     dt ? c->efield_dt : nullptr, c->stream);
   MG_TRY(check_launch());
   if (dt) {

@@ -25,7 +25,8 @@ namespace {
 
 constexpr int kT = 256;
 
-// FP32 minimum of a block (every thread passes its value).
+// FP32 minimum of a block (every thread passes its value; the result is
+// valid in thread 0).
 __device__ __forceinline__ float block_min(float v) {
   __shared__ float w[kT / 32];
 #pragma unroll
@@ -40,24 +41,22 @@ __device__ __forceinline__ float block_min(float v) {
   return v;
 }
 
-// One thread per cell along x (grid-stride over rows): blockIdx covers (x
-// blocks, rows); the per-block minimum goes to partial[block].
+// One thread per cell: blockIdx = (x block, j, k).  The block minimum of the
+// ratio (a non-negative FP32 number, whose bit pattern orders like an
+// unsigned integer) goes to *min_bits by atomicMin.
 __global__ void __launch_bounds__(kT) k_efield(const double* __restrict__ phi,
                                                const uint8_t* __restrict__ mask, Box b,
                                                double inv2h, Dir6 dir, Val6 g,
                                                const double* __restrict__ J,
                                                double* __restrict__ E, float eps0,
-                                               float* __restrict__ partial) {
+                                               unsigned* __restrict__ min_bits) {
   using namespace df;
   const long long n = b.n();
   const long long sy = b.nx, sz = (long long)b.nx * b.ny;
-  const long long rows = (long long)b.ny * b.nz;
+  const int i = blockIdx.x * kT + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   float best = FLT_MAX;
-  for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
-    const int j = (int)(row % b.ny), k = (int)(row / b.ny);
-    const int i = blockIdx.x * kT + threadIdx.x;
-    if (i >= b.nx) continue;
-    const long long c = row * b.nx + i;
+  if (i < b.nx) {
+    const long long c = ((long long)k * b.ny + j) * b.nx + i;
     const bool m = mask && mask[c];
     const double pc = phi[c];
     // neighbour value or the face ghost
@@ -84,42 +83,38 @@ __global__ void __launch_bounds__(kT) k_efield(const double* __restrict__ phi,
       if (j2 > 0.0f) best = fminf(best, eps0 * sqrtf(e2) * rsqrtf(j2));
     }
   }
+  if (!J) return;  // whole grid
   best = block_min(best);
-  if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = best;
+  if (threadIdx.x == 0 && best < FLT_MAX) atomicMin(min_bits, __float_as_uint(best));
 }
 
-__global__ void k_min_partials(const float* __restrict__ partial, int n, double* out) {
-  float v = FLT_MAX;
-  for (int t = threadIdx.x; t < n; t += kT) v = fminf(v, partial[t]);
-  v = block_min(v);
-  if (threadIdx.x == 0) *out = v == FLT_MAX ? __longlong_as_double(0x7ff0000000000000ll) : (double)v;
+__global__ void k_min_init(unsigned* min_bits) { *min_bits = __float_as_uint(FLT_MAX); }
+
+__global__ void k_min_final(const unsigned* min_bits, double* out) {
+  const float v = __uint_as_float(*min_bits);
+  *out = v == FLT_MAX ? __longlong_as_double(0x7ff0000000000000ll) : (double)v;
 }
 
 }  // namespace
 
-int efield_partials(const Box& b) {
-  const int gx = (b.nx + kT - 1) / kT;
-  const long long rows = (long long)b.ny * b.nz;
-  const long long gy = rows < 4096 ? rows : 4096;
-  return (int)(gx * gy);
-}
-
 void launch_efield(const double* phi, const uint8_t* mask, Box b, double h, const uint8_t dir[6],
-                   const double gval[6], const double* J, double* E, double eps0, float* partial,
-                   double* dt_out, cudaStream_t s) {
-  const int gx = (b.nx + kT - 1) / kT;
-  const long long rows = (long long)b.ny * b.nz;
-  const int gy = (int)(rows < 4096 ? rows : 4096);
+                   const double gval[6], const double* J, double* E, double eps0,
+                   unsigned* min_bits, double* dt_out, cudaStream_t s) {
   Dir6 d;
   Val6 g;
   for (int f = 0; f < 6; ++f) {
     d.d[f] = dir[f];
     g.v[f] = gval[f];
   }
-  k_efield<<<dim3(gx, gy), kT, 0, s>>>(phi, mask, b, 0.5 / h, d, g, J, E, (float)eps0, partial);
+  if (J) {
+    k_min_init<<<1, 1, 0, s>>>(min_bits);
+    add_launches(1);
+  }
+  const dim3 grid((b.nx + kT - 1) / kT, b.ny, b.nz);
+  k_efield<<<grid, kT, 0, s>>>(phi, mask, b, 0.5 / h, d, g, J, E, (float)eps0, min_bits);
   add_launches(1);
   if (J && dt_out) {
-    k_min_partials<<<1, kT, 0, s>>>(partial, gx * gy, dt_out);
+    k_min_final<<<1, 1, 0, s>>>(min_bits, dt_out);
     add_launches(1);
   }
 }

@@ -176,12 +176,11 @@ void launch_split_beta(const double* beta, const uint8_t* mask, const Split32& o
 // ---- electric field and relaxation time (mg_efield.cu) --------------------
 // E = -grad phi at cell centres (3 arrays of n, nullable) and, with J (3
 // arrays of n) and dt_out (device double), min over free cells of
-// eps0 |E| / |J| (+inf if J vanishes everywhere); partial holds
-// efield_partials(b) floats.
-int efield_partials(const Box& b);
+// eps0 |E| / |J| (+inf if J vanishes everywhere); min_bits is one device
+// unsigned of scratch.  Grids need ny, nz <= 65535.
 void launch_efield(const double* phi, const uint8_t* mask, Box b, double h, const uint8_t dir[6],
-                   const double gval[6], const double* J, double* E, double eps0, float* partial,
-                   double* dt_out, cudaStream_t s);
+                   const double gval[6], const double* J, double* E, double eps0,
+                   unsigned* min_bits, double* dt_out, cudaStream_t s);
 
 // ---- fused refinement step (mg_ir.cu) --------------------------------------
 // One pass: (u + e), r = b - A u, r -> FP32, per-CTA sums of r^2 (and of the
