@@ -432,7 +432,7 @@ long long mg_launch_count(void);
  *   cuda_stream  stream to enqueue on (NULL = legacy default stream).
  * Work is enqueued and the call returns without synchronising.  Scratch: a
  * library-owned static device array of 16384 FP64 partial sums (128 KiB per
- * GPU, held until the process exits); grids need ceil(nx/32)*ceil(ny/8) <=
+ * GPU, held until the process exits); grids need ceil(nx/30)*ceil(ny/14) <=
  * 16384 (every grid up to 2048 x 2048 x any nz), larger ones are rejected with
  * MG_ERR_UNSUPPORTED.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current, so make that first

@@ -13,9 +13,9 @@
 // FP64 pipe issues about 1/57 of the FP32 rate, and an FP64 stencil of about
 // ten operations per cell left this pass at 20 % of the HBM bandwidth.  The
 // iterate itself is kept as double-floats during a solve, so no FP64
-// instruction is left per cell.  Each CTA marches along z through a 32 x 16
-// (x, y) tile, keeping three planes of u + e (with a one-cell halo) in
-// shared memory as double-floats.
+// instruction is left per cell.  Each thread marches one (i, j) column of a
+// z-chunk with its planes in registers; y-neighbours go through shared
+// memory, x-neighbours through warp shuffles.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -36,8 +36,7 @@ namespace {
 
 using namespace df;
 
-constexpr int TX = 32, TY = 16, NT = TX * TY;
-constexpr int PX = TX + 2, PY = TY + 2, PN = PX * PY;
+constexpr int TX = 32, TY = 16, NT = TX * TY;  // a CTA's patch of columns (own: inner 30 x 14)
 
 // Template arguments:
 //   Faces   variable-coefficient operator (double-float face arrays);
@@ -50,98 +49,69 @@ constexpr int PX = TX + 2, PY = TY + 2, PN = PX * PY;
 //   ZNorm   also the norm of the residual of the guess that is 0 on free
 //           cells and u on electrode cells (||b|| of the stopping test),
 //           into partial_z
-// Software pipeline along z with four plane buffers: while plane k is
-// computed, plane k+2 is stored to shared memory from registers and the
-// loads of plane k+3 and of the own cells' b and coefficients of plane k+1
-// are in flight; one barrier per plane.
+// A CTA of 32 x 16 threads covers a 32 x 16 patch of (i, j) columns, of
+// which the inner 30 x 14 are its own cells and the rim is the halo.  Every
+// thread marches its column along z with u + e of planes k-1, k, k+1 in
+// registers (the z-neighbours), its raw loads of plane k+2 in flight; each
+// plane's u + e goes through a double-buffered shared-memory plane for the
+// y-neighbours, and the x-neighbours come from the adjacent lanes (a warp
+// is one row) by shuffle.  One barrier per plane.
 template <bool Faces, bool HasE, bool U64, int BIn, bool ZNorm>
-__global__ void __launch_bounds__(NT, 2) k_ir_df(IrArgs a) {
-  __shared__ float2 pl[4][PN];
-  __shared__ unsigned char mk[ZNorm ? 4 : 1][ZNorm ? PN : 1];  // electrode flags
+__global__ void __launch_bounds__(NT, Faces ? 2 : 3) k_ir_df(IrArgs a) {
+  __shared__ float2 pl[2][TY][TX];
+  __shared__ unsigned char mk[ZNorm ? 2 : 1][ZNorm ? TY : 1][TX];  // electrode flags
   __shared__ float red[2][NT / 32];
+  const unsigned FULL = 0xffffffffu;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * a.zchunk;
   const int nx = a.op.b.nx, ny = a.op.b.ny, nz = a.op.b.nz;
-  const int z1 = min(nz, z0 + a.zchunk);
+  const int i = blockIdx.x * (TX - 2) - 1 + tx, j = blockIdx.y * (TY - 2) - 1 + ty;
+  const int z0 = blockIdx.z * a.zchunk, z1 = min(nz, z0 + a.zchunk);
   const int W = a.W;
-  const int sy = nx;
   const long long sz = (long long)nx * ny, szW = (long long)W * ny;
-  const int i = x0 + tx, j = y0 + ty;
-  const bool own = i < nx && j < ny;
-  const int ooff = j * nx + i;        // in-plane offset of the own cell
-  const int oeoff = j * W + (i >> 1);  // and of its packed (split) position
+  const bool in = i >= 0 && i < nx && j >= 0 && j < ny;
+  const bool own = in && tx >= 1 && tx <= TX - 2 && ty >= 1 && ty <= TY - 2;
+  const int off = in ? j * nx + i : 0;        // in-plane offsets of the column
+  const int eoff = in ? j * W + (i >> 1) : 0;
+  const int par0 = (i + j) & 1;               // colour of the column at k = 0
   const bool zmask = ZNorm && a.op.mask != nullptr;
+  const bool xm = i > 0, xp = i < nx - 1, ym = j > 0, yp = j < ny - 1;
   // beta = 1: diagonal (in-box faces + 2 rho per domain face) / h^2 +
   // alpha; interior cells use the launcher's double-float 6/h^2 + alpha,
-  // boundary cells form theirs in FP64 (a few cells per plane)
+  // boundary cells form theirs in FP64
   double dxy = 0.0;
-  bool xy_in = true;
   if (!Faces) {
-    dxy += i > 0 ? 1.0 : 2.0 * a.op.rho[0];
-    dxy += i < nx - 1 ? 1.0 : 2.0 * a.op.rho[1];
-    dxy += j > 0 ? 1.0 : 2.0 * a.op.rho[2];
-    dxy += j < ny - 1 ? 1.0 : 2.0 * a.op.rho[3];
-    xy_in = i > 0 && i < nx - 1 && j > 0 && j < ny - 1;
+    dxy += xm ? 1.0 : 2.0 * a.op.rho[0];
+    dxy += xp ? 1.0 : 2.0 * a.op.rho[1];
+    dxy += ym ? 1.0 : 2.0 * a.op.rho[2];
+    dxy += yp ? 1.0 : 2.0 * a.op.rho[3];
   }
-  // the (at most two) tile cells this thread loads per plane
-  constexpr int NS = (PN + NT - 1) / NT;
-  int qoff[NS], qeoff[NS], qpar[NS];
-  bool qin[NS], qown[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    const int q = threadIdx.x + s * NT;
-    const int lx = q % PX, ly = q / PX;
-    const int gi = x0 + lx - 1, gj = y0 + ly - 1;
-    qin[s] = q < PN && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
-    qown[s] = qin[s] && lx >= 1 && lx <= TX && ly >= 1 && ly <= TY;
-    qoff[s] = gj * nx + gi;
-    qeoff[s] = gj * W + (gi >> 1);
-    qpar[s] = (gi + gj) & 1;
-  }
+  const bool xy_in = xm && xp && ym && yp;
 
-  // ---- tile planes: raw loads (fetch) and their use one iteration later (commit)
-  double rd[NS];         // FP64 iterate
-  float2 ru[NS];         // double-float iterate
-  float re[NS];          // correction
-  unsigned char rm[NS];  // electrode flag
+  // ---- the column: raw loads of a plane (fetch) and u + e (combine)
+  double rd = 0.0;
+  float2 ru = make_float2(0.0f, 0.0f);
+  float re = 0.0f;
+  bool rm = false;
   auto fetch = [&](int k) {
-    const bool kin = k >= 0 && k < nz;
-    const long long pb = (long long)k * sz, pe = (long long)k * szW;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      if (!(kin && qin[s])) continue;
-      const long long c = pb + qoff[s];
-      if (zmask) rm[s] = a.op.mask[c];
-      if (U64) {
-        rd[s] = a.u_in[c];
-      } else {
-        ru[s] = a.udf_in[c];
-        if (HasE) {
-          const long long t = pe + qeoff[s];
-          re[s] = ((qpar[s] + k) & 1) ? a.e[1][t] : a.e[0][t];
-        }
+    if (!(in && k >= 0 && k < nz)) return;
+    const long long c = (long long)k * sz + off;
+    if (zmask) rm = a.op.mask[c] != 0;
+    if (U64) {
+      rd = a.u_in[c];
+    } else {
+      ru = a.udf_in[c];
+      if (HasE) {
+        const long long t = (long long)k * szW + eoff;
+        re = ((par0 + k) & 1) ? a.e[1][t] : a.e[0][t];
       }
     }
   };
-  auto commit = [&](int buf, int k) {
-    const bool kin = k >= 0 && k < nz, kown = k >= z0 && k < z1;
-    const long long pb = (long long)k * sz;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const int q = threadIdx.x + s * NT;
-      if (NS * NT > PN && q >= PN) break;
-      float2 v = make_float2(0.0f, 0.0f);
-      unsigned char m = 0;
-      if (kin && qin[s]) {
-        if (U64) v = split_df(rd[s]);
-        else v = HasE ? df_add(ru[s], re[s]) : ru[s];
-        if (kown && qown[s] && a.udf_out) a.udf_out[pb + qoff[s]] = v;
-        if (zmask) m = rm[s];
-      }
-      pl[buf][q] = v;
-      if (ZNorm) mk[buf][q] = m;
-    }
+  auto combine = [&](int k, float2& v, bool& m) {
+    v = make_float2(0.0f, 0.0f);
+    m = false;
+    if (!(in && k >= 0 && k < nz)) return;
+    v = U64 ? split_df(rd) : (HasE ? df_add(ru, re) : ru);
+    m = rm;
   };
 
   // ---- own cell of a plane: b, electrode flag, coefficients
@@ -152,16 +122,16 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df(IrArgs a) {
   };
   auto cell_fetch = [&](int k, Cell& C) {
     if (!own || k >= z1) return;
-    const long long c = (long long)k * sz + ooff;
+    const long long c = (long long)k * sz + off;
     if (Faces) {
       C.dg = a.op.Dd[c];
       const float2* cx = a.op.cxd + c;
       const float2* cy = a.op.cyd + c;
       const float2* cz = a.op.czd + c;
       C.cxm = cx[0];
-      if (i < nx - 1) C.cxp = cx[1];
+      if (xp) C.cxp = cx[1];
       C.cym = cy[0];
-      if (j < ny - 1) C.cyp = cy[sy];
+      if (yp) C.cyp = cy[nx];
       C.czm = cz[0];
       if (k < nz - 1) C.czp = cz[sz];
     } else {
@@ -171,26 +141,34 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df(IrArgs a) {
     else C.bd = a.rhs[c];
   };
 
+  float2 um, uc, up;
+  bool mm, mc, mp;
   fetch(z0 - 1);
-  commit(0, z0 - 1);
+  combine(z0 - 1, um, mm);
   fetch(z0);
-  commit(1, z0);
+  combine(z0, uc, mc);
   fetch(z0 + 1);
-  commit(2, z0 + 1);
-  if (z0 + 2 <= z1) fetch(z0 + 2);
+  combine(z0 + 1, up, mp);
+  fetch(z0 + 2);
   Cell C{}, Cn{};
   cell_fetch(z0, C);
-  __syncthreads();
   float ss = 0.0f, sz2 = 0.0f;
   for (int k = z0; k < z1; ++k) {
-    // plane p sits in buffer (p - z0 + 1) & 3
-    const int b0 = (k - z0) & 3, bm = (k - z0 + 1) & 3, bp = (k - z0 + 2) & 3;
-    if (k + 2 <= z1) commit((k - z0 + 3) & 3, k + 2);
-    if (k + 3 <= z1) fetch(k + 3);
+    const int buf = (k - z0) & 1;
+    pl[buf][ty][tx] = uc;
+    if (ZNorm) mk[buf][ty][tx] = mc;
+    const long long c = (long long)k * sz + off;
+    if (own && a.udf_out) a.udf_out[c] = uc;
     cell_fetch(k + 1, Cn);
+    __syncthreads();
+    // x-neighbours from the adjacent lanes of the row
+    float2 ul, ur;
+    ul.x = __shfl_up_sync(FULL, uc.x, 1);
+    ul.y = __shfl_up_sync(FULL, uc.y, 1);
+    ur.x = __shfl_down_sync(FULL, uc.x, 1);
+    ur.y = __shfl_down_sync(FULL, uc.y, 1);
+    const bool ml = __shfl_up_sync(FULL, mc, 1), mr = __shfl_down_sync(FULL, mc, 1);
     if (own) {
-      const long long c = (long long)k * sz + ooff;
-      const int q = (ty + 1) * PX + (tx + 1);
       float r = 0.0f, rz = 0.0f;
       const bool m = Faces ? C.dg.x < 0.0f : C.m;
       float2 bb;
@@ -200,13 +178,13 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df(IrArgs a) {
         double bd = C.bd;
         if (BIn == 2) {
           bd *= a.rhs_scale;
-          const bool edge = i == 0 || i == nx - 1 || j == 0 || j == ny - 1 || k == 0 || k == nz - 1;
+          const bool edge = !xy_in || k == 0 || k == nz - 1;
           if (a.lift && edge && !m) {
             const double l = 2.0 * (a.beta0 ? a.beta0[c] : 1.0) * a.op.ih2;
-            if (i == 0 && a.op.rho[0] == 1.0) bd += l * a.bval.v[0];
-            if (i == nx - 1 && a.op.rho[1] == 1.0) bd += l * a.bval.v[1];
-            if (j == 0 && a.op.rho[2] == 1.0) bd += l * a.bval.v[2];
-            if (j == ny - 1 && a.op.rho[3] == 1.0) bd += l * a.bval.v[3];
+            if (!xm && a.op.rho[0] == 1.0) bd += l * a.bval.v[0];
+            if (!xp && a.op.rho[1] == 1.0) bd += l * a.bval.v[1];
+            if (!ym && a.op.rho[2] == 1.0) bd += l * a.bval.v[2];
+            if (!yp && a.op.rho[3] == 1.0) bd += l * a.bval.v[3];
             if (k == 0 && a.op.rho[4] == 1.0) bd += l * a.bval.v[4];
             if (k == nz - 1 && a.op.rho[5] == 1.0) bd += l * a.bval.v[5];
           }
@@ -217,64 +195,67 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df(IrArgs a) {
       if (!m) {
         DfAcc acc{bb.x, bb.y};
         DfAcc az{bb.x, bb.y};  // zero guess: only electrode neighbours contribute
-        // r = b - diag u_c + sum_f w_f u_nb
-        const float2 uc = pl[bm][q];
+        const bool zm = k > 0, zp = k < nz - 1;
         float2 dg;
         if (Faces) {
           dg = C.dg;
           if (a.has_alpha) acc.add(a.nalpha, uc);
+        } else if (xy_in && zm && zp) {
+          dg = a.dint;
         } else {
-          if (xy_in && k > 0 && k < nz - 1) {
-            dg = a.dint;
-          } else {
-            const double d = dxy + (k > 0 ? 1.0 : 2.0 * a.op.rho[4]) +
-                             (k < nz - 1 ? 1.0 : 2.0 * a.op.rho[5]);
-            dg = split_df(fma(d, a.op.ih2, a.alpha));
-          }
+          const double d = dxy + (zm ? 1.0 : 2.0 * a.op.rho[4]) + (zp ? 1.0 : 2.0 * a.op.rho[5]);
+          dg = split_df(fma(d, a.op.ih2, a.alpha));
         }
         acc.add(make_float2(-dg.x, -dg.y), uc);
-        auto nb = [&](bool in, float2 w, int buf, int qq) {
-          if (!in) return;
-          const float2 un = pl[buf][qq];
-          acc.add(w, un);
-          if (zmask && mk[buf][qq]) az.add(w, un);
+        auto nb = [&](bool inb, float2 w, float2 v, bool mk_) {
+          if (!inb) return;
+          acc.add(w, v);
+          if (zmask && mk_) az.add(w, v);
         };
+        const float2 us = pl[buf][ty - 1][tx], un = pl[buf][ty + 1][tx];
+        const bool ms = ZNorm && mk[buf][ty - 1][tx], mn = ZNorm && mk[buf][ty + 1][tx];
         if (Faces) {
-          nb(i > 0, C.cxm, bm, q - 1);
-          nb(i < nx - 1, C.cxp, bm, q + 1);
-          nb(j > 0, C.cym, bm, q - PX);
-          nb(j < ny - 1, C.cyp, bm, q + PX);
-          nb(k > 0, C.czm, b0, q);
-          nb(k < nz - 1, C.czp, bp, q);
+          nb(xm, C.cxm, ul, ml);
+          nb(xp, C.cxp, ur, mr);
+          nb(ym, C.cym, us, ms);
+          nb(yp, C.cyp, un, mn);
+          nb(zm, C.czm, um, mm);
+          nb(zp, C.czp, up, mp);
         } else {
           const float2 w = a.ih2d;
-          nb(i > 0, w, bm, q - 1);
-          nb(i < nx - 1, w, bm, q + 1);
-          nb(j > 0, w, bm, q - PX);
-          nb(j < ny - 1, w, bm, q + PX);
-          nb(k > 0, w, b0, q);
-          nb(k < nz - 1, w, bp, q);
+          nb(xm, w, ul, ml);
+          nb(xp, w, ur, mr);
+          nb(ym, w, us, ms);
+          nb(yp, w, un, mn);
+          nb(zm, w, um, mm);
+          nb(zp, w, up, mp);
         }
         r = acc.value();
         rz = az.value();
       }
-      if (a.r[0]) (((i + j + k) & 1) ? a.r[1] : a.r[0])[(long long)k * szW + oeoff] = r;
+      if (a.r[0]) (((par0 + k) & 1) ? a.r[1] : a.r[0])[(long long)k * szW + eoff] = r;
       ss = fmaf(r, r, ss);
       if (ZNorm) sz2 = fmaf(rz, rz, sz2);
     }
+    // advance the column: plane k+2 (loaded last step) becomes k+1
+    um = uc;
+    mm = mc;
+    uc = up;
+    mc = mp;
+    combine(k + 2, up, mp);
+    if (k + 3 <= z1) fetch(k + 3);
     C = Cn;
-    __syncthreads();
   }
   // CTA sums of r^2 (FP32 is ample for a stopping test; the partials and the
   // final sum are accumulated in FP64)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (ZNorm) sz2 += __shfl_xor_sync(0xffffffffu, sz2, o);
+    ss += __shfl_xor_sync(FULL, ss, o);
+    if (ZNorm) sz2 += __shfl_xor_sync(FULL, sz2, o);
   }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = ss;
-    if (ZNorm) red[1][threadIdx.x >> 5] = sz2;
+  if (tx == 0) {
+    red[0][ty] = ss;
+    if (ZNorm) red[1][ty] = sz2;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -283,7 +264,7 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df(IrArgs a) {
     for (int h = 0; h < (ZNorm ? 2 : 1); ++h) {
       double v = threadIdx.x < NT / 32 ? (double)red[h][threadIdx.x] : 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
       if (threadIdx.x == 0) (h ? a.partial_z : a.partial)[cta] = v;
     }
   }
@@ -302,10 +283,11 @@ __global__ void k_df_to_f64(const float2* __restrict__ in, const uint8_t* __rest
 }  // namespace
 
 static dim3 ir_grid(const Box& b, int* zchunk) {
-  const int gx = (b.nx + TX - 1) / TX, gy = (b.ny + TY - 1) / TY;
-  // enough CTAs to fill every SM (152 on GB300) a few times, long z runs
+  const int gx = (b.nx + TX - 3) / (TX - 2), gy = (b.ny + TY - 3) / (TY - 2);
+  // enough CTAs to fill every SM (152 on GB300, three 512-thread CTAs each)
+  // several times over, long z runs
   int zc = b.nz;
-  while (zc > 16 && (long long)gx * gy * ((b.nz + zc - 1) / zc) < 4 * 152 * 2) zc = (zc + 1) / 2;
+  while (zc > 16 && (long long)gx * gy * ((b.nz + zc - 1) / zc) < 8 * 152 * 3) zc = (zc + 1) / 2;
   *zchunk = zc;
   return dim3(gx, gy, (b.nz + zc - 1) / zc);
 }
@@ -481,7 +463,7 @@ extern "C" mg_status mg_residual_norm_noalloc(const mg_grid* grid, const mg_bc* 
   mg::Box box{grid->nx, grid->ny, grid->nz};
   const int nparts = mg::ir_partials(box);
   if (nparts > MG_NOALLOC_MAX_PARTIALS) {
-    mg::set_last_error("grid too large for the allocation-free scratch: ceil(nx/32)*ceil(ny/8) "
+    mg::set_last_error("grid too large for the allocation-free scratch: ceil(nx/30)*ceil(ny/14) "
                        "must not exceed 16384");
     return MG_ERR_UNSUPPORTED;
   }

@@ -98,7 +98,7 @@ def test_noalloc_matches_poisson_entry_point(mg):
 
 
 def test_noalloc_rejects_oversized_grid(mg):
-    """ceil(nx/32) * ceil(ny/8) above 16384 partial sums is refused up front
+    """ceil(nx/30) * ceil(ny/14) above 16384 partial sums is refused up front
     (no kernel runs, so no memory is touched)."""
     import ctypes
 
