@@ -262,7 +262,7 @@ __device__ __forceinline__ float2 ld2(const float* __restrict__ a, long long t, 
 // sweep) ended with a black half-sweep, after which every black cell
 // satisfies its own equation (Gauss-Seidel).
 template <bool VB, bool Vec2>
-__global__ void __launch_bounds__(kT, 2) k_resid_restrict(Split32 op, Split32 cop, float alpha,
+__global__ void __launch_bounds__(kT, 3) k_resid_restrict(Split32 op, Split32 cop, float alpha,
                                                           Ptr2 f, Ptr2 u, MPtr2 fc, MPtr2 uc) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
