@@ -204,10 +204,11 @@ KERNEL_SOURCES = {
 }
 
 
-def traffic_for(cls, cells):
-    """DRAM bytes per launch of the class's level-0 kernel from the committed
-    ncu summary (bytes per cell of the captured launch times the cells of
-    this grid), or None when there is none or the kernel source changed."""
+def traffic_for(cls, algorithmic_bytes):
+    """DRAM bytes per launch of the class: the ratio of DRAM to algorithmic
+    bytes that a committed ncu capture of the class's 512^3 launches
+    measured (profiles/traffic.json), times this launch's algorithmic bytes;
+    None when there is no capture or the kernel source changed since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -217,7 +218,7 @@ def traffic_for(cls, cells):
     ent = t.get(cls)
     if not ent or ent.get("source_hash") != source_hash(KERNEL_SOURCES.get(cls, [])):
         return None
-    return ent["dram_bytes_per_cell"] * cells
+    return round(ent["dram_over_algorithmic"] * algorithmic_bytes)
 
 
 def classes(prof):
@@ -245,7 +246,7 @@ def roofline(prof_serial, prof_overlap, n):
     share_s, gbs_s = classes(prof_serial)
     share_o, gbs_o = classes(prof_overlap)
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(gbs / peak, 4), "traffic": traffic_for(dom, n ** 3),
+            "frac": round(gbs / peak, 4), "traffic": traffic_for(dom, avg_bytes),
             "kernel": dom, "avg_launch_ms": round(avg_ms, 4),
             "algorithmic_bytes_per_launch": avg_bytes,
             "peak_source": (f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
