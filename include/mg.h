@@ -281,6 +281,103 @@ mg_status mg_solve_batch(const mg_problem* probs, int nprob, double tol, mg_stat
 mg_status mg_subbox_bc(const mg_ctx* parent, const double* parent_u, const int origin[3],
                        const int dims[3], double* faces);
 
+/* ---- composite AMR hierarchy ----------------------------------------------
+ *
+ * The paper solves its elliptic equations with second-order cell-centred
+ * finite volumes on patch-based AMR grids (Sec. 2 items (ii)-(iii); nested
+ * Berger-Rigoutsos patches in Secs. 3-4).  An mg_amr is a ratio-2 hierarchy:
+ * the base box (level 0, the mg_grid) and refined boxes of level l >= 1 with
+ * cells of size h / 2^l.  The composite problem is one linear system over the
+ * valid cells (cells not covered by a box of the next level; electrode cells
+ * excluded):
+ *   - same-level faces, domain faces and electrodes as on a single grid;
+ *   - a fine cell on the boundary of its box sees a ghost value across it,
+ *     g = (8/15) cc + (2/3) u_1 - (1/5) u_2: the quadratic along the normal
+ *     through the two fine cells inside and cc, the 2D quadratic (with mixed
+ *     term) of the 3 x 3 parent cells around the parent cell C holding the
+ *     ghost, at the ghost's offset; fine face flux hmean(beta_f, beta_C)
+ *     (g - u_1) / h_f (hmean: harmonic mean);
+ *   - a coarse cell next to a covered cell takes, through that face, the mean
+ *     of the four fine fluxes (refluxing): the discretisation is conservative.
+ * The paper does not print its coarse-fine treatment; this is the standard
+ * conservative one (refluxing, quadratic coarse-fine interpolation).
+ *
+ * Solve: fast adaptive composite iteration.  Per iteration and per level l
+ * (base first): the composite residual, an inner V-cycle solve on every box
+ * of level l (the base box with its domain faces, a refined box with Robin
+ * faces standing in for its coarse-fine ghosts), the correction added to the
+ * box and interpolated (trilinear) into every box refining it.  The residual
+ * is FP64; the corrections use the context precision (FP32 V-cycles in mixed
+ * mode), which changes the rate, not the answer.
+ *
+ * Arrays are per box: index 0 the base box, index q >= 1 the refined box
+ * boxes[q - 1]; each is device FP64, nx*ny*nz of that box, x fastest.
+ */
+typedef struct mg_amr mg_amr; /* opaque, library-owned */
+
+typedef struct {
+  int level; /* >= 1 */
+  int lo[3]; /* lower corner (x, y, z) in cells of this level, counted from the
+                domain's low corner; even */
+  int n[3];  /* cells (x, y, z); even, >= 2; the box grid must coarsen to <= 4096
+                cells (as in mg_create) */
+} mg_amr_box;
+
+/*
+ * mg_amr_create -- build a composite hierarchy.
+ *   base        level-0 grid (the domain).
+ *   nbox, boxes the refined boxes (any order).  Rules, checked: the box's
+ *               footprint on the level below (cells lo/2 .. (lo+n)/2), grown
+ *               by one cell, lies inside one box of that level (its parent);
+ *               it does not overlap the footprint of another box of the same
+ *               level; on level 0 it holds no electrode cell.
+ *   eps_r       NULL (coefficient 1 everywhere) or nbox + 1 device pointers
+ *               (each nullable: 1 on that box), copied at create: the cell
+ *               coefficient beta (relative permittivity of Eq. 2, diffusion
+ *               coefficient of a screened problem).
+ *   mask, mask_value  level-0 electrode cells and values (as mg_create).
+ *   bc, opt, cuda_stream  as mg_create; opt.max_cycles caps the FAC
+ *               iterations, opt.inner_cycles is the V-cycles per box per
+ *               iteration; rte_bc must be MG_RTE_BC_DIRICHLET for Helmholtz.
+ * Errors: MG_ERR_INVALID_ARG for a bad hierarchy (mg_last_error says which
+ * rule), MG_ERR_UNSUPPORTED for a box grid that does not coarsen to 4096
+ * cells or more than 255 refined boxes inside one box.  Synchronises.
+ */
+mg_status mg_amr_create(const mg_grid* base, int nbox, const mg_amr_box* boxes,
+                        const double* const* eps_r, const uint8_t* mask,
+                        const double* mask_value, const mg_bc* bc, const mg_options* opt,
+                        void* cuda_stream, mg_amr** out);
+
+/*
+ * mg_amr_solve -- solve the composite problem to ||b - A u||_2 / ||b||_2 <=
+ * tol over the valid cells (||b||: the residual of the zero guess with the
+ * electrode values kept).
+ *   kind   MG_PROBLEM_POISSON (rhs = rho, b = rho / eps0 + lifts, param
+ *          unused), MG_PROBLEM_SCREENED (param = alpha >= 0, rhs = f) or
+ *          MG_PROBLEM_HELMHOLTZ (param = kappa > 0, beta = 1, Psi = 0 on the
+ *          domain faces and electrodes, rhs = S).
+ *   rhs    nbox + 1 device arrays (valid cells are read).
+ *   u      nbox + 1 device arrays, in: guess, out: solution on the valid
+ *          cells, electrode values on electrode cells, the mean of the
+ *          children on covered cells.
+ * stats (nullable): cycles = FAC iterations, hist per iteration.
+ * Synchronises once per iteration.
+ */
+mg_status mg_amr_solve(mg_amr* amr, int kind, double param, const double* const* rhs,
+                       double* const* u, double tol, mg_stats* stats);
+
+/*
+ * mg_amr_residual -- r = b - A u of the composite problem (kind, param, rhs
+ * as in mg_amr_solve; u holds the electrode values on electrode cells):
+ * valid cells the composite residual, electrode cells 0, covered cells the
+ * mean of their children's values.  norm (nullable, host): ||r||_2 over the
+ * valid cells, which synchronises.
+ */
+mg_status mg_amr_residual(mg_amr* amr, int kind, double param, const double* const* rhs,
+                          const double* const* u, double* const* r, double* norm);
+
+void mg_amr_destroy(mg_amr* amr);
+
 /* Replace the solver options of a context (precision is fixed at create). */
 mg_status mg_set_options(mg_ctx* ctx, const mg_options* opt);
 

@@ -156,6 +156,9 @@ struct mg_ctx {
   std::vector<void*> allocs;
   std::vector<void*> host_allocs;
   unsigned long long clock = 0;
+  // >= 0: every domain face of every level is the Robin face
+  // n.grad u + robin_a u = 0 (the correction operator of an AMR box)
+  double robin_a = -1.0;
   unsigned* efield_min = nullptr;  // mg_efield scratch (allocated on first use)
   double* efield_dt = nullptr;
   mg_unet* net = nullptr;  // warm-start network
@@ -258,6 +261,10 @@ uint8_t poisson_dir(const mg_ctx* c, int f) { return c->bc.kind[f] == MG_BC_DIRI
 // (the Eddington closure of Eq. 3, whose coefficient is 3 kappa_p / 2, in
 // the Helmholtz scaling kappa = sqrt(3) kappa_p), rho = (ah/2)/(1 + ah/2).
 double face_rho(const mg_ctx* c, Kind kind, double alpha, int f, double h) {
+  if (c->robin_a >= 0.0) {
+    const double ah2 = 0.5 * c->robin_a * h;
+    return ah2 / (1.0 + ah2);
+  }
   if (kind == kPoisson) return poisson_dir(c, f) ? 1.0 : 0.0;
   if (c->opt.rte_bc == MG_RTE_BC_DIRICHLET) return 1.0;
   const double ah2 = 0.5 * (0.5 * std::sqrt(3.0) * std::sqrt(alpha)) * h;
@@ -1013,11 +1020,11 @@ mg_status build(mg_ctx* c, const double* eps_r, const uint8_t* mask, const doubl
     for (int l = 1; l < nlev; ++l)
       mg::launch_coarsen(c->lv[l - 1].beta64, c->lv[l - 1].mask, c->lv[l - 1].b, c->lv[l].beta64,
                          c->lv[l].mask, s);
-  uint8_t dir[6];
-  for (int f = 0; f < 6; ++f) dir[f] = poisson_dir(c, f);
   for (int l = 0; l < nlev; ++l) {
     Level& L = c->lv[l];
-    if (eps_r) mg::launch_faces64(L.beta64, L.mask, L.b, L.ih2, dir, L.cx, L.cy, L.cz, L.D, s);
+    double rho[6];
+    for (int f = 0; f < 6; ++f) rho[f] = face_rho(c, kPoisson, 0.0, f, L.h);
+    if (eps_r) mg::launch_faces64(L.beta64, L.mask, L.b, L.ih2, rho, L.cx, L.cy, L.cz, L.D, s);
     if (eps_r && l == 0) {
       const double* src[4] = {L.cx, L.cy, L.cz, L.D};
       float2* dst[4] = {L.cxd, L.cyd, L.czd, L.Dd};
@@ -1070,6 +1077,495 @@ mg_status check_helmholtz_args(const double* S, double* const psi[3], const doub
     if (!psi[j]) return fail(MG_ERR_INVALID_ARG, "psi[j] is NULL");
     if (!(kappa[j] > 0.0) || !std::isfinite(kappa[j]))
       return fail(MG_ERR_INVALID_ARG, "kappa must be finite and > 0");
+  }
+  return MG_OK;
+}
+
+}  // namespace
+
+// ---- composite AMR hierarchy ---------------------------------------------
+//
+// Fast adaptive composite (FAC) iteration on a ratio-2 hierarchy of boxes.
+// Every iteration, for each level l from the base upwards: the composite
+// residual of all levels >= l (finest first: coarse-fine ghosts, residual
+// with refluxing, children's residuals averaged onto covered cells), a
+// correction solve on every box of level l (inner V-cycles from zero; the
+// base box with its domain faces, a refined box with Robin faces that stand
+// in for its coarse-fine ghosts), and the correction added to the box and,
+// by trilinear interpolation, to every box refining it.  The residual is
+// FP64; corrections are FP32 V-cycles (mixed) or FP64 V-cycles, so the
+// iteration converges to the FP64 composite solution either way.
+
+namespace {
+
+// Face factor rho of a refined box's correction operator on its finest
+// level: Robin faces n.grad e + a e = 0 with a h / 2 = rho / (1 - rho), i.e.
+// the ghost (1 - 2 rho) e = (2/3) e, close to the coarse-fine ghost of a
+// smooth correction whose coarse part is zero, (2/3) e_1 - (1/5) e_2.  It
+// only affects the convergence rate of the iteration, not its fixed point.
+constexpr double kBoxRho = 1.0 / 6.0;
+constexpr int kMaxChildren = 255;
+
+struct AmrBox {
+  int level = 0, parent = -1;
+  int lo[3] = {0, 0, 0}, n[3] = {0, 0, 0};
+  int fo[3] = {0, 0, 0};  // footprint lower corner in the parent's cells
+  double h = 0.0;
+  mg_ctx* ctx = nullptr;
+  std::vector<int> children;
+  int child0 = 0;
+  uint8_t* cov = nullptr;  // 0 valid, k + 1 covered by child k (null: no children)
+  double* b = nullptr;     // right-hand side with lifts
+  double* r = nullptr;     // composite residual
+  double* ghost = nullptr; // level >= 1: coarse-fine ghosts, packed per face
+  double* delta = nullptr; // level >= 1 with children: increment passed on
+  double* e64 = nullptr;   // FP64 mode: correction
+  long long poff = 0;      // first partial sum of this box
+  mg::Box box() const { return mg::Box{n[0], n[1], n[2]}; }
+};
+
+}  // namespace
+
+struct mg_amr {
+  mg_options opt{};
+  cudaStream_t stream = nullptr;
+  std::vector<AmrBox> box;  // 0: base box; then the refined boxes in the caller's order
+  int nlev = 1;
+  mg::AmrDev* dev = nullptr;       // box descriptors on the device
+  mg::AmrDev* dev_host = nullptr;  // pinned staging copy
+  int* child_list = nullptr;
+  double* partial = nullptr;  // [2][npartial]: r^2 and zero-guess r^2 per block
+  long long npartial = 0;
+  double* norm_dev = nullptr;   // [2]
+  double* norm_host = nullptr;  // [2], pinned
+  cudaEvent_t ev = nullptr, upload = nullptr, t0 = nullptr, t1 = nullptr;
+  std::vector<void*> allocs;
+  std::vector<void*> host_allocs;
+
+  template <class T>
+  mg_status alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return MG_OK;
+    MG_CUDA(cudaMalloc((void**)p, sizeof(T) * count));
+    allocs.push_back(*p);
+    return MG_OK;
+  }
+};
+
+namespace {
+
+void amr_destroy(mg_amr* a) {
+  if (!a) return;
+  if (a->stream) cudaStreamSynchronize(a->stream);
+  for (AmrBox& B : a->box) destroy(B.ctx);
+  for (void* p : a->allocs) cudaFree(p);
+  for (void* p : a->host_allocs) cudaFreeHost(p);
+  for (cudaEvent_t e : {a->ev, a->upload, a->t0, a->t1})
+    if (e) cudaEventDestroy(e);
+  delete a;
+}
+
+bool box_inside(const int lo[3], const int hi[3], const int olo[3], const int ohi[3]) {
+  for (int d = 0; d < 3; ++d)
+    if (lo[d] < olo[d] || hi[d] > ohi[d]) return false;
+  return true;
+}
+
+bool box_overlap(const int lo[3], const int hi[3], const int olo[3], const int ohi[3]) {
+  for (int d = 0; d < 3; ++d)
+    if (lo[d] >= ohi[d] || olo[d] >= hi[d]) return false;
+  return true;
+}
+
+// Levels, parents, footprints and the nesting rules (host only).
+mg_status amr_layout(mg_amr* a, const mg_grid* g, int nbox, const mg_amr_box* boxes) {
+  a->box.resize((size_t)nbox + 1);
+  AmrBox& B0 = a->box[0];
+  B0.n[0] = g->nx;
+  B0.n[1] = g->ny;
+  B0.n[2] = g->nz;
+  B0.h = g->h;
+  for (int q = 1; q <= nbox; ++q) {
+    const mg_amr_box& in = boxes[q - 1];
+    AmrBox& B = a->box[q];
+    if (in.level < 1 || in.level > 20)
+      return fail(MG_ERR_INVALID_ARG, "refined box level must be in 1..20");
+    B.level = in.level;
+    B.h = g->h / (double)(1 << in.level);
+    for (int d = 0; d < 3; ++d) {
+      if (in.n[d] < 2 || (in.n[d] & 1) || (in.lo[d] & 1))
+        return fail(MG_ERR_INVALID_ARG, "refined box corners and sizes must be even, sizes >= 2");
+      B.lo[d] = in.lo[d];
+      B.n[d] = in.n[d];
+    }
+    a->nlev = std::max(a->nlev, B.level + 1);
+  }
+  for (int q = 1; q <= nbox; ++q) {
+    AmrBox& B = a->box[q];
+    int flo[3], fhi[3], glo[3], ghi[3];
+    for (int d = 0; d < 3; ++d) {
+      flo[d] = B.lo[d] / 2;
+      fhi[d] = (B.lo[d] + B.n[d]) / 2;
+      glo[d] = flo[d] - 1;
+      ghi[d] = fhi[d] + 1;
+    }
+    for (int p = 0; p <= nbox; ++p) {
+      const AmrBox& P = a->box[p];
+      if (P.level != B.level - 1) continue;
+      int phi[3];
+      for (int d = 0; d < 3; ++d) phi[d] = P.lo[d] + P.n[d];
+      if (!box_inside(glo, ghi, P.lo, phi)) continue;
+      if (B.parent >= 0) return fail(MG_ERR_INVALID_ARG, "refined box inside two parents");
+      B.parent = p;
+    }
+    if (B.parent < 0)
+      return fail(MG_ERR_INVALID_ARG,
+                  "refined box: footprint grown by one cell not inside a box of the level below");
+    AmrBox& P = a->box[B.parent];
+    for (int d = 0; d < 3; ++d) B.fo[d] = flo[d] - P.lo[d];
+    P.children.push_back(q);
+    if ((int)P.children.size() > kMaxChildren)
+      return fail(MG_ERR_UNSUPPORTED, "more than 255 refined boxes inside one box");
+    for (int o = 1; o <= nbox; ++o) {
+      const AmrBox& O = a->box[o];
+      if (o == q || O.level != B.level) continue;
+      int olo[3], ohi[3];
+      for (int d = 0; d < 3; ++d) {
+        olo[d] = O.lo[d] / 2;
+        ohi[d] = (O.lo[d] + O.n[d]) / 2;
+      }
+      if (box_overlap(glo, ghi, olo, ohi))
+        return fail(MG_ERR_INVALID_ARG,
+                    "refined boxes of one level must be at least one parent cell apart");
+    }
+  }
+  return MG_OK;
+}
+
+// Electrode cells may not lie under, or next to, a refined box.
+mg_status amr_check_mask(mg_amr* a, const uint8_t* mask) {
+  if (!mask) return MG_OK;
+  const AmrBox& B0 = a->box[0];
+  const mg::Box b = B0.box();
+  std::vector<uint8_t> m((size_t)b.n());
+  MG_CUDA(cudaMemcpy(m.data(), mask, m.size(), cudaMemcpyDeviceToHost));
+  for (int q : B0.children) {
+    const AmrBox& B = a->box[q];
+    for (int k = B.fo[2] - 1; k < B.fo[2] + B.n[2] / 2 + 1; ++k)
+      for (int j = B.fo[1] - 1; j < B.fo[1] + B.n[1] / 2 + 1; ++j)
+        for (int i = B.fo[0] - 1; i < B.fo[0] + B.n[0] / 2 + 1; ++i)
+          if (m[((size_t)k * b.ny + j) * b.nx + i])
+            return fail(MG_ERR_INVALID_ARG, "electrode cell under or next to a refined box");
+  }
+  return MG_OK;
+}
+
+// Context of a refined box: its own grid and coefficient, Robin faces.
+mg_status amr_box_ctx(mg_amr* a, AmrBox& B, const double* eps, const mg_options& o) {
+  mg_ctx* c = new (std::nothrow) mg_ctx;
+  if (!c) return fail(MG_ERR_OOM, "host allocation failed");
+  c->grid.nx = B.n[0];
+  c->grid.ny = B.n[1];
+  c->grid.nz = B.n[2];
+  c->grid.h = B.h;
+  for (int f = 0; f < 6; ++f) {
+    c->bc.kind[f] = MG_BC_NEUMANN;
+    c->bc.value[f] = 0.0;
+  }
+  c->opt = o;
+  c->opt.rte_bc = MG_RTE_BC_DIRICHLET;
+  c->stream = a->stream;
+  c->robin_a = 2.0 * (kBoxRho / (1.0 - kBoxRho)) / B.h;
+  const mg_status st = build(c, eps, nullptr, nullptr);
+  if (st != MG_OK) {
+    destroy(c);
+    return st;
+  }
+  B.ctx = c;
+  return MG_OK;
+}
+
+// Device arrays of every box, the child list and the partial sums.
+mg_status amr_alloc(mg_amr* a) {
+  std::vector<int> clist;
+  for (AmrBox& B : a->box) {
+    const mg::Box b = B.box();
+    const size_t n = (size_t)b.n();
+    MG_TRY(a->alloc(&B.b, n));
+    MG_TRY(a->alloc(&B.r, n));
+    if (B.level > 0) MG_TRY(a->alloc(&B.ghost, (size_t)mg::face_count(b)));
+    if (B.level > 0 && !B.children.empty()) MG_TRY(a->alloc(&B.delta, n));
+    if (a->opt.precision == MG_PREC_FP64) MG_TRY(a->alloc(&B.e64, n));
+    B.child0 = (int)clist.size();
+    for (int k : B.children) clist.push_back(k);
+    if (!B.children.empty()) {
+      std::vector<uint8_t> cov(n, 0);
+      for (size_t t = 0; t < B.children.size(); ++t) {
+        const AmrBox& K = a->box[B.children[t]];
+        for (int k = 0; k < K.n[2] / 2; ++k)
+          for (int j = 0; j < K.n[1] / 2; ++j)
+            for (int i = 0; i < K.n[0] / 2; ++i)
+              cov[((size_t)(K.fo[2] + k) * b.ny + K.fo[1] + j) * b.nx + K.fo[0] + i] =
+                  (uint8_t)(t + 1);
+      }
+      MG_TRY(a->alloc(&B.cov, n));
+      MG_CUDA(cudaMemcpy(B.cov, cov.data(), n, cudaMemcpyHostToDevice));
+    }
+    B.poff = a->npartial;
+    a->npartial += mg::amr_resid_blocks(b);
+  }
+  if (!clist.empty()) {
+    MG_TRY(a->alloc(&a->child_list, clist.size()));
+    MG_CUDA(cudaMemcpy(a->child_list, clist.data(), sizeof(int) * clist.size(),
+                       cudaMemcpyHostToDevice));
+  }
+  MG_TRY(a->alloc(&a->partial, 2 * (size_t)a->npartial));
+  MG_TRY(a->alloc(&a->norm_dev, 2));
+  MG_TRY(a->alloc(&a->dev, a->box.size()));
+  MG_CUDA(cudaMallocHost((void**)&a->dev_host, sizeof(mg::AmrDev) * a->box.size()));
+  a->host_allocs.push_back(a->dev_host);
+  MG_CUDA(cudaMallocHost((void**)&a->norm_host, 2 * sizeof(double)));
+  a->host_allocs.push_back(a->norm_host);
+  MG_CUDA(cudaEventCreateWithFlags(&a->ev, cudaEventDisableTiming));
+  MG_CUDA(cudaEventCreateWithFlags(&a->upload, cudaEventDisableTiming));
+  MG_CUDA(cudaEventCreate(&a->t0));
+  MG_CUDA(cudaEventCreate(&a->t1));
+  MG_CUDA(cudaEventRecord(a->upload, a->stream));
+  return MG_OK;
+}
+
+// Operator kind, alpha and right-hand-side scale of an AMR solve.
+mg_status amr_kind(const mg_amr* a, int kind, double param, Kind* k, double* alpha,
+                   double* scale) {
+  switch (kind) {
+    case MG_PROBLEM_POISSON:
+      *k = kPoisson;
+      *alpha = 0.0;
+      *scale = 1.0 / kEps0;
+      return MG_OK;
+    case MG_PROBLEM_SCREENED:
+      if (!(param >= 0.0) || !std::isfinite(param))
+        return fail(MG_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+      *k = kPoisson;
+      *alpha = param;
+      *scale = 1.0;
+      return MG_OK;
+    case MG_PROBLEM_HELMHOLTZ:
+      if (!(param > 0.0) || !std::isfinite(param))
+        return fail(MG_ERR_INVALID_ARG, "kappa must be finite and > 0");
+      if (a->opt.rte_bc != MG_RTE_BC_DIRICHLET)
+        return fail(MG_ERR_UNSUPPORTED, "AMR Helmholtz solves support Psi = 0 faces only");
+      *k = kHelmholtz;
+      *alpha = param * param;
+      *scale = 1.0;
+      return MG_OK;
+    default:
+      return fail(MG_ERR_INVALID_ARG, "unknown problem kind");
+  }
+}
+
+// Box descriptors for this call's iterate (the staging copy is reused once
+// the previous upload has left it).
+mg_status amr_upload(mg_amr* a, Kind kind, const double* const* u) {
+  MG_CUDA(cudaEventSynchronize(a->upload));
+  for (size_t q = 0; q < a->box.size(); ++q) {
+    const AmrBox& B = a->box[q];
+    mg::AmrDev& d = a->dev_host[q];
+    d = mg::AmrDev{};
+    d.b = B.box();
+    for (int e = 0; e < 3; ++e) d.fo[e] = B.fo[e];
+    d.parent = B.parent;
+    d.child0 = B.child0;
+    d.ih2 = 1.0 / (B.h * B.h);
+    d.u = u[q];
+    d.beta = kind == kPoisson ? B.ctx->lv[0].beta64 : nullptr;
+    d.ghost = B.ghost;
+    d.cov = B.cov;
+  }
+  MG_CUDA(cudaMemcpyAsync(a->dev, a->dev_host, sizeof(mg::AmrDev) * a->box.size(),
+                          cudaMemcpyHostToDevice, a->stream));
+  MG_CUDA(cudaEventRecord(a->upload, a->stream));
+  return MG_OK;
+}
+
+// b of every box: rhs * scale plus the base box's domain-face lifts.
+mg_status amr_rhs(mg_amr* a, Kind kind, double scale, const double* const* rhs) {
+  const double zero[6] = {0, 0, 0, 0, 0, 0};
+  for (size_t q = 0; q < a->box.size(); ++q) {
+    AmrBox& B = a->box[q];
+    const Level& L = B.ctx->lv[0];
+    uint8_t dir[6] = {0, 0, 0, 0, 0, 0};
+    if (q == 0)
+      for (int f = 0; f < 6; ++f) dir[f] = kind == kPoisson ? poisson_dir(B.ctx, f) : 1;
+    mg::launch_rhs64(rhs[q], scale, kind == kPoisson ? L.beta64 : nullptr, L.mask, L.b, L.ih2,
+                     dir, q == 0 && kind == kPoisson ? B.ctx->bc.value : zero, nullptr, B.b,
+                     a->stream);
+  }
+  return check_launch();
+}
+
+// Composite residual of every box of level >= lmin, finest level first;
+// with norm, ||r||^2 over the valid cells into norm_host[1] (and the
+// zero-guess ||b||^2 into norm_host[0] with znorm), asynchronously.
+mg_status amr_pass(mg_amr* a, Kind kind, double alpha, int lmin, bool norm, bool znorm) {
+  cudaStream_t s = a->stream;
+  for (int lev = a->nlev - 1; lev >= lmin; --lev)
+    for (size_t q = 0; q < a->box.size(); ++q) {
+      AmrBox& B = a->box[q];
+      if (B.level != lev) continue;
+      const mg::Box b = B.box();
+      if (lev > 0) mg::launch_amr_ghost(a->dev, (int)q, b, B.ghost, s);
+      const Level& L = B.ctx->lv[0];
+      mg::AmrResArgs ra{};
+      ra.alpha = alpha;
+      if (kind == kPoisson) {
+        ra.cx = L.cx;
+        ra.cy = L.cy;
+        ra.cz = L.cz;
+      }
+      ra.mask = L.mask;
+      for (int f = 0; f < 6; ++f) ra.rho[f] = q == 0 ? face_rho(B.ctx, kind, alpha, f, B.h) : 0.0;
+      ra.b = B.b;
+      ra.r = B.r;
+      ra.partial = norm ? a->partial + B.poff : nullptr;
+      ra.partial_z = znorm ? a->partial + a->npartial + B.poff : nullptr;
+      mg::launch_amr_resid(a->dev, a->child_list, (int)q, b, ra, s);
+      for (int k : B.children) {
+        const AmrBox& K = a->box[k];
+        mg::launch_amr_average(K.box(), K.fo, K.r, b, B.r, s);
+      }
+    }
+  if (norm) {
+    mg::launch_sum_partials(a->partial, (int)a->npartial, a->norm_dev + 1, s);
+    if (znorm) mg::launch_sum_partials(a->partial + a->npartial, (int)a->npartial, a->norm_dev, s);
+    MG_CUDA(cudaMemcpyAsync(a->norm_host, a->norm_dev, 2 * sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+  }
+  return check_launch();
+}
+
+// Correction solve on box q from its residual, added to the box and passed
+// on to every box refining it.
+mg_status amr_correct(mg_amr* a, Kind kind, double alpha, int q, double* const* u) {
+  AmrBox& B = a->box[q];
+  mg_ctx* c = B.ctx;
+  cudaStream_t s = a->stream;
+  const Level& L = c->lv[0];
+  const float* e0 = nullptr;
+  const float* e1 = nullptr;
+  const double* e64 = nullptr;
+  if (a->opt.precision == MG_PREC_MIXED) {
+    Work* w;
+    MG_TRY(get_work(c, 0, &w));
+    // the coarsest inverse is built on the context's stream: before the fork
+    const double* Minv;
+    MG_TRY(coarse_inverse(c, kind, alpha, &Minv));
+    LevelWork& X = w->lw[0];
+    mg::launch_amr_split(L.b, L.W, B.r, X.f32[0], X.f32[1], s);
+    MG_CUDA(cudaEventRecord(a->ev, s));
+    MG_CUDA(cudaStreamWaitEvent(w->s, a->ev, 0));
+    for (int ic = 0; ic < a->opt.inner_cycles; ++ic)
+      MG_TRY(vcycle32(c, w, kind, alpha, 0, ic == 0));
+    MG_CUDA(cudaEventRecord(w->ev, w->s));
+    MG_CUDA(cudaStreamWaitEvent(s, w->ev, 0));
+    e0 = X.u32[0];
+    e1 = X.u32[1];
+  } else {
+    MG_CUDA(cudaMemsetAsync(B.e64, 0, sizeof(double) * (size_t)L.b.n(), s));
+    for (int ic = 0; ic < a->opt.inner_cycles; ++ic)
+      MG_TRY(vcycle64(c, kind, alpha, 0, B.r, B.e64));
+    e64 = B.e64;
+  }
+  mg::launch_amr_add(L.b, L.W, e0, e1, e64, L.mask, u[q], nullptr, s);
+  // children from the correction, deeper boxes from their parent's increment
+  std::vector<int> todo;
+  for (int k : B.children) {
+    AmrBox& K = a->box[k];
+    mg::launch_amr_prolong(L.b, L.W, e0, e1, e64, K.box(), K.fo, u[k], K.delta, s);
+    if (!K.children.empty()) todo.push_back(k);
+  }
+  for (size_t t = 0; t < todo.size(); ++t) {
+    const AmrBox& P = a->box[todo[t]];
+    for (int k : P.children) {
+      AmrBox& K = a->box[k];
+      mg::launch_amr_prolong(P.box(), 0, nullptr, nullptr, P.delta, K.box(), K.fo, u[k], K.delta,
+                             s);
+      if (!K.children.empty()) todo.push_back(k);
+    }
+  }
+  return check_launch();
+}
+
+mg_status check_amr_arrays(const mg_amr* a, const void* const* p) {
+  if (!p) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  for (size_t q = 0; q < a->box.size(); ++q)
+    if (!p[q]) return fail(MG_ERR_INVALID_ARG, "NULL box array");
+  return MG_OK;
+}
+
+mg_status amr_solve(mg_amr* a, int kind_in, double param, const double* const* rhs,
+                    double* const* u, double tol, mg_stats* st) {
+  Kind kind;
+  double alpha, scale;
+  MG_TRY(amr_kind(a, kind_in, param, &kind, &alpha, &scale));
+  MG_TRY(check_amr_arrays(a, (const void* const*)rhs));
+  MG_TRY(check_amr_arrays(a, (const void* const*)u));
+  if (!(tol >= 0.0)) return fail(MG_ERR_INVALID_ARG, "tol must be >= 0");
+  cudaStream_t s = a->stream;
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    MG_CUDA(cudaEventRecord(a->t0, s));
+  }
+  const Level& L0 = a->box[0].ctx->lv[0];
+  if (L0.mask)
+    mg::launch_set_masked(L0.mask, kind == kPoisson ? a->box[0].ctx->mask_value : nullptr,
+                          L0.b.n(), u[0], s);
+  MG_TRY(amr_upload(a, kind, u));
+  MG_TRY(amr_rhs(a, kind, scale, rhs));
+  MG_TRY(amr_pass(a, kind, alpha, 0, true, true));
+  MG_CUDA(cudaStreamSynchronize(s));
+  double bnorm = std::sqrt(a->norm_host[0]);
+  double rel = std::isfinite(bnorm) ? std::sqrt(a->norm_host[1]) / (bnorm > 0.0 ? bnorm : 1.0)
+                                    : bnorm;
+  if (bnorm == 0.0) bnorm = 1.0;
+  if (st) st->hist[0] = rel;
+  int cyc = 0;
+  while (std::isfinite(rel) && rel > tol && cyc < a->opt.max_cycles) {
+    for (int l = 0; l < a->nlev; ++l) {
+      if (l > 0) MG_TRY(amr_pass(a, kind, alpha, l, false, false));
+      for (size_t q = 0; q < a->box.size(); ++q)
+        if (a->box[q].level == l) MG_TRY(amr_correct(a, kind, alpha, (int)q, u));
+    }
+    MG_TRY(amr_pass(a, kind, alpha, 0, true, false));
+    MG_CUDA(cudaStreamSynchronize(s));
+    rel = std::sqrt(a->norm_host[1]) / bnorm;
+    ++cyc;
+    if (st && cyc < 64) st->hist[cyc] = rel;
+  }
+  // covered cells: the mean of their children, finest level first
+  for (int lev = a->nlev - 1; lev >= 1; --lev)
+    for (size_t q = 0; q < a->box.size(); ++q) {
+      const AmrBox& B = a->box[q];
+      if (B.level != lev) continue;
+      mg::launch_amr_average(B.box(), B.fo, u[q], a->box[B.parent].box(), u[B.parent], s);
+    }
+  MG_TRY(check_launch());
+  if (st) {
+    MG_CUDA(cudaEventRecord(a->t1, s));
+    MG_CUDA(cudaEventSynchronize(a->t1));
+    float ms = 0.0f;
+    MG_CUDA(cudaEventElapsedTime(&ms, a->t0, a->t1));
+    st->cycles = cyc;
+    st->rel_resid = rel;
+    st->converged = rel <= tol;
+    st->time_ms = ms;
+  }
+  if (!std::isfinite(rel)) return fail(MG_ERR_NONFINITE, "non-finite value in input or residual");
+  if (rel > tol) {
+    char msg[128];
+    std::snprintf(msg, sizeof msg, "not converged: rel. residual %.3e after %d iterations", rel,
+                  cyc);
+    return fail(MG_ERR_NOT_CONVERGED, msg);
   }
   return MG_OK;
 }
@@ -1458,6 +1954,72 @@ const char* mg_error_string(mg_status s) {
   }
   return "unknown status";
 }
+
+mg_status mg_amr_create(const mg_grid* base, int nbox, const mg_amr_box* boxes,
+                        const double* const* eps_r, const uint8_t* mask, const double* mask_value,
+                        const mg_bc* bc, const mg_options* opt, void* cuda_stream, mg_amr** out) {
+  g_last_error.clear();
+  if (!out) return fail(MG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!base || !bc) return fail(MG_ERR_INVALID_ARG, "base grid or bc is NULL");
+  if (nbox < 0 || (nbox > 0 && !boxes)) return fail(MG_ERR_INVALID_ARG, "bad box list");
+  if (base->nx < 1 || base->ny < 1 || base->nz < 1 || !(base->h > 0.0) || !std::isfinite(base->h))
+    return fail(MG_ERR_INVALID_ARG, "grid sizes must be >= 1 and h > 0");
+  mg_options o;
+  MG_TRY(normalise_options(opt, &o));
+  mg_amr* a = new (std::nothrow) mg_amr;
+  if (!a) return fail(MG_ERR_OOM, "host allocation failed");
+  a->opt = o;
+  a->stream = (cudaStream_t)cuda_stream;
+  mg_status st = amr_layout(a, base, nbox, boxes);
+  if (st == MG_OK) st = amr_check_mask(a, mask);
+  if (st == MG_OK)
+    st = mg_create(base, eps_r ? eps_r[0] : nullptr, mask, mask_value, bc, &o, cuda_stream,
+                   &a->box[0].ctx);
+  for (int q = 1; st == MG_OK && q <= nbox; ++q)
+    st = amr_box_ctx(a, a->box[q], eps_r ? eps_r[q] : nullptr, o);
+  if (st == MG_OK) st = amr_alloc(a);
+  if (st != MG_OK) {
+    const std::string msg = g_last_error;
+    amr_destroy(a);
+    g_last_error = msg;
+    return st;
+  }
+  *out = a;
+  return MG_OK;
+}
+
+mg_status mg_amr_solve(mg_amr* amr, int kind, double param, const double* const* rhs,
+                       double* const* u, double tol, mg_stats* stats) {
+  g_last_error.clear();
+  if (!amr) return fail(MG_ERR_INVALID_ARG, "amr is NULL");
+  return amr_solve(amr, kind, param, rhs, u, tol, stats);
+}
+
+mg_status mg_amr_residual(mg_amr* amr, int kind, double param, const double* const* rhs,
+                          const double* const* u, double* const* r, double* norm) {
+  g_last_error.clear();
+  if (!amr) return fail(MG_ERR_INVALID_ARG, "amr is NULL");
+  Kind k;
+  double alpha, scale;
+  MG_TRY(amr_kind(amr, kind, param, &k, &alpha, &scale));
+  MG_TRY(check_amr_arrays(amr, (const void* const*)rhs));
+  MG_TRY(check_amr_arrays(amr, (const void* const*)u));
+  MG_TRY(check_amr_arrays(amr, (const void* const*)r));
+  MG_TRY(amr_upload(amr, k, u));
+  MG_TRY(amr_rhs(amr, k, scale, rhs));
+  MG_TRY(amr_pass(amr, k, alpha, 0, true, false));
+  for (size_t q = 0; q < amr->box.size(); ++q)
+    MG_CUDA(cudaMemcpyAsync(r[q], amr->box[q].r, sizeof(double) * (size_t)amr->box[q].box().n(),
+                            cudaMemcpyDeviceToDevice, amr->stream));
+  if (norm) {
+    MG_CUDA(cudaStreamSynchronize(amr->stream));
+    *norm = std::sqrt(amr->norm_host[1]);
+  }
+  return MG_OK;
+}
+
+void mg_amr_destroy(mg_amr* amr) { amr_destroy(amr); }
 
 const char* mg_last_error(void) { return g_last_error.c_str(); }
 

@@ -22,6 +22,19 @@ struct Box {
   __host__ __device__ long long n() const { return (long long)nx * ny * nz; }
 };
 
+// Packed per-face data of a box: faces -x, +x (ny*nz each, index k*ny + j),
+// -y, +y (nx*nz, index k*nx + i), -z, +z (nx*ny, index j*nx + i).
+__host__ __device__ inline long long face_offset(const Box& b, int f) {
+  const long long ax = (long long)b.ny * b.nz, ay = (long long)b.nx * b.nz,
+                  az = (long long)b.nx * b.ny;
+  const long long off[6] = {0, ax, 2 * ax, 2 * ax + ay, 2 * ax + 2 * ay, 2 * ax + 2 * ay + az};
+  return off[f];
+}
+// Entries of the packed face data of a box (2 (ny nz + nx nz + nx ny)).
+__host__ __device__ inline long long face_count(const Box& b) {
+  return face_offset(b, 5) + (long long)b.nx * b.ny;
+}
+
 // Small fixed arrays passed to kernels by value.
 struct Dir6 {
   uint8_t d[6];
@@ -111,8 +124,10 @@ struct IrArgs {
 // ---- setup ---------------------------------------------------------------
 // out = in as double-floats (hi = in rounded to FP32, lo = in - hi rounded)
 void launch_split_df(const double* in, float2* out, long long n, cudaStream_t s);
+// Face weights / h^2 of a level; domain face f adds 2 beta_c rho[f] / h^2 to
+// the diagonal (rho as in Op64).
 void launch_faces64(const double* beta, const uint8_t* mask, Box b, double ih2,
-                    const uint8_t dir[6], double* cx, double* cy, double* cz, double* D,
+                    const double rho[6], double* cx, double* cy, double* cz, double* D,
                     cudaStream_t s);
 void launch_coarsen(const double* beta_f, const uint8_t* mask_f, Box fb, double* beta_c,
                     uint8_t* mask_c, cudaStream_t s);
@@ -125,8 +140,6 @@ void launch_gj_invert(double* M, int n, double* rowp, double* colp, cudaStream_t
 void launch_rhs64(const double* f, double scale, const double* beta, const uint8_t* mask,
                   Box b, double ih2, const uint8_t dir[6], const double bval[6],
                   const double* faces, double* out, cudaStream_t s);
-// Entries of the packed face data of a box (2 (ny nz + nx nz + nx ny)).
-long long face_count(const Box& b);
 // Dirichlet face data of a ratio-2 sub-box at parent cell offset (ox,oy,oz)
 // by trilinear interpolation of the parent solution.
 void launch_subbox_bc(const double* parent_u, Box pb, int ox, int oy, int oz, Box sb,
@@ -191,5 +204,54 @@ void launch_ir_fused(const IrArgs& a, cudaStream_t s);
 void launch_df_to_f64(const float2* in, const uint8_t* mask, double* out, long long n,
                       cudaStream_t s);
 int ir_partials(const Box& b);
+
+// ---- composite AMR hierarchy (mg_amr.cu) ----------------------------------
+// One box of a ratio-2 AMR hierarchy as the kernels see it.
+struct AmrDev {
+  Box b;
+  int fo[3];            // level >= 1: footprint lower corner in the parent's cells
+  int parent;           // index of the parent box, -1 for the base box
+  int child0;           // first entry of this box's children in the child list
+  double ih2;
+  const double* u;      // iterate
+  const double* beta;   // cell coefficient (nullable: 1)
+  const double* ghost;  // level >= 1: coarse-fine ghost values, packed per face
+  const uint8_t* cov;   // nullable (no children): 0 valid, k + 1 covered by child k
+};
+
+struct AmrResArgs {
+  double alpha;
+  // same-level face weights / h^2 as in Op64 (nullable: beta = 1, weight 1/h^2)
+  const double* cx;
+  const double* cy;
+  const double* cz;
+  const uint8_t* mask;  // electrode cells (base box only, nullable)
+  double rho[6];        // base box: domain face factors (1 Dirichlet, 0 Neumann)
+  const double* b;      // right-hand side with lifts
+  double* r;            // composite residual (valid and electrode cells)
+  double* partial;      // nullable: per-block sums of r^2 over the valid cells
+  double* partial_z;    // nullable: the same for the zero guess (electrode
+                        // values kept)
+};
+
+// Ghost values of box q (level >= 1) from its own and its parent's iterate.
+void launch_amr_ghost(const AmrDev* D, int q, const Box& b, double* ghost, cudaStream_t s);
+// Composite residual of box q; children's ghosts must be current.
+void launch_amr_resid(const AmrDev* D, const int* child_list, int q, const Box& b,
+                      const AmrResArgs& a, cudaStream_t s);
+unsigned amr_resid_blocks(const Box& b);
+// dst (parent cells over the child's footprint fo) = mean of the 8 children.
+void launch_amr_average(const Box& cb, const int fo[3], const double* src, const Box& pb,
+                        double* dst, cudaStream_t s);
+// FP32 red/black split copy of an FP64 field (packed row width W).
+void launch_amr_split(const Box& b, int W, const double* r, float* f0, float* f1, cudaStream_t s);
+// u += e on free cells (e split FP32 (e0, e1, width W) or FP64 e64); delta
+// (nullable) = e.
+void launch_amr_add(const Box& b, int W, const float* e0, const float* e1, const double* e64,
+                    const uint8_t* mask, double* u, double* delta, cudaStream_t s);
+// Child u += trilinear interpolation of the parent correction (as above);
+// delta (nullable) = the increment.
+void launch_amr_prolong(const Box& pb, int W, const float* e0, const float* e1, const double* e64,
+                        const Box& cb, const int fo[3], double* u, double* delta, cudaStream_t s);
 
 }  // namespace mg

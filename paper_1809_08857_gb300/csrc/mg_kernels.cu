@@ -77,7 +77,7 @@ __device__ __forceinline__ double face_w(const double* beta, const uint8_t* mask
 }
 
 __global__ void k_faces64(const double* beta, const uint8_t* mask, Box b, double ih2,
-                          Dir6 dir, double* cx, double* cy, double* cz, double* D) {
+                          Val6 rho, double* cx, double* cy, double* cz, double* D) {
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= b.n()) return;
   const int i = (int)(c % b.nx);
@@ -86,13 +86,13 @@ __global__ void k_faces64(const double* beta, const uint8_t* mask, Box b, double
   const long long sy = b.nx, sz = (long long)b.nx * b.ny;
   const bool mc = mask && mask[c];
   const double bc = beta ? beta[c] : 1.0;
-  const double wb = mc ? 0.0 : 2.0 * bc;  // Dirichlet domain face
-  double wxm = i > 0 ? face_w(beta, mask, c, c - 1) : (dir.d[0] ? wb : 0.0);
-  double wym = j > 0 ? face_w(beta, mask, c, c - sy) : (dir.d[2] ? wb : 0.0);
-  double wzm = k > 0 ? face_w(beta, mask, c, c - sz) : (dir.d[4] ? wb : 0.0);
-  double wxp = i < b.nx - 1 ? face_w(beta, mask, c, c + 1) : (dir.d[1] ? wb : 0.0);
-  double wyp = j < b.ny - 1 ? face_w(beta, mask, c, c + sy) : (dir.d[3] ? wb : 0.0);
-  double wzp = k < b.nz - 1 ? face_w(beta, mask, c, c + sz) : (dir.d[5] ? wb : 0.0);
+  const double wb = mc ? 0.0 : 2.0 * bc;  // domain face, times its factor rho
+  double wxm = i > 0 ? face_w(beta, mask, c, c - 1) : wb * rho.v[0];
+  double wym = j > 0 ? face_w(beta, mask, c, c - sy) : wb * rho.v[2];
+  double wzm = k > 0 ? face_w(beta, mask, c, c - sz) : wb * rho.v[4];
+  double wxp = i < b.nx - 1 ? face_w(beta, mask, c, c + 1) : wb * rho.v[1];
+  double wyp = j < b.ny - 1 ? face_w(beta, mask, c, c + sy) : wb * rho.v[3];
+  double wzp = k < b.nz - 1 ? face_w(beta, mask, c, c + sz) : wb * rho.v[5];
   cx[c] = wxm * ih2;
   cy[c] = wym * ih2;
   cz[c] = wzm * ih2;
@@ -181,15 +181,6 @@ __global__ void k_gj_elim(double* M, int n, int p, const double* rowp, const dou
 }
 
 // ---- solve kernels --------------------------------------------------------
-
-// Packed Dirichlet face data: faces -x, +x (ny*nz each, index k*ny + j),
-// -y, +y (nx*nz, index k*nx + i), -z, +z (nx*ny, index j*nx + i).
-__host__ __device__ inline long long face_offset(const Box& b, int f) {
-  const long long ax = (long long)b.ny * b.nz, ay = (long long)b.nx * b.nz,
-                  az = (long long)b.nx * b.ny;
-  const long long off[6] = {0, ax, 2 * ax, 2 * ax + ay, 2 * ax + 2 * ay, 2 * ax + 2 * ay + az};
-  return off[f];
-}
 
 // b = f * scale + Dirichlet lifts 2 beta_c g / h^2, with g = bval[face] or,
 // when faces != nullptr, the packed per-face-cell values.
@@ -414,10 +405,11 @@ static Dir6 to_dir(const uint8_t d[6]) {
 }
 
 void launch_faces64(const double* beta, const uint8_t* mask, Box b, double ih2,
-                    const uint8_t dir[6], double* cx, double* cy, double* cz, double* D,
+                    const double rho[6], double* cx, double* cy, double* cz, double* D,
                     cudaStream_t s) {
-  k_faces64<<<blocks_for(b.n()), kThreads, 0, s>>>(beta, mask, b, ih2, to_dir(dir), cx, cy, cz,
-                                                    D);
+  Val6 r;
+  for (int f = 0; f < 6; ++f) r.v[f] = rho[f];
+  k_faces64<<<blocks_for(b.n()), kThreads, 0, s>>>(beta, mask, b, ih2, r, cx, cy, cz, D);
   add_launches(1);
 }
 
@@ -458,8 +450,6 @@ void launch_rhs64(const double* f, double scale, const double* beta, const uint8
                                                   faces, out);
   add_launches(1);
 }
-
-long long face_count(const Box& b) { return face_offset(b, 5) + (long long)b.nx * b.ny; }
 
 void launch_subbox_bc(const double* parent_u, Box pb, int ox, int oy, int oz, Box sb,
                       double* faces, cudaStream_t s) {

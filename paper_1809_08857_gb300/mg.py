@@ -39,6 +39,7 @@ EXPORTS = [
     "mg_unet_get_params", "mg_unet_set_params", "mg_unet_save", "mg_unet_load", "mg_nn_conv3d",
     "mg_nn_conv3d_wgrad", "mg_warmstart_attach", "mg_warmstart_load", "mg_warmstart_predict",
     "mg_poisson_residual", "mg_solve_screened", "mg_efield",
+    "mg_amr_create", "mg_amr_solve", "mg_amr_residual", "mg_amr_destroy",
 ]
 
 MG_PROBLEM_POISSON = 0
@@ -82,6 +83,10 @@ class Problem(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("kind", ctypes.c_int), ("kappa", ctypes.c_double),
                 ("rhs", ctypes.c_void_p), ("faces", ctypes.c_void_p), ("u", ctypes.c_void_p),
                 ("alpha", ctypes.c_double)]
+
+
+class AmrBox(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("lo", ctypes.c_int * 3), ("n", ctypes.c_int * 3)]
 
 
 class KProf(ctypes.Structure):
@@ -178,6 +183,16 @@ def load():
     lib.mg_warmstart_predict.argtypes = [P, P, P, P, ctypes.POINTER(I)]
     lib.mg_poisson_residual.argtypes = [P, P, P, P]
     lib.mg_poisson_residual.restype = ctypes.c_int
+    PP = ctypes.POINTER(P)
+    lib.mg_amr_create.argtypes = [ctypes.POINTER(Grid), I, ctypes.POINTER(AmrBox), PP, P, P,
+                                  ctypes.POINTER(BC), ctypes.POINTER(Options), P, ctypes.POINTER(P)]
+    lib.mg_amr_create.restype = ctypes.c_int
+    lib.mg_amr_solve.argtypes = [P, I, D, PP, PP, D, ctypes.POINTER(Stats)]
+    lib.mg_amr_solve.restype = ctypes.c_int
+    lib.mg_amr_residual.argtypes = [P, I, D, PP, PP, PP, ctypes.POINTER(D)]
+    lib.mg_amr_residual.restype = ctypes.c_int
+    lib.mg_amr_destroy.argtypes = [P]
+    lib.mg_amr_destroy.restype = None
     for name in ("mg_unet_create", "mg_unet_set_scales", "mg_unet_get_scales",
                  "mg_unet_train_step", "mg_unet_predict", "mg_unet_grads", "mg_unet_num_params",
                  "mg_unet_get_params", "mg_unet_set_params", "mg_unet_save", "mg_unet_load",
@@ -624,3 +639,89 @@ def conv3d_wgrad(dy, x1, x2=None, stream=None):
                                      None if x2 is None else _ptr(x2, torch.bfloat16), c2, n, d, h,
                                      ww, _ptr(dw, torch.float32), _stream_handle(stream)))
     return dw
+
+
+class Amr:
+    """A ratio-2 composite AMR hierarchy (mg_amr_create).
+
+    base_shape (nz, ny, nx) and h: the level-0 grid.  boxes: the refined
+    boxes as (level, lo, shape), lo and shape in (z, y, x) cells of that
+    level.  Per-box arrays are lists with the base box first, then the
+    refined boxes in the given order: eps_r (None, or one CUDA float64 tensor
+    or None per box); rhs, u and r of solve() and residual().  mask and
+    mask_value belong to the base box.  The library works on the stream that
+    is current at construction.
+    """
+
+    def __init__(self, base_shape, h, boxes=(), eps_r=None, mask=None, mask_value=None,
+                 bc_kind=(1, 1, 1, 1, 0, 0), bc_value=(0, 0, 0, 0, 0, 1),
+                 precision=MG_PREC_FP64, nu1=2, nu2=2, max_cycles=100, inner_cycles=1,
+                 stream=None, rte_bc=MG_RTE_BC_DIRICHLET):
+        lib = load()
+        nz, ny, nx = (int(v) for v in base_shape)
+        self.shapes = [(nz, ny, nx)] + [tuple(int(v) for v in b[2]) for b in boxes]
+        g = Grid(nx, ny, nz, float(h), (ctypes.c_double * 3)(0.0, 0.0, 0.0))
+        bc = BC((ctypes.c_int * 6)(*[int(k) for k in bc_kind]),
+                (ctypes.c_double * 6)(*[float(v) for v in bc_value]))
+        opt = Options(nu1, nu2, max_cycles, precision, inner_cycles, 1, 1, rte_bc)
+        arr = (AmrBox * max(1, len(boxes)))()
+        for q, (lev, lo, shape) in enumerate(boxes):
+            arr[q] = AmrBox(int(lev), (ctypes.c_int * 3)(*[int(v) for v in reversed(lo)]),
+                            (ctypes.c_int * 3)(*[int(v) for v in reversed(shape)]))
+        eps = None
+        if eps_r is not None:
+            if len(eps_r) != len(self.shapes):
+                raise ValueError("eps_r needs one entry per box")
+            for t, sh in zip(eps_r, self.shapes):
+                if t is not None and tuple(t.shape) != sh:
+                    raise ValueError("eps_r shape mismatch")
+            eps = (ctypes.c_void_p * len(eps_r))(*[None if t is None else _ptr(t, torch.float64).value
+                                                   for t in eps_r])
+        for t in (mask, mask_value):
+            if t is not None and tuple(t.shape) != self.shapes[0]:
+                raise ValueError("mask shape mismatch")
+        amr = ctypes.c_void_p()
+        st = lib.mg_amr_create(ctypes.byref(g), len(boxes), arr, eps, _ptr(mask, torch.uint8),
+                               _ptr(mask_value, torch.float64), ctypes.byref(bc),
+                               ctypes.byref(opt), _stream_handle(stream), ctypes.byref(amr))
+        _check(st)
+        self._amr = amr
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_amr", None):
+            self._lib.mg_amr_destroy(self._amr)
+            self._amr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arrays(self, ts):
+        if len(ts) != len(self.shapes):
+            raise ValueError("need one array per box")
+        for t, sh in zip(ts, self.shapes):
+            if tuple(t.shape) != sh:
+                raise ValueError("box array shape mismatch")
+        return (ctypes.c_void_p * len(ts))(*[_ptr(t, torch.float64).value for t in ts])
+
+    def solve(self, kind, rhs, u, tol=1e-10, param=0.0, raise_on_nonconvergence=True):
+        """mg_amr_solve: kind "poisson" (rhs = rho), "screened" (param =
+        alpha, rhs = f) or "helmholtz" (param = kappa, rhs = S); u is updated
+        in place.  Returns the stats as a dict."""
+        st = Stats()
+        status = self._lib.mg_amr_solve(self._amr, _KINDS[kind], float(param), self._arrays(rhs),
+                                        self._arrays(u), float(tol), ctypes.byref(st))
+        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        return st.as_dict()
+
+    def residual(self, kind, rhs, u, param=0.0):
+        """mg_amr_residual: per-box composite residuals and ||r||_2 over the
+        valid cells."""
+        r = [torch.empty(sh, dtype=torch.float64, device=u[0].device) for sh in self.shapes]
+        norm = ctypes.c_double()
+        _check(self._lib.mg_amr_residual(self._amr, _KINDS[kind], float(param), self._arrays(rhs),
+                                         self._arrays(u), self._arrays(r), ctypes.byref(norm)))
+        return r, norm.value

@@ -79,3 +79,30 @@ def test_default_options(lib):
     o = mg.default_options()
     assert (o.nu1, o.nu2, o.max_cycles, o.precision, o.inner_cycles, o.concurrency,
             o.no_graphs) == (2, 2, 100, 0, 1, 4, 0)
+
+
+@pytest.mark.parametrize("boxes,msg", [
+    ([(1, (8, 8, 0), (8, 8, 8))], b"footprint"),       # touches the domain boundary
+    ([(1, (8, 8, 8), (8, 8, 8)), (1, (8, 8, 16), (8, 8, 8))], b"apart"),  # siblings too close
+    ([(1, (8, 8, 7), (8, 8, 8))], b"even"),            # odd corner
+    ([(2, (20, 20, 20), (8, 8, 8))], b"footprint"),    # no level-1 parent
+    ([(0, (8, 8, 8), (8, 8, 8))], b"level"),
+])
+def test_amr_create_rejects_bad_hierarchies_without_gpu(lib, boxes, msg):
+    """The nesting rules of the composite hierarchy are checked on the host
+    before any device work (corners and sizes here in x, y, z order)."""
+    from paper_1809_08857_gb300 import mg
+
+    g = mg.Grid(16, 16, 16, 1.0 / 16, (ctypes.c_double * 3)())
+    bc = mg.BC((ctypes.c_int * 6)(1, 1, 1, 1, 0, 0), (ctypes.c_double * 6)(0, 0, 0, 0, 0, 1))
+    arr = (mg.AmrBox * len(boxes))()
+    for q, (lev, lo, n) in enumerate(boxes):
+        arr[q] = mg.AmrBox(lev, (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*n))
+    out = ctypes.c_void_p()
+    st = lib.mg_amr_create(ctypes.byref(g), len(boxes), arr, None, None, None, ctypes.byref(bc),
+                           None, None, ctypes.byref(out))
+    assert st == mg.MG_ERR_INVALID_ARG
+    assert msg in lib.mg_last_error()
+    assert not out.value
+    assert lib.mg_amr_solve(None, 0, 0.0, None, None, 1e-10, None) == mg.MG_ERR_INVALID_ARG
+    lib.mg_amr_destroy(None)
