@@ -341,7 +341,8 @@ typedef struct {
  *               iteration; rte_bc must be MG_RTE_BC_DIRICHLET for Helmholtz.
  * Errors: MG_ERR_INVALID_ARG for a bad hierarchy (mg_last_error says which
  * rule), MG_ERR_UNSUPPORTED for a box grid that does not coarsen to 4096
- * cells or more than 255 refined boxes inside one box.  Synchronises.
+ * cells (or a box of 2^31 cells or more) or more than 254 refined boxes inside
+ * one box.  Synchronises.
  */
 mg_status mg_amr_create(const mg_grid* base, int nbox, const mg_amr_box* boxes,
                         const double* const* eps_r, const uint8_t* mask,

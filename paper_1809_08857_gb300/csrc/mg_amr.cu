@@ -18,6 +18,8 @@
 //    coarse cell next to a covered cell takes the mean of the four fine
 //    fluxes through its face (refluxing), so every flux leaves one cell and
 //    enters another exactly.
+#include <algorithm>
+
 #include "mg_internal.h"
 
 namespace mg {
@@ -25,6 +27,7 @@ namespace mg {
 namespace {
 
 constexpr int kT = 256;
+constexpr int kResidBlocksMax = 152 * 8;  // grid of the residual pass (grid-stride)
 
 inline unsigned blocks_for(long long n) { return (unsigned)((n + kT - 1) / kT); }
 
@@ -66,6 +69,7 @@ __device__ __forceinline__ double tangential_weight(int a, int b, double s1, dou
 constexpr double kWc = 8.0 / 15.0;  // coarse value
 constexpr double kW1 = 2.0 / 3.0;   // first fine cell inward
 constexpr double kW2 = -1.0 / 5.0;  // second fine cell inward
+constexpr uint8_t kShell = 255;      // valid cell with a covered face neighbour
 
 // One thread per boundary-face cell of box q: ghost value across that face.
 __global__ void __launch_bounds__(kT) k_amr_ghost(const AmrDev* __restrict__ D, int q,
@@ -124,90 +128,207 @@ __device__ __forceinline__ void block_sum(double v, double* out) {
   }
 }
 
-// Composite residual r = b - A u on the valid cells of box q (electrode
-// cells 0; covered cells are left to k_amr_average).
-__global__ void __launch_bounds__(kT) k_amr_resid(const AmrDev* __restrict__ D,
-                                                   const int* __restrict__ child_list, int q,
-                                                   AmrResArgs a) {
-  const AmrDev B = D[q];
-  const Box& b = B.b;
-  const long long c = (long long)blockIdx.x * kT + threadIdx.x;
-  double rr = 0.0, rz = 0.0;
-  if (c < b.n()) {
-    int x[3];
-    x[0] = (int)(c % b.nx);
-    const long long jk = c / b.nx;
-    x[1] = (int)(jk % b.ny);
-    x[2] = (int)(jk / b.ny);
-    const bool m = a.mask && a.mask[c];
-    const bool cov = B.cov && B.cov[c];
-    if (m) a.r[c] = 0.0;
-    if (!m && !cov) {
-      const double uc = B.u[c];
-      const double bc = coef(B.beta, c);
-      double acc = a.alpha * uc, accz = 0.0;
-      const long long stride[3] = {1, b.nx, (long long)b.nx * b.ny};
-      const double* cw[3] = {a.cx, a.cy, a.cz};
-      for (int f = 0; f < 6; ++f) {
-        const int ax = f >> 1, side = (f & 1) ? 1 : -1;
-        const int xn = x[ax] + side;
-        if (xn >= 0 && xn < dim(b, ax)) {
-          const long long n = c + side * stride[ax];
-          if (B.cov && B.cov[n]) {
-            // refluxing: mean of the four fine fluxes through this face
-            const AmrDev K = D[child_list[B.child0 + B.cov[n] - 1]];
-            const int kf = side > 0 ? 2 * ax : 2 * ax + 1;  // the child's face
-            const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-            int y[3];
-            y[ax] = side > 0 ? 0 : dim(K.b, ax) - 1;
-            double sum = 0.0;
-            for (int d1 = 0; d1 < 2; ++d1)
-              for (int d2 = 0; d2 < 2; ++d2) {
-                y[t1] = 2 * (x[t1] - K.fo[t1]) + d1;
-                y[t2] = 2 * (x[t2] - K.fo[t2]) + d2;
-                const long long fc = lin3(K.b, y);
-                const double g = K.ghost[face_slot(K.b, kf, y)];
-                const double w = (K.beta || B.beta) ? hmean(coef(K.beta, fc), bc) : 1.0;
-                sum += w * (g - K.u[fc]);
-              }
-            acc += 0.5 * B.ih2 * sum;
-          } else {
-            // same-level face (weight of the face between the lower and the
-            // upper cell is stored at the upper cell)
-            const double w = cw[ax] ? cw[ax][side > 0 ? n : c] : B.ih2;
-            const double un = B.u[n];
-            acc += w * (uc - un);
-            if (a.mask && a.mask[n]) accz -= w * un;
-          }
-        } else if (B.parent < 0) {
-          // domain face: Dirichlet (value lifted into b) or Neumann
-          acc += 2.0 * bc * a.rho[f] * B.ih2 * uc;
-        } else {
-          // coarse-fine face: the ghost
-          const AmrDev P = D[B.parent];
-          int C[3];
-          for (int e = 0; e < 3; ++e) C[e] = B.fo[e] + (x[e] >> 1);
-          C[ax] = side < 0 ? B.fo[ax] - 1 : B.fo[ax] + dim(b, ax) / 2;
-          const double w = (B.beta || P.beta) ? hmean(bc, coef(P.beta, lin3(P.b, C))) : 1.0;
-          acc += w * B.ih2 * (uc - B.ghost[face_slot(b, f, x)]);
+// Output of the residual pass: FP64 natural, or (Split) the FP32 red/black
+// split right-hand side of the box's correction solve.
+template <bool Split>
+__device__ __forceinline__ void store_r(const AmrResArgs& a, unsigned c, unsigned i, unsigned jk,
+                                        unsigned j, unsigned k, double r) {
+  if (Split)
+    a.f32[(i + j + k) & 1][(size_t)jk * a.W + (i >> 1)] = (float)r;
+  else
+    a.r[c] = r;
+}
+
+// Contribution of face F of valid cell (i, j, k) to (A u)_c (acc) and to the
+// zero-guess row (accz) on the general path: domain face, coarse-fine ghost,
+// refluxed face next to a covered cell, or a same-level face.
+template <int F>
+__device__ __forceinline__ void face_general(const AmrDev* __restrict__ D,
+                                             const int* __restrict__ child_list,
+                                             const AmrDev* __restrict__ Bp, const AmrResArgs& a,
+                                             int i, int j, int k, long long c, double uc,
+                                             double bc, double& acc, double& accz) {
+  constexpr int ax = F >> 1, side = (F & 1) ? 1 : -1;
+  constexpr int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+  const Box b = Bp->b;
+  const int x[3] = {i, j, k};
+  const int dims[3] = {b.nx, b.ny, b.nz};
+  const long long stride = ax == 0 ? 1 : ax == 1 ? (long long)b.nx : (long long)b.nx * b.ny;
+  const double* cw = ax == 0 ? a.cx : ax == 1 ? a.cy : a.cz;
+  const int xn = x[ax] + side;
+  if (xn >= 0 && xn < dims[ax]) {
+    const long long n = c + side * stride;
+    const uint8_t kn = Bp->cov ? Bp->cov[n] : 0;
+    if (kn != 0 && kn != kShell) {
+      // refluxing: mean of the four fine fluxes through this face
+      const AmrDev* __restrict__ Kp = D + child_list[Bp->child0 + kn - 1];
+      const Box kb = Kp->b;
+      const int kdims[3] = {kb.nx, kb.ny, kb.nz};
+      constexpr int kf = side > 0 ? 2 * ax : 2 * ax + 1;  // the child's face
+      double sum = 0.0;
+#pragma unroll
+      for (int d1 = 0; d1 < 2; ++d1)
+#pragma unroll
+        for (int d2 = 0; d2 < 2; ++d2) {
+          int y[3];
+          y[ax] = side > 0 ? 0 : kdims[ax] - 1;
+          y[t1] = 2 * (x[t1] - Kp->fo[t1]) + d1;
+          y[t2] = 2 * (x[t2] - Kp->fo[t2]) + d2;
+          const long long fc = lin3(kb, y);
+          const double g = Kp->ghost[face_slot(kb, kf, y)];
+          const double w = (Kp->beta || Bp->beta) ? hmean(coef(Kp->beta, fc), bc) : 1.0;
+          sum += w * (g - Kp->u[fc]);
         }
+      acc += 0.5 * Bp->ih2 * sum;
+    } else {
+      // same-level face (the weight of the face between a cell and its lower
+      // neighbour is stored at the cell)
+      const double w = cw ? cw[side > 0 ? n : c] : Bp->ih2;
+      const double un = Bp->u[n];
+      acc += w * (uc - un);
+      if (a.mask && a.mask[n]) accz -= w * un;
+    }
+  } else if (Bp->parent < 0) {
+    // domain face: Dirichlet (value lifted into b) or Neumann
+    acc += 2.0 * bc * a.rho[F] * Bp->ih2 * uc;
+  } else {
+    // coarse-fine face: the ghost
+    const AmrDev* __restrict__ Pp = D + Bp->parent;
+    int C[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) C[e] = Bp->fo[e] + (x[e] >> 1);
+    C[ax] = side < 0 ? Bp->fo[ax] - 1 : Bp->fo[ax] + dims[ax] / 2;
+    const double w = (Bp->beta || Pp->beta) ? hmean(bc, coef(Pp->beta, lin3(Pp->b, C))) : 1.0;
+    acc += w * Bp->ih2 * (uc - Bp->ghost[face_slot(b, F, x)]);
+  }
+}
+
+// (A u)_c of a boundary or shell cell (general path, out of line so that it
+// does not weigh on the registers of the interior path); accz: the row of
+// the zero guess (electrode neighbours only).
+__device__ __noinline__ double general_row(const AmrDev* __restrict__ D,
+                                           const int* __restrict__ child_list,
+                                           const AmrDev* __restrict__ Bp, const AmrResArgs& a,
+                                           int i, int j, int k, long long c, double uc,
+                                           double* accz_out) {
+  const double bc = coef(Bp->beta, c);
+  double acc = a.alpha * uc, accz = 0.0;
+  face_general<0>(D, child_list, Bp, a, i, j, k, c, uc, bc, acc, accz);
+  face_general<1>(D, child_list, Bp, a, i, j, k, c, uc, bc, acc, accz);
+  face_general<2>(D, child_list, Bp, a, i, j, k, c, uc, bc, acc, accz);
+  face_general<3>(D, child_list, Bp, a, i, j, k, c, uc, bc, acc, accz);
+  face_general<4>(D, child_list, Bp, a, i, j, k, c, uc, bc, acc, accz);
+  face_general<5>(D, child_list, Bp, a, i, j, k, c, uc, bc, acc, accz);
+  *accz_out = accz;
+  return acc;
+}
+
+// Composite residual r = b - A u of the interior cells of box q (every
+// neighbour in the box) that are valid and have no covered neighbour: the
+// plain seven-point row.  Electrode cells get 0; covered and shell cells are
+// left to k_amr_average and k_amr_resid_special.  Grid-stride; r^2 (and the
+// zero-guess row's square) summed per block.
+template <bool Split>
+__global__ void __launch_bounds__(kT) k_amr_resid_interior(const AmrDev* __restrict__ D, int q,
+                                                           const __grid_constant__ AmrResArgs a) {
+  const AmrDev* __restrict__ Bp = D + q;
+  const int nx = Bp->b.nx, ny = Bp->b.ny, nz = Bp->b.nz;
+  const unsigned mx = nx - 2, my = ny - 2;
+  const unsigned m = mx * my * (unsigned)(nz - 2);
+  const unsigned sy = nx, sz = (unsigned)nx * ny;
+  const double* __restrict__ u = Bp->u;
+  const uint8_t* __restrict__ cov = Bp->cov;
+  const double ih2 = Bp->ih2;
+  double rr = 0.0, rz = 0.0;
+  for (unsigned t = blockIdx.x * kT + threadIdx.x; t < m; t += gridDim.x * kT) {
+    const unsigned i = t % mx + 1, t2 = t / mx;
+    const unsigned j = t2 % my + 1, k = t2 / my + 1;
+    const unsigned jk = k * ny + j;
+    const unsigned c = jk * nx + i;
+    if (cov && cov[c]) continue;
+    if (a.mask && a.mask[c]) {
+      store_r<Split>(a, c, i, jk, j, k, 0.0);
+      continue;
+    }
+    double wxm = ih2, wxp = ih2, wym = ih2, wyp = ih2, wzm = ih2, wzp = ih2;
+    if (a.cx) {
+      wxm = a.cx[c];
+      wxp = a.cx[c + 1];
+      wym = a.cy[c];
+      wyp = a.cy[c + sy];
+      wzm = a.cz[c];
+      wzp = a.cz[c + sz];
+    }
+    const double uc = u[c];
+    const double uxm = u[c - 1], uxp = u[c + 1], uym = u[c - sy], uyp = u[c + sy],
+                 uzm = u[c - sz], uzp = u[c + sz];
+    double acc = a.alpha * uc;
+    acc = fma(wxm, uc - uxm, acc);
+    acc = fma(wxp, uc - uxp, acc);
+    acc = fma(wym, uc - uym, acc);
+    acc = fma(wyp, uc - uyp, acc);
+    acc = fma(wzm, uc - uzm, acc);
+    acc = fma(wzp, uc - uzp, acc);
+    const double bb = a.b[c];
+    const double r = bb - acc;
+    store_r<Split>(a, c, i, jk, j, k, r);
+    if (a.partial) rr = fma(r, r, rr);
+    if (a.partial_z) {
+      double z = bb;
+      if (a.mask) {
+        if (a.mask[c - 1]) z += wxm * uxm;
+        if (a.mask[c + 1]) z += wxp * uxp;
+        if (a.mask[c - sy]) z += wym * uym;
+        if (a.mask[c + sy]) z += wyp * uyp;
+        if (a.mask[c - sz]) z += wzm * uzm;
+        if (a.mask[c + sz]) z += wzp * uzp;
       }
-      const double r = a.b[c] - acc;
-      a.r[c] = r;
-      rr = r * r;
-      const double z = a.b[c] - accz;
-      rz = z * z;
+      rz = fma(z, z, rz);
     }
   }
   if (a.partial) block_sum(rr, a.partial + blockIdx.x);
   if (a.partial_z) block_sum(rz, a.partial_z + blockIdx.x);
 }
 
+// The same for the listed cells of box q (its valid boundary cells and the
+// cells next to a covered cell): the general row with domain faces,
+// coarse-fine ghosts and refluxed faces.
+template <bool Split>
+__global__ void __launch_bounds__(kT) k_amr_resid_special(const AmrDev* __restrict__ D,
+                                                          const int* __restrict__ child_list,
+                                                          int q, const __grid_constant__ AmrResArgs a) {
+  const AmrDev* __restrict__ Bp = D + q;
+  const int nx = Bp->b.nx, ny = Bp->b.ny;
+  double rr = 0.0, rz = 0.0;
+  for (unsigned t = blockIdx.x * kT + threadIdx.x; t < a.nspecial; t += gridDim.x * kT) {
+    const unsigned c = a.special[t];
+    const unsigned i = c % nx, jk = c / nx;
+    const unsigned j = jk % ny, k = jk / ny;
+    if (a.mask && a.mask[c]) {
+      store_r<Split>(a, c, i, jk, j, k, 0.0);
+      continue;
+    }
+    double accz;
+    const double acc = general_row(D, child_list, Bp, a, i, j, k, c, Bp->u[c], &accz);
+    const double bb = a.b[c];
+    const double r = bb - acc;
+    store_r<Split>(a, c, i, jk, j, k, r);
+    rr = fma(r, r, rr);
+    const double z = bb - accz;
+    rz = fma(z, z, rz);
+  }
+  if (a.partial) block_sum(rr, a.partial + blockIdx.x);
+  if (a.partial_z) block_sum(rz, a.partial_z + blockIdx.x);
+}
+
 // dst (parent box) = mean of the 8 children in src (child box) over the
-// child's footprint; one thread per footprint cell.
+// child's footprint; one thread per footprint cell.  With Split the parent's
+// values go to its FP32 red/black split arrays (dst0, dst1, row width W).
+template <bool Split>
 __global__ void __launch_bounds__(kT) k_amr_average(Box cb, int fx, int fy, int fz,
                                                      const double* __restrict__ src, Box pb,
-                                                     double* __restrict__ dst) {
+                                                     double* __restrict__ dst, float* dst0,
+                                                     float* dst1, int W) {
   const Box fb{cb.nx / 2, cb.ny / 2, cb.nz / 2};
   const long long t = (long long)blockIdx.x * kT + threadIdx.x;
   if (t >= fb.n()) return;
@@ -218,7 +339,12 @@ __global__ void __launch_bounds__(kT) k_amr_average(Box cb, int fx, int fy, int 
   for (int dk = 0; dk < 2; ++dk)
     for (int dj = 0; dj < 2; ++dj)
       for (int di = 0; di < 2; ++di) s += src[lin(cb, 2 * I + di, 2 * J + dj, 2 * K + dk)];
-  dst[lin(pb, fx + I, fy + J, fz + K)] = 0.125 * s;
+  const int i = fx + I, j = fy + J, k = fz + K;
+  if (Split)
+    (((i + j + k) & 1) ? dst1 : dst0)[((long long)k * pb.ny + j) * W + (i >> 1)] =
+        (float)(0.125 * s);
+  else
+    dst[lin(pb, i, j, k)] = 0.125 * s;
 }
 
 // FP32 red/black split copy of r: colour (i+j+k)&1, packed row width W.
@@ -290,18 +416,49 @@ void launch_amr_ghost(const AmrDev* D, int q, const Box& b, double* ghost, cudaS
   add_launches(1);
 }
 
-unsigned amr_resid_blocks(const Box& b) { return blocks_for(b.n()); }
+static unsigned capped_blocks(long long n) {
+  return (unsigned)std::min<long long>(blocks_for(n), kResidBlocksMax);
+}
+
+unsigned amr_resid_blocks(const Box& b, long long nspecial) {
+  const long long m = (long long)std::max(b.nx - 2, 0) * std::max(b.ny - 2, 0) *
+                      std::max(b.nz - 2, 0);
+  return capped_blocks(m) + capped_blocks(nspecial);
+}
 
 void launch_amr_resid(const AmrDev* D, const int* child_list, int q, const Box& b,
                       const AmrResArgs& a, cudaStream_t s) {
-  k_amr_resid<<<blocks_for(b.n()), kT, 0, s>>>(D, child_list, q, a);
-  add_launches(1);
+  const long long m = (long long)std::max(b.nx - 2, 0) * std::max(b.ny - 2, 0) *
+                      std::max(b.nz - 2, 0);
+  const unsigned gi = capped_blocks(m), gs = capped_blocks(a.nspecial);
+  AmrResArgs as = a;  // the list kernel's partial sums follow the interior ones
+  if (a.partial) as.partial = a.partial + gi;
+  if (a.partial_z) as.partial_z = a.partial_z + gi;
+  if (gi) {
+    if (a.f32[0])
+      k_amr_resid_interior<true><<<gi, kT, 0, s>>>(D, q, a);
+    else
+      k_amr_resid_interior<false><<<gi, kT, 0, s>>>(D, q, a);
+    add_launches(1);
+  }
+  if (gs) {
+    if (a.f32[0])
+      k_amr_resid_special<true><<<gs, kT, 0, s>>>(D, child_list, q, as);
+    else
+      k_amr_resid_special<false><<<gs, kT, 0, s>>>(D, child_list, q, as);
+    add_launches(1);
+  }
 }
 
 void launch_amr_average(const Box& cb, const int fo[3], const double* src, const Box& pb,
-                        double* dst, cudaStream_t s) {
+                        double* dst, float* dst0, float* dst1, int W, cudaStream_t s) {
   const Box fb{cb.nx / 2, cb.ny / 2, cb.nz / 2};
-  k_amr_average<<<blocks_for(fb.n()), kT, 0, s>>>(cb, fo[0], fo[1], fo[2], src, pb, dst);
+  if (dst0)
+    k_amr_average<true><<<blocks_for(fb.n()), kT, 0, s>>>(cb, fo[0], fo[1], fo[2], src, pb,
+                                                          nullptr, dst0, dst1, W);
+  else
+    k_amr_average<false><<<blocks_for(fb.n()), kT, 0, s>>>(cb, fo[0], fo[1], fo[2], src, pb,
+                                                           dst, nullptr, nullptr, 0);
   add_launches(1);
 }
 

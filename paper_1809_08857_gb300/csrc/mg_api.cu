@@ -1104,7 +1104,7 @@ namespace {
 // smooth correction whose coarse part is zero, (2/3) e_1 - (1/5) e_2.  It
 // only affects the convergence rate of the iteration, not its fixed point.
 constexpr double kBoxRho = 1.0 / 6.0;
-constexpr int kMaxChildren = 255;
+constexpr int kMaxChildren = 254;
 
 struct AmrBox {
   int level = 0, parent = -1;
@@ -1114,13 +1114,16 @@ struct AmrBox {
   mg_ctx* ctx = nullptr;
   std::vector<int> children;
   int child0 = 0;
-  uint8_t* cov = nullptr;  // 0 valid, k + 1 covered by child k (null: no children)
+  uint8_t* cov = nullptr;  // 0 valid, k + 1 covered by child k, 255 valid next to a
+                           // covered cell (null: no children)
   double* b = nullptr;     // right-hand side with lifts
   double* r = nullptr;     // composite residual
   double* ghost = nullptr; // level >= 1: coarse-fine ghosts, packed per face
   double* delta = nullptr; // level >= 1 with children: increment passed on
   double* e64 = nullptr;   // FP64 mode: correction
   long long poff = 0;      // first partial sum of this box
+  unsigned* special = nullptr;  // valid boundary cells and cells next to a covered cell
+  unsigned nspecial = 0;
   mg::Box box() const { return mg::Box{n[0], n[1], n[2]}; }
 };
 
@@ -1180,6 +1183,8 @@ bool box_overlap(const int lo[3], const int hi[3], const int olo[3], const int o
 // Levels, parents, footprints and the nesting rules (host only).
 mg_status amr_layout(mg_amr* a, const mg_grid* g, int nbox, const mg_amr_box* boxes) {
   a->box.resize((size_t)nbox + 1);
+  if ((long long)g->nx * g->ny * g->nz >= (1ll << 31))
+    return fail(MG_ERR_UNSUPPORTED, "base grid with 2^31 cells or more");
   AmrBox& B0 = a->box[0];
   B0.n[0] = g->nx;
   B0.n[1] = g->ny;
@@ -1192,6 +1197,8 @@ mg_status amr_layout(mg_amr* a, const mg_grid* g, int nbox, const mg_amr_box* bo
       return fail(MG_ERR_INVALID_ARG, "refined box level must be in 1..20");
     B.level = in.level;
     B.h = g->h / (double)(1 << in.level);
+    if ((long long)in.n[0] * in.n[1] * in.n[2] >= (1ll << 31))
+      return fail(MG_ERR_UNSUPPORTED, "refined box with 2^31 cells or more");
     for (int d = 0; d < 3; ++d) {
       if (in.n[d] < 2 || (in.n[d] & 1) || (in.lo[d] & 1))
         return fail(MG_ERR_INVALID_ARG, "refined box corners and sizes must be even, sizes >= 2");
@@ -1225,7 +1232,7 @@ mg_status amr_layout(mg_amr* a, const mg_grid* g, int nbox, const mg_amr_box* bo
     for (int d = 0; d < 3; ++d) B.fo[d] = flo[d] - P.lo[d];
     P.children.push_back(q);
     if ((int)P.children.size() > kMaxChildren)
-      return fail(MG_ERR_UNSUPPORTED, "more than 255 refined boxes inside one box");
+      return fail(MG_ERR_UNSUPPORTED, "more than 254 refined boxes inside one box");
     for (int o = 1; o <= nbox; ++o) {
       const AmrBox& O = a->box[o];
       if (o == q || O.level != B.level) continue;
@@ -1298,8 +1305,10 @@ mg_status amr_alloc(mg_amr* a) {
     if (a->opt.precision == MG_PREC_FP64) MG_TRY(a->alloc(&B.e64, n));
     B.child0 = (int)clist.size();
     for (int k : B.children) clist.push_back(k);
+    std::vector<uint8_t> cov_host;
     if (!B.children.empty()) {
-      std::vector<uint8_t> cov(n, 0);
+      std::vector<uint8_t>& cov = cov_host;
+      cov.assign(n, 0);
       for (size_t t = 0; t < B.children.size(); ++t) {
         const AmrBox& K = a->box[B.children[t]];
         for (int k = 0; k < K.n[2] / 2; ++k)
@@ -1308,11 +1317,43 @@ mg_status amr_alloc(mg_amr* a) {
               cov[((size_t)(K.fo[2] + k) * b.ny + K.fo[1] + j) * b.nx + K.fo[0] + i] =
                   (uint8_t)(t + 1);
       }
+      // valid cells with a covered face neighbour take the refluxed row
+      const long long st[3] = {1, b.nx, (long long)b.nx * b.ny};
+      for (int k = 0; k < b.nz; ++k)
+        for (int j = 0; j < b.ny; ++j)
+          for (int i = 0; i < b.nx; ++i) {
+            const size_t c = ((size_t)k * b.ny + j) * b.nx + i;
+            if (cov[c]) continue;
+            const int x[3] = {i, j, k}, m[3] = {b.nx, b.ny, b.nz};
+            for (int d = 0; d < 3; ++d) {
+              if (x[d] > 0 && cov[c - st[d]] && cov[c - st[d]] != 255) cov[c] = 255;
+              if (x[d] + 1 < m[d] && cov[c + st[d]] && cov[c + st[d]] != 255) cov[c] = 255;
+            }
+          }
       MG_TRY(a->alloc(&B.cov, n));
       MG_CUDA(cudaMemcpy(B.cov, cov.data(), n, cudaMemcpyHostToDevice));
     }
+    // cells that take the general row: valid cells on the box boundary and
+    // valid cells next to a covered cell
+    {
+      std::vector<unsigned> sp;
+      for (int k = 0; k < b.nz; ++k)
+        for (int j = 0; j < b.ny; ++j)
+          for (int i = 0; i < b.nx; ++i) {
+            const size_t c = ((size_t)k * b.ny + j) * b.nx + i;
+            const uint8_t kc = B.cov ? cov_host[c] : 0;
+            const bool edge = i == 0 || j == 0 || k == 0 || i == b.nx - 1 || j == b.ny - 1 ||
+                              k == b.nz - 1;
+            if (kc == 255 || (kc == 0 && edge)) sp.push_back((unsigned)c);
+          }
+      B.nspecial = (unsigned)sp.size();
+      MG_TRY(a->alloc(&B.special, sp.size()));
+      if (!sp.empty())
+        MG_CUDA(cudaMemcpy(B.special, sp.data(), sizeof(unsigned) * sp.size(),
+                           cudaMemcpyHostToDevice));
+    }
     B.poff = a->npartial;
-    a->npartial += mg::amr_resid_blocks(b);
+    a->npartial += mg::amr_resid_blocks(b, B.nspecial);
   }
   if (!clist.empty()) {
     MG_TRY(a->alloc(&a->child_list, clist.size()));
@@ -1406,9 +1447,18 @@ mg_status amr_rhs(mg_amr* a, Kind kind, double scale, const double* const* rhs) 
 
 // Composite residual of every box of level >= lmin, finest level first;
 // with norm, ||r||^2 over the valid cells into norm_host[1] (and the
-// zero-guess ||b||^2 into norm_host[0] with znorm), asynchronously.
-mg_status amr_pass(mg_amr* a, Kind kind, double alpha, int lmin, bool norm, bool znorm) {
+// zero-guess ||b||^2 into norm_host[0] with znorm), asynchronously.  With
+// split_base the base box's residual goes straight to the FP32 split
+// right-hand side of its correction solve (mixed precision).
+mg_status amr_pass(mg_amr* a, Kind kind, double alpha, int lmin, bool norm, bool znorm,
+                   bool split_base = false) {
   cudaStream_t s = a->stream;
+  LevelWork* X0 = nullptr;
+  if (split_base && lmin == 0) {
+    Work* w;
+    MG_TRY(get_work(a->box[0].ctx, 0, &w));
+    X0 = &w->lw[0];
+  }
   for (int lev = a->nlev - 1; lev >= lmin; --lev)
     for (size_t q = 0; q < a->box.size(); ++q) {
       AmrBox& B = a->box[q];
@@ -1427,12 +1477,21 @@ mg_status amr_pass(mg_amr* a, Kind kind, double alpha, int lmin, bool norm, bool
       for (int f = 0; f < 6; ++f) ra.rho[f] = q == 0 ? face_rho(B.ctx, kind, alpha, f, B.h) : 0.0;
       ra.b = B.b;
       ra.r = B.r;
+      const bool split = q == 0 && X0;
+      if (split) {
+        ra.f32[0] = X0->f32[0];
+        ra.f32[1] = X0->f32[1];
+        ra.W = L.W;
+      }
       ra.partial = norm ? a->partial + B.poff : nullptr;
       ra.partial_z = znorm ? a->partial + a->npartial + B.poff : nullptr;
+      ra.special = B.special;
+      ra.nspecial = B.nspecial;
       mg::launch_amr_resid(a->dev, a->child_list, (int)q, b, ra, s);
       for (int k : B.children) {
         const AmrBox& K = a->box[k];
-        mg::launch_amr_average(K.box(), K.fo, K.r, b, B.r, s);
+        mg::launch_amr_average(K.box(), K.fo, K.r, b, B.r, split ? X0->f32[0] : nullptr,
+                               split ? X0->f32[1] : nullptr, L.W, s);
       }
     }
   if (norm) {
@@ -1446,7 +1505,8 @@ mg_status amr_pass(mg_amr* a, Kind kind, double alpha, int lmin, bool norm, bool
 
 // Correction solve on box q from its residual, added to the box and passed
 // on to every box refining it.
-mg_status amr_correct(mg_amr* a, Kind kind, double alpha, int q, double* const* u) {
+mg_status amr_correct(mg_amr* a, Kind kind, double alpha, int q, double* const* u,
+                      bool rhs_split) {
   AmrBox& B = a->box[q];
   mg_ctx* c = B.ctx;
   cudaStream_t s = a->stream;
@@ -1461,7 +1521,7 @@ mg_status amr_correct(mg_amr* a, Kind kind, double alpha, int q, double* const* 
     const double* Minv;
     MG_TRY(coarse_inverse(c, kind, alpha, &Minv));
     LevelWork& X = w->lw[0];
-    mg::launch_amr_split(L.b, L.W, B.r, X.f32[0], X.f32[1], s);
+    if (!rhs_split) mg::launch_amr_split(L.b, L.W, B.r, X.f32[0], X.f32[1], s);
     MG_CUDA(cudaEventRecord(a->ev, s));
     MG_CUDA(cudaStreamWaitEvent(w->s, a->ev, 0));
     for (int ic = 0; ic < a->opt.inner_cycles; ++ic)
@@ -1522,7 +1582,8 @@ mg_status amr_solve(mg_amr* a, int kind_in, double param, const double* const* r
                           L0.b.n(), u[0], s);
   MG_TRY(amr_upload(a, kind, u));
   MG_TRY(amr_rhs(a, kind, scale, rhs));
-  MG_TRY(amr_pass(a, kind, alpha, 0, true, true));
+  const bool mixed = a->opt.precision == MG_PREC_MIXED;
+  MG_TRY(amr_pass(a, kind, alpha, 0, true, true, mixed));
   MG_CUDA(cudaStreamSynchronize(s));
   double bnorm = std::sqrt(a->norm_host[0]);
   double rel = std::isfinite(bnorm) ? std::sqrt(a->norm_host[1]) / (bnorm > 0.0 ? bnorm : 1.0)
@@ -1534,9 +1595,10 @@ mg_status amr_solve(mg_amr* a, int kind_in, double param, const double* const* r
     for (int l = 0; l < a->nlev; ++l) {
       if (l > 0) MG_TRY(amr_pass(a, kind, alpha, l, false, false));
       for (size_t q = 0; q < a->box.size(); ++q)
-        if (a->box[q].level == l) MG_TRY(amr_correct(a, kind, alpha, (int)q, u));
+        if (a->box[q].level == l)
+          MG_TRY(amr_correct(a, kind, alpha, (int)q, u, q == 0 && mixed));
     }
-    MG_TRY(amr_pass(a, kind, alpha, 0, true, false));
+    MG_TRY(amr_pass(a, kind, alpha, 0, true, false, mixed));
     MG_CUDA(cudaStreamSynchronize(s));
     rel = std::sqrt(a->norm_host[1]) / bnorm;
     ++cyc;
@@ -1547,7 +1609,8 @@ mg_status amr_solve(mg_amr* a, int kind_in, double param, const double* const* r
     for (size_t q = 0; q < a->box.size(); ++q) {
       const AmrBox& B = a->box[q];
       if (B.level != lev) continue;
-      mg::launch_amr_average(B.box(), B.fo, u[q], a->box[B.parent].box(), u[B.parent], s);
+      mg::launch_amr_average(B.box(), B.fo, u[q], a->box[B.parent].box(), u[B.parent], nullptr,
+                             nullptr, 0, s);
     }
   MG_TRY(check_launch());
   if (st) {

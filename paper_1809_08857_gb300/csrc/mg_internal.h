@@ -217,6 +217,7 @@ struct AmrDev {
   const double* beta;   // cell coefficient (nullable: 1)
   const double* ghost;  // level >= 1: coarse-fine ghost values, packed per face
   const uint8_t* cov;   // nullable (no children): 0 valid, k + 1 covered by child k
+                        // (k < 254), 255 valid next to a covered cell
 };
 
 struct AmrResArgs {
@@ -228,21 +229,29 @@ struct AmrResArgs {
   const uint8_t* mask;  // electrode cells (base box only, nullable)
   double rho[6];        // base box: domain face factors (1 Dirichlet, 0 Neumann)
   const double* b;      // right-hand side with lifts
-  double* r;            // composite residual (valid and electrode cells)
+  double* r;            // composite residual (valid and electrode cells), or
+  float* f32[2];        // (when f32[0] is set) its FP32 red/black split copy
+  int W;                // packed row width of f32
   double* partial;      // nullable: per-block sums of r^2 over the valid cells
   double* partial_z;    // nullable: the same for the zero guess (electrode
                         // values kept)
+  const unsigned* special;  // the box's valid boundary cells and the valid
+  unsigned nspecial;        // cells next to a covered cell (general rows)
 };
 
 // Ghost values of box q (level >= 1) from its own and its parent's iterate.
 void launch_amr_ghost(const AmrDev* D, int q, const Box& b, double* ghost, cudaStream_t s);
-// Composite residual of box q; children's ghosts must be current.
+// Composite residual of box q: the plain interior rows, then the listed
+// special cells (grid-stride kernels, amr_resid_blocks(b, nspecial) partial
+// sums in all); children's ghosts must be current.
 void launch_amr_resid(const AmrDev* D, const int* child_list, int q, const Box& b,
                       const AmrResArgs& a, cudaStream_t s);
-unsigned amr_resid_blocks(const Box& b);
-// dst (parent cells over the child's footprint fo) = mean of the 8 children.
+unsigned amr_resid_blocks(const Box& b, long long nspecial);
+// dst (parent cells over the child's footprint fo) = mean of the 8 children;
+// with dst0 set, into the parent's FP32 red/black split arrays (dst0, dst1,
+// row width W) instead.
 void launch_amr_average(const Box& cb, const int fo[3], const double* src, const Box& pb,
-                        double* dst, cudaStream_t s);
+                        double* dst, float* dst0, float* dst1, int W, cudaStream_t s);
 // FP32 red/black split copy of an FP64 field (packed row width W).
 void launch_amr_split(const Box& b, int W, const double* r, float* f0, float* f1, cudaStream_t s);
 // u += e on free cells (e split FP32 (e0, e1, width W) or FP64 e64); delta

@@ -77,10 +77,13 @@ def streamer_shell(n, seed, radius=0.02, z0=0.4, z1=0.8, axis_xy=(0.5, 0.5),
 
 
 def streamer_shell_box(shape, h, origin, seed, radius=0.02, z0=0.4, z1=0.8, axis_xy=(0.5, 0.5),
-                       amplitude=1e-3, noise=0.1):
+                       amplitude=1e-3, noise=0.1, thickness=None):
     """The streamer shell sampled on a box of the given shape (nz, ny, nx),
-    cell size h and lower corner origin (x, y, z): cells within h of the
-    surface carry amplitude * eps0 / h^2 * exp(noise * xi)."""
+    cell size h and lower corner origin (x, y, z): cells within t of the
+    surface carry amplitude * eps0 / t^2 * exp(noise * xi), t = thickness
+    (default h; a fixed t gives one shell sampled alike on every level of an
+    AMR hierarchy)."""
+    t = h if thickness is None else float(thickness)
     rng = np.random.default_rng(seed)
     nz, ny, nx = shape
     x = origin[0] + (np.arange(nx) + 0.5) * h
@@ -89,10 +92,10 @@ def streamer_shell_box(shape, h, origin, seed, radius=0.02, z0=0.4, z1=0.8, axis
     shell = np.zeros(shape, dtype=bool)
     for k in range(nz):
         d = _shell_distance_slab(x, y, z[k], axis_xy, z0, z1, radius)
-        shell[k] = d <= h
+        shell[k] = d <= t
     rho = np.zeros(shape)
     cnt = int(shell.sum())
-    rho[shell] = amplitude / h**2 * np.exp(noise * rng.standard_normal(cnt))
+    rho[shell] = amplitude / t**2 * np.exp(noise * rng.standard_normal(cnt))
     return rho * EPS0
 
 
@@ -123,6 +126,35 @@ def subbox_layout(n_parent, count, seed, sizes=(32, 48, 64, 96, 128), lo=0.1, hi
         o = rng.integers(lo_c, hi_c + 1, size=3)
         out.append(((int(o[0]), int(o[1]), int(o[2])), (m, m, m)))
     return out
+
+
+def streamer_amr_layout(n0):
+    """Nested refined boxes (ratio 2) around the streamer channel and head of
+    streamer_shell on a base grid of n0^3 cells (n0 a multiple of 64), as the
+    refinement around streamer heads and space-charge layers of Sec. 4:
+      level 1 (h0/2): x, y in 0.5 +- 1/16, z in [0.34375, 0.875];
+      level 2 (h0/4): x, y in 0.5 +- 1/32, z in [0.703125, 0.859375];
+      level 3 (h0/8): x, y in 0.5 +- 1/64, z in [0.765625, 0.8359375].
+    Returns (level, lo, shape) per box, lo and shape in (z, y, x) cells of
+    that level."""
+    spec = ((1, 0.0625, 0.34375, 0.875), (2, 0.03125, 0.703125, 0.859375),
+            (3, 0.015625, 0.765625, 0.8359375))
+    boxes = []
+    for lev, half, z0, z1 in spec:
+        m = n0 * 2 ** lev
+        lo_xy = int(round((0.5 - half) * m))
+        n_xy = int(round(2 * half * m))
+        lo_z = int(round(z0 * m)) // 2 * 2
+        n_z = (int(round(z1 * m)) - lo_z) // 2 * 2
+        boxes.append((lev, (lo_z, lo_xy, lo_xy), (n_z, n_xy, n_xy)))
+    return boxes
+
+
+def amr_box_origin(h0, box):
+    """Lower corner (x, y, z) and cell size of a refined box (level, lo, shape)."""
+    lev, lo, _ = box
+    h = h0 / 2 ** lev
+    return (lo[2] * h, lo[1] * h, lo[0] * h), h
 
 
 def needle_mask(n, tip_z=0.8, tip_radius_cells=5.0, half_angle_deg=10.0, axis_xy=(0.5, 0.5)):
