@@ -48,6 +48,8 @@ def parse():
                     help="keep --inner-cycles and V(2,2) instead of the autotuned choice")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-amr", action="store_true",
+                    help="skip the composite AMR solve among the extras")
     return ap.parse_args()
 
 
@@ -302,6 +304,51 @@ def measure_extras(solver, rho, eps, phi, n, dev):
                                "alpha": alpha}}
 
 
+def measure_amr(dev, n0=256, reps=3):
+    """One composite AMR Poisson solve (outside the timed region): the base
+    grid n0^3 with the dielectric slab and three nested refined levels around
+    the streamer channel and head (workloads.streamer_amr_layout), the shell
+    charge sampled on every level, from zero to 1e-10 in mixed precision with
+    two inner V-cycles per box and iteration; device time per solve (CUDA
+    events), FAC iterations, valid cells."""
+    import numpy as np
+    import torch
+
+    from paper_1809_08857_gb300 import mg, workloads as W
+
+    h0 = 1.0 / n0
+    boxes = W.streamer_amr_layout(n0)
+    eps = [torch.from_numpy(W.dielectric_slab(n0)).to(dev)] + [None] * len(boxes)
+    rho = [W.streamer_shell_box((n0,) * 3, h0, (0, 0, 0), 0, thickness=h0)]
+    for q, b in enumerate(boxes):
+        o, h = W.amr_box_origin(h0, b)
+        rho.append(W.streamer_shell_box(b[2], h, o, q + 1, thickness=h0))
+    rho = [torch.from_numpy(r).to(dev) for r in rho]
+    A = mg.Amr((n0,) * 3, h0, boxes, eps_r=eps, bc_kind=W.GAP_BC_KIND, bc_value=W.GAP_BC_VALUE,
+               precision=mg.MG_PREC_MIXED, inner_cycles=2)
+    u = [torch.zeros(s, dtype=torch.float64, device=dev) for s in A.shapes]
+    A.solve("poisson", rho, u, tol=TOL)  # first call builds the coarse inverses
+    st = None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        for t in u:
+            t.zero_()
+        st = A.solve("poisson", rho, u, tol=TOL)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    A.close()
+    cells = sum(int(np.prod(s)) for s in A.shapes)
+    valid = cells - sum(int(np.prod(b[2])) // 8 for b in boxes)
+    return {"workload": f"streamer AMR: base {n0}^3 + 3 nested ratio-2 levels, composite "
+                        "Poisson (dielectric slab, shell charge) 1e-10 from zero",
+            "ms": round(ms, 2), "solves_per_s": round(1e3 / ms, 2),
+            "fac_iterations": st["cycles"], "rel_resid": st["rel_resid"], "cells": cells,
+            "valid_cells": valid, "valid_cells_per_s": round(valid * 1e3 / ms, 1)}
+
+
 # ---------------------------------------------------------------- arms
 
 
@@ -453,6 +500,8 @@ def run_ours(args):
     solver.set_options(concurrency=conc)
     solver.profile(False)
     extras = measure_extras(solver, rho, eps, phi, n, dev)
+    if not args.no_amr:
+        extras["amr_solve"] = measure_amr(dev)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

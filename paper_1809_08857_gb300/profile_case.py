@@ -5,7 +5,11 @@
       128 MiB each, larger than the 129 MB L2), concurrency 1, no graphs, so
       kernel launches are individually visible;
   python -m paper_1809_08857_gb300.profile_case --case unet64
-      one U-Net training step on a batch of 2 crops of 64^3.
+      one U-Net training step on a batch of 2 crops of 64^3;
+  python -m paper_1809_08857_gb300.profile_case --case amr256
+      one composite AMR Poisson solve: base 256^3 with three nested refined
+      levels around the streamer head (workloads.streamer_amr_layout), mixed
+      precision, two inner V-cycles, from zero to 1e-10.
 """
 import argparse
 import os
@@ -43,11 +47,30 @@ def unet64():
     net.close()
 
 
+def amr256():
+    n0 = 256
+    h0 = 1.0 / n0
+    boxes = W.streamer_amr_layout(n0)
+    eps = [torch.from_numpy(W.dielectric_slab(n0)).cuda()] + [None] * len(boxes)
+    rho = [W.streamer_shell_box((n0,) * 3, h0, (0, 0, 0), 0, thickness=h0)]
+    for q, b in enumerate(boxes):
+        o, h = W.amr_box_origin(h0, b)
+        rho.append(W.streamer_shell_box(b[2], h, o, q + 1, thickness=h0))
+    rho = [torch.from_numpy(r).cuda() for r in rho]
+    a = mg.Amr((n0,) * 3, h0, boxes, eps_r=eps, bc_kind=W.GAP_BC_KIND, bc_value=W.GAP_BC_VALUE,
+               precision=mg.MG_PREC_MIXED, inner_cycles=2)
+    u = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in a.shapes]
+    st = a.solve("poisson", rho, u, tol=1e-10)
+    torch.cuda.synchronize()
+    print("fac iterations", st["cycles"], "rel", st["rel_resid"])
+    a.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["solve256", "unet64"], required=True)
+    ap.add_argument("--case", choices=["solve256", "unet64", "amr256"], required=True)
     args = ap.parse_args()
-    {"solve256": solve256, "unet64": unet64}[args.case]()
+    {"solve256": solve256, "unet64": unet64, "amr256": amr256}[args.case]()
 
 
 if __name__ == "__main__":

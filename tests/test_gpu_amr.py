@@ -236,3 +236,41 @@ def test_bad_hierarchies_are_rejected(mg):
         A.solve("helmholtz", u, [torch.zeros_like(t) for t in u], param=3.0)
     assert e.value.status == mg.MG_ERR_UNSUPPORTED
     A.close()
+
+
+@pytest.mark.parametrize("n0", [64, 128])
+def test_streamer_hierarchy_meets_tol_by_the_oracle(mg, n0):
+    """The nested streamer-head hierarchy of the benchmark (three refined
+    levels around the channel and head, dielectric slab on the base, shell
+    charge sampled on every level) at a reduced base size, mixed precision
+    with two inner V-cycles as timed: the oracle's FP64 composite residual of
+    the GPU solution meets the tolerance, and the library's residual norm of
+    that solution agrees with the oracle's."""
+    from paper_1809_08857_gb300 import workloads as W
+
+    h0 = 1.0 / n0
+    boxes = W.streamer_amr_layout(n0)
+    eps = [W.dielectric_slab(n0)] + [None] * len(boxes)
+    rho = [W.streamer_shell_box((n0,) * 3, h0, (0, 0, 0), 0, thickness=h0)]
+    for q, b in enumerate(boxes):
+        o, h = W.amr_box_origin(h0, b)
+        rho.append(W.streamer_shell_box(b[2], h, o, q + 1, thickness=h0))
+    A = mg.Amr((n0,) * 3, h0, boxes, eps_r=[cuda(e) for e in eps], bc_kind=W.GAP_BC_KIND,
+               bc_value=W.GAP_BC_VALUE, precision=1, inner_cycles=2)
+    u = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in A.shapes]
+    rhs = [cuda(r) for r in rho]
+    st = A.solve("poisson", rhs, u, tol=TOL)
+    _, gpu_norm = A.residual("poisson", rhs, u)
+    A.close()
+    assert st["converged"] and st["cycles"] <= 12
+    H = oamr.Hierarchy((n0,) * 3, h0, boxes, beta=eps, bc_kind=W.GAP_BC_KIND,
+                       bc_value=W.GAP_BC_VALUE)
+    f = [r / oracle.EPS0 for r in rho]
+    un = [t.cpu().numpy() for t in u]
+    _, rn = H.residual(f, un)
+    bn = H.rhs_norm(f)
+    assert rn <= 1.01 * TOL * bn
+    assert abs(gpu_norm - rn) <= 1e-3 * rn
+    back = H.average_down(un)
+    for q in range(len(un)):
+        np.testing.assert_allclose(un[q], back[q], rtol=0, atol=1e-14 * np.abs(back[q]).max())
