@@ -205,7 +205,8 @@ def prolong_add(ec, cmask, bc_kind, uf, fmask=None):
 
 
 def coarsen(beta_f, mask_f, shape_f):
-    """Coarse (beta, mask): masked iff all 8 children masked, beta = mean of free children."""
+    """Coarse (beta, mask): masked iff at least 3 of the 8 children are masked,
+    beta = mean of the free children."""
     lib = _load()
     nz, ny, nx = shape_f
     cshape = (nz // 2, ny // 2, nx // 2)

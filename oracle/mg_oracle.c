@@ -19,8 +19,10 @@
  *     electrode value held at the masked cell's centre;
  *   - Dirichlet domain face with value g: ghost 2g - u_c, so w = 2 beta_c;
  *   - Neumann domain face: homogeneous, no flux;
- *   - coarse grids: cell masked iff its 8 children are, beta = mean of the
- *     free children, residual restricted by the 8-child average, correction
+ *   - coarse grids: cell masked iff at least 3 of its 8 children are (a
+ *     reading: the paper gives no coarsening rule; the rule shapes the coarse
+ *     operators, not the converged answer), beta = mean of the free
+ *     children, residual restricted by the 8-child average, correction
  *     prolonged trilinearly; the coarsest grid is solved by dense Cholesky.
  * The paper's coarse solver is BiCGStab; a dense factor on the small coarsest
  * grid reaches the same discrete answer.
@@ -223,8 +225,8 @@ void or_prolong_add(const or_grid* cg, const uint8_t* cmask, const double* ec,
       }
 }
 
-/* Coarse beta and mask: masked iff all 8 children masked; beta = mean of the
- * free children's beta. */
+/* Coarse beta and mask: masked iff at least 3 of the 8 children are masked;
+ * beta = mean of the free children's beta. */
 void or_coarsen(const or_grid* fg, const double* bf, const uint8_t* mf,
                 const or_grid* cg, double* bcoarse, uint8_t* mcoarse) {
   for (int K = 0; K < cg->nz; ++K)
@@ -239,7 +241,7 @@ void or_coarsen(const or_grid* fg, const double* bf, const uint8_t* mf,
           ++nfree;
         }
         long C = idx(cg, I, J, K);
-        if (mcoarse) mcoarse[C] = nfree == 0;
+        if (mcoarse) mcoarse[C] = 8 - nfree >= 3;
         if (bcoarse) bcoarse[C] = nfree ? s / nfree : 1.0;
       }
 }

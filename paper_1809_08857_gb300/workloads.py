@@ -173,6 +173,68 @@ def needle_mask(n, tip_z=0.8, tip_radius_cells=5.0, half_angle_deg=10.0, axis_xy
     return mask
 
 
+def branching_channels(seed, tip=(0.5, 0.5, 0.8), nchan=3):
+    """Axis segments of streamer channels leaving a needle tip: nchan primary
+    channels going down from the tip at tilt U[10, 30] degrees from -z and
+    azimuth 2 pi c / nchan + U[-0.3, 0.3], length U[0.12, 0.2]; each splits at
+    its end into two daughters of length U[0.08, 0.15], turned by +-U[10, 25]
+    degrees in the azimuth.  Returns a list of (start, end) points (x, y, z)."""
+    rng = np.random.default_rng(seed)
+    segs = []
+
+    def direction(tilt, az):
+        return np.array([np.sin(tilt) * np.cos(az), np.sin(tilt) * np.sin(az), -np.cos(tilt)])
+
+    p0 = np.asarray(tip, dtype=np.float64)
+    for c in range(nchan):
+        tilt = np.deg2rad(rng.uniform(10.0, 30.0))
+        az = 2.0 * np.pi * c / nchan + rng.uniform(-0.3, 0.3)
+        p1 = p0 + rng.uniform(0.12, 0.2) * direction(tilt, az)
+        segs.append((p0, p1))
+        for sgn in (-1.0, 1.0):
+            daz = sgn * np.deg2rad(rng.uniform(10.0, 25.0))
+            dtilt = np.deg2rad(rng.uniform(-5.0, 5.0))
+            p2 = p1 + rng.uniform(0.08, 0.15) * direction(tilt + dtilt, az + daz)
+            segs.append((p1, p2))
+    return segs
+
+
+def channel_shell_cells(n, seed, radius=0.01, amplitude=1e-3, noise=0.1):
+    """Charged shells of the branching channels of branching_channels(seed) on
+    an n^3 grid (h = 1/n): cells whose centre lies within h of the lateral
+    surface of the cylinder of the given radius around any segment (distance
+    to the segment's axis within radius +- h).  Returns (flat cell indices in
+    (k, j, i) order, sorted, and the density amplitude * eps0 / h^2 *
+    exp(noise * xi), xi ~ N(0, 1) drawn in index order), so that large grids
+    need no dense array on the host."""
+    h = 1.0 / n
+    rng = np.random.default_rng(seed + 1000)
+    hit = []
+    for a, b in branching_channels(seed):
+        lo = np.maximum(np.floor((np.minimum(a, b) - radius - 2 * h) * n).astype(int), 0)
+        hi = np.minimum(np.ceil((np.maximum(a, b) + radius + 2 * h) * n).astype(int), n)
+        x = (np.arange(lo[0], hi[0]) + 0.5) * h
+        y = (np.arange(lo[1], hi[1]) + 0.5) * h
+        ab = b - a
+        L2 = float(ab @ ab)
+        for k in range(lo[2], hi[2]):
+            z = (k + 0.5) * h
+            px = x[None, :] - a[0]
+            py = y[:, None] - a[1]
+            pz = z - a[2]
+            t = np.clip((px * ab[0] + py * ab[1] + pz * ab[2]) / L2, 0.0, 1.0)
+            dx = px - t * ab[0]
+            dy = py - t * ab[1]
+            dz = pz - t * ab[2]
+            d = np.sqrt(dx * dx + dy * dy + dz * dz)
+            jj, ii = np.nonzero(np.abs(d - radius) <= h)
+            if len(jj):
+                hit.append(((k * n + (jj + lo[1])) * n + (ii + lo[0])).astype(np.int64))
+    idx = np.unique(np.concatenate(hit)) if hit else np.zeros(0, dtype=np.int64)
+    val = amplitude / h**2 * np.exp(noise * rng.standard_normal(len(idx)))
+    return idx, val * EPS0
+
+
 def helmholtz_kappas():
     """Inverse absorption lengths of the three photon groups, kappa L = 10, 100, 1000."""
     return (10.0, 100.0, 1000.0)

@@ -377,15 +377,22 @@ def test_prolong_reproduces_constants_and_linears():
 
 
 def test_coarsen_rule():
+    """A coarse cell is an electrode iff at least 3 of its 8 children are;
+    beta is the mean of the free children."""
     beta = np.arange(1, 65, dtype=np.float64).reshape(4, 4, 4)
     mask = np.zeros((4, 4, 4), dtype=np.uint8)
-    mask[0:2, 0:2, 0:2] = 1
+    mask[0:2, 0:2, 0:2] = 1          # 8 children
     mask[2:4, 2:4, 2:4] = 1
-    mask[3, 3, 3] = 0
+    mask[3, 3, 3] = 0                # 7 children
+    mask[0, 2, 0] = mask[1, 3, 1] = 1  # coarse (0, 1, 0): 2 children
+    mask[2, 0, 0] = mask[3, 1, 1] = mask[2, 1, 0] = 1  # coarse (1, 0, 0): 3 children
     bc, mc = oracle.coarsen(beta, mask, (4, 4, 4))
-    assert mc[0, 0, 0] == 1 and mc[1, 1, 1] == 0 and mc[0, 1, 0] == 0
+    assert mc[0, 0, 0] == 1 and mc[1, 1, 1] == 1 and mc[1, 0, 0] == 1
+    assert mc[0, 1, 0] == 0 and mc[0, 0, 1] == 0
     assert bc[1, 1, 1] == beta[3, 3, 3]
-    np.testing.assert_allclose(bc[0, 1, 0], beta[0:2, 2:4, 0:2].mean())
+    free = beta[0:2, 2:4, 0:2][mask[0:2, 2:4, 0:2] == 0]
+    np.testing.assert_allclose(bc[0, 1, 0], free.mean())
+    np.testing.assert_allclose(bc[0, 0, 1], beta[0:2, 0:2, 2:4].mean())
 
 
 # ------------------------------------------------- per-face Dirichlet data
