@@ -104,6 +104,10 @@ typedef struct {
                        replaying each refinement step as a CUDA graph (0) */
   int rte_bc;       /* mg_rte_bc: domain faces of the Helmholtz problems
                        (MG_RTE_BC_DIRICHLET = 0); fixed at mg_create */
+  int ir_zchunk;    /* mixed mode, tile of the refinement pass: z planes
+                       marched by one CTA column, 0 (automatic: enough CTAs
+                       for 8 waves of three per SM) or >= 16; mg_autotune
+                       picks it among {auto, 16, 32, 64, 128} (0) */
 } mg_options;
 
 /* Per-solve statistics.  hist[c] is the relative residual after c cycles
@@ -385,9 +389,10 @@ mg_status mg_set_options(mg_ctx* ctx, const mg_options* opt);
 /*
  * mg_autotune -- pick the smoother sweeps (nu1, nu2) in {(1,1), (2,1), (2,2),
  * (3,3)} and, in mixed precision, the inner V-cycles per refinement step in
- * {1..4} by timing mg_solve_set on the caller's problem (each candidate run
- * twice from a zero guess, the faster counts; candidates that do not reach
- * tol are rejected).  The fastest is installed in the context and returned in
+ * {1..4}, then for the best of those the tile of the refinement pass
+ * (ir_zchunk in {auto, 16, 32, 64, 128}), by timing mg_solve_set on the
+ * caller's problem (each candidate run twice from a zero guess, the faster
+ * counts; candidates that do not reach tol are rejected).  The fastest is installed in the context and returned in
  * *best (*best_ms, nullable: its device time).  Allocates four scratch fields
  * for the duration of the call.  Arguments as in mg_solve_set.
  */

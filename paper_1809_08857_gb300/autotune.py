@@ -1,5 +1,6 @@
-"""Autotune cache: the sweep counts (nu1, nu2) and inner V-cycles per
-refinement step that mg_autotune picked for a problem signature, stored as
+"""Autotune cache: the sweep counts (nu1, nu2), inner V-cycles per
+refinement step and refinement-pass tile (ir_zchunk) that mg_autotune picked
+for a problem signature, stored as
 JSON keyed by device name and problem signature so that later runs on the
 same device and problem class skip the search."""
 import json
@@ -44,7 +45,8 @@ def tuned(solver, rho, S, kappa, tol=1e-10, has_eps=False, has_mask=False, preci
     key = signature(device, solver.shape, has_eps, has_mask, precision, tol)
     entry = load(cache_path).get(key)
     if entry:
-        solver.set_options(nu1=entry["nu1"], nu2=entry["nu2"], inner_cycles=entry["inner_cycles"])
+        solver.set_options(nu1=entry["nu1"], nu2=entry["nu2"], inner_cycles=entry["inner_cycles"],
+                           ir_zchunk=entry.get("ir_zchunk", 0))
         return entry, True
     opts, ms = solver.autotune(rho, S, kappa, tol)
     entry = dict(opts, ms=ms)

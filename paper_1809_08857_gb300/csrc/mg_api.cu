@@ -35,7 +35,8 @@
 namespace {
 
 constexpr double kEps0 = 8.8541878128e-12;  // F/m (CODATA 2018)
-constexpr int kDenseMax = 4096;             // largest coarsest grid inverted densely
+constexpr int kDenseMax = 4096;
+constexpr int kIrZchunkMin = 16;             // smallest tile of the refinement pass             // largest coarsest grid inverted densely
 constexpr int kMaxWork = 4;                 // concurrent problems per context
 constexpr int kMaxGraphs = 8;               // cached step graphs per work slot
 
@@ -111,7 +112,7 @@ struct LevelWork {
 struct StepGraph {
   int kind = 0;
   double alpha = 0;
-  int ic = 0, nu1 = 0, nu2 = 0;
+  int ic = 0, nu1 = 0, nu2 = 0, zc = 0;
   bool prof = false;
   const float2* b = nullptr;
   const float2* u_in = nullptr;
@@ -148,7 +149,8 @@ struct mg_ctx {
   cudaStream_t stream = nullptr;
   std::vector<Level> lv;
   double* mask_value = nullptr;
-  int npartial = 0;
+  int npartial = 0;  // partial sums allocated (the most any tile, automatic or
+                     // settable, needs)
   double *gj_row = nullptr, *gj_col = nullptr;
   std::vector<Coarse> coarse;
   std::vector<Work*> work;
@@ -517,6 +519,8 @@ mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha
   a.W = L0.W;
   a.partial = w->partial;
   a.partial_z = io.znorm ? w->partial + c->npartial : nullptr;
+  a.zchunk = c->opt.ir_zchunk;
+  const int nparts = mg::ir_partials(L0.b, c->opt.ir_zchunk);
   const double n = (double)L0.b.n();
   // u and b read, face arrays (or the electrode mask), e, u + e and b
   // written back, r
@@ -529,8 +533,8 @@ mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha
   }
   {
     Scope sc(c, s, MG_KCLASS_COARSE, 0);
-    mg::launch_sum_partials(w->partial, c->npartial, w->norm_dev + slot, s);
-    if (io.znorm) mg::launch_sum_partials(a.partial_z, c->npartial, w->norm_dev, s);
+    mg::launch_sum_partials(w->partial, nparts, w->norm_dev + slot, s);
+    if (io.znorm) mg::launch_sum_partials(a.partial_z, nparts, w->norm_dev, s);
   }
   MG_TRY(check_launch());
   const int lo = io.znorm ? 0 : slot;
@@ -634,7 +638,8 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
   const int ic = c->opt.inner_cycles;
   for (StepGraph& g : w->graphs)
     if (g.kind == p.kind && g.alpha == p.alpha && g.ic == ic && g.nu1 == c->opt.nu1 &&
-        g.nu2 == c->opt.nu2 && g.prof == c->prof && g.b == w->bdf && g.u_in == p.cur &&
+        g.nu2 == c->opt.nu2 && g.zc == c->opt.ir_zchunk && g.prof == c->prof && g.b == w->bdf &&
+        g.u_in == p.cur &&
         g.u_out == p.other) {
       g.stamp = ++c->clock;
       *out = &g;
@@ -659,6 +664,7 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
   g.ic = ic;
   g.nu1 = c->opt.nu1;
   g.nu2 = c->opt.nu2;
+  g.zc = c->opt.ir_zchunk;
   g.prof = c->prof;
   g.b = w->bdf;
   g.u_in = p.cur;
@@ -1033,7 +1039,9 @@ mg_status build(mg_ctx* c, const double* eps_r, const uint8_t* mask, const doubl
     if (eps_r || mask) mg::launch_split_beta(L.beta64, L.mask, sop(c, l, kPoisson, 0.0), mp(L.bp), s);
     if (mask) mg::launch_split_beta(nullptr, L.mask, sop(c, l, kHelmholtz, 0.0), mp(L.bh), s);
   }
-  c->npartial = mg::ir_partials(L0.b);
+  // the automatic tile can be shorter than the smallest settable one: room
+  // for whichever grid has more CTAs
+  c->npartial = std::max(mg::ir_partials(L0.b, 0), mg::ir_partials(L0.b, kIrZchunkMin));
   MG_TRY(c->alloc(&c->gj_row, (size_t)nc));
   MG_TRY(c->alloc(&c->gj_col, (size_t)nc));
   MG_CUDA(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
@@ -1054,6 +1062,8 @@ mg_status normalise_options(const mg_options* in, mg_options* out) {
     return fail(MG_ERR_INVALID_ARG, "no_graphs must be 0 or 1");
   if (in->rte_bc != MG_RTE_BC_DIRICHLET && in->rte_bc != MG_RTE_BC_MARSHAK)
     return fail(MG_ERR_INVALID_ARG, "rte_bc must be MG_RTE_BC_DIRICHLET or MG_RTE_BC_MARSHAK");
+  if (in->ir_zchunk != 0 && in->ir_zchunk < kIrZchunkMin)
+    return fail(MG_ERR_INVALID_ARG, "ir_zchunk must be 0 (automatic) or >= 16");
   if (in->nu1) out->nu1 = in->nu1;
   if (in->nu2) out->nu2 = in->nu2;
   if (in->max_cycles) out->max_cycles = in->max_cycles;
@@ -1062,6 +1072,7 @@ mg_status normalise_options(const mg_options* in, mg_options* out) {
   out->precision = in->precision;
   out->no_graphs = in->no_graphs;
   out->rte_bc = in->rte_bc;
+  out->ir_zchunk = in->ir_zchunk;
   return MG_OK;
 }
 
@@ -1874,6 +1885,40 @@ mg_status mg_autotune(mg_ctx* c, const double* rho, const double* S, const doubl
         best_o = o;
       }
     }
+  // then the tile of the refinement pass for the best candidate (mixed mode)
+  if (st == MG_OK && best_t < 1e300 && keep.precision == MG_PREC_MIXED) {
+    const int zcs[4] = {16, 32, 64, 128};
+    const mg_options base = best_o;
+    for (int z = 0; z < 4 && st == MG_OK; ++z) {
+      if (zcs[z] >= c->lv[0].b.nz) continue;
+      mg_options o = base;
+      o.ir_zchunk = zcs[z];
+      c->opt = o;
+      double t_min = 1e300;
+      for (int rep = 0; rep < 2 && st == MG_OK; ++rep) {
+        if (cudaMemsetAsync(scratch, 0, 4 * n * sizeof(double), c->stream) != cudaSuccess ||
+            cudaEventRecord(t0, c->stream) != cudaSuccess) {
+          st = fail(MG_ERR_CUDA, "autotune launch failed");
+          break;
+        }
+        const mg_status sv = mg_solve_set(c, rho, phi, S, psi, kappa, tol, nullptr);
+        cudaEventRecord(t1, c->stream);
+        cudaEventSynchronize(t1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (sv == MG_ERR_NOT_CONVERGED) break;
+        if (sv != MG_OK) {
+          st = sv;
+          break;
+        }
+        t_min = std::min(t_min, (double)ms);
+      }
+      if (st == MG_OK && t_min < best_t) {
+        best_t = t_min;
+        best_o = o;
+      }
+    }
+  }
   c->opt = st == MG_OK ? best_o : keep;
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);

@@ -114,7 +114,8 @@ struct IrArgs {
   double* partial;     // per-CTA sums of r^2
   double* partial_z;   // nullable: per-CTA sums of the squared residual of
                        // the guess that is 0 on free cells (FP64 guess only)
-  int zchunk;          // set by the launcher
+  int zchunk;          // z planes per CTA column, 0: automatic (the launcher
+                       // replaces it by the planes used)
   // set by the launcher: 1/h^2, -alpha and the interior beta = 1 diagonal
   // 6/h^2 + alpha as double-floats; alpha != 0
   float2 ih2d, nalpha, dint;
@@ -203,7 +204,9 @@ void launch_ir_fused(const IrArgs& a, cudaStream_t s);
 // electrode cells (mask nonzero, nullable) are left as they are
 void launch_df_to_f64(const float2* in, const uint8_t* mask, double* out, long long n,
                       cudaStream_t s);
-int ir_partials(const Box& b);
+// CTAs (= partial sums) of the refinement pass for z planes per CTA column
+// zchunk (0: automatic).
+int ir_partials(const Box& b, int zchunk = 0);
 
 // ---- composite AMR hierarchy (mg_amr.cu) ----------------------------------
 // One box of a ratio-2 AMR hierarchy as the kernels see it.

@@ -22,6 +22,8 @@
 
 #include "../../include/mg.h"
 #include "df.cuh"
+#include <algorithm>
+
 #include "mg_internal.h"
 
 // Largest number of CTAs (partial sums) one call may use: 16384 doubles,
@@ -282,19 +284,26 @@ __global__ void k_df_to_f64(const float2* __restrict__ in, const uint8_t* __rest
 
 }  // namespace
 
-static dim3 ir_grid(const Box& b, int* zchunk) {
+// Grid of the refinement pass for z planes per CTA column `hint` (0:
+// automatic); *zchunk receives the planes used.
+static dim3 ir_grid(const Box& b, int hint, int* zchunk) {
   const int gx = (b.nx + TX - 3) / (TX - 2), gy = (b.ny + TY - 3) / (TY - 2);
-  // enough CTAs to fill every SM (152 on GB300, three 512-thread CTAs each)
-  // several times over, long z runs
   int zc = b.nz;
-  while (zc > 16 && (long long)gx * gy * ((b.nz + zc - 1) / zc) < 8 * 152 * 3) zc = (zc + 1) / 2;
+  if (hint > 0) {
+    zc = std::min(hint, b.nz);
+  } else {
+    // enough CTAs to fill every SM (152 on GB300, three 512-thread CTAs
+    // each) several times over, long z runs
+    while (zc > 16 && (long long)gx * gy * ((b.nz + zc - 1) / zc) < 8 * 152 * 3)
+      zc = (zc + 1) / 2;
+  }
   *zchunk = zc;
   return dim3(gx, gy, (b.nz + zc - 1) / zc);
 }
 
-int ir_partials(const Box& b) {
+int ir_partials(const Box& b, int zchunk) {
   int zc;
-  dim3 g = ir_grid(b, &zc);
+  dim3 g = ir_grid(b, zchunk, &zc);
   return (int)(g.x * g.y * g.z);
 }
 
@@ -343,7 +352,7 @@ static void ir_constants(IrArgs& a) {
 
 void launch_ir_fused(const IrArgs& args, cudaStream_t s) {
   IrArgs a = args;
-  dim3 g = ir_grid(a.op.b, &a.zchunk);
+  dim3 g = ir_grid(a.op.b, args.zchunk, &a.zchunk);
   ir_constants(a);
   dispatch(a, g, s);
   add_launches(1);
@@ -431,7 +440,7 @@ mg_status noalloc_scratch(double** out) {
 // partial sums in the static scratch, then the final sum and square root.
 void launch_noalloc(IrArgs a, double* scratch, int nparts, double* norm_out, cudaStream_t s) {
   a.partial = scratch;
-  dim3 g = ir_grid(a.op.b, &a.zchunk);
+  dim3 g = ir_grid(a.op.b, 0, &a.zchunk);
   ir_constants(a);
   dispatch(a, g, s);
   k_noalloc_finish<<<1, NT, 0, s>>>(scratch, nparts, norm_out);

@@ -64,7 +64,7 @@ class Options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("concurrency", ctypes.c_int), ("no_graphs", ctypes.c_int),
-                ("rte_bc", ctypes.c_int)]
+                ("rte_bc", ctypes.c_int), ("ir_zchunk", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -359,7 +359,9 @@ class Solver:
                 for i, k in enumerate(KCLASSES)}
 
     def set_options(self, **kw):
-        """Change nu1, nu2, max_cycles, inner_cycles, concurrency or graphs."""
+        """Change nu1, nu2, max_cycles, inner_cycles, concurrency, graphs or
+        ir_zchunk (the refinement pass's z planes per CTA column, 0 =
+        automatic)."""
         o = Options.from_buffer_copy(self.options)
         for k, v in kw.items():
             if k == "graphs":
@@ -379,7 +381,8 @@ class Solver:
         _check(self._lib.mg_autotune(self._ctx, _ptr(rho, torch.float64), _ptr(S, torch.float64),
                                      kap, float(tol), ctypes.byref(best), ctypes.byref(ms)))
         self.options = best
-        return ({"nu1": best.nu1, "nu2": best.nu2, "inner_cycles": best.inner_cycles}, ms.value)
+        return ({"nu1": best.nu1, "nu2": best.nu2, "inner_cycles": best.inner_cycles,
+                 "ir_zchunk": best.ir_zchunk}, ms.value)
 
     def poisson_residual(self, rho, phi, out=None):
         """r = b - A phi in FP64 (electrode cells of phi are set first)."""
