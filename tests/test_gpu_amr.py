@@ -274,3 +274,35 @@ def test_streamer_hierarchy_meets_tol_by_the_oracle(mg, n0):
     back = H.average_down(un)
     for q in range(len(un)):
         np.testing.assert_allclose(un[q], back[q], rtol=0, atol=1e-14 * np.abs(back[q]).max())
+
+
+# margin of exactly one parent cell (shell cells on the domain faces) and the
+# smallest box (2^3 fine cells: its whole grid is the dense coarsest solve)
+EDGE = ((12, 12, 12), [(1, (2, 2, 2), (8, 10, 6)), (1, (14, 14, 16), (2, 2, 2)),
+                       (2, (6, 6, 6), (4, 4, 4))])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_edge_hierarchy_matches_oracle(mg, precision):
+    """A box whose grown footprint reaches the domain faces, a 2x2x2 box and
+    a level-2 box inside the first: residual cell by cell and the solve
+    against the oracle (Dirichlet z faces, variable coefficient)."""
+    layout = EDGE
+    beta = coefficients(layout, 61, 0.4)
+    H = oracle_of(layout, 0.0, beta)
+    rho = smooth_source(H, 62)
+    rng = np.random.default_rng(63)
+    u = [rng.standard_normal(s) for s in shapes_of(layout)]
+    A = make(mg, layout, beta, precision=precision)
+    rhs = [cuda(x * oracle.EPS0) for x in rho]
+    r, _ = A.residual("poisson", rhs, [cuda(x) for x in u])
+    ref, _ = H.residual(rho, u)
+    ref = H.average_down(ref)
+    scale = max(np.abs(x).max() for x in ref)
+    for q in range(len(u)):
+        np.testing.assert_allclose(r[q].cpu().numpy(), ref[q], rtol=0, atol=1e-12 * scale)
+    sol = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in shapes_of(layout)]
+    st = A.solve("poisson", rhs, sol, tol=TOL)
+    A.close()
+    assert st["converged"]
+    assert H.rel_l2([t.cpu().numpy() for t in sol], H.solve(rho)) <= PARITY
