@@ -332,7 +332,8 @@ typedef struct {
  *   base        level-0 grid (the domain).
  *   nbox, boxes the refined boxes (any order).  Rules, checked: the box's
  *               footprint on the level below (cells lo/2 .. (lo+n)/2), grown
- *               by one cell, lies inside one box of that level (its parent);
+ *               by one cell (two cells when that level is itself refined),
+ *               lies inside one box of that level (its parent);
  *               it does not overlap the footprint of another box of the same
  *               level; on level 0 it holds no electrode cell.
  *   eps_r       NULL (coefficient 1 everywhere) or nbox + 1 device pointers

@@ -18,8 +18,10 @@ the quadratic coarse-fine interpolation of Martin and Cartwright):
   corner and shape in level-l cell indices counted from the domain's low
   corner (both even, so that it covers whole cells of level l - 1: its
   footprint).  Its footprint grown by one cell must lie inside one box of
-  level l - 1 (the parent), must not reach another box of level l, and on
-  level 0 must hold no electrode cell.
+  level l - 1 (the parent) -- grown by two cells when the parent is itself
+  a refined box, whose own coarse-fine ghosts read its two outermost cell
+  layers --, must not reach another box of level l, and on level 0 must
+  hold no electrode cell.
 
 * Unknowns.  The valid cells: cells of a box not covered by a box of the next
   level; electrode cells (level 0) are excluded and hold their given value.
@@ -171,8 +173,11 @@ class Hierarchy:
             flo, fhi = b.footprint()
             glo = tuple(v - 1 for v in flo)
             ghi = tuple(v + 1 for v in fhi)
+            # a refined parent's ghosts read its two outermost layers
+            g = 1 if b.level == 1 else 2
             par = [p for p, o in enumerate(self.boxes)
-                   if o.level == b.level - 1 and _inside(glo, ghi, o.lo, o.hi)]
+                   if o.level == b.level - 1
+                   and _inside(tuple(v - g for v in flo), tuple(v + g for v in fhi), o.lo, o.hi)]
             if len(par) != 1:
                 raise ValueError("box %d: grown footprint not inside one box of level %d"
                                  % (q, b.level - 1))

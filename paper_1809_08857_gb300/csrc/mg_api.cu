@@ -1168,6 +1168,12 @@ struct mg_amr {
 
 namespace {
 
+// double-float (hi, lo) of a host double
+float2 df_host(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
 void amr_destroy(mg_amr* a) {
   if (!a) return;
   if (a->stream) cudaStreamSynchronize(a->stream);
@@ -1221,24 +1227,32 @@ mg_status amr_layout(mg_amr* a, const mg_grid* g, int nbox, const mg_amr_box* bo
   for (int q = 1; q <= nbox; ++q) {
     AmrBox& B = a->box[q];
     int flo[3], fhi[3], glo[3], ghi[3];
+    // the footprint grown by one parent cell must lie inside the parent, by
+    // two when the parent is a refined box (its own ghosts read its two
+    // outermost cell layers, which must stay valid)
+    const int margin = B.level == 1 ? 1 : 2;
+    int mlo[3], mhi[3];
     for (int d = 0; d < 3; ++d) {
       flo[d] = B.lo[d] / 2;
       fhi[d] = (B.lo[d] + B.n[d]) / 2;
       glo[d] = flo[d] - 1;
       ghi[d] = fhi[d] + 1;
+      mlo[d] = flo[d] - margin;
+      mhi[d] = fhi[d] + margin;
     }
     for (int p = 0; p <= nbox; ++p) {
       const AmrBox& P = a->box[p];
       if (P.level != B.level - 1) continue;
       int phi[3];
       for (int d = 0; d < 3; ++d) phi[d] = P.lo[d] + P.n[d];
-      if (!box_inside(glo, ghi, P.lo, phi)) continue;
+      if (!box_inside(mlo, mhi, P.lo, phi)) continue;
       if (B.parent >= 0) return fail(MG_ERR_INVALID_ARG, "refined box inside two parents");
       B.parent = p;
     }
     if (B.parent < 0)
       return fail(MG_ERR_INVALID_ARG,
-                  "refined box: footprint grown by one cell not inside a box of the level below");
+                  "refined box: footprint grown by one cell (two inside a refined box) not "
+                  "inside a box of the level below");
     AmrBox& P = a->box[B.parent];
     for (int d = 0; d < 3; ++d) B.fo[d] = flo[d] - P.lo[d];
     P.children.push_back(q);
@@ -1483,7 +1497,15 @@ mg_status amr_pass(mg_amr* a, Kind kind, double alpha, int lmin, bool norm, bool
         ra.cx = L.cx;
         ra.cy = L.cy;
         ra.cz = L.cz;
+        ra.cxd = L.cxd;
+        ra.cyd = L.cyd;
+        ra.czd = L.czd;
+        ra.Dd = L.Dd;
       }
+      ra.ih2d = df_host(L.ih2);
+      ra.dint = df_host(6.0 * L.ih2 + alpha);
+      ra.nalpha = df_host(-alpha);
+      ra.has_alpha = alpha != 0.0;
       ra.mask = L.mask;
       for (int f = 0; f < 6; ++f) ra.rho[f] = q == 0 ? face_rho(B.ctx, kind, alpha, f, B.h) : 0.0;
       ra.b = B.b;

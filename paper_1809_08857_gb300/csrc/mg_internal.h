@@ -240,6 +240,15 @@ struct AmrResArgs {
                         // values kept)
   const unsigned* special;  // the box's valid boundary cells and the valid
   unsigned nspecial;        // cells next to a covered cell (general rows)
+  // the interior rows in double-float arithmetic: the box's level-0 face
+  // weights and diagonal as double-floats (nullable: beta = 1), 1/h^2,
+  // 6/h^2 + alpha and -alpha as double-floats
+  const float2* cxd;
+  const float2* cyd;
+  const float2* czd;
+  const float2* Dd;
+  float2 ih2d, dint, nalpha;
+  int has_alpha;
 };
 
 // Ghost values of box q (level >= 1) from its own and its parent's iterate.

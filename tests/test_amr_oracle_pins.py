@@ -171,6 +171,7 @@ def test_average_down_of_a_linear_function_is_the_coarse_value():
     [(1, (8, 8, 8), (8, 8, 8)), (1, (16, 8, 8), (8, 8, 8))],  # siblings too close
     [(1, (7, 8, 8), (8, 8, 8))],                              # odd corner
     [(2, (20, 20, 20), (8, 8, 8))],                           # no parent
+    [(1, (8, 8, 8), (12, 16, 8)), (2, (18, 18, 18), (4, 4, 4))],  # one cell inside a refined parent
 ])
 def test_bad_hierarchies_are_rejected(boxes):
     with pytest.raises(ValueError):

@@ -121,7 +121,8 @@ def test_composite_residual_matches_oracle(mg, kind):
     scale = max(np.abs(x).max() for x in ref)
     for q in range(len(shapes)):
         np.testing.assert_allclose(r[q], ref[q], rtol=0, atol=1e-12 * scale)
-    assert abs(norm - ref_norm) <= 1e-12 * ref_norm
+    # r^2 is summed in FP32 per thread (FP64 across blocks)
+    assert abs(norm - ref_norm) <= 1e-6 * ref_norm
 
 
 def test_composite_residual_conserves_flux(mg):
@@ -270,23 +271,26 @@ def test_streamer_hierarchy_meets_tol_by_the_oracle(mg, n0):
     _, rn = H.residual(f, un)
     bn = H.rhs_norm(f)
     assert rn <= 1.01 * TOL * bn
-    assert abs(gpu_norm - rn) <= 1e-3 * rn
+    # the library's residual (double-float rows on the interior cells) agrees
+    # with the oracle's to its rounding floor, far below the tolerance
+    assert abs(gpu_norm - rn) <= 1e-11 * bn
     back = H.average_down(un)
     for q in range(len(un)):
         np.testing.assert_allclose(un[q], back[q], rtol=0, atol=1e-14 * np.abs(back[q]).max())
 
 
-# margin of exactly one parent cell (shell cells on the domain faces) and the
+# margin of exactly one base cell (shell cells on the domain faces), the
 # smallest box (2^3 fine cells: its whole grid is the dense coarsest solve)
+# and a level-2 box at the smallest margin inside a refined parent (two cells)
 EDGE = ((12, 12, 12), [(1, (2, 2, 2), (8, 10, 6)), (1, (14, 14, 16), (2, 2, 2)),
-                       (2, (6, 6, 6), (4, 4, 4))])
+                       (2, (8, 8, 8), (4, 4, 4))])
 
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_edge_hierarchy_matches_oracle(mg, precision):
     """A box whose grown footprint reaches the domain faces, a 2x2x2 box and
-    a level-2 box inside the first: residual cell by cell and the solve
-    against the oracle (Dirichlet z faces, variable coefficient)."""
+    a level-2 box two cells inside the first: residual cell by cell and the
+    solve against the oracle (Dirichlet z faces, variable coefficient)."""
     layout = EDGE
     beta = coefficients(layout, 61, 0.4)
     H = oracle_of(layout, 0.0, beta)
