@@ -48,6 +48,9 @@ def parse():
                     help="keep --inner-cycles and V(2,2) instead of the autotuned choice")
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ir-zchunk", type=int, default=0,
+                    help="refinement-pass tile (z planes per CTA column) when not autotuning; "
+                         "0 = automatic")
     ap.add_argument("--no-amr", action="store_true",
                     help="skip the composite AMR solve among the extras")
     return ap.parse_args()
@@ -400,6 +403,8 @@ def run_ours(args):
     solver = mg.Solver((n, n, n), h, eps_r=eps, precision=prec, inner_cycles=args.inner_cycles,
                        concurrency=args.concurrency, graphs=not args.no_graphs)
     tuned = None
+    if args.ir_zchunk:
+        solver.set_options(ir_zchunk=args.ir_zchunk)
     if not args.no_autotune:
         import tempfile as _tf
 

@@ -310,3 +310,41 @@ def test_edge_hierarchy_matches_oracle(mg, precision):
     A.close()
     assert st["converged"]
     assert H.rel_l2([t.cpu().numpy() for t in sol], H.solve(rho)) <= PARITY
+
+
+def test_zero_problem_takes_no_iteration(mg):
+    """b = 0 and a zero guess: converged before any iteration, u stays 0."""
+    A = make(mg, TWO, None, bc=NEUMANN)
+    u = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in A.shapes]
+    st = A.solve("screened", [torch.zeros_like(t) for t in u], u, tol=TOL, param=3.0)
+    A.close()
+    assert st["cycles"] == 0 and st["converged"]
+    assert all(bool((t == 0).all()) for t in u)
+
+
+def test_nonfinite_input_is_reported(mg):
+    A = make(mg, TWO, None, bc=NEUMANN)
+    u = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in A.shapes]
+    f = [torch.ones_like(t) for t in u]
+    f[1][3, 4, 5] = float("nan")
+    with pytest.raises(mg.MGError) as e:
+        A.solve("screened", f, u, tol=TOL, param=3.0)
+    A.close()
+    assert e.value.status == mg.MG_ERR_NONFINITE
+
+
+def test_iteration_cap_reports_not_converged_with_stats(mg):
+    """max_cycles = 2: status not converged, two iterations, a decreasing
+    history, and the iterate of the last iteration returned."""
+    H = oracle_of(TWO, 5.0, None, bc=NEUMANN)
+    f = smooth_source(H, 71)
+    A = make(mg, TWO, None, bc=NEUMANN, max_cycles=2)
+    u = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in A.shapes]
+    st = A.solve("screened", [cuda(x) for x in f], u, tol=TOL, param=5.0,
+                 raise_on_nonconvergence=False)
+    A.close()
+    assert not st["converged"] and st["cycles"] == 2
+    h = st["hist"]
+    assert len(h) == 3 and h[0] == 1.0 and h[2] < h[1] < h[0]
+    _, rn = H.residual(f, [t.cpu().numpy() for t in u])
+    assert abs(rn / H.rhs_norm(f) - st["rel_resid"]) <= 1e-6 * st["rel_resid"]
