@@ -56,6 +56,31 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world, device):
+    """The largest of the ranks' x (every rank passes its own and gets the
+    maximum); world == 1 returns x."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, seconds_per_step):
+    """Sets per second of the whole job: every rank solves its own replica
+    (weak scaling), the step time is the slowest rank's."""
+    return world / seconds_per_step
+
+
+def emit(line, rank):
+    """The JSON line, printed by rank 0 only."""
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
@@ -447,15 +472,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
     launches = mg.launch_count() - l0
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms_per_step = ms / args.steps
-    value = world * 1e3 / ms_per_step
+    value = whole_job_rate(world, ms_per_step * 1e-3)
 
     # end to end through host buffers (pinned), copies inside the timed
     # region: every step uploads its rho and S and downloads its four
@@ -520,14 +539,10 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     solver.set_stream(torch.cuda.current_stream())
     del bufs
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
     cells = n ** 3
-    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * cells,
+    e2e = {"value": whole_job_rate(world, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * 8 * cells,
            "d2h_bytes_per_step": 4 * 8 * cells}
 
     # kernel profile (outside the timed region): one set at the timed
@@ -562,8 +577,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_sample(inputs, n)
         line["cpu_baseline"] = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    emit(line, rank)
     solver.close()
     if world > 1:
         import torch.distributed as dist
