@@ -337,8 +337,9 @@ def measure_amr(dev, n0=256, reps=3):
     grid n0^3 with the dielectric slab and three nested refined levels around
     the streamer channel and head (workloads.streamer_amr_layout), the shell
     charge sampled on every level, from zero to 1e-10 in mixed precision with
-    two inner V-cycles per box and iteration; device time per solve (CUDA
-    events), FAC iterations, valid cells."""
+    three inner V-cycles per box and iteration (2: 7 iterations, 3: 5, the
+    fastest; 4: 5, slower); device time per solve (CUDA events), FAC
+    iterations, valid cells."""
     import numpy as np
     import torch
 
@@ -353,7 +354,7 @@ def measure_amr(dev, n0=256, reps=3):
         rho.append(W.streamer_shell_box(b[2], h, o, q + 1, thickness=h0))
     rho = [torch.from_numpy(r).to(dev) for r in rho]
     A = mg.Amr((n0,) * 3, h0, boxes, eps_r=eps, bc_kind=W.GAP_BC_KIND, bc_value=W.GAP_BC_VALUE,
-               precision=mg.MG_PREC_MIXED, inner_cycles=2)
+               precision=mg.MG_PREC_MIXED, inner_cycles=3)
     u = [torch.zeros(s, dtype=torch.float64, device=dev) for s in A.shapes]
     A.solve("poisson", rho, u, tol=TOL)  # first call builds the coarse inverses
     st = None
