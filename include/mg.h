@@ -410,7 +410,8 @@ mg_status mg_autotune(mg_ctx* ctx, const double* rho, const double* S, const dou
  * the new charge and the previous potential:
  *     phi_guess = phi_prev + U(rho_n * s_rho, phi_prev * s_phi) / s_out.
  * Activations and weights are BF16 with FP32 accumulation on the tensor
- * cores (mma.sync); FP32 master weights are trained with Adam.  The paper has
+ * cores (tcgen05 MMAs into tensor memory, operands staged by tiled tensor
+ * copies); FP32 master weights are trained with Adam.  The paper has
  * no network: this is the warm start of the solver, and multigrid corrects
  * its guess to the same tolerance, so it cannot change the answer.
  * Field arguments are device FP64 [n][d][h][w] (x fastest), d, h, w
@@ -452,8 +453,10 @@ mg_status mg_unet_load(mg_unet* net, const char* path);
 
 /* Single 3x3x3 convolution (zero padding) on channels-last BF16 tensors, the
  * network's kernel exposed for tests: y = relu?(conv(concat(x1, x2)) + bias),
- * weights [cout][27][c1 + c2] BF16, c1, c2 multiples of 16, cout in
- * {16, 32, 48, 64, 96}; bias (FP32, nullable). */
+ * weights [cout][27][c1 + c2] BF16, c1 >= 16 and c2 multiples of 16, cout in
+ * {16, 32, 48, 64, 96}; bias (FP32, nullable).  x1, x2 and w are read by the
+ * tensor memory accelerator and must be 16-byte aligned (MG_ERR_INVALID_ARG
+ * otherwise). */
 mg_status mg_nn_conv3d(const void* x1, int c1, const void* x2, int c2, const void* w,
                        const float* bias, int relu, int cout, int n, int d, int h, int w_,
                        void* y, void* cuda_stream);

@@ -32,8 +32,10 @@ struct ConvArgs {
 };
 
 bool conv_supported(int cin_total, int cout);
-size_t conv_smem_bytes(int cout);
 cudaError_t launch_conv3d(const ConvArgs& a, int cout, cudaStream_t s);
+// True once any conv CTA gave up waiting for its tensor-core MMAs (a bounded
+// wait; its outputs were not written).  Synchronises.
+bool conv_timed_out();
 void launch_flip_weights(const __nv_bfloat16* w, int co, int ci, __nv_bfloat16* wt,
                          cudaStream_t s);
 void launch_relu_bwd(const __nv_bfloat16* y, __nv_bfloat16* dy, long long n, cudaStream_t s);

@@ -6,14 +6,13 @@
 // 16; 3x3x3 conv weights [Cout][27][Cin] (tap t = (kd*3 + kh)*3 + kw) in
 // BF16 with an FP32 master copy.
 //
-// conv3d forward is an implicit GEMM on the tensor cores (mma.sync
-// m16n8k16 bf16 -> fp32): M = output voxels, N = Cout, K = 27 Cin.  A CTA owns
-// a 16 x 4 x 2 (w, h, d) block of output voxels and all output channels; for
-// each 16-channel input chunk it stages the (18 x 6 x 4) halo tile and the 27
-// taps of weights in shared memory (rows padded to 48 bytes so the ldmatrix
-// row groups hit distinct banks), then every warp multiplies two w-rows of 16
-// voxels against all output channels, tap by tap.  The input gradient is the
-// same kernel with flipped, transposed weights.
+// conv3d forward is an implicit GEMM on the tcgen05 tensor cores (BF16 x
+// BF16 -> FP32 accumulators in tensor memory, operands staged in shared
+// memory by the tensor memory accelerator, one producer and one MMA-issuing
+// thread per CTA): M = output voxels, N = Cout, K = 27 Cin.  The input
+// gradient is the same kernel with flipped, transposed weights.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -24,157 +23,308 @@ namespace nn {
 
 namespace {
 
-constexpr int TW = 16, TH = 4, TD = 2;            // output voxel tile
-constexpr int HW = TW + 2, HH = TH + 2, HD = TD + 2;  // halo tile
-constexpr int HALO = HW * HH * HD;                // 432 voxels
-constexpr int ROWB = 48;                          // bytes per 16-channel row in smem
-constexpr int kConvThreads = 128;                 // 4 warps x 2 w-rows = 8 rows
+// Output tile of a CTA: MT UMMA M-tiles of 8 (w) x 16 (h) voxels at d0 ..
+// d0 + MT - 1 (MT = 2: 256 voxels sharing the weights staged in shared
+// memory; MT = 1 on small grids, for more CTAs).
+constexpr int TW = 8, TH = 16;
+constexpr int HW = TW + 2, HH = TH + 2;  // halo tile rows
+constexpr int kConvThreads = 128;                     // 4 warps: TMEM lane quarters
+constexpr int kMmaM = 128;                            // rows (voxels) of one MMA
+constexpr long long kWaitIters = 1ll << 24;           // bound of an mbarrier wait
+constexpr int kMaxStages = 2;                         // shared-memory stages of the K loop
+
+__host__ __device__ constexpr int round1k(int b) { return (b + 1023) / 1024 * 1024; }
+
+// Shared-memory plan of one stage: the two 8-channel halves of the halo
+// (each [voxel] x 16 B, padded to 1 KB) and the chunk's weights
+// [tap][half][co] x 16 B.
+template <int N, int MT>
+struct ConvPlan {
+  static constexpr int kHalo = HW * HH * (MT + 2);         // halo voxels
+  static constexpr int kHalfBytes = round1k(kHalo * 16);   // one channel half
+  static constexpr int kHaloTx = 2 * kHalo * 16;           // bytes the two halo loads bring
+  static constexpr int kWBytes = 27 * 2 * N * 16;          // weights of a 16-channel chunk
+  static constexpr int kStage = 2 * kHalfBytes + round1k(kWBytes);
+  static constexpr int smem(int stages) { return stages * kStage + 1024; }  // + alignment slack
+  // TMEM columns: MT accumulators, each starting on a multiple of 32
+  // columns; the allocation is a power of two >= 32
+  static constexpr int kTile = (N + 31) / 32 * 32;
+  static constexpr int kAlloc = MT * kTile <= 32 ? 32 : MT * kTile <= 64 ? 64
+                                : MT * kTile <= 128 ? 128 : MT * kTile <= 256 ? 256 : 512;
+};
+
+// Set when a CTA gave up waiting on an mbarrier (its outputs are not written).
+__device__ unsigned g_conv_timeout = 0;
 
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
-                                        uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(r0), "=r"(r1)
-               : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// NF = Cout / 8 output-channel fragments.
-template <int NF>
-__global__ void __launch_bounds__(kConvThreads) k_conv3d(ConvArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char* halo = smem;                       // HALO rows of ROWB bytes
-  unsigned char* wsm = smem + HALO * ROWB;          // [27][NF*8] rows of ROWB bytes
-  const int Co = NF * 8;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // tile origin
+// Shared-memory matrix descriptor of the tensor-core MMA for an operand in
+// the K-major layout without swizzle: 8-row x 16-byte core matrices whose
+// rows are 16 bytes apart; lbo = byte distance between the two core
+// matrices adjacent in K, sbo = between those adjacent in M (or N); bits
+// 46-47 carry the descriptor version of this architecture (1).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3ffffu) >> 4) | ((uint64_t)((lbo & 0x3ffffu) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3ffffu) >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
+// both operands K-major, M x N.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+  return (1u << 4)      // D: FP32
+         | (1u << 7)    // A: BF16
+         | (1u << 10)   // B: BF16
+         | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// Wait for the mbarrier phase with the given parity; false after kWaitIters
+// unsuccessful tries.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (long long it = 0; it < kWaitIters; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar),
+               "r"(bytes)
+               : "memory");
+}
+
+// Tiled tensor loads (global -> shared), completing on an mbarrier.
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, uint32_t mbar,
+                                            int c0, int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(c4)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t mbar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+// 3D convolution (3x3x3, pad 1) as an implicit GEMM on the fifth-generation
+// tensor cores: M = output voxels, N = Cout, K = 27 taps x Cin, in chunks
+// of 16 input channels.
+//
+// Staging: for every chunk the producer thread (warp 0) issues three tiled
+// tensor loads into a free stage: the halo tile of each 8-channel half
+// ([voxel] x 16 B, voxels w-fastest; out-of-range voxels are zero-filled by
+// the copy engine, which is the convolution's zero padding) and the chunk's
+// weights [tap][half][co] x 16 B (a 4D view of the [co][tap][ci] weights).
+// The A operand of tap (kw, kh, kd) is the halo itself seen from offset
+// (kw, kh, kd): 8 voxels along w form a core matrix (contiguous 16-byte
+// rows), the next h row is one halo row further (sbo), the other channel
+// half one padded half-plane further (lbo).
+//
+// The number of stages S (1 or 2) is a launch argument: with two or more
+// waves of CTAs one stage per CTA is faster (more CTAs per SM hide each
+// other's load latency: 348 against 463 us for 32 -> 32 channels on 128^3),
+// on small grids two (26 against 36 us for 96 -> 48 on 2 x 16^3).
+//
+// MMA: one thread (warp 1) waits for a stage's loads, issues its MT x 27
+// MMAs into the MT TMEM accumulators (128 lanes = voxels, Cout columns) and
+// commits them to the stage's "empty" barrier, which frees the stage for the
+// producer; after the last chunk it commits to the "done" barrier.  Every
+// wait is bounded; a CTA that gives up sets g_conv_timeout, waits (bounded)
+// for its copies and MMAs still in flight and writes nothing.
+//
+// Epilogue: the four warps read their TMEM lane quarters with tcgen05.ld and
+// apply bias, ReLU and the BF16 store (two outputs split by channel).
+template <int N, int MT>
+__global__ void __launch_bounds__(kConvThreads)
+    k_conv3d(ConvArgs a, const __grid_constant__ CUtensorMap map_x1,
+             const __grid_constant__ CUtensorMap map_x2, const __grid_constant__ CUtensorMap map_w,
+             int S) {
+  using P = ConvPlan<N, MT>;
+  constexpr int TD = MT;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * kMaxStages + 1];  // full[], empty[], done
+  __shared__ uint32_t tmem_slot;
+  __shared__ int issued_s, committed_s, fail_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tiles_w = (a.W + TW - 1) / TW, tiles_h = (a.H + TH - 1) / TH;
+  const int tiles_d = (a.D + TD - 1) / TD;
   int bid = blockIdx.x;
   const int tw = bid % tiles_w;
   bid /= tiles_w;
   const int th = bid % tiles_h;
   bid /= tiles_h;
-  const int tiles_d = (a.D + TD - 1) / TD;
   const int td = bid % tiles_d;
   const int n = bid / tiles_d;
   const int w0 = tw * TW, h0 = th * TH, d0 = td * TD;
-
-  float acc[2][NF][4];
-#pragma unroll
-  for (int m = 0; m < 2; ++m)
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[m][f][q] = 0.0f;
-
   const int nchunks = (a.C1 + a.C2) / 16;
-  for (int ch = 0; ch < nchunks; ++ch) {
-    // input chunk: channels [16 ch, 16 ch + 16) of concat(x1, x2)
-    const bool first = ch * 16 < a.C1;
-    const __nv_bfloat16* src = first ? a.x1 : a.x2;
-    const int cs = first ? a.C1 : a.C2;
-    const int c0 = first ? ch * 16 : ch * 16 - a.C1;
-    // halo tile: 432 voxels x 32 bytes, as 16-byte pieces
-    for (int q = threadIdx.x; q < HALO * 2; q += kConvThreads) {
-      const int v = q >> 1, half = q & 1;
-      const int hx = v % HW, hy = (v / HW) % HH, hz = v / (HW * HH);
-      const int x = w0 + hx - 1, y = h0 + hy - 1, z = d0 + hz - 1;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (x >= 0 && x < a.W && y >= 0 && y < a.H && z >= 0 && z < a.D) {
-        const long long vox = (((long long)n * a.D + z) * a.H + y) * a.W + x;
-        val = *reinterpret_cast<const uint4*>(src + vox * cs + c0 + half * 8);
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t bar0 = smem_u32(&bars[0]);
+  auto full = [&](int st) { return bar0 + 8u * (uint32_t)st; };
+  auto empty = [&](int st) { return bar0 + 8u * (uint32_t)(kMaxStages + st); };
+  const uint32_t done_bar = bar0 + 8u * (uint32_t)(2 * kMaxStages);
+
+  if (tid == 0) {
+    for (int i = 0; i < 2 * kMaxStages + 1; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8u * i) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    issued_s = 0;
+    committed_s = 0;
+    fail_s = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(P::kAlloc)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (tid == 0) {
+    // producer: chunk ch goes to stage ch % S once the MMAs of chunk ch - S
+    // (that stage's previous use, phase ch / S - 1 of its empty barrier) are done
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int st = ch % S;
+      if (ch >= S && !mbar_wait(empty(st), (uint32_t)((ch / S - 1) & 1))) {
+        atomicExch(&fail_s, 1);
+        break;
       }
-      *reinterpret_cast<uint4*>(halo + v * ROWB + half * 16) = val;
+      if (*(volatile int*)&fail_s) break;
+      const uint32_t halo = base + (uint32_t)(st * P::kStage);
+      const uint32_t wsm = halo + 2u * P::kHalfBytes;
+      const bool first = ch * 16 < a.C1;
+      const CUtensorMap* mx = first ? &map_x1 : &map_x2;
+      const int c0 = first ? ch * 16 : ch * 16 - a.C1;
+      mbar_expect_tx(full(st), (uint32_t)(P::kHaloTx + P::kWBytes));
+      tma_load_5d(halo, mx, full(st), c0, w0 - 1, h0 - 1, d0 - 1, n);
+      tma_load_5d(halo + P::kHalfBytes, mx, full(st), c0 + 8, w0 - 1, h0 - 1, d0 - 1, n);
+      tma_load_4d(wsm, &map_w, full(st), 0, 0, 2 * ch, 0);
+      issued_s = ch + 1;
     }
-    // weights of this chunk: [tap][co] rows of 16 input channels
-    for (int q = threadIdx.x; q < 27 * Co * 2; q += kConvThreads) {
-      const int half = q & 1, r = q >> 1;
-      const int co = r % Co, tap = r / Co;
-      const uint4 val = *reinterpret_cast<const uint4*>(
-          a.w + ((long long)co * 27 + tap) * (a.C1 + a.C2) + ch * 16 + half * 8);
-      *reinterpret_cast<uint4*>(wsm + (tap * Co + co) * ROWB + half * 16) = val;
-    }
-    __syncthreads();
-    // this warp's two w-rows: rows 2 warp, 2 warp + 1 of the 8 (h, d) rows
+  } else if (tid == 32) {
+    // MMA issue: chunk ch waits for phase ch / S of its stage's full barrier
+    const uint32_t idesc = instr_desc(kMmaM, N);
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int st = ch % S;
+      if (!mbar_wait(full(st), (uint32_t)((ch / S) & 1))) {
+        atomicExch(&fail_s, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t halo = base + (uint32_t)(st * P::kStage);
+      const uint32_t wsm = halo + 2u * P::kHalfBytes;
 #pragma unroll 1
-    for (int tap = 0; tap < 27; ++tap) {
-      const int kw = tap % 3, kh = (tap / 3) % 3, kd = tap / 9;
-      uint32_t af[2][4];
-#pragma unroll
-      for (int m = 0; m < 2; ++m) {
-        const int row = warp * 2 + m;
-        const int hy = row % TH, hz = row / TH;
-        // ldmatrix x4: matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7),
-        // (rows 0-7, k 8-15), (rows 8-15, k 8-15); lane gives one row address
-        const int mj = lane >> 3, rr = lane & 7;
-        const int wx = rr + 8 * (mj & 1);
-        const int v = ((hz + kd) * HH + (hy + kh)) * HW + (wx + kw);
-        ldsm_x4(smem_u32(halo + v * ROWB + (mj >> 1) * 16), af[m][0], af[m][1], af[m][2],
-                af[m][3]);
-      }
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        uint32_t b0, b1;
-        // x2: matrices (co 8f..8f+7, k 0-7), (co 8f..8f+7, k 8-15)
-        const int mj = (lane >> 3) & 1, rr = lane & 7;
-        ldsm_x2(smem_u32(wsm + (tap * Co + f * 8 + rr) * ROWB + mj * 16), b0, b1);
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-          mma_bf16(acc[m][f], af[m][0], af[m][1], af[m][2], af[m][3], b0, b1);
-      }
+      for (int s = 0; s < TD; ++s)
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+          const int kw = tap % 3, kh = (tap / 3) % 3, kd = tap / 9;
+          const uint32_t aoff = 16u * (uint32_t)(kw + HW * (kh + HH * (kd + s)));
+          const uint64_t ad = smem_desc(halo + aoff, P::kHalfBytes, HW * 16);
+          const uint64_t bd = smem_desc(wsm + (uint32_t)(tap * 2 * N * 16), N * 16, 128);
+          mma_f16(tmem + (uint32_t)(s * P::kTile), ad, bd, idesc, (ch > 0 || tap > 0) ? 1u : 0u);
+        }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              empty(st))
+          : "memory");
+      committed_s = ch + 1;
     }
-    __syncthreads();
+    if (!*(volatile int*)&fail_s)
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              done_bar)
+          : "memory");
   }
-  // epilogue: bias, ReLU, BF16, store (two outputs split by channel)
-  const int g = lane >> 2, tq = lane & 3;
-#pragma unroll
-  for (int m = 0; m < 2; ++m) {
-    const int row = warp * 2 + m;
-    const int y = h0 + row % TH, z = d0 + row / TH;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int x = w0 + g + 8 * half;
-      if (x >= a.W || y >= a.H || z >= a.D) continue;
+  __syncwarp();
+  // every thread: wait for the last MMAs (bounded; skipped once a role gave up)
+  bool ok = !*(volatile int*)&fail_s && mbar_wait(done_bar, 0);
+  ok = __syncthreads_and(ok) && !fail_s;
+  if (!ok && tid == 0) {
+    atomicExch(&g_conv_timeout, 1u);
+    // bounded waits for the copies and MMAs still in flight
+    for (int ch = issued_s - S < 0 ? 0 : issued_s - S; ch < issued_s; ++ch)
+      mbar_wait(full(ch % S), (uint32_t)((ch / S) & 1));
+    if (committed_s > 0)
+      mbar_wait(empty((committed_s - 1) % S), (uint32_t)(((committed_s - 1) / S) & 1));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+
+  if (ok) {
+    // epilogue: TMEM lane 32 warp + lane = voxel (w = m % 8, h = m / 8)
+    const int m = warp * 32 + lane;
+    const int x = w0 + (m % TW), y = h0 + m / TW;
+#pragma unroll 1
+    for (int s = 0; s < TD; ++s) {
+      const int z = d0 + s;
+      const bool in = x < a.W && y < a.H && z < a.D;
       const long long vox = (((long long)n * a.D + z) * a.H + y) * a.W + x;
+#pragma unroll 1
+      for (int cb = 0; cb < N; cb += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * P::kTile + cb);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+            "%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (!in) continue;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const int co = f * 8 + tq * 2;
-        float v0 = acc[m][f][half * 2 + 0], v1 = acc[m][f][half * 2 + 1];
-        if (a.bias) {
-          v0 += a.bias[co];
-          v1 += a.bias[co + 1];
+        for (int j = 0; j < 16; j += 2) {
+          const int co = cb + j;
+          float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+          if (a.bias) {
+            v0 += a.bias[co];
+            v1 += a.bias[co + 1];
+          }
+          if (a.relu) {
+            v0 = fmaxf(v0, 0.0f);
+            v1 = fmaxf(v1, 0.0f);
+          }
+          const __nv_bfloat162 pr = __floats2bfloat162_rn(v0, v1);
+          if (co < a.O1)
+            *reinterpret_cast<__nv_bfloat162*>(a.y1 + vox * a.Ys1 + a.Yo1 + co) = pr;
+          else
+            *reinterpret_cast<__nv_bfloat162*>(a.y2 + vox * a.Ys2 + a.Yo2 + (co - a.O1)) = pr;
         }
-        if (a.relu) {
-          v0 = fmaxf(v0, 0.0f);
-          v1 = fmaxf(v1, 0.0f);
-        }
-        const __nv_bfloat162 pr = __floats2bfloat162_rn(v0, v1);
-        if (co < a.O1)
-          *reinterpret_cast<__nv_bfloat162*>(a.y1 + vox * a.Ys1 + a.Yo1 + co) = pr;
-        else
-          *reinterpret_cast<__nv_bfloat162*>(a.y2 + vox * a.Ys2 + a.Yo2 + (co - a.O1)) = pr;
       }
     }
   }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(P::kAlloc)
+                 : "memory");
 }
 
 // W'[ci][t][co] = W[co][26 - t][ci]: weights of the input-gradient conv.
@@ -465,36 +615,107 @@ __global__ void k_target(const double* phi, const double* prev, double scale, lo
 
 // ---- launchers ------------------------------------------------------------
 
-size_t conv_smem_bytes(int cout) { return (size_t)(HALO + 27 * cout) * ROWB; }
-
 bool conv_supported(int cin_total, int cout) {
   return cin_total % 16 == 0 && cin_total > 0 &&
          (cout == 16 || cout == 32 || cout == 48 || cout == 64 || cout == 96);
 }
 
+// cuTensorMapEncodeTiled, fetched from the driver once.
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// Halo map of a channels-last activation [n][d][h][w][c]: dims (c, w, h, d, n),
+// box (8 channels, HW, HH, mt + 2, 1), zero fill outside.
+static bool halo_map(CUtensorMap* m, const __nv_bfloat16* x, int c, const ConvArgs& a, int mt) {
+  const cuuint64_t dim[5] = {(cuuint64_t)c, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D,
+                             (cuuint64_t)a.N};
+  const cuuint64_t row = (cuuint64_t)c * 2;
+  const cuuint64_t stride[4] = {row, row * a.W, row * a.W * a.H, row * a.W * a.H * a.D};
+  const cuuint32_t box[5] = {8, HW, HH, (cuuint32_t)(mt + 2), 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return encode_tiled()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)x, dim, stride, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Weight map of w[co][tap][ci] seen as (8 channels, co, ci / 8, tap) with
+// strides (2 B, 27 Ct x 2 B, 16 B, Ct x 2 B): the box (8, cout, 2, 27) at
+// (0, 0, 2 chunk, 0) lands in shared memory as [tap][half][co] x 16 B.
+static bool weight_map(CUtensorMap* m, const __nv_bfloat16* w, int ct, int cout) {
+  const cuuint64_t dim[4] = {8, (cuuint64_t)cout, (cuuint64_t)(ct / 8), 27};
+  const cuuint64_t stride[3] = {(cuuint64_t)27 * ct * 2, 16, (cuuint64_t)ct * 2};
+  const cuuint32_t box[4] = {8, (cuuint32_t)cout, 2, 27};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return encode_tiled()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)w, dim, stride, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_conv3d(const ConvArgs& a, int cout, cudaStream_t s) {
-  const long long tiles = (long long)a.N * ((a.D + TD - 1) / TD) * ((a.H + TH - 1) / TH) *
-                          ((a.W + TW - 1) / TW);
-  const size_t sm = conv_smem_bytes(cout);
-  static bool attr_done[13] = {};
-  const int nf = cout / 8;
-  auto go = [&](auto kernel) {
-    if (!attr_done[nf]) {
-      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm + 1024);
-      attr_done[nf] = true;
+  const int ct = a.C1 + a.C2;
+  if (!conv_supported(ct, cout) || a.C1 % 16 || a.C2 % 16 || a.C1 <= 0 ||
+      ((uintptr_t)a.x1 | (uintptr_t)a.x2 | (uintptr_t)a.w) % 16)
+    return cudaErrorInvalidValue;
+  if (!encode_tiled()) return cudaErrorNotSupported;
+  // two M-tiles per CTA when that still gives two waves of CTAs on 152 SMs
+  const long long plane = (long long)a.N * ((a.H + TH - 1) / TH) * ((a.W + TW - 1) / TW);
+  const int mt = plane * ((a.D + 1) / 2) >= 2 * 152 ? 2 : 1;
+  const long long tiles = plane * ((a.D + mt - 1) / mt);
+  CUtensorMap mx1, mx2, mw;
+  if (!halo_map(&mx1, a.x1, a.C1, a, mt) ||
+      (a.C2 > 0 ? !halo_map(&mx2, a.x2, a.C2, a, mt) : false) || !weight_map(&mw, a.w, ct, cout))
+    return cudaErrorInvalidValue;
+  if (a.C2 == 0) mx2 = mx1;
+  // one stage once the CTAs fill the SMs twice, else two (when there are
+  // two chunks)
+  const int stages = tiles >= 2 * 152 || ct == 16 ? 1 : 2;
+  static bool attr_done[2][5] = {};
+  auto go = [&](auto kernel, auto plan, int slot) {
+    using P = decltype(plan);
+    static_assert(P::smem(kMaxStages) <= 227 * 1024 - 1024, "two stages fit");
+    if (!attr_done[mt - 1][slot]) {
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           P::smem(kMaxStages));
+      attr_done[mt - 1][slot] = true;
     }
-    kernel<<<(unsigned)tiles, kConvThreads, sm, s>>>(a);
+    kernel<<<(unsigned)tiles, kConvThreads, P::smem(stages), s>>>(a, mx1, mx2, mw, stages);
   };
-  switch (nf) {
-    case 2: go(k_conv3d<2>); break;
-    case 4: go(k_conv3d<4>); break;
-    case 6: go(k_conv3d<6>); break;
-    case 8: go(k_conv3d<8>); break;
-    case 12: go(k_conv3d<12>); break;
+#define CONV_CASE(C, SLOT)                                                   \
+  case C:                                                                    \
+    if (mt == 2)                                                             \
+      go(k_conv3d<C, 2>, ConvPlan<C, 2>{}, SLOT);                            \
+    else                                                                     \
+      go(k_conv3d<C, 1>, ConvPlan<C, 1>{}, SLOT);                            \
+    break;
+  switch (cout) {
+    CONV_CASE(16, 0)
+    CONV_CASE(32, 1)
+    CONV_CASE(48, 2)
+    CONV_CASE(64, 3)
+    CONV_CASE(96, 4)
     default: return cudaErrorInvalidValue;
   }
+#undef CONV_CASE
   add_launches(1);
   return cudaGetLastError();
+}
+
+bool conv_timed_out() {
+  unsigned v = 0;
+  cudaMemcpyFromSymbol(&v, g_conv_timeout, sizeof(v));
+  return v != 0;
 }
 
 void launch_flip_weights(const __nv_bfloat16* w, int co, int ci, __nv_bfloat16* wt,

@@ -483,6 +483,7 @@ mg_status mg_unet_grads(mg_unet* u, const double* rho, const double* prev, const
   NN_TRY(run_forward(u, rho, prev, phi, n, d, h, w, s));
   NN_TRY(backward(u, s));
   NN_CUDA(cudaStreamSynchronize(s));
+  if (conv_timed_out()) return nn_fail(MG_ERR_CUDA, "conv3d: a tensor-core completion wait gave up");
   long long off = 0;
   cudaError_t e = cudaSuccess;
   for_each_conv(u, [&](Conv& c) {
@@ -524,6 +525,8 @@ mg_status mg_unet_train_step(mg_unet* u, const double* rho, const double* prev, 
   if (loss) {
     NN_CUDA(cudaMemcpyAsync(loss, u->act.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
     NN_CUDA(cudaStreamSynchronize(s));
+    if (conv_timed_out())
+      return nn_fail(MG_ERR_CUDA, "conv3d: a tensor-core completion wait gave up");
   }
   return MG_OK;
 }
@@ -582,9 +585,12 @@ mg_status mg_nn_conv3d(const void* x1, int c1, const void* x2, int c2, const voi
                        const float* bias, int relu, int cout, int n, int d, int h, int w_,
                        void* y, void* cuda_stream) {
   if (!x1 || !w || !y || (c2 > 0 && !x2)) return nn_fail(MG_ERR_INVALID_ARG, "NULL argument");
-  if (!conv_supported(c1 + c2, cout) || c1 % 16 || c2 % 16 || n < 1 || d < 1 || h < 1 || w_ < 1)
+  if (!conv_supported(c1 + c2, cout) || c1 < 16 || c1 % 16 || c2 % 16 || n < 1 || d < 1 ||
+      h < 1 || w_ < 1)
     return nn_fail(MG_ERR_UNSUPPORTED,
                    "conv3d: channels must be multiples of 16, cout in {16,32,48,64,96}");
+  if (((uintptr_t)x1 | (uintptr_t)x2 | (uintptr_t)w) % 16)
+    return nn_fail(MG_ERR_INVALID_ARG, "conv3d: x1, x2 and w must be 16-byte aligned");
   ConvArgs a{};
   a.x1 = (const bf16*)x1;
   a.C1 = c1;

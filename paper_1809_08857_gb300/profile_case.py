@@ -9,7 +9,13 @@
   python -m paper_1809_08857_gb300.profile_case --case amr256
       one composite AMR Poisson solve: base 256^3 with three nested refined
       levels around the streamer head (workloads.streamer_amr_layout), mixed
-      precision, two inner V-cycles, from zero to 1e-10.
+      precision, two inner V-cycles, from zero to 1e-10;
+  python -m paper_1809_08857_gb300.profile_case --case conv128
+      one 3x3x3 convolution, 32 -> 32 channels on a 128^3 BF16 volume (128 MiB
+      in, 128 MiB out), three untimed launches, then 20 timed with CUDA events;
+  python -m paper_1809_08857_gb300.profile_case --case conv_shapes
+      the same timing for the convolution shapes of the U-Net levels (batch 2
+      at 64^3 .. 8^3) and two 128^3 volumes.
 """
 import argparse
 import os
@@ -66,11 +72,44 @@ def amr256():
     a.close()
 
 
+def _time_conv(n, s, cin, cout, reps=20):
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = (torch.randn((n, s, s, s, cin), generator=g) * 0.5).to(torch.bfloat16).cuda()
+    w = (torch.randn((cout, 27, cin), generator=g) * 0.1).to(torch.bfloat16).cuda()
+    b = torch.randn(cout, generator=g).cuda()
+    for _ in range(3):
+        y = mg.conv3d(x, w, b, relu=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        y = mg.conv3d(x, w, b, relu=True)
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) / reps * 1e3
+    flop = 2.0 * 27 * cin * cout * n * s ** 3
+    print(f"conv {n} x {s}^3 {cin}->{cout}: {us:.1f} us per launch, "
+          f"{flop / us * 1e-6:.1f} TFLOP/s, checksum {float(y.float().sum()):.6e}")
+
+
+def conv128():
+    _time_conv(1, 128, 32, 32)
+
+
+def conv_shapes():
+    for shape in [(2, 64, 16, 16), (2, 64, 32, 16), (2, 32, 16, 32), (2, 32, 32, 32),
+                  (2, 32, 64, 32), (2, 16, 32, 48), (2, 16, 48, 48), (2, 16, 96, 48),
+                  (2, 8, 48, 64), (2, 8, 64, 64), (1, 128, 16, 16), (1, 128, 32, 32)]:
+        _time_conv(*shape)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["solve256", "unet64", "amr256"], required=True)
+    cases = {"solve256": solve256, "unet64": unet64, "amr256": amr256, "conv128": conv128,
+             "conv_shapes": conv_shapes}
+    ap.add_argument("--case", choices=sorted(cases), required=True)
     args = ap.parse_args()
-    {"solve256": solve256, "unet64": unet64, "amr256": amr256}[args.case]()
+    cases[args.case]()
 
 
 if __name__ == "__main__":

@@ -106,3 +106,23 @@ def test_amr_create_rejects_bad_hierarchies_without_gpu(lib, boxes, msg):
     assert not out.value
     assert lib.mg_amr_solve(None, 0, 0.0, None, None, 1e-10, None) == mg.MG_ERR_INVALID_ARG
     lib.mg_amr_destroy(None)
+
+
+def test_conv3d_rejects_bad_arguments_without_gpu(lib):
+    """The network convolution checks channels and 16-byte alignment (its
+    operands are read by tiled tensor copies) before touching any memory;
+    the pointer values below are never dereferenced."""
+    from paper_1809_08857_gb300 import mg
+
+    P = ctypes.c_void_p
+    good, odd = P(0x10000), P(0x10002)
+    conv = lib.mg_nn_conv3d
+    args = lambda x1, c1, x2, c2, w, cout: (x1, c1, x2, c2, w, None, 1, cout, 1, 8, 8, 8, good, None)
+    assert conv(*args(odd, 16, None, 0, good, 16)) == mg.MG_ERR_INVALID_ARG
+    assert b"aligned" in lib.mg_last_error()
+    assert conv(*args(good, 16, odd, 16, good, 16)) == mg.MG_ERR_INVALID_ARG
+    assert conv(*args(good, 16, None, 0, odd, 32)) == mg.MG_ERR_INVALID_ARG
+    assert conv(*args(good, 24, None, 0, good, 16)) == mg.MG_ERR_UNSUPPORTED
+    assert conv(*args(good, 0, good, 16, good, 16)) == mg.MG_ERR_UNSUPPORTED
+    assert conv(*args(good, 16, None, 0, good, 80)) == mg.MG_ERR_UNSUPPORTED
+    assert conv(*args(None, 16, None, 0, good, 16)) == mg.MG_ERR_INVALID_ARG
