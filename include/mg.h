@@ -460,9 +460,14 @@ mg_status mg_unet_load(mg_unet* net, const char* path);
 mg_status mg_nn_conv3d(const void* x1, int c1, const void* x2, int c2, const void* w,
                        const float* bias, int relu, int cout, int n, int d, int h, int w_,
                        void* y, void* cuda_stream);
-/* Its weight gradient dW[co][t][ci] = sum_v dy[v][co] x[v + off(t)][ci] (FP32, overwritten). */
+/* Its weight gradient dW[co][t][ci] = sum_v dy[v][co] x[v + off(t)][ci] (FP32, overwritten)
+ * and, when db is not NULL, the bias gradient db[co] = sum_v dy[v][co] (FP32, overwritten),
+ * on the tensor cores (BF16 products, FP32 sums; the order of the sums varies
+ * from run to run).  Same channel rules as mg_nn_conv3d; dy, x1 and x2 must be
+ * 16-byte aligned. */
 mg_status mg_nn_conv3d_wgrad(const void* dy, int cout, const void* x1, int c1, const void* x2,
-                             int c2, int n, int d, int h, int w, float* dw, void* cuda_stream);
+                             int c2, int n, int d, int h, int w, float* dw, float* db,
+                             void* cuda_stream);
 
 /* Attach a network to a context (not owned; NULL detaches), or load one from
  * a file (owned by the context). */

@@ -48,10 +48,10 @@ void launch_up(const __nv_bfloat16* x, int N, int D, int H, int W, int C, __nv_b
                cudaStream_t s);
 void launch_up_bwd(const __nv_bfloat16* dy, int N, int D, int H, int W, int C, __nv_bfloat16* dx,
                    cudaStream_t s);
+// dw += weight gradient; db += bias gradient when db is not null.
 cudaError_t launch_wgrad(const __nv_bfloat16* dy, int co, const __nv_bfloat16* x1, int c1,
                          const __nv_bfloat16* x2, int c2, int N, int D, int H, int W, float* dw,
-                         cudaStream_t s);
-void launch_bias_grad(const __nv_bfloat16* dy, long long nvox, int C, float* db, cudaStream_t s);
+                         float* db, cudaStream_t s);
 void launch_head(const __nv_bfloat16* x, int C, const float* w, const float* b, long long nvox,
                  float* out, cudaStream_t s);
 void launch_head_bwd(const __nv_bfloat16* x, int C, const float* w, const float* g,

@@ -423,100 +423,200 @@ __global__ void k_up_bwd(const __nv_bfloat16* dy, int N, int D, int H, int W, in
   dx[q] = __float2bfloat16(s);
 }
 
-// dW[co][t][ci] += sum_v dY[v][co] X[v + off(t)][ci]: one CTA per (tap, voxel
-// split); each thread owns a 4 x 4 block of (co, ci); voxels are staged in
-// shared memory 32 at a time.  FP32 CUDA cores, FP32 atomics per CTA.
-template <int CO, int CI>
-__global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__ dy,
-                                               const __nv_bfloat16* __restrict__ x1, int C1,
-                                               const __nv_bfloat16* __restrict__ x2, int C2,
-                                               int N, int D, int H, int W, float* dw,
-                                               int splits) {
-  constexpr int VB = 32;
-  constexpr int BCO = CO / 4, BCI = CI / 4;  // 4 x 4 (co, ci) blocks
-  constexpr int NB = (BCO * BCI + 255) / 256;
-  __shared__ float sdy[VB][CO];
-  __shared__ float sx[VB][CI + 1];
-  const int tap = blockIdx.x;
-  const int kw = tap % 3 - 1, kh = (tap / 3) % 3 - 1, kd = tap / 9 - 1;
-  const long long nvox = (long long)N * D * H * W;
-  const long long per = (nvox + splits - 1) / splits;
-  const long long v0 = blockIdx.y * per, v1 = min(nvox, v0 + per);
-  float acc[NB][4][4] = {};
-  for (long long vb = v0; vb < v1; vb += VB) {
-    for (int q = threadIdx.x; q < VB * (CO + CI); q += 256) {
-      const int r = q / (CO + CI), c = q % (CO + CI);
-      const long long v = vb + r;
-      float val = 0.0f;
-      if (v < v1) {
-        if (c < CO) {
-          val = __bfloat162float(dy[v * CO + c]);
-        } else {
-          long long t = v;
-          const int xx = (int)(t % W);
-          t /= W;
-          const int yy = (int)(t % H);
-          t /= H;
-          const int zz = (int)(t % D);
-          const int nn = (int)(t / D);
-          const int xs = xx + kw, ys = yy + kh, zs = zz + kd;
-          if (xs >= 0 && xs < W && ys >= 0 && ys < H && zs >= 0 && zs < D) {
-            const long long src = (((long long)nn * D + zs) * H + ys) * W + xs;
-            const int ci = c - CO;
-            val = ci < C1 ? __bfloat162float(x1[src * C1 + ci])
-                          : __bfloat162float(x2[src * C2 + ci - C1]);
-          }
-        }
-      }
-      if (c < CO) sdy[r][c] = val;
-      else sx[r][c - CO] = val;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int nb = 0; nb < NB; ++nb) {
-      const int blk = threadIdx.x + nb * 256;
-      if (blk < BCO * BCI) {
-        const int bo = blk / BCI, bi = blk % BCI;
-#pragma unroll 4
-        for (int r = 0; r < VB; ++r) {
-          float dv[4], xv[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            dv[q] = sdy[r][bo * 4 + q];
-            xv[q] = sx[r][bi * 4 + q];
-          }
-#pragma unroll
-          for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[nb][p][q] = fmaf(dv[p], xv[q], acc[nb][p][q]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int nb = 0; nb < NB; ++nb) {
-    const int blk = threadIdx.x + nb * 256;
-    if (blk < BCO * BCI) {
-      const int bo = blk / BCI, bi = blk % BCI;
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          atomicAdd(&dw[((long long)(bo * 4 + p) * 27 + tap) * CI + bi * 4 + q], acc[nb][p][q]);
-    }
-  }
-}
+// Weight gradient dW[co][t][ci] += sum_v dY[v][co] X[v + off(t)][ci] on the
+// tensor cores.  GEMM rows are (tap, 8-channel input group) pairs, 16 groups
+// (128 rows) per M-tile; N = Cout; K runs over voxels, 128 per stage (a box
+// of 8 x 4 x 4 voxels).  Both operands are MN-major in shared memory: the
+// tiled tensor copy of a box of one 8-channel group is [voxel][8 channels],
+// i.e. core matrices of 8 voxels (K) x 16 bytes (8 rows), so the copy lands
+// directly in the operand layout (lbo = 128 B between 8-voxel blocks, sbo =
+// one group's box between row groups).  The input box of group (t, c) is
+// the output box shifted by tap t's offset; zero fill at the volume's edge is
+// the convolution's padding, and voxels of a box beyond the volume carry a
+// zero dY.  A CTA accumulates its range of boxes in TMEM and adds the result
+// to dW with FP32 atomics.  With db given, the last M-tile's first unused
+// group holds BF16 ones, so its rows accumulate db[co] += sum_v dY[v][co].
+// Producer / MMA / epilogue roles and bounded waits as in k_conv3d.
+constexpr int kWgBX = 8, kWgBY = 4, kWgBZ = 4;         // voxel box of one stage
+constexpr int kWgKV = kWgBX * kWgBY * kWgBZ;           // K per stage (128)
+constexpr int kWgGroups = 16;                          // 8-row groups per M-tile
 
-// db[c] += sum_v dY[v][c]
-__global__ void k_bias_grad(const __nv_bfloat16* dy, long long nvox, int C, float* db) {
-  const int c = blockIdx.y;
-  float s = 0.0f;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nvox;
-       v += (long long)gridDim.x * blockDim.x)
-    s += __bfloat162float(dy[v * C + c]);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&db[c], s);
+template <int N>
+struct WgPlan {
+  static constexpr int kGroupBytes = kWgKV * 16;        // one group's box (2 KB)
+  static constexpr int kABytes = kWgGroups * kGroupBytes;
+  static constexpr int kStage = kABytes + N / 8 * kGroupBytes;
+  static constexpr int smem(int stages) { return stages * kStage + 1024; }
+  static constexpr int kAlloc = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+};
+
+struct WgArgs {
+  int C1, C2, N, D, H, W;
+  float* dw;
+  float* db;     // nullable
+  int splits;    // CTAs sharing an M-tile (voxel ranges)
+};
+
+template <int N>
+__global__ void __launch_bounds__(kConvThreads)
+    k_wgrad_tc(WgArgs a, const __grid_constant__ CUtensorMap map_x1,
+               const __grid_constant__ CUtensorMap map_x2,
+               const __grid_constant__ CUtensorMap map_dy, int S) {
+  using P = WgPlan<N>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * kMaxStages + 1];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int issued_s, committed_s, fail_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ci_total = a.C1 + a.C2, c8 = ci_total / 8;
+  const int groups = 27 * c8;
+  const int g0 = blockIdx.y * kWgGroups;
+  const int ng = min(kWgGroups, groups - g0);
+  const int bias_g = (a.db && ng < kWgGroups) ? ng : -1;  // the group of ones
+  const int nbx = (a.W + kWgBX - 1) / kWgBX, nby = (a.H + kWgBY - 1) / kWgBY,
+            nbz = (a.D + kWgBZ - 1) / kWgBZ;
+  const long long nboxes = (long long)a.N * nbz * nby * nbx;
+  const long long per = (nboxes + a.splits - 1) / a.splits;
+  const long long b0 = blockIdx.x * per;
+  const int nk = (int)max(0ll, min(nboxes, b0 + per) - b0);
+  if (nk == 0) return;  // uniform over the CTA
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t bar0 = smem_u32(&bars[0]);
+  auto full = [&](int st) { return bar0 + 8u * (uint32_t)st; };
+  auto empty = [&](int st) { return bar0 + 8u * (uint32_t)(kMaxStages + st); };
+  const uint32_t done_bar = bar0 + 8u * (uint32_t)(2 * kMaxStages);
+
+  if (bias_g >= 0) {
+    // the ones group of every stage (never written by the copies)
+    unsigned char* sm = smem_raw + (base - smem_u32(smem_raw));
+    const uint4 ones = make_uint4(0x3f803f80u, 0x3f803f80u, 0x3f803f80u, 0x3f803f80u);
+    for (int q = tid; q < S * (P::kGroupBytes / 16); q += kConvThreads) {
+      const int st = q / (P::kGroupBytes / 16), e = q % (P::kGroupBytes / 16);
+      *reinterpret_cast<uint4*>(sm + st * P::kStage + bias_g * P::kGroupBytes + e * 16) = ones;
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 2 * kMaxStages + 1; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8u * i) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    issued_s = 0;
+    committed_s = 0;
+    fail_s = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(P::kAlloc)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (tid == 0) {
+    // producer
+    for (int i = 0; i < nk; ++i) {
+      const int st = i % S;
+      if (i >= S && !mbar_wait(empty(st), (uint32_t)((i / S - 1) & 1))) {
+        atomicExch(&fail_s, 1);
+        break;
+      }
+      if (*(volatile int*)&fail_s) break;
+      long long b = b0 + i;
+      const int x0 = (int)(b % nbx) * kWgBX;
+      b /= nbx;
+      const int y0 = (int)(b % nby) * kWgBY;
+      b /= nby;
+      const int z0 = (int)(b % nbz) * kWgBZ;
+      const int n = (int)(b / nbz);
+      const uint32_t stage = base + (uint32_t)(st * P::kStage);
+      mbar_expect_tx(full(st), (uint32_t)((ng + N / 8) * P::kGroupBytes));
+      for (int g = 0; g < ng; ++g) {
+        const int G = g0 + g, t = G / c8, ch = (G % c8) * 8;
+        const int kw = t % 3, kh = (t / 3) % 3, kd = t / 9;
+        const bool first = ch < a.C1;
+        tma_load_5d(stage + (uint32_t)(g * P::kGroupBytes), first ? &map_x1 : &map_x2, full(st),
+                    first ? ch : ch - a.C1, x0 + kw - 1, y0 + kh - 1, z0 + kd - 1, n);
+      }
+      for (int j = 0; j < N / 8; ++j)
+        tma_load_5d(stage + (uint32_t)(P::kABytes + j * P::kGroupBytes), &map_dy, full(st), 8 * j,
+                    x0, y0, z0, n);
+      issued_s = i + 1;
+    }
+  } else if (tid == 32) {
+    // MMA issue: both operands MN-major (instruction descriptor bits 15, 16)
+    const uint32_t idesc = instr_desc(kMmaM, N) | (1u << 15) | (1u << 16);
+    for (int i = 0; i < nk; ++i) {
+      const int st = i % S;
+      if (!mbar_wait(full(st), (uint32_t)((i / S) & 1))) {
+        atomicExch(&fail_s, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t stage = base + (uint32_t)(st * P::kStage);
+#pragma unroll 1
+      for (int kk = 0; kk < kWgKV / 16; ++kk) {
+        const uint64_t ad = smem_desc(stage + 256u * kk, 128, P::kGroupBytes);
+        const uint64_t bd = smem_desc(stage + P::kABytes + 256u * kk, 128, P::kGroupBytes);
+        mma_f16(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              empty(st))
+          : "memory");
+      committed_s = i + 1;
+    }
+    if (!*(volatile int*)&fail_s)
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              done_bar)
+          : "memory");
+  }
+  __syncwarp();
+  bool ok = !*(volatile int*)&fail_s && mbar_wait(done_bar, 0);
+  ok = __syncthreads_and(ok) && !fail_s;
+  if (!ok && tid == 0) {
+    atomicExch(&g_conv_timeout, 1u);
+    for (int i = issued_s - S < 0 ? 0 : issued_s - S; i < issued_s; ++i)
+      mbar_wait(full(i % S), (uint32_t)((i / S) & 1));
+    if (committed_s > 0)
+      mbar_wait(empty((committed_s - 1) % S), (uint32_t)(((committed_s - 1) / S) & 1));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+
+  if (ok) {
+    // epilogue: TMEM lane r = row (group r / 8, channel r % 8 of the group)
+    const int r = warp * 32 + lane, g = r / 8;
+    const int G = g0 + g, t = G / c8, ci = (G % c8) * 8 + r % 8;
+    const bool wrow = g < ng, brow = g == bias_g && r % 8 == 0;
+#pragma unroll 1
+    for (int cb = 0; cb < N; cb += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+          "%12,%13,%14,%15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+            "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+            "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (wrow)
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          atomicAdd(&a.dw[((long long)(cb + j) * 27 + t) * ci_total + ci], __uint_as_float(v[j]));
+      if (brow)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) atomicAdd(&a.db[cb + j], __uint_as_float(v[j]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(P::kAlloc)
+                 : "memory");
 }
 
 // 1x1x1 head: out[v] = sum_c x[v][c] w[c] + b (FP32 output)
@@ -754,30 +854,64 @@ void launch_up_bwd(const __nv_bfloat16* dy, int N, int D, int H, int W, int C, _
   add_launches(1);
 }
 
-cudaError_t launch_wgrad(const __nv_bfloat16* dy, int co, const __nv_bfloat16* x1, int c1,
-                         const __nv_bfloat16* x2, int c2, int N, int D, int H, int W, float* dw,
-                         cudaStream_t s) {
-  const long long nvox = (long long)N * D * H * W;
-  int splits = (int)std::min<long long>(4096, (nvox + 1023) / 1024);
-  if (splits < 1) splits = 1;
-  dim3 g(27, splits);
-  const int ci = c1 + c2;
-#define WG(CO_, CI_)                                                                       \
-  if (co == CO_ && ci == CI_) {                                                            \
-    k_wgrad<CO_, CI_><<<g, 256, 0, s>>>(dy, x1, c1, x2, c2, N, D, H, W, dw, splits);       \
-    add_launches(1);                                                                       \
-    return cudaGetLastError();                                                             \
-  }
-  WG(16, 16) WG(32, 16) WG(32, 32) WG(48, 32) WG(48, 48) WG(64, 48) WG(64, 64)
-  WG(48, 64) WG(48, 96) WG(32, 48) WG(32, 64) WG(16, 32)
-#undef WG
-  return cudaErrorInvalidValue;
+// Map of a channels-last tensor [n][d][h][w][c] for the weight gradient:
+// box (8 channels, 8, 4, 4 voxels, 1), zero fill outside.
+static bool wg_map(CUtensorMap* m, const __nv_bfloat16* x, int c, int N, int D, int H, int W) {
+  const cuuint64_t dim[5] = {(cuuint64_t)c, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D,
+                             (cuuint64_t)N};
+  const cuuint64_t row = (cuuint64_t)c * 2;
+  const cuuint64_t stride[4] = {row, row * W, row * W * H, row * W * H * D};
+  const cuuint32_t box[5] = {8, kWgBX, kWgBY, kWgBZ, 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return encode_tiled()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)x, dim, stride, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-void launch_bias_grad(const __nv_bfloat16* dy, long long nvox, int C, float* db, cudaStream_t s) {
-  dim3 g((unsigned)std::min<long long>(1024, (nvox + 255) / 256), C);
-  k_bias_grad<<<g, 256, 0, s>>>(dy, nvox, C, db);
+cudaError_t launch_wgrad(const __nv_bfloat16* dy, int co, const __nv_bfloat16* x1, int c1,
+                         const __nv_bfloat16* x2, int c2, int N, int D, int H, int W, float* dw,
+                         float* db, cudaStream_t s) {
+  const int ci = c1 + c2;
+  if (!conv_supported(ci, co) || c1 % 16 || c2 % 16 || c1 <= 0 ||
+      ((uintptr_t)dy | (uintptr_t)x1 | (uintptr_t)x2) % 16)
+    return cudaErrorInvalidValue;
+  if (!encode_tiled()) return cudaErrorNotSupported;
+  CUtensorMap mx1, mx2, mdy;
+  if (!wg_map(&mx1, x1, c1, N, D, H, W) || (c2 > 0 && !wg_map(&mx2, x2, c2, N, D, H, W)) ||
+      !wg_map(&mdy, dy, co, N, D, H, W))
+    return cudaErrorInvalidValue;
+  if (c2 == 0) mx2 = mx1;
+  // with db, one group more: the ones (an extra M-tile when the last is full)
+  const int mtiles = (27 * ci / 8 + (db ? 1 : 0) + kWgGroups - 1) / kWgGroups;
+  const long long nboxes = (long long)N * ((D + kWgBZ - 1) / kWgBZ) *
+                           ((H + kWgBY - 1) / kWgBY) * ((W + kWgBX - 1) / kWgBX);
+  // about two CTAs per SM in one wave, each over a contiguous range of boxes
+  WgArgs a{c1, c2, N, D, H, W, dw, db, 1};
+  a.splits = (int)std::max<long long>(1, std::min<long long>(nboxes, (2 * 152 + mtiles - 1) / mtiles));
+  const int stages = 2;
+  static bool attr_done[5] = {};
+  auto go = [&](auto kernel, auto plan, int slot) {
+    using P = decltype(plan);
+    static_assert(P::smem(kMaxStages) <= 227 * 1024 - 1024, "two stages fit");
+    if (!attr_done[slot]) {
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           P::smem(kMaxStages));
+      attr_done[slot] = true;
+    }
+    kernel<<<dim3((unsigned)a.splits, (unsigned)mtiles), kConvThreads, P::smem(stages), s>>>(
+        a, mx1, mx2, mdy, stages);
+  };
+  switch (co) {
+    case 16: go(k_wgrad_tc<16>, WgPlan<16>{}, 0); break;
+    case 32: go(k_wgrad_tc<32>, WgPlan<32>{}, 1); break;
+    case 48: go(k_wgrad_tc<48>, WgPlan<48>{}, 2); break;
+    case 64: go(k_wgrad_tc<64>, WgPlan<64>{}, 3); break;
+    case 96: go(k_wgrad_tc<96>, WgPlan<96>{}, 4); break;
+    default: return cudaErrorInvalidValue;
+  }
   add_launches(1);
+  return cudaGetLastError();
 }
 
 void launch_head(const __nv_bfloat16* x, int C, const float* w, const float* b, long long nvox,

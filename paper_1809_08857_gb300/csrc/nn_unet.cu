@@ -212,8 +212,7 @@ mg_status conv_bwd(Conv& c, const bf16* x1, const bf16* x2, const bf16* y, bf16*
                    bf16* g2, int N, int D, int H, int W, cudaStream_t s) {
   const long long nv = (long long)N * D * H * W;
   launch_relu_bwd(y, gy, nv * c.cout, s);
-  NN_CUDA(launch_wgrad(gy, c.cout, x1, c.cin1, x2, c.cin2, N, D, H, W, c.dw, s));
-  launch_bias_grad(gy, nv, c.cout, c.db, s);
+  NN_CUDA(launch_wgrad(gy, c.cout, x1, c.cin1, x2, c.cin2, N, D, H, W, c.dw, c.db, s));
   if (g1) {
     ConvArgs a{};
     a.x1 = gy;
@@ -611,12 +610,20 @@ mg_status mg_nn_conv3d(const void* x1, int c1, const void* x2, int c2, const voi
 }
 
 mg_status mg_nn_conv3d_wgrad(const void* dy, int cout, const void* x1, int c1, const void* x2,
-                             int c2, int n, int d, int h, int w, float* dw, void* cuda_stream) {
+                             int c2, int n, int d, int h, int w, float* dw, float* db,
+                             void* cuda_stream) {
   if (!dy || !x1 || !dw || (c2 > 0 && !x2)) return nn_fail(MG_ERR_INVALID_ARG, "NULL argument");
+  if (!conv_supported(c1 + c2, cout) || c1 < 16 || c1 % 16 || c2 % 16 || n < 1 || d < 1 ||
+      h < 1 || w < 1)
+    return nn_fail(MG_ERR_UNSUPPORTED,
+                   "conv3d_wgrad: channels must be multiples of 16, cout in {16,32,48,64,96}");
+  if (((uintptr_t)dy | (uintptr_t)x1 | (uintptr_t)x2) % 16)
+    return nn_fail(MG_ERR_INVALID_ARG, "conv3d_wgrad: dy, x1 and x2 must be 16-byte aligned");
   NN_CUDA(cudaMemsetAsync(dw, 0, (size_t)cout * 27 * (c1 + c2) * sizeof(float),
                           (cudaStream_t)cuda_stream));
+  if (db) NN_CUDA(cudaMemsetAsync(db, 0, (size_t)cout * sizeof(float), (cudaStream_t)cuda_stream));
   NN_CUDA(launch_wgrad((const bf16*)dy, cout, (const bf16*)x1, c1, (const bf16*)x2, c2, n, d, h, w,
-                       dw, (cudaStream_t)cuda_stream));
+                       dw, db, (cudaStream_t)cuda_stream));
   return MG_OK;
 }
 

@@ -177,7 +177,7 @@ def load():
     lib.mg_unet_save.argtypes = [P, ctypes.c_char_p]
     lib.mg_unet_load.argtypes = [P, ctypes.c_char_p]
     lib.mg_nn_conv3d.argtypes = [P, I, P, I, P, P, I, I, I, I, I, I, P, P]
-    lib.mg_nn_conv3d_wgrad.argtypes = [P, I, P, I, P, I, I, I, I, I, P, P]
+    lib.mg_nn_conv3d_wgrad.argtypes = [P, I, P, I, P, I, I, I, I, I, P, P, P]
     lib.mg_warmstart_attach.argtypes = [P, P]
     lib.mg_warmstart_load.argtypes = [P, ctypes.c_char_p]
     lib.mg_warmstart_predict.argtypes = [P, P, P, P, ctypes.POINTER(I)]
@@ -632,16 +632,20 @@ def conv3d(x1, w, bias=None, x2=None, relu=False, stream=None):
     return y
 
 
-def conv3d_wgrad(dy, x1, x2=None, stream=None):
-    """Weight gradient (mg_nn_conv3d_wgrad) as float32 (cout, 27, c1 + c2)."""
+def conv3d_wgrad(dy, x1, x2=None, stream=None, bias=False):
+    """Weight gradient (mg_nn_conv3d_wgrad) as float32 (cout, 27, c1 + c2);
+    with bias=True also the bias gradient, float32 (cout,): (dw, db)."""
     n, d, h, ww, cout = dy.shape
     c1 = x1.shape[-1]
     c2 = 0 if x2 is None else x2.shape[-1]
     dw = torch.empty((cout, 27, c1 + c2), dtype=torch.float32, device=dy.device)
+    db = torch.empty((cout,), dtype=torch.float32, device=dy.device) if bias else None
     _check(load().mg_nn_conv3d_wgrad(_ptr(dy, torch.bfloat16), cout, _ptr(x1, torch.bfloat16), c1,
                                      None if x2 is None else _ptr(x2, torch.bfloat16), c2, n, d, h,
-                                     ww, _ptr(dw, torch.float32), _stream_handle(stream)))
-    return dw
+                                     ww, _ptr(dw, torch.float32),
+                                     None if db is None else _ptr(db, torch.float32),
+                                     _stream_handle(stream)))
+    return (dw, db) if bias else dw
 
 
 class Amr:

@@ -51,17 +51,30 @@ def test_conv3d_matches_oracle(mg, shape, c1, c2, cout, relu):
     assert np.all(np.abs(got - ref) <= 2.0**-8 * np.abs(ref) + 1e-4 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("cout,c1,c2", [(16, 16, 0), (48, 48, 48), (64, 64, 0), (32, 16, 0)])
-def test_wgrad_matches_oracle(mg, cout, c1, c2):
+@pytest.mark.parametrize("cout,c1,c2,shape", [
+    (16, 16, 0, (2, 4, 6, 9)),      # ragged against the 8 x 4 x 4 voxel box
+    (48, 48, 48, (2, 4, 6, 9)),     # concatenated input
+    (64, 64, 0, (2, 4, 6, 9)),
+    (32, 16, 0, (2, 4, 6, 9)),
+    (96, 32, 16, (1, 5, 7, 10)),    # widest output
+    (16, 16, 0, (2, 32, 32, 32)),   # several boxes per CTA: both stages reused
+])
+def test_wgrad_matches_oracle(mg, cout, c1, c2, shape):
+    """Weight and bias gradients on the tensor cores against the oracle's
+    plain per-tap products (FP32 sums in a run-dependent order)."""
     rng = np.random.default_rng(cout * 7 + c1)
-    n, d, h, w = 2, 4, 6, 9
+    n, d, h, w = shape
     x1 = U.to_bf16(rng.standard_normal((n, d, h, w, c1)))
     x2 = U.to_bf16(rng.standard_normal((n, d, h, w, c2))) if c2 else None
     dy = U.to_bf16(rng.standard_normal((n, d, h, w, cout)))
-    dw = mg.conv3d_wgrad(bf(dy), bf(x1), None if x2 is None else bf(x2)).cpu().numpy()
+    dw, db = mg.conv3d_wgrad(bf(dy), bf(x1), None if x2 is None else bf(x2), bias=True)
+    dw, db = dw.cpu().numpy(), db.cpu().numpy()
     xin = x1 if x2 is None else np.concatenate([x1, x2], axis=-1)
-    _, ref, _ = U.conv3d_backward(xin, np.zeros((cout, 27, c1 + c2)), dy)
+    _, ref, refb = U.conv3d_backward(xin, np.zeros((cout, 27, c1 + c2)), dy)
     assert np.abs(dw - ref).max() <= 1e-5 * np.abs(ref).max()
+    # each |sum| is at most the sum of |dy|: FP32 rounding of that many terms
+    bound = np.abs(dy).reshape(-1, cout).sum(axis=0)
+    assert np.all(np.abs(db - refb) <= 1e-6 * bound + 1e-6)
 
 
 def _batch(rng, n, s):
