@@ -332,6 +332,42 @@ def measure_extras(solver, rho, eps, phi, n, dev):
                                "alpha": alpha}}
 
 
+def measure_unet(dev, n=256, reps=5):
+    """One warm-start U-Net forward pass (mg_unet_predict) on a 256^3 volume
+    (outside the timed region): device time per pass (CUDA events) and the
+    convolutions' FLOPs over that time (pooling, upsampling, head and input
+    packing included in the time), as a fraction of the measured BF16 dense
+    peak (burst: the pass is timed on its own)."""
+    import torch
+
+    from paper_1809_08857_gb300 import mg, workloads as W
+
+    pk, _ = peaks()
+    net = mg.UNet(seed=0)
+    net.set_scales(1.0, 1.0, 1.0)
+    rho = torch.from_numpy(W.streamer_shell(n, 0)).to(dev)
+    prev = torch.zeros_like(rho)
+    out = torch.empty_like(rho)
+    for _ in range(2):
+        net.predict(rho, prev, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        net.predict(rho, prev, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    net.close()
+    flops = mg.unet_conv_flops(1, n, n, n)
+    tf = flops / (ms * 1e-3) / 1e12
+    return {"workload": f"U-Net warm-start forward, {n}^3, channels 16/32/48/64",
+            "ms": round(ms, 3), "conv_tflop": round(flops / 1e12, 3),
+            "achieved_tflops": round(tf, 1), "peak_tflops": float(pk["bf16_tflops"]),
+            "frac": round(tf / float(pk["bf16_tflops"]), 4),
+            "note": "fraction of the measured BF16 dense (cuBLAS) burst peak"}
+
+
 def measure_amr(dev, n0=256, reps=3):
     """One composite AMR Poisson solve (outside the timed region): the base
     grid n0^3 with the dielectric slab and three nested refined levels around
@@ -560,6 +596,7 @@ def run_ours(args):
     solver.set_options(concurrency=conc)
     solver.profile(False)
     extras = measure_extras(solver, rho, eps, phi, n, dev)
+    extras["unet_forward"] = measure_unet(dev)
     if not args.no_amr:
         extras["amr_solve"] = measure_amr(dev)
 

@@ -524,6 +524,27 @@ class Solver:
         return st
 
 
+UNET_CHANNELS = (16, 32, 48, 64)
+
+
+def unet_conv_flops(n, d, h, w):
+    """FLOPs (2 per multiply-add) of the 3x3x3 convolutions of one U-Net
+    forward pass on a batch of n volumes d x h x w: per level l (grid >> l)
+    two encoder convolutions (input 16 channels at level 0, the level above's
+    width below), and on the way up an upsampling convolution from the level
+    below, a convolution of the concatenated skip and one more."""
+    C = UNET_CHANNELS
+    total = 0
+    for l in range(4):
+        vox = n * (d >> l) * (h >> l) * (w >> l)
+        cin = 16 if l == 0 else C[l - 1]
+        layers = [(cin, C[l]), (C[l], C[l])]
+        if l < 3:
+            layers += [(C[l + 1], C[l]), (2 * C[l], C[l]), (C[l], C[l])]
+        total += sum(2 * 27 * ci * co * vox for ci, co in layers)
+    return total
+
+
 class UNet:
     """The warm-start U-Net of libmg (mg_unet_*): fields are CUDA float64
     tensors of shape (n, d, h, w) or (d, h, w) with d, h, w multiples of 8."""
