@@ -131,6 +131,16 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Tiled tensor store (shared -> global) of a 5D box, as one bulk group.
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, uint32_t src, int c0, int c1,
+                                             int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group"
+      " [%0, {%2, %3, %4, %5, %6}], [%1];\n" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+
 // 3D convolution (3x3x3, pad 1) as an implicit GEMM on the fifth-generation
 // tensor cores: M = output voxels, N = Cout, K = 27 taps x Cin, in chunks
 // of 16 input channels.
@@ -158,12 +168,19 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
 // for its copies and MMAs still in flight and writes nothing.
 //
 // Epilogue: the four warps read their TMEM lane quarters with tcgen05.ld and
-// apply bias, ReLU and the BF16 store (two outputs split by channel).
+// apply bias and ReLU.  With tma_out (every output channel slice 16-byte
+// aligned), the BF16 tile is staged in the first stage's shared memory
+// ([z][y][x][channel], one region per output) and written by one tiled
+// tensor store per output, which also clips the tile at the volume's edge:
+// each output byte crosses to L2 once, where per-thread stores of a voxel's
+// channels sent every 32-byte sector as eight partial writes.  Otherwise
+// each thread stores its voxel's channels itself.
 template <int N, int MT>
 __global__ void __launch_bounds__(kConvThreads)
     k_conv3d(ConvArgs a, const __grid_constant__ CUtensorMap map_x1,
              const __grid_constant__ CUtensorMap map_x2, const __grid_constant__ CUtensorMap map_w,
-             int S) {
+             const __grid_constant__ CUtensorMap map_y1,
+             const __grid_constant__ CUtensorMap map_y2, int S, int tma_out) {
   using P = ConvPlan<N, MT>;
   constexpr int TD = MT;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -280,6 +297,9 @@ __global__ void __launch_bounds__(kConvThreads)
     // epilogue: TMEM lane 32 warp + lane = voxel (w = m % 8, h = m / 8)
     const int m = warp * 32 + lane;
     const int x = w0 + (m % TW), y = h0 + m / TW;
+    const int O2 = N - a.O1;
+    unsigned char* stg = smem_raw + (base - smem_u32(smem_raw));  // stage 0, free now
+    unsigned char* stg2 = stg + TD * kMmaM * a.O1 * 2;
 #pragma unroll 1
     for (int s = 0; s < TD; ++s) {
       const int z = d0 + s;
@@ -297,7 +317,7 @@ __global__ void __launch_bounds__(kConvThreads)
               "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (!in) continue;
+        uint32_t pk[8];
 #pragma unroll
         for (int j = 0; j < 16; j += 2) {
           const int co = cb + j;
@@ -311,13 +331,40 @@ __global__ void __launch_bounds__(kConvThreads)
             v1 = fmaxf(v1, 0.0f);
           }
           const __nv_bfloat162 pr = __floats2bfloat162_rn(v0, v1);
-          if (co < a.O1)
-            *reinterpret_cast<__nv_bfloat162*>(a.y1 + vox * a.Ys1 + a.Yo1 + co) = pr;
-          else
-            *reinterpret_cast<__nv_bfloat162*>(a.y2 + vox * a.Ys2 + a.Yo2 + (co - a.O1)) = pr;
+          pk[j / 2] = *reinterpret_cast<const uint32_t*>(&pr);
+        }
+        if (tma_out) {
+          // the 16 channels lie in one output (O1 is a multiple of 16)
+          uint4* d = cb < a.O1
+                         ? reinterpret_cast<uint4*>(stg + ((s * kMmaM + m) * a.O1 + cb) * 2)
+                         : reinterpret_cast<uint4*>(stg2 + ((s * kMmaM + m) * O2 + cb - a.O1) * 2);
+          d[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          d[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        } else if (in) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const int co = cb + j;
+            if (co < a.O1)
+              *reinterpret_cast<uint32_t*>(a.y1 + vox * a.Ys1 + a.Yo1 + co) = pk[j / 2];
+            else
+              *reinterpret_cast<uint32_t*>(a.y2 + vox * a.Ys2 + a.Yo2 + (co - a.O1)) = pk[j / 2];
+          }
         }
       }
     }
+    if (tma_out) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        tma_store_5d(&map_y1, base, a.Yo1, w0, h0, d0, n);
+        if (O2 > 0)
+          tma_store_5d(&map_y2, base + (uint32_t)(TD * kMmaM * a.O1 * 2), a.Yo2, w0, h0, d0, n);
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(&g_conv_timeout, 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -749,6 +796,22 @@ static bool halo_map(CUtensorMap* m, const __nv_bfloat16* x, int c, const ConvAr
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Output map of a channels-last tensor with ys channels per voxel, written
+// o channels at a time: box (o, TW, TH, mt, 1).
+static bool out_map(CUtensorMap* m, const __nv_bfloat16* y, int ys, int o, const ConvArgs& a,
+                    int mt) {
+  const cuuint64_t dim[5] = {(cuuint64_t)ys, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D,
+                             (cuuint64_t)a.N};
+  const cuuint64_t row = (cuuint64_t)ys * 2;
+  const cuuint64_t stride[4] = {row, row * a.W, row * a.W * a.H, row * a.W * a.H * a.D};
+  const cuuint32_t box[5] = {(cuuint32_t)o, TW, TH, (cuuint32_t)mt, 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return encode_tiled()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)y, dim, stride, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Weight map of w[co][tap][ci] seen as (8 channels, co, ci / 8, tap) with
 // strides (2 B, 27 Ct x 2 B, 16 B, Ct x 2 B): the box (8, cout, 2, 27) at
 // (0, 0, 2 chunk, 0) lands in shared memory as [tap][half][co] x 16 B.
@@ -778,6 +841,17 @@ cudaError_t launch_conv3d(const ConvArgs& a, int cout, cudaStream_t s) {
       (a.C2 > 0 ? !halo_map(&mx2, a.x2, a.C2, a, mt) : false) || !weight_map(&mw, a.w, ct, cout))
     return cudaErrorInvalidValue;
   if (a.C2 == 0) mx2 = mx1;
+  // output maps: channel slices [Yo, Yo + O) of tensors with Ys channels
+  const int O2 = cout - a.O1;
+  auto slice_ok = [](const void* p, int ys, int yo, int o) {
+    return p && (uintptr_t)p % 16 == 0 && ys % 8 == 0 && yo % 8 == 0 && o % 16 == 0 && o > 0 &&
+           yo + o <= ys;
+  };
+  int tma_out = slice_ok(a.y1, a.Ys1, a.Yo1, a.O1) && (O2 == 0 || slice_ok(a.y2, a.Ys2, a.Yo2, O2));
+  CUtensorMap my1 = mx1, my2 = mx1;
+  if (tma_out && (!out_map(&my1, a.y1, a.Ys1, a.O1, a, mt) ||
+                  (O2 > 0 && !out_map(&my2, a.y2, a.Ys2, O2, a, mt))))
+    tma_out = 0;
   // one stage once the CTAs fill the SMs twice, else two (when there are
   // two chunks)
   const int stages = tiles >= 2 * 152 || ct == 16 ? 1 : 2;
@@ -790,7 +864,8 @@ cudaError_t launch_conv3d(const ConvArgs& a, int cout, cudaStream_t s) {
                            P::smem(kMaxStages));
       attr_done[mt - 1][slot] = true;
     }
-    kernel<<<(unsigned)tiles, kConvThreads, P::smem(stages), s>>>(a, mx1, mx2, mw, stages);
+    kernel<<<(unsigned)tiles, kConvThreads, P::smem(stages), s>>>(a, mx1, mx2, mw, my1, my2, stages,
+                                                                  tma_out);
   };
 #define CONV_CASE(C, SLOT)                                                   \
   case C:                                                                    \
