@@ -9,11 +9,14 @@
 // conv3d forward is an implicit GEMM on the tcgen05 tensor cores (BF16 x
 // BF16 -> FP32 accumulators in tensor memory, operands staged in shared
 // memory by the tensor memory accelerator, one producer and one MMA-issuing
-// thread per CTA): M = output voxels, N = Cout, K = 27 Cin.  The input
-// gradient is the same kernel with flipped, transposed weights.
+// thread per CTA; a persistent form with a ring of stages and two
+// accumulators for large grids): M = output voxels, N = Cout, K = 27 Cin.
+// The input gradient is the same kernel with flipped, transposed weights;
+// the weight gradient is a second tcgen05 GEMM over voxels.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include "nn_internal.h"
@@ -129,6 +132,28 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       " [%0], [%1, {%3, %4, %5, %6}], [%2];\n" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
+}
+
+// The MT x 27 MMAs of one 16-channel chunk.  The A view of tap (kw, kh, kd)
+// for M-tile s starts kw + HW (kh + HH (kd + s)) 16-byte rows into the halo
+// and tap t's weights t 2 N rows into the chunk's weights, so every
+// descriptor is the chunk's first one plus a compile-time count of 16-byte
+// units in its address field (no carry: shared addresses stay below 256 KB);
+// the unrolled loop issues each MMA after one add per operand.
+template <int N, int MT, int kTileCols>
+__device__ __forceinline__ void conv_chunk_mmas(uint32_t acc, uint32_t halo, uint32_t wsm,
+                                                uint32_t half_bytes, uint32_t idesc,
+                                                bool accumulate) {
+  const uint64_t a0 = smem_desc(halo, half_bytes, HW * 16);
+  const uint64_t b0 = smem_desc(wsm, N * 16, 128);
+#pragma unroll
+  for (int s = 0; s < MT; ++s)
+#pragma unroll
+    for (int tap = 0; tap < 27; ++tap) {
+      const int kw = tap % 3, kh = (tap / 3) % 3, kd = tap / 9;
+      mma_f16(acc + (uint32_t)(s * kTileCols), a0 + (uint64_t)(kw + HW * (kh + HH * (kd + s))),
+              b0 + (uint64_t)(tap * 2 * N), idesc, (accumulate || tap > 0) ? 1u : 0u);
+    }
 }
 
 // Tiled tensor store (shared -> global) of a 5D box, as one bulk group.
@@ -256,17 +281,8 @@ __global__ void __launch_bounds__(kConvThreads)
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t halo = base + (uint32_t)(st * P::kStage);
-      const uint32_t wsm = halo + 2u * P::kHalfBytes;
-#pragma unroll 1
-      for (int s = 0; s < TD; ++s)
-#pragma unroll 1
-        for (int tap = 0; tap < 27; ++tap) {
-          const int kw = tap % 3, kh = (tap / 3) % 3, kd = tap / 9;
-          const uint32_t aoff = 16u * (uint32_t)(kw + HW * (kh + HH * (kd + s)));
-          const uint64_t ad = smem_desc(halo + aoff, P::kHalfBytes, HW * 16);
-          const uint64_t bd = smem_desc(wsm + (uint32_t)(tap * 2 * N * 16), N * 16, 128);
-          mma_f16(tmem + (uint32_t)(s * P::kTile), ad, bd, idesc, (ch > 0 || tap > 0) ? 1u : 0u);
-        }
+      conv_chunk_mmas<N, TD, P::kTile>(tmem, halo, halo + 2u * P::kHalfBytes, P::kHalfBytes, idesc,
+                                       ch > 0);
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               empty(st))
@@ -470,6 +486,257 @@ __global__ void k_up_bwd(const __nv_bfloat16* dy, int N, int D, int H, int W, in
   dx[q] = __float2bfloat16(s);
 }
 
+// Persistent form of k_conv3d for large grids (two M-tiles per tile, Cout
+// <= 64): about one CTA per SM walks its tiles (blockIdx.x, + gridDim.x,
+// ...) with three roles.  Warp 0 (one thread) fills a ring of S shared-
+// memory stages with each chunk's halo (and weights, unless they are
+// resident); warp 1 allocates TMEM and one thread issues the MMAs into two
+// accumulators used in turn, so the MMAs of one tile run while the four
+// epilogue warps (2..5, TMEM lane quarters warp % 4) drain the other: they
+// read it back, apply bias and ReLU, stage the BF16 tile in shared memory
+// and one of them writes it with tiled tensor stores.  With RW the weights
+// of all chunks are loaded once per CTA.  Barriers: full/empty per stage,
+// acc_full (MMA commit) and acc_empty (128 epilogue arrivals) per
+// accumulator, one for the resident weights; every wait is bounded.
+constexpr int kPThreads = 192;
+constexpr int kPMaxStages = 4;
+
+template <int N, bool RW>
+struct PPlan {
+  static constexpr int MT = 2;
+  static constexpr int kHalo = HW * HH * (MT + 2);
+  static constexpr int kHalfBytes = round1k(kHalo * 16);
+  static constexpr int kHaloTx = 2 * kHalo * 16;
+  static constexpr int kWBytes = 27 * 2 * N * 16;              // one chunk's weights
+  static constexpr int kStage = 2 * kHalfBytes + (RW ? 0 : round1k(kWBytes));
+  static constexpr int kStg = MT * kMmaM * N * 2;                // BF16 output tile
+  static constexpr int kTile = (N + 31) / 32 * 32;
+  static constexpr int kAcc = MT * kTile;                        // columns of one accumulator
+  static constexpr int kAlloc = 2 * kAcc <= 32 ? 32 : 2 * kAcc <= 64 ? 64
+                                : 2 * kAcc <= 128 ? 128 : 2 * kAcc <= 256 ? 256 : 512;
+  // bytes for S stages and nchunks resident chunks of weights
+  static constexpr int smem(int S, int nchunks) {
+    return S * kStage + (RW ? round1k(nchunks * kWBytes) : 0) + kStg + 1024;
+  }
+};
+
+template <int N, bool RW>
+__global__ void __launch_bounds__(kPThreads, 1)
+    k_conv3d_p(ConvArgs a, const __grid_constant__ CUtensorMap map_x1,
+               const __grid_constant__ CUtensorMap map_x2, const __grid_constant__ CUtensorMap map_w,
+               const __grid_constant__ CUtensorMap map_y1,
+               const __grid_constant__ CUtensorMap map_y2, int S) {
+  using P = PPlan<N, RW>;
+  constexpr int MT = P::MT;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // full[4], empty[4], acc_full[2], acc_empty[2], weights
+  __shared__ __align__(8) uint64_t bars[2 * kPMaxStages + 5];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tiles_w = (a.W + TW - 1) / TW, tiles_h = (a.H + TH - 1) / TH;
+  const int tiles_d = (a.D + MT - 1) / MT;
+  const long long tiles = (long long)a.N * tiles_d * tiles_h * tiles_w;
+  const int nch = (a.C1 + a.C2) / 16;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t wreg = base + (uint32_t)(S * P::kStage);                  // resident weights
+  const uint32_t stg = wreg + (uint32_t)(RW ? round1k(nch * P::kWBytes) : 0);  // output tile
+  const uint32_t bar0 = smem_u32(&bars[0]);
+  auto full = [&](int st) { return bar0 + 8u * (uint32_t)st; };
+  auto empty = [&](int st) { return bar0 + 8u * (uint32_t)(kPMaxStages + st); };
+  auto acc_full = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kPMaxStages + b); };
+  auto acc_empty = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kPMaxStages + 2 + b); };
+  const uint32_t wbar = bar0 + 8u * (uint32_t)(2 * kPMaxStages + 4);
+  auto tile_origin = [&](long long t, int& w0, int& h0, int& d0, int& n) {
+    w0 = (int)(t % tiles_w) * TW;
+    t /= tiles_w;
+    h0 = (int)(t % tiles_h) * TH;
+    t /= tiles_h;
+    d0 = (int)(t % tiles_d) * MT;
+    n = (int)(t / tiles_d);
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < 2 * kPMaxStages + 5; ++i) {
+      const bool epi = i == 2 * kPMaxStages + 2 || i == 2 * kPMaxStages + 3;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar0 + 8u * i),
+                   "r"(epi ? 128 : 1)
+                   : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    fail_s = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(P::kAlloc)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  auto failed = [&]() { return *(volatile int*)&fail_s != 0; };
+  auto give_up = [&]() { atomicExch(&fail_s, 1); };
+
+  if (tid == 0) {
+    // ---- producer
+    long long q = 0;
+    if (RW) {
+      mbar_expect_tx(wbar, (uint32_t)(nch * P::kWBytes));
+      for (int ch = 0; ch < nch; ++ch)
+        tma_load_4d(wreg + (uint32_t)(ch * P::kWBytes), &map_w, wbar, 0, 0, 2 * ch, 0);
+    }
+    for (long long t = blockIdx.x; t < tiles && !failed(); t += gridDim.x) {
+      int w0, h0, d0, n;
+      tile_origin(t, w0, h0, d0, n);
+      for (int ch = 0; ch < nch; ++ch, ++q) {
+        const int st = (int)(q % S);
+        if (q >= S && !mbar_wait(empty(st), (uint32_t)((q / S - 1) & 1))) {
+          give_up();
+          break;
+        }
+        const uint32_t halo = base + (uint32_t)(st * P::kStage);
+        const bool first = ch * 16 < a.C1;
+        const CUtensorMap* mx = first ? &map_x1 : &map_x2;
+        const int c0 = first ? ch * 16 : ch * 16 - a.C1;
+        mbar_expect_tx(full(st), (uint32_t)(P::kHaloTx + (RW ? 0 : P::kWBytes)));
+        tma_load_5d(halo, mx, full(st), c0, w0 - 1, h0 - 1, d0 - 1, n);
+        tma_load_5d(halo + P::kHalfBytes, mx, full(st), c0 + 8, w0 - 1, h0 - 1, d0 - 1, n);
+        if (!RW) tma_load_4d(halo + 2u * P::kHalfBytes, &map_w, full(st), 0, 0, 2 * ch, 0);
+      }
+    }
+    // copies still in flight (the last use of every stage), bounded
+    const long long q0 = q - S < 0 ? 0 : q - S;
+    for (long long p = q0; p < q; ++p) mbar_wait(full((int)(p % S)), (uint32_t)((p / S) & 1));
+    if (RW) mbar_wait(wbar, 0);
+  } else if (tid == 32) {
+    // ---- MMA issue
+    const uint32_t idesc = instr_desc(kMmaM, N);
+    long long q = 0, done_q = -1;
+    int lt = 0;
+    bool ok = !RW || mbar_wait(wbar, 0);
+    if (!ok) give_up();
+    for (long long t = blockIdx.x; ok && t < tiles && !failed(); t += gridDim.x, ++lt) {
+      const int b = lt & 1;
+      if (lt >= 2 && !mbar_wait(acc_empty(b), (uint32_t)(((lt >> 1) - 1) & 1))) {
+        give_up();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t acc = tmem + (uint32_t)(b * P::kAcc);
+      for (int ch = 0; ch < nch; ++ch, ++q) {
+        const int st = (int)(q % S);
+        if (!mbar_wait(full(st), (uint32_t)((q / S) & 1))) {
+          give_up();
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t halo = base + (uint32_t)(st * P::kStage);
+        const uint32_t wsm = RW ? wreg + (uint32_t)(ch * P::kWBytes) : halo + 2u * P::kHalfBytes;
+        conv_chunk_mmas<N, MT, P::kTile>(acc, halo, wsm, P::kHalfBytes, idesc, ch > 0);
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                empty(st))
+            : "memory");
+        done_q = q;
+      }
+      if (!ok) break;
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              acc_full(b))
+          : "memory");
+    }
+    // MMAs still in flight (the last commit covers the earlier ones), bounded
+    if (done_q >= 0) mbar_wait(empty((int)(done_q % S)), (uint32_t)((done_q / S) & 1));
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM lane quarter warp % 4, voxel m = lane of the tile
+    const int m = (warp & 3) * 32 + lane;
+    const bool leader = tid == 64;
+    const int O2 = N - a.O1;
+    unsigned char* stg_p = smem_raw + (stg - smem_u32(smem_raw));
+    int lt = 0;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
+      const int b = lt & 1;
+      const bool got = mbar_wait(acc_full(b), (uint32_t)((lt >> 1) & 1));
+      // the staging tile is free once the previous tile's stores have read it
+      if (leader) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+      // the four warps agree (barrier with an OR vote) on whether to go on
+      uint32_t bad = (!got || failed()) ? 1u : 0u;
+      asm volatile(
+          "{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\n"
+          "bar.red.or.pred po, 1, 128, pi;\nselp.u32 %0, 1, 0, po;\n}\n"
+          : "=r"(bad)
+          : "r"(bad)
+          : "memory");
+      if (bad) {
+        give_up();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll 1
+      for (int s = 0; s < MT; ++s)
+#pragma unroll 1
+        for (int cb = 0; cb < N; cb += 16) {
+          uint32_t r[16];
+          const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                 (uint32_t)(b * P::kAcc + s * P::kTile + cb);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+              "%12,%13,%14,%15}, [%16];\n"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          uint32_t pk[8];
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const int co = cb + j;
+            float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+            if (a.bias) {
+              v0 += a.bias[co];
+              v1 += a.bias[co + 1];
+            }
+            if (a.relu) {
+              v0 = fmaxf(v0, 0.0f);
+              v1 = fmaxf(v1, 0.0f);
+            }
+            const __nv_bfloat162 pr = __floats2bfloat162_rn(v0, v1);
+            pk[j / 2] = *reinterpret_cast<const uint32_t*>(&pr);
+          }
+          uint4* d = cb < a.O1 ? reinterpret_cast<uint4*>(stg_p + ((s * kMmaM + m) * a.O1 + cb) * 2)
+                               : reinterpret_cast<uint4*>(stg_p + MT * kMmaM * a.O1 * 2 +
+                                                          ((s * kMmaM + m) * O2 + cb - a.O1) * 2);
+          d[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          d[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+      // the accumulator is free for the tile after next
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acc_empty(b)) : "memory");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      asm volatile("bar.sync 1, 128;\n" ::: "memory");
+      if (leader) {
+        int w0, h0, d0, n;
+        tile_origin(t, w0, h0, d0, n);
+        tma_store_5d(&map_y1, stg, a.Yo1, w0, h0, d0, n);
+        if (O2 > 0) tma_store_5d(&map_y2, stg + (uint32_t)(MT * kMmaM * a.O1 * 2), a.Yo2, w0, h0, d0, n);
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+      }
+    }
+    if (leader) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+  }
+  __syncwarp();
+  __syncthreads();
+  if (tid == 0 && fail_s) atomicExch(&g_conv_timeout, 1u);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(P::kAlloc)
+                 : "memory");
+}
+
 // Weight gradient dW[co][t][ci] += sum_v dY[v][co] X[v + off(t)][ci] on the
 // tensor cores.  GEMM rows are (tap, 8-channel input group) pairs, 16 groups
 // (128 rows) per M-tile; N = Cout; K runs over voxels, 128 per stage (a box
@@ -603,12 +870,13 @@ __global__ void __launch_bounds__(kConvThreads)
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t stage = base + (uint32_t)(st * P::kStage);
-#pragma unroll 1
-      for (int kk = 0; kk < kWgKV / 16; ++kk) {
-        const uint64_t ad = smem_desc(stage + 256u * kk, 128, P::kGroupBytes);
-        const uint64_t bd = smem_desc(stage + P::kABytes + 256u * kk, 128, P::kGroupBytes);
-        mma_f16(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-      }
+      // 16 voxels (256 bytes = 16 descriptor units) per MMA
+      const uint64_t a0 = smem_desc(stage, 128, P::kGroupBytes);
+      const uint64_t b0 = smem_desc(stage + P::kABytes, 128, P::kGroupBytes);
+#pragma unroll
+      for (int kk = 0; kk < kWgKV / 16; ++kk)
+        mma_f16(tmem, a0 + (uint64_t)(16 * kk), b0 + (uint64_t)(16 * kk), idesc,
+                (i > 0 || kk > 0) ? 1u : 0u);
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               empty(st))
@@ -826,6 +1094,39 @@ static bool weight_map(CUtensorMap* m, const __nv_bfloat16* w, int ct, int cout)
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The persistent kernel on one CTA per SM (the occupancy query allows more
+// only where the shared memory does), with as many stages (2 .. 4) as fit.
+template <int N, bool RW>
+static cudaError_t launch_conv3d_p(const ConvArgs& a, const CUtensorMap& mx1,
+                                   const CUtensorMap& mx2, const CUtensorMap& mw,
+                                   const CUtensorMap& my1, const CUtensorMap& my2,
+                                   long long tiles, cudaStream_t s) {
+  using P = PPlan<N, RW>;
+  constexpr int kDyn = 227 * 1024 - 2048;  // opt-in limit less the kernel's static shared memory
+  const int nch = (a.C1 + a.C2) / 16;
+  // as many stages as fit one CTA per SM (two CTAs per SM with fewer stages
+  // each measured the same)
+  int S = kPMaxStages;
+  while (S > 2 && P::smem(S, nch) > kDyn) --S;
+  if (P::smem(S, nch) > kDyn) return cudaErrorNotSupported;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_conv3d_p<N, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+    attr_done = true;
+  }
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3d_p<N, RW>, kPThreads,
+                                                P::smem(S, nch));
+  occ = std::max(1, std::min(occ, 512 / P::kAlloc));  // TMEM columns of an SM
+  const long long grid = std::min<long long>(tiles, (long long)nsm * occ);
+  k_conv3d_p<N, RW><<<(unsigned)grid, kPThreads, P::smem(S, nch), s>>>(a, mx1, mx2, mw, my1, my2,
+                                                                       S);
+  add_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_conv3d(const ConvArgs& a, int cout, cudaStream_t s) {
   const int ct = a.C1 + a.C2;
   if (!conv_supported(ct, cout) || a.C1 % 16 || a.C2 % 16 || a.C1 <= 0 ||
@@ -852,6 +1153,23 @@ cudaError_t launch_conv3d(const ConvArgs& a, int cout, cudaStream_t s) {
   if (tma_out && (!out_map(&my1, a.y1, a.Ys1, a.O1, a, mt) ||
                   (O2 > 0 && !out_map(&my2, a.y2, a.Ys2, O2, a, mt))))
     tma_out = 0;
+  // large grids: the persistent kernel (its configuration fits for Cout <= 64)
+  if (mt == 2 && tma_out && cout <= 64) {
+    const int nch = ct / 16;
+    const bool rw = 27 * 2 * cout * 16 * nch <= 64 * 1024;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (cout * 2 + (rw ? 1 : 0)) {
+      case 32: e = launch_conv3d_p<16, false>(a, mx1, mx2, mw, my1, my2, tiles, s); break;
+      case 33: e = launch_conv3d_p<16, true>(a, mx1, mx2, mw, my1, my2, tiles, s); break;
+      case 64: e = launch_conv3d_p<32, false>(a, mx1, mx2, mw, my1, my2, tiles, s); break;
+      case 65: e = launch_conv3d_p<32, true>(a, mx1, mx2, mw, my1, my2, tiles, s); break;
+      case 96: e = launch_conv3d_p<48, false>(a, mx1, mx2, mw, my1, my2, tiles, s); break;
+      case 97: e = launch_conv3d_p<48, true>(a, mx1, mx2, mw, my1, my2, tiles, s); break;
+      case 128: e = launch_conv3d_p<64, false>(a, mx1, mx2, mw, my1, my2, tiles, s); break;
+      case 129: e = launch_conv3d_p<64, true>(a, mx1, mx2, mw, my1, my2, tiles, s); break;
+    }
+    if (e != cudaErrorNotSupported) return e;  // NotSupported: no stage count fits
+  }
   // one stage once the CTAs fill the SMs twice, else two (when there are
   // two chunks)
   const int stages = tiles >= 2 * 152 || ct == 16 ? 1 : 2;

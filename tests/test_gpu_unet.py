@@ -51,6 +51,34 @@ def test_conv3d_matches_oracle(mg, shape, c1, c2, cout, relu):
     assert np.all(np.abs(got - ref) <= 2.0**-8 * np.abs(ref) + 1e-4 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("c1,c2,cout,relu", [
+    (16, 0, 16, True),     # resident weights, four stages
+    (32, 32, 32, False),   # concatenated input, streamed weights
+    (48, 0, 48, True),     # three stages
+    (64, 0, 64, True),     # two stages
+    (16, 0, 64, False),
+])
+def test_conv3d_persistent_matches_oracle(mg, c1, c2, cout, relu):
+    """A volume large enough for the persistent kernel (540 tiles of 8 x 16 x
+    2 voxels on at most one CTA per SM, so each CTA runs several tiles
+    through both accumulators and around its stage ring), ragged in every
+    direction against the tile."""
+    rng = np.random.default_rng(100 + c1 + c2 + cout)
+    n, d, h, w = 1, 40, 44, 70
+    x1 = U.to_bf16(rng.standard_normal((n, d, h, w, c1)))
+    x2 = U.to_bf16(rng.standard_normal((n, d, h, w, c2))) if c2 else None
+    wt = U.to_bf16(rng.standard_normal((cout, 27, c1 + c2)) * 0.1)
+    b = rng.standard_normal(cout).astype(np.float32)
+    y = mg.conv3d(bf(x1), bf(wt), torch.from_numpy(b).cuda(), None if x2 is None else bf(x2), relu)
+    torch.cuda.synchronize()
+    got = y.float().cpu().numpy().astype(np.float64)
+    xin = x1 if x2 is None else np.concatenate([x1, x2], axis=-1)
+    ref = U.conv3d(xin, wt, b.astype(np.float64))
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    assert np.all(np.abs(got - ref) <= 2.0**-8 * np.abs(ref) + 1e-4 * np.abs(ref).max())
+
+
 @pytest.mark.parametrize("cout,c1,c2,shape", [
     (16, 16, 0, (2, 4, 6, 9)),      # ragged against the 8 x 4 x 4 voxel box
     (48, 48, 48, (2, 4, 6, 9)),     # concatenated input
@@ -88,9 +116,12 @@ def _cuda64(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def test_network_gradients_match_oracle(mg):
-    """Loss and every layer's weight gradient of the whole U-Net (n = 2,
-    16^3) against the oracle with BF16 storage emulated."""
+@pytest.mark.parametrize("n,s", [(2, 16), (1, 48)])
+def test_network_gradients_match_oracle(mg, n, s):
+    """Loss and every layer's weight gradient of the whole U-Net against the
+    oracle with BF16 storage emulated; at 48^3 the level-0 convolutions and
+    their input gradients (one of them split into two outputs) run on the
+    persistent kernel."""
     rng = np.random.default_rng(5)
     net = mg.UNet(seed=3)
     params = net.get_params()
@@ -98,7 +129,7 @@ def test_network_gradients_match_oracle(mg):
     params[-1] = 0.05
     net.set_params(params)
     net.set_scales(0.8, 1.2, 4.0)
-    rho, prev, phi = _batch(rng, 2, 16)
+    rho, prev, phi = _batch(rng, n, s)
     g, loss = net.grads(_cuda64(rho), _cuda64(prev), _cuda64(phi))
     p = U.unpack(params.astype(np.float64))
     ref_loss, G = U.loss_and_grads(p, rho, prev, phi, (0.8, 1.2, 4.0), bf16=True)
