@@ -27,6 +27,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# Hardware work queues of the device (read when the CUDA context is created,
+# so before any CUDA call).  The end-to-end leg drives the solver's four
+# problem streams and its own upload, download and solve streams; with the
+# default 8 queues some of them share one, and a problem's step then waits
+# behind the 4 GiB download of the previous set's answers (141 against 131 ms
+# per set measured).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 METRIC = "Poisson+3×Helmholtz solves/s to 1e-10 rel. residual at 512³; % HBM roofline"
 UNIT = "solve sets/s (1 set = 1 Poisson + 3 Helmholtz)"
 TOL = 1e-10

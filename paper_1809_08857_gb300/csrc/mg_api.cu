@@ -134,8 +134,12 @@ struct Work {
   float2* udf[2] = {nullptr, nullptr};
   float2* bdf = nullptr;
   double* partial = nullptr;
-  double* norm_dev = nullptr;   // [2]
-  double* norm_host = nullptr;  // [2], pinned
+  // [2], pinned; norm_map is its device-side address: the reduction kernel
+  // stores the norms there itself, so no copy engine is involved (a small
+  // device-to-host copy per step waits behind any bulk download in flight,
+  // e.g. the previous time step's answers)
+  double* norm_host = nullptr;
+  double* norm_map = nullptr;
   cudaEvent_t ev = nullptr, t0 = nullptr, t1 = nullptr;
   std::vector<StepGraph> graphs;
 };
@@ -360,9 +364,9 @@ mg_status get_work(mg_ctx* c, int q, Work** out) {
         if (l == nlev - 1) MG_TRY(c->alloc(&w->lw[l].r32[col], ns, true));
       }
     MG_TRY(c->alloc(&w->partial, 2 * (size_t)c->npartial));
-    MG_TRY(c->alloc(&w->norm_dev, 2));
     MG_CUDA(cudaMallocHost((void**)&w->norm_host, 2 * sizeof(double)));
     c->host_allocs.push_back(w->norm_host);
+    MG_CUDA(cudaHostGetDevicePointer((void**)&w->norm_map, w->norm_host, 0));
     // the zero fills above ran on the context's stream
     MG_CUDA(cudaStreamSynchronize(c->stream));
   }
@@ -533,14 +537,10 @@ mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha
   }
   {
     Scope sc(c, s, MG_KCLASS_COARSE, 0);
-    mg::launch_sum_partials(w->partial, nparts, w->norm_dev + slot, s);
-    if (io.znorm) mg::launch_sum_partials(a.partial_z, nparts, w->norm_dev, s);
+    mg::launch_sum_partials(w->partial, nparts, w->norm_map + slot, s);
+    if (io.znorm) mg::launch_sum_partials(a.partial_z, nparts, w->norm_map, s);
   }
-  MG_TRY(check_launch());
-  const int lo = io.znorm ? 0 : slot;
-  MG_CUDA(cudaMemcpyAsync(w->norm_host + lo, w->norm_dev + lo, sizeof(double) * (slot - lo + 1),
-                          cudaMemcpyDeviceToHost, s));
-  return MG_OK;
+  return check_launch();
 }
 
 // One problem of a (possibly concurrent) solve.
@@ -1150,8 +1150,8 @@ struct mg_amr {
   int* child_list = nullptr;
   double* partial = nullptr;  // [2][npartial]: r^2 and zero-guess r^2 per block
   long long npartial = 0;
-  double* norm_dev = nullptr;   // [2]
-  double* norm_host = nullptr;  // [2], pinned
+  double* norm_host = nullptr;  // [2], pinned, written by the reduction kernel
+  double* norm_map = nullptr;   // its device-side address
   cudaEvent_t ev = nullptr, upload = nullptr, t0 = nullptr, t1 = nullptr;
   std::vector<void*> allocs;
   std::vector<void*> host_allocs;
@@ -1386,12 +1386,12 @@ mg_status amr_alloc(mg_amr* a) {
                        cudaMemcpyHostToDevice));
   }
   MG_TRY(a->alloc(&a->partial, 2 * (size_t)a->npartial));
-  MG_TRY(a->alloc(&a->norm_dev, 2));
   MG_TRY(a->alloc(&a->dev, a->box.size()));
   MG_CUDA(cudaMallocHost((void**)&a->dev_host, sizeof(mg::AmrDev) * a->box.size()));
   a->host_allocs.push_back(a->dev_host);
   MG_CUDA(cudaMallocHost((void**)&a->norm_host, 2 * sizeof(double)));
   a->host_allocs.push_back(a->norm_host);
+  MG_CUDA(cudaHostGetDevicePointer((void**)&a->norm_map, a->norm_host, 0));
   MG_CUDA(cudaEventCreateWithFlags(&a->ev, cudaEventDisableTiming));
   MG_CUDA(cudaEventCreateWithFlags(&a->upload, cudaEventDisableTiming));
   MG_CUDA(cudaEventCreate(&a->t0));
@@ -1528,10 +1528,8 @@ mg_status amr_pass(mg_amr* a, Kind kind, double alpha, int lmin, bool norm, bool
       }
     }
   if (norm) {
-    mg::launch_sum_partials(a->partial, (int)a->npartial, a->norm_dev + 1, s);
-    if (znorm) mg::launch_sum_partials(a->partial + a->npartial, (int)a->npartial, a->norm_dev, s);
-    MG_CUDA(cudaMemcpyAsync(a->norm_host, a->norm_dev, 2 * sizeof(double),
-                            cudaMemcpyDeviceToHost, s));
+    mg::launch_sum_partials(a->partial, (int)a->npartial, a->norm_map + 1, s);
+    if (znorm) mg::launch_sum_partials(a->partial + a->npartial, (int)a->npartial, a->norm_map, s);
   }
   return check_launch();
 }

@@ -170,7 +170,8 @@ void launch_resid64(const Op64& op, double alpha, const double* f, const double*
 void launch_dense_apply64(const double* Minv, int n, const double* r, double* u, cudaStream_t s);
 
 
-// sum of partial[0..n) into *out (single block, fixed order).
+// sum of partial[0..n) into *out (single block, fixed order); out may be the
+// device-side address of mapped pinned host memory.
 void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s);
 
 // ---- FP32 split-storage inner V-cycle (mg_split32.cu) -----------------------
