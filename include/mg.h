@@ -460,6 +460,18 @@ mg_status mg_unet_load(mg_unet* net, const char* path);
 mg_status mg_nn_conv3d(const void* x1, int c1, const void* x2, int c2, const void* w,
                        const float* bias, int relu, int cout, int n, int d, int h, int w_,
                        void* y, void* cuda_stream);
+/* Self-check of the bounded waits of the tensor-core kernels: the same
+ * convolution, except that the first chunk's shared-memory barrier expects
+ * 16 bytes more than its copies deliver, so its wait cannot complete.  Every
+ * wait of the kernel gives up after 50 ms (normally 2 s), the kernel waits
+ * (bounded) for its copies and MMAs in flight, frees its tensor memory and
+ * returns without writing y; the call synchronises the stream and returns
+ * MG_ERR_CUDA ("a tensor-core completion wait gave up"), as a real stall
+ * would be reported, and the context stays usable.  Returns MG_OK only if the
+ * wait did not give up (a broken check). */
+mg_status mg_nn_conv3d_stalled(const void* x1, int c1, const void* x2, int c2, const void* w,
+                               const float* bias, int relu, int cout, int n, int d, int h,
+                               int w_, void* y, void* cuda_stream);
 /* Its weight gradient dW[co][t][ci] = sum_v dy[v][co] x[v + off(t)][ci] (FP32, overwritten)
  * and, when db is not NULL, the bias gradient db[co] = sum_v dy[v][co] (FP32, overwritten),
  * on the tensor cores (BF16 products, FP32 sums; the order of the sums varies

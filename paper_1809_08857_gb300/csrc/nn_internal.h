@@ -29,12 +29,19 @@ struct ConvArgs {
   int Ys1, Yo1;
   __nv_bfloat16* y2;
   int Ys2, Yo2;
+  // self-check of the bounded waits (0 in normal use): bytes added to the
+  // first chunk's expected copy size, which the copies never deliver, and
+  // the wait limit in ns (0: the default)
+  unsigned stall_bytes;
+  unsigned long long wait_ns;
 };
 
 bool conv_supported(int cin_total, int cout);
 cudaError_t launch_conv3d(const ConvArgs& a, int cout, cudaStream_t s);
 // True once any conv CTA gave up waiting for its tensor-core MMAs (a bounded
 // wait; its outputs were not written).  Synchronises.
+// Whether a tensor-core kernel gave up waiting since the last call (the flag
+// is cleared by reading it).
 bool conv_timed_out();
 void launch_flip_weights(const __nv_bfloat16* w, int co, int ci, __nv_bfloat16* wt,
                          cudaStream_t s);

@@ -33,7 +33,8 @@ constexpr int TW = 8, TH = 16;
 constexpr int HW = TW + 2, HH = TH + 2;  // halo tile rows
 constexpr int kConvThreads = 128;                     // 4 warps: TMEM lane quarters
 constexpr int kMmaM = 128;                            // rows (voxels) of one MMA
-constexpr long long kWaitIters = 1ll << 24;           // bound of an mbarrier wait
+constexpr long long kWaitIters = 1ll << 24;           // bound of an mbarrier wait (tries)
+constexpr unsigned long long kWaitNs = 2000000000ull; // and its time limit (2 s)
 constexpr int kMaxStages = 2;                         // shared-memory stages of the K loop
 
 __host__ __device__ constexpr int round1k(int b) { return (b + 1023) / 1024 * 1024; }
@@ -92,9 +93,17 @@ __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Wait for the mbarrier phase with the given parity; false after kWaitIters
-// unsuccessful tries.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// unsuccessful tries or limit_ns nanoseconds, whichever comes first.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitNs) {
+  unsigned long long t0 = 0;
   for (long long it = 0; it < kWaitIters; ++it) {
     uint32_t done;
     asm volatile(
@@ -104,6 +113,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 63) == 0) {
+      const unsigned long long t = now_ns();
+      if (it == 0) t0 = t;
+      else if (t - t0 > limit_ns) return false;
+    }
   }
   return false;
 }
@@ -225,6 +239,7 @@ __global__ void __launch_bounds__(kConvThreads)
   const int w0 = tw * TW, h0 = th * TH, d0 = td * TD;
   const int nchunks = (a.C1 + a.C2) / 16;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const unsigned long long lim = a.wait_ns ? a.wait_ns : kWaitNs;
   const uint32_t bar0 = smem_u32(&bars[0]);
   auto full = [&](int st) { return bar0 + 8u * (uint32_t)st; };
   auto empty = [&](int st) { return bar0 + 8u * (uint32_t)(kMaxStages + st); };
@@ -254,7 +269,7 @@ __global__ void __launch_bounds__(kConvThreads)
     // (that stage's previous use, phase ch / S - 1 of its empty barrier) are done
     for (int ch = 0; ch < nchunks; ++ch) {
       const int st = ch % S;
-      if (ch >= S && !mbar_wait(empty(st), (uint32_t)((ch / S - 1) & 1))) {
+      if (ch >= S && !mbar_wait(empty(st), (uint32_t)((ch / S - 1) & 1), lim)) {
         atomicExch(&fail_s, 1);
         break;
       }
@@ -264,7 +279,7 @@ __global__ void __launch_bounds__(kConvThreads)
       const bool first = ch * 16 < a.C1;
       const CUtensorMap* mx = first ? &map_x1 : &map_x2;
       const int c0 = first ? ch * 16 : ch * 16 - a.C1;
-      mbar_expect_tx(full(st), (uint32_t)(P::kHaloTx + P::kWBytes));
+      mbar_expect_tx(full(st), (uint32_t)(P::kHaloTx + P::kWBytes) + (ch == 0 ? a.stall_bytes : 0u));
       tma_load_5d(halo, mx, full(st), c0, w0 - 1, h0 - 1, d0 - 1, n);
       tma_load_5d(halo + P::kHalfBytes, mx, full(st), c0 + 8, w0 - 1, h0 - 1, d0 - 1, n);
       tma_load_4d(wsm, &map_w, full(st), 0, 0, 2 * ch, 0);
@@ -275,7 +290,7 @@ __global__ void __launch_bounds__(kConvThreads)
     const uint32_t idesc = instr_desc(kMmaM, N);
     for (int ch = 0; ch < nchunks; ++ch) {
       const int st = ch % S;
-      if (!mbar_wait(full(st), (uint32_t)((ch / S) & 1))) {
+      if (!mbar_wait(full(st), (uint32_t)((ch / S) & 1), lim)) {
         atomicExch(&fail_s, 1);
         break;
       }
@@ -297,15 +312,15 @@ __global__ void __launch_bounds__(kConvThreads)
   }
   __syncwarp();
   // every thread: wait for the last MMAs (bounded; skipped once a role gave up)
-  bool ok = !*(volatile int*)&fail_s && mbar_wait(done_bar, 0);
+  bool ok = !*(volatile int*)&fail_s && mbar_wait(done_bar, 0, lim);
   ok = __syncthreads_and(ok) && !fail_s;
   if (!ok && tid == 0) {
     atomicExch(&g_conv_timeout, 1u);
     // bounded waits for the copies and MMAs still in flight
     for (int ch = issued_s - S < 0 ? 0 : issued_s - S; ch < issued_s; ++ch)
-      mbar_wait(full(ch % S), (uint32_t)((ch / S) & 1));
+      mbar_wait(full(ch % S), (uint32_t)((ch / S) & 1), lim);
     if (committed_s > 0)
-      mbar_wait(empty((committed_s - 1) % S), (uint32_t)(((committed_s - 1) / S) & 1));
+      mbar_wait(empty((committed_s - 1) % S), (uint32_t)(((committed_s - 1) / S) & 1), lim);
   }
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
@@ -1153,8 +1168,9 @@ cudaError_t launch_conv3d(const ConvArgs& a, int cout, cudaStream_t s) {
   if (tma_out && (!out_map(&my1, a.y1, a.Ys1, a.O1, a, mt) ||
                   (O2 > 0 && !out_map(&my2, a.y2, a.Ys2, O2, a, mt))))
     tma_out = 0;
-  // large grids: the persistent kernel (its configuration fits for Cout <= 64)
-  if (mt == 2 && tma_out && cout <= 64) {
+  // large grids: the persistent kernel (its configuration fits for Cout <= 64;
+  // the wait self-check runs on the tile kernel)
+  if (mt == 2 && tma_out && cout <= 64 && a.stall_bytes == 0) {
     const int nch = ct / 16;
     const bool rw = 27 * 2 * cout * 16 * nch <= 64 * 1024;
     cudaError_t e = cudaErrorInvalidValue;
@@ -1208,6 +1224,10 @@ cudaError_t launch_conv3d(const ConvArgs& a, int cout, cudaStream_t s) {
 bool conv_timed_out() {
   unsigned v = 0;
   cudaMemcpyFromSymbol(&v, g_conv_timeout, sizeof(v));
+  if (v) {
+    const unsigned zero = 0;
+    cudaMemcpyToSymbol(g_conv_timeout, &zero, sizeof(zero));
+  }
   return v != 0;
 }
 

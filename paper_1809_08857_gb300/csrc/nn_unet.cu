@@ -580,9 +580,13 @@ mg_status mg_unet_load(mg_unet* u, const char* path) {
   return MG_OK;
 }
 
-mg_status mg_nn_conv3d(const void* x1, int c1, const void* x2, int c2, const void* w,
-                       const float* bias, int relu, int cout, int n, int d, int h, int w_,
-                       void* y, void* cuda_stream) {
+}  // extern "C"
+
+// Argument checks and launch of one network convolution; stalled: the wait
+// self-check (see mg_nn_conv3d_stalled).
+static mg_status conv3d_entry(const void* x1, int c1, const void* x2, int c2, const void* w,
+                              const float* bias, int relu, int cout, int n, int d, int h, int w_,
+                              void* y, void* cuda_stream, bool stalled) {
   if (!x1 || !w || !y || (c2 > 0 && !x2)) return nn_fail(MG_ERR_INVALID_ARG, "NULL argument");
   if (!conv_supported(c1 + c2, cout) || c1 < 16 || c1 % 16 || c2 % 16 || n < 1 || d < 1 ||
       h < 1 || w_ < 1)
@@ -605,8 +609,32 @@ mg_status mg_nn_conv3d(const void* x1, int c1, const void* x2, int c2, const voi
   a.y1 = (bf16*)y;
   a.O1 = cout;
   a.Ys1 = cout;
-  NN_CUDA(launch_conv3d(a, cout, (cudaStream_t)cuda_stream));
+  if (stalled) {
+    a.stall_bytes = 16;         // never delivered: the first chunk's wait must run out
+    a.wait_ns = 50000000ull;    // after 50 ms
+  }
+  const cudaStream_t s = (cudaStream_t)cuda_stream;
+  NN_CUDA(launch_conv3d(a, cout, s));
+  if (stalled) {
+    NN_CUDA(cudaStreamSynchronize(s));
+    if (conv_timed_out())
+      return nn_fail(MG_ERR_CUDA, "conv3d: a tensor-core completion wait gave up");
+  }
   return MG_OK;
+}
+
+extern "C" {
+
+mg_status mg_nn_conv3d(const void* x1, int c1, const void* x2, int c2, const void* w,
+                       const float* bias, int relu, int cout, int n, int d, int h, int w_,
+                       void* y, void* cuda_stream) {
+  return conv3d_entry(x1, c1, x2, c2, w, bias, relu, cout, n, d, h, w_, y, cuda_stream, false);
+}
+
+mg_status mg_nn_conv3d_stalled(const void* x1, int c1, const void* x2, int c2, const void* w,
+                               const float* bias, int relu, int cout, int n, int d, int h,
+                               int w_, void* y, void* cuda_stream) {
+  return conv3d_entry(x1, c1, x2, c2, w, bias, relu, cout, n, d, h, w_, y, cuda_stream, true);
 }
 
 mg_status mg_nn_conv3d_wgrad(const void* dy, int cout, const void* x1, int c1, const void* x2,

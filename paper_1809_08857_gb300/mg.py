@@ -37,7 +37,7 @@ EXPORTS = [
     "mg_unet_create", "mg_unet_destroy", "mg_unet_set_scales", "mg_unet_get_scales",
     "mg_unet_train_step", "mg_unet_predict", "mg_unet_grads", "mg_unet_num_params",
     "mg_unet_get_params", "mg_unet_set_params", "mg_unet_save", "mg_unet_load", "mg_nn_conv3d",
-    "mg_nn_conv3d_wgrad", "mg_warmstart_attach", "mg_warmstart_load", "mg_warmstart_predict",
+    "mg_nn_conv3d_stalled", "mg_nn_conv3d_wgrad", "mg_warmstart_attach", "mg_warmstart_load", "mg_warmstart_predict",
     "mg_poisson_residual", "mg_solve_screened", "mg_efield",
     "mg_amr_create", "mg_amr_solve", "mg_amr_residual", "mg_amr_destroy",
 ]
@@ -177,6 +177,7 @@ def load():
     lib.mg_unet_save.argtypes = [P, ctypes.c_char_p]
     lib.mg_unet_load.argtypes = [P, ctypes.c_char_p]
     lib.mg_nn_conv3d.argtypes = [P, I, P, I, P, P, I, I, I, I, I, I, P, P]
+    lib.mg_nn_conv3d_stalled.argtypes = lib.mg_nn_conv3d.argtypes
     lib.mg_nn_conv3d_wgrad.argtypes = [P, I, P, I, P, I, I, I, I, I, P, P, P]
     lib.mg_warmstart_attach.argtypes = [P, P]
     lib.mg_warmstart_load.argtypes = [P, ctypes.c_char_p]
@@ -196,7 +197,8 @@ def load():
     for name in ("mg_unet_create", "mg_unet_set_scales", "mg_unet_get_scales",
                  "mg_unet_train_step", "mg_unet_predict", "mg_unet_grads", "mg_unet_num_params",
                  "mg_unet_get_params", "mg_unet_set_params", "mg_unet_save", "mg_unet_load",
-                 "mg_nn_conv3d", "mg_nn_conv3d_wgrad", "mg_warmstart_attach",
+                 "mg_nn_conv3d", "mg_nn_conv3d_stalled", "mg_nn_conv3d_wgrad",
+                 "mg_warmstart_attach",
                  "mg_warmstart_load", "mg_warmstart_predict"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -639,17 +641,20 @@ class UNet:
         _check(self._lib.mg_unet_load(self._p, str(path).encode()))
 
 
-def conv3d(x1, w, bias=None, x2=None, relu=False, stream=None):
+def conv3d(x1, w, bias=None, x2=None, relu=False, stream=None, stalled=False):
     """One network convolution (mg_nn_conv3d): x1/x2 channels-last bfloat16
-    CUDA tensors (n, d, h, w, c), w bfloat16 (cout, 27, c1 + c2), bias float32."""
+    CUDA tensors (n, d, h, w, c), w bfloat16 (cout, 27, c1 + c2), bias float32.
+    stalled=True runs the bounded-wait self-check (mg_nn_conv3d_stalled),
+    which raises MGError with MG_ERR_CUDA when the check works."""
     n, d, h, ww, c1 = x1.shape
     c2 = 0 if x2 is None else x2.shape[-1]
     cout = w.shape[0]
     y = torch.empty((n, d, h, ww, cout), dtype=torch.bfloat16, device=x1.device)
-    _check(load().mg_nn_conv3d(_ptr(x1, torch.bfloat16), c1, None if x2 is None else _ptr(x2, torch.bfloat16),
-                               c2, _ptr(w, torch.bfloat16), None if bias is None else _ptr(bias, torch.float32),
-                               1 if relu else 0, cout, n, d, h, ww, _ptr(y, torch.bfloat16),
-                               _stream_handle(stream)))
+    fn = load().mg_nn_conv3d_stalled if stalled else load().mg_nn_conv3d
+    _check(fn(_ptr(x1, torch.bfloat16), c1, None if x2 is None else _ptr(x2, torch.bfloat16),
+              c2, _ptr(w, torch.bfloat16), None if bias is None else _ptr(bias, torch.float32),
+              1 if relu else 0, cout, n, d, h, ww, _ptr(y, torch.bfloat16),
+              _stream_handle(stream)))
     return y
 
 

@@ -126,3 +126,7 @@ def test_conv3d_rejects_bad_arguments_without_gpu(lib):
     assert conv(*args(good, 0, good, 16, good, 16)) == mg.MG_ERR_UNSUPPORTED
     assert conv(*args(good, 16, None, 0, good, 80)) == mg.MG_ERR_UNSUPPORTED
     assert conv(*args(None, 16, None, 0, good, 16)) == mg.MG_ERR_INVALID_ARG
+    # the wait self-check runs the same checks first
+    stalled = lib.mg_nn_conv3d_stalled
+    assert stalled(*args(odd, 16, None, 0, good, 16)) == mg.MG_ERR_INVALID_ARG
+    assert stalled(*args(good, 24, None, 0, good, 16)) == mg.MG_ERR_UNSUPPORTED

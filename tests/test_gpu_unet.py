@@ -51,6 +51,25 @@ def test_conv3d_matches_oracle(mg, shape, c1, c2, cout, relu):
     assert np.all(np.abs(got - ref) <= 2.0**-8 * np.abs(ref) + 1e-4 * np.abs(ref).max())
 
 
+def test_conv3d_bounded_wait_gives_up_and_context_stays_usable(mg):
+    """The tensor-core kernels' waits are bounded: the self-check asks the
+    first chunk's barrier for 16 bytes its copies never deliver, the wait
+    gives up after 50 ms, the kernel drains and frees its tensor memory, the
+    call reports MG_ERR_CUDA, and the next convolution is correct."""
+    rng = np.random.default_rng(77)
+    x = U.to_bf16(rng.standard_normal((1, 2, 16, 8, 16)))
+    wt = U.to_bf16(rng.standard_normal((16, 27, 16)) * 0.1)
+    b = rng.standard_normal(16).astype(np.float32)
+    with pytest.raises(mg.MGError) as err:
+        mg.conv3d(bf(x), bf(wt), torch.from_numpy(b).cuda(), relu=True, stalled=True)
+    assert err.value.status == mg.MG_ERR_CUDA and "gave up" in str(err.value)
+    y = mg.conv3d(bf(x), bf(wt), torch.from_numpy(b).cuda(), relu=True)
+    torch.cuda.synchronize()
+    got = y.float().cpu().numpy().astype(np.float64)
+    ref = np.maximum(U.conv3d(x, wt, b.astype(np.float64)), 0.0)
+    assert np.all(np.abs(got - ref) <= 2.0**-8 * np.abs(ref) + 1e-4 * np.abs(ref).max())
+
+
 @pytest.mark.parametrize("c1,c2,cout,relu", [
     (16, 0, 16, True),     # resident weights, four stages
     (32, 32, 32, False),   # concatenated input, streamed weights
