@@ -575,6 +575,20 @@ def run_ours(args):
             d2h(i)
         s_d2h.synchronize()
 
+    # this box's copy rates (1 GiB each way, on the leg's own streams): the
+    # leg is copy-bound where they are low
+    def copy_gbs(dst, src, stream):
+        with torch.cuda.stream(stream):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dst.copy_(src, non_blocking=True)
+            b.record(stream)
+        b.synchronize()
+        return round(src.numel() * src.element_size() / (a.elapsed_time(b) * 1e-3) / 1e9, 1)
+
+    copy_gbs(bufs[0]["rho"], rho_h, s_h2d)
+    rates = {"h2d_gbs": copy_gbs(bufs[0]["rho"], rho_h, s_h2d),
+             "d2h_gbs": copy_gbs(out_h[0], bufs[0]["rho"], s_d2h)}
     e2e_run(2)
     torch.cuda.synchronize()
     barrier()
@@ -588,7 +602,7 @@ def run_ours(args):
     cells = n ** 3
     e2e = {"value": whole_job_rate(world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": 2 * 8 * cells,
-           "d2h_bytes_per_step": 4 * 8 * cells}
+           "d2h_bytes_per_step": 4 * 8 * cells, "box_copy_rates": rates}
 
     # kernel profile (outside the timed region): one set at the timed
     # concurrency, then one set with the problems run one after another
