@@ -1126,14 +1126,19 @@ static cudaError_t launch_conv3d_p(const ConvArgs& a, const CUtensorMap& mx1,
   if (P::smem(S, nch) > kDyn) return cudaErrorNotSupported;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(k_conv3d_p<N, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_conv3d_p<N, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+    if (e != cudaSuccess) return e;
     attr_done = true;
   }
   int dev = 0, nsm = 0, occ = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3d_p<N, RW>, kPThreads,
-                                                P::smem(S, nch));
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3d_p<N, RW>, kPThreads,
+                                                      P::smem(S, nch));
+  if (e != cudaSuccess) return e;
+  if (nsm < 1) return cudaErrorInvalidDevice;
   occ = std::max(1, std::min(occ, 512 / P::kAlloc));  // TMEM columns of an SM
   const long long grid = std::min<long long>(tiles, (long long)nsm * occ);
   k_conv3d_p<N, RW><<<(unsigned)grid, kPThreads, P::smem(S, nch), s>>>(a, mx1, mx2, mw, my1, my2,
@@ -1194,8 +1199,9 @@ cudaError_t launch_conv3d(const ConvArgs& a, int cout, cudaStream_t s) {
     using P = decltype(plan);
     static_assert(P::smem(kMaxStages) <= 227 * 1024 - 1024, "two stages fit");
     if (!attr_done[mt - 1][slot]) {
-      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           P::smem(kMaxStages));
+      if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               P::smem(kMaxStages)) != cudaSuccess)
+        return;  // the launch below is skipped; cudaGetLastError reports the failure
       attr_done[mt - 1][slot] = true;
     }
     kernel<<<(unsigned)tiles, kConvThreads, P::smem(stages), s>>>(a, mx1, mx2, mw, my1, my2, stages,
@@ -1308,8 +1314,9 @@ cudaError_t launch_wgrad(const __nv_bfloat16* dy, int co, const __nv_bfloat16* x
     using P = decltype(plan);
     static_assert(P::smem(kMaxStages) <= 227 * 1024 - 1024, "two stages fit");
     if (!attr_done[slot]) {
-      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           P::smem(kMaxStages));
+      if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               P::smem(kMaxStages)) != cudaSuccess)
+        return;  // the launch below is skipped; cudaGetLastError reports the failure
       attr_done[slot] = true;
     }
     kernel<<<dim3((unsigned)a.splits, (unsigned)mtiles), kConvThreads, P::smem(stages), s>>>(
