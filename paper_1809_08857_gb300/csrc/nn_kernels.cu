@@ -753,31 +753,39 @@ __global__ void __launch_bounds__(kPThreads, 1)
 }
 
 // Weight gradient dW[co][t][ci] += sum_v dY[v][co] X[v + off(t)][ci] on the
-// tensor cores.  GEMM rows are (tap, 8-channel input group) pairs, 16 groups
-// (128 rows) per M-tile; N = Cout; K runs over voxels, 128 per stage (a box
-// of 8 x 4 x 4 voxels).  Both operands are MN-major in shared memory: the
-// tiled tensor copy of a box of one 8-channel group is [voxel][8 channels],
-// i.e. core matrices of 8 voxels (K) x 16 bytes (8 rows), so the copy lands
-// directly in the operand layout (lbo = 128 B between 8-voxel blocks, sbo =
-// one group's box between row groups).  The input box of group (t, c) is
-// the output box shifted by tap t's offset; zero fill at the volume's edge is
-// the convolution's padding, and voxels of a box beyond the volume carry a
-// zero dY.  A CTA accumulates its range of boxes in TMEM and adds the result
-// to dW with FP32 atomics.  With db given, the last M-tile's first unused
-// group holds BF16 ones, so its rows accumulate db[co] += sum_v dY[v][co].
-// Producer / MMA / epilogue roles and bounded waits as in k_conv3d.
+// tensor cores.  GEMM rows are (tap, 16-channel input group) pairs, 8 such
+// atoms (128 rows) per M-tile; N = Cout; K runs over voxels, 128 per stage
+// (a box of 8 x 4 x 4 voxels).  Both operands are MN-major in shared memory
+// with the 32-byte swizzle: the tiled tensor copy of one 16-channel box,
+// written with that swizzle, is [voxel][16 channels] = one atom of the
+// canonical layout (8-voxel K groups of 256 bytes one after another, so sbo =
+// 256 B; atoms one box apart, lbo = 4 KB), and every copied piece is a whole
+// 32-byte sector.  The input box of atom (t, c) is the output box shifted by
+// tap t's offset; zero fill at the volume's edge is the convolution's
+// padding, and voxels of a box beyond the volume carry a zero dY.  A CTA
+// accumulates its range of boxes in TMEM and adds the result to dW with FP32
+// atomics.  With db given, the last M-tile's first unused atom holds BF16
+// ones, so its rows accumulate db[co] += sum_v dY[v][co].  Producer / MMA /
+// epilogue roles and bounded waits as in k_conv3d.
 constexpr int kWgBX = 8, kWgBY = 4, kWgBZ = 4;         // voxel box of one stage
 constexpr int kWgKV = kWgBX * kWgBY * kWgBZ;           // K per stage (128)
-constexpr int kWgGroups = 16;                          // 8-row groups per M-tile
+constexpr int kWgAtoms = 8;                            // 16-row atoms per M-tile
 
 template <int N>
 struct WgPlan {
-  static constexpr int kGroupBytes = kWgKV * 16;        // one group's box (2 KB)
-  static constexpr int kABytes = kWgGroups * kGroupBytes;
-  static constexpr int kStage = kABytes + N / 8 * kGroupBytes;
+  static constexpr int kAtomBytes = kWgKV * 32;         // one 16-channel box (4 KB)
+  static constexpr int kABytes = kWgAtoms * kAtomBytes;
+  static constexpr int kStage = kABytes + N / 16 * kAtomBytes;
   static constexpr int smem(int stages) { return stages * kStage + 1024; }
   static constexpr int kAlloc = N <= 32 ? 32 : N <= 64 ? 64 : 128;
 };
+
+// Shared-memory descriptor of an MN-major operand with the 32-byte swizzle
+// (layout type 6 in bits 61-63): lbo = distance between 16-element atoms,
+// sbo = between 8-row groups along K.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return smem_desc(addr, lbo, sbo) | (6ull << 61);
+}
 
 struct WgArgs {
   int C1, C2, N, D, H, W;
@@ -797,11 +805,11 @@ __global__ void __launch_bounds__(kConvThreads)
   __shared__ uint32_t tmem_slot;
   __shared__ int issued_s, committed_s, fail_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ci_total = a.C1 + a.C2, c8 = ci_total / 8;
-  const int groups = 27 * c8;
-  const int g0 = blockIdx.y * kWgGroups;
-  const int ng = min(kWgGroups, groups - g0);
-  const int bias_g = (a.db && ng < kWgGroups) ? ng : -1;  // the group of ones
+  const int ci_total = a.C1 + a.C2, c16 = ci_total / 16;
+  const int atoms = 27 * c16;
+  const int g0 = blockIdx.y * kWgAtoms;
+  const int ng = max(0, min(kWgAtoms, atoms - g0));
+  const int bias_g = (a.db && ng < kWgAtoms) ? ng : -1;  // the atom of ones
   const int nbx = (a.W + kWgBX - 1) / kWgBX, nby = (a.H + kWgBY - 1) / kWgBY,
             nbz = (a.D + kWgBZ - 1) / kWgBZ;
   const long long nboxes = (long long)a.N * nbz * nby * nbx;
@@ -819,9 +827,9 @@ __global__ void __launch_bounds__(kConvThreads)
     // the ones group of every stage (never written by the copies)
     unsigned char* sm = smem_raw + (base - smem_u32(smem_raw));
     const uint4 ones = make_uint4(0x3f803f80u, 0x3f803f80u, 0x3f803f80u, 0x3f803f80u);
-    for (int q = tid; q < S * (P::kGroupBytes / 16); q += kConvThreads) {
-      const int st = q / (P::kGroupBytes / 16), e = q % (P::kGroupBytes / 16);
-      *reinterpret_cast<uint4*>(sm + st * P::kStage + bias_g * P::kGroupBytes + e * 16) = ones;
+    for (int q = tid; q < S * (P::kAtomBytes / 16); q += kConvThreads) {
+      const int st = q / (P::kAtomBytes / 16), e = q % (P::kAtomBytes / 16);
+      *reinterpret_cast<uint4*>(sm + st * P::kStage + bias_g * P::kAtomBytes + e * 16) = ones;
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
@@ -861,17 +869,17 @@ __global__ void __launch_bounds__(kConvThreads)
       const int z0 = (int)(b % nbz) * kWgBZ;
       const int n = (int)(b / nbz);
       const uint32_t stage = base + (uint32_t)(st * P::kStage);
-      mbar_expect_tx(full(st), (uint32_t)((ng + N / 8) * P::kGroupBytes));
+      mbar_expect_tx(full(st), (uint32_t)((ng + N / 16) * P::kAtomBytes));
       for (int g = 0; g < ng; ++g) {
-        const int G = g0 + g, t = G / c8, ch = (G % c8) * 8;
+        const int G = g0 + g, t = G / c16, ch = (G % c16) * 16;
         const int kw = t % 3, kh = (t / 3) % 3, kd = t / 9;
         const bool first = ch < a.C1;
-        tma_load_5d(stage + (uint32_t)(g * P::kGroupBytes), first ? &map_x1 : &map_x2, full(st),
+        tma_load_5d(stage + (uint32_t)(g * P::kAtomBytes), first ? &map_x1 : &map_x2, full(st),
                     first ? ch : ch - a.C1, x0 + kw - 1, y0 + kh - 1, z0 + kd - 1, n);
       }
-      for (int j = 0; j < N / 8; ++j)
-        tma_load_5d(stage + (uint32_t)(P::kABytes + j * P::kGroupBytes), &map_dy, full(st), 8 * j,
-                    x0, y0, z0, n);
+      for (int j = 0; j < N / 16; ++j)
+        tma_load_5d(stage + (uint32_t)(P::kABytes + j * P::kAtomBytes), &map_dy, full(st),
+                    16 * j, x0, y0, z0, n);
       issued_s = i + 1;
     }
   } else if (tid == 32) {
@@ -885,12 +893,12 @@ __global__ void __launch_bounds__(kConvThreads)
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t stage = base + (uint32_t)(st * P::kStage);
-      // 16 voxels (256 bytes = 16 descriptor units) per MMA
-      const uint64_t a0 = smem_desc(stage, 128, P::kGroupBytes);
-      const uint64_t b0 = smem_desc(stage + P::kABytes, 128, P::kGroupBytes);
+      // 16 voxels (two 256-byte K groups = 32 descriptor units) per MMA
+      const uint64_t a0 = smem_desc_sw32(stage, P::kAtomBytes, 256);
+      const uint64_t b0 = smem_desc_sw32(stage + P::kABytes, P::kAtomBytes, 256);
 #pragma unroll
       for (int kk = 0; kk < kWgKV / 16; ++kk)
-        mma_f16(tmem, a0 + (uint64_t)(16 * kk), b0 + (uint64_t)(16 * kk), idesc,
+        mma_f16(tmem, a0 + (uint64_t)(32 * kk), b0 + (uint64_t)(32 * kk), idesc,
                 (i > 0 || kk > 0) ? 1u : 0u);
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
@@ -917,10 +925,10 @@ __global__ void __launch_bounds__(kConvThreads)
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
   if (ok) {
-    // epilogue: TMEM lane r = row (group r / 8, channel r % 8 of the group)
-    const int r = warp * 32 + lane, g = r / 8;
-    const int G = g0 + g, t = G / c8, ci = (G % c8) * 8 + r % 8;
-    const bool wrow = g < ng, brow = g == bias_g && r % 8 == 0;
+    // epilogue: TMEM lane r = row (atom r / 16, channel r % 16 of the atom)
+    const int r = warp * 32 + lane, g = r / 16;
+    const int G = g0 + g, t = G / c16, ci = (G % c16) * 16 + r % 16;
+    const bool wrow = g < ng, brow = g == bias_g && r % 16 == 0;
 #pragma unroll 1
     for (int cb = 0; cb < N; cb += 16) {
       uint32_t v[16];
@@ -1274,16 +1282,17 @@ void launch_up_bwd(const __nv_bfloat16* dy, int N, int D, int H, int W, int C, _
 }
 
 // Map of a channels-last tensor [n][d][h][w][c] for the weight gradient:
-// box (8 channels, 8, 4, 4 voxels, 1), zero fill outside.
+// box (16 channels, 8, 4, 4 voxels, 1) written with the 32-byte swizzle,
+// zero fill outside.
 static bool wg_map(CUtensorMap* m, const __nv_bfloat16* x, int c, int N, int D, int H, int W) {
   const cuuint64_t dim[5] = {(cuuint64_t)c, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D,
                              (cuuint64_t)N};
   const cuuint64_t row = (cuuint64_t)c * 2;
   const cuuint64_t stride[4] = {row, row * W, row * W * H, row * W * H * D};
-  const cuuint32_t box[5] = {8, kWgBX, kWgBY, kWgBZ, 1};
+  const cuuint32_t box[5] = {16, kWgBX, kWgBY, kWgBZ, 1};
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return encode_tiled()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)x, dim, stride, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -1301,8 +1310,8 @@ cudaError_t launch_wgrad(const __nv_bfloat16* dy, int co, const __nv_bfloat16* x
       !wg_map(&mdy, dy, co, N, D, H, W))
     return cudaErrorInvalidValue;
   if (c2 == 0) mx2 = mx1;
-  // with db, one group more: the ones (an extra M-tile when the last is full)
-  const int mtiles = (27 * ci / 8 + (db ? 1 : 0) + kWgGroups - 1) / kWgGroups;
+  // with db, one atom more: the ones (an extra M-tile when the last is full)
+  const int mtiles = (27 * ci / 16 + (db ? 1 : 0) + kWgAtoms - 1) / kWgAtoms;
   const long long nboxes = (long long)N * ((D + kWgBZ - 1) / kWgBZ) *
                            ((H + kWgBY - 1) / kWgBY) * ((W + kWgBX - 1) / kWgBX);
   // about two CTAs per SM in one wave, each over a contiguous range of boxes
