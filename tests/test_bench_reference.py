@@ -1,6 +1,9 @@
-"""The reference arm of bench.py on the CPU: its JSON line carries every key
-of the benchmark contract (with the oracle's timing stubbed out), and the
-oracle sampling itself runs on a small set."""
+"""Host logic of bench.py on the CPU: the reference arm's JSON line carries
+every key of the benchmark contract (with the oracle's timing stubbed out),
+the oracle sampling runs on a small set, and the roofline object follows its
+definition (dominant fine-level class, algorithmic bytes per launch over the
+average launch time, measured peak, traffic scaled from the committed capture
+and null once the kernel source changed)."""
 import json
 import os
 import sys
@@ -55,3 +58,49 @@ def test_oracle_sample_times_the_oracle_on_a_small_set():
     assert res["kind"] == "oracle" and res["cores"] >= 1 and res["unit"] == bench.UNIT
     assert res["value"] > 0 and abs(res["value"] * res["seconds_per_set"] - 1.0) < 1e-12
     assert "V(2,2)" in res["sample"] and "16^3" in res["sample"]
+
+
+def _prof():
+    return {"smooth": {"ms": 100.0, "launches": 500, "bytes": 500 * 969.0e6},
+            "resid64": {"ms": 50.0, "launches": 20, "bytes": 20 * 4.3e9},
+            "coarse": {"ms": 40.0, "launches": 1000, "bytes": 0.0}}
+
+
+def test_roofline_of_the_dominant_class():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    pk, src = bench.peaks()
+    r = bench.roofline(_prof(), _prof(), 512)
+    assert r["kernel"] == "smooth" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    achieved = 969.0e6 / (0.2e-3) / 1e9          # bytes per launch over 0.2 ms per launch
+    assert abs(r["achieved"] - round(achieved, 1)) < 1e-9
+    assert r["peak"] == float(pk["hbm_gbs"])
+    assert abs(r["frac"] - round(achieved / float(pk["hbm_gbs"]), 4)) < 1e-12
+    assert abs(sum(r["class_share"].values()) - 1.0) < 1e-3
+    assert "coarse" not in r["class_gbs"] and set(r["class_gbs"]) == {"smooth", "resid64"}
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        ent = json.load(fh)["smooth"]
+    if ent["source_hash"] == bench.source_hash(bench.KERNEL_SOURCES["smooth"]):
+        assert r["traffic"] == round(ent["dram_over_algorithmic"] * 969.0e6)
+    else:
+        assert r["traffic"] is None
+
+
+def test_traffic_is_null_once_the_kernel_source_changed(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setitem(bench.KERNEL_SOURCES, "smooth", ["bench.py"])  # another file's hash
+    assert bench.traffic_for("smooth", 1e9) is None
+    assert bench.traffic_for("no-such-class", 1e9) is None
+
+
+def test_roofline_needs_a_fine_level_class_and_peaks_fall_back(monkeypatch, tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.roofline({"coarse": {"ms": 5.0, "launches": 10, "bytes": 0.0}}, {}, 512) is None
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))  # no MEASURED_PEAKS.json there
+    pk, src = bench.peaks()
+    assert src == "fallback" and pk["hbm_gbs"] == 6800.0
