@@ -105,6 +105,7 @@ def test_conv3d_persistent_matches_oracle(mg, c1, c2, cout, relu):
     (32, 16, 0, (2, 4, 6, 9)),
     (96, 32, 16, (1, 5, 7, 10)),    # widest output
     (16, 16, 0, (2, 32, 32, 32)),   # several boxes per CTA: both stages reused
+    (16, 128, 0, (1, 4, 5, 9)),     # 216 atoms fill the last M-tile: the ones get their own
 ])
 def test_wgrad_matches_oracle(mg, cout, c1, c2, shape):
     """Weight and bias gradients on the tensor cores against the oracle's
