@@ -42,7 +42,13 @@ def test_conv3d_backward_finite_differences():
         wp[idx] += eps
         wm[idx] -= eps
         assert abs((f(x, wp) - f(x, wm)) / (2 * eps) - gw[idx]) < 1e-6
-    np.testing.assert_allclose(gb, gy.reshape(-1, 3).sum(0))
+    b = rng.standard_normal(3)
+    fb = lambda bb: float(np.sum(U.conv3d(x, w, bb) * gy))
+    for co in range(3):
+        bp, bm = b.copy(), b.copy()
+        bp[co] += eps
+        bm[co] -= eps
+        assert abs((fb(bp) - fb(bm)) / (2 * eps) - gb[co]) < 1e-6
 
 
 def test_pool_up_identities():
@@ -66,10 +72,12 @@ def test_bf16_rounding():
     assert abs(r[4] - 1e-3) < 1e-3 * 2**-8
 
 
+@pytest.mark.parametrize("part", ["w", "b"])
 @pytest.mark.parametrize("layer", ["enc0a", "enc2b", "enc3a", "up1", "dec0a", "dec2b", "head"])
-def test_network_gradient_finite_differences(layer):
-    """Whole U-Net (FP64): analytic parameter gradients of the MSE loss agree
-    with central differences."""
+def test_network_gradient_finite_differences(layer, part):
+    """Whole U-Net (FP64): analytic gradients of the MSE loss with respect to
+    weights and biases (every sampled layer, the head included) agree with
+    central differences."""
     rng = np.random.default_rng(3)
     shapes = U.layer_shapes()
     flat = []
@@ -82,10 +90,10 @@ def test_network_gradient_finite_differences(layer):
     phi = prev + 0.1 * rng.standard_normal((1, 8, 8, 8))
     sc = (0.7, 1.3, 5.0)
     loss, G = U.loss_and_grads(p, rho, prev, phi, sc)
-    key = layer + (".w" if layer != "head" else ".w")
+    key = f"{layer}.{part}"
     eps = 1e-6
     flatk = p[key].reshape(-1)
-    for q in rng.choice(flatk.size, size=3, replace=False):
+    for q in rng.choice(flatk.size, size=min(3, flatk.size), replace=False):
         orig = flatk[q]
         flatk[q] = orig + eps
         lp, _ = U.loss_and_grads(p, rho, prev, phi, sc)
