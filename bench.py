@@ -61,6 +61,8 @@ def parse():
                          "0 = automatic")
     ap.add_argument("--no-amr", action="store_true",
                     help="skip the composite AMR solve among the extras")
+    ap.add_argument("--no-fp64-leg", action="store_true",
+                    help="skip the FP64-mode GPU solve set among the extras")
     return ap.parse_args()
 
 
@@ -123,40 +125,47 @@ def oracle_problems(n, inputs=None):
     return probs
 
 
-def oracle_sample(inputs, n, count_n=256):
-    """Time the FP64 CPU oracle on the host cores, on a bounded sample of the
-    set: per problem kind, a solve capped at 0 cycles (setup, norms) and at 1
-    cycle at n^3; the difference is the cost of one V(2,2)-cycle.  The set
-    time is that cost times the cycles the oracle itself needs to reach 1e-10
-    on the same workload, counted by full oracle solves at count_n^3 (the
-    V-cycle count of multigrid hardly depends on the grid size)."""
-    cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    counts = []
-    for p, f in oracle_problems(count_n):
-        _, cyc, rel, _ = p.solve(f, tol=TOL, max_cycles=200)
-        counts.append(cyc)
+def oracle_set(inputs, n):
+    """One whole solve set by the FP64 CPU oracle on the host cores, as it
+    stands: the Poisson problem and the three Helmholtz problems, each from a
+    zero guess to the same 1e-10 relative residual as the GPU (the oracle's
+    own V(2,2)-cycles, set-up included).  Returns (seconds, [(cycles, rel)])."""
     probs = oracle_problems(n, inputs)
-    t_set = 0.0
-    per = []
-    for q, (p, f) in enumerate(probs):
-        if q <= 1:  # the Poisson and one Helmholtz problem; the others cost the same per cycle
-            ta = time.perf_counter()
-            p.solve(f, tol=0.0, max_cycles=0)
-            tb = time.perf_counter()
-            p.solve(f, tol=0.0, max_cycles=1)
-            tc = time.perf_counter()
-            tcyc = max((tc - tb) - (tb - ta), 1e-9)
-        per.append(tcyc)
-        t_set += tcyc * counts[q]
-    wall = time.perf_counter() - t0
-    return {"value": 1.0 / t_set, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"FP64 C oracle (OpenMP, {cores} threads): one V(2,2)-cycle at {n}^3 timed "
-                       f"for the Poisson and a Helmholtz problem (cap 1 minus cap 0), "
-                       f"{[round(x, 2) for x in per]} s/cycle, times the oracle's own V-cycle "
-                       f"counts to 1e-10 {counts} (full solves at {count_n}^3); "
-                       f"{wall:.0f} s of CPU work"),
-            "seconds_per_set": t_set}
+    t0 = time.perf_counter()
+    info = []
+    for p, f in probs:
+        _, cyc, rel, _ = p.solve(f, tol=TOL, max_cycles=200)
+        info.append((int(cyc), float(rel)))
+    return time.perf_counter() - t0, info
+
+
+def oracle_sets(inputs, n, max_sets, budget_s):
+    """Whole oracle solve sets, one after another, until max_sets have run or
+    the next one would end after budget_s seconds (at least one runs).
+    Returns (seconds per set, sets run, per-problem (cycles, rel) of the last
+    set, threads)."""
+    cores = os.cpu_count() or 1
+    times, info = [], None
+    t_start = time.perf_counter()
+    while len(times) < max(1, max_sets):
+        if times and (time.perf_counter() - t_start) + statistics.mean(times) > budget_s:
+            break
+        t, info = oracle_set(inputs, n)
+        times.append(t)
+    return statistics.mean(times), len(times), info, cores
+
+
+def oracle_baseline(inputs, n, max_sets=1, budget_s=120.0):
+    """cpu_baseline object: whole oracle solve sets at n^3 timed on all host
+    cores (no extrapolation from a partial solve)."""
+    sec, nsets, info, cores = oracle_sets(inputs, n, max_sets, budget_s)
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 C oracle (OpenMP, {cores} threads), {nsets} whole solve set(s) at "
+                       f"{n}^3: Poisson + 3 Helmholtz, each from zero to 1e-10 relative residual "
+                       f"with the oracle's own V(2,2)-cycles (cycles {[c for c, _ in info]}), "
+                       f"{sec:.1f} s per set"),
+            "seconds_per_set": sec, "sets": nsets,
+            "cycles": [c for c, _ in info], "rel_resid": [r for _, r in info]}
 
 
 # ---------------------------------------------------------------- clocks
@@ -340,6 +349,67 @@ def measure_extras(solver, rho, eps, phi, n, dev):
                                "alpha": alpha}}
 
 
+def fp64_residuals(solver, rho, phi, S, psi):
+    """Relative residual ||b - A u|| / ||b|| of each answer of a set (Poisson,
+    then the three Helmholtz problems), formed by the library's plain FP64
+    kernel (mg_residual_norms)."""
+    out = []
+    rn, bn = solver.residual_norms("poisson", rho, phi)
+    out.append(rn / bn)
+    for p, k in zip(psi, KAPPAS):
+        rn, bn = solver.residual_norms("helmholtz", S, p, k)
+        out.append(rn / bn)
+    return out
+
+
+def measure_fp64_gpu(rho, eps, S, n, dev, phi_mixed, psi_mixed, mixed_sets_per_s, reps=2):
+    """The same solve set in FP64 mode on the same GPU (plain FP64 V(2,2)
+    multigrid, one problem after another, the form of the paper's solver):
+    sets/s by CUDA events over `reps` sets after one untimed set, its answers'
+    FP64 residuals, and the relative L2 distance of the mixed-precision
+    answers from them (outside the timed region)."""
+    import torch
+
+    from paper_1809_08857_gb300 import mg
+
+    s64 = mg.Solver((n, n, n), 1.0 / n, eps_r=eps, precision=mg.MG_PREC_FP64)
+    phi = torch.zeros_like(phi_mixed)
+    psi = [torch.zeros_like(phi) for _ in range(3)]
+    st = None
+
+    def one():
+        nonlocal st
+        phi.zero_()
+        for p in psi:
+            p.zero_()
+        st = s64.solve_set(rho, phi, S, psi, KAPPAS, TOL)
+
+    one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    res = fp64_residuals(s64, rho, phi, S, psi)
+    s64.close()
+
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+    dist = [rel(phi_mixed, phi)] + [rel(a, b) for a, b in zip(psi_mixed, psi)]
+    del phi, psi
+    torch.cuda.empty_cache()
+    return {"workload": "the same set, FP64 V(2,2)-cycles on the GPU (no mixed precision, "
+                        "problems one after another)",
+            "ms": round(ms, 1), "sets_per_s": round(1e3 / ms, 3),
+            "cycles": [x["cycles"] for x in st], "rel_resid_fp64": res,
+            "mixed_over_fp64": round(mixed_sets_per_s * ms * 1e-3, 2),
+            "rel_l2_mixed_vs_fp64": dist}
+
+
 def measure_unet(dev, n=256, reps=5):
     """One warm-start U-Net forward pass (mg_unet_predict) on a 256^3 volume
     (outside the timed region): device time per pass (CUDA events) and the
@@ -425,23 +495,42 @@ def measure_amr(dev, n0=256, reps=3):
 # ---------------------------------------------------------------- arms
 
 
+def reference_config(args):
+    return {"workload": f"poisson_slab_shell_{args.n}^3 + 3x helmholtz_{args.n}^3 (kappa L = 10, 100, 1000)",
+            "grid": [args.n] * 3, "tol": TOL, "implementation": "FP64 C oracle (oracle/mg_oracle.c)",
+            "precision": "fp64", "smoother": "red-black Gauss-Seidel V(2,2)",
+            "coarsest": "exact solve of the coarsest grid", "threads": os.cpu_count() or 1,
+            "device": "host CPU cores (OpenMP)", "guess": "zero"}
+
+
+# whole oracle sets of the reference arm end within this many seconds (a set
+# at 512^3 takes about 45 s on 16 Arm cores)
+REFERENCE_BUDGET_S = 200.0
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
     inputs = workload(args.n)
-    res = None
     t0 = time.perf_counter()
-    for _ in range(max(1, args.steps)):
-        res = oracle_sample(inputs, args.n)
+    sec, nsets, info, cores = oracle_sets(inputs, args.n, args.steps, REFERENCE_BUDGET_S)
     wall = time.perf_counter() - t0
-    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / res["value"],
+    value = 1.0 / sec
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": nsets, "warmup": 0, "steps_requested": args.steps,
+            "warmup_requested": args.warmup, "ms_per_step": 1e3 * sec,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded streamer shell, dielectric slab, smoothed ionisation source)",
-            "config": config(args), "impl": "reference",
-            "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
-            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+            "config": reference_config(args), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": (f"{nsets} whole oracle solve set(s) at {args.n}^3 timed "
+                                        f"one after another (no warm-up: plain CPU code), "
+                                        f"cycles {[c for c, _ in info]}, "
+                                        f"final rel. residuals {[f'{r:.2e}' for _, r in info]}; "
+                                        f"stops before a set would end after "
+                                        f"{REFERENCE_BUDGET_S:.0f} s")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "wall_s": round(wall, 1)}
     print(json.dumps(line), flush=True)
@@ -517,6 +606,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
     launches = mg.launch_count() - l0
+    # each answer of the last timed set checked in plain FP64 (not by the
+    # double-float refinement pass that decided to stop)
+    fp64_check = fp64_residuals(solver, rho, phi, S, psi)
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms_per_step = ms / args.steps
     value = whole_job_rate(world, ms_per_step * 1e-3)
@@ -617,7 +709,13 @@ def run_ours(args):
     prof_serial = solver.profile_read(reset=True)
     solver.set_options(concurrency=conc)
     solver.profile(False)
+    if prec == mg.MG_PREC_MIXED and not args.no_fp64_leg:
+        extras_fp64 = measure_fp64_gpu(rho, eps, S, n, dev, phi, psi, value)
+    else:
+        extras_fp64 = None
     extras = measure_extras(solver, rho, eps, phi, n, dev)
+    if extras_fp64:
+        extras["fp64_gpu"] = extras_fp64
     extras["unet_forward"] = measure_unet(dev)
     if not args.no_amr:
         extras["amr_solve"] = measure_amr(dev)
@@ -625,17 +723,19 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 (FP32 V-cycles in FP64 refinement)" if prec else "f64",
+            "dtype": ("double-float (FP32 pairs) refinement over FP32 V-cycles; FP64 data"
+                      if prec else "f64"),
             "data": "synthetic (seeded streamer shell, dielectric slab, smoothed ionisation source)",
             "config": dict(config(args), autotuned=tuned, nu1=solver.options.nu1,
                            nu2=solver.options.nu2, inner_cycles=solver.options.inner_cycles,
                            ir_zchunk=solver.options.ir_zchunk),
             "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": launches, "cycles_per_problem": cycles,
+            "rel_resid_fp64": fp64_check,
             "roofline": roofline(prof_serial, prof_overlap, n), "kernel_profile": prof_serial,
             "extras": extras}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res = oracle_sample(inputs, n)
+        res = oracle_baseline(inputs, n)
         line["cpu_baseline"] = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
     emit(line, rank)
     solver.close()

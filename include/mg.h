@@ -194,6 +194,21 @@ mg_status mg_solve_helmholtz_batch(mg_ctx* ctx, const double* S, double* const p
                                    const double kappa[3], double tol, mg_stats stats[3]);
 
 /*
+ * mg_solve_photoionization -- the three-term radiative-transfer solves of
+ * Eq. 3 with a source amplitude per term: (kappa_j^2 - lap) Psi_j = A_j S,
+ * j = 0, 1, 2.  In the paper's three-group photoionisation model each group
+ * has its own amplitude and absorption coefficient and the photoionisation
+ * source is the sum of the three solutions; the paper prints neither set of
+ * coefficients, so both come from the caller.  Boundary conditions, kappa,
+ * psi, tol and stats as in mg_solve_helmholtz_batch.
+ *   amp    host, three finite amplitudes A_j (A_j = 1 is
+ *          mg_solve_helmholtz_batch).
+ */
+mg_status mg_solve_photoionization(mg_ctx* ctx, const double* S, double* const psi[3],
+                                   const double kappa[3], const double amp[3], double tol,
+                                   mg_stats stats[3]);
+
+/*
  * mg_solve_set -- the elliptic solves of one time step of the paper's scheme
  * (Sec. 2.2: the field update followed by the radiative-transfer update):
  * the Poisson problem of mg_solve_poisson and the three Helmholtz problems of
@@ -491,6 +506,25 @@ mg_status mg_warmstart_load(mg_ctx* ctx, const char* weights_path);
 mg_status mg_poisson_residual(mg_ctx* ctx, const double* rho, double* phi, double* r);
 
 /*
+ * mg_residual_norms -- the norms of the stopping test of a solve, in plain
+ * FP64 arithmetic on the natural layout (a check of an answer that does not
+ * reuse the double-float refinement pass): norms[0] = ||b - A u||_2 and
+ * norms[1] = ||b||_2 (the residual of the guess that is 0 on free cells and
+ * keeps the electrode values), both over the free cells, for the problem of
+ * the discretisation of Sec. 2 items (ii)-(iii) on the context's grid,
+ * coefficients, electrodes and boundary conditions.
+ *   kind   MG_PROBLEM_POISSON (Eq. 2, rhs = rho, b = rho/eps0 + lifts, param
+ *          unused), MG_PROBLEM_HELMHOLTZ (Eq. 3, param = kappa > 0, rhs = S)
+ *          or MG_PROBLEM_SCREENED (param = alpha >= 0, rhs = f).
+ *   u      device, nx*ny*nz FP64 iterate whose electrode cells hold their
+ *          values (as every solve leaves them).
+ *   norms  host, two FP64 (output).
+ * Uses the context's stream and work slot 0; synchronises.
+ */
+mg_status mg_residual_norms(mg_ctx* ctx, int kind, double param, const double* rhs,
+                            const double* u, double norms[2]);
+
+/*
  * mg_warmstart_predict -- guess for the Poisson solve of rho from the
  * previous potential.  The network is applied to the residual of the
  * previous potential, r = b_n - A phi_prev = A (phi_n - phi_prev) (its first
@@ -556,9 +590,12 @@ long long mg_launch_count(void);
  *   cuda_stream  stream to enqueue on (NULL = legacy default stream).
  * Work is enqueued and the call returns without synchronising.  Scratch: a
  * library-owned static device array of 16384 FP64 partial sums (128 KiB per
- * GPU, held until the process exits); grids need ceil(nx/30)*ceil(ny/14) <=
- * 16384 (every grid up to 2048 x 2048 x any nz), larger ones are rejected with
- * MG_ERR_UNSUPPORTED.  The first call on a device looks up the array's device
+ * GPU, held until the process exits), one per thread block of the residual
+ * kernel: ceil(nx/30) * ceil(ny/14) * (z-chunks of its automatic tile), which
+ * the tile keeps at most max(ceil(nx/30) * ceil(ny/14), 10944).  So every
+ * grid with ceil(nx/30) * ceil(ny/14) <= 16384 fits (every grid up to 2048 x
+ * 2048 in x and y); nz and ceil(ny/14) must not exceed 65535.  Larger grids
+ * are rejected with MG_ERR_UNSUPPORTED before anything is launched.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current, so make that first
  * call before capturing work into a CUDA graph on that device.  Every call
  * shares the array: calls that overlap on the GPU (other streams or host

@@ -575,7 +575,7 @@ Prob make_prob(mg_ctx* c, Kind kind, double alpha, const double* rhs, const doub
   p.c = c;
   p.kind = kind;
   p.alpha = alpha;
-  p.rhs_scale = kind == kPoisson ? rhs_scale : 1.0;
+  p.rhs_scale = kind == kPoisson ? rhs_scale : 1.0;  // set after the call for a scaled source
   p.rhs = rhs;
   p.faces = faces;
   p.u = u;
@@ -587,6 +587,26 @@ Prob make_prob(mg_ctx* c, Kind kind, double alpha, const double* rhs, const doub
 // Electrode values into u and the right-hand side with lifts, on stream s:
 // Poisson b = rho/eps0 + lifts (screened: f + lifts); Helmholtz b = S (+
 // lifts of face data).
+// b = rhs * scale + the domain-face lifts of the problem kind (Dirichlet
+// values of the context's bc, or the packed face data) into out, on stream s.
+mg_status form_b(mg_ctx* c, Kind kind, double scale, const double* rhs, const double* faces,
+                 double* out, cudaStream_t s) {
+  Level& L0 = c->lv[0];
+  uint8_t dir[6];
+  double zero[6] = {0, 0, 0, 0, 0, 0};
+  for (int f = 0; f < 6; ++f)
+    dir[f] = kind == kPoisson ? poisson_dir(c, f) : c->opt.rte_bc == MG_RTE_BC_DIRICHLET;
+  {
+    Scope sc(c, s, MG_KCLASS_COARSE, 0);
+    if (kind == kPoisson)
+      mg::launch_rhs64(rhs, scale, L0.beta64, L0.mask, L0.b, L0.ih2, dir, c->bc.value, faces, out,
+                       s);
+    else
+      mg::launch_rhs64(rhs, scale, nullptr, L0.mask, L0.b, L0.ih2, dir, zero, faces, out, s);
+  }
+  return check_launch();
+}
+
 mg_status prepare(Prob& p, cudaStream_t s) {
   mg_ctx* c = p.c;
   Level& L0 = c->lv[0];
@@ -594,26 +614,14 @@ mg_status prepare(Prob& p, cudaStream_t s) {
     Scope sc(c, s, MG_KCLASS_COARSE, 0);
     mg::launch_set_masked(L0.mask, p.kind == kPoisson ? c->mask_value : nullptr, L0.b.n(), p.u, s);
   }
-  if (p.kind == kHelmholtz && !p.faces) {
+  if (p.kind == kHelmholtz && !p.faces && p.rhs_scale == 1.0) {
     p.b = p.rhs;
     return check_launch();
   }
   if (!p.w->b64) MG_TRY(c->alloc(&p.w->b64, (size_t)L0.b.n()));
-  uint8_t dir[6];
-  double zero[6] = {0, 0, 0, 0, 0, 0};
-  for (int f = 0; f < 6; ++f)
-    dir[f] = p.kind == kPoisson ? poisson_dir(c, f) : c->opt.rte_bc == MG_RTE_BC_DIRICHLET;
-  {
-    Scope sc(c, s, MG_KCLASS_COARSE, 0);
-    if (p.kind == kPoisson)
-      mg::launch_rhs64(p.rhs, p.rhs_scale, L0.beta64, L0.mask, L0.b, L0.ih2, dir, c->bc.value,
-                       p.faces, p.w->b64, s);
-    else
-      mg::launch_rhs64(p.rhs, 1.0, nullptr, L0.mask, L0.b, L0.ih2, dir, zero, p.faces, p.w->b64,
-                       s);
-  }
+  MG_TRY(form_b(c, p.kind, p.rhs_scale, p.rhs, p.faces, p.w->b64, s));
   p.b = p.w->b64;
-  return check_launch();
+  return MG_OK;
 }
 
 // The refinement step of p: inner V-cycles on A e = r, then the fused FP64
@@ -1768,6 +1776,24 @@ mg_status mg_solve_helmholtz_batch(mg_ctx* c, const double* S, double* const psi
   return solve(P);
 }
 
+mg_status mg_solve_photoionization(mg_ctx* c, const double* S, double* const psi[3],
+                                   const double kappa[3], const double amp[3], double tol,
+                                   mg_stats stats[3]) {
+  g_last_error.clear();
+  MG_TRY(check_ctx_tol(c, tol));
+  MG_TRY(check_helmholtz_args(S, psi, kappa));
+  if (!amp) return fail(MG_ERR_INVALID_ARG, "NULL amplitudes");
+  for (int j = 0; j < 3; ++j)
+    if (!std::isfinite(amp[j])) return fail(MG_ERR_INVALID_ARG, "amplitudes must be finite");
+  std::vector<Prob> P;
+  for (int j = 0; j < 3; ++j) {
+    P.push_back(make_prob(c, kHelmholtz, kappa[j] * kappa[j], S, nullptr, psi[j], tol,
+                          stats ? &stats[j] : nullptr));
+    P.back().rhs_scale = amp[j];
+  }
+  return solve(P);
+}
+
 mg_status mg_solve_set(mg_ctx* c, const double* rho, double* phi, const double* S,
                        double* const psi[3], const double kappa[3], double tol,
                        mg_stats stats[4]) {
@@ -1994,6 +2020,46 @@ mg_status mg_poisson_residual(mg_ctx* c, const double* rho, double* phi, double*
   g_last_error.clear();
   if (!c || !rho || !phi || !r) return fail(MG_ERR_INVALID_ARG, "NULL argument");
   return poisson_residual(c, rho, phi, r, nullptr);
+}
+
+mg_status mg_residual_norms(mg_ctx* c, int kind, double param, const double* rhs,
+                            const double* u, double norms[2]) {
+  g_last_error.clear();
+  if (!c || !rhs || !u || !norms) return fail(MG_ERR_INVALID_ARG, "NULL argument");
+  Kind k = kPoisson;
+  double alpha = 0.0, scale = 1.0 / kEps0;
+  if (kind == MG_PROBLEM_HELMHOLTZ) {
+    if (!(param > 0.0) || !std::isfinite(param))
+      return fail(MG_ERR_INVALID_ARG, "kappa must be finite and > 0");
+    k = kHelmholtz;
+    alpha = param * param;
+    scale = 1.0;
+  } else if (kind == MG_PROBLEM_SCREENED) {
+    if (!(param >= 0.0) || !std::isfinite(param))
+      return fail(MG_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+    alpha = param;
+    scale = 1.0;
+  } else if (kind != MG_PROBLEM_POISSON) {
+    return fail(MG_ERR_INVALID_ARG, "unknown problem kind");
+  }
+  cudaStream_t s = c->stream;
+  Work* w;
+  MG_TRY(get_work(c, 0, &w));
+  const Level& L0 = c->lv[0];
+  if (!w->b64) MG_TRY(c->alloc(&w->b64, (size_t)L0.b.n()));
+  MG_TRY(form_b(c, k, scale, rhs, nullptr, w->b64, s));
+  const int nblk = mg::resid_norms_blocks(L0.b, c->npartial);
+  {
+    Scope sc(c, s, MG_KCLASS_COARSE, 0);
+    mg::launch_resid_norms64(op64(c, 0, k, alpha), alpha, w->b64, u, w->partial, nblk, s);
+    mg::launch_sum_partials(w->partial, nblk, w->norm_map + 1, s);
+    mg::launch_sum_partials(w->partial + nblk, nblk, w->norm_map, s);
+  }
+  MG_TRY(check_launch());
+  MG_CUDA(cudaStreamSynchronize(s));
+  norms[0] = std::sqrt(w->norm_host[1]);
+  norms[1] = std::sqrt(w->norm_host[0]);
+  return MG_OK;
 }
 
 mg_status mg_warmstart_predict(mg_ctx* c, const double* rho, const double* phi_prev,

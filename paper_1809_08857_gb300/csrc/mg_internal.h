@@ -170,6 +170,14 @@ void launch_resid64(const Op64& op, double alpha, const double* f, const double*
 void launch_dense_apply64(const double* Minv, int n, const double* r, double* u, cudaStream_t s);
 
 
+// FP64 norms of the residual of u (plain FP64 on the natural layout): per
+// block the sums over free cells of (f - A u)^2 into part[0..nblk) and of
+// the zero guess's residual (electrode values kept) into part[nblk..2 nblk);
+// nblk = resid_norms_blocks(b, capacity of each half).
+int resid_norms_blocks(const Box& b, int cap);
+void launch_resid_norms64(const Op64& op, double alpha, const double* f, const double* u,
+                          double* part, int nblk, cudaStream_t s);
+
 // sum of partial[0..n) into *out (single block, fixed order); out may be the
 // device-side address of mapped pinned host memory.
 void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s);

@@ -17,6 +17,7 @@
 // z-chunk with its planes in registers; y-neighbours go through shared
 // memory, x-neighbours through warp shuffles.
 #include <cmath>
+#include <cstdio>
 #include <mutex>
 #include <string>
 
@@ -284,28 +285,42 @@ __global__ void k_df_to_f64(const float2* __restrict__ in, const uint8_t* __rest
 
 }  // namespace
 
+// CTA columns of the refinement pass along x and y (30 x 14 own columns
+// per CTA), in 64-bit so that no grid size can wrap them.
+static long long ir_gx(const Box& b) { return ((long long)b.nx + TX - 3) / (TX - 2); }
+static long long ir_gy(const Box& b) { return ((long long)b.ny + TY - 3) / (TY - 2); }
+
 // Grid of the refinement pass for z planes per CTA column `hint` (0:
-// automatic); *zchunk receives the planes used.
+// automatic); *zchunk receives the planes used.  The automatic choice halves
+// the z run while the grid has fewer than 8 * 152 * 3 CTAs (8 waves of three
+// 512-thread CTAs on each of GB300's 152 SMs) and the run is longer than 16
+// planes, so its CTA count is gx * gy when gx * gy >= 3648 and below
+// 3 * 3648 otherwise: at most max(gx * gy, 10944).
 static dim3 ir_grid(const Box& b, int hint, int* zchunk) {
-  const int gx = (b.nx + TX - 3) / (TX - 2), gy = (b.ny + TY - 3) / (TY - 2);
+  const long long gx = ir_gx(b), gy = ir_gy(b);
   int zc = b.nz;
   if (hint > 0) {
     zc = std::min(hint, b.nz);
   } else {
-    // enough CTAs to fill every SM (152 on GB300, three 512-thread CTAs
-    // each) several times over, long z runs
-    while (zc > 16 && (long long)gx * gy * ((b.nz + zc - 1) / zc) < 8 * 152 * 3)
+    while (zc > 16 && gx * gy * (((long long)b.nz + zc - 1) / zc) < 8 * 152 * 3)
       zc = (zc + 1) / 2;
   }
   *zchunk = zc;
-  return dim3(gx, gy, (b.nz + zc - 1) / zc);
+  return dim3((unsigned)gx, (unsigned)gy, (unsigned)((b.nz + zc - 1) / zc));
 }
 
-int ir_partials(const Box& b, int zchunk) {
-  int zc;
-  dim3 g = ir_grid(b, zchunk, &zc);
-  return (int)(g.x * g.y * g.z);
+// CTAs of the refinement pass (64-bit, computed before any dim3 narrowing).
+static long long ir_ctas(const Box& b, int zchunk) {
+  int zc = b.nz;
+  if (zchunk > 0) {
+    zc = std::min(zchunk, b.nz);
+  } else {
+    ir_grid(b, 0, &zc);
+  }
+  return ir_gx(b) * ir_gy(b) * (((long long)b.nz + zc - 1) / zc);
 }
+
+int ir_partials(const Box& b, int zchunk) { return (int)ir_ctas(b, zchunk); }
 
 template <bool F, bool E, bool U, int B, bool Z>
 static void go(const IrArgs& a, dim3 g, cudaStream_t s) {
@@ -470,10 +485,21 @@ extern "C" mg_status mg_residual_norm_noalloc(const mg_grid* grid, const mg_bc* 
       return MG_ERR_INVALID_ARG;
     }
   mg::Box box{grid->nx, grid->ny, grid->nz};
-  const int nparts = mg::ir_partials(box);
+  // launch limits of the kernel's grid: y and z extents below 65536
+  if (mg::ir_gy(box) > 65535 || box.nz > 65535) {
+    mg::set_last_error("grid too large for the refinement kernel's launch: ceil(ny/14) and nz "
+                       "must not exceed 65535");
+    return MG_ERR_UNSUPPORTED;
+  }
+  const long long nparts = mg::ir_ctas(box, 0);
   if (nparts > MG_NOALLOC_MAX_PARTIALS) {
-    mg::set_last_error("grid too large for the allocation-free scratch: ceil(nx/30)*ceil(ny/14) "
-                       "must not exceed 16384");
+    char msg[256];
+    std::snprintf(msg, sizeof msg,
+                  "grid too large for the allocation-free scratch: the residual kernel needs "
+                  "%lld partial sums (ceil(nx/30) * ceil(ny/14) * z-chunks), more than the "
+                  "16384 of the static array",
+                  nparts);
+    mg::set_last_error(msg);
     return MG_ERR_UNSUPPORTED;
   }
   double* scratch = nullptr;
@@ -493,7 +519,7 @@ extern "C" mg_status mg_residual_norm_noalloc(const mg_grid* grid, const mg_bc* 
   a.rhs_scale = rhs_scale;
   a.lift = 1;
   a.u_in = u;
-  mg::launch_noalloc(a, scratch, nparts, norm_out, (cudaStream_t)cuda_stream);
+  mg::launch_noalloc(a, scratch, (int)nparts, norm_out, (cudaStream_t)cuda_stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     mg::set_last_error(std::string("kernel launch: ") + cudaGetErrorString(e));

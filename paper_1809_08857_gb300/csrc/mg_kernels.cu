@@ -5,6 +5,8 @@
 // Discretisation: Sec. 2 items (ii)-(iii) of arXiv:1809.08857 (second-order
 // cell-centred finite volumes for Eqs. 2 and 3); smoother: red-black
 // Gauss-Seidel (Sec. 2 item (ii)).
+#include <algorithm>
+
 #include "mg_internal.h"
 
 namespace mg {
@@ -391,6 +393,38 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;  // valid in thread 0
 }
 
+// FP64 norms of a field's residual, plain FP64 arithmetic on the natural
+// layout (independent of the double-float refinement pass): per block, the
+// sum over free cells of (f - A u)^2 into part[block] and of the residual of
+// the guess that is 0 on free cells and u on electrode cells (the norm of b
+// with the electrode lifts) into part[nblk + block].  Grid-stride.
+__global__ void k_resid_norms64(Op64 op, double alpha, const double* __restrict__ f,
+                                const double* __restrict__ u, double* part, int nblk) {
+  const long long n = op.b.n();
+  double s = 0.0, sb = 0.0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    if (masked(op, c)) continue;
+    const int i = (int)(c % op.b.nx);
+    const long long jk = c / op.b.nx;
+    const int j = (int)(jk % op.b.ny), k = (int)(jk / op.b.ny);
+    double diag, off, offb;
+    row(op, i, j, k, c, [&](long long q) { return u[q]; }, diag, off);
+    row(op, i, j, k, c, [&](long long q) { return masked(op, q) ? u[q] : 0.0; }, diag, offb);
+    const double r = f[c] - ((diag + alpha) * u[c] - off);
+    const double rb = f[c] + offb;
+    s += r * r;
+    sb += rb * rb;
+  }
+  s = block_sum(s);
+  __syncthreads();  // block_sum's shared scratch is reused
+  sb = block_sum(sb);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s;
+    part[nblk + blockIdx.x] = sb;
+  }
+}
+
 __global__ void k_sum_partials(const double* partial, int n, double* out) {
   double s = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) s += partial[t];
@@ -503,6 +537,17 @@ void launch_resid64(const Op64& op, double alpha, const double* f, const double*
 void launch_dense_apply64(const double* Minv, int n, const double* r, double* u,
                           cudaStream_t s) {
   k_dense_apply<double><<<blocks_for((long long)n * 32), kThreads, 0, s>>>(Minv, n, r, u);
+  add_launches(1);
+}
+
+int resid_norms_blocks(const Box& b, int cap) {
+  const long long want = (b.n() + kThreads - 1) / kThreads;
+  return (int)std::max(1LL, std::min<long long>(want, std::min(cap, 152 * 8)));
+}
+
+void launch_resid_norms64(const Op64& op, double alpha, const double* f, const double* u,
+                          double* part, int nblk, cudaStream_t s) {
+  k_resid_norms64<<<nblk, kThreads, 0, s>>>(op, alpha, f, u, part, nblk);
   add_launches(1);
 }
 

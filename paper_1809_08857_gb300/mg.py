@@ -38,7 +38,8 @@ EXPORTS = [
     "mg_unet_train_step", "mg_unet_predict", "mg_unet_grads", "mg_unet_num_params",
     "mg_unet_get_params", "mg_unet_set_params", "mg_unet_save", "mg_unet_load", "mg_nn_conv3d",
     "mg_nn_conv3d_stalled", "mg_nn_conv3d_wgrad", "mg_warmstart_attach", "mg_warmstart_load", "mg_warmstart_predict",
-    "mg_poisson_residual", "mg_solve_screened", "mg_efield",
+    "mg_poisson_residual", "mg_solve_screened", "mg_efield", "mg_solve_photoionization",
+    "mg_residual_norms",
     "mg_amr_create", "mg_amr_solve", "mg_amr_residual", "mg_amr_destroy",
 ]
 
@@ -129,6 +130,14 @@ def load():
     lib.mg_solve_set.argtypes = [P, P, P, P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_double),
                                  ctypes.c_double, ctypes.POINTER(Stats)]
     lib.mg_solve_set.restype = ctypes.c_int
+    lib.mg_solve_photoionization.argtypes = [P, P, ctypes.POINTER(P),
+                                             ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                             ctypes.POINTER(Stats)]
+    lib.mg_solve_photoionization.restype = ctypes.c_int
+    lib.mg_residual_norms.argtypes = [P, ctypes.c_int, ctypes.c_double, P, P,
+                                      ctypes.POINTER(ctypes.c_double)]
+    lib.mg_residual_norms.restype = ctypes.c_int
     lib.mg_set_stream.argtypes = [P, P]
     lib.mg_set_stream.restype = ctypes.c_int
     lib.mg_level_info.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -242,6 +251,17 @@ def residual_norm_noalloc(u, rhs, h, alpha=0.0, rhs_scale=1.0, mask=None,
     float64 tensor of one element that receives the norm (allocated here by
     torch if not given); the call is asynchronous on the stream."""
     lib = load()
+    if u.dim() != 3:
+        raise ValueError(f"u must be a 3-D (nz, ny, nx) field, got shape {tuple(u.shape)}")
+    if tuple(rhs.shape) != tuple(u.shape):
+        raise ValueError(f"rhs shape {tuple(rhs.shape)} != u shape {tuple(u.shape)}")
+    if mask is not None and tuple(mask.shape) != tuple(u.shape):
+        raise ValueError(f"mask shape {tuple(mask.shape)} != u shape {tuple(u.shape)}")
+    if out is not None and out.numel() < 1:
+        raise ValueError("out must hold at least one element")
+    for name, t in (("rhs", rhs), ("mask", mask), ("out", out)):
+        if t is not None and t.device != u.device:
+            raise ValueError(f"{name} is on {t.device}, u on {u.device}")
     nz, ny, nx = (int(s) for s in u.shape)
     g = Grid(nx, ny, nz, float(h), (ctypes.c_double * 3)(0.0, 0.0, 0.0))
     bc = BC((ctypes.c_int * 6)(*[int(k) for k in bc_kind]),
@@ -494,6 +514,40 @@ class Solver:
                                                     float(tol), st)
         _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
         return [s.as_dict() for s in st]
+
+    def solve_photoionization(self, S, psi, kappa, amp, tol=1e-10,
+                              raise_on_nonconvergence=True):
+        """(kappa_j^2 - lap) Psi_j = amp_j S in place on psi[0..2]
+        (mg_solve_photoionization)."""
+        self._check_field(S)
+        if len(psi) != 3 or len(kappa) != 3 or len(amp) != 3:
+            raise ValueError("need three psi arrays, three kappas and three amplitudes")
+        for p in psi:
+            self._check_field(p)
+        self.set_stream()
+        ptrs = (ctypes.c_void_p * 3)(*[p.data_ptr() for p in psi])
+        for p in psi:
+            _ptr(p, torch.float64)
+        kap = (ctypes.c_double * 3)(*[float(k) for k in kappa])
+        am = (ctypes.c_double * 3)(*[float(a) for a in amp])
+        st = (Stats * 3)()
+        status = self._lib.mg_solve_photoionization(self._ctx, _ptr(S, torch.float64), ptrs, kap,
+                                                    am, float(tol), st)
+        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        return [s.as_dict() for s in st]
+
+    def residual_norms(self, kind, rhs, u, param=0.0):
+        """(||b - A u||_2, ||b||_2) over the free cells in plain FP64
+        (mg_residual_norms); kind "poisson", "helmholtz" (param = kappa) or
+        "screened" (param = alpha)."""
+        self._check_field(rhs)
+        self._check_field(u)
+        self.set_stream()
+        out = (ctypes.c_double * 2)()
+        _check(self._lib.mg_residual_norms(self._ctx, _KINDS[kind], float(param),
+                                           _ptr(rhs, torch.float64), _ptr(u, torch.float64),
+                                           out))
+        return out[0], out[1]
 
     def solve_set(self, rho, phi, S, psi, kappa, tol=1e-10, raise_on_nonconvergence=True):
         """Poisson (in place on phi) and the three Helmholtz problems (in place

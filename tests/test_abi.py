@@ -130,3 +130,21 @@ def test_conv3d_rejects_bad_arguments_without_gpu(lib):
     stalled = lib.mg_nn_conv3d_stalled
     assert stalled(*args(odd, 16, None, 0, good, 16)) == mg.MG_ERR_INVALID_ARG
     assert stalled(*args(good, 24, None, 0, good, 16)) == mg.MG_ERR_UNSUPPORTED
+
+
+def test_noalloc_binding_rejects_mismatched_shapes():
+    """The binding of mg_residual_norm_noalloc checks shapes, rank and the
+    output size before anything reaches the library (so a smaller rhs or mask
+    can never be read past its end)."""
+    torch = pytest.importorskip("torch")
+    from paper_1809_08857_gb300 import mg
+
+    u = torch.zeros((4, 5, 6), dtype=torch.float64)
+    with pytest.raises(ValueError, match="rhs shape"):
+        mg.residual_norm_noalloc(u, torch.zeros((4, 5, 5), dtype=torch.float64), 0.1)
+    with pytest.raises(ValueError, match="mask shape"):
+        mg.residual_norm_noalloc(u, u, 0.1, mask=torch.zeros((4, 5, 5), dtype=torch.uint8))
+    with pytest.raises(ValueError, match="3-D"):
+        mg.residual_norm_noalloc(u.view(-1), u.view(-1), 0.1)
+    with pytest.raises(ValueError, match="at least one"):
+        mg.residual_norm_noalloc(u, u, 0.1, out=torch.empty(0, dtype=torch.float64))

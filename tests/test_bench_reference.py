@@ -1,6 +1,6 @@
 """Host logic of bench.py on the CPU: the reference arm's JSON line carries
 every key of the benchmark contract (with the oracle's timing stubbed out),
-the oracle sampling runs on a small set, and the roofline object follows its
+whole oracle solve sets are timed within the budget, and the roofline object follows its
 definition (dominant fine-level class, algorithmic bytes per launch over the
 average launch time, measured peak, traffic scaled from the committed capture
 and null once the kernel source changed)."""
@@ -24,9 +24,9 @@ def _args(monkeypatch, argv):
 def test_reference_line_carries_the_contract(monkeypatch, capsys):
     bench, args = _args(monkeypatch, ["--impl", "reference", "--n", "16", "--steps", "2",
                                       "--warmup", "3"])
-    stub = {"value": 0.5, "unit": bench.UNIT, "cores": 4, "kind": "oracle", "sample": "stub",
-            "seconds_per_set": 2.0}
-    monkeypatch.setattr(bench, "oracle_sample", lambda inputs, n, count_n=256: dict(stub))
+    info = [(14, 9e-11), (10, 8e-11), (8, 7e-11), (3, 6e-11)]
+    monkeypatch.setattr(bench, "oracle_sets",
+                        lambda inputs, n, max_sets, budget: (2.0, 2, list(info), 4))
     assert bench.run_reference(args) == 0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     required = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
@@ -35,11 +35,39 @@ def test_reference_line_carries_the_contract(monkeypatch, capsys):
     assert required <= set(line)
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["value"] == 0.5 and line["ms_per_step"] == 2000.0 and line["higher_is_better"]
-    assert (line["steps"], line["warmup"], line["n_gpus"]) == (2, 3, 1)
+    # the steps that ran (whole oracle sets), the requested counts beside them
+    assert (line["steps"], line["warmup"], line["n_gpus"]) == (2, 0, 1)
+    assert (line["steps_requested"], line["warmup_requested"]) == (2, 3)
     assert line["e2e"] == {"value": 0.5, "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert set(line["cpu_baseline"]) == {"value", "unit", "cores", "kind", "sample"}
-    assert line["config"]["grid"] == [16, 16, 16]
+    assert line["cpu_baseline"]["cores"] == 4 and line["cpu_baseline"]["value"] == 0.5
+    # the config describes the CPU oracle, not the GPU run
+    cfg = line["config"]
+    assert cfg["grid"] == [16, 16, 16] and cfg["precision"] == "fp64"
+    assert "oracle" in cfg["implementation"] and "concurrency" not in cfg
+
+
+def test_oracle_sets_stop_within_the_budget(monkeypatch):
+    """Whole sets run until the requested count, or until the next one would
+    end after the budget; at least one always runs."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    clock = [0.0]
+    monkeypatch.setattr(bench.time, "perf_counter", lambda: clock[0])
+
+    def fake_set(inputs, n):
+        clock[0] += 30.0
+        return 30.0, [(5, 1e-11)] * 4
+
+    monkeypatch.setattr(bench, "oracle_set", fake_set)
+    sec, nsets, info, _ = bench.oracle_sets(None, 16, max_sets=20, budget_s=100.0)
+    assert (sec, nsets) == (30.0, 3)  # a fourth set would end at 120 s
+    sec, nsets, _, _ = bench.oracle_sets(None, 16, max_sets=2, budget_s=1000.0)
+    assert nsets == 2
+    sec, nsets, _, _ = bench.oracle_sets(None, 16, max_sets=5, budget_s=1.0)
+    assert nsets == 1
 
 
 def test_reference_arm_other_ranks_print_nothing(monkeypatch, capsys):
@@ -50,14 +78,16 @@ def test_reference_arm_other_ranks_print_nothing(monkeypatch, capsys):
     assert capsys.readouterr().out == ""
 
 
-def test_oracle_sample_times_the_oracle_on_a_small_set():
+def test_oracle_baseline_times_whole_solves_on_a_small_set():
     sys.path.insert(0, ROOT)
     import bench
 
-    res = bench.oracle_sample(bench.workload(16), 16, count_n=16)
+    res = bench.oracle_baseline(bench.workload(16), 16)
     assert res["kind"] == "oracle" and res["cores"] >= 1 and res["unit"] == bench.UNIT
     assert res["value"] > 0 and abs(res["value"] * res["seconds_per_set"] - 1.0) < 1e-12
-    assert "V(2,2)" in res["sample"] and "16^3" in res["sample"]
+    assert res["sets"] == 1 and len(res["cycles"]) == 4 and min(res["cycles"]) >= 1
+    assert max(res["rel_resid"]) <= bench.TOL
+    assert "whole solve set" in res["sample"] and "16^3" in res["sample"]
 
 
 def _prof():

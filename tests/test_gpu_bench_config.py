@@ -1,0 +1,214 @@
+"""GPU parity of the configuration the benchmark times, and of the options
+it can choose.
+
+The benchmark solves one set (the Poisson problem with the dielectric slab
+and the streamer-shell charge, the three radiative-transfer problems with the
+smoothed source) at 512^3 through mg_solve_set with four problems in flight,
+CUDA-graph steps and the options mg_autotune installs (on GB300: V(2,1), three
+inner V-cycles per refinement step, 128-plane refinement tile).  Here the same
+set is solved with those options and with the autotuner's own choice, and
+every answer is checked by the FP64 oracle's residual (a property that holds
+at any size) and against the FP64-mode GPU answer of the same set.  Smaller
+cases sweep every settable refinement tile against the converged oracle,
+check the per-term amplitudes of the three-term radiative-transfer solve
+(Eq. 3) and the plain FP64 residual norms the benchmark reports.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_08857_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-10
+PARITY = 1e-9
+KAPPAS = (10.0, 100.0, 1000.0)
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_08857_gb300 import build, mg as _mg
+
+    build.build()
+    _mg.load()
+    return _mg
+
+
+@pytest.fixture(scope="module")
+def set512():
+    n = 512
+    return {"n": n, "rho": W.streamer_shell(n, 0), "eps": W.dielectric_slab(n),
+            "S": W.ionization_source(n, 0)}
+
+
+def solve_set(mg, inp, prec, options=None, tune_cache=None):
+    n = inp["n"]
+    dev = "cuda"
+    rho = torch.from_numpy(inp["rho"]).to(dev)
+    S = torch.from_numpy(inp["S"]).to(dev)
+    s = mg.Solver((n, n, n), 1.0 / n, eps_r=torch.from_numpy(inp["eps"]).to(dev), precision=prec,
+                  concurrency=4)
+    if options:
+        s.set_options(**options)
+    tuned = None
+    if tune_cache is not None:
+        from paper_1809_08857_gb300 import autotune
+
+        tuned, _ = autotune.tuned(s, rho, S, KAPPAS, TOL, has_eps=True, precision=prec,
+                                  cache_path=tune_cache)
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
+    psi = [torch.zeros_like(phi) for _ in KAPPAS]
+    st = s.solve_set(rho, phi, S, psi, KAPPAS, TOL)
+    norms = [s.residual_norms("poisson", rho, phi)]
+    norms += [s.residual_norms("helmholtz", S, p, k) for p, k in zip(psi, KAPPAS)]
+    s.close()
+    out = [phi.cpu().numpy()] + [p.cpu().numpy() for p in psi]
+    del phi, psi, rho, S
+    torch.cuda.empty_cache()
+    return out, st, norms, tuned
+
+
+def oracle_checks(inp, answers, norms):
+    """Each answer's relative residual by the oracle (FP64, its own operator
+    and lifts) is <= 1.01 tol, and the library's plain FP64 norms agree with
+    the oracle's."""
+    n = inp["n"]
+    h = 1.0 / n
+    probs = [(oracle.poisson((n, n, n), h, eps_r=inp["eps"]), inp["rho"] / oracle.EPS0)]
+    probs += [(oracle.helmholtz((n, n, n), h, k), inp["S"]) for k in KAPPAS]
+    rels = []
+    for (p, f), u, (rn_lib, bn_lib) in zip(probs, answers, norms):
+        _, rn = p.residual(f, u)
+        bn = p.rhs_norm(f, np.zeros_like(u))
+        rels.append(rn / bn)
+        assert rn / bn <= 1.01 * TOL, rels
+        assert bn_lib == pytest.approx(bn, rel=1e-12)
+        assert rn_lib == pytest.approx(rn, rel=1e-6, abs=1e-3 * TOL * bn)
+    return rels
+
+
+def test_bench_set_512_tuned_options(mg, set512):
+    """The set with the options the benchmark runs on GB300 (V(2,1), three
+    inner V-cycles, 128-plane refinement tile, four problems in flight,
+    graph steps): every answer meets 1e-10 by the oracle's FP64 residual and
+    agrees with the FP64-mode GPU answer to 1e-9."""
+    opts = {"nu1": 2, "nu2": 1, "inner_cycles": 3, "ir_zchunk": 128}
+    mixed, st, norms, _ = solve_set(mg, set512, mg.MG_PREC_MIXED, opts)
+    assert all(x["converged"] for x in st)
+    oracle_checks(set512, mixed, norms)
+    fp64, st64, norms64, _ = solve_set(mg, set512, mg.MG_PREC_FP64)
+    assert all(x["converged"] for x in st64)
+    for a, b in zip(mixed, fp64):
+        assert oracle.rel_l2(a, b) <= PARITY
+
+
+def test_bench_set_512_autotuned(mg, set512, tmp_path):
+    """The set with whatever mg_autotune installs from an empty cache (as
+    the benchmark does on a fresh machine): every answer meets 1e-10 by the
+    oracle's FP64 residual."""
+    mixed, st, norms, tuned = solve_set(mg, set512, mg.MG_PREC_MIXED,
+                                        tune_cache=str(tmp_path / "tune.json"))
+    assert tuned is not None and tuned["ir_zchunk"] in (0, 16, 32, 64, 128)
+    assert all(x["converged"] for x in st)
+    oracle_checks(set512, mixed, norms)
+
+
+@pytest.mark.parametrize("zchunk", [0, 16, 32, 64, 128])
+def test_refinement_tiles_match_oracle(mg, zchunk):
+    """Every settable tile of the refinement pass (z planes per CTA column;
+    0 = automatic) on a non-cubic box whose 200 planes leave a ragged last
+    chunk for each of them, with a dielectric slab, a shell charge, an
+    electrode block, and one Helmholtz problem: converged answers within 1e-9
+    of the oracle."""
+    shape = (200, 40, 48)  # (nz, ny, nx)
+    nz, ny, nx = shape
+    h = 1.0 / nz
+    rng = np.random.default_rng(11)
+    eps = np.where((np.arange(nz) + 0.5)[:, None, None] * h < 0.2, 4.0, 1.0) * np.ones(shape)
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[150:170, 12:22, 20:30] = 1
+    mval = np.where(mask, 1.0, 0.0)
+    rho = W.EPS0 * rng.standard_normal(shape) * 200
+    S = np.abs(rng.standard_normal(shape))
+    dev = "cuda"
+    s = mg.Solver(shape, h, eps_r=torch.from_numpy(eps).to(dev),
+                  mask=torch.from_numpy(mask).to(dev), mask_value=torch.from_numpy(mval).to(dev),
+                  bc_kind=W.GAP_BC_KIND, bc_value=W.GAP_BC_VALUE, precision=mg.MG_PREC_MIXED,
+                  max_cycles=400)
+    s.set_options(ir_zchunk=zchunk, nu1=2, nu2=1, inner_cycles=2)
+    phi = torch.zeros(shape, dtype=torch.float64, device=dev)
+    psi = torch.zeros_like(phi)
+    st = mg.solve_batch([{"solver": s, "kind": "poisson", "rhs": torch.from_numpy(rho).to(dev),
+                          "u": phi},
+                         {"solver": s, "kind": "helmholtz", "rhs": torch.from_numpy(S).to(dev),
+                          "u": psi, "kappa": 30.0}], TOL)
+    s.close()
+    assert all(x["converged"] for x in st)
+    P = oracle.Problem(shape, h, 0.0, eps, mask, W.GAP_BC_KIND, W.GAP_BC_VALUE)
+    ref, _, rel, _ = P.solve(rho / oracle.EPS0, u0=mval, max_cycles=2000)
+    assert rel < 1e-12
+    assert oracle.rel_l2(phi.cpu().numpy(), ref, mask) <= PARITY
+    refh, _, rel, _ = oracle.helmholtz(shape, h, 30.0, mask=mask).solve(S, max_cycles=2000)
+    assert rel < 1e-12
+    assert oracle.rel_l2(psi.cpu().numpy(), refh, mask) <= PARITY
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_photoionization_amplitudes(mg, prec):
+    """(kappa_j^2 - lap) Psi_j = A_j S with a different amplitude per term
+    (one of them negative), from a nonzero guess: each answer within 1e-9 of
+    the oracle's solution for the scaled source."""
+    n = 48
+    h = 1.0 / n
+    S = W.ionization_source(n, 4)
+    amp = (0.37, 1.0, -2.5)
+    kap = (15.0, 150.0, 40.0)
+    s = mg.Solver((n, n, n), h, precision=prec)
+    psi = [torch.full((n, n, n), 0.5, dtype=torch.float64, device="cuda") for _ in range(3)]
+    st = s.solve_photoionization(torch.from_numpy(S).cuda(), psi, kap, amp, TOL)
+    s.close()
+    for j in range(3):
+        got = psi[j].cpu().numpy()
+        assert st[j]["converged"]
+        ref, _, rel, _ = oracle.helmholtz((n, n, n), h, kap[j]).solve(S * amp[j])
+        assert rel < 1e-12
+        assert oracle.rel_l2(got, ref) <= PARITY, j
+
+
+def test_fp64_residual_norms_match_oracle(mg):
+    """mg_residual_norms (plain FP64) against the oracle's residual and ||b||
+    for the three problem kinds, with electrodes, a dielectric and the gap
+    faces, on a random iterate."""
+    shape = (24, 20, 28)
+    nz, ny, nx = shape
+    h = 1.0 / 28
+    rng = np.random.default_rng(12)
+    eps = rng.uniform(1.0, 4.0, shape)
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[10:14, 5:9, 8:12] = 1
+    mval = np.where(mask, 0.6, 0.0)
+    f = rng.standard_normal(shape)
+    u = rng.standard_normal(shape)
+    dev = "cuda"
+    s = mg.Solver(shape, h, eps_r=torch.from_numpy(eps).to(dev),
+                  mask=torch.from_numpy(mask).to(dev), mask_value=torch.from_numpy(mval).to(dev),
+                  bc_kind=W.GAP_BC_KIND, bc_value=W.GAP_BC_VALUE)
+    cases = [("poisson", 0.0, oracle.Problem(shape, h, 0.0, eps, mask, W.GAP_BC_KIND,
+                                             W.GAP_BC_VALUE), f * W.EPS0, f, np.where(mask, 0.6, u)),
+             ("screened", 7.5, oracle.Problem(shape, h, 7.5, eps, mask, W.GAP_BC_KIND,
+                                              W.GAP_BC_VALUE), f, f, np.where(mask, 0.6, u)),
+             ("helmholtz", 20.0, oracle.helmholtz(shape, h, 20.0, mask=mask), f, f,
+              np.where(mask, 0.0, u))]
+    for kind, param, P, rhs, fo, uu in cases:
+        rn, bn = s.residual_norms(kind, torch.from_numpy(rhs).to(dev),
+                                  torch.from_numpy(uu).to(dev), param)
+        _, rn_ref = P.residual(fo, uu)
+        bn_ref = P.rhs_norm(fo, np.where(mask, uu, 0.0))
+        assert rn == pytest.approx(rn_ref, rel=1e-12), kind
+        assert bn == pytest.approx(bn_ref, rel=1e-12), kind
+    s.close()
