@@ -61,6 +61,8 @@ def parse():
                          "0 = automatic")
     ap.add_argument("--no-amr", action="store_true",
                     help="skip the composite AMR solve among the extras")
+    ap.add_argument("--no-needle", action="store_true",
+                    help="skip the 896^3 needle-plane set among the extras")
     ap.add_argument("--no-fp64-leg", action="store_true",
                     help="skip the FP64-mode GPU solve set among the extras")
     return ap.parse_args()
@@ -410,6 +412,71 @@ def measure_fp64_gpu(rho, eps, S, n, dev, phi_mixed, psi_mixed, mixed_sets_per_s
             "rel_l2_mixed_vs_fp64": dist}
 
 
+def measure_needle_plane(dev, n=896, reps=2):
+    """The full-size needle-plane set (outside the timed region): 896^3 cells
+    (719 M), a needle electrode held at phi = 1 reaching a hyperboloid tip of
+    radius 5h at z = 0.8, the grounded plane z = 0, Neumann sides, charge on
+    the shells of three seeded branching channels leaving the tip; the Poisson
+    problem and the three Helmholtz problems (source |rho| / eps0, Psi = 0 on
+    the faces and the needle) in one mixed-precision mg_solve_set from zero
+    to 1e-10, after one untimed set (graphs, coarse inverses); device time
+    per set by CUDA events, and each answer's plain FP64 residual.  Skipped
+    when the device has less than 200 GB free."""
+    import torch
+
+    from paper_1809_08857_gb300 import mg, workloads as W
+
+    free, _ = torch.cuda.mem_get_info()
+    if free < 200e9:
+        return {"skipped": f"needs about 170 GB of free device memory, {free / 1e9:.0f} GB free"}
+    t_in = time.perf_counter()
+    mask = torch.from_numpy(W.needle_mask(n)).to(dev)
+    mv = mask.to(torch.float64)
+    idx, val = W.channel_shell_cells(n, 0)
+    rho = torch.zeros(n ** 3, dtype=torch.float64, device=dev)
+    rho[torch.from_numpy(idx).to(dev)] = torch.from_numpy(val).to(dev)
+    rho = rho.view(n, n, n)
+    S = rho.abs() / W.EPS0
+    t_in = time.perf_counter() - t_in
+    s = mg.Solver((n, n, n), 1.0 / n, mask=mask, mask_value=mv, bc_kind=W.GAP_BC_KIND,
+                  bc_value=W.GAP_BC_VALUE, precision=mg.MG_PREC_MIXED, max_cycles=400,
+                  inner_cycles=2)
+    del mv
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
+    psi = [torch.zeros_like(phi) for _ in KAPPAS]
+    st = None
+
+    def one():
+        nonlocal st
+        phi.zero_()
+        for p in psi:
+            p.zero_()
+        st = s.solve_set(rho, phi, S, psi, KAPPAS, TOL)
+
+    one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    res = fp64_residuals(s, rho, phi, S, psi)
+    used = torch.cuda.max_memory_allocated()
+    s.close()
+    del phi, psi, rho, S, mask
+    torch.cuda.empty_cache()
+    return {"workload": f"needle-plane set, {n}^3 ({n ** 3 / 1e6:.0f} M cells): Poisson (needle at "
+                        "phi = 1, three branching charged channels) + 3 Helmholtz, mixed, "
+                        "2 inner V-cycles per refinement step",
+            "ms": round(ms, 1), "sets_per_s": round(1e3 / ms, 3),
+            "steps": [x["cycles"] for x in st], "rel_resid_fp64": res,
+            "input_build_s": round(t_in, 1),
+            "torch_peak_gb": round(used / 1e9, 1),
+            "warm_start": "not used: a cold solve has no previous potential to start from"}
+
+
 def measure_unet(dev, n=256, reps=5):
     """One warm-start U-Net forward pass (mg_unet_predict) on a 256^3 volume
     (outside the timed region): device time per pass (CUDA events) and the
@@ -734,11 +801,15 @@ def run_ours(args):
             "rel_resid_fp64": fp64_check,
             "roofline": roofline(prof_serial, prof_overlap, n), "kernel_profile": prof_serial,
             "extras": extras}
+    solver.close()
+    del solver
+    torch.cuda.empty_cache()
+    if not args.no_needle:
+        extras["needle_plane_896"] = measure_needle_plane(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_baseline(inputs, n)
         line["cpu_baseline"] = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
     emit(line, rank)
-    solver.close()
     if world > 1:
         import torch.distributed as dist
 
