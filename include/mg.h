@@ -88,6 +88,19 @@ typedef enum { MG_PREC_FP64 = 0, MG_PREC_MIXED = 1 } mg_precision;
  *                        the normal derivative (u_g - u_c)/h. */
 typedef enum { MG_RTE_BC_DIRICHLET = 0, MG_RTE_BC_MARSHAK = 1 } mg_rte_bc;
 
+/* Coarse-grid operator of a variable-coefficient (eps_r) context.  The paper
+ * names geometric multigrid (Sec. 2 item (ii)) without its coarse operators;
+ * they shape the convergence rate, not the converged answer.
+ *   MG_COARSE_FACE  each coarse face weight is built from the finer level's
+ *                   face weights: on each of the 4 fine lines crossing the
+ *                   coarse face, the 3 fine faces between the two coarse
+ *                   centres in series (weights 1/4, 1/2, 1/4), the lines in
+ *                   parallel (their mean); faces towards coarse electrode
+ *                   cells and domain faces as MG_COARSE_CELL.
+ *   MG_COARSE_CELL  a coarse cell's eps_r is the mean of its free children and
+ *                   faces take the harmonic mean, as on the finest level. */
+typedef enum { MG_COARSE_FACE = 0, MG_COARSE_CELL = 1 } mg_coarse_op;
+
 /* Solver options.  Zero-initialised fields take the defaults shown. */
 typedef struct {
   int nu1;          /* pre-smoothing red-black sweeps per level, >= 1 (0: default 2) */
@@ -108,6 +121,8 @@ typedef struct {
                        marched by one CTA column, 0 (automatic: enough CTAs
                        for 8 waves of three per SM) or >= 16; mg_autotune
                        picks it among {auto, 16, 32, 64, 128} (0) */
+  int coarse_op;    /* mg_coarse_op of a context with eps_r (MG_COARSE_FACE =
+                       0); fixed at mg_create */
 } mg_options;
 
 /* Per-solve statistics.  hist[c] is the relative residual after c cycles

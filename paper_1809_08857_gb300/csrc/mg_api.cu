@@ -35,8 +35,8 @@
 namespace {
 
 constexpr double kEps0 = 8.8541878128e-12;  // F/m (CODATA 2018)
-constexpr int kDenseMax = 4096;
-constexpr int kIrZchunkMin = 16;             // smallest tile of the refinement pass             // largest coarsest grid inverted densely
+constexpr int kDenseMax = 4096;              // largest coarsest grid inverted densely
+constexpr int kIrZchunkMin = 16;             // smallest tile of the refinement pass
 constexpr int kMaxWork = 4;                 // concurrent problems per context
 constexpr int kMaxGraphs = 8;               // cached step graphs per work slot
 
@@ -87,6 +87,12 @@ struct Level {
   float* bh[2] = {nullptr, nullptr};
   // FP64-mode correction arrays (levels >= 1) and coarsest residual
   double *u64 = nullptr, *f64 = nullptr, *r64 = nullptr;
+  // levels >= 1 of a variable-coefficient context with the face-rule coarse
+  // operator: FP32 split copies of the face weights (-x, -y, -z) and diagonal
+  float* fx[2] = {nullptr, nullptr};
+  float* fy[2] = {nullptr, nullptr};
+  float* fz[2] = {nullptr, nullptr};
+  float* dg[2] = {nullptr, nullptr};
 };
 
 struct Coarse {
@@ -307,6 +313,13 @@ mg::Split32 sop(const mg_ctx* c, int l, Kind kind, double alpha) {
   op.beta[0] = beta[0];
   op.beta[1] = beta[1];
   for (int f = 0; f < 6; ++f) op.rho[f] = (float)face_rho(c, kind, alpha, f, L.h);
+  if (kind == kPoisson && L.dg[0])
+    for (int col = 0; col < 2; ++col) {
+      op.fx[col] = L.fx[col];
+      op.fy[col] = L.fy[col];
+      op.fz[col] = L.fz[col];
+      op.dg[col] = L.dg[col];
+    }
   return op;
 }
 
@@ -430,13 +443,17 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
   mg::Split32 op = sop(c, l, kind, alpha);
   const float a32 = (float)alpha;
   const double n = (double)L.b.n();
-  const double fb = op.beta[0] ? 4.0 : 0.0;
+  // coefficient bytes per cell of a half-sweep: the cell coefficient of both
+  // colours, or (face rule) own diagonal and three faces, the other colour's
+  // three faces
+  const double fb = op.dg[0] ? 14.0 : (op.beta[0] ? 4.0 : 0.0);
   if (l == Lc) {
     const double* Minv;
     MG_TRY(coarse_inverse(c, kind, alpha, &Minv));
     {
       Scope sc(c, s, MG_KCLASS_COARSE, 0);
-      mg::launch_resid32s(op, a32, cp(X.f32), cp(X.u32), mp(X.r32), s);
+      if (op.dg[0]) mg::launch_resid32f(op, a32, cp(X.f32), cp(X.u32), mp(X.r32), s);
+      else mg::launch_resid32s(op, a32, cp(X.f32), cp(X.u32), mp(X.r32), s);
     }
     {
       Scope sc(c, s, MG_KCLASS_COARSE, 0);
@@ -451,8 +468,12 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
         const bool zo = zero && q == 0 && col == 0;
         // other colour (unless known zero) + own rhs + own write + coefficients
         Scope sc(c, s, cls_s, n * ((zo ? 0.0 : 2.0) + 2.0 + 2.0 + fb));
-        mg::launch_half_sweep32(op, a32, col, X.f32[col], X.u32[col], X.u32[col ^ 1], zo,
-                                L.mask != nullptr, s);
+        if (op.dg[0])
+          mg::launch_half_sweep32f(op, a32, col, X.f32[col], X.u32[col], X.u32[col ^ 1], zo,
+                                   L.mask != nullptr, s);
+        else
+          mg::launch_half_sweep32(op, a32, col, X.f32[col], X.u32[col], X.u32[col ^ 1], zo,
+                                  L.mask != nullptr, s);
       }
   };
   smooth(c->opt.nu1, first_zero);
@@ -463,7 +484,10 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
     // cells carry a residual.  u both colours, f red, beta both colours,
     // coarse f and u
     Scope sc(c, s, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE, n * (4.0 + 2.0 + fb + 1.0));
-    mg::launch_resid_restrict32s(op, cop, a32, cp(X.f32), cp(X.u32), mp(Y.f32), mp(Y.u32), s);
+    if (op.dg[0])
+      mg::launch_resid_restrict32f(op, cop, a32, cp(X.f32), cp(X.u32), mp(Y.f32), mp(Y.u32), s);
+    else
+      mg::launch_resid_restrict32s(op, cop, a32, cp(X.f32), cp(X.u32), mp(Y.f32), mp(Y.u32), s);
   }
   MG_TRY(vcycle32(c, w, kind, alpha, l + 1, true));
   {
@@ -471,7 +495,15 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
     // black cells take the correction.  Fine black u read + write, coarse
     // e, black beta for the electrode test
     Scope sc(c, s, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE, n * (4.0 + 0.5 + fb / 2));
-    mg::launch_prolong32s(op, cop, cp(Y.u32), mp(X.u32), s);
+    // the prolongation reads the fine level's cell coefficient only for its
+    // sign (electrode cells stay untouched); on a face-rule level the
+    // diagonal carries that sign
+    mg::Split32 pop = op;
+    if (op.dg[0]) {
+      pop.beta[0] = op.dg[0];
+      pop.beta[1] = op.dg[1];
+    }
+    mg::launch_prolong32s(pop, cop, cp(Y.u32), mp(X.u32), s);
   }
   smooth(c->opt.nu2, false);
   return check_launch();
@@ -524,16 +556,16 @@ mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha
   a.partial = w->partial;
   a.partial_z = io.znorm ? w->partial + c->npartial : nullptr;
   a.zchunk = c->opt.ir_zchunk;
-  const int nparts = mg::ir_partials(L0.b, c->opt.ir_zchunk);
   const double n = (double)L0.b.n();
   // u and b read, face arrays (or the electrode mask), e, u + e and b
   // written back, r
   const double bytes = n * (8.0 + 8.0 + (a.op.cxd ? 32.0 : (a.op.mask ? 1.0 : 0.0)) +
                             (io.with_e ? 4.0 : 0.0) + (io.udf_out ? 8.0 : 0.0) +
                             (io.bdf_out ? 8.0 : 0.0) + (io.store_r ? 4.0 : 0.0));
+  int nparts;
   {
     Scope sc(c, s, MG_KCLASS_RESID64, bytes);
-    mg::launch_ir_fused(a, s);
+    nparts = mg::launch_ir_fused(a, s);
   }
   {
     Scope sc(c, s, MG_KCLASS_COARSE, 0);
@@ -1034,11 +1066,27 @@ mg_status build(mg_ctx* c, const double* eps_r, const uint8_t* mask, const doubl
     for (int l = 1; l < nlev; ++l)
       mg::launch_coarsen(c->lv[l - 1].beta64, c->lv[l - 1].mask, c->lv[l - 1].b, c->lv[l].beta64,
                          c->lv[l].mask, s);
+  const bool face_rule = eps_r && c->opt.coarse_op == MG_COARSE_FACE;
   for (int l = 0; l < nlev; ++l) {
     Level& L = c->lv[l];
     double rho[6];
     for (int f = 0; f < 6; ++f) rho[f] = face_rho(c, kPoisson, 0.0, f, L.h);
-    if (eps_r) mg::launch_faces64(L.beta64, L.mask, L.b, L.ih2, rho, L.cx, L.cy, L.cz, L.D, s);
+    if (eps_r && face_rule && l > 0) {
+      // coarse operator from the finer level's face weights (levels in order)
+      const Level& F = c->lv[l - 1];
+      mg::launch_coarsen_faces64(F.cx, F.cy, F.cz, F.b, L.beta64, L.mask, L.b, L.ih2, rho, L.cx,
+                                 L.cy, L.cz, L.D, s);
+      for (int col = 0; col < 2; ++col) {
+        MG_TRY(c->alloc(&L.fx[col], (size_t)L.ns, true));
+        MG_TRY(c->alloc(&L.fy[col], (size_t)L.ns, true));
+        MG_TRY(c->alloc(&L.fz[col], (size_t)L.ns, true));
+        MG_TRY(c->alloc(&L.dg[col], (size_t)L.ns, true));
+      }
+      mg::launch_split_faces(L.cx, L.cy, L.cz, L.D, L.b, L.W, mp(L.fx), mp(L.fy), mp(L.fz),
+                             mp(L.dg), s);
+    } else if (eps_r) {
+      mg::launch_faces64(L.beta64, L.mask, L.b, L.ih2, rho, L.cx, L.cy, L.cz, L.D, s);
+    }
     if (eps_r && l == 0) {
       const double* src[4] = {L.cx, L.cy, L.cz, L.D};
       float2* dst[4] = {L.cxd, L.cyd, L.czd, L.Dd};
@@ -1072,6 +1120,8 @@ mg_status normalise_options(const mg_options* in, mg_options* out) {
     return fail(MG_ERR_INVALID_ARG, "rte_bc must be MG_RTE_BC_DIRICHLET or MG_RTE_BC_MARSHAK");
   if (in->ir_zchunk != 0 && in->ir_zchunk < kIrZchunkMin)
     return fail(MG_ERR_INVALID_ARG, "ir_zchunk must be 0 (automatic) or >= 16");
+  if (in->coarse_op != MG_COARSE_FACE && in->coarse_op != MG_COARSE_CELL)
+    return fail(MG_ERR_INVALID_ARG, "coarse_op must be MG_COARSE_FACE or MG_COARSE_CELL");
   if (in->nu1) out->nu1 = in->nu1;
   if (in->nu2) out->nu2 = in->nu2;
   if (in->max_cycles) out->max_cycles = in->max_cycles;
@@ -1081,6 +1131,7 @@ mg_status normalise_options(const mg_options* in, mg_options* out) {
   out->no_graphs = in->no_graphs;
   out->rte_bc = in->rte_bc;
   out->ir_zchunk = in->ir_zchunk;
+  out->coarse_op = in->coarse_op;
   return MG_OK;
 }
 
@@ -1876,6 +1927,8 @@ mg_status mg_set_options(mg_ctx* c, const mg_options* opt) {
     return fail(MG_ERR_INVALID_ARG, "the precision mode is fixed at mg_create");
   if (o.rte_bc != c->opt.rte_bc)
     return fail(MG_ERR_INVALID_ARG, "rte_bc is fixed at mg_create");
+  if (o.coarse_op != c->opt.coarse_op)
+    return fail(MG_ERR_INVALID_ARG, "coarse_op is fixed at mg_create");
   c->opt = o;
   return MG_OK;
 }

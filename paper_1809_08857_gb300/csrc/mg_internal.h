@@ -81,6 +81,13 @@ struct Split32 {
   int W;
   float ih2;
   float rho[6];  // face factors as in Op64 (this level's h)
+  // Face-rule coarse levels (see mg_faces32.cu; dg[0] == nullptr otherwise):
+  // per colour, the weights (already / h^2) of the faces towards -x, -y, -z
+  // and the diagonal (sum of all six, < 0 on electrode cells).
+  const float* fx[2];
+  const float* fy[2];
+  const float* fz[2];
+  const float* dg[2];
 };
 
 struct Ptr2 {
@@ -132,6 +139,15 @@ void launch_faces64(const double* beta, const uint8_t* mask, Box b, double ih2,
                     cudaStream_t s);
 void launch_coarsen(const double* beta_f, const uint8_t* mask_f, Box fb, double* beta_c,
                     uint8_t* mask_c, cudaStream_t s);
+// Face weights and diagonal of coarse level cb (layout of launch_faces64) from
+// the fine level's face weights: between free coarse cells the mean over the 4
+// crossing fine lines of the (1/4, 1/2, 1/4) series of the 3 fine faces
+// between the coarse centres; towards a coarse electrode cell and on domain
+// faces the cell rule on the coarse coefficient beta_c and mask mask_c.
+void launch_coarsen_faces64(const double* fcx, const double* fcy, const double* fcz, Box fb,
+                            const double* beta_c, const uint8_t* mask_c, Box cb, double ih2c,
+                            const double rho[6], double* cx, double* cy, double* cz, double* D,
+                            cudaStream_t s);
 void launch_assemble_dense(Op64 op, double alpha, double* M, cudaStream_t s);
 void launch_gj_invert(double* M, int n, double* rowp, double* colp, cudaStream_t s);
 
@@ -196,6 +212,15 @@ void launch_dense_apply32s(const Split32& op, const double* Minv, Ptr2 r, MPtr2 
 void launch_split_beta(const double* beta, const uint8_t* mask, const Split32& op, MPtr2 out,
                        cudaStream_t s);
 
+// ---- face-rule coarse levels (mg_faces32.cu) ------------------------------
+void launch_half_sweep32f(const Split32& op, float alpha, int col, const float* f, float* u,
+                          const float* uo, bool zero_other, bool has_mask, cudaStream_t s);
+void launch_resid_restrict32f(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
+                              MPtr2 fc, MPtr2 uc, cudaStream_t s);
+void launch_resid32f(const Split32& op, float alpha, Ptr2 f, Ptr2 u, MPtr2 r, cudaStream_t s);
+void launch_split_faces(const double* cx, const double* cy, const double* cz, const double* D,
+                        Box b, int W, MPtr2 fx, MPtr2 fy, MPtr2 fz, MPtr2 dg, cudaStream_t s);
+
 // ---- electric field and relaxation time (mg_efield.cu) --------------------
 // E = -grad phi at cell centres (3 arrays of n, nullable) and, with J (3
 // arrays of n) and dt_out (device double), min over free cells of
@@ -208,13 +233,14 @@ void launch_efield(const double* phi, const uint8_t* mask, Box b, double h, cons
 // ---- fused refinement step (mg_ir.cu) --------------------------------------
 // One pass: (u + e), r = b - A u, r -> FP32, per-CTA sums of r^2 (and of the
 // squared residual of the zero guess when a.partial_z is set).
-void launch_ir_fused(const IrArgs& a, cudaStream_t s);
+// Returns the thread blocks launched (= per-block partial sums written).
+int launch_ir_fused(const IrArgs& a, cudaStream_t s);
 // out = hi + lo in FP64 (the final iterate of a mixed-precision solve);
 // electrode cells (mask nonzero, nullable) are left as they are
 void launch_df_to_f64(const float2* in, const uint8_t* mask, double* out, long long n,
                       cudaStream_t s);
-// CTAs (= partial sums) of the refinement pass for z planes per CTA column
-// zchunk (0: automatic).
+// Most CTAs (= partial sums) the refinement pass can launch for z planes
+// per CTA column zchunk (0: automatic), over its one- and two-cell kernels.
 int ir_partials(const Box& b, int zchunk = 0);
 
 // ---- composite AMR hierarchy (mg_amr.cu) ----------------------------------

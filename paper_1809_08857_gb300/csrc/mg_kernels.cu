@@ -102,6 +102,69 @@ __global__ void k_faces64(const double* beta, const uint8_t* mask, Box b, double
             : wxm * ih2 + wxp * ih2 + wym * ih2 + wyp * ih2 + wzm * ih2 + wzp * ih2;
 }
 
+// ---- face-based coarse operator ------------------------------------------
+//
+// Weight of the coarse face between C - e_a and C along axis a (C_a >= 1),
+// from the fine level's face weights w (cx, cy or cz: w[c] is the face between
+// c and c - e_a, already divided by h_f^2): on each of the 4 fine lines that
+// cross the coarse face (the transverse children), the path between the two
+// coarse centres passes half of fine cell 2C_a - 1, the fine face 2C_a and
+// half of fine cell 2C_a, i.e. the fine faces 2C_a - 1, 2C_a, 2C_a + 1 in
+// series with weights 1/4, 1/2, 1/4 (a zero weight, a face between two
+// electrode cells, blocks the line); the lines conduct in parallel (their
+// mean); the factor 1/4 takes 1/h_f^2 to 1/h_c^2.  For a coefficient that
+// is constant on the 4 x 3 cells involved this is the fine rule itself.
+__device__ double coarse_face_series(const double* __restrict__ w, const Box& fb, int axis,
+                                     int I, int J, int K) {
+  double sum = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    int i = 2 * I, j = 2 * J, k = 2 * K;
+    long long st;
+    if (axis == 0) { j += q & 1; k += q >> 1; st = 1; }
+    else if (axis == 1) { i += q & 1; k += q >> 1; st = fb.nx; }
+    else { i += q & 1; j += q >> 1; st = (long long)fb.nx * fb.ny; }
+    const long long c = cidx(fb, i, j, k);  // fine cell 2C_a on this line
+    const double w1 = w[c - st], w2 = w[c], w3 = w[c + st];
+    if (w1 > 0.0 && w2 > 0.0 && w3 > 0.0) sum += 1.0 / (0.25 / w1 + 0.5 / w2 + 0.25 / w3);
+  }
+  return 0.25 * 0.25 * sum;
+}
+
+// Coarse face weights and diagonal (the layout of k_faces64) by the face rule
+// above between free coarse cells; a face towards a coarse electrode cell and
+// a domain face follow the cell rule of k_faces64 on the coarse cell
+// coefficient bc (the mean of the free children, k_coarsen) and mask mc.
+__global__ void k_coarsen_faces64(const double* __restrict__ fcx, const double* __restrict__ fcy,
+                                  const double* __restrict__ fcz, Box fb,
+                                  const double* __restrict__ bc, const uint8_t* __restrict__ mc,
+                                  Box cb, double ih2c, Val6 rho, double* cx, double* cy,
+                                  double* cz, double* D) {
+  const long long C = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= cb.n()) return;
+  const int I = (int)(C % cb.nx);
+  const long long JK = C / cb.nx;
+  const int J = (int)(JK % cb.ny), K = (int)(JK / cb.ny);
+  const long long sy = cb.nx, sz = (long long)cb.nx * cb.ny;
+  const bool m = mc && mc[C];
+  const double wb = m ? 0.0 : 2.0 * (bc ? bc[C] : 1.0);
+  // face towards the in-box coarse neighbour N, whose face with C is face
+  // (axis, A) in the numbering of coarse_face_series
+  auto face = [&](long long N, int axis, int A, int B, int Cc) {
+    if (m || (mc && mc[N])) return face_w(bc, mc, C, N) * ih2c;
+    return coarse_face_series(axis == 0 ? fcx : (axis == 1 ? fcy : fcz), fb, axis, A, B, Cc);
+  };
+  const double wxm = I > 0 ? face(C - 1, 0, I, J, K) : wb * rho.v[0] * ih2c;
+  const double wxp = I < cb.nx - 1 ? face(C + 1, 0, I + 1, J, K) : wb * rho.v[1] * ih2c;
+  const double wym = J > 0 ? face(C - sy, 1, I, J, K) : wb * rho.v[2] * ih2c;
+  const double wyp = J < cb.ny - 1 ? face(C + sy, 1, I, J + 1, K) : wb * rho.v[3] * ih2c;
+  const double wzm = K > 0 ? face(C - sz, 2, I, J, K) : wb * rho.v[4] * ih2c;
+  const double wzp = K < cb.nz - 1 ? face(C + sz, 2, I, J, K + 1) : wb * rho.v[5] * ih2c;
+  cx[C] = wxm;
+  cy[C] = wym;
+  cz[C] = wzm;
+  D[C] = m ? -1.0 : wxm + wxp + wym + wyp + wzm + wzp;
+}
+
 __global__ void k_split_df(const double* __restrict__ in, float2* __restrict__ out, long long n) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
@@ -454,6 +517,17 @@ void launch_faces64(const double* beta, const uint8_t* mask, Box b, double ih2,
   Val6 r;
   for (int f = 0; f < 6; ++f) r.v[f] = rho[f];
   k_faces64<<<blocks_for(b.n()), kThreads, 0, s>>>(beta, mask, b, ih2, r, cx, cy, cz, D);
+  add_launches(1);
+}
+
+void launch_coarsen_faces64(const double* fcx, const double* fcy, const double* fcz, Box fb,
+                            const double* beta_c, const uint8_t* mask_c, Box cb, double ih2c,
+                            const double rho[6], double* cx, double* cy, double* cz, double* D,
+                            cudaStream_t s) {
+  Val6 r;
+  for (int f = 0; f < 6; ++f) r.v[f] = rho[f];
+  k_coarsen_faces64<<<blocks_for(cb.n()), kThreads, 0, s>>>(fcx, fcy, fcz, fb, beta_c, mask_c, cb,
+                                                             ih2c, r, cx, cy, cz, D);
   add_launches(1);
 }
 

@@ -27,6 +27,8 @@ MG_PREC_FP64 = 0
 MG_PREC_MIXED = 1
 MG_RTE_BC_DIRICHLET = 0
 MG_RTE_BC_MARSHAK = 1
+MG_COARSE_FACE = 0
+MG_COARSE_CELL = 1
 
 EXPORTS = [
     "mg_default_options", "mg_create", "mg_solve_poisson", "mg_solve_helmholtz_batch",
@@ -65,7 +67,8 @@ class Options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("concurrency", ctypes.c_int), ("no_graphs", ctypes.c_int),
-                ("rte_bc", ctypes.c_int), ("ir_zchunk", ctypes.c_int)]
+                ("rte_bc", ctypes.c_int), ("ir_zchunk", ctypes.c_int),
+                ("coarse_op", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -324,7 +327,8 @@ class Solver:
     def __init__(self, shape, h, eps_r=None, mask=None, mask_value=None,
                  bc_kind=(1, 1, 1, 1, 0, 0), bc_value=(0, 0, 0, 0, 0, 1),
                  precision=MG_PREC_FP64, nu1=2, nu2=2, max_cycles=100, inner_cycles=1,
-                 concurrency=4, graphs=True, stream=None, rte_bc=MG_RTE_BC_DIRICHLET):
+                 concurrency=4, graphs=True, stream=None, rte_bc=MG_RTE_BC_DIRICHLET,
+                 coarse_op=None):
         lib = load()
         nz, ny, nx = (int(s) for s in shape)
         self.shape = (nz, ny, nx)
@@ -332,7 +336,8 @@ class Solver:
         bc = BC((ctypes.c_int * 6)(*[int(k) for k in bc_kind]),
                 (ctypes.c_double * 6)(*[float(v) for v in bc_value]))
         opt = Options(nu1, nu2, max_cycles, precision, inner_cycles, concurrency,
-                      0 if graphs else 1, rte_bc)
+                      0 if graphs else 1, rte_bc, 0,
+                      MG_COARSE_FACE if coarse_op is None else coarse_op)
         for t in (eps_r, mask, mask_value):
             if t is not None and tuple(t.shape) != self.shape:
                 raise ValueError("coefficient shape mismatch")

@@ -64,10 +64,13 @@ def blobs(shape, seed):
 
 def one_cycle_gpu(mg, prec, shape, h, nu, rho=None, eps=None, mask=None, mask_value=None,
                   kappa=None, S=None, bc_kind=W.GAP_BC_KIND, bc_value=W.GAP_BC_VALUE,
-                  alpha=None, rte_bc=0):
+                  alpha=None, rte_bc=0, coarse_op=1):
+    """One cycle on the GPU.  coarse_op defaults to the cell rule
+    (MG_COARSE_CELL), the oracle's coarse operator, so that the cycle can be
+    compared with the oracle's."""
     s = mg.Solver(shape, h, eps_r=cuda(eps), mask=cuda(mask), mask_value=cuda(mask_value),
                   bc_kind=bc_kind, bc_value=bc_value, precision=prec, nu1=nu[0], nu2=nu[1],
-                  max_cycles=1, inner_cycles=1, rte_bc=rte_bc)
+                  max_cycles=1, inner_cycles=1, rte_bc=rte_bc, coarse_op=coarse_op)
     try:
         if alpha is not None:
             u = torch.zeros(shape, dtype=torch.float64, device="cuda")
@@ -186,3 +189,90 @@ def test_one_cycle_marshak(mg, prec, nu):
     got = one_cycle_gpu(mg, prec, shape, h, nu, kappa=kap, S=S, rte_bc=1)
     for g, k in zip(got, kap):
         check(g, one_cycle_oracle(oracle.helmholtz(shape, h, k, marshak=True), S, nu), prec)
+
+
+# ---- the face-rule coarse operator (MG_COARSE_FACE, the default) ----------
+#
+# Its coarse faces are built from the finer level's face weights (series along
+# the face normal, parallel across), which the oracle's cycle does not use.
+# Where the coefficient is constant the rule gives the oracle's coarse
+# operator, so one cycle equals the oracle's; elsewhere the FP32 face kernels
+# (mg_faces32.cu) are checked against the FP64 natural-layout kernels, which
+# read the same FP64 face weights, and the converged answers against the
+# oracle (the parity tests, which run with the default rule).
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nu", [(2, 2), (2, 1)])
+def test_face_rule_constant_coefficient_equals_oracle_cycle(mg, prec, nu):
+    """eps_r = 2.5 everywhere, gap faces: the face rule's coarse faces are the
+    cell rule's, so one cycle matches the oracle's."""
+    shape = (40, 48, 32)
+    h = 1.0 / 48
+    rho = blobs(shape, 13)
+    eps = np.full(shape, 2.5)
+    got = one_cycle_gpu(mg, prec, shape, h, nu, rho=rho, eps=eps, coarse_op=0)
+    p = oracle.Problem(shape, h, 0.0, eps, None, W.GAP_BC_KIND, W.GAP_BC_VALUE)
+    check(got, one_cycle_oracle(p, rho / oracle.EPS0, nu), prec)
+
+
+@pytest.mark.parametrize("case", ["slab", "electrode", "odd", "screened"])
+def test_face_rule_fp32_cycle_matches_fp64_cycle(mg, case):
+    """One mixed-precision cycle (FP32 split face kernels on the coarse
+    levels) against one FP64 cycle (natural-layout FP64 kernels on the same
+    face-rule operators), within FP32 rounding: a slab not aligned with the
+    coarse cells, a needle electrode with a dielectric, an odd coarse packed
+    width (40 x 48 x 32 -> 5 x 6 x 4) and the screened problem."""
+    nu = (2, 1)
+    kw = {}
+    if case == "slab":
+        shape, h = (40, 48, 32), 1.0 / 48
+        rho = blobs(shape, 14)
+        kw["eps"] = W.dielectric_slab_box(shape, h, (0.0, 0.0, 0.0), z_top=0.37)
+    elif case == "electrode":
+        n = 32
+        shape, h = (n, n, n), 1.0 / n
+        mask = W.needle_mask(n, tip_z=0.6, tip_radius_cells=3.0)
+        kw.update(eps=W.dielectric_slab(n, z_top=0.33), mask=mask,
+                  mask_value=mask.astype(np.float64))
+        rho = blobs(shape, 15)
+    elif case == "odd":
+        shape, h = (32, 48, 40), 1.0 / 48
+        rho = blobs(shape, 16)
+        kw["eps"] = W.dielectric_slab_box(shape, h, (0.0, 0.0, 0.0), z_top=0.29) * (
+            1.0 + np.random.default_rng(17).random(shape))
+        kw.update(bc_kind=(0, 1, 1, 0, 0, 0), bc_value=(0.2, 0.0, 0.0, -0.3, 0.0, 1.0))
+    else:
+        shape, h = (24, 32, 40), 1.0 / 40
+        rho = blobs(shape, 18) / W.EPS0
+        kw["eps"] = W.dielectric_slab_box(shape, h, (0.0, 0.0, 0.0), z_top=0.31) * (
+            1.0 + 0.5 * np.random.default_rng(19).random(shape))
+        kw["alpha"] = 400.0
+    u64 = one_cycle_gpu(mg, 0, shape, h, nu, rho=rho, coarse_op=0, **kw)
+    u32 = one_cycle_gpu(mg, 1, shape, h, nu, rho=rho, coarse_op=0, **kw)
+    mask = kw.get("mask")
+    assert oracle.rel_l2(u32, u64, mask) <= FP32_TOL
+    # and the face rule really differs from the cell rule here
+    ucell = one_cycle_gpu(mg, 0, shape, h, nu, rho=rho, coarse_op=1, **kw)
+    assert oracle.rel_l2(ucell, u64, mask) > 10 * FP32_TOL
+
+
+def test_face_rule_converges_faster_on_the_slab(mg):
+    """The reason for the face rule: on the dielectric slab (eps_r = 4 below
+    z = 0.2, an interface inside coarse cells from the second coarse level
+    on) FP64 V(2,1)-cycles from zero reach 1e-10 in fewer cycles than with the
+    cell rule, and both reach the same answer."""
+    n = 128
+    h = 1.0 / n
+    rho = W.streamer_shell(n, 0)
+    eps = W.dielectric_slab(n)
+    out, cyc = {}, {}
+    for rule in (0, 1):
+        s = mg.Solver((n, n, n), h, eps_r=cuda(eps), precision=0, nu1=2, nu2=1,
+                      coarse_op=rule)
+        u = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+        st = s.solve_poisson(cuda(rho), u, 1e-10)
+        s.close()
+        out[rule], cyc[rule] = u.cpu().numpy(), st["cycles"]
+    assert cyc[0] < cyc[1], cyc
+    assert oracle.rel_l2(out[0], out[1]) <= 1e-9
