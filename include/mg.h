@@ -123,6 +123,11 @@ typedef struct {
                        picks it among {auto, 16, 32, 64, 128} (0) */
   int coarse_op;    /* mg_coarse_op of a context with eps_r (MG_COARSE_FACE =
                        0); fixed at mg_create */
+  int fixed_cycles; /* mixed mode: 0 = from the second refinement step on, a
+                       step whose measured contraction per V-cycle (taken 15 %
+                       weaker) reaches tol in fewer than inner_cycles
+                       V-cycles runs only that many; 1 = every step runs
+                       inner_cycles (0) */
 } mg_options;
 
 /* Per-solve statistics.  hist[c] is the relative residual after c cycles
@@ -135,6 +140,9 @@ typedef struct {
                        FP32, across thread blocks in FP64 */
   double time_ms;   /* device time of the solve (CUDA events) */
   double hist[64];
+  int vcycles;      /* V-cycles run: FP64 mode = cycles; mixed mode = the inner
+                       V-cycles of all refinement steps; composite AMR solve =
+                       FAC iterations x inner V-cycles (per box) */
 } mg_stats;
 
 /* Fill *opt with the defaults. */
@@ -543,11 +551,13 @@ mg_status mg_residual_norms(mg_ctx* ctx, int kind, double param, const double* r
  * mg_warmstart_predict -- guess for the Poisson solve of rho from the
  * previous potential.  The network is applied to the residual of the
  * previous potential, r = b_n - A phi_prev = A (phi_n - phi_prev) (its first
- * input channel), and phi_prev (second channel); the guess is
- * phi_prev + U(r s_rho, phi_prev s_phi) / s_out, unless its FP64 residual
- * ||b - A phi|| is larger than that of phi_prev, in which case phi_prev is
- * used (plain multigrid judges the network).  *used_net (nullable) tells
- * which.  Synchronises the context's stream.
+ * input channel), and phi_prev (second channel), giving the candidate
+ * phi_prev + U(r s_rho, phi_prev s_phi) / s_out.  Plain multigrid judges it:
+ * the candidate and phi_prev each get nu1 FP64 red-black Gauss-Seidel sweeps
+ * (which remove the high-frequency part of the network's BF16 rounding), and
+ * the smoothed candidate is the guess unless its FP64 residual ||b - A phi||
+ * is larger than that of the smoothed phi_prev, which is then the guess.
+ * *used_net (nullable) tells which.  Synchronises the context's stream.
  */
 mg_status mg_warmstart_predict(mg_ctx* ctx, const double* rho, const double* phi_prev,
                                double* phi_guess, int* used_net);

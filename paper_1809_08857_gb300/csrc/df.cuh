@@ -89,6 +89,68 @@ __device__ __forceinline__ float2 df_add(float2 a, float b) {
   return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
 }
 
+// ---- paired forms: two cells at once ----------------------------------------
+//
+// The same error-free steps lane by lane on float2 values (lane x: cell A,
+// lane y: cell B) with the FP32x2 instructions of sm_100 and later (one
+// FADD2 / FMUL2 / FFMA2 does two correctly rounded FP32 operations), so two
+// cells cost the instructions of one.  a - b is formed as fma(b, -1, a): the
+// product is exact, so the single rounding gives the correctly rounded
+// difference.
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// A pair of double-floats: hi = (A.hi, B.hi), lo = (A.lo, B.lo).
+struct Df2 {
+  float2 hi, lo;
+};
+
+// Running sums s + e of the pair (DfAcc lane by lane).
+struct DfAcc2 {
+  float2 s, e;
+  // s + e += c * u, c and u pairs of double-floats
+  __device__ __forceinline__ void add(const Df2& c, const Df2& u) {
+    const float2 p = mul2(c.hi, u.hi);
+    float2 q = fma2(c.hi, u.hi, make_float2(-p.x, -p.y));
+    q = fma2(c.hi, u.lo, q);
+    q = fma2(c.lo, u.hi, q);
+    const float2 t = add2(s, p);
+    const float2 v = sub2(t, s);
+    const float2 err = add2(sub2(s, sub2(t, v)), sub2(p, v));
+    s = t;
+    e = add2(e, add2(err, q));
+  }
+  __device__ __forceinline__ float2 value() const { return add2(s, e); }
+};
+
+// a + b (pair of double-floats plus a pair of FP32), renormalised (df_add
+// lane by lane).
+__device__ __forceinline__ Df2 df_add2(const Df2& a, float2 b) {
+  const float2 s = add2(a.hi, b);
+  const float2 v = sub2(s, a.hi);
+  const float2 t = add2(sub2(a.hi, sub2(s, v)), sub2(b, v));
+  const float2 lo = add2(t, a.lo);
+  const float2 hi = add2(s, lo);
+  return Df2{hi, sub2(lo, sub2(hi, s))};
+}
+
+// a + b for a pair of double-floats plus one double-float b (the same b for
+// both cells), renormalised: two-sum of the leading parts, the low parts and
+// the two-sum error summed, then a fast two-sum.
+__device__ __forceinline__ Df2 df_add_df2(const Df2& a, float2 b) {
+  const float2 bh = make_float2(b.x, b.x), bl = make_float2(b.y, b.y);
+  const float2 s = add2(a.hi, bh);
+  const float2 v = sub2(s, a.hi);
+  const float2 t = add2(add2(sub2(a.hi, sub2(s, v)), sub2(bh, v)), add2(a.lo, bl));
+  const float2 hi = add2(s, t);
+  return Df2{hi, sub2(t, sub2(hi, s))};
+}
+
 }  // namespace df
 }  // namespace mg
 

@@ -527,6 +527,7 @@ struct IrIo {
   bool with_e = false;
   bool store_r = false;
   bool znorm = false;
+  double in_scale = 1.0;  // FP64 inputs (b64, u64) multiplied by this power of two on load
 };
 
 // Enqueue one fused refinement pass on level 0 and the read-back of ||r||^2
@@ -556,6 +557,7 @@ mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha
   a.partial = w->partial;
   a.partial_z = io.znorm ? w->partial + c->npartial : nullptr;
   a.zchunk = c->opt.ir_zchunk;
+  a.in_scale = io.in_scale;
   const double n = (double)L0.b.n();
   // u and b read, face arrays (or the electrode mask), e, u + e and b
   // written back, r
@@ -592,11 +594,36 @@ struct Prob {
   float2* other = nullptr;
   int cyc = 0;
   double bnorm = 1.0, rel = 0.0;
+  double rel_prev = 0.0;  // relative residual before the last step
+  int ic = 0;             // inner V-cycles of the next (last enqueued) step
+  int ic_last = 0;        // inner V-cycles of the step that just finished
+  int vcycles = 0;        // inner V-cycles of all finished steps
+  // mixed precision: the problem is solved for s u (s a power of two, 1
+  // unless b's magnitude is far from 1; see rescale)
+  double scale = 1.0;
   int phase = 0;
   bool done = false;
   mg_status status = MG_OK;
   const StepGraph* g = nullptr;
 };
+
+// Inner V-cycles of p's next refinement step: the context's inner_cycles,
+// or fewer when the contraction per V-cycle measured over the last step
+// (from the second step on) says that fewer reach tol.  The measured rate is
+// taken 15 % weaker in its logarithm, so that a step that varies a little
+// from the last one still lands below tol; if it does not, the step after it
+// runs the full count again.  The fixed point and the tolerance test are
+// unchanged: only the number of V-cycles in the last step can shrink.
+int next_inner_cycles(const Prob& p) {
+  const int full = p.c->opt.inner_cycles;
+  if (p.c->opt.fixed_cycles || p.cyc < 2 || p.ic_last < 1 || !(p.rel_prev > 0.0) ||
+      !(p.rel > 0.0) || !(p.rel < p.rel_prev))
+    return full;
+  const double per_cycle = std::log(p.rel / p.rel_prev) / p.ic_last;  // < 0
+  const double need = std::log(p.tol / p.rel) / (0.85 * per_cycle);
+  if (!(need > 0.0) || need >= full) return full;
+  return std::max(1, (int)std::ceil(need));
+}
 
 // kind Poisson with alpha = 0 is Eq. 2 (b = rho / eps0 + lifts); with
 // rhs_scale = 1 and any alpha >= 0 it is the screened variable-coefficient
@@ -660,7 +687,7 @@ mg_status prepare(Prob& p, cudaStream_t s) {
 // step u_out = u_in + e, r = b - A u_out, ||r||^2 -> host slot 1.
 mg_status enqueue_step_direct(Prob& p) {
   mg_ctx* c = p.c;
-  for (int q = 0; q < c->opt.inner_cycles; ++q)
+  for (int q = 0; q < p.ic; ++q)
     MG_TRY(vcycle32(c, p.w, p.kind, p.alpha, 0, q == 0));
   IrIo io;
   io.bdf = p.w->bdf;
@@ -675,7 +702,7 @@ mg_status enqueue_step_direct(Prob& p) {
 mg_status step_graph(Prob& p, const StepGraph** out) {
   mg_ctx* c = p.c;
   Work* w = p.w;
-  const int ic = c->opt.inner_cycles;
+  const int ic = p.ic;
   for (StepGraph& g : w->graphs)
     if (g.kind == p.kind && g.alpha == p.alpha && g.ic == ic && g.nu1 == c->opt.nu1 &&
         g.nu2 == c->opt.nu2 && g.zc == c->opt.ir_zchunk && g.prof == c->prof && g.b == w->bdf &&
@@ -761,7 +788,7 @@ mg_status finish(Prob& p) {
   // step the caller's guess stays as it was
   if (p.cyc > 0) {
     Scope sc(p.c, p.w->s, MG_KCLASS_COARSE, 0);
-    mg::launch_df_to_f64(p.cur, p.c->lv[0].mask, p.u, p.c->lv[0].b.n(), p.w->s);
+    mg::launch_df_to_f64(p.cur, p.c->lv[0].mask, p.u, p.c->lv[0].b.n(), 1.0 / p.scale, p.w->s);
   }
   if (p.st) MG_CUDA(cudaEventRecord(p.w->t1, p.w->s));
   p.done = true;
@@ -777,6 +804,59 @@ mg_status finish(Prob& p) {
   return MG_OK;
 }
 
+// The first pass of p: ||b|| (slot 0) and the residual of the guess (slot
+// 1) in one pass; b and the guess become double-floats (times p.scale) on
+// the way.
+mg_status enqueue_first(Prob& p) {
+  Work* w = p.w;
+  IrIo r0;
+  r0.b64 = p.b;
+  r0.bdf_out = w->bdf;
+  r0.u64 = p.u;
+  r0.udf_out = p.cur;
+  r0.store_r = true;
+  r0.znorm = true;
+  r0.in_scale = p.scale;
+  MG_TRY(enqueue_ir(p.c, w, w->s, p.kind, p.alpha, r0, 1));
+  MG_CUDA(cudaEventRecord(w->ev, w->s));
+  return MG_OK;
+}
+
+// Double-floats keep 48 bits only for magnitudes between about 2^-100
+// (below 2^-74 the low part is dropped) and the FP32 range: a problem whose
+// b is far below that (a radiative-transfer sub-box far from the source,
+// with Psi ~ 1e-20) would be solved to FP32 accuracy.  The relative residual
+// does not change when b and u are scaled together, so such a problem is
+// solved for s u with s = 2^k bringing the RMS of b near 1 (exact: a power of
+// two), and the answer divided by s at the end.  Returns the scale for an
+// RMS of b (1 inside [2^-30, 2^30]).
+double rescale(double bnorm, long long n) {
+  const double rms = bnorm / std::sqrt((double)std::max(1LL, n));
+  if (!(rms > 0.0) || !std::isfinite(rms) || (rms >= 0x1p-30 && rms <= 0x1p30)) return 1.0;
+  return std::ldexp(1.0, -std::ilogb(rms));
+}
+
+// ||b|| of p in plain FP64 (the zero guess's residual with the electrode
+// values kept, mg_residual_norms' kernel), on p's stream; synchronises it.
+// The first pass sums squares in FP32, which underflow for |b| below about
+// 1e-19, so a problem of that size shows ||b|| = 0 there.
+mg_status fp64_bnorm(Prob& p, double* out) {
+  mg_ctx* c = p.c;
+  Work* w = p.w;
+  const Level& L0 = c->lv[0];
+  const int nblk = mg::resid_norms_blocks(L0.b, c->npartial);
+  {
+    Scope sc(c, w->s, MG_KCLASS_COARSE, 0);
+    mg::launch_resid_norms64(op64(c, 0, p.kind, p.alpha), p.alpha, p.b, p.u, w->partial, nblk,
+                             w->s);
+    mg::launch_sum_partials(w->partial + nblk, nblk, w->norm_map, w->s);
+  }
+  MG_TRY(check_launch());
+  MG_CUDA(cudaStreamSynchronize(w->s));
+  *out = std::sqrt(w->norm_host[0]);
+  return MG_OK;
+}
+
 // Host side of one finished step of p.
 mg_status advance(Prob& p) {
   const double* h = p.w->norm_host;
@@ -787,15 +867,29 @@ mg_status advance(Prob& p) {
       p.rel = p.bnorm;
       return finish(p);
     }
+    const long long n = p.c->lv[0].b.n();
+    if (p.scale == 1.0 && (p.bnorm == 0.0 || rescale(p.bnorm, n) != 1.0)) {
+      double b64 = 0.0;
+      MG_TRY(fp64_bnorm(p, &b64));
+      const double sc = rescale(b64, n);
+      if (sc != 1.0) {  // the first pass again, on the scaled problem
+        p.scale = sc;
+        return enqueue_first(p);
+      }
+    }
     if (p.bnorm == 0.0) p.bnorm = 1.0;
     p.phase = 1;
   } else {
     std::swap(p.cur, p.other);
     ++p.cyc;
+    p.vcycles += p.ic;
   }
+  p.rel_prev = p.rel;
   p.rel = std::sqrt(h[1]) / p.bnorm;
   if (p.st && p.cyc < 64) p.st->hist[p.cyc] = p.rel;
   if (!std::isfinite(p.rel) || p.rel <= p.tol || p.cyc >= p.c->opt.max_cycles) return finish(p);
+  p.ic_last = p.ic;
+  p.ic = next_inner_cycles(p);
   return enqueue_step(p);
 }
 
@@ -832,18 +926,9 @@ mg_status solve_mixed(std::vector<Prob>& P) {
     MG_TRY(prepare(p, w->s));
     p.cur = w->udf[0];
     p.other = w->udf[1];
+    p.ic = p.c->opt.inner_cycles;
     // ||b|| (slot 0) and the residual of the initial guess (slot 1, r -> FP32)
-    // ||b|| (slot 0) and the residual of the guess (slot 1) in one pass;
-    // b and the guess become double-floats on the way
-    IrIo r0;
-    r0.b64 = p.b;
-    r0.bdf_out = w->bdf;
-    r0.u64 = p.u;
-    r0.udf_out = p.cur;
-    r0.store_r = true;
-    r0.znorm = true;
-    MG_TRY(enqueue_ir(p.c, w, w->s, p.kind, p.alpha, r0, 1));
-    MG_CUDA(cudaEventRecord(w->ev, w->s));
+    MG_TRY(enqueue_first(p));
   }
   size_t left = P.size();
   while (left) {
@@ -866,6 +951,7 @@ mg_status solve_mixed(std::vector<Prob>& P) {
       float ms = 0;
       MG_CUDA(cudaEventElapsedTime(&ms, p.w->t0, p.w->t1));
       p.st->cycles = p.cyc;
+      p.st->vcycles = p.vcycles;
       p.st->rel_resid = p.rel;
       p.st->converged = p.rel <= p.tol;
       p.st->time_ms = ms;
@@ -918,6 +1004,7 @@ mg_status solve_fp64(Prob& p) {
     float ms = 0;
     MG_CUDA(cudaEventElapsedTime(&ms, w->t0, w->t1));
     p.st->cycles = p.cyc;
+    p.st->vcycles = p.cyc;
     p.st->rel_resid = p.rel;
     p.st->converged = p.rel <= p.tol;
     p.st->time_ms = ms;
@@ -1132,6 +1219,9 @@ mg_status normalise_options(const mg_options* in, mg_options* out) {
   out->rte_bc = in->rte_bc;
   out->ir_zchunk = in->ir_zchunk;
   out->coarse_op = in->coarse_op;
+  if (in->fixed_cycles != 0 && in->fixed_cycles != 1)
+    return fail(MG_ERR_INVALID_ARG, "fixed_cycles must be 0 or 1");
+  out->fixed_cycles = in->fixed_cycles;
   return MG_OK;
 }
 
@@ -1709,6 +1799,7 @@ mg_status amr_solve(mg_amr* a, int kind_in, double param, const double* const* r
     float ms = 0.0f;
     MG_CUDA(cudaEventElapsedTime(&ms, a->t0, a->t1));
     st->cycles = cyc;
+    st->vcycles = cyc * a->opt.inner_cycles;  // per box of every level
     st->rel_resid = rel;
     st->converged = rel <= tol;
     st->time_ms = ms;
@@ -2130,18 +2221,30 @@ mg_status mg_warmstart_predict(mg_ctx* c, const double* rho, const double* phi_p
   double* r = p.w->phi_tmp;
   MG_TRY(poisson_residual(c, rho, phi_guess, r, &p));
   MG_TRY(mg_unet_predict(c->net, r, phi_guess, phi_guess, 1, b.nz, b.ny, b.nx, s));
-  // plain multigrid judges the guess: FP64 residual of both candidates
+  // plain multigrid judges the guess: both candidates get the same nu1 FP64
+  // red-black Gauss-Seidel sweeps (the network's BF16 noise is high-frequency
+  // and would otherwise dominate its residual), then their FP64 residuals
+  // are compared; the better smoothed candidate is the guess
+  double* prev_s = r;  // the network input is no longer needed
+  MG_CUDA(cudaMemcpyAsync(prev_s, phi_prev, sizeof(double) * b.n(), cudaMemcpyDeviceToDevice, s));
+  const mg::Op64 op = op64(c, 0, kPoisson, 0.0);
+  for (double* u : {phi_guess, prev_s})
+    for (int q = 0; q < c->opt.nu1; ++q)
+      for (int col = 0; col < 2; ++col) {
+        Scope sc(c, s, MG_KCLASS_COARSE, 0);
+        mg::launch_rbgs64(op, 0.0, p.b, u, col, s);
+      }
   IrIo io;
   io.b64 = p.b;
   io.u64 = phi_guess;
   MG_TRY(enqueue_ir(c, p.w, s, kPoisson, 0.0, io, 0));
-  io.u64 = phi_prev;
+  io.u64 = prev_s;
   MG_TRY(enqueue_ir(c, p.w, s, kPoisson, 0.0, io, 1));
   MG_CUDA(cudaStreamSynchronize(s));
   const double r_net = p.w->norm_host[0], r_prev = p.w->norm_host[1];
   const bool use = std::isfinite(r_net) && r_net <= r_prev;
   if (!use)
-    MG_CUDA(cudaMemcpyAsync(phi_guess, phi_prev, sizeof(double) * b.n(), cudaMemcpyDeviceToDevice, s));
+    MG_CUDA(cudaMemcpyAsync(phi_guess, prev_s, sizeof(double) * b.n(), cudaMemcpyDeviceToDevice, s));
   MG_CUDA(cudaStreamSynchronize(s));
   if (used_net) *used_net = use ? 1 : 0;
   return MG_OK;

@@ -123,10 +123,15 @@ struct IrArgs {
                        // the guess that is 0 on free cells (FP64 guess only)
   int zchunk;          // z planes per CTA column, 0: automatic (the launcher
                        // replaces it by the planes used)
+  double in_scale;     // FP64 inputs (u_in, rhs) times this power of two on
+                       // load (1: as they are)
   // set by the launcher: 1/h^2, -alpha and the interior beta = 1 diagonal
   // 6/h^2 + alpha as double-floats; alpha != 0
   float2 ih2d, nalpha, dint;
   int has_alpha;
+  // beta = 1: what a -z / +z domain face changes in the diagonal,
+  // (2 rho - 1) / h^2, as double-floats
+  float2 dzm, dzp;
 };
 
 // ---- setup ---------------------------------------------------------------
@@ -235,10 +240,11 @@ void launch_efield(const double* phi, const uint8_t* mask, Box b, double h, cons
 // squared residual of the zero guess when a.partial_z is set).
 // Returns the thread blocks launched (= per-block partial sums written).
 int launch_ir_fused(const IrArgs& a, cudaStream_t s);
-// out = hi + lo in FP64 (the final iterate of a mixed-precision solve);
-// electrode cells (mask nonzero, nullable) are left as they are
+// out = (hi + lo) * scale in FP64 (the final iterate of a mixed-precision
+// solve; scale a power of two); electrode cells (mask nonzero, nullable) are
+// left as they are
 void launch_df_to_f64(const float2* in, const uint8_t* mask, double* out, long long n,
-                      cudaStream_t s);
+                      double scale, cudaStream_t s);
 // Most CTAs (= partial sums) the refinement pass can launch for z planes
 // per CTA column zchunk (0: automatic), over its one- and two-cell kernels.
 int ir_partials(const Box& b, int zchunk = 0);

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(NT, Faces ? 2 : 3) k_ir_df(IrArgs a) {
     if (zmask) rm = a.op.mask[c] != 0;
     if (U64) {
       rd = a.u_in[c];
+      if (a.in_scale != 1.0) rd *= a.in_scale;
     } else {
       ru = a.udf_in[c];
       if (HasE) {
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(NT, Faces ? 2 : 3) k_ir_df(IrArgs a) {
       C.m = a.op.mask && a.op.mask[c];
     }
     if (BIn == 0) C.bb = a.bdf[c];
-    else C.bd = a.rhs[c];
+    else C.bd = a.in_scale != 1.0 ? a.rhs[c] * a.in_scale : a.rhs[c];
   };
 
   float2 um, uc, up;
@@ -273,21 +274,263 @@ __global__ void __launch_bounds__(NT, Faces ? 2 : 3) k_ir_df(IrArgs a) {
   }
 }
 
+// The same pass for the constant-coefficient operator (beta = 1) with two
+// x-adjacent cells per thread, the pair (i0, i0 + 1) with i0 even (cell A,
+// cell B): every double-float operation of the pair is one FP32x2
+// instruction (DfAcc2, df_add2), the x-neighbours of the pair are two
+// shuffles (B of the previous lane, A of the next), a thread's plane entry in
+// shared memory is one 16-byte word.  Needs nx even and 16-byte aligned
+// arrays (the launcher checks and otherwise runs k_ir_df).  A CTA of 32 x 16
+// threads covers 64 x 16 columns, of which the inner 60 x 14 are its own.
+// Template arguments as for k_ir_df (no Faces).
+template <bool HasE, bool U64, int BIn, bool ZNorm>
+__global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
+  __shared__ float4 pl[2][TY][TX];
+  __shared__ uchar2 mk[ZNorm ? 2 : 1][ZNorm ? TY : 1][TX];  // electrode flags of A, B
+  __shared__ float red[2][NT / 32];
+  const unsigned FULL = 0xffffffffu;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int nx = a.op.b.nx, ny = a.op.b.ny, nz = a.op.b.nz;
+  const int i0 = 2 * (blockIdx.x * (TX - 2) - 1 + tx), j = blockIdx.y * (TY - 2) - 1 + ty;
+  const int z0 = blockIdx.z * a.zchunk, z1 = min(nz, z0 + a.zchunk);
+  const int W = a.W;
+  const long long sz = (long long)nx * ny, szW = (long long)W * ny;
+  const bool in = i0 >= 0 && i0 < nx && j >= 0 && j < ny;  // nx even: i0 + 1 < nx as well
+  const bool own = in && tx >= 1 && tx <= TX - 2 && ty >= 1 && ty <= TY - 2;
+  const int off = in ? j * nx + i0 : 0;  // in-plane offset of cell A
+  const int eoff = in ? j * W + (i0 >> 1) : 0;  // packed index of A and of B
+  const int par0 = (i0 + j) & 1;                // colour of A at k = 0; B has the other
+  const bool zmask = ZNorm && a.op.mask != nullptr;
+  const bool xmA = i0 > 0, xpB = i0 + 2 < nx, ym = j > 0, yp = j < ny - 1;
+  const float2 zero2 = make_float2(0.0f, 0.0f);
+  // beta = 1: the diagonal of each cell of the pair on an interior plane,
+  // 4/h^2 for its in-plane in-box faces plus 2 rho/h^2 for its domain faces
+  // (A's +x neighbour and B's -x neighbour are each other) plus 2/h^2 + alpha,
+  // formed once in FP64 here; the planes k = 0 and nz - 1 add the double-float
+  // correction (2 rho - 1)/h^2 of their z face in the loop (FP32 only)
+  Df2 dxy;
+  if (xmA && xpB && ym && yp) {
+    dxy = Df2{make_float2(a.dint.x, a.dint.x), make_float2(a.dint.y, a.dint.y)};
+  } else {
+    const double dy = (ym ? 1.0 : 2.0 * a.op.rho[2]) + (yp ? 1.0 : 2.0 * a.op.rho[3]);
+    const double dA = (xmA ? 1.0 : 2.0 * a.op.rho[0]) + 1.0 + dy + 2.0;
+    const double dB = 1.0 + (xpB ? 1.0 : 2.0 * a.op.rho[1]) + dy + 2.0;
+    const float2 sA = split_df(fma(dA, a.op.ih2, a.alpha));
+    const float2 sB = split_df(fma(dB, a.op.ih2, a.alpha));
+    dxy = Df2{make_float2(sA.x, sB.x), make_float2(sA.y, sB.y)};
+  }
+
+  // ---- the column pair: raw loads of a plane (fetch) and u + e (combine)
+  double2 rd = make_double2(0.0, 0.0);
+  Df2 ru{zero2, zero2};
+  float2 re = zero2;
+  uchar2 rm = make_uchar2(0, 0);
+  auto fetch = [&](int k) {
+    if (!(in && k >= 0 && k < nz)) return;
+    const long long c = (long long)k * sz + off;
+    if (zmask) rm = *reinterpret_cast<const uchar2*>(a.op.mask + c);
+    if (U64) {
+      rd = *reinterpret_cast<const double2*>(a.u_in + c);
+      if (a.in_scale != 1.0) rd = make_double2(rd.x * a.in_scale, rd.y * a.in_scale);
+    } else {
+      const float4 v = *reinterpret_cast<const float4*>(a.udf_in + c);
+      ru = Df2{make_float2(v.x, v.z), make_float2(v.y, v.w)};
+      if (HasE) {
+        const long long t = (long long)k * szW + eoff;
+        const bool ca = (par0 + k) & 1;
+        re = make_float2(ca ? a.e[1][t] : a.e[0][t], ca ? a.e[0][t] : a.e[1][t]);
+      }
+    }
+  };
+  auto combine = [&](int k, Df2& v, uchar2& m) {
+    v = Df2{zero2, zero2};
+    m = make_uchar2(0, 0);
+    if (!(in && k >= 0 && k < nz)) return;
+    if (U64) {
+      const float2 A = split_df(rd.x), B = split_df(rd.y);
+      v = Df2{make_float2(A.x, B.x), make_float2(A.y, B.y)};
+    } else {
+      v = HasE ? df_add2(ru, re) : ru;
+    }
+    m = rm;
+  };
+  auto pair4 = [](const float4& v) { return Df2{make_float2(v.x, v.z), make_float2(v.y, v.w)}; };
+
+  // ---- own cells of a plane: b and electrode flags
+  struct Cell {
+    double2 bd;
+    Df2 bb;
+    uchar2 m;
+  };
+  auto cell_fetch = [&](int k, Cell& C) {
+    if (!own || k >= z1) return;
+    const long long c = (long long)k * sz + off;
+    C.m = a.op.mask ? *reinterpret_cast<const uchar2*>(a.op.mask + c) : make_uchar2(0, 0);
+    if (BIn == 0) C.bb = pair4(*reinterpret_cast<const float4*>(a.bdf + c));
+    else C.bd = *reinterpret_cast<const double2*>(a.rhs + c);
+    if (BIn != 0 && a.in_scale != 1.0) C.bd = make_double2(C.bd.x * a.in_scale, C.bd.y * a.in_scale);
+  };
+  // b of one cell formed in FP64 (BIn 1: as given; 2: scaled plus the
+  // Dirichlet-face lifts of the cell's domain faces)
+  auto form_b = [&](double bd, long long c, bool m, bool xm, bool xp, int k) {
+    if (BIn == 2) {
+      bd *= a.rhs_scale;
+      const bool edge = !(xm && xp && ym && yp) || k == 0 || k == nz - 1;
+      if (a.lift && edge && !m) {
+        const double l = 2.0 * (a.beta0 ? a.beta0[c] : 1.0) * a.op.ih2;
+        if (!xm && a.op.rho[0] == 1.0) bd += l * a.bval.v[0];
+        if (!xp && a.op.rho[1] == 1.0) bd += l * a.bval.v[1];
+        if (!ym && a.op.rho[2] == 1.0) bd += l * a.bval.v[2];
+        if (!yp && a.op.rho[3] == 1.0) bd += l * a.bval.v[3];
+        if (k == 0 && a.op.rho[4] == 1.0) bd += l * a.bval.v[4];
+        if (k == nz - 1 && a.op.rho[5] == 1.0) bd += l * a.bval.v[5];
+      }
+    }
+    return bd;
+  };
+
+  Df2 um, uc, up;
+  uchar2 mm, mc, mp;
+  fetch(z0 - 1);
+  combine(z0 - 1, um, mm);
+  fetch(z0);
+  combine(z0, uc, mc);
+  fetch(z0 + 1);
+  combine(z0 + 1, up, mp);
+  fetch(z0 + 2);
+  // the own cells' data of the next plane is fetched one plane ahead
+  Cell C{}, Cn{};
+  cell_fetch(z0, C);
+  float2 ss = zero2, sz2 = zero2;
+  for (int k = z0; k < z1; ++k) {
+    const int buf = (k - z0) & 1;
+    const float4 uc4 = make_float4(uc.hi.x, uc.lo.x, uc.hi.y, uc.lo.y);
+    pl[buf][ty][tx] = uc4;
+    if (ZNorm) mk[buf][ty][tx] = mc;
+    const long long c = (long long)k * sz + off;
+    if (own && a.udf_out) *reinterpret_cast<float4*>(a.udf_out + c) = uc4;
+    cell_fetch(k + 1, Cn);
+    __syncthreads();
+    // x-neighbours: L = (B of the previous lane, own A), R = (own B, A of the
+    // next lane)
+    const float pbh = __shfl_up_sync(FULL, uc.hi.y, 1), pbl = __shfl_up_sync(FULL, uc.lo.y, 1);
+    const float nah = __shfl_down_sync(FULL, uc.hi.x, 1), nal = __shfl_down_sync(FULL, uc.lo.x, 1);
+    unsigned char pbm = 0, nam = 0;
+    if (ZNorm) {
+      pbm = (unsigned char)__shfl_up_sync(FULL, (int)mc.y, 1);
+      nam = (unsigned char)__shfl_down_sync(FULL, (int)mc.x, 1);
+    }
+    if (own) {
+      const Df2 L{make_float2(pbh, uc.hi.x), make_float2(pbl, uc.lo.x)};
+      const Df2 R{make_float2(uc.hi.y, nah), make_float2(uc.lo.y, nal)};
+      const bool mA = C.m.x != 0, mB = C.m.y != 0;
+      Df2 bb;
+      if (BIn == 0) {
+        bb = C.bb;
+      } else {
+        const float2 bA = split_df(form_b(C.bd.x, c, mA, xmA, true, k));
+        const float2 bB = split_df(form_b(C.bd.y, c + 1, mB, true, xpB, k));
+        bb = Df2{make_float2(bA.x, bB.x), make_float2(bA.y, bB.y)};
+        if (a.bdf_out)
+          *reinterpret_cast<float4*>(a.bdf_out + c) = make_float4(bA.x, bA.y, bB.x, bB.y);
+      }
+      DfAcc2 acc{bb.hi, bb.lo};
+      DfAcc2 az{bb.hi, bb.lo};  // zero guess: only electrode neighbours contribute
+      const bool zm = k > 0, zp = k < nz - 1;
+      Df2 dg = dxy;
+      if (!zm) dg = df_add_df2(dg, a.dzm);
+      if (!zp) dg = df_add_df2(dg, a.dzp);
+      acc.add(Df2{make_float2(-dg.hi.x, -dg.hi.y), make_float2(-dg.lo.x, -dg.lo.y)}, uc);
+      // masked-neighbour weights for the zero guess
+      auto zw = [](const Df2& w, bool ma, bool mb) {
+        return Df2{make_float2(ma ? w.hi.x : 0.0f, mb ? w.hi.y : 0.0f),
+                   make_float2(ma ? w.lo.x : 0.0f, mb ? w.lo.y : 0.0f)};
+      };
+      auto nb = [&](const Df2& w, const Df2& v, bool ma, bool mb) {
+        acc.add(w, v);
+        if (zmask && (ma || mb)) az.add(zw(w, ma, mb), v);
+      };
+      const float4 s4 = pl[buf][ty - 1][tx], n4 = pl[buf][ty + 1][tx];
+      const uchar2 ms = ZNorm ? mk[buf][ty - 1][tx] : make_uchar2(0, 0);
+      const uchar2 mn = ZNorm ? mk[buf][ty + 1][tx] : make_uchar2(0, 0);
+      const Df2 w{make_float2(a.ih2d.x, a.ih2d.x), make_float2(a.ih2d.y, a.ih2d.y)};
+      // no neighbour across A's -x or B's +x domain face: weight 0
+      const Df2 wl{make_float2(xmA ? a.ih2d.x : 0.0f, a.ih2d.x),
+                   make_float2(xmA ? a.ih2d.y : 0.0f, a.ih2d.y)};
+      const Df2 wr{make_float2(a.ih2d.x, xpB ? a.ih2d.x : 0.0f),
+                   make_float2(a.ih2d.y, xpB ? a.ih2d.y : 0.0f)};
+      nb(wl, L, xmA && pbm, mc.x);
+      nb(wr, R, mc.y, xpB && nam);
+      if (ym) nb(w, pair4(s4), ms.x, ms.y);
+      if (yp) nb(w, pair4(n4), mn.x, mn.y);
+      if (zm) nb(w, um, mm.x, mm.y);
+      if (zp) nb(w, up, mp.x, mp.y);
+      float2 r = acc.value(), rz = az.value();
+      if (mA) r.x = rz.x = 0.0f;
+      if (mB) r.y = rz.y = 0.0f;
+      if (a.r[0]) {
+        const long long t = (long long)k * szW + eoff;
+        const bool ca = (par0 + k) & 1;
+        (ca ? a.r[1] : a.r[0])[t] = r.x;
+        (ca ? a.r[0] : a.r[1])[t] = r.y;
+      }
+      ss = fma2(r, r, ss);
+      if (ZNorm) sz2 = fma2(rz, rz, sz2);
+    }
+    // advance the column pair: plane k+2 (loaded last step) becomes k+1
+    um = uc;
+    mm = mc;
+    uc = up;
+    mc = mp;
+    combine(k + 2, up, mp);
+    if (k + 3 <= z1) fetch(k + 3);
+    C = Cn;
+  }
+  // CTA sums of r^2 (FP32 per thread, FP64 across the CTA)
+  float s1 = ss.x + ss.y, s2 = sz2.x + sz2.y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(FULL, s1, o);
+    if (ZNorm) s2 += __shfl_xor_sync(FULL, s2, o);
+  }
+  if (tx == 0) {
+    red[0][ty] = s1;
+    if (ZNorm) red[1][ty] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int h = 0; h < (ZNorm ? 2 : 1); ++h) {
+      double v = threadIdx.x < NT / 32 ? (double)red[h][threadIdx.x] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+      if (threadIdx.x == 0) (h ? a.partial_z : a.partial)[cta] = v;
+    }
+  }
+}
+
 // FP64 result of a double-float iterate: exact widening of both parts on
-// the integer pipe, one FP64 add.  Electrode cells keep the caller's value.
+// the integer pipe, one FP64 add, times the power-of-two scale that undoes a
+// scaled solve (exact).  Electrode cells keep the caller's value.
 __global__ void k_df_to_f64(const float2* __restrict__ in, const uint8_t* __restrict__ mask,
-                            double* __restrict__ out, long long n) {
+                            double* __restrict__ out, long long n, double scale) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n || (mask && mask[c])) return;
   const float2 v = in[c];
-  out[c] = widen(v.x) + widen(v.y);
+  const double u = widen(v.x) + widen(v.y);
+  out[c] = scale != 1.0 ? u * scale : u;
 }
 
 }  // namespace
 
 // CTA columns of the refinement pass along x and y (30 x 14 own columns
-// per CTA), in 64-bit so that no grid size can wrap them.
-static long long ir_gx(const Box& b) { return ((long long)b.nx + TX - 3) / (TX - 2); }
+// per CTA, 60 x 14 for the two-cell kernel), in 64-bit so that no grid size
+// can wrap them.
+static long long ir_gx(const Box& b, bool paired) {
+  const long long own = paired ? 2 * (TX - 2) : TX - 2;
+  return ((long long)b.nx + own - 1) / own;
+}
 static long long ir_gy(const Box& b) { return ((long long)b.ny + TY - 3) / (TY - 2); }
 
 // Grid of the refinement pass for z planes per CTA column `hint` (0:
@@ -296,8 +539,8 @@ static long long ir_gy(const Box& b) { return ((long long)b.ny + TY - 3) / (TY -
 // 512-thread CTAs on each of GB300's 152 SMs) and the run is longer than 16
 // planes, so its CTA count is gx * gy when gx * gy >= 3648 and below
 // 3 * 3648 otherwise: at most max(gx * gy, 10944).
-static dim3 ir_grid(const Box& b, int hint, int* zchunk) {
-  const long long gx = ir_gx(b), gy = ir_gy(b);
+static dim3 ir_grid(const Box& b, int hint, int* zchunk, bool paired) {
+  const long long gx = ir_gx(b, paired), gy = ir_gy(b);
   int zc = b.nz;
   if (hint > 0) {
     zc = std::min(hint, b.nz);
@@ -309,45 +552,65 @@ static dim3 ir_grid(const Box& b, int hint, int* zchunk) {
   return dim3((unsigned)gx, (unsigned)gy, (unsigned)((b.nz + zc - 1) / zc));
 }
 
-// CTAs of the refinement pass (64-bit, computed before any dim3 narrowing).
+// CTAs of the refinement pass (64-bit, computed before any dim3 narrowing)
+// for either kernel, whichever is larger.
 static long long ir_ctas(const Box& b, int zchunk) {
-  int zc = b.nz;
-  if (zchunk > 0) {
-    zc = std::min(zchunk, b.nz);
-  } else {
-    ir_grid(b, 0, &zc);
+  long long most = 0;
+  for (int paired = 0; paired < 2; ++paired) {
+    int zc = b.nz;
+    if (zchunk > 0) zc = std::min(zchunk, b.nz);
+    else ir_grid(b, 0, &zc, paired != 0);
+    most = std::max(most, ir_gx(b, paired != 0) * ir_gy(b) * (((long long)b.nz + zc - 1) / zc));
   }
-  return ir_gx(b) * ir_gy(b) * (((long long)b.nz + zc - 1) / zc);
+  return most;
 }
 
 int ir_partials(const Box& b, int zchunk) { return (int)ir_ctas(b, zchunk); }
 
-template <bool F, bool E, bool U, int B, bool Z>
-static void go(const IrArgs& a, dim3 g, cudaStream_t s) {
-  k_ir_df<F, E, U, B, Z><<<g, NT, 0, s>>>(a);
+// The two-cell kernel runs the constant-coefficient operator (beta = 1);
+// it needs an even nx (whole pairs) and arrays on 16-byte boundaries (one
+// 16-byte load per pair; 2 bytes for the electrode flags).  With face
+// arrays the pair's 28 coefficient values leave no room to fetch them a
+// plane ahead in 64 registers, and the one-cell kernel, which does, is
+// faster (280 against 327 us per 256^3 step on GB300).
+static bool ir_pairable(const IrArgs& a) {
+  auto al = [](const void* p, unsigned m) { return ((uintptr_t)p & (m - 1)) == 0; };
+  return !a.op.cxd && a.op.b.nx % 2 == 0 && al(a.udf_in, 16) && al(a.udf_out, 16) &&
+         al(a.bdf, 16) && al(a.bdf_out, 16) && al(a.u_in, 16) && al(a.rhs, 16) &&
+         al(a.op.mask, 2);
 }
 
-template <bool F>
+template <bool P, bool F, bool E, bool U, int B, bool Z>
+static void go(const IrArgs& a, dim3 g, cudaStream_t s) {
+  if (P) k_ir_df2<E, U, B, Z><<<g, NT, 0, s>>>(a);
+  else k_ir_df<F, E, U, B, Z><<<g, NT, 0, s>>>(a);
+}
+
+template <bool P, bool F>
 static void dispatch_f(const IrArgs& a, dim3 g, cudaStream_t s) {
   const int bin = a.bdf ? 0 : (a.lift || a.rhs_scale != 1.0 ? 2 : 1);
   if (a.udf_in) {  // double-float iterate (+ correction)
-    if (a.e[0]) go<F, true, false, 0, false>(a, g, s);
-    else go<F, false, false, 0, false>(a, g, s);
+    if (a.e[0]) go<P, F, true, false, 0, false>(a, g, s);
+    else go<P, F, false, false, 0, false>(a, g, s);
   } else if (a.partial_z) {  // FP64 guess, both norms
-    if (bin == 0) go<F, false, true, 0, true>(a, g, s);
-    else go<F, false, true, 1, true>(a, g, s);
+    if (bin == 0) go<P, F, false, true, 0, true>(a, g, s);
+    else go<P, F, false, true, 1, true>(a, g, s);
   } else if (bin == 0) {
-    go<F, false, true, 0, false>(a, g, s);
+    go<P, F, false, true, 0, false>(a, g, s);
   } else if (bin == 1) {
-    go<F, false, true, 1, false>(a, g, s);
+    go<P, F, false, true, 1, false>(a, g, s);
   } else {
-    go<F, false, true, 2, false>(a, g, s);
+    go<P, F, false, true, 2, false>(a, g, s);
   }
 }
 
-static void dispatch(const IrArgs& a, dim3 g, cudaStream_t s) {
-  if (a.op.cxd) dispatch_f<true>(a, g, s);
-  else dispatch_f<false>(a, g, s);
+static void dispatch(const IrArgs& a, dim3 g, bool paired, cudaStream_t s) {
+  if (paired) {
+    dispatch_f<true, false>(a, g, s);  // beta = 1 only (ir_pairable)
+  } else {
+    if (a.op.cxd) dispatch_f<false, true>(a, g, s);
+    else dispatch_f<false, false>(a, g, s);
+  }
 }
 
 // double-float of a host double
@@ -363,19 +626,24 @@ static void ir_constants(IrArgs& a) {
   a.nalpha = df_host(-a.alpha);
   a.dint = df_host(6.0 * a.op.ih2 + a.alpha);
   a.has_alpha = a.alpha != 0.0;
+  a.dzm = df_host((2.0 * a.op.rho[4] - 1.0) * a.op.ih2);
+  a.dzp = df_host((2.0 * a.op.rho[5] - 1.0) * a.op.ih2);
 }
 
-void launch_ir_fused(const IrArgs& args, cudaStream_t s) {
+int launch_ir_fused(const IrArgs& args, cudaStream_t s) {
   IrArgs a = args;
-  dim3 g = ir_grid(a.op.b, args.zchunk, &a.zchunk);
+  if (a.in_scale == 0.0) a.in_scale = 1.0;  // zero-initialised arguments: no scaling
+  const bool paired = ir_pairable(a);
+  dim3 g = ir_grid(a.op.b, args.zchunk, &a.zchunk, paired);
   ir_constants(a);
-  dispatch(a, g, s);
+  dispatch(a, g, paired, s);
   add_launches(1);
+  return (int)(g.x * g.y * g.z);
 }
 
 void launch_df_to_f64(const float2* in, const uint8_t* mask, double* out, long long n,
-                      cudaStream_t s) {
-  k_df_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, mask, out, n);
+                      double scale, cudaStream_t s) {
+  k_df_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, mask, out, n, scale);
   add_launches(1);
 }
 
@@ -453,12 +721,13 @@ mg_status noalloc_scratch(double** out) {
 
 // The refinement-residual kernel (no correction, not the norm of b) with its
 // partial sums in the static scratch, then the final sum and square root.
-void launch_noalloc(IrArgs a, double* scratch, int nparts, double* norm_out, cudaStream_t s) {
+void launch_noalloc(IrArgs a, double* scratch, double* norm_out, cudaStream_t s) {
   a.partial = scratch;
-  dim3 g = ir_grid(a.op.b, 0, &a.zchunk);
+  const bool paired = ir_pairable(a);
+  dim3 g = ir_grid(a.op.b, 0, &a.zchunk, paired);
   ir_constants(a);
-  dispatch(a, g, s);
-  k_noalloc_finish<<<1, NT, 0, s>>>(scratch, nparts, norm_out);
+  dispatch(a, g, paired, s);
+  k_noalloc_finish<<<1, NT, 0, s>>>(scratch, (int)(g.x * g.y * g.z), norm_out);
   add_launches(2);
 }
 
@@ -486,7 +755,7 @@ extern "C" mg_status mg_residual_norm_noalloc(const mg_grid* grid, const mg_bc* 
     }
   mg::Box box{grid->nx, grid->ny, grid->nz};
   // launch limits of the kernel's grid: y and z extents below 65536
-  if (mg::ir_gy(box) > 65535 || box.nz > 65535) {
+  if (mg::ir_gy(box) > 65535 || box.nz > 65535) {  // (same for either kernel)
     mg::set_last_error("grid too large for the refinement kernel's launch: ceil(ny/14) and nz "
                        "must not exceed 65535");
     return MG_ERR_UNSUPPORTED;
@@ -496,7 +765,8 @@ extern "C" mg_status mg_residual_norm_noalloc(const mg_grid* grid, const mg_bc* 
     char msg[256];
     std::snprintf(msg, sizeof msg,
                   "grid too large for the allocation-free scratch: the residual kernel needs "
-                  "%lld partial sums (ceil(nx/30) * ceil(ny/14) * z-chunks), more than the "
+                  "up to %lld partial sums (ceil(nx/30) * ceil(ny/14) * z-chunks), more than "
+                  "the "
                   "16384 of the static array",
                   nparts);
     mg::set_last_error(msg);
@@ -519,7 +789,8 @@ extern "C" mg_status mg_residual_norm_noalloc(const mg_grid* grid, const mg_bc* 
   a.rhs_scale = rhs_scale;
   a.lift = 1;
   a.u_in = u;
-  mg::launch_noalloc(a, scratch, (int)nparts, norm_out, (cudaStream_t)cuda_stream);
+  a.in_scale = 1.0;
+  mg::launch_noalloc(a, scratch, norm_out, (cudaStream_t)cuda_stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     mg::set_last_error(std::string("kernel launch: ") + cudaGetErrorString(e));

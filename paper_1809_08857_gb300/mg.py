@@ -68,19 +68,19 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("concurrency", ctypes.c_int), ("no_graphs", ctypes.c_int),
                 ("rte_bc", ctypes.c_int), ("ir_zchunk", ctypes.c_int),
-                ("coarse_op", ctypes.c_int)]
+                ("coarse_op", ctypes.c_int), ("fixed_cycles", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("converged", ctypes.c_int),
                 ("rel_resid", ctypes.c_double), ("time_ms", ctypes.c_double),
-                ("hist", ctypes.c_double * 64)]
+                ("hist", ctypes.c_double * 64), ("vcycles", ctypes.c_int)]
 
     def as_dict(self):
         n = min(self.cycles + 1, 64)
         return {"cycles": self.cycles, "converged": bool(self.converged),
                 "rel_resid": self.rel_resid, "time_ms": self.time_ms,
-                "hist": list(self.hist[:n])}
+                "hist": list(self.hist[:n]), "vcycles": self.vcycles}
 
 
 class Problem(ctypes.Structure):
