@@ -83,20 +83,40 @@ def streamer_shell_box(shape, h, origin, seed, radius=0.02, z0=0.4, z1=0.8, axis
     surface carry amplitude * eps0 / t^2 * exp(noise * xi), t = thickness
     (default h; a fixed t gives one shell sampled alike on every level of an
     AMR hierarchy)."""
+    idx, val = streamer_shell_cells(shape, h, origin, seed, radius, z0, z1, axis_xy, amplitude,
+                                    noise, thickness)
+    rho = np.zeros(shape)
+    rho.reshape(-1)[idx] = val
+    return rho
+
+
+def streamer_shell_cells(shape, h, origin, seed, radius=0.02, z0=0.4, z1=0.8,
+                         axis_xy=(0.5, 0.5), amplitude=1e-3, noise=0.1, thickness=None):
+    """The cells of streamer_shell_box as (flat indices in (k, j, i) order,
+    values incl. eps0), without a dense array: only the columns within
+    radius + t + h of the axis can hold shell cells, so the distance test
+    runs on that window of every plane; xi ~ N(0, 1) is drawn per shell cell
+    in index order."""
     t = h if thickness is None else float(thickness)
     rng = np.random.default_rng(seed)
     nz, ny, nx = shape
     x = origin[0] + (np.arange(nx) + 0.5) * h
     y = origin[1] + (np.arange(ny) + 0.5) * h
     z = origin[2] + (np.arange(nz) + 0.5) * h
-    shell = np.zeros(shape, dtype=bool)
-    for k in range(nz):
-        d = _shell_distance_slab(x, y, z[k], axis_xy, z0, z1, radius)
-        shell[k] = d <= t
-    rho = np.zeros(shape)
-    cnt = int(shell.sum())
-    rho[shell] = amplitude / t**2 * np.exp(noise * rng.standard_normal(cnt))
-    return rho * EPS0
+    reach = radius + t + h
+    ix = np.nonzero(np.abs(x - axis_xy[0]) <= reach)[0]
+    iy = np.nonzero(np.abs(y - axis_xy[1]) <= reach)[0]
+    hit = []
+    if len(ix) and len(iy):
+        x0, y0 = int(ix[0]), int(iy[0])
+        xs, ys = x[x0:ix[-1] + 1], y[y0:iy[-1] + 1]
+        for k in range(nz):
+            jj, ii = np.nonzero(_shell_distance_slab(xs, ys, z[k], axis_xy, z0, z1, radius) <= t)
+            if len(jj):
+                hit.append(((k * ny + (jj + y0)) * nx + (ii + x0)).astype(np.int64))
+    idx = np.concatenate(hit) if hit else np.zeros(0, dtype=np.int64)
+    val = amplitude / t**2 * np.exp(noise * rng.standard_normal(len(idx)))
+    return idx, val * EPS0
 
 
 def ionization_source(n, seed, sigma_cells=2.0):

@@ -186,19 +186,28 @@ def test_training_reduces_loss_and_save_load_roundtrip(mg, tmp_path):
 
 
 def test_untrained_network_predicts_previous_potential(mg):
-    """The head starts at zero: the guess is phi_prev exactly, and the
-    judged warm start accepts it (equal residual)."""
+    """The head starts at zero: the network's candidate is phi_prev exactly,
+    so both candidates of the judged warm start are phi_prev after the same
+    nu1 = 2 red-black sweeps, it accepts the network's (equal residual), and
+    the guess equals the oracle's two sweeps of phi_prev."""
+    import oracle
+
     n = 32
     rng = np.random.default_rng(7)
     from paper_1809_08857_gb300 import workloads as W
 
-    rho = _cuda64(W.gaussian_blobs(n, 1))
-    prev = _cuda64(rng.standard_normal((n, n, n)))
+    rho_np, prev_np = W.gaussian_blobs(n, 1), rng.standard_normal((n, n, n))
+    rho, prev = _cuda64(rho_np), _cuda64(prev_np)
     net = mg.UNet(seed=2)
-    s = mg.Solver((n, n, n), 1.0 / n, precision=1)
+    s = mg.Solver((n, n, n), 1.0 / n, precision=1, nu1=2)
     s.warmstart_attach(net)
     guess, used = s.warmstart_predict(rho, prev)
     torch.cuda.synchronize()
-    assert torch.equal(guess, prev) and used
+    assert used
+    P = oracle.poisson((n, n, n), 1.0 / n)
+    ref = prev_np
+    for _ in range(2):
+        ref = P.rbgs(rho_np / oracle.EPS0, P.rbgs(rho_np / oracle.EPS0, ref, 0), 1)
+    assert oracle.rel_l2(guess.cpu().numpy(), ref) <= 1e-13
     s.close()
     net.close()
