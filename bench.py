@@ -61,6 +61,8 @@ def parse():
                          "0 = automatic")
     ap.add_argument("--no-amr", action="store_true",
                     help="skip the composite AMR solve among the extras")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the 256^3 parent + 16 sub-box pass among the extras")
     ap.add_argument("--no-needle", action="store_true",
                     help="skip the 896^3 needle-plane set among the extras")
     ap.add_argument("--no-fp64-leg", action="store_true",
@@ -477,6 +479,43 @@ def measure_needle_plane(dev, n=896, reps=2):
             "warm_start": "not used: a cold solve has no previous potential to start from"}
 
 
+def measure_config3(dev, reps=3):
+    """The sub-box configuration (outside the timed region): the Poisson + 3
+    Helmholtz set on a 256^3 parent, face data for 16 refined sub-boxes of
+    sizes drawn from {32, 48, 64, 96, 128}^3 (ratio 2) interpolated from the
+    parent answers, and the 64 sub-box problems in one mg_solve_batch, all
+    from zero to 1e-10 (subboxes.Config3); device time per pass by CUDA
+    events after one untimed pass (contexts, graphs and inputs built
+    beforehand)."""
+    import torch
+
+    from paper_1809_08857_gb300 import subboxes
+
+    c = subboxes.Config3(n=256, count=16, seed=0)
+    c.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        stp, stb = c.run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    parent_cells, box_cells = c.cells()
+    out = {"workload": "256^3 Poisson + 3 Helmholtz, then 16 ratio-2 sub-boxes of sizes "
+                       "{32, 48, 64, 96, 128}^3 with Dirichlet data from the parent answers, "
+                       "4 problems each in one batch; mixed, 3 inner V-cycles",
+           "ms": round(ms, 2), "passes_per_s": round(1e3 / ms, 2),
+           "parent_steps": [x["cycles"] for x in stp],
+           "subbox_steps_max": max(x["cycles"] for x in stb),
+           "subbox_rel_resid_max": max(x["rel_resid"] for x in stb),
+           "cells": {"parent": parent_cells, "subboxes": box_cells},
+           "box_sizes": sorted(b["dims"][0] for b in c.boxes)}
+    c.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_unet(dev, n=256, reps=5):
     """One warm-start U-Net forward pass (mg_unet_predict) on a 256^3 volume
     (outside the timed region): device time per pass (CUDA events) and the
@@ -642,6 +681,7 @@ def run_ours(args):
     phi = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
     psi = [torch.zeros_like(phi) for _ in range(3)]
     cycles = [0, 0, 0, 0]
+    history = [[], [], [], []]
 
     def step():
         phi.zero_()
@@ -649,6 +689,7 @@ def run_ours(args):
             p.zero_()
         st = solver.solve_set(rho, phi, S, psi, KAPPAS, TOL)
         cycles[:] = [s["cycles"] for s in st]
+        history[:] = [[float(f"{x:.3e}") for x in s["hist"]] for s in st]
 
     def barrier():
         if world > 1:
@@ -786,6 +827,8 @@ def run_ours(args):
     extras["unet_forward"] = measure_unet(dev)
     if not args.no_amr:
         extras["amr_solve"] = measure_amr(dev)
+    if not args.no_config3:
+        extras["subboxes_256"] = measure_config3(dev)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -798,6 +841,7 @@ def run_ours(args):
                            ir_zchunk=solver.options.ir_zchunk),
             "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": launches, "cycles_per_problem": cycles,
+            "residual_per_step": history,
             "rel_resid_fp64": fp64_check,
             "roofline": roofline(prof_serial, prof_overlap, n), "kernel_profile": prof_serial,
             "extras": extras}

@@ -154,3 +154,51 @@ def test_batched_uneven_subboxes_match_oracle(mg, prec):
     for pr, ref, stt in zip(probs, refs, st):
         assert stt["converged"]
         assert oracle.rel_l2(pr["u"].cpu().numpy(), ref) <= PARITY
+
+
+def test_config3_parent_set_and_16_subboxes(mg):
+    """The full-size sub-box configuration: the Poisson + three Helmholtz set on
+    the 256^3 parent, then 16 sub-boxes of sizes drawn from {32, 48, 64, 96,
+    128}^3 (ratio 2), each with its Poisson and three Helmholtz problems on
+    Dirichlet data interpolated from the parent answers, all 64 solved in one
+    batch.  Every sub-box answer meets 1e-10 by the oracle's FP64 residual on
+    the same face data; the smallest and the largest box's four answers are
+    within 1e-9 of the oracle's converged solutions; the parent answers meet
+    1e-10 by the oracle's residual."""
+    from paper_1809_08857_gb300 import subboxes
+
+    c = subboxes.Config3(n=256, count=16, seed=0)
+    st_parent, st_boxes = c.run()
+    torch.cuda.synchronize()
+    assert all(x["converged"] for x in st_parent) and all(x["converged"] for x in st_boxes)
+    assert sorted({b["dims"][0] for b in c.boxes}) == [32, 48, 64, 96, 128]
+    n = c.n
+    hp = 1.0 / n
+    P = oracle.poisson((n, n, n), hp, eps_r=c.eps.cpu().numpy())
+    f = c.rho.cpu().numpy() / oracle.EPS0
+    _, rn = P.residual(f, c.phi.cpu().numpy())
+    assert rn <= 1.01 * TOL * P.rhs_norm(f, np.zeros((n, n, n)))
+    S = c.S.cpu().numpy()
+    for k, psi in zip(subboxes.KAPPAS, c.psi):
+        H = oracle.helmholtz((n, n, n), hp, k)
+        _, rn = H.residual(S, psi.cpu().numpy())
+        assert rn <= 1.01 * TOL * H.rhs_norm(S, np.zeros((n, n, n)))
+    sizes = [int(np.prod(b["shape"])) for b in c.boxes]
+    full = {int(np.argmin(sizes)), int(np.argmax(sizes))}
+    hf = hp / 2
+    for q, b in enumerate(c.boxes):
+        shape = b["shape"]
+        rhs = [b["rho"].cpu().numpy() / oracle.EPS0] + [b["S"].cpu().numpy()] * 3
+        alphas = [0.0] + [k * k for k in subboxes.KAPPAS]
+        betas = [b["eps"], None, None, None]
+        for j in range(4):
+            fd = b["faces"][j].cpu().numpy()
+            Pb = oracle.Problem(shape, hf, alphas[j], betas[j], None, ALL_DIR, (0.0,) * 6, fd)
+            u = b["u"][j].cpu().numpy()
+            _, rn = Pb.residual(rhs[j], u)
+            assert rn <= 1.01 * TOL * Pb.rhs_norm(rhs[j], np.zeros(shape)), (q, j)
+            if q in full:
+                ref, _, rel, _ = Pb.solve(rhs[j])
+                assert rel < 1e-12
+                assert oracle.rel_l2(u, ref) <= PARITY, (q, j)
+    c.close()
