@@ -119,8 +119,10 @@ typedef struct {
                        (MG_RTE_BC_DIRICHLET = 0); fixed at mg_create */
   int ir_zchunk;    /* mixed mode, tile of the refinement pass: z planes
                        marched by one CTA column, 0 (automatic: enough CTAs
-                       for 8 waves of three per SM) or >= 16; mg_autotune
-                       picks it among {auto, 16, 32, 64, 128} (0) */
+                       for 8 waves of three per SM) or >= 16 (half as many
+                       for the two-cell kernel of constant-coefficient
+                       problems, whose CTAs span twice the columns);
+                       mg_autotune picks it among {auto, 16, 32, 64, 128} (0) */
   int coarse_op;    /* mg_coarse_op of a context with eps_r (MG_COARSE_FACE =
                        0); fixed at mg_create */
   int fixed_cycles; /* mixed mode: 0 = from the second refinement step on, a

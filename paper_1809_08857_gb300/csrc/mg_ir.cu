@@ -282,12 +282,12 @@ __global__ void __launch_bounds__(NT, Faces ? 2 : 3) k_ir_df(IrArgs a) {
 // shared memory is one 16-byte word.  Needs nx even and 16-byte aligned
 // arrays (the launcher checks and otherwise runs k_ir_df).  A CTA of 32 x 16
 // threads covers 64 x 16 columns, of which the inner 60 x 14 are its own.
-// Template arguments as for k_ir_df (no Faces).
-template <bool HasE, bool U64, int BIn, bool ZNorm>
+// Template arguments as for k_ir_df (no Faces, no ZNorm: the first pass of
+// a solve runs k_ir_df).
+template <bool HasE, bool U64, int BIn>
 __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
   __shared__ float4 pl[2][TY][TX];
-  __shared__ uchar2 mk[ZNorm ? 2 : 1][ZNorm ? TY : 1][TX];  // electrode flags of A, B
-  __shared__ float red[2][NT / 32];
+  __shared__ float red[NT / 32];
   const unsigned FULL = 0xffffffffu;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int nx = a.op.b.nx, ny = a.op.b.ny, nz = a.op.b.nz;
@@ -300,7 +300,6 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
   const int off = in ? j * nx + i0 : 0;  // in-plane offset of cell A
   const int eoff = in ? j * W + (i0 >> 1) : 0;  // packed index of A and of B
   const int par0 = (i0 + j) & 1;                // colour of A at k = 0; B has the other
-  const bool zmask = ZNorm && a.op.mask != nullptr;
   const bool xmA = i0 > 0, xpB = i0 + 2 < nx, ym = j > 0, yp = j < ny - 1;
   const float2 zero2 = make_float2(0.0f, 0.0f);
   // beta = 1: the diagonal of each cell of the pair on an interior plane,
@@ -324,11 +323,9 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
   double2 rd = make_double2(0.0, 0.0);
   Df2 ru{zero2, zero2};
   float2 re = zero2;
-  uchar2 rm = make_uchar2(0, 0);
   auto fetch = [&](int k) {
     if (!(in && k >= 0 && k < nz)) return;
     const long long c = (long long)k * sz + off;
-    if (zmask) rm = *reinterpret_cast<const uchar2*>(a.op.mask + c);
     if (U64) {
       rd = *reinterpret_cast<const double2*>(a.u_in + c);
       if (a.in_scale != 1.0) rd = make_double2(rd.x * a.in_scale, rd.y * a.in_scale);
@@ -342,9 +339,8 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
       }
     }
   };
-  auto combine = [&](int k, Df2& v, uchar2& m) {
+  auto combine = [&](int k, Df2& v) {
     v = Df2{zero2, zero2};
-    m = make_uchar2(0, 0);
     if (!(in && k >= 0 && k < nz)) return;
     if (U64) {
       const float2 A = split_df(rd.x), B = split_df(rd.y);
@@ -352,7 +348,6 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
     } else {
       v = HasE ? df_add2(ru, re) : ru;
     }
-    m = rm;
   };
   auto pair4 = [](const float4& v) { return Df2{make_float2(v.x, v.z), make_float2(v.y, v.w)}; };
 
@@ -390,23 +385,21 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
   };
 
   Df2 um, uc, up;
-  uchar2 mm, mc, mp;
   fetch(z0 - 1);
-  combine(z0 - 1, um, mm);
+  combine(z0 - 1, um);
   fetch(z0);
-  combine(z0, uc, mc);
+  combine(z0, uc);
   fetch(z0 + 1);
-  combine(z0 + 1, up, mp);
+  combine(z0 + 1, up);
   fetch(z0 + 2);
   // the own cells' data of the next plane is fetched one plane ahead
   Cell C{}, Cn{};
   cell_fetch(z0, C);
-  float2 ss = zero2, sz2 = zero2;
+  float2 ss = zero2;
   for (int k = z0; k < z1; ++k) {
     const int buf = (k - z0) & 1;
     const float4 uc4 = make_float4(uc.hi.x, uc.lo.x, uc.hi.y, uc.lo.y);
     pl[buf][ty][tx] = uc4;
-    if (ZNorm) mk[buf][ty][tx] = mc;
     const long long c = (long long)k * sz + off;
     if (own && a.udf_out) *reinterpret_cast<float4*>(a.udf_out + c) = uc4;
     cell_fetch(k + 1, Cn);
@@ -415,11 +408,6 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
     // next lane)
     const float pbh = __shfl_up_sync(FULL, uc.hi.y, 1), pbl = __shfl_up_sync(FULL, uc.lo.y, 1);
     const float nah = __shfl_down_sync(FULL, uc.hi.x, 1), nal = __shfl_down_sync(FULL, uc.lo.x, 1);
-    unsigned char pbm = 0, nam = 0;
-    if (ZNorm) {
-      pbm = (unsigned char)__shfl_up_sync(FULL, (int)mc.y, 1);
-      nam = (unsigned char)__shfl_down_sync(FULL, (int)mc.x, 1);
-    }
     if (own) {
       const Df2 L{make_float2(pbh, uc.hi.x), make_float2(pbl, uc.lo.x)};
       const Df2 R{make_float2(uc.hi.y, nah), make_float2(uc.lo.y, nal)};
@@ -435,39 +423,27 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
           *reinterpret_cast<float4*>(a.bdf_out + c) = make_float4(bA.x, bA.y, bB.x, bB.y);
       }
       DfAcc2 acc{bb.hi, bb.lo};
-      DfAcc2 az{bb.hi, bb.lo};  // zero guess: only electrode neighbours contribute
       const bool zm = k > 0, zp = k < nz - 1;
       Df2 dg = dxy;
       if (!zm) dg = df_add_df2(dg, a.dzm);
       if (!zp) dg = df_add_df2(dg, a.dzp);
       acc.add(Df2{make_float2(-dg.hi.x, -dg.hi.y), make_float2(-dg.lo.x, -dg.lo.y)}, uc);
-      // masked-neighbour weights for the zero guess
-      auto zw = [](const Df2& w, bool ma, bool mb) {
-        return Df2{make_float2(ma ? w.hi.x : 0.0f, mb ? w.hi.y : 0.0f),
-                   make_float2(ma ? w.lo.x : 0.0f, mb ? w.lo.y : 0.0f)};
-      };
-      auto nb = [&](const Df2& w, const Df2& v, bool ma, bool mb) {
-        acc.add(w, v);
-        if (zmask && (ma || mb)) az.add(zw(w, ma, mb), v);
-      };
       const float4 s4 = pl[buf][ty - 1][tx], n4 = pl[buf][ty + 1][tx];
-      const uchar2 ms = ZNorm ? mk[buf][ty - 1][tx] : make_uchar2(0, 0);
-      const uchar2 mn = ZNorm ? mk[buf][ty + 1][tx] : make_uchar2(0, 0);
       const Df2 w{make_float2(a.ih2d.x, a.ih2d.x), make_float2(a.ih2d.y, a.ih2d.y)};
       // no neighbour across A's -x or B's +x domain face: weight 0
       const Df2 wl{make_float2(xmA ? a.ih2d.x : 0.0f, a.ih2d.x),
                    make_float2(xmA ? a.ih2d.y : 0.0f, a.ih2d.y)};
       const Df2 wr{make_float2(a.ih2d.x, xpB ? a.ih2d.x : 0.0f),
                    make_float2(a.ih2d.y, xpB ? a.ih2d.y : 0.0f)};
-      nb(wl, L, xmA && pbm, mc.x);
-      nb(wr, R, mc.y, xpB && nam);
-      if (ym) nb(w, pair4(s4), ms.x, ms.y);
-      if (yp) nb(w, pair4(n4), mn.x, mn.y);
-      if (zm) nb(w, um, mm.x, mm.y);
-      if (zp) nb(w, up, mp.x, mp.y);
-      float2 r = acc.value(), rz = az.value();
-      if (mA) r.x = rz.x = 0.0f;
-      if (mB) r.y = rz.y = 0.0f;
+      acc.add(wl, L);
+      acc.add(wr, R);
+      if (ym) acc.add(w, pair4(s4));
+      if (yp) acc.add(w, pair4(n4));
+      if (zm) acc.add(w, um);
+      if (zp) acc.add(w, up);
+      float2 r = acc.value();
+      if (mA) r.x = 0.0f;
+      if (mB) r.y = 0.0f;
       if (a.r[0]) {
         const long long t = (long long)k * szW + eoff;
         const bool ca = (par0 + k) & 1;
@@ -475,38 +451,26 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
         (ca ? a.r[0] : a.r[1])[t] = r.y;
       }
       ss = fma2(r, r, ss);
-      if (ZNorm) sz2 = fma2(rz, rz, sz2);
     }
     // advance the column pair: plane k+2 (loaded last step) becomes k+1
     um = uc;
-    mm = mc;
     uc = up;
-    mc = mp;
-    combine(k + 2, up, mp);
+    combine(k + 2, up);
     if (k + 3 <= z1) fetch(k + 3);
     C = Cn;
   }
   // CTA sums of r^2 (FP32 per thread, FP64 across the CTA)
-  float s1 = ss.x + ss.y, s2 = sz2.x + sz2.y;
+  float s1 = ss.x + ss.y;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s1 += __shfl_xor_sync(FULL, s1, o);
-    if (ZNorm) s2 += __shfl_xor_sync(FULL, s2, o);
-  }
-  if (tx == 0) {
-    red[0][ty] = s1;
-    if (ZNorm) red[1][ty] = s2;
-  }
+  for (int o = 16; o > 0; o >>= 1) s1 += __shfl_xor_sync(FULL, s1, o);
+  if (tx == 0) red[ty] = s1;
   __syncthreads();
   if (threadIdx.x < 32) {
     const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    double v = threadIdx.x < NT / 32 ? (double)red[threadIdx.x] : 0.0;
 #pragma unroll
-    for (int h = 0; h < (ZNorm ? 2 : 1); ++h) {
-      double v = threadIdx.x < NT / 32 ? (double)red[h][threadIdx.x] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-      if (threadIdx.x == 0) (h ? a.partial_z : a.partial)[cta] = v;
-    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (threadIdx.x == 0) a.partial[cta] = v;
   }
 }
 
@@ -522,6 +486,27 @@ __global__ void k_df_to_f64(const float2* __restrict__ in, const uint8_t* __rest
   out[c] = scale != 1.0 ? u * scale : u;
 }
 
+// The same for two cells per thread (n even, arrays on 16-byte boundaries):
+// one 16-byte load and one 16-byte store per pair.
+__global__ void k_df_to_f64x2(const float4* __restrict__ in, const uchar2* __restrict__ mask,
+                              double2* __restrict__ out, long long npair, double scale) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= npair) return;
+  const float4 v = in[c];
+  double2 u = make_double2(widen(v.x) + widen(v.y), widen(v.z) + widen(v.w));
+  if (scale != 1.0) u = make_double2(u.x * scale, u.y * scale);
+  if (mask) {
+    const uchar2 m = mask[c];
+    if (m.x || m.y) {  // electrode cells keep the caller's values
+      double* o = reinterpret_cast<double*>(out + c);
+      if (!m.x) o[0] = u.x;
+      if (!m.y) o[1] = u.y;
+      return;
+    }
+  }
+  out[c] = u;
+}
+
 }  // namespace
 
 // CTA columns of the refinement pass along x and y (30 x 14 own columns
@@ -534,16 +519,23 @@ static long long ir_gx(const Box& b, bool paired) {
 static long long ir_gy(const Box& b) { return ((long long)b.ny + TY - 3) / (TY - 2); }
 
 // Grid of the refinement pass for z planes per CTA column `hint` (0:
-// automatic); *zchunk receives the planes used.  The automatic choice halves
+// automatic; halved for the two-cell kernel); *zchunk receives the planes
+// used.  The automatic choice halves
 // the z run while the grid has fewer than 8 * 152 * 3 CTAs (8 waves of three
 // 512-thread CTAs on each of GB300's 152 SMs) and the run is longer than 16
 // planes, so its CTA count is gx * gy when gx * gy >= 3648 and below
 // 3 * 3648 otherwise: at most max(gx * gy, 10944).
+static int ir_planes(int hint, bool paired) {
+  // a two-cell CTA covers twice the columns of a one-cell CTA: half the
+  // planes give it the same cells, so one tile setting suits both kernels
+  return paired ? std::max(1, hint / 2) : hint;
+}
+
 static dim3 ir_grid(const Box& b, int hint, int* zchunk, bool paired) {
   const long long gx = ir_gx(b, paired), gy = ir_gy(b);
   int zc = b.nz;
   if (hint > 0) {
-    zc = std::min(hint, b.nz);
+    zc = std::min(ir_planes(hint, paired), b.nz);
   } else {
     while (zc > 16 && gx * gy * (((long long)b.nz + zc - 1) / zc) < 8 * 152 * 3)
       zc = (zc + 1) / 2;
@@ -558,7 +550,7 @@ static long long ir_ctas(const Box& b, int zchunk) {
   long long most = 0;
   for (int paired = 0; paired < 2; ++paired) {
     int zc = b.nz;
-    if (zchunk > 0) zc = std::min(zchunk, b.nz);
+    if (zchunk > 0) zc = std::min(ir_planes(zchunk, paired != 0), b.nz);
     else ir_grid(b, 0, &zc, paired != 0);
     most = std::max(most, ir_gx(b, paired != 0) * ir_gy(b) * (((long long)b.nz + zc - 1) / zc));
   }
@@ -567,22 +559,25 @@ static long long ir_ctas(const Box& b, int zchunk) {
 
 int ir_partials(const Box& b, int zchunk) { return (int)ir_ctas(b, zchunk); }
 
-// The two-cell kernel runs the constant-coefficient operator (beta = 1);
-// it needs an even nx (whole pairs) and arrays on 16-byte boundaries (one
-// 16-byte load per pair; 2 bytes for the electrode flags).  With face
-// arrays the pair's 28 coefficient values leave no room to fetch them a
-// plane ahead in 64 registers, and the one-cell kernel, which does, is
-// faster (280 against 327 us per 256^3 step on GB300).
+// The two-cell kernel runs the constant-coefficient operator (beta = 1)
+// except the first pass of a solve (the norm of the zero guess as well); it
+// needs an even nx (whole pairs) and arrays on 16-byte boundaries (one
+// 16-byte load per pair; 2 bytes for the electrode flags).  With face arrays
+// the pair's 28 coefficient values leave no room to fetch them a plane ahead
+// in 64 registers, and the one-cell kernel, which does, is faster (280
+// against 327 us per 256^3 step on GB300); the first pass spills in 64
+// registers and is faster one cell per thread too (2.9 against 2.4 ms at
+// 512^3).
 static bool ir_pairable(const IrArgs& a) {
   auto al = [](const void* p, unsigned m) { return ((uintptr_t)p & (m - 1)) == 0; };
-  return !a.op.cxd && a.op.b.nx % 2 == 0 && al(a.udf_in, 16) && al(a.udf_out, 16) &&
-         al(a.bdf, 16) && al(a.bdf_out, 16) && al(a.u_in, 16) && al(a.rhs, 16) &&
-         al(a.op.mask, 2);
+  return !a.op.cxd && !a.partial_z && a.op.b.nx % 2 == 0 && al(a.udf_in, 16) &&
+         al(a.udf_out, 16) && al(a.bdf, 16) && al(a.bdf_out, 16) && al(a.u_in, 16) &&
+         al(a.rhs, 16) && al(a.op.mask, 2);
 }
 
 template <bool P, bool F, bool E, bool U, int B, bool Z>
 static void go(const IrArgs& a, dim3 g, cudaStream_t s) {
-  if (P) k_ir_df2<E, U, B, Z><<<g, NT, 0, s>>>(a);
+  if (P && !Z) k_ir_df2<E, U, B><<<g, NT, 0, s>>>(a);
   else k_ir_df<F, E, U, B, Z><<<g, NT, 0, s>>>(a);
 }
 
@@ -643,7 +638,15 @@ int launch_ir_fused(const IrArgs& args, cudaStream_t s) {
 
 void launch_df_to_f64(const float2* in, const uint8_t* mask, double* out, long long n,
                       double scale, cudaStream_t s) {
-  k_df_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, mask, out, n, scale);
+  auto al = [](const void* p, unsigned m) { return ((uintptr_t)p & (m - 1)) == 0; };
+  if (n % 2 == 0 && al(in, 16) && al(out, 16) && al(mask, 2)) {
+    const long long np = n / 2;
+    k_df_to_f64x2<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<const float4*>(in), reinterpret_cast<const uchar2*>(mask),
+        reinterpret_cast<double2*>(out), np, scale);
+  } else {
+    k_df_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, mask, out, n, scale);
+  }
   add_launches(1);
 }
 

@@ -259,15 +259,16 @@ __global__ void k_gj_elim(double* M, int n, int p, const double* rowp, const dou
 
 // b = f * scale + Dirichlet lifts 2 beta_c g / h^2, with g = bval[face] or,
 // when faces != nullptr, the packed per-face-cell values.
+// One row (j = blockIdx.y, k = blockIdx.z) per grid row, x across threads:
+// no 64-bit index division per cell.
 __global__ void k_rhs64(const double* f, double scale, const double* beta, const uint8_t* mask,
                         Box b, double ih2, Dir6 dir, Val6 bval, const double* faces,
                         double* out) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= b.n()) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  if (i >= b.nx) return;
+  const long long c = cidx(b, i, j, k);
   if (mask && mask[c]) { out[c] = 0.0; return; }
-  const int i = (int)(c % b.nx);
-  const long long jk = c / b.nx;
-  const int j = (int)(jk % b.ny), k = (int)(jk / b.ny);
   double v = f[c] * scale;
   const double bc = beta ? beta[c] : 1.0;
   auto g = [&](int face) -> double {
@@ -564,8 +565,8 @@ void launch_rhs64(const double* f, double scale, const double* beta, const uint8
                   const double* faces, double* out, cudaStream_t s) {
   Val6 v;
   for (int q = 0; q < 6; ++q) v.v[q] = bval[q];
-  k_rhs64<<<blocks_for(b.n()), kThreads, 0, s>>>(f, scale, beta, mask, b, ih2, to_dir(dir), v,
-                                                  faces, out);
+  dim3 g(blocks_for(b.nx), b.ny, b.nz);
+  k_rhs64<<<g, kThreads, 0, s>>>(f, scale, beta, mask, b, ih2, to_dir(dir), v, faces, out);
   add_launches(1);
 }
 

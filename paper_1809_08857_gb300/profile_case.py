@@ -4,6 +4,9 @@
       one mixed-precision Poisson + 3 Helmholtz set at 256^3 (arrays of
       128 MiB each, larger than the 129 MB L2), concurrency 1, no graphs, so
       kernel launches are individually visible;
+  python -m paper_1809_08857_gb300.profile_case --case set512
+      one solve set at 512^3 with the benchmark's options, one problem at a
+      time, no graphs, after an untimed set; prints libmg's launch counts;
   python -m paper_1809_08857_gb300.profile_case --case unet64
       one U-Net training step on a batch of 2 crops of 64^3;
   python -m paper_1809_08857_gb300.profile_case --case amr256
@@ -40,6 +43,36 @@ def solve256():
     st = s.solve_set(rho, phi, S, psi, W.helmholtz_kappas(), 1e-10)
     torch.cuda.synchronize()
     print("steps", [x["cycles"] for x in st])
+    s.close()
+
+
+def set512():
+    """One solve set at 512^3 with the options the benchmark times (V(2,1),
+    4 inner V-cycles with the last step trimmed, 128-plane refinement tile),
+    one problem at a time and without graphs so that every launch is
+    visible: a first set builds the coarse inverses, then the set to
+    profile.  Prints libmg's launch counts before and during that set (the
+    -s / -c of an ncu launch list filtered to libmg's kernels)."""
+    n = 512
+    h = 1.0 / n
+    rho = torch.from_numpy(W.streamer_shell(n, 0)).cuda()
+    eps = torch.from_numpy(W.dielectric_slab(n)).cuda()
+    S = torch.from_numpy(W.ionization_source(n, 0)).cuda()
+    s = mg.Solver((n, n, n), h, eps_r=eps, precision=mg.MG_PREC_MIXED, nu1=2, nu2=1,
+                  inner_cycles=4, concurrency=1, graphs=False)
+    s.set_options(ir_zchunk=128)
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    psi = [torch.zeros_like(phi) for _ in range(3)]
+    s.solve_set(rho, phi, S, psi, W.helmholtz_kappas(), 1e-10)
+    torch.cuda.synchronize()
+    l0 = mg.launch_count()
+    phi.zero_()
+    for p in psi:
+        p.zero_()
+    st = s.solve_set(rho, phi, S, psi, W.helmholtz_kappas(), 1e-10)
+    torch.cuda.synchronize()
+    print("launches_before", l0, "launches_set", mg.launch_count() - l0)
+    print("steps", [x["cycles"] for x in st], "vcycles", [x["vcycles"] for x in st])
     s.close()
 
 
@@ -105,7 +138,8 @@ def conv_shapes():
 
 def main():
     ap = argparse.ArgumentParser()
-    cases = {"solve256": solve256, "unet64": unet64, "amr256": amr256, "conv128": conv128,
+    cases = {"solve256": solve256, "set512": set512, "unet64": unet64, "amr256": amr256,
+             "conv128": conv128,
              "conv_shapes": conv_shapes}
     ap.add_argument("--case", choices=sorted(cases), required=True)
     args = ap.parse_args()

@@ -39,15 +39,23 @@ def test_trained_warm_start_gain(mg):
     held = WS.episode(n, 99, 10)
     net = mg.UNet(seed=0)
     net.set_scales(*WS.scales(train_eps))
+    # a fixed validation batch: the whole 64^3 field of every held-out step
+    # (the mini-batch losses of training vary several-fold from crop to crop)
+    val = [torch.stack([held[k][q] for k in range(1, len(held))]).contiguous() for q in (2,)]
+    val_prev = torch.stack([held[k - 1][1] for k in range(1, len(held))]).contiguous()
+    val_phi = torch.stack([held[k][1] for k in range(1, len(held))]).contiguous()
+    _, loss_before = net.grads(val[0], val_prev, val_phi)
     losses = WS.train(net, train_eps, iters=300, crop=32, batch=4, lr=1e-3)
-    assert np.mean(losses[-30:]) < np.mean(losses[:30])
+    _, loss_after = net.grads(val[0], val_prev, val_phi)
+    assert loss_after < loss_before, (loss_before, loss_after)
     res = WS.evaluate(net, held, n)
     print("warm start:", json.dumps(res))
     report = os.environ.get("MG_WARMSTART_REPORT")  # optional JSON report path
     if report:
         with open(report, "w") as fh:
             json.dump(dict(res, loss_first=float(np.mean(losses[:30])),
-                           loss_last=float(np.mean(losses[-30:]))), fh)
+                           loss_last=float(np.mean(losses[-30:])),
+                           val_loss_before=loss_before, val_loss_after=loss_after), fh)
     assert res["max_rel_diff"] <= 1e-9
     # the trained network's guess is closer to the answer than phi_{n-1}
     assert res["err_net"] < res["err_plain"]
