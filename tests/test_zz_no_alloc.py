@@ -21,7 +21,10 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-NORM_RTOL = 1e-12  # the solver reports the same kernel's norm in the same order
+# the solver's first pass sums r^2 one cell per thread, this entry point
+# (constant coefficients, even nx, aligned arrays) two cells per thread: the
+# same r, FP32 per-thread sums in another order
+NORM_RTOL = 1e-6
 # against the oracle: r in double-float arithmetic, rounded to FP32 and squared
 # and summed per thread in FP32 (about 2^-24 relative per term)
 ORACLE_RTOL = 1e-6
