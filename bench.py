@@ -251,7 +251,7 @@ KERNEL_SOURCES = {
     "smooth": ["paper_1809_08857_gb300/csrc/mg_split32.cu"],
     "restrict": ["paper_1809_08857_gb300/csrc/mg_split32.cu"],
     "prolong": ["paper_1809_08857_gb300/csrc/mg_split32.cu"],
-    "resid64": ["paper_1809_08857_gb300/csrc/mg_ir.cu"],
+    "resid64": ["paper_1809_08857_gb300/csrc/mg_ir.cu", "paper_1809_08857_gb300/csrc/df.cuh"],
 }
 
 
