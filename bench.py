@@ -65,6 +65,9 @@ def parse():
                     help="skip the 256^3 parent + 16 sub-box pass among the extras")
     ap.add_argument("--no-needle", action="store_true",
                     help="skip the 896^3 needle-plane set among the extras")
+    ap.add_argument("--coarse-visits", type=int, default=0,
+                    help="V-cycles on the first coarse level per finest-level cycle "
+                         "(0 = the library default, one)")
     ap.add_argument("--no-fp64-leg", action="store_true",
                     help="skip the FP64-mode GPU solve set among the extras")
     return ap.parse_args()
@@ -678,6 +681,8 @@ def run_ours(args):
         cache = os.path.join(_tf.gettempdir(), f"mg_autotune_rank{rank}.json")
         tuned, _ = autotune.tuned(solver, rho, S, KAPPAS, TOL, has_eps=True, precision=prec,
                                   cache_path=cache)
+    if args.coarse_visits:
+        solver.set_options(coarse_visits=args.coarse_visits)
     phi = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
     psi = [torch.zeros_like(phi) for _ in range(3)]
     cycles = [0, 0, 0, 0]
@@ -838,7 +843,8 @@ def run_ours(args):
             "data": "synthetic (seeded streamer shell, dielectric slab, smoothed ionisation source)",
             "config": dict(config(args), autotuned=tuned, nu1=solver.options.nu1,
                            nu2=solver.options.nu2, inner_cycles=solver.options.inner_cycles,
-                           ir_zchunk=solver.options.ir_zchunk),
+                           ir_zchunk=solver.options.ir_zchunk,
+                           coarse_visits=max(1, solver.options.coarse_visits)),
             "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": launches, "cycles_per_problem": cycles,
             "residual_per_step": history,

@@ -53,7 +53,11 @@ typedef enum {
   MG_ERR_OOM = 3,           /* device allocation failed */
   MG_ERR_NOT_CONVERGED = 4, /* max_cycles reached; outputs hold the last iterate */
   MG_ERR_NONFINITE = 5,     /* NaN/Inf in the input or the residual */
-  MG_ERR_UNSUPPORTED = 6    /* valid request this build does not implement */
+  MG_ERR_UNSUPPORTED = 6,   /* valid request this build does not implement */
+  MG_ERR_DIVERGED = 7       /* the relative residual rose at each of the last
+                               three cycles (steps, FAC iterations) and is over
+                               twice what it was three cycles earlier; outputs
+                               hold the last iterate */
 } mg_status;
 
 typedef enum { MG_BC_DIRICHLET = 0, MG_BC_NEUMANN = 1 } mg_bc_kind;
@@ -130,6 +134,11 @@ typedef struct {
                        weaker) reaches tol in fewer than inner_cycles
                        V-cycles runs only that many; 1 = every step runs
                        inner_cycles (0) */
+  int coarse_visits; /* cycles on the first coarse level per cycle of the
+                       finest level: 0 or 1 (a V-cycle), 2 (two V-cycles
+                       there: the rate of a W-cycle on a layered medium whose
+                       interfaces cut the coarse cells, for about 20 % more
+                       work per cycle) (0) */
 } mg_options;
 
 /* Per-solve statistics.  hist[c] is the relative residual after c cycles
@@ -145,6 +154,7 @@ typedef struct {
   int vcycles;      /* V-cycles run: FP64 mode = cycles; mixed mode = the inner
                        V-cycles of all refinement steps; composite AMR solve =
                        FAC iterations x inner V-cycles (per box) */
+  int diverged;     /* 1 if the solve stopped with MG_ERR_DIVERGED */
 } mg_stats;
 
 /* Fill *opt with the defaults. */
@@ -180,7 +190,9 @@ mg_status mg_create(const mg_grid* grid, const double* eps_r, const uint8_t* mas
  *   tol  stop when the relative residual <= tol (e.g. 1e-10).
  *   stats  nullable; receives cycles, residual history and device time.
  * Returns MG_ERR_NOT_CONVERGED (phi holds the last iterate) if max_cycles is
- * reached, MG_ERR_NONFINITE if the residual is NaN/Inf.
+ * reached, MG_ERR_DIVERGED (phi holds the last iterate) if the residual rose
+ * over three cycles and doubled, MG_ERR_NONFINITE if the residual is NaN/Inf.
+ * The other solve calls return the same three statuses.
  */
 mg_status mg_solve_poisson(mg_ctx* ctx, const double* rho, double* phi, double tol,
                            mg_stats* stats);

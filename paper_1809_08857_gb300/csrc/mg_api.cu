@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "../../include/mg.h"
+#include "mg_diverge.h"
 #include "mg_internal.h"
 
 namespace {
@@ -140,7 +141,8 @@ struct Work {
   float2* udf[2] = {nullptr, nullptr};
   float2* bdf = nullptr;
   double* partial = nullptr;
-  // [2], pinned; norm_map is its device-side address: the reduction kernel
+  // [3] ([0], [1] norms, [2] the zero-guess flag), pinned; norm_map is its
+  // device-side address: the reduction kernel
   // stores the norms there itself, so no copy engine is involved (a small
   // device-to-host copy per step waits behind any bulk download in flight,
   // e.g. the previous time step's answers)
@@ -377,7 +379,8 @@ mg_status get_work(mg_ctx* c, int q, Work** out) {
         if (l == nlev - 1) MG_TRY(c->alloc(&w->lw[l].r32[col], ns, true));
       }
     MG_TRY(c->alloc(&w->partial, 2 * (size_t)c->npartial));
-    MG_CUDA(cudaMallocHost((void**)&w->norm_host, 2 * sizeof(double)));
+    // [0], [1]: norms; [2]: the zero-guess flag
+    MG_CUDA(cudaMallocHost((void**)&w->norm_host, 3 * sizeof(double)));
     c->host_allocs.push_back(w->norm_host);
     MG_CUDA(cudaHostGetDevicePointer((void**)&w->norm_map, w->norm_host, 0));
     // the zero fills above ran on the context's stream
@@ -385,6 +388,21 @@ mg_status get_work(mg_ctx* c, int q, Work** out) {
   }
   *out = c->work[q];
   return MG_OK;
+}
+
+// Cycles on the first coarse level per cycle of the finest level.  On a
+// layered medium whose interfaces cut the coarse cells (the dielectric slab),
+// one V-cycle from level 1 down leaves the finest level's two-grid correction
+// inexact and the fine cycle contracts by 0.16-0.23; two V-cycles there give
+// 0.09 (a CPU prototype of the cycle at 64^3 and 128^3: the same rate as a
+// full W-cycle, whose deeper revisits add nothing), for about 20 % more work
+// per cycle.  The default stays one: with two, the mixed-precision Poisson
+// solve of the 512^3 gap problem meets tol in as many refinement steps but
+// lands closer to it, and there the error of the answer is 30 times its
+// relative residual (3e-9 at 1e-10).
+int coarse_visits(const mg_ctx* c, int l) {
+  if (l != 0 || c->lv.size() < 3) return 1;
+  return c->opt.coarse_visits > 1 ? c->opt.coarse_visits : 1;
 }
 
 // ---- FP64 V-cycle (natural layout) ----------------------------------------
@@ -422,7 +440,8 @@ mg_status vcycle64(mg_ctx* c, Kind kind, double alpha, int l, const double* f, d
     Scope sc(c, s, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE, n * (16.0 + fb + 2.0));
     mg::launch_resid_restrict64(op, alpha, f, u, C.f64, C.u64, s);
   }
-  MG_TRY(vcycle64(c, kind, alpha, l + 1, C.f64, C.u64));
+  for (int q = coarse_visits(c, l); q > 0; --q)
+    MG_TRY(vcycle64(c, kind, alpha, l + 1, C.f64, C.u64));
   {
     Scope sc(c, s, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE, n * (16.0 + 1.0 + fb));
     mg::launch_prolong64(op, op64(c, l + 1, kind, alpha), C.u64, u, s);
@@ -489,7 +508,8 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
     else
       mg::launch_resid_restrict32s(op, cop, a32, cp(X.f32), cp(X.u32), mp(Y.f32), mp(Y.u32), s);
   }
-  MG_TRY(vcycle32(c, w, kind, alpha, l + 1, true));
+  const int visits = coarse_visits(c, l);
+  for (int q = 0; q < visits; ++q) MG_TRY(vcycle32(c, w, kind, alpha, l + 1, q == 0));
   {
     // nu2 >= 1: the post-smoothing starts with a red half-sweep, so only
     // black cells take the correction.  Fine black u read + write, coarse
@@ -528,6 +548,7 @@ struct IrIo {
   bool store_r = false;
   bool znorm = false;
   double in_scale = 1.0;  // FP64 inputs (b64, u64) multiplied by this power of two on load
+  bool zero_guess = false;  // first pass of a zero guess without electrodes (pointwise)
 };
 
 // Enqueue one fused refinement pass on level 0 and the read-back of ||r||^2
@@ -565,7 +586,11 @@ mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha
                             (io.with_e ? 4.0 : 0.0) + (io.udf_out ? 8.0 : 0.0) +
                             (io.bdf_out ? 8.0 : 0.0) + (io.store_r ? 4.0 : 0.0));
   int nparts;
-  {
+  if (io.zero_guess) {
+    // b read, b and the zero iterate written as double-floats, r written
+    Scope sc(c, s, MG_KCLASS_RESID64, n * (8.0 + 8.0 + 8.0 + 4.0));
+    nparts = mg::launch_first_zero(a, c->npartial, s);
+  } else {
     Scope sc(c, s, MG_KCLASS_RESID64, bytes);
     nparts = mg::launch_ir_fused(a, s);
   }
@@ -601,6 +626,9 @@ struct Prob {
   // mixed precision: the problem is solved for s u (s a power of two, 1
   // unless b's magnitude is far from 1; see rescale)
   double scale = 1.0;
+  bool zero_guess = false;  // the guess is 0 and the grid has no electrode cells
+  mg::Growth growth;        // divergence rule over the relative residuals
+  bool diverged = false;
   int phase = 0;
   bool done = false;
   mg_status status = MG_OK;
@@ -613,7 +641,12 @@ struct Prob {
 // taken 15 % weaker in its logarithm, so that a step that varies a little
 // from the last one still lands below tol; if it does not, the step after it
 // runs the full count again.  The fixed point and the tolerance test are
-// unchanged: only the number of V-cycles in the last step can shrink.
+// unchanged: only the number of V-cycles in the last step can shrink.  (An
+// answer that meets tol is as close to the exact discrete solution as its
+// problem's conditioning allows: the error of the 512^3 gap Poisson answer is
+// up to 30 times its relative residual, since the boundary lift dominates
+// ||b||; a stricter aim than tol removed every trimmed V-cycle of the
+// benchmark's set.)
 int next_inner_cycles(const Prob& p) {
   const int full = p.c->opt.inner_cycles;
   if (p.c->opt.fixed_cycles || p.cyc < 2 || p.ic_last < 1 || !(p.rel_prev > 0.0) ||
@@ -796,9 +829,10 @@ mg_status finish(Prob& p) {
     p.status = MG_ERR_NONFINITE;
     g_last_error = "non-finite value in input or residual";
   } else if (p.rel > p.tol) {
-    p.status = MG_ERR_NOT_CONVERGED;
+    p.status = p.diverged ? MG_ERR_DIVERGED : MG_ERR_NOT_CONVERGED;
     char msg[128];
-    std::snprintf(msg, sizeof msg, "not converged: rel. residual %.3e after %d steps", p.rel, p.cyc);
+    std::snprintf(msg, sizeof msg, "%s: rel. residual %.3e after %d steps",
+                  p.diverged ? "diverged" : "not converged", p.rel, p.cyc);
     g_last_error = msg;
   }
   return MG_OK;
@@ -817,6 +851,7 @@ mg_status enqueue_first(Prob& p) {
   r0.store_r = true;
   r0.znorm = true;
   r0.in_scale = p.scale;
+  r0.zero_guess = p.zero_guess;
   MG_TRY(enqueue_ir(p.c, w, w->s, p.kind, p.alpha, r0, 1));
   MG_CUDA(cudaEventRecord(w->ev, w->s));
   return MG_OK;
@@ -887,7 +922,9 @@ mg_status advance(Prob& p) {
   p.rel_prev = p.rel;
   p.rel = std::sqrt(h[1]) / p.bnorm;
   if (p.st && p.cyc < 64) p.st->hist[p.cyc] = p.rel;
-  if (!std::isfinite(p.rel) || p.rel <= p.tol || p.cyc >= p.c->opt.max_cycles) return finish(p);
+  p.diverged = p.growth.push(p.rel) && p.rel > p.tol;
+  if (!std::isfinite(p.rel) || p.rel <= p.tol || p.cyc >= p.c->opt.max_cycles || p.diverged)
+    return finish(p);
   p.ic_last = p.ic;
   p.ic = next_inner_cycles(p);
   return enqueue_step(p);
@@ -927,6 +964,19 @@ mg_status solve_mixed(std::vector<Prob>& P) {
     p.cur = w->udf[0];
     p.other = w->udf[1];
     p.ic = p.c->opt.inner_cycles;
+    // a zero guess on a grid without electrode cells (a cold start) has
+    // residual b: its first pass is pointwise (checked on the device)
+    if (!p.c->lv[0].mask) {
+      w->norm_host[2] = 0.0;
+      Scope sc(p.c, w->s, MG_KCLASS_COARSE, 0);
+      mg::launch_nonzero(p.u, p.c->lv[0].b.n(), w->norm_map + 2, w->s);
+    }
+  }
+  for (Prob& p : P) {
+    if (!p.c->lv[0].mask) {
+      MG_CUDA(cudaStreamSynchronize(p.w->s));
+      p.zero_guess = p.w->norm_host[2] == 0.0;
+    }
     // ||b|| (slot 0) and the residual of the initial guess (slot 1, r -> FP32)
     MG_TRY(enqueue_first(p));
   }
@@ -954,6 +1004,7 @@ mg_status solve_mixed(std::vector<Prob>& P) {
       p.st->vcycles = p.vcycles;
       p.st->rel_resid = p.rel;
       p.st->converged = p.rel <= p.tol;
+      p.st->diverged = p.diverged;
       p.st->time_ms = ms;
     }
     if (p.status == MG_ERR_NONFINITE || (p.status != MG_OK && worst == MG_OK)) worst = p.status;
@@ -991,12 +1042,14 @@ mg_status solve_fp64(Prob& p) {
   if (p.bnorm == 0.0) p.bnorm = 1.0;
   p.rel = std::sqrt(w->norm_host[1]) / p.bnorm;
   if (p.st) p.st->hist[0] = p.rel;
-  while (std::isfinite(p.rel) && p.rel > p.tol && p.cyc < c->opt.max_cycles) {
+  p.growth.push(p.rel);
+  while (std::isfinite(p.rel) && p.rel > p.tol && p.cyc < c->opt.max_cycles && !p.diverged) {
     MG_TRY(vcycle64(c, p.kind, p.alpha, 0, p.b, p.u));
     MG_TRY(norms(false));
     p.rel = std::sqrt(w->norm_host[1]) / p.bnorm;
     ++p.cyc;
     if (p.st && p.cyc < 64) p.st->hist[p.cyc] = p.rel;
+    p.diverged = p.growth.push(p.rel) && p.rel > p.tol;
   }
   if (p.st) {
     MG_CUDA(cudaEventRecord(w->t1, s));
@@ -1007,13 +1060,15 @@ mg_status solve_fp64(Prob& p) {
     p.st->vcycles = p.cyc;
     p.st->rel_resid = p.rel;
     p.st->converged = p.rel <= p.tol;
+    p.st->diverged = p.diverged;
     p.st->time_ms = ms;
   }
   if (!std::isfinite(p.rel)) return fail(MG_ERR_NONFINITE, "non-finite residual");
   if (p.rel > p.tol) {
     char msg[128];
-    std::snprintf(msg, sizeof msg, "not converged: rel. residual %.3e after %d cycles", p.rel, p.cyc);
-    return fail(MG_ERR_NOT_CONVERGED, msg);
+    std::snprintf(msg, sizeof msg, "%s: rel. residual %.3e after %d cycles",
+                  p.diverged ? "diverged" : "not converged", p.rel, p.cyc);
+    return fail(p.diverged ? MG_ERR_DIVERGED : MG_ERR_NOT_CONVERGED, msg);
   }
   return MG_OK;
 }
@@ -1222,6 +1277,9 @@ mg_status normalise_options(const mg_options* in, mg_options* out) {
   if (in->fixed_cycles != 0 && in->fixed_cycles != 1)
     return fail(MG_ERR_INVALID_ARG, "fixed_cycles must be 0 or 1");
   out->fixed_cycles = in->fixed_cycles;
+  if (in->coarse_visits < 0 || in->coarse_visits > 2)
+    return fail(MG_ERR_INVALID_ARG, "coarse_visits must be 0, 1 or 2");
+  out->coarse_visits = in->coarse_visits;
   return MG_OK;
 }
 
@@ -1771,7 +1829,10 @@ mg_status amr_solve(mg_amr* a, int kind_in, double param, const double* const* r
   if (bnorm == 0.0) bnorm = 1.0;
   if (st) st->hist[0] = rel;
   int cyc = 0;
-  while (std::isfinite(rel) && rel > tol && cyc < a->opt.max_cycles) {
+  mg::Growth growth;
+  growth.push(rel);
+  bool diverged = false;
+  while (std::isfinite(rel) && rel > tol && cyc < a->opt.max_cycles && !diverged) {
     for (int l = 0; l < a->nlev; ++l) {
       if (l > 0) MG_TRY(amr_pass(a, kind, alpha, l, false, false));
       for (size_t q = 0; q < a->box.size(); ++q)
@@ -1783,6 +1844,7 @@ mg_status amr_solve(mg_amr* a, int kind_in, double param, const double* const* r
     rel = std::sqrt(a->norm_host[1]) / bnorm;
     ++cyc;
     if (st && cyc < 64) st->hist[cyc] = rel;
+    diverged = growth.push(rel) && rel > tol;
   }
   // covered cells: the mean of their children, finest level first
   for (int lev = a->nlev - 1; lev >= 1; --lev)
@@ -1802,14 +1864,15 @@ mg_status amr_solve(mg_amr* a, int kind_in, double param, const double* const* r
     st->vcycles = cyc * a->opt.inner_cycles;  // per box of every level
     st->rel_resid = rel;
     st->converged = rel <= tol;
+    st->diverged = diverged;
     st->time_ms = ms;
   }
   if (!std::isfinite(rel)) return fail(MG_ERR_NONFINITE, "non-finite value in input or residual");
   if (rel > tol) {
     char msg[128];
-    std::snprintf(msg, sizeof msg, "not converged: rel. residual %.3e after %d iterations", rel,
-                  cyc);
-    return fail(MG_ERR_NOT_CONVERGED, msg);
+    std::snprintf(msg, sizeof msg, "%s: rel. residual %.3e after %d iterations",
+                  diverged ? "diverged" : "not converged", rel, cyc);
+    return fail(diverged ? MG_ERR_DIVERGED : MG_ERR_NOT_CONVERGED, msg);
   }
   return MG_OK;
 }
@@ -2301,6 +2364,7 @@ const char* mg_error_string(mg_status s) {
     case MG_ERR_NOT_CONVERGED: return "not converged within max_cycles";
     case MG_ERR_NONFINITE: return "non-finite value in input or residual";
     case MG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MG_ERR_DIVERGED: return "diverged: the residual grew over three cycles";
   }
   return "unknown status";
 }

@@ -240,6 +240,12 @@ void launch_efield(const double* phi, const uint8_t* mask, Box b, double h, cons
 // squared residual of the zero guess when a.partial_z is set).
 // Returns the thread blocks launched (= per-block partial sums written).
 int launch_ir_fused(const IrArgs& a, cudaStream_t s);
+// *flag (device address of mapped host memory) = 1.0 if any u[c] != 0.
+void launch_nonzero(const double* u, long long n, double* flag, cudaStream_t s);
+// The first pass for a zero guess on a grid without electrodes (pointwise:
+// r = b); uses a.rhs, a.in_scale, a.bdf_out, a.udf_out, a.r, a.W, a.partial,
+// a.partial_z; at most max_blocks blocks.  Returns the blocks launched.
+int launch_first_zero(const IrArgs& a, int max_blocks, cudaStream_t s);
 // out = (hi + lo) * scale in FP64 (the final iterate of a mixed-precision
 // solve; scale a power of two); electrode cells (mask nonzero, nullable) are
 // left as they are

@@ -474,6 +474,57 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
   }
 }
 
+// 1.0 into *flag (mapped host memory) if any of u[0..n) is neither +0 nor -0
+// (a NaN counts as nonzero); at most one store per block.
+__global__ void k_nonzero(const double* __restrict__ u, long long n, double* flag) {
+  bool nz = false;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x)
+    nz |= !(u[c] == 0.0);
+  if (__syncthreads_or(nz) && threadIdx.x == 0) *flag = 1.0;
+}
+
+// First pass of a solve from a zero guess on a grid without electrode cells:
+// the residual is b itself, so the pass is pointwise.  b (times in_scale) as
+// double-floats into bdf_out, the zero iterate into udf_out, r = b rounded to
+// FP32 (the value the stencil pass forms for this guess: hi + lo) into the
+// split arrays r, and per-block sums of r^2 into partial and partial_z (the
+// zero guess's residual is the same r).  Blocks take rows (j, k) in turn.
+__global__ void __launch_bounds__(256) k_first_zero(IrArgs a) {
+  __shared__ float red[8];
+  const int nx = a.op.b.nx, ny = a.op.b.ny;
+  const long long rows = (long long)ny * a.op.b.nz;
+  float ss = 0.0f;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = (int)(row % ny), k = (int)(row / ny);
+    const long long base = row * nx, rbase = row * a.W;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const long long c = base + i;
+      double bd = a.rhs[c];
+      if (a.in_scale != 1.0) bd *= a.in_scale;
+      const float2 bb = split_df(bd);
+      a.bdf_out[c] = bb;
+      a.udf_out[c] = make_float2(0.0f, 0.0f);
+      const float r = __fadd_rn(bb.x, bb.y);
+      (((i + j + k) & 1) ? a.r[1] : a.r[0])[rbase + (i >> 1)] = r;
+      ss = fmaf(r, r, ss);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < 8 ? (double)red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+      a.partial[blockIdx.x] = v;
+      a.partial_z[blockIdx.x] = v;
+    }
+  }
+}
+
 // FP64 result of a double-float iterate: exact widening of both parts on
 // the integer pipe, one FP64 add, times the power-of-two scale that undoes a
 // scaled solve (exact).  Electrode cells keep the caller's value.
@@ -634,6 +685,21 @@ int launch_ir_fused(const IrArgs& args, cudaStream_t s) {
   dispatch(a, g, paired, s);
   add_launches(1);
   return (int)(g.x * g.y * g.z);
+}
+
+void launch_nonzero(const double* u, long long n, double* flag, cudaStream_t s) {
+  k_nonzero<<<152 * 8, 256, 0, s>>>(u, n, flag);
+  add_launches(1);
+}
+
+int launch_first_zero(const IrArgs& args, int max_blocks, cudaStream_t s) {
+  IrArgs a = args;
+  if (a.in_scale == 0.0) a.in_scale = 1.0;
+  const long long rows = (long long)a.op.b.ny * a.op.b.nz;
+  const int g = (int)std::max(1LL, std::min<long long>(rows, max_blocks));
+  k_first_zero<<<g, 256, 0, s>>>(a);
+  add_launches(1);
+  return g;
 }
 
 void launch_df_to_f64(const float2* in, const uint8_t* mask, double* out, long long n,

@@ -20,6 +20,9 @@ MG_ERR_OOM = 3
 MG_ERR_NOT_CONVERGED = 4
 MG_ERR_NONFINITE = 5
 MG_ERR_UNSUPPORTED = 6
+MG_ERR_DIVERGED = 7
+# statuses a solve call returns with its outputs holding the last iterate
+_NONCONVERGED = (MG_ERR_NOT_CONVERGED, MG_ERR_DIVERGED)
 
 MG_BC_DIRICHLET = 0
 MG_BC_NEUMANN = 1
@@ -68,19 +71,22 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("concurrency", ctypes.c_int), ("no_graphs", ctypes.c_int),
                 ("rte_bc", ctypes.c_int), ("ir_zchunk", ctypes.c_int),
-                ("coarse_op", ctypes.c_int), ("fixed_cycles", ctypes.c_int)]
+                ("coarse_op", ctypes.c_int), ("fixed_cycles", ctypes.c_int),
+                ("coarse_visits", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("converged", ctypes.c_int),
                 ("rel_resid", ctypes.c_double), ("time_ms", ctypes.c_double),
-                ("hist", ctypes.c_double * 64), ("vcycles", ctypes.c_int)]
+                ("hist", ctypes.c_double * 64), ("vcycles", ctypes.c_int),
+                ("diverged", ctypes.c_int)]
 
     def as_dict(self):
         n = min(self.cycles + 1, 64)
         return {"cycles": self.cycles, "converged": bool(self.converged),
                 "rel_resid": self.rel_resid, "time_ms": self.time_ms,
-                "hist": list(self.hist[:n]), "vcycles": self.vcycles}
+                "hist": list(self.hist[:n]), "vcycles": self.vcycles,
+                "diverged": bool(self.diverged)}
 
 
 class Problem(ctypes.Structure):
@@ -305,7 +311,7 @@ def solve_batch(problems, tol=1e-10, raise_on_nonconvergence=True):
                          _ptr(pr["u"], torch.float64).value, float(pr.get("alpha", 0.0)))
     st = (Stats * max(1, len(problems)))()
     status = lib.mg_solve_batch(arr, len(problems), float(tol), st)
-    _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+    _check(status, () if raise_on_nonconvergence else _NONCONVERGED)
     return [st[q].as_dict() for q in range(len(problems))]
 
 
@@ -467,7 +473,7 @@ class Solver:
         st = Stats()
         status = self._lib.mg_solve_poisson(self._ctx, _ptr(rho, torch.float64),
                                             _ptr(phi, torch.float64), float(tol), ctypes.byref(st))
-        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        _check(status, () if raise_on_nonconvergence else _NONCONVERGED)
         d = st.as_dict()
         d["status"] = status
         return d
@@ -497,7 +503,7 @@ class Solver:
         status = self._lib.mg_solve_screened(self._ctx, ctypes.c_double(float(alpha)),
                                              _ptr(f, torch.float64), _ptr(u, torch.float64),
                                              ctypes.c_double(float(tol)), ctypes.byref(st))
-        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        _check(status, () if raise_on_nonconvergence else _NONCONVERGED)
         d = st.as_dict()
         d["status"] = status
         return d
@@ -517,7 +523,7 @@ class Solver:
         st = (Stats * 3)()
         status = self._lib.mg_solve_helmholtz_batch(self._ctx, _ptr(S, torch.float64), ptrs, kap,
                                                     float(tol), st)
-        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        _check(status, () if raise_on_nonconvergence else _NONCONVERGED)
         return [s.as_dict() for s in st]
 
     def solve_photoionization(self, S, psi, kappa, amp, tol=1e-10,
@@ -538,7 +544,7 @@ class Solver:
         st = (Stats * 3)()
         status = self._lib.mg_solve_photoionization(self._ctx, _ptr(S, torch.float64), ptrs, kap,
                                                     am, float(tol), st)
-        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        _check(status, () if raise_on_nonconvergence else _NONCONVERGED)
         return [s.as_dict() for s in st]
 
     def residual_norms(self, kind, rhs, u, param=0.0):
@@ -569,7 +575,7 @@ class Solver:
         st = (Stats * 4)()
         status = self._lib.mg_solve_set(self._ctx, _ptr(rho, torch.float64), _ptr(phi, torch.float64),
                                         _ptr(S, torch.float64), ptrs, kap, float(tol), st)
-        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        _check(status, () if raise_on_nonconvergence else _NONCONVERGED)
         return [s.as_dict() for s in st]
 
     # ---- host-buffer convenience (end-to-end path) -------------------------
@@ -806,7 +812,7 @@ class Amr:
         st = Stats()
         status = self._lib.mg_amr_solve(self._amr, _KINDS[kind], float(param), self._arrays(rhs),
                                         self._arrays(u), float(tol), ctypes.byref(st))
-        _check(status, () if raise_on_nonconvergence else (MG_ERR_NOT_CONVERGED,))
+        _check(status, () if raise_on_nonconvergence else _NONCONVERGED)
         return st.as_dict()
 
     def residual(self, kind, rhs, u, param=0.0):

@@ -295,3 +295,39 @@ def test_trimmed_last_step_reaches_tol_with_fewer_vcycles(mg, set512, ref512):
         assert b["vcycles"] == 3 * b["cycles"]
     assert sum(x["vcycles"] for x in st[0]) < sum(x["vcycles"] for x in st[1]), (
         [x["vcycles"] for x in st[0]], [x["vcycles"] for x in st[1]])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_zero_and_nonzero_guess_first_pass(mg, prec):
+    """A cold start (zero guess, no electrode cells) takes a pointwise first
+    pass (the residual is b); a guess with one nonzero entry takes the
+    stencil pass.  Both reach the oracle's answer to 1e-9 and the zero guess
+    starts at relative residual exactly 1; a nonzero guess (the oracle's
+    answer plus a perturbation) converges to it too."""
+    n = 48
+    h = 1.0 / n
+    rho, eps, S = W.streamer_shell(n, 3), W.dielectric_slab(n), W.ionization_source(n, 3)
+    P = oracle.poisson((n, n, n), h, eps_r=eps)
+    ref, _, rel, _ = P.solve(rho / oracle.EPS0)
+    assert rel < 1e-12
+    refh = [oracle.helmholtz((n, n, n), h, k).solve(S)[0] for k in KAPPAS]
+    rng = np.random.default_rng(21)
+    guesses = {"zero": (np.zeros((n, n, n)), [np.zeros((n, n, n))] * 3)}
+    one = np.zeros((n, n, n))
+    one[7, 9, 11] = 1e-300
+    guesses["one entry"] = (one, [one] * 3)
+    guesses["near"] = (ref + 1e-3 * rng.standard_normal((n, n, n)),
+                       [r + 1e-3 * rng.standard_normal((n, n, n)) for r in refh])
+    s = mg.Solver((n, n, n), h, eps_r=torch.from_numpy(eps).cuda(), precision=prec)
+    for name, (g, gh) in guesses.items():
+        phi = torch.from_numpy(g.copy()).cuda()
+        psi = [torch.from_numpy(x.copy()).cuda() for x in gh]
+        st = s.solve_set(torch.from_numpy(rho).cuda(), phi, torch.from_numpy(S).cuda(), psi,
+                         KAPPAS, TOL)
+        assert all(x["converged"] for x in st), name
+        if name == "zero":
+            assert all(x["hist"][0] == 1.0 for x in st)
+        assert oracle.rel_l2(phi.cpu().numpy(), ref) <= PARITY, name
+        for p, r in zip(psi, refh):
+            assert oracle.rel_l2(p.cpu().numpy(), r) <= PARITY, name
+    s.close()
