@@ -1010,6 +1010,8 @@ mg_status solve_mixed(std::vector<Prob>& P) {
     if (p.status == MG_ERR_NONFINITE || (p.status != MG_OK && worst == MG_OK)) worst = p.status;
   }
   for (mg_ctx* c : ctxs) harvest(c);
+  if (mg::sweep_timed_out())
+    return fail(MG_ERR_CUDA, "a staged half-sweep gave up waiting for a plane copy");
   if (worst == MG_ERR_NONFINITE) g_last_error = "non-finite value in input or residual";
   return worst;
 }
@@ -1855,6 +1857,8 @@ mg_status amr_solve(mg_amr* a, int kind_in, double param, const double* const* r
                              nullptr, 0, s);
     }
   MG_TRY(check_launch());
+  if (mixed && mg::sweep_timed_out())
+    return fail(MG_ERR_CUDA, "a staged half-sweep gave up waiting for a plane copy");
   if (st) {
     MG_CUDA(cudaEventRecord(a->t1, s));
     MG_CUDA(cudaEventSynchronize(a->t1));
@@ -1920,6 +1924,7 @@ mg_status mg_create(const mg_grid* grid, const double* eps_r, const uint8_t* mas
     destroy(c);
     return st;
   }
+  mg::sweep_kernels_ready();
   *out = c;
   return MG_OK;
 }

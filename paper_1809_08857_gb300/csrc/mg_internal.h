@@ -204,6 +204,12 @@ void launch_resid_norms64(const Op64& op, double alpha, const double* f, const d
 void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s);
 
 // ---- FP32 split-storage inner V-cycle (mg_split32.cu) -----------------------
+// True (and cleared) if a staged half-sweep gave up waiting for a plane since
+// the last call (synchronous read of a device flag).
+bool sweep_timed_out();
+// Sets the staged half-sweeps' shared-memory limits once; false if they
+// cannot run (the register-fed half-sweep is used then).
+bool sweep_kernels_ready();
 void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
                          const float* uo, bool zero_other, bool has_mask, cudaStream_t s);
 // Residual of the red cells only (needs nu1 >= 1: black residuals are 0).

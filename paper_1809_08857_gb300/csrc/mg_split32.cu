@@ -16,6 +16,10 @@
 // 2 b_c b_n / (b_c + b_n) is one add and one reciprocal: w = 1 / (hb_c +
 // hb_n); towards an electrode w = 1 / (2 hb_c); on a domain face
 // rho_f / hb_c.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
 #include "mg_internal.h"
 
 namespace mg {
@@ -33,6 +37,7 @@ __device__ __forceinline__ float* sel(const MPtr2& a, int c) { return c ? a.p[1]
 __device__ __forceinline__ const float* bsel(const Split32& op, int c) {
   return c ? op.beta[1] : op.beta[0];
 }
+inline const float* bsel_h(const Split32& op, int c) { return c ? op.beta[1] : op.beta[0]; }
 
 // face weight between a free cell (hb = hc) and an in-box neighbour (hn)
 __device__ __forceinline__ float wface(float hc, float hn) {
@@ -231,6 +236,246 @@ __global__ void __launch_bounds__(kT, 4) k_half_sweep_v4(Split32 op, float alpha
   const float4 v = s ? quad_update<VB, ZeroOther, HasMask, 1>(op, alpha, q, pp, ym, yp, zm, zp)
                      : quad_update<VB, ZeroOther, HasMask, 0>(op, alpha, q, pp, ym, yp, zm, zp);
   if (active) *reinterpret_cast<float4*>(u + t0) = v;
+}
+
+// ---- half-sweep with planes staged by the tensor memory accelerator ------
+//
+// The update of k_half_sweep_v4 (four packed cells per thread, a warp per
+// row of 128 packed cells, block 32 x 8), but a CTA marches through up to
+// kTmaZ planes of its 128 x 8 tile and every plane reaches shared memory by
+// a tiled tensor copy issued ahead of its use: the other colour's u and hb
+// with a halo of one row in y and four packed entries in x (the copy's x
+// start, p0 - 4, stays on a 16-byte boundary), and the own colour's f and
+// hb.  Plane k reads the other colour at k - 1, k and k + 1 (a ring of kRingO
+// slots keeps the next plane in flight) and its own colour at k (ring of
+// kRingW).  A thread's registers hold only the plane it updates, so the
+// copies in flight no longer compete with the arithmetic for registers (the
+// register-fed form keeps 14 float4 loads of one plane in flight and no
+// more).  Copies outside the level (halo rows and columns past the edge) are
+// filled with zeros and never enter a face weight; planes -1 and nz are not
+// copied at all (their barrier phase completes by a plain arrive).
+//
+// Every wait on a plane is bounded (kSweepWaitNs); a CTA that gives up sets
+// g_sweep_timeout, waits (bounded) for the copies it issued, and returns
+// without writing the rest of its planes.  The host reads the flag after
+// each solve.
+constexpr int kTmaZ = 32;      // planes per CTA
+constexpr int kRingO = 4;      // other-colour slots: planes k-1, k, k+1 and one in flight
+constexpr int kRingW = 2;      // own-colour slots: plane k and one in flight
+constexpr int kOX = 136;       // other-colour box: 128 + 2 x 4 packed entries
+constexpr int kOY = 10;        // rows: 8 + 2
+constexpr int kOArr = 5504;    // bytes of one other-colour array box (10 x 136 x 4), to 128
+constexpr int kWArr = 4096;    // bytes of one own-colour array box (8 x 128 x 4)
+constexpr unsigned long long kSweepWaitNs = 1000000000ull;  // 1 s
+constexpr long long kSweepWaitIters = 1ll << 24;
+
+__device__ unsigned g_sweep_timeout = 0;
+
+template <bool VB>
+struct TmaPlan {
+  static constexpr int kO = (VB ? 2 : 1) * kOArr;  // one other-colour slot
+  static constexpr int kW = (VB ? 2 : 1) * kWArr;  // one own-colour slot
+  static constexpr int kBars = 8 * (kRingO + kRingW);
+  static constexpr int smem() { return 128 + kRingO * kO + kRingW * kW + kBars; }
+};
+
+// One tensor map per array: the colour array as (W, ny, nz) FP32.
+struct SweepMaps {
+  CUtensorMap uo, bo_other, f, bo_own;
+};
+
+__device__ __forceinline__ uint32_t sm_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long sweep_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// true once the phase with this parity has completed; false after the
+// iteration or time limit
+__device__ __forceinline__ bool sweep_wait(uint32_t bar, uint32_t parity) {
+  unsigned long long t0 = 0;
+  for (long long it = 0; it < kSweepWaitIters; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 0) {
+      const unsigned long long t = sweep_now();
+      if (it == 0) t0 = t;
+      else if (t - t0 > kSweepWaitNs) return false;
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ void sweep_tma3(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                           int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ float4 lds4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+
+template <bool VB, bool HasMask>
+__global__ void __launch_bounds__(kT, VB ? 3 : 4)
+    k_half_sweep_tma(Split32 op, float alpha, int col, float* __restrict__ u,
+                     const __grid_constant__ SweepMaps maps) {
+  using P = TmaPlan<VB>;
+  extern __shared__ unsigned char sweep_smem[];
+  const unsigned FULL = 0xffffffffu;
+  const int W = op.W, ny = op.b.ny, nz = op.b.nz;
+  const int lane = threadIdx.x, warp = threadIdx.y, tid = warp * 32 + lane;
+  const int p0 = blockIdx.x * 128, j0 = blockIdx.y * 8;
+  const int ka = blockIdx.z * kTmaZ, kb = min(nz, ka + kTmaZ);
+  const uint32_t base = (sm_u32(sweep_smem) + 127u) & ~127u;
+  unsigned char* gbase = sweep_smem + (base - sm_u32(sweep_smem));
+  const uint32_t oslot0 = base, wslot0 = base + kRingO * P::kO;
+  const uint32_t bar0 = wslot0 + kRingW * P::kW;
+  auto obar = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+  auto wbar = [&](int s) { return bar0 + 8u * (uint32_t)(kRingO + s); };
+  // generic pointers of the slots
+  auto optr = [&](int s, int a) {
+    return reinterpret_cast<const float*>(gbase + s * P::kO + a * kOArr);
+  };
+  auto wptr = [&](int s, int a) {
+    return reinterpret_cast<const float*>(gbase + kRingO * P::kO + s * P::kW + a * kWArr);
+  };
+  const int no = kb - ka + 2;  // other-colour planes ka - 1 .. kb
+  const int nw = kb - ka;      // own-colour planes ka .. kb - 1
+
+  // producer (thread 0): other-colour sequence number q is plane ka - 1 + q
+  auto issue_o = [&](int q) {
+    const int s = q % kRingO, z = ka - 1 + q;
+    const uint32_t b = obar(s);
+    if (z < 0 || z >= nz) {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(b) : "memory");
+      return;
+    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b),
+                 "r"((uint32_t)((VB ? 2 : 1) * kOX * kOY * 4))
+                 : "memory");
+    const uint32_t d = oslot0 + (uint32_t)(s * P::kO);
+    sweep_tma3(d, &maps.uo, b, p0 - 4, j0 - 1, z);
+    if (VB) sweep_tma3(d + kOArr, &maps.bo_other, b, p0 - 4, j0 - 1, z);
+  };
+  auto issue_w = [&](int q) {
+    const int s = q % kRingW, z = ka + q;
+    const uint32_t b = wbar(s);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b),
+                 "r"((uint32_t)((VB ? 2 : 1) * 128 * 8 * 4))
+                 : "memory");
+    const uint32_t d = wslot0 + (uint32_t)(s * P::kW);
+    sweep_tma3(d, &maps.f, b, p0, j0, z);
+    if (VB) sweep_tma3(d + kWArr, &maps.bo_own, b, p0, j0, z);
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < kRingO + kRingW; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8u * i) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    for (int q = 0; q < min(kRingO - 1, no); ++q) issue_o(q);
+    for (int q = 0; q < min(kRingW - 1, nw); ++q) issue_w(q);
+  }
+  __syncthreads();
+
+  const int j = j0 + warp, pp = p0 + 4 * lane;
+  const bool active = j < ny && pp < W;
+  const bool ym = j > 0, yp = j < ny - 1;
+  const int r = warp + 1;  // the thread's row in the other-colour box
+  const int c = 4 + 4 * lane;
+  const float4 half = make_float4(0.5f, 0.5f, 0.5f, 0.5f);
+  int issued_o = min(kRingO - 1, no), issued_w = min(kRingW - 1, nw);
+  bool ok = true;
+  for (int i = 0; i < nw; ++i) {
+    const int k = ka + i;
+    if (tid == 0) {
+      if (issued_o < no) issue_o(issued_o++);
+      if (issued_w < nw) issue_w(issued_w++);
+    }
+    // other planes k - 1, k, k + 1 are sequence numbers i, i + 1, i + 2
+    if (i == 0) {
+      ok = ok && sweep_wait(obar(0), 0u);
+      ok = ok && sweep_wait(obar(1 % kRingO), (uint32_t)((1 / kRingO) & 1));
+    }
+    ok = ok && sweep_wait(obar((i + 2) % kRingO), (uint32_t)(((i + 2) / kRingO) & 1));
+    ok = ok && sweep_wait(wbar(i % kRingW), (uint32_t)((i / kRingW) & 1));
+    if (ok) {
+      const int sm = i % kRingO, sc = (i + 1) % kRingO, sp = (i + 2) % kRingO;
+      const float* uoc = optr(sc, 0) + r * kOX;
+      const float* boc = optr(sc, 1) + r * kOX;
+      Quad q;
+      q.F = lds4(wptr(i % kRingW, 0) + warp * 128 + 4 * lane);
+      q.BO = VB ? lds4(wptr(i % kRingW, 1) + warp * 128 + 4 * lane) : half;
+      q.U = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float4 UO = lds4(uoc + c);
+      const float4 BT = VB ? lds4(boc + c) : half;
+      q.UYm = lds4(uoc - kOX + c);
+      q.UYp = lds4(uoc + kOX + c);
+      q.UZm = lds4(optr(sm, 0) + r * kOX + c);
+      q.UZp = lds4(optr(sp, 0) + r * kOX + c);
+      q.BYm = VB ? lds4(boc - kOX + c) : half;
+      q.BYp = VB ? lds4(boc + kOX + c) : half;
+      q.BZm = VB ? lds4(optr(sm, 1) + r * kOX + c) : half;
+      q.BZp = VB ? lds4(optr(sp, 1) + r * kOX + c) : half;
+      float uprev = __shfl_up_sync(FULL, UO.w, 1), unext = __shfl_down_sync(FULL, UO.x, 1);
+      float bprev = __shfl_up_sync(FULL, BT.w, 1), bnext = __shfl_down_sync(FULL, BT.x, 1);
+      if (lane == 0) {
+        uprev = uoc[3];
+        if (VB) bprev = boc[3];
+      }
+      if (lane == 31) {
+        unext = uoc[4 + 128];
+        if (VB) bnext = boc[4 + 128];
+      }
+      q.ux[0] = uprev; q.ux[1] = UO.x; q.ux[2] = UO.y; q.ux[3] = UO.z; q.ux[4] = UO.w;
+      q.ux[5] = unext;
+      q.bx[0] = bprev; q.bx[1] = BT.x; q.bx[2] = BT.y; q.bx[3] = BT.z; q.bx[4] = BT.w;
+      q.bx[5] = bnext;
+      const bool zm = k > 0, zp = k < nz - 1;
+      const int sx = (j + k + col) & 1;  // warp-uniform
+      const float4 v = sx ? quad_update<VB, false, HasMask, 1>(op, alpha, q, pp, ym, yp, zm, zp)
+                          : quad_update<VB, false, HasMask, 0>(op, alpha, q, pp, ym, yp, zm, zp);
+      if (active) {
+        float* dst = u + ((long long)k * ny + j) * W + pp;
+        if (!HasMask || (q.BO.x >= 0.0f && q.BO.y >= 0.0f && q.BO.z >= 0.0f && q.BO.w >= 0.0f)) {
+          *reinterpret_cast<float4*>(dst) = v;
+        } else {
+          // electrode cells keep their values
+          if (q.BO.x >= 0.0f) dst[0] = v.x;
+          if (q.BO.y >= 0.0f) dst[1] = v.y;
+          if (q.BO.z >= 0.0f) dst[2] = v.z;
+          if (q.BO.w >= 0.0f) dst[3] = v.w;
+        }
+      }
+    }
+    // the slots of other plane k - 1 and own plane k are free after this
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+  }
+  if (!ok && tid == 0) {
+    atomicExch(&g_sweep_timeout, 1u);
+    // the copies issued and not yet waited for by everyone: wait for each
+    // slot's last issued phase (bounded) before the CTA's shared memory goes
+    for (int q = max(0, issued_o - kRingO); q < issued_o; ++q)
+      sweep_wait(obar(q % kRingO), (uint32_t)((q / kRingO) & 1));
+    for (int q = max(0, issued_w - kRingW); q < issued_w; ++q)
+      sweep_wait(wbar(q % kRingW), (uint32_t)((q / kRingW) & 1));
+  }
 }
 
 __device__ __forceinline__ long long spos(const Split32& op, int i, int j, int k) {
@@ -566,11 +811,106 @@ __global__ void k_split_beta(const double* beta, const uint8_t* mask, Split32 op
   sel(out, (i + j + k) & 1)[spos(op, i, j, k)] = v;
 }
 
+// cuTensorMapEncodeTiled, fetched from the driver once (null if absent).
+PFN_cuTensorMapEncodeTiled_v12000 sweep_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// A colour array of the level as a (W, ny, nz) FP32 tensor, copied in boxes
+// of bx x by x 1; zero fill outside.
+bool colour_map(CUtensorMap* m, const float* p, const Split32& op, int bx, int by) {
+  const cuuint64_t dim[3] = {(cuuint64_t)op.W, (cuuint64_t)op.b.ny, (cuuint64_t)op.b.nz};
+  const cuuint64_t stride[2] = {(cuuint64_t)op.W * 4, (cuuint64_t)op.W * op.b.ny * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return sweep_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)p, dim, stride, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 }  // namespace
+
+// The staged half-sweeps' shared-memory limits, set once (contexts call this
+// on creation, outside any graph capture).
+bool sweep_kernels_ready() {
+  static const bool ok = [] {
+    return cudaFuncSetAttribute(k_half_sweep_tma<true, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TmaPlan<true>::smem()) == cudaSuccess &&
+           cudaFuncSetAttribute(k_half_sweep_tma<true, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TmaPlan<true>::smem()) == cudaSuccess &&
+           cudaFuncSetAttribute(k_half_sweep_tma<false, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TmaPlan<false>::smem()) == cudaSuccess;
+  }();
+  return ok;
+}
+
+namespace {
+
+// The staged half-sweep where it applies (not the first half-sweep from
+// zero, W a multiple of 4 and at least one 128-entry tile, 16-byte aligned
+// arrays, tensor maps encodable); false otherwise (nothing launched).
+bool try_half_sweep_tma(const Split32& op, float alpha, int col, const float* f, float* u,
+                        const float* uo, bool has_mask, cudaStream_t s) {
+  const bool vb = op.beta[0] != nullptr;
+  if (op.b.nx % 8 != 0 || op.W < 128 || !sweep_encoder()) return false;
+  if (!aligned16(f) || !aligned16(u) || !aligned16(uo)) return false;
+  if (vb && (!aligned16(op.beta[0]) || !aligned16(op.beta[1]))) return false;
+  SweepMaps maps;
+  if (!colour_map(&maps.uo, uo, op, kOX, kOY) || !colour_map(&maps.f, f, op, 128, 8)) return false;
+  if (vb) {
+    if (!colour_map(&maps.bo_other, bsel_h(op, col ^ 1), op, kOX, kOY) ||
+        !colour_map(&maps.bo_own, bsel_h(op, col), op, 128, 8))
+      return false;
+  } else {
+    maps.bo_other = maps.uo;
+    maps.bo_own = maps.f;
+  }
+  if (!sweep_kernels_ready()) return false;
+  dim3 blk(32, 8), g((op.W + 127) / 128, (op.b.ny + 7) / 8, (op.b.nz + kTmaZ - 1) / kTmaZ);
+  auto go = [&](auto kern, int smem) { kern<<<g, blk, smem, s>>>(op, alpha, col, u, maps); };
+  if (vb) {
+    if (has_mask) go(k_half_sweep_tma<true, true>, TmaPlan<true>::smem());
+    else go(k_half_sweep_tma<true, false>, TmaPlan<true>::smem());
+  } else {
+    go(k_half_sweep_tma<false, false>, TmaPlan<false>::smem());
+  }
+  return true;
+}
+
+}  // namespace
+
+bool sweep_timed_out() {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_sweep_timeout, sizeof(v)) != cudaSuccess) return false;
+  if (v) {
+    const unsigned zero = 0;
+    cudaMemcpyToSymbol(g_sweep_timeout, &zero, sizeof(zero));
+  }
+  return v != 0;
+}
 
 void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
                          const float* uo, bool zero_other, bool has_mask, cudaStream_t s) {
   const bool vb = op.beta[0] != nullptr;
+  if (!zero_other && try_half_sweep_tma(op, alpha, col, f, u, uo, has_mask, s)) {
+    add_launches(1);
+    return;
+  }
   dim3 blk(32, 8);
   if (op.b.nx % 8 == 0) {
     dim3 g((op.W / 4 + 31) / 32, (op.b.ny + 7) / 8, op.b.nz);

@@ -192,6 +192,73 @@ def test_one_cycle_marshak(mg, prec, nu):
         check(g, one_cycle_oracle(oracle.helmholtz(shape, h, k, marshak=True), S, nu), prec)
 
 
+# ---- the finest level at a width that takes the staged half-sweep ---------
+#
+# Levels whose packed width W = nx / 2 is at least 128 run the half-sweep
+# whose planes arrive in shared memory by tensor copies (tiles of 128 packed
+# entries x 8 rows, 32 planes per CTA).  264 x 20 x 40 cells (x, y, z): W =
+# 132, so the second x-tile holds one active quad and its halo lies past the
+# level's edge; 20 rows end in a half-empty row tile; 40 planes are a chunk of
+# 32 and one of 8.  The level below (W = 66) runs the register-fed kernel.
+
+TMA_SHAPE = (40, 20, 264)
+
+
+@pytest.mark.parametrize("nu", [(2, 2), (2, 1)])
+def test_one_cycle_staged_sweep_poisson_slab_electrode(mg, nu):
+    """Variable permittivity and an electrode block that reaches into the
+    last x-tile: the FP32 cycle equals the oracle's FP64 cycle to FP32
+    rounding."""
+    shape = TMA_SHAPE
+    nz, ny, nx = shape
+    h = 1.0 / nx
+    rho = blobs(shape, 31)
+    eps = W.dielectric_slab_box(shape, h, (0.0, 0.0, 0.0), z_top=0.07)
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[18:27, 6:13, 250:262] = 1
+    mv = np.where(mask != 0, 0.5, 0.0)
+    got = one_cycle_gpu(mg, 1, shape, h, nu, rho=rho, eps=eps, mask=mask, mask_value=mv)
+    p = oracle.Problem(shape, h, 0.0, eps, mask, W.GAP_BC_KIND, W.GAP_BC_VALUE)
+    check(got, one_cycle_oracle(p, rho / oracle.EPS0, nu, u0=mv), 1)
+
+
+@pytest.mark.parametrize("nu", [(2, 2), (1, 1)])
+def test_one_cycle_staged_sweep_helmholtz(mg, nu):
+    """Constant coefficient (the staged kernel without coefficient arrays)."""
+    shape = TMA_SHAPE
+    h = 1.0 / shape[2]
+    S = np.abs(blobs(shape, 32)) / W.EPS0
+    kap = W.helmholtz_kappas()
+    got = one_cycle_gpu(mg, 1, shape, h, nu, kappa=kap, S=S)
+    for g, k in zip(got, kap):
+        check(g, one_cycle_oracle(oracle.helmholtz(shape, h, k), S, nu), 1)
+
+
+def test_staged_sweep_converges_to_oracle(mg):
+    """The same box solved to 1e-10 in mixed precision with the slab, the
+    electrode and Neumann sides: within 1e-9 of the oracle's answer."""
+    shape = TMA_SHAPE
+    nz, ny, nx = shape
+    h = 1.0 / nx
+    rho = blobs(shape, 33)
+    eps = W.dielectric_slab_box(shape, h, (0.0, 0.0, 0.0), z_top=0.07)
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[18:27, 6:13, 250:262] = 1
+    mv = np.where(mask != 0, 0.5, 0.0)
+    bc_kind = (1, 1, 1, 1, 0, 0)
+    bc_value = (0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+    s = mg.Solver(shape, h, eps_r=cuda(eps), mask=cuda(mask), mask_value=cuda(mv),
+                  bc_kind=bc_kind, bc_value=bc_value, precision=1)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st = s.solve_poisson(cuda(rho), u, 1e-10)
+    s.close()
+    assert st["converged"]
+    p = oracle.Problem(shape, h, 0.0, eps, mask, bc_kind, bc_value)
+    ref, _, rel, _ = p.solve(rho / oracle.EPS0, u0=mv, tol=1e-13)
+    assert rel < 1e-12
+    assert oracle.rel_l2(u.cpu().numpy(), ref) <= 1e-9
+
+
 # ---- the face-rule coarse operator (MG_COARSE_FACE, the default) ----------
 #
 # Its coarse faces are built from the finer level's face weights (series along
