@@ -844,6 +844,7 @@ def run_ours(args):
             "config": dict(config(args), autotuned=tuned, nu1=solver.options.nu1,
                            nu2=solver.options.nu2, inner_cycles=solver.options.inner_cycles,
                            ir_zchunk=solver.options.ir_zchunk,
+                           sweep_zchunk=solver.options.sweep_zchunk,
                            coarse_visits=max(1, solver.options.coarse_visits)),
             "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": launches, "cycles_per_problem": cycles,

@@ -139,6 +139,13 @@ typedef struct {
                        there: the rate of a W-cycle on a layered medium whose
                        interfaces cut the coarse cells, for about 20 % more
                        work per cycle) (0) */
+  int sweep_zchunk; /* FP32 half-sweeps of levels with at least 256 cells
+                       along x: z planes per CTA of the form whose planes
+                       arrive in shared memory by tensor copies, 8, 16 or 32;
+                       0 = automatic (the largest of them that still gives
+                       about four CTAs per SM slot, and the register-fed form
+                       where even 8 gives fewer than two); -1 = the
+                       register-fed form on every level (0) */
 } mg_options;
 
 /* Per-solve statistics.  hist[c] is the relative residual after c cycles
@@ -443,7 +450,8 @@ mg_status mg_set_options(mg_ctx* ctx, const mg_options* opt);
  * mg_autotune -- pick the smoother sweeps (nu1, nu2) in {(1,1), (2,1), (2,2),
  * (3,3)} and, in mixed precision, the inner V-cycles per refinement step in
  * {1..4}, then for the best of those the tile of the refinement pass
- * (ir_zchunk in {auto, 16, 32, 64, 128}), by timing mg_solve_set on the
+ * (ir_zchunk in {auto, 16, 32, 64, 128}) and the z planes per CTA of the
+ * staged half-sweep (sweep_zchunk in {auto, 16, 32}), by timing mg_solve_set on the
  * caller's problem (each candidate run twice from a zero guess, the faster
  * counts; candidates that do not reach tol are rejected).  The fastest is installed in the context and returned in
  * *best (*best_ms, nullable: its device time).  Allocates four scratch fields

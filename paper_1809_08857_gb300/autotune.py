@@ -1,6 +1,7 @@
 """Autotune cache: the sweep counts (nu1, nu2), inner V-cycles per
-refinement step and refinement-pass tile (ir_zchunk) that mg_autotune picked
-for a problem signature, stored as
+refinement step, refinement-pass tile (ir_zchunk) and staged half-sweep
+planes per CTA (sweep_zchunk) that mg_autotune picked for a problem
+signature, stored as
 JSON keyed by device name and problem signature so that later runs on the
 same device and problem class skip the search."""
 import json
@@ -46,7 +47,8 @@ def tuned(solver, rho, S, kappa, tol=1e-10, has_eps=False, has_mask=False, preci
     entry = load(cache_path).get(key)
     if entry:
         solver.set_options(nu1=entry["nu1"], nu2=entry["nu2"], inner_cycles=entry["inner_cycles"],
-                           ir_zchunk=entry.get("ir_zchunk", 0))
+                           ir_zchunk=entry.get("ir_zchunk", 0),
+                           sweep_zchunk=entry.get("sweep_zchunk", 0))
         return entry, True
     opts, ms = solver.autotune(rho, S, kappa, tol)
     entry = dict(opts, ms=ms)

@@ -119,7 +119,7 @@ struct LevelWork {
 struct StepGraph {
   int kind = 0;
   double alpha = 0;
-  int ic = 0, nu1 = 0, nu2 = 0, zc = 0;
+  int ic = 0, nu1 = 0, nu2 = 0, zc = 0, cv = 0, sz = 0;
   bool prof = false;
   const float2* b = nullptr;
   const float2* u_in = nullptr;
@@ -492,7 +492,7 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
                                    L.mask != nullptr, s);
         else
           mg::launch_half_sweep32(op, a32, col, X.f32[col], X.u32[col], X.u32[col ^ 1], zo,
-                                  L.mask != nullptr, s);
+                                  L.mask != nullptr, c->opt.sweep_zchunk, s);
       }
   };
   smooth(c->opt.nu1, first_zero);
@@ -738,7 +738,8 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
   const int ic = p.ic;
   for (StepGraph& g : w->graphs)
     if (g.kind == p.kind && g.alpha == p.alpha && g.ic == ic && g.nu1 == c->opt.nu1 &&
-        g.nu2 == c->opt.nu2 && g.zc == c->opt.ir_zchunk && g.prof == c->prof && g.b == w->bdf &&
+        g.nu2 == c->opt.nu2 && g.zc == c->opt.ir_zchunk && g.cv == c->opt.coarse_visits &&
+        g.sz == c->opt.sweep_zchunk && g.prof == c->prof && g.b == w->bdf &&
         g.u_in == p.cur &&
         g.u_out == p.other) {
       g.stamp = ++c->clock;
@@ -765,6 +766,8 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
   g.nu1 = c->opt.nu1;
   g.nu2 = c->opt.nu2;
   g.zc = c->opt.ir_zchunk;
+  g.cv = c->opt.coarse_visits;
+  g.sz = c->opt.sweep_zchunk;
   g.prof = c->prof;
   g.b = w->bdf;
   g.u_in = p.cur;
@@ -1010,8 +1013,10 @@ mg_status solve_mixed(std::vector<Prob>& P) {
     if (p.status == MG_ERR_NONFINITE || (p.status != MG_OK && worst == MG_OK)) worst = p.status;
   }
   for (mg_ctx* c : ctxs) harvest(c);
-  if (mg::sweep_timed_out())
-    return fail(MG_ERR_CUDA, "a staged half-sweep gave up waiting for a plane copy");
+  const bool sweep_late = mg::sweep_timed_out(), ir_late = mg::ir_timed_out();
+  if (sweep_late || ir_late)
+    return fail(MG_ERR_CUDA, sweep_late ? "a staged half-sweep gave up waiting for a plane copy"
+                                        : "a staged refinement step gave up waiting for a plane copy");
   if (worst == MG_ERR_NONFINITE) g_last_error = "non-finite value in input or residual";
   return worst;
 }
@@ -1282,6 +1287,10 @@ mg_status normalise_options(const mg_options* in, mg_options* out) {
   if (in->coarse_visits < 0 || in->coarse_visits > 2)
     return fail(MG_ERR_INVALID_ARG, "coarse_visits must be 0, 1 or 2");
   out->coarse_visits = in->coarse_visits;
+  if (in->sweep_zchunk != 0 && in->sweep_zchunk != -1 && in->sweep_zchunk != 8 &&
+      in->sweep_zchunk != 16 && in->sweep_zchunk != 32)
+    return fail(MG_ERR_INVALID_ARG, "sweep_zchunk must be 0, -1, 8, 16 or 32");
+  out->sweep_zchunk = in->sweep_zchunk;
   return MG_OK;
 }
 
@@ -1925,6 +1934,7 @@ mg_status mg_create(const mg_grid* grid, const double* eps_r, const uint8_t* mas
     return st;
   }
   mg::sweep_kernels_ready();
+  mg::ir_tma_ready();
   *out = c;
   return MG_OK;
 }
@@ -2112,38 +2122,49 @@ mg_status mg_autotune(mg_ctx* c, const double* rho, const double* S, const doubl
   mg_status st = MG_OK;
   if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
     st = fail(MG_ERR_CUDA, "cudaEventCreate failed");
+  // device time of one candidate: the faster of two runs from zero (the
+  // first builds its graphs); false if it does not reach tol
+  auto time_opts = [&](const mg_options& o, double* t_out) -> bool {
+    c->opt = o;
+    double t_min = 1e300;
+    for (int rep = 0; rep < 2 && st == MG_OK; ++rep) {
+      if (cudaMemsetAsync(scratch, 0, 4 * n * sizeof(double), c->stream) != cudaSuccess ||
+          cudaEventRecord(t0, c->stream) != cudaSuccess) {
+        st = fail(MG_ERR_CUDA, "autotune launch failed");
+        break;
+      }
+      const mg_status sv = mg_solve_set(c, rho, phi, S, psi, kappa, tol, nullptr);
+      cudaEventRecord(t1, c->stream);
+      cudaEventSynchronize(t1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (sv == MG_ERR_NOT_CONVERGED || sv == MG_ERR_DIVERGED) return false;  // rejected
+      if (sv != MG_OK) {
+        st = sv;
+        break;
+      }
+      t_min = std::min(t_min, (double)ms);
+    }
+    *t_out = t_min;
+    return st == MG_OK;
+  };
+  auto consider = [&](const mg_options& o) {
+    double t;
+    if (time_opts(o, &t) && t < best_t) {
+      best_t = t;
+      best_o = o;
+    }
+  };
   for (int a = 0; a < 4 && st == MG_OK; ++a)
     for (int b = 0; b < n_inner && st == MG_OK; ++b) {
       mg_options o = keep;
       o.nu1 = sweeps[a][0];
       o.nu2 = sweeps[a][1];
       o.inner_cycles = c->opt.precision == MG_PREC_MIXED ? inner_mixed[b] : 1;
-      c->opt = o;
-      double t_min = 1e300;
-      for (int rep = 0; rep < 2 && st == MG_OK; ++rep) {  // first run builds graphs
-        if (cudaMemsetAsync(scratch, 0, 4 * n * sizeof(double), c->stream) != cudaSuccess ||
-            cudaEventRecord(t0, c->stream) != cudaSuccess) {
-          st = fail(MG_ERR_CUDA, "autotune launch failed");
-          break;
-        }
-        const mg_status sv = mg_solve_set(c, rho, phi, S, psi, kappa, tol, nullptr);
-        cudaEventRecord(t1, c->stream);
-        cudaEventSynchronize(t1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, t0, t1);
-        if (sv == MG_ERR_NOT_CONVERGED) break;  // candidate rejected
-        if (sv != MG_OK) {
-          st = sv;
-          break;
-        }
-        t_min = std::min(t_min, (double)ms);
-      }
-      if (st == MG_OK && t_min < best_t) {
-        best_t = t_min;
-        best_o = o;
-      }
+      consider(o);
     }
-  // then the tile of the refinement pass for the best candidate (mixed mode)
+  // then, for the best candidate (mixed mode), the tile of the refinement
+  // pass and the z planes per CTA of the staged half-sweep
   if (st == MG_OK && best_t < 1e300 && keep.precision == MG_PREC_MIXED) {
     const int zcs[4] = {16, 32, 64, 128};
     const mg_options base = best_o;
@@ -2151,30 +2172,15 @@ mg_status mg_autotune(mg_ctx* c, const double* rho, const double* S, const doubl
       if (zcs[z] >= c->lv[0].b.nz) continue;
       mg_options o = base;
       o.ir_zchunk = zcs[z];
-      c->opt = o;
-      double t_min = 1e300;
-      for (int rep = 0; rep < 2 && st == MG_OK; ++rep) {
-        if (cudaMemsetAsync(scratch, 0, 4 * n * sizeof(double), c->stream) != cudaSuccess ||
-            cudaEventRecord(t0, c->stream) != cudaSuccess) {
-          st = fail(MG_ERR_CUDA, "autotune launch failed");
-          break;
-        }
-        const mg_status sv = mg_solve_set(c, rho, phi, S, psi, kappa, tol, nullptr);
-        cudaEventRecord(t1, c->stream);
-        cudaEventSynchronize(t1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, t0, t1);
-        if (sv == MG_ERR_NOT_CONVERGED) break;
-        if (sv != MG_OK) {
-          st = sv;
-          break;
-        }
-        t_min = std::min(t_min, (double)ms);
-      }
-      if (st == MG_OK && t_min < best_t) {
-        best_t = t_min;
-        best_o = o;
-      }
+      consider(o);
+    }
+    const int szs[2] = {16, 32};
+    const mg_options base2 = best_o;
+    for (int z = 0; z < 2 && st == MG_OK; ++z) {
+      if (base2.sweep_zchunk == szs[z]) continue;
+      mg_options o = base2;
+      o.sweep_zchunk = szs[z];
+      consider(o);
     }
   }
   c->opt = st == MG_OK ? best_o : keep;

@@ -210,8 +210,14 @@ bool sweep_timed_out();
 // Sets the staged half-sweeps' shared-memory limits once; false if they
 // cannot run (the register-fed half-sweep is used then).
 bool sweep_kernels_ready();
+// The same for the staged refinement step (mg_ir.cu).
+bool ir_tma_ready();
+bool ir_timed_out();
+// zchunk: mg_options.sweep_zchunk (0 automatic, -1 register-fed only, or the
+// staged form's z planes per CTA).
 void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
-                         const float* uo, bool zero_other, bool has_mask, cudaStream_t s);
+                         const float* uo, bool zero_other, bool has_mask, int zchunk,
+                         cudaStream_t s);
 // Residual of the red cells only (needs nu1 >= 1: black residuals are 0).
 void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
                               MPtr2 fc, MPtr2 uc, cudaStream_t s);

@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "mg_internal.h"
+#include "tma.cuh"
 
 // Largest number of CTAs (partial sums) one call may use: 16384 doubles,
 // 128 KiB.  Every GPU that loads libmg holds this array until process exit.
@@ -474,6 +475,220 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
   }
 }
 
+// ---- the two-cell refinement step with its planes staged by tensor copies --
+//
+// k_ir_df2<HasE=1, U64=0, BIn=0> (a constant-coefficient refinement step
+// after the first pass, on a grid without electrode cells) with its inputs
+// brought to shared memory by tiled tensor copies instead of register
+// prefetches.  Per plane: the CTA's 64 x 16 patch of the double-float iterate
+// (box 128 x 16 floats from x = 2 i0, a 16-byte boundary), the 32 packed
+// corrections of each colour (box 36 x 16 from the packed start rounded down
+// to a multiple of 4 entries; a thread indexes from the remainder) and b of
+// the 60 x 14 own cells (box 120 x 14).  The iterate and correction of plane
+// k + 2 are combined into registers at the end of plane k from a ring of
+// three slots, whose copies are issued two to three planes ahead; b of plane
+// k comes from a ring of three.  Everything else (the y-neighbours through
+// the shared plane, the x-neighbours by shuffle, the FP32x2 double-float
+// arithmetic) is k_ir_df2's.  Waits are bounded (tma::kWaitNs); a CTA that
+// gives up sets g_ir_timeout, waits for its own copies and stops.
+constexpr int kIrU = 3, kIrB = 3;                  // ring slots
+constexpr int kIrUBytes = TY * 4 * TX * 4;         // 16 rows x 128 floats = 8192
+constexpr int kIrEBytes = TY * 36 * 4;             // 2304 per colour
+constexpr int kIrUSlot = kIrUBytes + 2 * kIrEBytes;  // 12800 = 100 x 128
+constexpr int kIrBBytes = (TY - 2) * 120 * 4;      // 6720
+constexpr int kIrBSlot = 6784;                     // 53 x 128
+constexpr int kIrSmem = 128 + kIrU * kIrUSlot + kIrB * kIrBSlot + 8 * (kIrU + kIrB);
+
+struct IrMaps {
+  CUtensorMap u, e0, e1, b;
+};
+
+__device__ unsigned g_ir_timeout = 0;
+
+__global__ void __launch_bounds__(NT, 2) k_ir_df2_tma(IrArgs a,
+                                                      const __grid_constant__ IrMaps maps) {
+  extern __shared__ unsigned char ir_smem[];
+  __shared__ float4 pl[2][TY][TX];
+  __shared__ float red[NT / 32];
+  const unsigned FULL = 0xffffffffu;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int nx = a.op.b.nx, ny = a.op.b.ny, nz = a.op.b.nz;
+  const int bx = blockIdx.x, by = blockIdx.y;
+  const int i0 = 2 * (bx * (TX - 2) - 1 + tx), j = by * (TY - 2) - 1 + ty;
+  const int z0 = blockIdx.z * a.zchunk, z1 = min(nz, z0 + a.zchunk);
+  const int n = z1 - z0, nq = n + 2;
+  const int W = a.W;
+  const long long sz = (long long)nx * ny, szW = (long long)W * ny;
+  const bool in = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
+  const bool own = in && tx >= 1 && tx <= TX - 2 && ty >= 1 && ty <= TY - 2;
+  const int off = in ? j * nx + i0 : 0;
+  const int eoff = in ? j * W + (i0 >> 1) : 0;
+  const int par0 = (i0 + j) & 1;
+  const bool xmA = i0 > 0, xpB = i0 + 2 < nx, ym = j > 0, yp = j < ny - 1;
+  const float2 zero2 = make_float2(0.0f, 0.0f);
+  // box origins: the iterate and b in floats (two per cell), the corrections
+  // in packed entries rounded down to a multiple of 4
+  const int ux = 4 * (bx * (TX - 2) - 1), uy = by * (TY - 2) - 1;
+  const int pe = bx * (TX - 2) - 1, ex = pe & ~3, eo = pe - ex;
+  const int bxo = 4 * bx * (TX - 2), byo = by * (TY - 2);
+
+  const uint32_t base = (tma::smem_addr(ir_smem) + 127u) & ~127u;
+  unsigned char* gbase = ir_smem + (base - tma::smem_addr(ir_smem));
+  const uint32_t bar0 = base + kIrU * kIrUSlot + kIrB * kIrBSlot;
+  auto ubar = [&](int q) { return bar0 + 8u * (uint32_t)(q % kIrU); };
+  auto bbar = [&](int w) { return bar0 + 8u * (uint32_t)(kIrU + w % kIrB); };
+  auto upar = [&](int q) { return (uint32_t)((q / kIrU) & 1); };
+  auto bpar = [&](int w) { return (uint32_t)((w / kIrB) & 1); };
+  auto uslot = [&](int q) { return gbase + (q % kIrU) * kIrUSlot; };
+  auto bslot = [&](int w) { return gbase + kIrU * kIrUSlot + (w % kIrB) * kIrBSlot; };
+
+  // producer (thread 0): iterate/correction sequence q is plane z0 - 1 + q,
+  // b sequence w is plane z0 + w
+  auto issue_u = [&](int q) {
+    const int z = z0 - 1 + q;
+    const uint32_t b = ubar(q);
+    if (z < 0 || z >= nz) {
+      tma::bar_arrive(b);
+      return;
+    }
+    tma::bar_arrive_tx(b, (uint32_t)kIrUSlot);  // the three boxes fill the slot exactly
+    const uint32_t d = base + (uint32_t)((q % kIrU) * kIrUSlot);
+    tma::load3(d, &maps.u, b, ux, uy, z);
+    tma::load3(d + kIrUBytes, &maps.e0, b, ex, uy, z);
+    tma::load3(d + kIrUBytes + kIrEBytes, &maps.e1, b, ex, uy, z);
+  };
+  auto issue_b = [&](int w) {
+    const uint32_t b = bbar(w);
+    tma::bar_arrive_tx(b, (uint32_t)kIrBBytes);
+    tma::load3(base + (uint32_t)(kIrU * kIrUSlot + (w % kIrB) * kIrBSlot), &maps.b, b, bxo, byo,
+               z0 + w);
+  };
+  // u + e of plane z0 - 1 + q for the thread's pair, from its ring slot
+  auto combine = [&](int q, Df2& v) {
+    const int k = z0 - 1 + q;
+    v = Df2{zero2, zero2};
+    if (!(in && k >= 0 && k < nz)) return;
+    const unsigned char* sl = uslot(q);
+    const float4 u4 = reinterpret_cast<const float4*>(sl)[ty * TX + tx];
+    const float* e0 = reinterpret_cast<const float*>(sl + kIrUBytes) + ty * 36 + tx + eo;
+    const float* e1 = reinterpret_cast<const float*>(sl + kIrUBytes + kIrEBytes) + ty * 36 + tx + eo;
+    const bool ca = (par0 + k) & 1;
+    const float2 re = make_float2(ca ? *e1 : *e0, ca ? *e0 : *e1);
+    v = df_add2(Df2{make_float2(u4.x, u4.z), make_float2(u4.y, u4.w)}, re);
+  };
+
+  Df2 dxy;
+  if (xmA && xpB && ym && yp) {
+    dxy = Df2{make_float2(a.dint.x, a.dint.x), make_float2(a.dint.y, a.dint.y)};
+  } else {
+    const double dy = (ym ? 1.0 : 2.0 * a.op.rho[2]) + (yp ? 1.0 : 2.0 * a.op.rho[3]);
+    const double dA = (xmA ? 1.0 : 2.0 * a.op.rho[0]) + 1.0 + dy + 2.0;
+    const double dB = 1.0 + (xpB ? 1.0 : 2.0 * a.op.rho[1]) + dy + 2.0;
+    const float2 sA = split_df(fma(dA, a.op.ih2, a.alpha));
+    const float2 sB = split_df(fma(dB, a.op.ih2, a.alpha));
+    dxy = Df2{make_float2(sA.x, sB.x), make_float2(sA.y, sB.y)};
+  }
+
+  int issued_u = min(kIrU, nq), issued_b = min(kIrB, n);
+  if (tid == 0) {
+    for (int i = 0; i < kIrU + kIrB; ++i) tma::bar_init(bar0 + 8u * i);
+    tma::bar_init_fence();
+    for (int q = 0; q < issued_u; ++q) issue_u(q);
+    for (int w = 0; w < issued_b; ++w) issue_b(w);
+  }
+  __syncthreads();
+  bool ok = tma::bar_wait(ubar(0), 0u) && tma::bar_wait(ubar(1), 0u) && tma::bar_wait(ubar(2), 0u);
+  Df2 um, uc, up;
+  combine(0, um);
+  combine(1, uc);
+  combine(2, up);
+  float2 ss = zero2;
+  if (!__syncthreads_or(!ok)) {
+    if (tid == 0)
+      for (; issued_u < min(nq, 6); ++issued_u) issue_u(issued_u);
+    for (int i = 0; i < n; ++i) {
+      const int k = z0 + i;
+      ok = tma::bar_wait(bbar(i), bpar(i)) && ok;
+      const int buf = i & 1;
+      const float4 uc4 = make_float4(uc.hi.x, uc.lo.x, uc.hi.y, uc.lo.y);
+      pl[buf][ty][tx] = uc4;
+      const long long c = (long long)k * sz + off;
+      if (own && a.udf_out) *reinterpret_cast<float4*>(a.udf_out + c) = uc4;
+      if (__syncthreads_or(!ok)) {
+        ok = false;
+        break;
+      }
+      // every thread is past plane k - 1: its b slot and the slot of the
+      // iterate it combined last are free
+      if (tid == 0 && i >= 1) {
+        if (issued_u < nq) issue_u(issued_u++);
+        if (issued_b < n) issue_b(issued_b++);
+      }
+      const float pbh = __shfl_up_sync(FULL, uc.hi.y, 1), pbl = __shfl_up_sync(FULL, uc.lo.y, 1);
+      const float nah = __shfl_down_sync(FULL, uc.hi.x, 1), nal = __shfl_down_sync(FULL, uc.lo.x, 1);
+      if (own) {
+        const Df2 L{make_float2(pbh, uc.hi.x), make_float2(pbl, uc.lo.x)};
+        const Df2 R{make_float2(uc.hi.y, nah), make_float2(uc.lo.y, nal)};
+        const float4 b4 =
+            reinterpret_cast<const float4*>(bslot(i))[(ty - 1) * ((TX - 2)) + (tx - 1)];
+        DfAcc2 acc{make_float2(b4.x, b4.z), make_float2(b4.y, b4.w)};
+        const bool zm = k > 0, zp = k < nz - 1;
+        Df2 dg = dxy;
+        if (!zm) dg = df_add_df2(dg, a.dzm);
+        if (!zp) dg = df_add_df2(dg, a.dzp);
+        acc.add(Df2{make_float2(-dg.hi.x, -dg.hi.y), make_float2(-dg.lo.x, -dg.lo.y)}, uc);
+        const float4 s4 = pl[buf][ty - 1][tx], n4 = pl[buf][ty + 1][tx];
+        const Df2 w{make_float2(a.ih2d.x, a.ih2d.x), make_float2(a.ih2d.y, a.ih2d.y)};
+        const Df2 wl{make_float2(xmA ? a.ih2d.x : 0.0f, a.ih2d.x),
+                     make_float2(xmA ? a.ih2d.y : 0.0f, a.ih2d.y)};
+        const Df2 wr{make_float2(a.ih2d.x, xpB ? a.ih2d.x : 0.0f),
+                     make_float2(a.ih2d.y, xpB ? a.ih2d.y : 0.0f)};
+        acc.add(wl, L);
+        acc.add(wr, R);
+        if (ym) acc.add(w, Df2{make_float2(s4.x, s4.z), make_float2(s4.y, s4.w)});
+        if (yp) acc.add(w, Df2{make_float2(n4.x, n4.z), make_float2(n4.y, n4.w)});
+        if (zm) acc.add(w, um);
+        if (zp) acc.add(w, up);
+        const float2 r = acc.value();
+        if (a.r[0]) {
+          const long long t = (long long)k * szW + eoff;
+          const bool ca = (par0 + k) & 1;
+          (ca ? a.r[1] : a.r[0])[t] = r.x;
+          (ca ? a.r[0] : a.r[1])[t] = r.y;
+        }
+        ss = fma2(r, r, ss);
+      }
+      um = uc;
+      uc = up;
+      if (i + 1 < n) {
+        ok = tma::bar_wait(ubar(i + 3), upar(i + 3)) && ok;
+        combine(i + 3, up);
+      }
+    }
+  } else {
+    ok = false;
+  }
+  if (!ok && tid == 0) {
+    atomicExch(&g_ir_timeout, 1u);
+    for (int q = max(0, issued_u - kIrU); q < issued_u; ++q) tma::bar_wait(ubar(q), upar(q));
+    for (int w = max(0, issued_b - kIrB); w < issued_b; ++w) tma::bar_wait(bbar(w), bpar(w));
+  }
+  // CTA sums of r^2 (FP32 per thread, FP64 across the CTA)
+  float s1 = ss.x + ss.y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s1 += __shfl_xor_sync(FULL, s1, o);
+  if (tx == 0) red[ty] = s1;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    double v = threadIdx.x < NT / 32 ? (double)red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (threadIdx.x == 0) a.partial[cta] = v;
+  }
+}
+
 // 1.0 into *flag (mapped host memory) if any of u[0..n) is neither +0 nor -0
 // (a NaN counts as nonzero); at most one store per block.
 __global__ void k_nonzero(const double* __restrict__ u, long long n, double* flag) {
@@ -610,6 +825,23 @@ static long long ir_ctas(const Box& b, int zchunk) {
 
 int ir_partials(const Box& b, int zchunk) { return (int)ir_ctas(b, zchunk); }
 
+bool ir_tma_ready() {
+  static const bool ok = cudaFuncSetAttribute(k_ir_df2_tma,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              kIrSmem) == cudaSuccess;
+  return ok;
+}
+
+bool ir_timed_out() {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_ir_timeout, sizeof(v)) != cudaSuccess) return false;
+  if (v) {
+    const unsigned zero = 0;
+    cudaMemcpyToSymbol(g_ir_timeout, &zero, sizeof(zero));
+  }
+  return v != 0;
+}
+
 // The two-cell kernel runs the constant-coefficient operator (beta = 1)
 // except the first pass of a solve (the norm of the zero guess as well); it
 // needs an even nx (whole pairs) and arrays on 16-byte boundaries (one
@@ -626,10 +858,34 @@ static bool ir_pairable(const IrArgs& a) {
          al(a.rhs, 16) && al(a.op.mask, 2);
 }
 
+// The staged two-cell step (k_ir_df2_tma) where it applies: a refinement
+// step (double-float iterate plus correction, double-float b) on a grid
+// without electrode cells, nx a multiple of 8 (the packed corrections' rows
+// on 16-byte boundaries) and at least 128 x 16 cells per plane, 16-byte
+// aligned arrays and encodable tensor maps.  False: nothing launched.
+static bool ir_tma(const IrArgs& a, dim3 g, cudaStream_t s) {
+  const Box& b = a.op.b;
+  if (a.op.mask || b.nx % 8 != 0 || b.nx < 128 || b.ny < 16 || !a.udf_in || !a.bdf ||
+      !a.e[0] || !a.e[1] || !ir_tma_ready())
+    return false;
+  IrMaps m;
+  if (!tma_map_f32(&m.u, a.udf_in, 2LL * b.nx, b.ny, b.nz, 4 * TX, TY) ||
+      !tma_map_f32(&m.e0, a.e[0], a.W, b.ny, b.nz, 36, TY) ||
+      !tma_map_f32(&m.e1, a.e[1], a.W, b.ny, b.nz, 36, TY) ||
+      !tma_map_f32(&m.b, a.bdf, 2LL * b.nx, b.ny, b.nz, 4 * (TX - 2), TY - 2))
+    return false;
+  k_ir_df2_tma<<<g, NT, kIrSmem, s>>>(a, m);
+  return true;
+}
+
 template <bool P, bool F, bool E, bool U, int B, bool Z>
 static void go(const IrArgs& a, dim3 g, cudaStream_t s) {
-  if (P && !Z) k_ir_df2<E, U, B><<<g, NT, 0, s>>>(a);
-  else k_ir_df<F, E, U, B, Z><<<g, NT, 0, s>>>(a);
+  if (P && !Z) {
+    if (E && !U && B == 0 && ir_tma(a, g, s)) return;
+    k_ir_df2<E, U, B><<<g, NT, 0, s>>>(a);
+  } else {
+    k_ir_df<F, E, U, B, Z><<<g, NT, 0, s>>>(a);
+  }
 }
 
 template <bool P, bool F>

@@ -16,11 +16,10 @@
 // 2 b_c b_n / (b_c + b_n) is one add and one reciprocal: w = 1 / (hb_c +
 // hb_n); towards an electrode w = 1 / (2 hb_c); on a domain face
 // rho_f / hb_c.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include "mg_internal.h"
+#include "tma.cuh"
 
 namespace mg {
 
@@ -241,8 +240,8 @@ __global__ void __launch_bounds__(kT, 4) k_half_sweep_v4(Split32 op, float alpha
 // ---- half-sweep with planes staged by the tensor memory accelerator ------
 //
 // The update of k_half_sweep_v4 (four packed cells per thread, a warp per
-// row of 128 packed cells, block 32 x 8), but a CTA marches through up to
-// kTmaZ planes of its 128 x 8 tile and every plane reaches shared memory by
+// row of 128 packed cells, block 32 x 8), but a CTA marches through zc (8,
+// 16 or 32) planes of its 128 x 8 tile and every plane reaches shared memory by
 // a tiled tensor copy issued ahead of its use: the other colour's u and hb
 // with a halo of one row in y and four packed entries in x (the copy's x
 // start, p0 - 4, stays on a 16-byte boundary), and the own colour's f and
@@ -255,20 +254,16 @@ __global__ void __launch_bounds__(kT, 4) k_half_sweep_v4(Split32 op, float alpha
 // filled with zeros and never enter a face weight; planes -1 and nz are not
 // copied at all (their barrier phase completes by a plain arrive).
 //
-// Every wait on a plane is bounded (kSweepWaitNs); a CTA that gives up sets
+// Every wait on a plane is bounded (tma::kWaitNs); a CTA that gives up sets
 // g_sweep_timeout, waits (bounded) for the copies it issued, and returns
 // without writing the rest of its planes.  The host reads the flag after
 // each solve.
-constexpr int kTmaZ = 32;      // planes per CTA
 constexpr int kRingO = 4;      // other-colour slots: planes k-1, k, k+1 and one in flight
 constexpr int kRingW = 2;      // own-colour slots: plane k and one in flight
 constexpr int kOX = 136;       // other-colour box: 128 + 2 x 4 packed entries
 constexpr int kOY = 10;        // rows: 8 + 2
 constexpr int kOArr = 5504;    // bytes of one other-colour array box (10 x 136 x 4), to 128
 constexpr int kWArr = 4096;    // bytes of one own-colour array box (8 x 128 x 4)
-constexpr unsigned long long kSweepWaitNs = 1000000000ull;  // 1 s
-constexpr long long kSweepWaitIters = 1ll << 24;
-
 __device__ unsigned g_sweep_timeout = 0;
 
 template <bool VB>
@@ -284,54 +279,13 @@ struct SweepMaps {
   CUtensorMap uo, bo_other, f, bo_own;
 };
 
-__device__ __forceinline__ uint32_t sm_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ unsigned long long sweep_now() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// true once the phase with this parity has completed; false after the
-// iteration or time limit
-__device__ __forceinline__ bool sweep_wait(uint32_t bar, uint32_t parity) {
-  unsigned long long t0 = 0;
-  for (long long it = 0; it < kSweepWaitIters; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 63) == 0) {
-      const unsigned long long t = sweep_now();
-      if (it == 0) t0 = t;
-      else if (t - t0 > kSweepWaitNs) return false;
-    }
-  }
-  return false;
-}
-
-__device__ __forceinline__ void sweep_tma3(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                           int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
 __device__ __forceinline__ float4 lds4(const float* p) {
   return *reinterpret_cast<const float4*>(p);
 }
 
 template <bool VB, bool HasMask>
 __global__ void __launch_bounds__(kT, VB ? 3 : 4)
-    k_half_sweep_tma(Split32 op, float alpha, int col, float* __restrict__ u,
+    k_half_sweep_tma(Split32 op, float alpha, int col, int zc, float* __restrict__ u,
                      const __grid_constant__ SweepMaps maps) {
   using P = TmaPlan<VB>;
   extern __shared__ unsigned char sweep_smem[];
@@ -339,9 +293,9 @@ __global__ void __launch_bounds__(kT, VB ? 3 : 4)
   const int W = op.W, ny = op.b.ny, nz = op.b.nz;
   const int lane = threadIdx.x, warp = threadIdx.y, tid = warp * 32 + lane;
   const int p0 = blockIdx.x * 128, j0 = blockIdx.y * 8;
-  const int ka = blockIdx.z * kTmaZ, kb = min(nz, ka + kTmaZ);
-  const uint32_t base = (sm_u32(sweep_smem) + 127u) & ~127u;
-  unsigned char* gbase = sweep_smem + (base - sm_u32(sweep_smem));
+  const int ka = blockIdx.z * zc, kb = min(nz, ka + zc);
+  const uint32_t base = (tma::smem_addr(sweep_smem) + 127u) & ~127u;
+  unsigned char* gbase = sweep_smem + (base - tma::smem_addr(sweep_smem));
   const uint32_t oslot0 = base, wslot0 = base + kRingO * P::kO;
   const uint32_t bar0 = wslot0 + kRingW * P::kW;
   auto obar = [&](int s) { return bar0 + 8u * (uint32_t)s; };
@@ -361,31 +315,26 @@ __global__ void __launch_bounds__(kT, VB ? 3 : 4)
     const int s = q % kRingO, z = ka - 1 + q;
     const uint32_t b = obar(s);
     if (z < 0 || z >= nz) {
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(b) : "memory");
+      tma::bar_arrive(b);
       return;
     }
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b),
-                 "r"((uint32_t)((VB ? 2 : 1) * kOX * kOY * 4))
-                 : "memory");
+    tma::bar_arrive_tx(b, (uint32_t)((VB ? 2 : 1) * kOX * kOY * 4));
     const uint32_t d = oslot0 + (uint32_t)(s * P::kO);
-    sweep_tma3(d, &maps.uo, b, p0 - 4, j0 - 1, z);
-    if (VB) sweep_tma3(d + kOArr, &maps.bo_other, b, p0 - 4, j0 - 1, z);
+    tma::load3(d, &maps.uo, b, p0 - 4, j0 - 1, z);
+    if (VB) tma::load3(d + kOArr, &maps.bo_other, b, p0 - 4, j0 - 1, z);
   };
   auto issue_w = [&](int q) {
     const int s = q % kRingW, z = ka + q;
     const uint32_t b = wbar(s);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b),
-                 "r"((uint32_t)((VB ? 2 : 1) * 128 * 8 * 4))
-                 : "memory");
+    tma::bar_arrive_tx(b, (uint32_t)((VB ? 2 : 1) * 128 * 8 * 4));
     const uint32_t d = wslot0 + (uint32_t)(s * P::kW);
-    sweep_tma3(d, &maps.f, b, p0, j0, z);
-    if (VB) sweep_tma3(d + kWArr, &maps.bo_own, b, p0, j0, z);
+    tma::load3(d, &maps.f, b, p0, j0, z);
+    if (VB) tma::load3(d + kWArr, &maps.bo_own, b, p0, j0, z);
   };
 
   if (tid == 0) {
-    for (int i = 0; i < kRingO + kRingW; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8u * i) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    for (int i = 0; i < kRingO + kRingW; ++i) tma::bar_init(bar0 + 8u * i);
+    tma::bar_init_fence();
     for (int q = 0; q < min(kRingO - 1, no); ++q) issue_o(q);
     for (int q = 0; q < min(kRingW - 1, nw); ++q) issue_w(q);
   }
@@ -407,11 +356,11 @@ __global__ void __launch_bounds__(kT, VB ? 3 : 4)
     }
     // other planes k - 1, k, k + 1 are sequence numbers i, i + 1, i + 2
     if (i == 0) {
-      ok = ok && sweep_wait(obar(0), 0u);
-      ok = ok && sweep_wait(obar(1 % kRingO), (uint32_t)((1 / kRingO) & 1));
+      ok = ok && tma::bar_wait(obar(0), 0u);
+      ok = ok && tma::bar_wait(obar(1 % kRingO), (uint32_t)((1 / kRingO) & 1));
     }
-    ok = ok && sweep_wait(obar((i + 2) % kRingO), (uint32_t)(((i + 2) / kRingO) & 1));
-    ok = ok && sweep_wait(wbar(i % kRingW), (uint32_t)((i / kRingW) & 1));
+    ok = ok && tma::bar_wait(obar((i + 2) % kRingO), (uint32_t)(((i + 2) / kRingO) & 1));
+    ok = ok && tma::bar_wait(wbar(i % kRingW), (uint32_t)((i / kRingW) & 1));
     if (ok) {
       const int sm = i % kRingO, sc = (i + 1) % kRingO, sp = (i + 2) % kRingO;
       const float* uoc = optr(sc, 0) + r * kOX;
@@ -472,9 +421,9 @@ __global__ void __launch_bounds__(kT, VB ? 3 : 4)
     // the copies issued and not yet waited for by everyone: wait for each
     // slot's last issued phase (bounded) before the CTA's shared memory goes
     for (int q = max(0, issued_o - kRingO); q < issued_o; ++q)
-      sweep_wait(obar(q % kRingO), (uint32_t)((q / kRingO) & 1));
+      tma::bar_wait(obar(q % kRingO), (uint32_t)((q / kRingO) & 1));
     for (int q = max(0, issued_w - kRingW); q < issued_w; ++q)
-      sweep_wait(wbar(q % kRingW), (uint32_t)((q / kRingW) & 1));
+      tma::bar_wait(wbar(q % kRingW), (uint32_t)((q / kRingW) & 1));
   }
 }
 
@@ -811,31 +760,9 @@ __global__ void k_split_beta(const double* beta, const uint8_t* mask, Split32 op
   sel(out, (i + j + k) & 1)[spos(op, i, j, k)] = v;
 }
 
-// cuTensorMapEncodeTiled, fetched from the driver once (null if absent).
-PFN_cuTensorMapEncodeTiled_v12000 sweep_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      p = nullptr;
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }();
-  return fn;
-}
-
-// A colour array of the level as a (W, ny, nz) FP32 tensor, copied in boxes
-// of bx x by x 1; zero fill outside.
+// A colour array of the level as a (W, ny, nz) FP32 tensor.
 bool colour_map(CUtensorMap* m, const float* p, const Split32& op, int bx, int by) {
-  const cuuint64_t dim[3] = {(cuuint64_t)op.W, (cuuint64_t)op.b.ny, (cuuint64_t)op.b.nz};
-  const cuuint64_t stride[2] = {(cuuint64_t)op.W * 4, (cuuint64_t)op.W * op.b.ny * 4};
-  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
-  const cuuint32_t es[3] = {1, 1, 1};
-  return sweep_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)p, dim, stride, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return tma_map_f32(m, p, op.W, op.b.ny, op.b.nz, bx, by);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -865,9 +792,19 @@ namespace {
 // zero, W a multiple of 4 and at least one 128-entry tile, 16-byte aligned
 // arrays, tensor maps encodable); false otherwise (nothing launched).
 bool try_half_sweep_tma(const Split32& op, float alpha, int col, const float* f, float* u,
-                        const float* uo, bool has_mask, cudaStream_t s) {
+                        const float* uo, bool has_mask, int zchunk, cudaStream_t s) {
   const bool vb = op.beta[0] != nullptr;
-  if (op.b.nx % 8 != 0 || op.W < 128 || !sweep_encoder()) return false;
+  if (zchunk < 0 || op.b.nx % 8 != 0 || op.W < 128) return false;
+  const long long tiles = (long long)((op.W + 127) / 128) * ((op.b.ny + 7) / 8);
+  auto ctas = [&](int z) { return tiles * ((op.b.nz + z - 1) / z); };
+  int zc = zchunk;
+  if (zc == 0) {
+    // about four CTAs per slot of the GPU (152 SMs x 3 CTAs), else two;
+    // below that the register-fed kernel (one plane per CTA) fills it better
+    constexpr long long kSlots = 152 * 3;
+    zc = ctas(32) >= 4 * kSlots ? 32 : ctas(16) >= 4 * kSlots ? 16 : 8;
+    if (ctas(zc) < 2 * kSlots) return false;
+  }
   if (!aligned16(f) || !aligned16(u) || !aligned16(uo)) return false;
   if (vb && (!aligned16(op.beta[0]) || !aligned16(op.beta[1]))) return false;
   SweepMaps maps;
@@ -881,8 +818,8 @@ bool try_half_sweep_tma(const Split32& op, float alpha, int col, const float* f,
     maps.bo_own = maps.f;
   }
   if (!sweep_kernels_ready()) return false;
-  dim3 blk(32, 8), g((op.W + 127) / 128, (op.b.ny + 7) / 8, (op.b.nz + kTmaZ - 1) / kTmaZ);
-  auto go = [&](auto kern, int smem) { kern<<<g, blk, smem, s>>>(op, alpha, col, u, maps); };
+  dim3 blk(32, 8), g((op.W + 127) / 128, (op.b.ny + 7) / 8, (op.b.nz + zc - 1) / zc);
+  auto go = [&](auto kern, int smem) { kern<<<g, blk, smem, s>>>(op, alpha, col, zc, u, maps); };
   if (vb) {
     if (has_mask) go(k_half_sweep_tma<true, true>, TmaPlan<true>::smem());
     else go(k_half_sweep_tma<true, false>, TmaPlan<true>::smem());
@@ -893,6 +830,33 @@ bool try_half_sweep_tma(const Split32& op, float alpha, int col, const float* f,
 }
 
 }  // namespace
+
+// cuTensorMapEncodeTiled, fetched from the driver once (null if absent).
+static PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+bool tma_map_f32(CUtensorMap* m, const void* p, long long nx, long long ny, long long nz, int bx,
+                 int by) {
+  if (!tma_encoder() || ((uintptr_t)p & 15u) || (nx * 4) % 16) return false;
+  const cuuint64_t dim[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t stride[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny * 4)};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return tma_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(p), dim, stride,
+                       box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 bool sweep_timed_out() {
   unsigned v = 0;
@@ -905,9 +869,10 @@ bool sweep_timed_out() {
 }
 
 void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
-                         const float* uo, bool zero_other, bool has_mask, cudaStream_t s) {
+                         const float* uo, bool zero_other, bool has_mask, int zchunk,
+                         cudaStream_t s) {
   const bool vb = op.beta[0] != nullptr;
-  if (!zero_other && try_half_sweep_tma(op, alpha, col, f, u, uo, has_mask, s)) {
+  if (!zero_other && try_half_sweep_tma(op, alpha, col, f, u, uo, has_mask, zchunk, s)) {
     add_launches(1);
     return;
   }

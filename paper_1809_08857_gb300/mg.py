@@ -72,7 +72,7 @@ class Options(ctypes.Structure):
                 ("concurrency", ctypes.c_int), ("no_graphs", ctypes.c_int),
                 ("rte_bc", ctypes.c_int), ("ir_zchunk", ctypes.c_int),
                 ("coarse_op", ctypes.c_int), ("fixed_cycles", ctypes.c_int),
-                ("coarse_visits", ctypes.c_int)]
+                ("coarse_visits", ctypes.c_int), ("sweep_zchunk", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -392,15 +392,20 @@ class Solver:
                 for i, k in enumerate(KCLASSES)}
 
     def set_options(self, **kw):
-        """Change nu1, nu2, max_cycles, inner_cycles, concurrency, graphs or
-        ir_zchunk (the refinement pass's z planes per CTA column, 0 =
-        automatic)."""
+        """Change any field of mg_options by name (nu1, nu2, max_cycles,
+        inner_cycles, concurrency, ir_zchunk, fixed_cycles, coarse_visits,
+        sweep_zchunk, ...; graphs=bool sets no_graphs).  The precision,
+        rte_bc and coarse_op are fixed at creation (the library refuses a
+        change)."""
         o = Options.from_buffer_copy(self.options)
+        names = {f[0] for f in Options._fields_}
         for k, v in kw.items():
             if k == "graphs":
                 o.no_graphs = 0 if v else 1
-            else:
+            elif k in names:
                 setattr(o, k, int(v))
+            else:
+                raise TypeError(f"unknown option {k!r}")
         _check(self._lib.mg_set_options(self._ctx, ctypes.byref(o)))
         self.options = o
 
@@ -415,7 +420,7 @@ class Solver:
                                      kap, float(tol), ctypes.byref(best), ctypes.byref(ms)))
         self.options = best
         return ({"nu1": best.nu1, "nu2": best.nu2, "inner_cycles": best.inner_cycles,
-                 "ir_zchunk": best.ir_zchunk}, ms.value)
+                 "ir_zchunk": best.ir_zchunk, "sweep_zchunk": best.sweep_zchunk}, ms.value)
 
     def poisson_residual(self, rho, phi, out=None):
         """r = b - A phi in FP64 (electrode cells of phi are set first)."""

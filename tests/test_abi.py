@@ -148,3 +148,24 @@ def test_noalloc_binding_rejects_mismatched_shapes():
         mg.residual_norm_noalloc(u.view(-1), u.view(-1), 0.1)
     with pytest.raises(ValueError, match="at least one"):
         mg.residual_norm_noalloc(u, u, 0.1, out=torch.empty(0, dtype=torch.float64))
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("sweep_zchunk", 7, b"sweep_zchunk"),
+    ("sweep_zchunk", -2, b"sweep_zchunk"),
+    ("coarse_visits", 3, b"coarse_visits"),
+    ("fixed_cycles", 2, b"fixed_cycles"),
+])
+def test_create_rejects_bad_option_values(lib, field, value, msg):
+    """Option values outside their documented sets are refused before any
+    device work."""
+    from paper_1809_08857_gb300 import mg
+
+    ctx = ctypes.c_void_p()
+    bc = mg.BC((ctypes.c_int * 6)(1, 1, 1, 1, 0, 0), (ctypes.c_double * 6)(0, 0, 0, 0, 0, 1))
+    good = mg.Grid(8, 8, 8, 0.1, (ctypes.c_double * 3)())
+    opt = mg.default_options()
+    setattr(opt, field, value)
+    assert lib.mg_create(ctypes.byref(good), None, None, None, ctypes.byref(bc), ctypes.byref(opt),
+                         None, ctypes.byref(ctx)) == mg.MG_ERR_INVALID_ARG
+    assert msg in lib.mg_last_error()

@@ -15,7 +15,7 @@ class FakeSolver:
 
     def autotune(self, rho, S, kappa, tol):
         self.tunes += 1
-        return {"nu1": 2, "nu2": 1, "inner_cycles": 3, "ir_zchunk": 32}, 12.5
+        return {"nu1": 2, "nu2": 1, "inner_cycles": 3, "ir_zchunk": 32, "sweep_zchunk": 16}, 12.5
 
 
 def test_signature_distinguishes_problem_classes():
@@ -34,7 +34,8 @@ def test_tune_then_hit_cache(tmp_path):
     s2 = FakeSolver()
     e2, hit2 = autotune.tuned(s2, None, None, (1, 2, 3), has_eps=True, cache_path=path, device="D")
     assert hit2 and s2.tunes == 0
-    assert s2.set_calls == [{"nu1": 2, "nu2": 1, "inner_cycles": 3, "ir_zchunk": 32}]
+    assert s2.set_calls == [{"nu1": 2, "nu2": 1, "inner_cycles": 3, "ir_zchunk": 32,
+                             "sweep_zchunk": 16}]
     s3 = FakeSolver()
     _, hit3 = autotune.tuned(s3, None, None, (1, 2, 3), has_eps=False, cache_path=path, device="D")
     assert not hit3 and s3.tunes == 1
@@ -49,11 +50,13 @@ def test_corrupt_cache_is_ignored(tmp_path):
 
 
 def test_entry_without_tile_installs_the_automatic_tile(tmp_path):
-    """Entries written before the refinement-pass tile was tuned install
-    ir_zchunk = 0 (automatic)."""
+    """Entries written before the refinement-pass tile and the staged
+    half-sweep's planes were tuned install ir_zchunk = sweep_zchunk = 0
+    (automatic)."""
     path = str(tmp_path / "cache.json")
     key = autotune.signature("D", FakeSolver.shape, True, False, 1, 1e-10)
     autotune.store(path, key, {"nu1": 1, "nu2": 1, "inner_cycles": 2, "ms": 3.0})
     s = FakeSolver()
     _, hit = autotune.tuned(s, None, None, (1, 2, 3), has_eps=True, cache_path=path, device="D")
-    assert hit and s.set_calls == [{"nu1": 1, "nu2": 1, "inner_cycles": 2, "ir_zchunk": 0}]
+    assert hit and s.set_calls == [{"nu1": 1, "nu2": 1, "inner_cycles": 2, "ir_zchunk": 0,
+                                    "sweep_zchunk": 0}]

@@ -234,9 +234,13 @@ def test_one_cycle_staged_sweep_helmholtz(mg, nu):
         check(g, one_cycle_oracle(oracle.helmholtz(shape, h, k), S, nu), 1)
 
 
-def test_staged_sweep_converges_to_oracle(mg):
+@pytest.mark.parametrize("zchunk", [0, -1, 8, 16, 32])
+def test_staged_sweep_converges_to_oracle(mg, zchunk):
     """The same box solved to 1e-10 in mixed precision with the slab, the
-    electrode and Neumann sides: within 1e-9 of the oracle's answer."""
+    electrode and Neumann sides, for every settable sweep_zchunk (0
+    automatic, -1 the register-fed kernel, 8 / 16 / 32 planes per CTA: 40
+    planes leave a ragged last chunk for each): within 1e-9 of the oracle's
+    answer."""
     shape = TMA_SHAPE
     nz, ny, nx = shape
     h = 1.0 / nx
@@ -249,6 +253,7 @@ def test_staged_sweep_converges_to_oracle(mg):
     bc_value = (0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
     s = mg.Solver(shape, h, eps_r=cuda(eps), mask=cuda(mask), mask_value=cuda(mv),
                   bc_kind=bc_kind, bc_value=bc_value, precision=1)
+    s.set_options(sweep_zchunk=zchunk)
     u = torch.zeros(shape, dtype=torch.float64, device="cuda")
     st = s.solve_poisson(cuda(rho), u, 1e-10)
     s.close()
@@ -257,6 +262,29 @@ def test_staged_sweep_converges_to_oracle(mg):
     ref, _, rel, _ = p.solve(rho / oracle.EPS0, u0=mv, tol=1e-13)
     assert rel < 1e-12
     assert oracle.rel_l2(u.cpu().numpy(), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("ir_zchunk", [0, 16, 32, 128])
+def test_staged_refinement_helmholtz_converges_to_oracle(mg, ir_zchunk):
+    """The three Helmholtz problems of the staged-sweep box solved to 1e-10:
+    their refinement steps run the two-cell pass whose planes arrive by
+    tensor copies (5 CTA columns of 60 cells over 264, the last with 24;
+    2 row tiles of 14 over 20; chunks of 8, 16, 40 or the automatic run over
+    40 planes).  Each answer within 1e-9 of the oracle's."""
+    shape = TMA_SHAPE
+    h = 1.0 / shape[2]
+    S = np.abs(blobs(shape, 34)) / W.EPS0
+    kap = W.helmholtz_kappas()
+    s = mg.Solver(shape, h, precision=1, nu1=2, nu2=1, inner_cycles=2)
+    s.set_options(ir_zchunk=ir_zchunk)
+    psi = [torch.zeros(shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    st = s.solve_helmholtz_batch(cuda(S), psi, kap, 1e-10)
+    s.close()
+    assert all(x["converged"] and x["cycles"] >= 2 for x in st)
+    for p, k in zip(psi, kap):
+        ref, _, rel, _ = oracle.helmholtz(shape, h, k).solve(S, tol=1e-13)
+        assert rel < 1e-12
+        assert oracle.rel_l2(p.cpu().numpy(), ref) <= 1e-9
 
 
 # ---- the face-rule coarse operator (MG_COARSE_FACE, the default) ----------
