@@ -39,6 +39,7 @@ METRIC = "Poisson+3×Helmholtz solves/s to 1e-10 rel. residual at 512³; % HBM r
 UNIT = "solve sets/s (1 set = 1 Poisson + 3 Helmholtz)"
 TOL = 1e-10
 KAPPAS = (10.0, 100.0, 1000.0)
+COPY_STREAMS = 4  # streams per copy direction in the end-to-end leg
 
 
 def parse():
@@ -738,6 +739,27 @@ def run_ours(args):
     bufs = [{"rho": torch.empty_like(rho), "S": torch.empty_like(S),
              "out": [torch.empty_like(phi) for _ in range(4)]} for _ in range(2)]
     s_comp, s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    # each array's copy is split into slabs over several streams, so that
+    # more than one copy engine can carry a direction
+    s_h2d_x = [s_h2d] + [torch.cuda.Stream() for _ in range(COPY_STREAMS - 1)]
+    s_d2h_x = [s_d2h] + [torch.cuda.Stream() for _ in range(COPY_STREAMS - 1)]
+
+    def split_copy(dst, src, streams, after):
+        """dst <- src in len(streams) slabs along z, slab q on streams[q]
+        (each stream first waits for the event `after`, if any); returns the
+        events of the slabs."""
+        nz_ = src.shape[0]
+        evs = []
+        for q, st_ in enumerate(streams):
+            a_, b_ = q * nz_ // len(streams), (q + 1) * nz_ // len(streams)
+            with torch.cuda.stream(st_):
+                if after is not None:
+                    st_.wait_event(after)
+                dst[a_:b_].copy_(src[a_:b_], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(st_)
+                evs.append(ev)
+        return evs
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
@@ -745,11 +767,12 @@ def run_ours(args):
 
     def h2d(i):
         b = bufs[i % 2]
+        # step i - 2 no longer reads these buffers once its solve is done
+        after = ev_done[i % 2] if i >= 2 else None
+        evs = split_copy(b["rho"], rho_h, s_h2d_x, after) + split_copy(b["S"], S_h, s_h2d_x, after)
         with torch.cuda.stream(s_h2d):
-            if i >= 2:
-                s_h2d.wait_event(ev_done[i % 2])  # step i - 2 no longer reads them
-            b["rho"].copy_(rho_h, non_blocking=True)
-            b["S"].copy_(S_h, non_blocking=True)
+            for ev in evs:
+                s_h2d.wait_event(ev)
             ev_in[i % 2].record(s_h2d)
 
     def solve(i):
@@ -765,10 +788,12 @@ def run_ours(args):
 
     def d2h(i):
         b = bufs[i % 2]
+        evs = []
+        for o, d in zip(out_h, b["out"]):
+            evs += split_copy(o, d, s_d2h_x, ev_done[i % 2])
         with torch.cuda.stream(s_d2h):
-            s_d2h.wait_event(ev_done[i % 2])
-            for o, d in zip(out_h, b["out"]):
-                o.copy_(d, non_blocking=True)
+            for ev in evs:
+                s_d2h.wait_event(ev)
             ev_out[i % 2].record(s_d2h)
 
     def e2e_run(k):
@@ -791,9 +816,19 @@ def run_ours(args):
         b.synchronize()
         return round(src.numel() * src.element_size() / (a.elapsed_time(b) * 1e-3) / 1e9, 1)
 
+    def split_gbs(dst, src, streams):
+        torch.cuda.synchronize()
+        t0_ = time.perf_counter()
+        split_copy(dst, src, streams, None)
+        torch.cuda.synchronize()
+        return round(src.numel() * src.element_size() / (time.perf_counter() - t0_) / 1e9, 1)
+
     copy_gbs(bufs[0]["rho"], rho_h, s_h2d)
     rates = {"h2d_gbs": copy_gbs(bufs[0]["rho"], rho_h, s_h2d),
-             "d2h_gbs": copy_gbs(out_h[0], bufs[0]["rho"], s_d2h)}
+             "d2h_gbs": copy_gbs(out_h[0], bufs[0]["rho"], s_d2h),
+             "streams": COPY_STREAMS,
+             "h2d_gbs_split": split_gbs(bufs[0]["rho"], rho_h, s_h2d_x),
+             "d2h_gbs_split": split_gbs(out_h[0], bufs[0]["rho"], s_d2h_x)}
     e2e_run(2)
     torch.cuda.synchronize()
     barrier()

@@ -540,8 +540,18 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2_tma(IrArgs a,
   auto bbar = [&](int w) { return bar0 + 8u * (uint32_t)(kIrU + w % kIrB); };
   auto upar = [&](int q) { return (uint32_t)((q / kIrU) & 1); };
   auto bpar = [&](int w) { return (uint32_t)((w / kIrB) & 1); };
-  auto uslot = [&](int q) { return gbase + (q % kIrU) * kIrUSlot; };
-  auto bslot = [&](int w) { return gbase + kIrU * kIrUSlot + (w % kIrB) * kIrBSlot; };
+  // the consumers walk both rings in order: slot and phase parity of the
+  // next sequence number, advanced without divisions
+  struct Ring {
+    int slot = 0;
+    uint32_t par = 0;
+    __device__ void next(int n) {
+      if (++slot == n) {
+        slot = 0;
+        par ^= 1u;
+      }
+    }
+  };
 
   // producer (thread 0): iterate/correction sequence q is plane z0 - 1 + q,
   // b sequence w is plane z0 + w
@@ -564,12 +574,12 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2_tma(IrArgs a,
     tma::load3(base + (uint32_t)(kIrU * kIrUSlot + (w % kIrB) * kIrBSlot), &maps.b, b, bxo, byo,
                z0 + w);
   };
-  // u + e of plane z0 - 1 + q for the thread's pair, from its ring slot
-  auto combine = [&](int q, Df2& v) {
+  // u + e of plane z0 - 1 + q for the thread's pair, from ring slot `slot`
+  auto combine = [&](int q, int slot, Df2& v) {
     const int k = z0 - 1 + q;
     v = Df2{zero2, zero2};
     if (!(in && k >= 0 && k < nz)) return;
-    const unsigned char* sl = uslot(q);
+    const unsigned char* sl = gbase + slot * kIrUSlot;
     const float4 u4 = reinterpret_cast<const float4*>(sl)[ty * TX + tx];
     const float* e0 = reinterpret_cast<const float*>(sl + kIrUBytes) + ty * 36 + tx + eo;
     const float* e1 = reinterpret_cast<const float*>(sl + kIrUBytes + kIrEBytes) + ty * 36 + tx + eo;
@@ -600,16 +610,20 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2_tma(IrArgs a,
   __syncthreads();
   bool ok = tma::bar_wait(ubar(0), 0u) && tma::bar_wait(ubar(1), 0u) && tma::bar_wait(ubar(2), 0u);
   Df2 um, uc, up;
-  combine(0, um);
-  combine(1, uc);
-  combine(2, up);
+  combine(0, 0, um);
+  combine(1, 1, uc);
+  combine(2, 2, up);
+  Ring ur, br;  // next iterate sequence to combine: 3 (slot 0, parity 1); next b: 0
+  ur.par = 1u;
   float2 ss = zero2;
   if (!__syncthreads_or(!ok)) {
     if (tid == 0)
       for (; issued_u < min(nq, 6); ++issued_u) issue_u(issued_u);
     for (int i = 0; i < n; ++i) {
       const int k = z0 + i;
-      ok = tma::bar_wait(bbar(i), bpar(i)) && ok;
+      ok = tma::bar_wait(bar0 + 8u * (uint32_t)(kIrU + br.slot), br.par) && ok;
+      const unsigned char* bsl = gbase + kIrU * kIrUSlot + br.slot * kIrBSlot;
+      br.next(kIrB);
       const int buf = i & 1;
       const float4 uc4 = make_float4(uc.hi.x, uc.lo.x, uc.hi.y, uc.lo.y);
       pl[buf][ty][tx] = uc4;
@@ -630,8 +644,7 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2_tma(IrArgs a,
       if (own) {
         const Df2 L{make_float2(pbh, uc.hi.x), make_float2(pbl, uc.lo.x)};
         const Df2 R{make_float2(uc.hi.y, nah), make_float2(uc.lo.y, nal)};
-        const float4 b4 =
-            reinterpret_cast<const float4*>(bslot(i))[(ty - 1) * ((TX - 2)) + (tx - 1)];
+        const float4 b4 = reinterpret_cast<const float4*>(bsl)[(ty - 1) * (TX - 2) + (tx - 1)];
         DfAcc2 acc{make_float2(b4.x, b4.z), make_float2(b4.y, b4.w)};
         const bool zm = k > 0, zp = k < nz - 1;
         Df2 dg = dxy;
@@ -662,8 +675,9 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2_tma(IrArgs a,
       um = uc;
       uc = up;
       if (i + 1 < n) {
-        ok = tma::bar_wait(ubar(i + 3), upar(i + 3)) && ok;
-        combine(i + 3, up);
+        ok = tma::bar_wait(bar0 + 8u * (uint32_t)ur.slot, ur.par) && ok;
+        combine(i + 3, ur.slot, up);
+        ur.next(kIrU);
       }
     }
   } else {
@@ -691,12 +705,27 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2_tma(IrArgs a,
 
 // 1.0 into *flag (mapped host memory) if any of u[0..n) is neither +0 nor -0
 // (a NaN counts as nonzero); at most one store per block.
+// The test is on the bits (all but the sign zero), on the integer pipe, 16
+// bytes per load where u is 16-byte aligned.
 __global__ void k_nonzero(const double* __restrict__ u, long long n, double* flag) {
-  bool nz = false;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x)
-    nz |= !(u[c] == 0.0);
-  if (__syncthreads_or(nz) && threadIdx.x == 0) *flag = 1.0;
+  const unsigned long long mag = 0x7fffffffffffffffull;
+  unsigned long long any = 0;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long head = 0;
+  if (((uintptr_t)u & 15u) == 0) {
+    const ulonglong2* u2 = reinterpret_cast<const ulonglong2*>(u);
+    const long long n2 = n / 2;
+    for (long long c = t0; c < n2; c += 2 * stride) {
+      const ulonglong2 a = u2[c];
+      const ulonglong2 b = c + stride < n2 ? u2[c + stride] : make_ulonglong2(0, 0);
+      any |= (a.x | a.y | b.x | b.y) & mag;
+    }
+    head = 2 * n2;
+  }
+  const unsigned long long* ub = reinterpret_cast<const unsigned long long*>(u);
+  for (long long c = head + t0; c < n; c += stride) any |= ub[c] & mag;
+  if (__syncthreads_or(any != 0) && threadIdx.x == 0) *flag = 1.0;
 }
 
 // First pass of a solve from a zero guess on a grid without electrode cells:
@@ -753,24 +782,41 @@ __global__ void k_df_to_f64(const float2* __restrict__ in, const uint8_t* __rest
 }
 
 // The same for two cells per thread (n even, arrays on 16-byte boundaries):
-// one 16-byte load and one 16-byte store per pair.
-__global__ void k_df_to_f64x2(const float4* __restrict__ in, const uchar2* __restrict__ mask,
-                              double2* __restrict__ out, long long npair, double scale) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= npair) return;
-  const float4 v = in[c];
-  double2 u = make_double2(widen(v.x) + widen(v.y), widen(v.z) + widen(v.w));
-  if (scale != 1.0) u = make_double2(u.x * scale, u.y * scale);
-  if (mask) {
-    const uchar2 m = mask[c];
-    if (m.x || m.y) {  // electrode cells keep the caller's values
-      double* o = reinterpret_cast<double*>(out + c);
-      if (!m.x) o[0] = u.x;
-      if (!m.y) o[1] = u.y;
-      return;
-    }
+// one 16-byte load and one 16-byte store per pair, kX2 pairs per thread a
+// grid stride apart (their loads issue back to back).  Scaled: the answer
+// of a rescaled problem (times 1 / scale); Masked: electrode cells keep the
+// caller's values.
+constexpr int kX2 = 4;
+template <bool Scaled, bool Masked>
+__global__ void __launch_bounds__(256) k_df_to_f64x2(const float4* __restrict__ in,
+                                                     const uchar2* __restrict__ mask,
+                                                     double2* __restrict__ out, long long npair,
+                                                     double scale) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float4 v[kX2];
+#pragma unroll
+  for (int q = 0; q < kX2; ++q) {
+    const long long c = c0 + q * stride;
+    v[q] = c < npair ? in[c] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   }
-  out[c] = u;
+#pragma unroll
+  for (int q = 0; q < kX2; ++q) {
+    const long long c = c0 + q * stride;
+    if (c >= npair) break;
+    double2 u = make_double2(widen(v[q].x) + widen(v[q].y), widen(v[q].z) + widen(v[q].w));
+    if (Scaled) u = make_double2(u.x * scale, u.y * scale);
+    if (Masked) {
+      const uchar2 m = mask[c];
+      if (m.x || m.y) {
+        double* o = reinterpret_cast<double*>(out + c);
+        if (!m.x) o[0] = u.x;
+        if (!m.y) o[1] = u.y;
+        continue;
+      }
+    }
+    out[c] = u;
+  }
 }
 
 }  // namespace
@@ -963,9 +1009,17 @@ void launch_df_to_f64(const float2* in, const uint8_t* mask, double* out, long l
   auto al = [](const void* p, unsigned m) { return ((uintptr_t)p & (m - 1)) == 0; };
   if (n % 2 == 0 && al(in, 16) && al(out, 16) && al(mask, 2)) {
     const long long np = n / 2;
-    k_df_to_f64x2<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
-        reinterpret_cast<const float4*>(in), reinterpret_cast<const uchar2*>(mask),
-        reinterpret_cast<double2*>(out), np, scale);
+    const unsigned g = (unsigned)((np + 256LL * kX2 - 1) / (256LL * kX2));
+    const auto* i4 = reinterpret_cast<const float4*>(in);
+    const auto* m2 = reinterpret_cast<const uchar2*>(mask);
+    auto* o2 = reinterpret_cast<double2*>(out);
+    if (scale != 1.0) {
+      if (mask) k_df_to_f64x2<true, true><<<g, 256, 0, s>>>(i4, m2, o2, np, scale);
+      else k_df_to_f64x2<true, false><<<g, 256, 0, s>>>(i4, m2, o2, np, scale);
+    } else {
+      if (mask) k_df_to_f64x2<false, true><<<g, 256, 0, s>>>(i4, m2, o2, np, scale);
+      else k_df_to_f64x2<false, false><<<g, 256, 0, s>>>(i4, m2, o2, np, scale);
+    }
   } else {
     k_df_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, mask, out, n, scale);
   }

@@ -185,6 +185,45 @@ __device__ __forceinline__ float4 quad_update(const Split32& op, float alpha, co
   return make_float4(out[0], out[1], out[2], out[3]);
 }
 
+// quad_update (other colour known) with each cell's face sums formed as
+// trees: the six face weights are independent, so their reciprocals issue
+// back to back, and the diagonal and off-diagonal sums are three adds deep
+// instead of six.  The staged half-sweep, whose operands come from shared
+// memory, is bound by the latency of these dependent chains rather than by
+// HBM.  Same weights and faces as quad_update; only the order of the FP32
+// additions differs.
+template <bool VB, bool HasMask, int S>
+__device__ __forceinline__ float4 quad_update_tree(const Split32& op, float alpha, const Quad& q,
+                                                   int pp, bool ym, bool yp, bool zm, bool zp) {
+  float out[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int p = pp + e;
+    const float hc = VB ? el(q.BO, e) : 0.5f;
+    const float wd = VB ? wdir(hc) : 2.0f;
+    // faces -x, +x, -y, +y, -z, +z: in-box neighbour or domain face
+    const bool inb[6] = {!(S == 0 && p == 0), !(S == 1 && p == op.W - 1), ym, yp, zm, zp};
+    const float hn[6] = {q.bx[e + S], q.bx[e + S + 1], el(q.BYm, e),
+                         el(q.BYp, e), el(q.BZm, e),   el(q.BZp, e)};
+    const float un[6] = {q.ux[e + S], q.ux[e + S + 1], el(q.UYm, e),
+                         el(q.UYp, e), el(q.UZm, e),   el(q.UZp, e)};
+    float w[6], t[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      float wf = 1.0f;
+      if (VB) wf = HasMask ? wface(hc, hn[f]) : __fdividef(1.0f, hc + hn[f]);
+      w[f] = inb[f] ? wf : wd * op.rho[f];  // a domain face adds wd rho_f to the diagonal
+      t[f] = inb[f] ? wf * un[f] : 0.0f;
+    }
+    const float d = ((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]);
+    const float o = ((t[0] + t[1]) + (t[2] + t[3])) + (t[4] + t[5]);
+    float v = __fdividef(fmaf(o, op.ih2, el(q.F, e)), fmaf(d, op.ih2, alpha));
+    if (HasMask && hc < 0.0f) v = el(q.U, e);
+    out[e] = v;
+  }
+  return make_float4(out[0], out[1], out[2], out[3]);
+}
+
 template <bool VB, bool ZeroOther, bool HasMask>
 __global__ void __launch_bounds__(kT, 4) k_half_sweep_v4(Split32 op, float alpha, int col,
                                                          const float* __restrict__ f,
@@ -395,8 +434,8 @@ __global__ void __launch_bounds__(kT, VB ? 3 : 4)
       q.bx[5] = bnext;
       const bool zm = k > 0, zp = k < nz - 1;
       const int sx = (j + k + col) & 1;  // warp-uniform
-      const float4 v = sx ? quad_update<VB, false, HasMask, 1>(op, alpha, q, pp, ym, yp, zm, zp)
-                          : quad_update<VB, false, HasMask, 0>(op, alpha, q, pp, ym, yp, zm, zp);
+      const float4 v = sx ? quad_update_tree<VB, HasMask, 1>(op, alpha, q, pp, ym, yp, zm, zp)
+                          : quad_update_tree<VB, HasMask, 0>(op, alpha, q, pp, ym, yp, zm, zp);
       if (active) {
         float* dst = u + ((long long)k * ny + j) * W + pp;
         if (!HasMask || (q.BO.x >= 0.0f && q.BO.y >= 0.0f && q.BO.z >= 0.0f && q.BO.w >= 0.0f)) {

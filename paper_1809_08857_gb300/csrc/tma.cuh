@@ -49,24 +49,27 @@ __device__ __forceinline__ void bar_arrive_tx(uint32_t bar, uint32_t bytes) {
                : "memory");
 }
 
+// one test of the phase with this parity (true once it has completed)
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
 // true once the phase with this parity has completed; false after kWaitIters
-// tries or kWaitNs nanoseconds
+// tries or kWaitNs nanoseconds.  The first test needs no clock (the copies
+// are usually in by then).
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-  unsigned long long t0 = 0;
-  for (long long it = 0; it < kWaitIters; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 63) == 0) {
-      const unsigned long long t = now_ns();
-      if (it == 0) t0 = t;
-      else if (t - t0 > kWaitNs) return false;
-    }
+  if (bar_try(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  for (long long it = 1; it < kWaitIters; ++it) {
+    if (bar_try(bar, parity)) return true;
+    if ((it & 63) == 0 && now_ns() - t0 > kWaitNs) return false;
   }
   return false;
 }
