@@ -252,10 +252,11 @@ def source_hash(files):
 
 
 KERNEL_SOURCES = {
-    "smooth": ["paper_1809_08857_gb300/csrc/mg_split32.cu"],
+    "smooth": ["paper_1809_08857_gb300/csrc/mg_split32.cu", "paper_1809_08857_gb300/csrc/tma.cuh"],
     "restrict": ["paper_1809_08857_gb300/csrc/mg_split32.cu"],
     "prolong": ["paper_1809_08857_gb300/csrc/mg_split32.cu"],
-    "resid64": ["paper_1809_08857_gb300/csrc/mg_ir.cu", "paper_1809_08857_gb300/csrc/df.cuh"],
+    "resid64": ["paper_1809_08857_gb300/csrc/mg_ir.cu", "paper_1809_08857_gb300/csrc/df.cuh",
+                "paper_1809_08857_gb300/csrc/tma.cuh"],
 }
 
 
