@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--coarse-visits", type=int, default=0,
                     help="V-cycles on the first coarse level per finest-level cycle "
                          "(0 = the library default, one)")
+    ap.add_argument("--stack", action="store_true",
+                    help="stack the Helmholtz problems' V-cycles (mg_options.stack)")
     ap.add_argument("--no-fp64-leg", action="store_true",
                     help="skip the FP64-mode GPU solve set among the extras")
     return ap.parse_args()
@@ -685,6 +687,8 @@ def run_ours(args):
                                   cache_path=cache)
     if args.coarse_visits:
         solver.set_options(coarse_visits=args.coarse_visits)
+    if args.stack:
+        solver.set_options(stack=1)
     phi = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
     psi = [torch.zeros_like(phi) for _ in range(3)]
     cycles = [0, 0, 0, 0]
@@ -881,7 +885,8 @@ def run_ours(args):
                            nu2=solver.options.nu2, inner_cycles=solver.options.inner_cycles,
                            ir_zchunk=solver.options.ir_zchunk,
                            sweep_zchunk=solver.options.sweep_zchunk,
-                           coarse_visits=max(1, solver.options.coarse_visits)),
+                           coarse_visits=max(1, solver.options.coarse_visits),
+                           stack=solver.options.stack),
             "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": launches, "cycles_per_problem": cycles,
             "residual_per_step": history,

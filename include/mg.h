@@ -146,6 +146,16 @@ typedef struct {
                        about four CTAs per SM slot, and the register-fed form
                        where even 8 gives fewer than two); -1 = the
                        register-fed form on every level (0) */
+  int stack;        /* mixed mode: 1 = the Helmholtz problems of one context
+                       in one solve call (those of mg_solve_helmholtz_batch,
+                       mg_solve_set, mg_solve_photoionization, or of one
+                       context in mg_solve_batch) run their FP32 V-cycles
+                       stacked along z, one launch per level step for all of
+                       them, where the grid has no electrode cells, Dirichlet
+                       radiative-transfer faces and an even number of planes
+                       on every level; 0 = every problem its own V-cycles on
+                       its own stream (0: measured faster at 512^3, where the
+                       problems' concurrency already hides the coarse levels) */
 } mg_options;
 
 /* Per-solve statistics.  hist[c] is the relative residual after c cycles

@@ -124,14 +124,22 @@ struct StepGraph {
   const float2* b = nullptr;
   const float2* u_in = nullptr;
   float2* u_out = nullptr;
+  // a stack's step: the members taking part, and per member its work slot,
+  // iterate parity and alpha
+  unsigned act = 0;
+  std::vector<const void*> key;
+  std::vector<double> keyd;
   cudaGraphExec_t exec = nullptr;
   long long launches = 0;
   std::vector<ProfRec> recs;  // event pairs baked into the graph (profiling)
   unsigned long long stamp = 0;
 };
 
-// Everything one problem needs to run concurrently with the others.
+// Everything one problem needs to run concurrently with the others (or, with
+// nb > 1, the stacked FP32 level arrays and stream of nb problems whose
+// V-cycles run together; see vcycle32_stack).
 struct Work {
+  int nb = 1;
   cudaStream_t s = nullptr;
   std::vector<LevelWork> lw;
   double* phi_tmp = nullptr;  // FP64 scratch field (warm start; allocated when needed)
@@ -166,6 +174,7 @@ struct mg_ctx {
   double *gj_row = nullptr, *gj_col = nullptr;
   std::vector<Coarse> coarse;
   std::vector<Work*> work;
+  std::vector<Work*> stacks;  // stacked level arrays, one per stack size in use
   cudaEvent_t fork = nullptr;
   std::vector<void*> allocs;
   std::vector<void*> host_allocs;
@@ -529,6 +538,145 @@ mg_status vcycle32(mg_ctx* c, Work* w, Kind kind, double alpha, int l, bool firs
   return check_launch();
 }
 
+// ---- stacked Helmholtz V-cycles -------------------------------------------
+//
+// The Helmholtz problems of one context (the three terms of Eq. 3) share the
+// grid and the constant coefficient and differ in alpha = kappa_j^2 and in
+// their right-hand sides.  Their FP32 V-cycles run as one stacked level: in
+// every level array the problems follow one another along z (Split32::nb,
+// nzp), so each half-sweep, restriction and prolongation of a level is one
+// launch for all of them, and a problem that has met tol drops out through
+// the active mask while the others go on.  Each problem keeps its own
+// double-float iterate, b, refinement pass, norms and statistics; the
+// coarsest level is solved per problem (its own dense inverse for its alpha).
+
+// A context's Helmholtz problems are stacked if its options ask for it and the
+// grid allows it: no electrode cells (the
+// constant-coefficient kernels), domain faces that do not depend on alpha
+// (Dirichlet radiative-transfer faces, no composite-solve Robin faces), and an
+// even number of planes on every level (a cell's colour is then the same
+// counted in its problem or in the stack).
+bool stack_ok(const mg_ctx* c) {
+  if (!c->opt.stack || c->lv[0].mask || c->robin_a >= 0.0 ||
+      c->opt.rte_bc != MG_RTE_BC_DIRICHLET)
+    return false;
+  for (const Level& L : c->lv)
+    if (L.b.nz % 2 != 0 || L.bh[0]) return false;
+  return true;
+}
+
+// The stacked work of nb problems (allocated on first use).
+mg_status get_stack(mg_ctx* c, int nb, Work** out) {
+  for (Work* w : c->stacks)
+    if (w->nb == nb) {
+      *out = w;
+      return MG_OK;
+    }
+  Work* w = new (std::nothrow) Work;
+  if (!w) return fail(MG_ERR_OOM, "host allocation failed");
+  c->stacks.push_back(w);
+  w->nb = nb;
+  MG_CUDA(cudaStreamCreateWithFlags(&w->s, cudaStreamNonBlocking));
+  MG_CUDA(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming));
+  const int nlev = (int)c->lv.size();
+  w->lw.resize(nlev);
+  for (int l = 0; l < nlev; ++l)
+    for (int col = 0; col < 2; ++col) {
+      const size_t ns = (size_t)c->lv[l].ns * nb;
+      MG_TRY(c->alloc(&w->lw[l].u32[col], ns, true));
+      MG_TRY(c->alloc(&w->lw[l].f32[col], ns, true));
+      if (l == nlev - 1) MG_TRY(c->alloc(&w->lw[l].r32[col], ns, true));
+    }
+  MG_CUDA(cudaStreamSynchronize(c->stream));
+  *out = w;
+  return MG_OK;
+}
+
+// The level-l operator of a stack of nb Helmholtz problems (its planes span
+// the stack) and the stack's description (alpha[q] of member q; bit q of
+// active: member q takes part).
+mg::Split32 sop_stack(const mg_ctx* c, int l, const double* alpha, int nb, unsigned active,
+                      mg::Stk32* st) {
+  mg::Split32 op = sop(c, l, kHelmholtz, alpha[0]);
+  op.b.nz *= nb;
+  *st = mg::Stk32{};
+  st->nb = nb;
+  st->nzp = c->lv[l].b.nz;
+  st->active = active;
+  for (int q = 0; q < nb; ++q) st->pa[q] = (float)alpha[q];
+  return op;
+}
+
+int popcount(unsigned v) {
+  int k = 0;
+  for (; v; v &= v - 1) ++k;
+  return k;
+}
+
+// One FP32 V-cycle of the active members of a stack from level l down
+// (vcycle32 for nb problems at once).
+mg_status vcycle32_stack(mg_ctx* c, Work* w, const double* alpha, unsigned active, int l,
+                         bool first_zero) {
+  cudaStream_t s = w->s;
+  const int nb = w->nb;
+  const int Lc = (int)c->lv.size() - 1;
+  Level& L = c->lv[l];
+  LevelWork& X = w->lw[l];
+  const double n = (double)L.b.n() * popcount(active);
+  if (l == Lc) {
+    for (int q = 0; q < nb; ++q) {
+      if (!((active >> q) & 1u)) continue;
+      const double* Minv;
+      MG_TRY(coarse_inverse(c, kHelmholtz, alpha[q], &Minv));
+      const mg::Split32 op = sop(c, l, kHelmholtz, alpha[q]);
+      const long long o = (long long)q * L.ns;
+      float* f[2] = {X.f32[0] + o, X.f32[1] + o};
+      float* u[2] = {X.u32[0] + o, X.u32[1] + o};
+      float* r[2] = {X.r32[0] + o, X.r32[1] + o};
+      {
+        Scope sc(c, s, MG_KCLASS_COARSE, 0);
+        mg::launch_resid32s(op, (float)alpha[q], cp(f), cp(u), mp(r), s);
+      }
+      {
+        Scope sc(c, s, MG_KCLASS_COARSE, 0);
+        mg::launch_dense_apply32s(op, Minv, cp(r), mp(u), s);
+      }
+    }
+    return check_launch();
+  }
+  mg::Stk32 st;
+  const mg::Split32 op = sop_stack(c, l, alpha, nb, active, &st);
+  const float a32 = (float)alpha[0];  // the kernels take each member's from st.pa
+  const int cls_s = l == 0 ? MG_KCLASS_SMOOTH : MG_KCLASS_COARSE;
+  auto smooth = [&](int sweeps, bool zero) {
+    for (int q = 0; q < sweeps; ++q)
+      for (int col = 0; col < 2; ++col) {
+        const bool zo = zero && q == 0 && col == 0;
+        Scope sc(c, s, cls_s, n * ((zo ? 0.0 : 2.0) + 2.0 + 2.0));
+        mg::launch_half_sweep32(op, a32, col, X.f32[col], X.u32[col], X.u32[col ^ 1], zo, false,
+                                c->opt.sweep_zchunk, s, &st);
+      }
+  };
+  smooth(c->opt.nu1, first_zero);
+  LevelWork& Y = w->lw[l + 1];
+  mg::Stk32 cst;
+  const mg::Split32 cop = sop_stack(c, l + 1, alpha, nb, active, &cst);
+  {
+    Scope sc(c, s, l == 0 ? MG_KCLASS_RESTRICT : MG_KCLASS_COARSE, n * (4.0 + 2.0 + 1.0));
+    mg::launch_resid_restrict32s(op, cop, a32, cp(X.f32), cp(X.u32), mp(Y.f32), mp(Y.u32), s,
+                                 &st);
+  }
+  const int visits = coarse_visits(c, l);
+  for (int q = 0; q < visits; ++q)
+    MG_TRY(vcycle32_stack(c, w, alpha, active, l + 1, q == 0));
+  {
+    Scope sc(c, s, l == 0 ? MG_KCLASS_PROLONG : MG_KCLASS_COARSE, n * (4.0 + 0.5));
+    mg::launch_prolong32s(op, cop, cp(Y.u32), mp(X.u32), s, &st);
+  }
+  smooth(c->opt.nu2, false);
+  return check_launch();
+}
+
 // ---- FP64 refinement step / residual norm ----------------------------------
 
 // Operands of one refinement pass: b as double-floats (bdf) or FP64 (b64,
@@ -549,6 +697,10 @@ struct IrIo {
   bool znorm = false;
   double in_scale = 1.0;  // FP64 inputs (b64, u64) multiplied by this power of two on load
   bool zero_guess = false;  // first pass of a zero guess without electrodes (pointwise)
+  // the correction e and the residual r in other split arrays than the work
+  // slot's level 0 (a member's slice of a stack); null: the work slot's
+  const float* e_ptr[2] = {nullptr, nullptr};
+  float* r_ptr[2] = {nullptr, nullptr};
 };
 
 // Enqueue one fused refinement pass on level 0 and the read-back of ||r||^2
@@ -570,10 +722,10 @@ mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha
   a.udf_in = io.udf_in;
   a.u_in = io.u64;
   a.udf_out = io.udf_out;
-  a.e[0] = io.with_e ? X.u32[0] : nullptr;
-  a.e[1] = io.with_e ? X.u32[1] : nullptr;
-  a.r[0] = io.store_r ? X.f32[0] : nullptr;
-  a.r[1] = io.store_r ? X.f32[1] : nullptr;
+  for (int col = 0; col < 2; ++col) {
+    a.e[col] = io.with_e ? (io.e_ptr[col] ? io.e_ptr[col] : X.u32[col]) : nullptr;
+    a.r[col] = io.store_r ? (io.r_ptr[col] ? io.r_ptr[col] : X.f32[col]) : nullptr;
+  }
   a.W = L0.W;
   a.partial = w->partial;
   a.partial_z = io.znorm ? w->partial + c->npartial : nullptr;
@@ -601,6 +753,8 @@ mg_status enqueue_ir(mg_ctx* c, Work* w, cudaStream_t s, Kind kind, double alpha
   }
   return check_launch();
 }
+
+struct Stack;
 
 // One problem of a (possibly concurrent) solve.
 struct Prob {
@@ -632,6 +786,24 @@ struct Prob {
   int phase = 0;
   bool done = false;
   mg_status status = MG_OK;
+  const StepGraph* g = nullptr;
+  // member sq of a stack: its refinement steps run with the stack's
+  // (waiting: ready for the stack's next step)
+  Stack* stk = nullptr;
+  int sq = 0;
+  bool waiting = false;
+};
+
+// Helmholtz problems of one context stepping together (vcycle32_stack).
+struct Stack {
+  mg_ctx* c = nullptr;
+  Work* w = nullptr;          // stacked level arrays, stream, step graphs
+  std::vector<Prob*> m;       // members, m[q] has sq = q
+  double alpha[mg::kMaxStack] = {};
+  bool started = false;       // the first step has been enqueued
+  bool running = false;       // a step is in flight on w->s
+  unsigned stepping = 0;      // members of the step in flight
+  int ic = 0;                 // its inner V-cycles
   const StepGraph* g = nullptr;
 };
 
@@ -731,24 +903,12 @@ mg_status enqueue_step_direct(Prob& p) {
   return enqueue_ir(c, p.w, p.w->s, p.kind, p.alpha, io, 1);
 }
 
-// Cached graph of the step for p's current (u_in, u_out) parity.
-mg_status step_graph(Prob& p, const StepGraph** out) {
-  mg_ctx* c = p.c;
-  Work* w = p.w;
-  const int ic = p.ic;
-  for (StepGraph& g : w->graphs)
-    if (g.kind == p.kind && g.alpha == p.alpha && g.ic == ic && g.nu1 == c->opt.nu1 &&
-        g.nu2 == c->opt.nu2 && g.zc == c->opt.ir_zchunk && g.cv == c->opt.coarse_visits &&
-        g.sz == c->opt.sweep_zchunk && g.prof == c->prof && g.b == w->bdf &&
-        g.u_in == p.cur &&
-        g.u_out == p.other) {
-      g.stamp = ++c->clock;
-      *out = &g;
-      return MG_OK;
-    }
-  const double* Minv;
-  MG_TRY(coarse_inverse(c, p.kind, p.alpha, &Minv));  // never inside the capture
-  if ((int)w->graphs.size() >= kMaxGraphs) {         // evict the least recently used
+// Captures body() on w's stream into g (whose key the caller set; the option
+// fields are filled here), evicting the least recently used graph of w when
+// it holds kMaxGraphs; *out points at the stored graph.
+template <class Body>
+mg_status capture_step(mg_ctx* c, Work* w, StepGraph&& g, Body body, const StepGraph** out) {
+  if ((int)w->graphs.size() >= kMaxGraphs) {  // evict the least recently used
     size_t old = 0;
     for (size_t q = 1; q < w->graphs.size(); ++q)
       if (w->graphs[q].stamp < w->graphs[old].stamp) old = q;
@@ -759,19 +919,12 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
     }
     w->graphs.erase(w->graphs.begin() + old);
   }
-  StepGraph g;
-  g.kind = p.kind;
-  g.alpha = p.alpha;
-  g.ic = ic;
   g.nu1 = c->opt.nu1;
   g.nu2 = c->opt.nu2;
   g.zc = c->opt.ir_zchunk;
   g.cv = c->opt.coarse_visits;
   g.sz = c->opt.sweep_zchunk;
   g.prof = c->prof;
-  g.b = w->bdf;
-  g.u_in = p.cur;
-  g.u_out = p.other;
   // the event pool must not need to grow inside the capture
   if (c->prof)
     while (c->pool.size() < 1024) {
@@ -782,7 +935,7 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
   const long long l0 = mg::launch_count();
   MG_CUDA(cudaStreamBeginCapture(w->s, cudaStreamCaptureModeThreadLocal));
   c->capture = &g.recs;
-  mg_status st = enqueue_step_direct(p);
+  mg_status st = body();
   c->capture = nullptr;
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(w->s, &graph);
@@ -804,8 +957,39 @@ mg_status step_graph(Prob& p, const StepGraph** out) {
   return MG_OK;
 }
 
+// Cached graph of the step for p's current (u_in, u_out) parity.
+mg_status step_graph(Prob& p, const StepGraph** out) {
+  mg_ctx* c = p.c;
+  Work* w = p.w;
+  const int ic = p.ic;
+  for (StepGraph& g : w->graphs)
+    if (g.kind == p.kind && g.alpha == p.alpha && g.ic == ic && g.nu1 == c->opt.nu1 &&
+        g.nu2 == c->opt.nu2 && g.zc == c->opt.ir_zchunk && g.cv == c->opt.coarse_visits &&
+        g.sz == c->opt.sweep_zchunk && g.prof == c->prof && g.b == w->bdf &&
+        g.u_in == p.cur &&
+        g.u_out == p.other) {
+      g.stamp = ++c->clock;
+      *out = &g;
+      return MG_OK;
+    }
+  const double* Minv;
+  MG_TRY(coarse_inverse(c, p.kind, p.alpha, &Minv));  // never inside the capture
+  StepGraph g;
+  g.kind = p.kind;
+  g.alpha = p.alpha;
+  g.ic = ic;
+  g.b = w->bdf;
+  g.u_in = p.cur;
+  g.u_out = p.other;
+  return capture_step(c, w, std::move(g), [&] { return enqueue_step_direct(p); }, out);
+}
+
 mg_status enqueue_step(Prob& p) {
   p.g = nullptr;
+  if (p.stk) {  // the stack's next step takes it (solve_mixed)
+    p.waiting = true;
+    return MG_OK;
+  }
   if (p.c->opt.no_graphs) {
     MG_TRY(enqueue_step_direct(p));
   } else {
@@ -819,7 +1003,95 @@ mg_status enqueue_step(Prob& p) {
   return MG_OK;
 }
 
+// The stack's refinement step for the members in act: ic stacked V-cycles on
+// their residuals, then each member's refinement pass (u_out = u_in + e,
+// r = b - A u_out into its slice of the stack's level 0, ||r||^2 into its
+// host slot 1), all on the stack's stream.
+mg_status enqueue_stack_direct(Stack& S, unsigned act, int ic) {
+  mg_ctx* c = S.c;
+  for (int v = 0; v < ic; ++v) MG_TRY(vcycle32_stack(c, S.w, S.alpha, act, 0, v == 0));
+  const long long ns0 = c->lv[0].ns;
+  LevelWork& X = S.w->lw[0];
+  for (Prob* pp : S.m) {
+    Prob& p = *pp;
+    if (!((act >> p.sq) & 1u)) continue;
+    IrIo io;
+    io.bdf = p.w->bdf;
+    io.udf_in = p.cur;
+    io.udf_out = p.other;
+    io.with_e = true;
+    io.store_r = true;
+    for (int col = 0; col < 2; ++col) {
+      io.e_ptr[col] = X.u32[col] + p.sq * ns0;
+      io.r_ptr[col] = X.f32[col] + p.sq * ns0;
+    }
+    MG_TRY(enqueue_ir(c, p.w, S.w->s, p.kind, p.alpha, io, 1));
+  }
+  return MG_OK;
+}
+
+// Cached graph of the stack's step (members act, ic inner V-cycles, the
+// members' current iterate parity).
+mg_status stack_graph(Stack& S, unsigned act, int ic, const StepGraph** out) {
+  mg_ctx* c = S.c;
+  Work* w = S.w;
+  std::vector<const void*> key;
+  std::vector<double> keyd;
+  for (const Prob* p : S.m) {
+    key.push_back(p->w);
+    key.push_back(p->cur);
+    keyd.push_back(p->alpha);
+  }
+  for (StepGraph& g : w->graphs)
+    if (g.act == act && g.ic == ic && g.nu1 == c->opt.nu1 && g.nu2 == c->opt.nu2 &&
+        g.zc == c->opt.ir_zchunk && g.cv == c->opt.coarse_visits &&
+        g.sz == c->opt.sweep_zchunk && g.prof == c->prof && g.key == key && g.keyd == keyd) {
+      g.stamp = ++c->clock;
+      *out = &g;
+      return MG_OK;
+    }
+  for (const Prob* p : S.m) {
+    const double* Minv;
+    MG_TRY(coarse_inverse(c, kHelmholtz, p->alpha, &Minv));  // never inside the capture
+  }
+  StepGraph g;
+  g.kind = kHelmholtz;
+  g.ic = ic;
+  g.act = act;
+  g.key = std::move(key);
+  g.keyd = std::move(keyd);
+  return capture_step(c, w, std::move(g), [&] { return enqueue_stack_direct(S, act, ic); }, out);
+}
+
+// Enqueue the stack's next step for the members in act (all of them wait).
+mg_status enqueue_stack_step(Stack& S, unsigned act, int ic) {
+  for (Prob* p : S.m)
+    if ((act >> p->sq) & 1u) {
+      p->ic = ic;
+      // the member's first pass (or its last own work) precedes the step
+      if (!S.started) MG_CUDA(cudaStreamWaitEvent(S.w->s, p->w->ev, 0));
+    }
+  S.started = true;
+  S.g = nullptr;
+  if (S.c->opt.no_graphs) {
+    MG_TRY(enqueue_stack_direct(S, act, ic));
+  } else {
+    const StepGraph* g;
+    MG_TRY(stack_graph(S, act, ic, &g));
+    MG_CUDA(cudaGraphLaunch(g->exec, S.w->s));
+    mg::add_launches(g->launches);
+    S.g = g;
+  }
+  MG_CUDA(cudaEventRecord(S.w->ev, S.w->s));
+  S.running = true;
+  S.stepping = act;
+  S.ic = ic;
+  return MG_OK;
+}
+
 mg_status finish(Prob& p) {
+  // a stack member's last step ran on the stack's stream
+  if (p.stk && p.stk->started) MG_CUDA(cudaStreamWaitEvent(p.w->s, p.stk->w->ev, 0));
   // the iterate back to FP64 (electrode cells keep their values); without a
   // step the caller's guess stays as it was
   if (p.cyc > 0) {
@@ -855,6 +1127,10 @@ mg_status enqueue_first(Prob& p) {
   r0.znorm = true;
   r0.in_scale = p.scale;
   r0.zero_guess = p.zero_guess;
+  if (p.stk) {
+    const long long o = p.sq * p.c->lv[0].ns;
+    for (int col = 0; col < 2; ++col) r0.r_ptr[col] = p.stk->w->lw[0].f32[col] + o;
+  }
   MG_TRY(enqueue_ir(p.c, w, w->s, p.kind, p.alpha, r0, 1));
   MG_CUDA(cudaEventRecord(w->ev, w->s));
   return MG_OK;
@@ -955,6 +1231,26 @@ mg_status solve_mixed(std::vector<Prob>& P) {
     MG_TRY(coarse_inverse(p.c, p.kind, p.alpha, &Minv));
     if (std::find(ctxs.begin(), ctxs.end(), p.c) == ctxs.end()) ctxs.push_back(p.c);
   }
+  // the Helmholtz problems of each context that allows it step as a stack
+  std::vector<Stack> stacks;
+  stacks.reserve(ctxs.size());
+  for (mg_ctx* c : ctxs) {
+    if (!stack_ok(c)) continue;
+    std::vector<Prob*> m;
+    for (Prob& p : P)
+      if (p.c == c && p.kind == kHelmholtz && (int)m.size() < mg::kMaxStack) m.push_back(&p);
+    if (m.size() < 2) continue;
+    stacks.emplace_back();
+    Stack& S = stacks.back();
+    S.c = c;
+    S.m = m;
+    MG_TRY(get_stack(c, (int)m.size(), &S.w));
+    for (size_t q = 0; q < m.size(); ++q) {
+      m[q]->stk = &S;
+      m[q]->sq = (int)q;
+      S.alpha[q] = m[q]->alpha;
+    }
+  }
   for (mg_ctx* c : ctxs) MG_CUDA(cudaEventRecord(c->fork, c->stream));
   for (Prob& p : P) {
     Work* w = p.w;
@@ -987,7 +1283,7 @@ mg_status solve_mixed(std::vector<Prob>& P) {
   while (left) {
     bool progress = false;
     for (Prob& p : P) {
-      if (p.done) continue;
+      if (p.done || p.waiting) continue;  // a waiting member is its stack's
       const cudaError_t q = cudaEventQuery(p.w->ev);
       if (q == cudaErrorNotReady) continue;
       if (q != cudaSuccess) return fail(MG_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(q));
@@ -995,8 +1291,43 @@ mg_status solve_mixed(std::vector<Prob>& P) {
       MG_TRY(advance(p));
       if (p.done) --left;
     }
+    for (Stack& S : stacks) {
+      if (S.running) {
+        const cudaError_t q = cudaEventQuery(S.w->ev);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess)
+          return fail(MG_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(q));
+        progress = true;
+        S.running = false;
+        if (S.g) harvest_graph(S.c, *S.g);
+        for (Prob* p : S.m) {
+          if (!((S.stepping >> p->sq) & 1u)) continue;
+          p->waiting = false;
+          MG_TRY(advance(*p));
+          if (p->done) --left;
+        }
+      }
+      // the next step once every member not yet done waits for it
+      unsigned act = 0;
+      int ic = 0;
+      bool ready = true;
+      for (Prob* p : S.m) {
+        if (p->done) continue;
+        if (!p->waiting) {
+          ready = false;
+          break;
+        }
+        act |= 1u << p->sq;
+        ic = std::max(ic, p->ic);
+      }
+      if (ready && act) {
+        progress = true;
+        MG_TRY(enqueue_stack_step(S, act, ic));
+      }
+    }
     if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
+  for (Stack& S : stacks) MG_CUDA(cudaStreamSynchronize(S.w->s));
   mg_status worst = MG_OK;
   for (Prob& p : P) {
     MG_CUDA(cudaStreamSynchronize(p.w->s));
@@ -1124,6 +1455,8 @@ mg_status solve(std::vector<Prob>& P) {
 void destroy(mg_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (Work* w : c->stacks) c->work.push_back(w);
+  c->stacks.clear();
   for (Work* w : c->work) {
     if (w->s) cudaStreamSynchronize(w->s);
     for (StepGraph& g : w->graphs) {
@@ -1291,6 +1624,8 @@ mg_status normalise_options(const mg_options* in, mg_options* out) {
       in->sweep_zchunk != 16 && in->sweep_zchunk != 32)
     return fail(MG_ERR_INVALID_ARG, "sweep_zchunk must be 0, -1, 8, 16 or 32");
   out->sweep_zchunk = in->sweep_zchunk;
+  if (in->stack != 0 && in->stack != 1) return fail(MG_ERR_INVALID_ARG, "stack must be 0 or 1");
+  out->stack = in->stack;
   return MG_OK;
 }
 

@@ -90,6 +90,24 @@ struct Split32 {
   const float* dg[2];
 };
 
+// A stack of nb > 1 constant-coefficient problems on one grid (the stacked
+// V-cycle of the Helmholtz problems): with it a Split32 level holds the
+// problems one after another along z, b.nz = nb nzp; problem q owns planes
+// [q nzp, (q+1) nzp) of every array, has its own alpha pa[q] and takes part
+// only while bit q of `active` is set.  Its domain faces at z are those of
+// its own planes; nzp is even on every level, so that a cell's colour is the
+// same counted in its problem or in the stack.  (Kept out of Split32: a
+// larger Split32 changed the register allocation, and the speed, of the
+// one-problem kernels.)
+struct Stk32 {
+  int nb;
+  int nzp;
+  float pa[4];
+  unsigned active;
+};
+
+constexpr int kMaxStack = 4;  // problems in one stacked V-cycle
+
 struct Ptr2 {
   const float* p[2];
 };
@@ -215,14 +233,17 @@ bool ir_tma_ready();
 bool ir_timed_out();
 // zchunk: mg_options.sweep_zchunk (0 automatic, -1 register-fed only, or the
 // staged form's z planes per CTA).
+// stk: a stack of problems (op's planes span the stack; null: one problem).
 void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
                          const float* uo, bool zero_other, bool has_mask, int zchunk,
-                         cudaStream_t s);
+                         cudaStream_t s, const Stk32* stk = nullptr);
 // Residual of the red cells only (needs nu1 >= 1: black residuals are 0).
+// stk (nullable): the fine level's stack (its nzp; the coarse level has half)
 void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
-                              MPtr2 fc, MPtr2 uc, cudaStream_t s);
+                              MPtr2 fc, MPtr2 uc, cudaStream_t s, const Stk32* stk = nullptr);
 // Corrects black cells only (needs nu2 >= 1: red cells are overwritten next).
-void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s);
+void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s,
+                       const Stk32* stk = nullptr);
 void launch_resid32s(const Split32& op, float alpha, Ptr2 f, Ptr2 u, MPtr2 r, cudaStream_t s);
 void launch_dense_apply32s(const Split32& op, const double* Minv, Ptr2 r, MPtr2 u,
                            cudaStream_t s);

@@ -38,6 +38,23 @@ __device__ __forceinline__ const float* bsel(const Split32& op, int c) {
 }
 inline const float* bsel_h(const Split32& op, int c) { return c ? op.beta[1] : op.beta[0]; }
 
+// Stacked levels (kernels instantiated with Stk, launched when op.nb > 1):
+// the problem of global plane k, its planes, its alpha, and whether it takes
+// part.  Without Stk the level is one problem and all of it folds away.
+template <bool Stk>
+__device__ __forceinline__ int sprob(const Stk32& st, int k, int nzp) {
+  return Stk ? k / nzp : 0;
+}
+template <bool Stk>
+__device__ __forceinline__ float salpha(const Stk32& st, int q, float alpha) {
+  if (!Stk) return alpha;
+  return q == 0 ? st.pa[0] : q == 1 ? st.pa[1] : q == 2 ? st.pa[2] : st.pa[3];
+}
+template <bool Stk>
+__device__ __forceinline__ bool sactive(const Stk32& st, int q) {
+  return !Stk || ((st.active >> q) & 1u) != 0;
+}
+
 // face weight between a free cell (hb = hc) and an in-box neighbour (hn)
 __device__ __forceinline__ float wface(float hc, float hn) {
   return __fdividef(1.0f, hn < 0.0f ? hc + hc : hc + hn);
@@ -133,6 +150,28 @@ __global__ void __launch_bounds__(kT) k_half_sweep(Split32 op, float alpha, int 
   u[t] = __fdividef(ZeroOther ? f[t] : f[t] + off, diag + alpha);
 }
 
+// The same on a stack of constant-coefficient problems (Stk32): blockIdx.z
+// runs over the stack's planes; the operator row sees the cell's own
+// problem's planes.
+template <bool ZeroOther>
+__global__ void __launch_bounds__(kT) k_half_sweep_stk(Split32 op, Stk32 st, int col,
+                                                       const float* __restrict__ f,
+                                                       float* __restrict__ u,
+                                                       const float* __restrict__ uo) {
+  const int p = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  const int q = k / st.nzp;
+  if (p >= op.W || j >= op.b.ny || !sactive<true>(st, q)) return;
+  const int i = 2 * p + ((j + k + col) & 1);
+  if (i >= op.b.nx) return;
+  const long long t = ((long long)k * op.b.ny + j) * op.W + p;
+  Split32 opl = op;
+  opl.b.nz = st.nzp;
+  float diag, off;
+  row32<false>(opl, col, t, i, j, k - q * st.nzp, uo, diag, off);
+  u[t] = __fdividef(ZeroOther ? f[t] : f[t] + off, diag + salpha<true>(st, q, 0.0f));
+}
+
 __device__ __forceinline__ float4 ld4(const float* p) {
   return *reinterpret_cast<const float4*>(p);
 }
@@ -224,15 +263,20 @@ __device__ __forceinline__ float4 quad_update_tree(const Split32& op, float alph
   return make_float4(out[0], out[1], out[2], out[3]);
 }
 
-template <bool VB, bool ZeroOther, bool HasMask>
-__global__ void __launch_bounds__(kT, 4) k_half_sweep_v4(Split32 op, float alpha, int col,
-                                                         const float* __restrict__ f,
-                                                         float* __restrict__ u,
-                                                         const float* __restrict__ uo) {
+// Body of the vectorised half-sweep; Stk: on a stack of constant-coefficient
+// problems (blockIdx.z runs over the stack's planes).
+template <bool VB, bool ZeroOther, bool HasMask, bool Stk>
+__device__ __forceinline__ void hs4_body(const Split32& op, const Stk32& st, float alpha, int col,
+                                         const float* __restrict__ f, float* __restrict__ u,
+                                         const float* __restrict__ uo) {
   const unsigned FULL = 0xffffffffu;
-  const int W = op.W, ny = op.b.ny, nz = op.b.nz;
+  const int W = op.W, ny = op.b.ny, nz = Stk ? st.nzp : op.b.nz;
   const int lane = threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  const int sq = sprob<Stk>(st, k, nz);
+  if (!sactive<Stk>(st, sq)) return;  // whole CTA
+  const int kz = k - sq * nz;
+  alpha = salpha<Stk>(st, sq, alpha);
   const int p0 = 4 * (blockIdx.x * 32 + lane);
   const bool active = j < ny && p0 < W;
   const int jj = min(j, ny - 1);
@@ -243,7 +287,7 @@ __global__ void __launch_bounds__(kT, 4) k_half_sweep_v4(Split32 op, float alpha
   const float* bt = bsel(op, col ^ 1);
   const float4 half = make_float4(0.5f, 0.5f, 0.5f, 0.5f);
   const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  const bool ym = jj > 0, yp = jj < ny - 1, zm = k > 0, zp = k < nz - 1;
+  const bool ym = jj > 0, yp = jj < ny - 1, zm = kz > 0, zp = kz < nz - 1;
   Quad q;
   q.F = ld4(f + t0);
   q.BO = VB ? ld4(bo + t0) : half;
@@ -274,6 +318,22 @@ __global__ void __launch_bounds__(kT, 4) k_half_sweep_v4(Split32 op, float alpha
   const float4 v = s ? quad_update<VB, ZeroOther, HasMask, 1>(op, alpha, q, pp, ym, yp, zm, zp)
                      : quad_update<VB, ZeroOther, HasMask, 0>(op, alpha, q, pp, ym, yp, zm, zp);
   if (active) *reinterpret_cast<float4*>(u + t0) = v;
+}
+
+template <bool VB, bool ZeroOther, bool HasMask>
+__global__ void __launch_bounds__(kT, 4) k_half_sweep_v4(Split32 op, float alpha, int col,
+                                                         const float* __restrict__ f,
+                                                         float* __restrict__ u,
+                                                         const float* __restrict__ uo) {
+  hs4_body<VB, ZeroOther, HasMask, false>(op, Stk32{}, alpha, col, f, u, uo);
+}
+
+template <bool ZeroOther>
+__global__ void __launch_bounds__(kT, 4) k_half_sweep_v4_stk(Split32 op, Stk32 st, int col,
+                                                             const float* __restrict__ f,
+                                                             float* __restrict__ u,
+                                                             const float* __restrict__ uo) {
+  hs4_body<false, ZeroOther, false, true>(op, st, 0.0f, col, f, u, uo);
 }
 
 // ---- half-sweep with planes staged by the tensor memory accelerator ------
@@ -322,9 +382,9 @@ __device__ __forceinline__ float4 lds4(const float* p) {
   return *reinterpret_cast<const float4*>(p);
 }
 
-template <bool VB, bool HasMask>
+template <bool VB, bool HasMask, bool Stk = false>
 __global__ void __launch_bounds__(kT, VB ? 3 : 4)
-    k_half_sweep_tma(Split32 op, float alpha, int col, int zc, float* __restrict__ u,
+    k_half_sweep_tma(Split32 op, Stk32 st, float alpha, int col, int zc, float* __restrict__ u,
                      const __grid_constant__ SweepMaps maps) {
   using P = TmaPlan<VB>;
   extern __shared__ unsigned char sweep_smem[];
@@ -332,7 +392,14 @@ __global__ void __launch_bounds__(kT, VB ? 3 : 4)
   const int W = op.W, ny = op.b.ny, nz = op.b.nz;
   const int lane = threadIdx.x, warp = threadIdx.y, tid = warp * 32 + lane;
   const int p0 = blockIdx.x * 128, j0 = blockIdx.y * 8;
-  const int ka = blockIdx.z * zc, kb = min(nz, ka + zc);
+  // blockIdx.z: chunk of zc planes of problem sq of a stacked level (the
+  // chunks of one problem never reach into the next)
+  const int nzl = Stk ? st.nzp : nz, cpp = (nzl + zc - 1) / zc;
+  const int sq = Stk ? (int)blockIdx.z / cpp : 0;
+  if (!sactive<Stk>(st, sq)) return;  // whole CTA, before any barrier exists
+  alpha = salpha<Stk>(st, sq, alpha);
+  const int zbase = sq * nzl;
+  const int ka = zbase + ((int)blockIdx.z - sq * cpp) * zc, kb = min(zbase + nzl, ka + zc);
   const uint32_t base = (tma::smem_addr(sweep_smem) + 127u) & ~127u;
   unsigned char* gbase = sweep_smem + (base - tma::smem_addr(sweep_smem));
   const uint32_t oslot0 = base, wslot0 = base + kRingO * P::kO;
@@ -432,7 +499,7 @@ __global__ void __launch_bounds__(kT, VB ? 3 : 4)
       q.ux[5] = unext;
       q.bx[0] = bprev; q.bx[1] = BT.x; q.bx[2] = BT.y; q.bx[3] = BT.z; q.bx[4] = BT.w;
       q.bx[5] = bnext;
-      const bool zm = k > 0, zp = k < nz - 1;
+      const bool zm = k > zbase, zp = k < zbase + nzl - 1;
       const int sx = (j + k + col) & 1;  // warp-uniform
       const float4 v = sx ? quad_update_tree<VB, HasMask, 1>(op, alpha, q, pp, ym, yp, zm, zp)
                           : quad_update_tree<VB, HasMask, 0>(op, alpha, q, pp, ym, yp, zm, zp);
@@ -494,19 +561,23 @@ __device__ __forceinline__ float2 ld2(const float* __restrict__ a, long long t, 
 // Only the red children carry a residual: the pre-smoothing (at least one
 // sweep) ended with a black half-sweep, after which every black cell
 // satisfies its own equation (Gauss-Seidel).
-template <bool VB, bool Vec2>
-__global__ void __launch_bounds__(kT, 3) k_resid_restrict(Split32 op, Split32 cop, float alpha,
-                                                          Ptr2 f, Ptr2 u, MPtr2 fc, MPtr2 uc) {
+template <bool VB, bool Vec2, bool Stk>
+__device__ __forceinline__ void rr_body(const Split32& op, const Split32& cop, const Stk32& st,
+                                        float alpha, Ptr2 f, Ptr2 u, MPtr2 fc, MPtr2 uc) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
   const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
   const int cny = cop.b.ny, cnx = cop.b.nx, cW = cop.W;
-  if (J >= cny) return;  // whole warp
+  // stacked level: problem sq's fine planes are [kb0, kb0 + nz)
+  const int sq = sprob<Stk>(st, K, Stk ? st.nzp / 2 : 1);
+  if (J >= cny || !sactive<Stk>(st, sq)) return;  // whole warp
+  alpha = salpha<Stk>(st, sq, alpha);
   const int Pl = blockIdx.x * 32 + lane;
   const bool live = Pl < cW;
   const int P = live ? Pl : cW - 1;  // idle lanes read a valid pair
   const bool has1 = 2 * P + 1 < cnx;
-  const int nx = op.b.nx, ny = op.b.ny, nz = op.b.nz, W = op.W;
+  const int nx = op.b.nx, ny = op.b.ny, nz = Stk ? st.nzp : op.b.nz, W = op.W;
+  const int kb0 = sq * nz;
   const float half = 0.5f;
   float acc0 = 0.0f, acc1 = 0.0f;  // coarse X = 2P, 2P+1
   {
@@ -523,7 +594,7 @@ __global__ void __launch_bounds__(kT, 3) k_resid_restrict(Split32 op, Split32 co
         const bool inner_j = jj == 1 || jj == 2, inner_k = kk == 1 || kk == 2;
         if (!inner_j && !inner_k) continue;
         const int j = 2 * J - 1 + jj, k = 2 * K - 1 + kk;
-        const bool in = j >= 0 && j < ny && k >= 0 && k < nz;
+        const bool in = j >= 0 && j < ny && k >= kb0 && k < kb0 + nz;
         const long long t = ((long long)k * ny + j) * W + 2 * P;
         UO[jj][kk] = in ? ld2<Vec2>(uo, t, has1) : make_float2(0.0f, 0.0f);
         BO[jj][kk] = (VB && in) ? ld2<Vec2>(bo, t, has1) : make_float2(half, half);
@@ -558,7 +629,7 @@ __global__ void __launch_bounds__(kT, 3) k_resid_restrict(Split32 op, Split32 co
         const float2 yb[2] = {BO[b][c + 1], BO[b + 2][c + 1]};
         const float2 zn[2] = {UO[b + 1][c], UO[b + 1][c + 2]};
         const float2 zb[2] = {BO[b + 1][c], BO[b + 1][c + 2]};
-        const bool ym = j > 0, yp = j < ny - 1, zm = k > 0, zp = k < nz - 1;
+        const bool ym = j > 0, yp = j < ny - 1, zm = k > kb0, zp = k < kb0 + nz - 1;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const int i = 4 * P + 2 * e + s;
@@ -594,6 +665,19 @@ __global__ void __launch_bounds__(kT, 3) k_resid_restrict(Split32 op, Split32 co
   }
 }
 
+template <bool VB, bool Vec2>
+__global__ void __launch_bounds__(kT, 3) k_resid_restrict(Split32 op, Split32 cop, float alpha,
+                                                          Ptr2 f, Ptr2 u, MPtr2 fc, MPtr2 uc) {
+  rr_body<VB, Vec2, false>(op, cop, Stk32{}, alpha, f, u, fc, uc);
+}
+
+template <bool Vec2>
+__global__ void __launch_bounds__(kT, 3) k_resid_restrict_stk(Split32 op, Split32 cop, Stk32 st,
+                                                              Ptr2 f, Ptr2 u, MPtr2 fc,
+                                                              MPtr2 uc) {
+  rr_body<false, Vec2, true>(op, cop, st, 0.0f, f, u, fc, uc);
+}
+
 
 // u_fine += trilinear (27, 9, 3, 1)/64 interpolation of the coarse
 // correction; electrode cells untouched.  The interpolation is separable:
@@ -615,24 +699,29 @@ __global__ void __launch_bounds__(kT, 3) k_resid_restrict(Split32 op, Split32 co
 // starts with a red half-sweep, which overwrites every red cell without
 // reading it.
 // Vec2: the fine packed width is even, so the pair (2P, 2P+1) is one float2.
-template <bool VB, bool Vec2>
-__global__ void __launch_bounds__(kT) k_prolong(Split32 op, Split32 cop, Ptr2 ec, MPtr2 u) {
+template <bool VB, bool Vec2, bool Stk>
+__device__ __forceinline__ void pro_body(const Split32& op, const Split32& cop, const Stk32& st,
+                                         Ptr2 ec, MPtr2 u) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
   const int P = blockIdx.x * 32 + lane;
   const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
-  const int cnx = cop.b.nx, cny = cop.b.ny, cnz = cop.b.nz, cW = cop.W;
-  if (J >= cny) return;  // whole warp
+  const int cnx = cop.b.nx, cny = cop.b.ny, cW = cop.W;
+  // stacked level: problem sq owns coarse planes [kc0, kc1)
+  const int cnz = Stk ? st.nzp / 2 : cop.b.nz;
+  const int sq = sprob<Stk>(st, K, cnz);
+  if (J >= cny || !sactive<Stk>(st, sq)) return;  // whole warp
+  const int kc0 = sq * cnz, kc1 = kc0 + cnz;
   const bool live = P < cW;
   const bool has1 = 2 * P + 1 < cnx;
   // coarse rows J-1, J, J+1 and planes K-1, K, K+1 (reflected at the faces)
   const int Jr[3] = {J > 0 ? J - 1 : J, J, J < cny - 1 ? J + 1 : J};
-  const int Kr[3] = {K > 0 ? K - 1 : K, K, K < cnz - 1 ? K + 1 : K};
+  const int Kr[3] = {K > kc0 ? K - 1 : K, K, K < kc1 - 1 ? K + 1 : K};
   // ghost factors 1 - 2 rho of the coarse level's faces
   const float wJm = 0.25f * (J > 0 ? 1.0f : 1.0f - 2.0f * cop.rho[2]);
   const float wJp = 0.25f * (J < cny - 1 ? 1.0f : 1.0f - 2.0f * cop.rho[3]);
-  const float wKm = 0.25f * (K > 0 ? 1.0f : 1.0f - 2.0f * cop.rho[4]);
-  const float wKp = 0.25f * (K < cnz - 1 ? 1.0f : 1.0f - 2.0f * cop.rho[5]);
+  const float wKm = 0.25f * (K > kc0 ? 1.0f : 1.0f - 2.0f * cop.rho[4]);
+  const float wKp = 0.25f * (K < kc1 - 1 ? 1.0f : 1.0f - 2.0f * cop.rho[5]);
   const float sXm = 1.0f - 2.0f * cop.rho[0], sXp = 1.0f - 2.0f * cop.rho[1];
 
   // z blend of the three rows: Z[c][y] for c = 0 (towards K-1), 1 (K+1);
@@ -748,6 +837,17 @@ __global__ void __launch_bounds__(kT) k_prolong(Split32 op, Split32 cop, Ptr2 ec
     }
 }
 
+template <bool VB, bool Vec2>
+__global__ void __launch_bounds__(kT) k_prolong(Split32 op, Split32 cop, Ptr2 ec, MPtr2 u) {
+  pro_body<VB, Vec2, false>(op, cop, Stk32{}, ec, u);
+}
+
+template <bool Vec2>
+__global__ void __launch_bounds__(kT) k_prolong_stk(Split32 op, Split32 cop, Stk32 st, Ptr2 ec,
+                                                    MPtr2 u) {
+  pro_body<false, Vec2, true>(op, cop, st, ec, u);
+}
+
 // r = f - A u at every cell of the level (electrode and padding cells: 0).
 template <bool VB>
 __global__ void __launch_bounds__(kT) k_resid(Split32 op, float alpha, Ptr2 f, Ptr2 u, MPtr2 r) {
@@ -820,6 +920,9 @@ bool sweep_kernels_ready() {
                                 TmaPlan<true>::smem()) == cudaSuccess &&
            cudaFuncSetAttribute(k_half_sweep_tma<false, false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TmaPlan<false>::smem()) == cudaSuccess &&
+           cudaFuncSetAttribute(k_half_sweep_tma<false, false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 TmaPlan<false>::smem()) == cudaSuccess;
   }();
   return ok;
@@ -831,11 +934,13 @@ namespace {
 // zero, W a multiple of 4 and at least one 128-entry tile, 16-byte aligned
 // arrays, tensor maps encodable); false otherwise (nothing launched).
 bool try_half_sweep_tma(const Split32& op, float alpha, int col, const float* f, float* u,
-                        const float* uo, bool has_mask, int zchunk, cudaStream_t s) {
+                        const float* uo, bool has_mask, int zchunk, cudaStream_t s,
+                        const Stk32* stk) {
   const bool vb = op.beta[0] != nullptr;
   if (zchunk < 0 || op.b.nx % 8 != 0 || op.W < 128) return false;
   const long long tiles = (long long)((op.W + 127) / 128) * ((op.b.ny + 7) / 8);
-  auto ctas = [&](int z) { return tiles * ((op.b.nz + z - 1) / z); };
+  const long long nbz = stk ? stk->nb : 1, nzl = stk ? stk->nzp : op.b.nz;
+  auto ctas = [&](int z) { return tiles * nbz * ((nzl + z - 1) / z); };
   int zc = zchunk;
   if (zc == 0) {
     // about four CTAs per slot of the GPU (152 SMs x 3 CTAs), else two;
@@ -857,9 +962,14 @@ bool try_half_sweep_tma(const Split32& op, float alpha, int col, const float* f,
     maps.bo_own = maps.f;
   }
   if (!sweep_kernels_ready()) return false;
-  dim3 blk(32, 8), g((op.W + 127) / 128, (op.b.ny + 7) / 8, (op.b.nz + zc - 1) / zc);
-  auto go = [&](auto kern, int smem) { kern<<<g, blk, smem, s>>>(op, alpha, col, zc, u, maps); };
-  if (vb) {
+  dim3 blk(32, 8), g((op.W + 127) / 128, (op.b.ny + 7) / 8,
+                    (unsigned)(nbz * ((nzl + zc - 1) / zc)));
+  const Stk32 st = stk ? *stk : Stk32{};
+  auto go = [&](auto kern, int smem) { kern<<<g, blk, smem, s>>>(op, st, alpha, col, zc, u, maps); };
+  if (stk) {
+    if (vb || has_mask) return false;  // stacks are constant-coefficient
+    go(k_half_sweep_tma<false, false, true>, TmaPlan<false>::smem());
+  } else if (vb) {
     if (has_mask) go(k_half_sweep_tma<true, true>, TmaPlan<true>::smem());
     else go(k_half_sweep_tma<true, false>, TmaPlan<true>::smem());
   } else {
@@ -909,13 +1019,27 @@ bool sweep_timed_out() {
 
 void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f, float* u,
                          const float* uo, bool zero_other, bool has_mask, int zchunk,
-                         cudaStream_t s) {
+                         cudaStream_t s, const Stk32* stk) {
   const bool vb = op.beta[0] != nullptr;
-  if (!zero_other && try_half_sweep_tma(op, alpha, col, f, u, uo, has_mask, zchunk, s)) {
+  if (!zero_other && try_half_sweep_tma(op, alpha, col, f, u, uo, has_mask, zchunk, s, stk)) {
     add_launches(1);
     return;
   }
   dim3 blk(32, 8);
+  if (stk) {  // a stack of constant-coefficient problems
+    const Stk32 st = *stk;
+    if (op.b.nx % 8 == 0) {
+      dim3 g((op.W / 4 + 31) / 32, (op.b.ny + 7) / 8, op.b.nz);
+      if (zero_other) k_half_sweep_v4_stk<true><<<g, blk, 0, s>>>(op, st, col, f, u, uo);
+      else k_half_sweep_v4_stk<false><<<g, blk, 0, s>>>(op, st, col, f, u, uo);
+    } else {
+      dim3 g((op.W + 31) / 32, (op.b.ny + 7) / 8, op.b.nz);
+      if (zero_other) k_half_sweep_stk<true><<<g, blk, 0, s>>>(op, st, col, f, u, uo);
+      else k_half_sweep_stk<false><<<g, blk, 0, s>>>(op, st, col, f, u, uo);
+    }
+    add_launches(1);
+    return;
+  }
   if (op.b.nx % 8 == 0) {
     dim3 g((op.W / 4 + 31) / 32, (op.b.ny + 7) / 8, op.b.nz);
 #define HS4(A, B, C) k_half_sweep_v4<A, B, C><<<g, blk, 0, s>>>(op, alpha, col, f, u, uo)
@@ -940,9 +1064,15 @@ void launch_half_sweep32(const Split32& op, float alpha, int col, const float* f
 }
 
 void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
-                              MPtr2 fc, MPtr2 uc, cudaStream_t s) {
+                              MPtr2 fc, MPtr2 uc, cudaStream_t s, const Stk32* stk) {
   dim3 blk(32, 8), g((cop.W + 31) / 32, (cop.b.ny + 7) / 8, cop.b.nz);
   const bool vec2 = op.W % 2 == 0;
+  if (stk) {
+    if (vec2) k_resid_restrict_stk<true><<<g, blk, 0, s>>>(op, cop, *stk, f, u, fc, uc);
+    else k_resid_restrict_stk<false><<<g, blk, 0, s>>>(op, cop, *stk, f, u, fc, uc);
+    add_launches(1);
+    return;
+  }
 #define RR(A, B) k_resid_restrict<A, B><<<g, blk, 0, s>>>(op, cop, alpha, f, u, fc, uc)
   if (op.beta[0]) { if (vec2) RR(true, true); else RR(true, false); }
   else { if (vec2) RR(false, true); else RR(false, false); }
@@ -950,9 +1080,16 @@ void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha
   add_launches(1);
 }
 
-void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s) {
+void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s,
+                       const Stk32* stk) {
   dim3 blk(32, 8), g((cop.W + 31) / 32, (cop.b.ny + 7) / 8, cop.b.nz);
   const bool vec2 = op.W % 2 == 0;
+  if (stk) {
+    if (vec2) k_prolong_stk<true><<<g, blk, 0, s>>>(op, cop, *stk, ec, u);
+    else k_prolong_stk<false><<<g, blk, 0, s>>>(op, cop, *stk, ec, u);
+    add_launches(1);
+    return;
+  }
 #define PRO(A, B) k_prolong<A, B><<<g, blk, 0, s>>>(op, cop, ec, u)
   if (op.beta[0]) { if (vec2) PRO(true, true); else PRO(true, false); }
   else { if (vec2) PRO(false, true); else PRO(false, false); }

@@ -72,7 +72,8 @@ class Options(ctypes.Structure):
                 ("concurrency", ctypes.c_int), ("no_graphs", ctypes.c_int),
                 ("rte_bc", ctypes.c_int), ("ir_zchunk", ctypes.c_int),
                 ("coarse_op", ctypes.c_int), ("fixed_cycles", ctypes.c_int),
-                ("coarse_visits", ctypes.c_int), ("sweep_zchunk", ctypes.c_int)]
+                ("coarse_visits", ctypes.c_int), ("sweep_zchunk", ctypes.c_int),
+                ("stack", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
