@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep --inner-cycles and V(2,2) instead of the autotuned choice")
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ir-zchunk", type=int, default=0,
                     help="refinement-pass tile (z planes per CTA column) when not autotuning; "

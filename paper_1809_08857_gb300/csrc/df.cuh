@@ -128,6 +128,23 @@ struct DfAcc2 {
   __device__ __forceinline__ float2 value() const { return add2(s, e); }
 };
 
+// Running double-float sums s + e of pairs of double-floats: two-sum of the
+// leading parts (exact), the low parts and the two-sum errors summed in FP32
+// into e.  The neighbour sum of a constant-coefficient stencil, formed before
+// its one product by 1/h^2 (8 operations per term against 12 for a product
+// and sum).  s + e need not be renormalised before the product: e stays a few
+// ulp of s.
+struct DfSum2 {
+  float2 s, e;
+  __device__ __forceinline__ void add(const Df2& v) {
+    const float2 t = add2(s, v.hi);
+    const float2 bv = sub2(t, s);
+    const float2 err = add2(sub2(s, sub2(t, bv)), sub2(v.hi, bv));
+    s = t;
+    e = add2(e, add2(err, v.lo));
+  }
+};
+
 // a + b (pair of double-floats plus a pair of FP32), renormalised (df_add
 // lane by lane).
 __device__ __forceinline__ Df2 df_add2(const Df2& a, float2 b) {

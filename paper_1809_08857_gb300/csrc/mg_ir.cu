@@ -653,16 +653,17 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2_tma(IrArgs a,
         acc.add(Df2{make_float2(-dg.hi.x, -dg.hi.y), make_float2(-dg.lo.x, -dg.lo.y)}, uc);
         const float4 s4 = pl[buf][ty - 1][tx], n4 = pl[buf][ty + 1][tx];
         const Df2 w{make_float2(a.ih2d.x, a.ih2d.x), make_float2(a.ih2d.y, a.ih2d.y)};
-        const Df2 wl{make_float2(xmA ? a.ih2d.x : 0.0f, a.ih2d.x),
-                     make_float2(xmA ? a.ih2d.y : 0.0f, a.ih2d.y)};
-        const Df2 wr{make_float2(a.ih2d.x, xpB ? a.ih2d.x : 0.0f),
-                     make_float2(a.ih2d.y, xpB ? a.ih2d.y : 0.0f)};
-        acc.add(wl, L);
-        acc.add(wr, R);
-        if (ym) acc.add(w, Df2{make_float2(s4.x, s4.z), make_float2(s4.y, s4.w)});
-        if (yp) acc.add(w, Df2{make_float2(n4.x, n4.z), make_float2(n4.y, n4.w)});
-        if (zm) acc.add(w, um);
-        if (zp) acc.add(w, up);
+        // the six neighbours summed first (none across A's -x or B's +x
+        // domain face), then one product by 1/h^2
+        DfSum2 nb{make_float2(xmA ? L.hi.x : 0.0f, L.hi.y),
+                  make_float2(xmA ? L.lo.x : 0.0f, L.lo.y)};
+        nb.add(Df2{make_float2(R.hi.x, xpB ? R.hi.y : 0.0f),
+                   make_float2(R.lo.x, xpB ? R.lo.y : 0.0f)});
+        if (ym) nb.add(Df2{make_float2(s4.x, s4.z), make_float2(s4.y, s4.w)});
+        if (yp) nb.add(Df2{make_float2(n4.x, n4.z), make_float2(n4.y, n4.w)});
+        if (zm) nb.add(um);
+        if (zp) nb.add(up);
+        acc.add(w, Df2{nb.s, nb.e});
         const float2 r = acc.value();
         if (a.r[0]) {
           const long long t = (long long)k * szW + eoff;
