@@ -431,17 +431,15 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2(IrArgs a) {
       acc.add(Df2{make_float2(-dg.hi.x, -dg.hi.y), make_float2(-dg.lo.x, -dg.lo.y)}, uc);
       const float4 s4 = pl[buf][ty - 1][tx], n4 = pl[buf][ty + 1][tx];
       const Df2 w{make_float2(a.ih2d.x, a.ih2d.x), make_float2(a.ih2d.y, a.ih2d.y)};
-      // no neighbour across A's -x or B's +x domain face: weight 0
-      const Df2 wl{make_float2(xmA ? a.ih2d.x : 0.0f, a.ih2d.x),
-                   make_float2(xmA ? a.ih2d.y : 0.0f, a.ih2d.y)};
-      const Df2 wr{make_float2(a.ih2d.x, xpB ? a.ih2d.x : 0.0f),
-                   make_float2(a.ih2d.y, xpB ? a.ih2d.y : 0.0f)};
-      acc.add(wl, L);
-      acc.add(wr, R);
-      if (ym) acc.add(w, pair4(s4));
-      if (yp) acc.add(w, pair4(n4));
-      if (zm) acc.add(w, um);
-      if (zp) acc.add(w, up);
+      // the six neighbours summed first (none across A's -x or B's +x domain
+      // face), then one product by 1/h^2
+      DfSum2 nb{make_float2(xmA ? L.hi.x : 0.0f, L.hi.y), make_float2(xmA ? L.lo.x : 0.0f, L.lo.y)};
+      nb.add(Df2{make_float2(R.hi.x, xpB ? R.hi.y : 0.0f), make_float2(R.lo.x, xpB ? R.lo.y : 0.0f)});
+      if (ym) nb.add(pair4(s4));
+      if (yp) nb.add(pair4(n4));
+      if (zm) nb.add(um);
+      if (zp) nb.add(up);
+      acc.add(w, Df2{nb.s, nb.e});
       float2 r = acc.value();
       if (mA) r.x = 0.0f;
       if (mB) r.y = 0.0f;

@@ -671,6 +671,194 @@ __global__ void __launch_bounds__(kT, 3) k_resid_restrict(Split32 op, Split32 co
   rr_body<VB, Vec2, false>(op, cop, Stk32{}, alpha, f, u, fc, uc);
 }
 
+// ---- variable-coefficient restriction with its planes staged by tensor copies
+//
+// rr_body's residual and restriction (variable coefficient, packed width a
+// multiple of 4) for a CTA of 32 coarse pairs x 8 coarse rows that marches
+// through kRrZ coarse planes.  The other (black) colour's u and hb arrive
+// plane by plane over the CTA's fine window (box 72 x 18: packed 2 P0 - 4 ..
+// 2 P0 + 67, a 16-byte start, fine rows 2 J0 - 1 .. 2 J0 + 16) into a ring of
+// six slots: a coarse plane K reads fine planes 2K - 1 .. 2K + 2, and the next
+// two are in flight.  The own (red) colour's f, u and hb of fine planes 2K and
+// 2K + 1 (box 64 x 16) come through a ring of four.  The register-fed kernel
+// loads its 36 float2 of a coarse plane into registers (80 registers with
+// spills at three CTAs per SM); here they come from shared memory.  Fine
+// planes outside the level are not copied (plain arrive: their slots hold
+// stale data, which only faces that the boundary tests exclude would read).
+// Waits are bounded as in the staged half-sweep (g_sweep_timeout).
+constexpr int kRrZ = 16;               // coarse planes per CTA
+constexpr int kRrB = 6, kRrW = 4;      // ring slots: black fine planes, own fine planes
+constexpr int kRrBX = 72, kRrBY = 18;  // black box
+constexpr int kRrBArr = 5248;          // one black array box (72 x 18 x 4 = 5184 bytes), to 128
+constexpr int kRrWArr = 4096;          // one own array box (64 x 16 x 4)
+constexpr int kRrBSlot = 2 * kRrBArr, kRrWSlot = 3 * kRrWArr;
+constexpr int kRrSmem = 128 + kRrB * kRrBSlot + kRrW * kRrWSlot + 8 * (kRrB + kRrW);
+
+struct RrMaps {
+  CUtensorMap ub, hb, f, u, ho;  // black u, black hb; own f, own u, own hb
+};
+
+__device__ __forceinline__ float2 lds2(const float* p) {
+  return *reinterpret_cast<const float2*>(p);
+}
+
+__global__ void __launch_bounds__(kT, 2)
+    k_resid_restrict_tma(Split32 op, Split32 cop, float alpha, MPtr2 fc, MPtr2 uc,
+                         const __grid_constant__ RrMaps maps) {
+  extern __shared__ unsigned char rr_smem[];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x, warp = threadIdx.y, tid = warp * 32 + lane;
+  const int cny = cop.b.ny, cnx = cop.b.nx, cW = cop.W, cnz = cop.b.nz;
+  const int nx = op.b.nx, ny = op.b.ny, nz = op.b.nz;
+  const int P0 = blockIdx.x * 32, J0 = blockIdx.y * 8;
+  const int Ka = blockIdx.z * kRrZ, Kb = min(cnz, Ka + kRrZ);
+  const int nk = Kb - Ka, nq = 2 * nk + 2, nw = 2 * nk;
+  const uint32_t base = (tma::smem_addr(rr_smem) + 127u) & ~127u;
+  unsigned char* gbase = rr_smem + (base - tma::smem_addr(rr_smem));
+  const uint32_t wbase = base + kRrB * kRrBSlot;
+  const uint32_t bar0 = wbase + kRrW * kRrWSlot;
+  auto bbar = [&](int q) { return bar0 + 8u * (uint32_t)(q % kRrB); };
+  auto wbar = [&](int w) { return bar0 + 8u * (uint32_t)(kRrB + w % kRrW); };
+  auto bpar = [&](int q) { return (uint32_t)((q / kRrB) & 1); };
+  auto wpar = [&](int w) { return (uint32_t)((w / kRrW) & 1); };
+  // black sequence q is fine plane 2 Ka - 1 + q; own sequence w is 2 Ka + w
+  auto issue_b = [&](int q) {
+    const int z = 2 * Ka - 1 + q;
+    const uint32_t b = bbar(q);
+    if (z < 0 || z >= nz) {
+      tma::bar_arrive(b);
+      return;
+    }
+    tma::bar_arrive_tx(b, (uint32_t)(2 * kRrBX * kRrBY * 4));
+    const uint32_t d = base + (uint32_t)((q % kRrB) * kRrBSlot);
+    tma::load3(d, &maps.ub, b, 2 * P0 - 4, 2 * J0 - 1, z);
+    tma::load3(d + kRrBArr, &maps.hb, b, 2 * P0 - 4, 2 * J0 - 1, z);
+  };
+  auto issue_w = [&](int w) {
+    const int z = 2 * Ka + w;
+    const uint32_t b = wbar(w);
+    tma::bar_arrive_tx(b, (uint32_t)(3 * 64 * 16 * 4));
+    const uint32_t d = wbase + (uint32_t)((w % kRrW) * kRrWSlot);
+    tma::load3(d, &maps.f, b, 2 * P0, 2 * J0, z);
+    tma::load3(d + kRrWArr, &maps.u, b, 2 * P0, 2 * J0, z);
+    tma::load3(d + 2 * kRrWArr, &maps.ho, b, 2 * P0, 2 * J0, z);
+  };
+  auto bslot = [&](int q, int a) {
+    return reinterpret_cast<const float*>(gbase + (q % kRrB) * kRrBSlot + a * kRrBArr);
+  };
+  auto wslot = [&](int w, int a) {
+    return reinterpret_cast<const float*>(gbase + kRrB * kRrBSlot + (w % kRrW) * kRrWSlot +
+                                          a * kRrWArr);
+  };
+  int issued_b = min(kRrB, nq), issued_w = min(kRrW, nw);
+  if (tid == 0) {
+    for (int i = 0; i < kRrB + kRrW; ++i) tma::bar_init(bar0 + 8u * i);
+    tma::bar_init_fence();
+    for (int q = 0; q < issued_b; ++q) issue_b(q);
+    for (int w = 0; w < issued_w; ++w) issue_w(w);
+  }
+  __syncthreads();
+  const int J = J0 + warp, Pl = P0 + lane;
+  const bool live = Pl < cW && J < cny;
+  const int P = Pl;  // lanes past the level read zero-filled columns and store nothing
+  const bool has1 = 2 * P + 1 < cnx;
+  bool ok = true;
+  for (int i = 0; i < nk; ++i) {
+    const int K = Ka + i;
+    if (tid == 0 && i >= 1) {
+      for (int q = 2 * i + 4; q < 2 * i + 6 && q < nq; ++q) issue_b(issued_b++);
+      for (int w = 2 * i + 2; w < 2 * i + 4 && w < nw; ++w) issue_w(issued_w++);
+    }
+    // black fine planes 2K - 1 .. 2K + 2 are sequences 2i .. 2i + 3; own 2i, 2i + 1
+    for (int q = (i == 0 ? 0 : 2 * i + 2); q < 2 * i + 4; ++q)
+      ok = tma::bar_wait(bbar(q), bpar(q)) && ok;
+    ok = tma::bar_wait(wbar(2 * i), wpar(2 * i)) && ok;
+    ok = tma::bar_wait(wbar(2 * i + 1), wpar(2 * i + 1)) && ok;
+    if (ok) {
+      float acc0 = 0.0f, acc1 = 0.0f;  // coarse X = 2P, 2P+1
+      const int col2 = 2 * lane + 4;   // packed 2P in the black box
+      float2 UO[4][4], BO[4][4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const bool inner_j = jj == 1 || jj == 2, inner_k = kk == 1 || kk == 2;
+          if (!inner_j && !inner_k) continue;
+          const int row = 2 * warp + jj;
+          UO[jj][kk] = lds2(bslot(2 * i + kk, 0) + row * kRrBX + col2);
+          BO[jj][kk] = lds2(bslot(2 * i + kk, 1) + row * kRrBX + col2);
+        }
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int j = 2 * J + b, k = 2 * K + c;
+          const int s = (b + c) & 1;  // own (red) cells at i = 4P+s, 4P+2+s
+          const int orow = (2 * warp + b) * 64 + 2 * lane;
+          const float2 F = lds2(wslot(2 * i + c, 0) + orow);
+          const float2 U = lds2(wslot(2 * i + c, 1) + orow);
+          const float2 HC = lds2(wslot(2 * i + c, 2) + orow);
+          const float2 ur = UO[b + 1][c + 1], br = BO[b + 1][c + 1];
+          // other colour at packed 2P-1 (s = 0) or 2P+2 (s = 1), from the box
+          const float* crow_u = bslot(2 * i + c + 1, 0) + (2 * warp + b + 1) * kRrBX;
+          const float* crow_b = bslot(2 * i + c + 1, 1) + (2 * warp + b + 1) * kRrBX;
+          const float uh = s ? crow_u[col2 + 2] : crow_u[col2 - 1];
+          const float bh = s ? crow_b[col2 + 2] : crow_b[col2 - 1];
+          const float ux[3] = {s ? ur.x : uh, s ? ur.y : ur.x, s ? uh : ur.y};
+          const float bx[3] = {s ? br.x : bh, s ? br.y : br.x, s ? bh : br.y};
+          const float2 yn[2] = {UO[b][c + 1], UO[b + 2][c + 1]};
+          const float2 yb[2] = {BO[b][c + 1], BO[b + 2][c + 1]};
+          const float2 zn[2] = {UO[b + 1][c], UO[b + 1][c + 2]};
+          const float2 zb[2] = {BO[b + 1][c], BO[b + 1][c + 2]};
+          const bool ym = j > 0, yp = j < ny - 1, zm = k > 0, zp = k < nz - 1;
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int ic = 4 * P + 2 * e + s;
+            const float hc = e ? HC.y : HC.x;
+            float d = 0.0f, o = 0.0f;
+            auto face = [&](float hn, float un) {
+              const float w = wface(hc, hn);
+              d += w;
+              o = fmaf(w, un, o);
+            };
+            auto dface = [&](float r) { d = fmaf(wdir(hc), r, d); };
+            if (ic > 0) face(bx[e], ux[e]); else dface(op.rho[0]);
+            if (ic < nx - 1) face(bx[e + 1], ux[e + 1]); else dface(op.rho[1]);
+            if (ym) face(e ? yb[0].y : yb[0].x, e ? yn[0].y : yn[0].x); else dface(op.rho[2]);
+            if (yp) face(e ? yb[1].y : yb[1].x, e ? yn[1].y : yn[1].x); else dface(op.rho[3]);
+            if (zm) face(e ? zb[0].y : zb[0].x, e ? zn[0].y : zn[0].x); else dface(op.rho[4]);
+            if (zp) face(e ? zb[1].y : zb[1].x, e ? zn[1].y : zn[1].x); else dface(op.rho[5]);
+            const float uc0 = e ? U.y : U.x, fc0 = e ? F.y : F.x;
+            float r = fc0 - fmaf(fmaf(d, op.ih2, alpha), uc0, -o * op.ih2);
+            if (hc < 0.0f || (e == 1 && !has1)) r = 0.0f;
+            if (e == 0) acc0 += r; else acc1 += r;
+          }
+        }
+      if (live) {
+        const int cpar = (J + K) & 1;  // colour of coarse X = 2P
+        const long long ct = ((long long)K * cny + J) * cW + P;
+        sel(fc, cpar)[ct] = 0.125f * acc0;
+        sel(uc, cpar)[ct] = 0.0f;
+        if (has1) {
+          sel(fc, cpar ^ 1)[ct] = 0.125f * acc1;
+          sel(uc, cpar ^ 1)[ct] = 0.0f;
+        }
+      }
+    }
+    // the slots of black planes 2K - 1, 2K and own planes 2K, 2K + 1 are free
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+  }
+  (void)FULL;
+  if (!ok && tid == 0) {
+    atomicExch(&g_sweep_timeout, 1u);
+    for (int q = max(0, issued_b - kRrB); q < issued_b; ++q) tma::bar_wait(bbar(q), bpar(q));
+    for (int w = max(0, issued_w - kRrW); w < issued_w; ++w) tma::bar_wait(wbar(w), wpar(w));
+  }
+}
+
 template <bool Vec2>
 __global__ void __launch_bounds__(kT, 3) k_resid_restrict_stk(Split32 op, Split32 cop, Stk32 st,
                                                               Ptr2 f, Ptr2 u, MPtr2 fc,
@@ -923,7 +1111,9 @@ bool sweep_kernels_ready() {
                                 TmaPlan<false>::smem()) == cudaSuccess &&
            cudaFuncSetAttribute(k_half_sweep_tma<false, false, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TmaPlan<false>::smem()) == cudaSuccess;
+                                TmaPlan<false>::smem()) == cudaSuccess &&
+           cudaFuncSetAttribute(k_resid_restrict_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kRrSmem) == cudaSuccess;
   }();
   return ok;
 }
@@ -975,6 +1165,23 @@ bool try_half_sweep_tma(const Split32& op, float alpha, int col, const float* f,
   } else {
     go(k_half_sweep_tma<false, false>, TmaPlan<false>::smem());
   }
+  return true;
+}
+
+// The staged restriction where it applies (variable coefficient, packed width
+// a multiple of 4 and at least 128, 16-byte aligned arrays, encodable maps);
+// false otherwise (nothing launched).
+bool try_resid_restrict_tma(const Split32& op, const Split32& cop, float alpha, Ptr2 f, Ptr2 u,
+                            MPtr2 fc, MPtr2 uc, cudaStream_t s) {
+  if (!op.beta[0] || op.W % 4 != 0 || op.W < 128 || op.b.nx % 8 != 0 || !sweep_kernels_ready())
+    return false;
+  RrMaps m;
+  if (!colour_map(&m.ub, u.p[1], op, kRrBX, kRrBY) ||
+      !colour_map(&m.hb, op.beta[1], op, kRrBX, kRrBY) || !colour_map(&m.f, f.p[0], op, 64, 16) ||
+      !colour_map(&m.u, u.p[0], op, 64, 16) || !colour_map(&m.ho, op.beta[0], op, 64, 16))
+    return false;
+  dim3 blk(32, 8), g((cop.W + 31) / 32, (cop.b.ny + 7) / 8, (cop.b.nz + kRrZ - 1) / kRrZ);
+  k_resid_restrict_tma<<<g, blk, kRrSmem, s>>>(op, cop, alpha, fc, uc, m);
   return true;
 }
 
@@ -1067,6 +1274,10 @@ void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha
                               MPtr2 fc, MPtr2 uc, cudaStream_t s, const Stk32* stk) {
   dim3 blk(32, 8), g((cop.W + 31) / 32, (cop.b.ny + 7) / 8, cop.b.nz);
   const bool vec2 = op.W % 2 == 0;
+  if (!stk && try_resid_restrict_tma(op, cop, alpha, f, u, fc, uc, s)) {
+    add_launches(1);
+    return;
+  }
   if (stk) {
     if (vec2) k_resid_restrict_stk<true><<<g, blk, 0, s>>>(op, cop, *stk, f, u, fc, uc);
     else k_resid_restrict_stk<false><<<g, blk, 0, s>>>(op, cop, *stk, f, u, fc, uc);
