@@ -887,14 +887,40 @@ __global__ void __launch_bounds__(kT, 3) k_resid_restrict_stk(Split32 op, Split3
 // starts with a red half-sweep, which overwrites every red cell without
 // reading it.
 // Vec2: the fine packed width is even, so the pair (2P, 2P+1) is one float2.
-template <bool VB, bool Vec2, bool Stk>
+// Tensor maps of the prefetching prolongation: the fine level's black u and
+// hb as (W, ny, nz), copied in boxes of 64 packed x 16 rows x 2 planes (the
+// fine black cells of one CTA of coarse pairs).
+struct ProMaps {
+  CUtensorMap ub, hb;
+};
+
+// Pre: the fine black rows (and hb) of the CTA are fetched by one tensor copy
+// issued before the coarse loads, so their latency overlaps the coarse blend;
+// the read-modify-write then reads them from shared memory (pm: the maps).
+template <bool VB, bool Vec2, bool Stk, bool Pre = false>
 __device__ __forceinline__ void pro_body(const Split32& op, const Split32& cop, const Stk32& st,
-                                         Ptr2 ec, MPtr2 u) {
+                                         Ptr2 ec, MPtr2 u, const ProMaps* pm = nullptr) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
   const int P = blockIdx.x * 32 + lane;
   const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
   const int cnx = cop.b.nx, cny = cop.b.ny, cW = cop.W;
+  __shared__ __align__(128) float sfine[Pre ? (VB ? 2 : 1) : 1][Pre ? 2 : 1][Pre ? 16 : 1]
+                                       [Pre ? 64 : 1];
+  __shared__ __align__(8) unsigned long long pbar;
+  if (Pre) {
+    // thread 0 starts the copy of this CTA's fine black tile before anything else
+    const uint32_t bar = tma::smem_addr(&pbar);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      tma::bar_init(bar);
+      tma::bar_init_fence();
+      tma::bar_arrive_tx(bar, (uint32_t)((VB ? 2 : 1) * 64 * 16 * 2 * 4));
+      const int x0 = 2 * (int)blockIdx.x * 32, y0 = 2 * (int)blockIdx.y * 8, z0 = 2 * K;
+      tma::load3(tma::smem_addr(&sfine[0][0][0][0]), &pm->ub, bar, x0, y0, z0);
+      if (VB) tma::load3(tma::smem_addr(&sfine[VB ? 1 : 0][0][0][0]), &pm->hb, bar, x0, y0, z0);
+    }
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+  }
   // stacked level: problem sq owns coarse planes [kc0, kc1)
   const int cnz = Stk ? st.nzp / 2 : cop.b.nz;
   const int sq = sprob<Stk>(st, K, cnz);
@@ -987,12 +1013,20 @@ __device__ __forceinline__ void pro_body(const Split32& op, const Split32& cop, 
   // is written, so the four read-modify-writes overlap
   long long t[2][2];
   float2 w[2][2], g[2][2];
+  if (Pre && !tma::bar_wait(tma::smem_addr(&pbar), 0u)) {
+    atomicExch(&g_sweep_timeout, 1u);  // the copy never arrived: leave the cells
+    return;
+  }
 #pragma unroll
   for (int b = 0; b < 2; ++b)
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       t[b][c] = ((long long)(2 * K + c) * ny + (2 * J + b)) * W + 2 * P;
-      if (Vec2) {
+      if (Pre) {
+        const int row = 2 * (int)threadIdx.y + b;
+        w[b][c] = *reinterpret_cast<const float2*>(&sfine[0][c][row][2 * lane]);
+        if (VB) g[b][c] = *reinterpret_cast<const float2*>(&sfine[VB ? 1 : 0][c][row][2 * lane]);
+      } else if (Vec2) {
         w[b][c] = *reinterpret_cast<const float2*>(ub + t[b][c]);
         if (VB) g[b][c] = *reinterpret_cast<const float2*>(hb + t[b][c]);
       } else {
@@ -1034,6 +1068,12 @@ template <bool Vec2>
 __global__ void __launch_bounds__(kT) k_prolong_stk(Split32 op, Split32 cop, Stk32 st, Ptr2 ec,
                                                     MPtr2 u) {
   pro_body<false, Vec2, true>(op, cop, st, ec, u);
+}
+
+template <bool VB>
+__global__ void __launch_bounds__(kT) k_prolong_tma(Split32 op, Split32 cop, Ptr2 ec, MPtr2 u,
+                                                    const __grid_constant__ ProMaps maps) {
+  pro_body<VB, true, false, true>(op, cop, Stk32{}, ec, u, &maps);
 }
 
 // r = f - A u at every cell of the level (electrode and padding cells: 0).
@@ -1202,11 +1242,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
 }
 
 bool tma_map_f32(CUtensorMap* m, const void* p, long long nx, long long ny, long long nz, int bx,
-                 int by) {
+                 int by, int bz) {
   if (!tma_encoder() || ((uintptr_t)p & 15u) || (nx * 4) % 16) return false;
   const cuuint64_t dim[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
   const cuuint64_t stride[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny * 4)};
-  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
   const cuuint32_t es[3] = {1, 1, 1};
   return tma_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(p), dim, stride,
                        box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1293,6 +1333,20 @@ void launch_resid_restrict32s(const Split32& op, const Split32& cop, float alpha
 
 void launch_prolong32s(const Split32& op, const Split32& cop, Ptr2 ec, MPtr2 u, cudaStream_t s,
                        const Stk32* stk) {
+  // the fine black tile of a CTA by one tensor copy ahead of the coarse blend
+  if (!stk && op.W % 4 == 0 && op.W >= 128 && op.b.nx % 8 == 0) {
+    ProMaps m;
+    const bool vbp = op.beta[0] != nullptr;
+    if (tma_map_f32(&m.ub, u.p[1], op.W, op.b.ny, op.b.nz, 64, 16, 2) &&
+        (!vbp || tma_map_f32(&m.hb, op.beta[1], op.W, op.b.ny, op.b.nz, 64, 16, 2))) {
+      if (!vbp) m.hb = m.ub;
+      dim3 blk(32, 8), g((cop.W + 31) / 32, (cop.b.ny + 7) / 8, cop.b.nz);
+      if (vbp) k_prolong_tma<true><<<g, blk, 0, s>>>(op, cop, ec, u, m);
+      else k_prolong_tma<false><<<g, blk, 0, s>>>(op, cop, ec, u, m);
+      add_launches(1);
+      return;
+    }
+  }
   dim3 blk(32, 8), g((cop.W + 31) / 32, (cop.b.ny + 7) / 8, cop.b.nz);
   const bool vec2 = op.W % 2 == 0;
   if (stk) {

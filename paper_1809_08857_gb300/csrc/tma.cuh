@@ -87,11 +87,11 @@ __device__ __forceinline__ void load3(uint32_t dst, const CUtensorMap* map, uint
 }  // namespace tma
 
 // Host side (defined in mg_split32.cu).  An FP32 array of nx x ny x nz
-// (x fastest, rows of nx floats) as a 3D tensor copied in boxes of bx x by x 1
+// (x fastest, rows of nx floats) as a 3D tensor copied in boxes of bx x by x bz
 // with zero fill; false if the driver entry point is missing or the encoding
 // is refused (the caller then runs its register-fed kernel).
 bool tma_map_f32(CUtensorMap* m, const void* p, long long nx, long long ny, long long nz, int bx,
-                 int by);
+                 int by, int bz = 1);
 
 }  // namespace mg
 
