@@ -231,7 +231,9 @@ __device__ __forceinline__ float4 quad_update(const Split32& op, float alpha, co
 // memory, is bound by the latency of these dependent chains rather than by
 // HBM.  Same weights and faces as quad_update; only the order of the FP32
 // additions differs.
-template <bool VB, bool HasMask, int S>
+// YZin: the row and plane have in-box neighbours in y and z (known for the
+// whole warp), so only the x faces need the domain-face test.
+template <bool VB, bool HasMask, int S, bool YZin = false>
 __device__ __forceinline__ float4 quad_update_tree(const Split32& op, float alpha, const Quad& q,
                                                    int pp, bool ym, bool yp, bool zm, bool zp) {
   float out[4];
@@ -241,7 +243,8 @@ __device__ __forceinline__ float4 quad_update_tree(const Split32& op, float alph
     const float hc = VB ? el(q.BO, e) : 0.5f;
     const float wd = VB ? wdir(hc) : 2.0f;
     // faces -x, +x, -y, +y, -z, +z: in-box neighbour or domain face
-    const bool inb[6] = {!(S == 0 && p == 0), !(S == 1 && p == op.W - 1), ym, yp, zm, zp};
+    const bool inb[6] = {!(S == 0 && p == 0), !(S == 1 && p == op.W - 1), YZin || ym,
+                         YZin || yp,          YZin || zm,                   YZin || zp};
     const float hn[6] = {q.bx[e + S], q.bx[e + S + 1], el(q.BYm, e),
                          el(q.BYp, e), el(q.BZm, e),   el(q.BZp, e)};
     const float un[6] = {q.ux[e + S], q.ux[e + S + 1], el(q.UYm, e),
@@ -501,8 +504,14 @@ __global__ void __launch_bounds__(kT, VB ? 3 : 4)
       q.bx[5] = bnext;
       const bool zm = k > zbase, zp = k < zbase + nzl - 1;
       const int sx = (j + k + col) & 1;  // warp-uniform
-      const float4 v = sx ? quad_update_tree<VB, HasMask, 1>(op, alpha, q, pp, ym, yp, zm, zp)
-                          : quad_update_tree<VB, HasMask, 0>(op, alpha, q, pp, ym, yp, zm, zp);
+      // all but the boundary rows and planes: y and z faces without domain tests
+      float4 v;
+      if (ym && yp && zm && zp)
+        v = sx ? quad_update_tree<VB, HasMask, 1, true>(op, alpha, q, pp, ym, yp, zm, zp)
+               : quad_update_tree<VB, HasMask, 0, true>(op, alpha, q, pp, ym, yp, zm, zp);
+      else
+        v = sx ? quad_update_tree<VB, HasMask, 1>(op, alpha, q, pp, ym, yp, zm, zp)
+               : quad_update_tree<VB, HasMask, 0>(op, alpha, q, pp, ym, yp, zm, zp);
       if (active) {
         float* dst = u + ((long long)k * ny + j) * W + pp;
         if (!HasMask || (q.BO.x >= 0.0f && q.BO.y >= 0.0f && q.BO.z >= 0.0f && q.BO.w >= 0.0f)) {
