@@ -702,6 +702,221 @@ __global__ void __launch_bounds__(NT, 2) k_ir_df2_tma(IrArgs a,
   }
 }
 
+// ---- the face-array refinement step with its planes staged by tensor copies --
+//
+// k_ir_df<Faces=1, HasE=1, U64=0, BIn=0> (the variable-coefficient refinement
+// step after the first pass) with its inputs brought to shared memory by
+// tiled tensor copies: per plane the CTA's 32 x 16 patch of the double-float
+// iterate (box 68 x 16 floats from 2 i0 - 2, a 16-byte boundary; a thread
+// indexes from the remainder) and of both colours' packed corrections (box
+// 24 x 16 from the packed start rounded down to 4 entries) into a ring of
+// three slots; b, the diagonal, the -x faces (one column more, for the +x
+// face) and the -y faces (one row more) of the 30 x 14 own cells into a ring
+// of three; the -z faces into a ring of four (plane k + 1 gives the +z face
+// of plane k).  The march, the shared plane for the y-neighbours, the
+// shuffles for the x-neighbours and the double-float arithmetic are k_ir_df's.
+constexpr int kFsU = 3, kFsO = 3, kFsZ = 4;         // ring slots
+constexpr int kFsUBytes = 16 * 68 * 4;              // 4352
+constexpr int kFsEBytes = 16 * 24 * 4;              // 1536 per colour
+constexpr int kFsUSlot = kFsUBytes + 2 * kFsEBytes;  // 7424 = 58 x 128
+constexpr int kFsB = 14 * 60 * 4;                   // 3360: b, D, cz (60 floats x 14 rows)
+constexpr int kFsBPad = 3456;                       // to 128
+constexpr int kFsX = 14 * 64 * 4;                   // 3584: -x faces, 31 cells
+constexpr int kFsY = 15 * 60 * 4;                   // 3600: -y faces, 15 rows
+constexpr int kFsYPad = 3712;
+constexpr int kFsOSlot = 2 * kFsBPad + kFsX + kFsYPad;  // b, D, cx, cy: 14208 = 111 x 128
+constexpr int kFsSmem = 128 + kFsU * kFsUSlot + kFsO * kFsOSlot + kFsZ * kFsBPad +
+                        8 * (kFsU + kFsO + kFsZ);
+
+struct FsMaps {
+  CUtensorMap u, e0, e1, b, d, cx, cy, cz;
+};
+
+__global__ void __launch_bounds__(NT, 2) k_ir_dff_tma(IrArgs a,
+                                                      const __grid_constant__ FsMaps maps) {
+  extern __shared__ unsigned char fs_smem[];
+  __shared__ float2 pl[2][TY][TX];
+  __shared__ float red[NT / 32];
+  const unsigned FULL = 0xffffffffu;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int nx = a.op.b.nx, ny = a.op.b.ny, nz = a.op.b.nz;
+  const int bx = blockIdx.x, by = blockIdx.y;
+  const int i = bx * (TX - 2) - 1 + tx, j = by * (TY - 2) - 1 + ty;
+  const int z0 = blockIdx.z * a.zchunk, z1 = min(nz, z0 + a.zchunk);
+  const int n = z1 - z0, nq = n + 2, nv = min(z1 + 1, nz) - z0;
+  const int W = a.W;
+  const long long sz = (long long)nx * ny, szW = (long long)W * ny;
+  const bool in = i >= 0 && i < nx && j >= 0 && j < ny;
+  const bool own = in && tx >= 1 && tx <= TX - 2 && ty >= 1 && ty <= TY - 2;
+  const int off = in ? j * nx + i : 0;
+  const int eoff = in ? j * W + (i >> 1) : 0;
+  const int par0 = (i + j) & 1;
+  const bool xm = i > 0, xp = i < nx - 1, ym = j > 0, yp = j < ny - 1;
+  // box origins: the iterate from 2 i0 - 2 floats rounded down to a multiple
+  // of 4 (2 i0 = 60 bx - 2, so 60 bx - 4; a thread's pair sits at 2 tx + 2),
+  // the corrections from the packed start rounded down to 4, the own cells'
+  // arrays from cell 30 bx (60 bx floats) and row 14 by
+  const int ux = 2 * bx * (TX - 2) - 4, uy = by * (TY - 2) - 1;
+  const int ex = ((bx * (TX - 2) - 1) >> 1) & ~3;
+  const int ecol = in ? (i >> 1) - ex : 0;
+  const int ox = 2 * bx * (TX - 2), oy = by * (TY - 2);
+  const float2 zero2 = make_float2(0.0f, 0.0f);
+
+  const uint32_t base = (tma::smem_addr(fs_smem) + 127u) & ~127u;
+  unsigned char* gbase = fs_smem + (base - tma::smem_addr(fs_smem));
+  const uint32_t oS = base + kFsU * kFsUSlot, zS = oS + kFsO * kFsOSlot;
+  const uint32_t bar0 = zS + kFsZ * kFsBPad;
+  auto ubar = [&](int q) { return bar0 + 8u * (uint32_t)(q % kFsU); };
+  auto obar = [&](int w) { return bar0 + 8u * (uint32_t)(kFsU + w % kFsO); };
+  auto zbar = [&](int v) { return bar0 + 8u * (uint32_t)(kFsU + kFsO + v % kFsZ); };
+  auto par3 = [](int q) { return (uint32_t)((q / 3) & 1); };
+  auto par4 = [](int q) { return (uint32_t)((q / 4) & 1); };
+  // producer (thread 0): iterate/correction sequence q is plane z0 - 1 + q;
+  // own-cell sequence w and -z face sequence v are plane z0 + w (v)
+  auto issue_u = [&](int q) {
+    const int z = z0 - 1 + q;
+    const uint32_t b = ubar(q);
+    if (z < 0 || z >= nz) {
+      tma::bar_arrive(b);
+      return;
+    }
+    tma::bar_arrive_tx(b, (uint32_t)kFsUSlot);  // the three boxes fill the slot exactly
+    const uint32_t d = base + (uint32_t)((q % kFsU) * kFsUSlot);
+    tma::load3(d, &maps.u, b, ux, uy, z);
+    tma::load3(d + kFsUBytes, &maps.e0, b, ex, uy, z);
+    tma::load3(d + kFsUBytes + kFsEBytes, &maps.e1, b, ex, uy, z);
+  };
+  auto issue_o = [&](int w) {
+    const uint32_t b = obar(w);
+    tma::bar_arrive_tx(b, (uint32_t)(2 * kFsB + kFsX + kFsY));
+    const uint32_t d = oS + (uint32_t)((w % kFsO) * kFsOSlot);
+    tma::load3(d, &maps.b, b, ox, oy, z0 + w);
+    tma::load3(d + kFsBPad, &maps.d, b, ox, oy, z0 + w);
+    tma::load3(d + 2 * kFsBPad, &maps.cx, b, ox, oy, z0 + w);
+    tma::load3(d + 2 * kFsBPad + kFsX, &maps.cy, b, ox, oy, z0 + w);
+  };
+  auto issue_z = [&](int v) {
+    const uint32_t b = zbar(v);
+    tma::bar_arrive_tx(b, (uint32_t)kFsB);
+    tma::load3(zS + (uint32_t)((v % kFsZ) * kFsBPad), &maps.cz, b, ox, oy, z0 + v);
+  };
+  // u + e of plane z0 - 1 + q from ring slot `slot`
+  auto combine = [&](int q, int slot, float2& v) {
+    const int k = z0 - 1 + q;
+    v = zero2;
+    if (!(in && k >= 0 && k < nz)) return;
+    const unsigned char* sl = gbase + slot * kFsUSlot;
+    const float2 u2 = reinterpret_cast<const float2*>(sl)[ty * 34 + tx + 1];
+    const float* e0 = reinterpret_cast<const float*>(sl + kFsUBytes) + ty * 24 + ecol;
+    const float* e1 = reinterpret_cast<const float*>(sl + kFsUBytes + kFsEBytes) + ty * 24 + ecol;
+    v = df_add(u2, ((par0 + k) & 1) ? *e1 : *e0);
+  };
+
+  int issued_u = min(kFsU, nq), issued_o = min(kFsO, n), issued_z = min(kFsZ, nv);
+  if (tid == 0) {
+    for (int q = 0; q < kFsU + kFsO + kFsZ; ++q) tma::bar_init(bar0 + 8u * q);
+    tma::bar_init_fence();
+    for (int q = 0; q < issued_u; ++q) issue_u(q);
+    for (int w = 0; w < issued_o; ++w) issue_o(w);
+    for (int v = 0; v < issued_z; ++v) issue_z(v);
+  }
+  __syncthreads();
+  bool ok = tma::bar_wait(ubar(0), 0u) && tma::bar_wait(ubar(1), 0u) && tma::bar_wait(ubar(2), 0u);
+  float2 um, uc, up;
+  combine(0, 0, um);
+  combine(1, 1, uc);
+  combine(2, 2, up);
+  float ss = 0.0f;
+  if (!__syncthreads_or(!ok)) {
+    if (tid == 0)
+      for (; issued_u < min(nq, 6); ++issued_u) issue_u(issued_u);
+    for (int it = 0; it < n; ++it) {
+      const int k = z0 + it;
+      ok = tma::bar_wait(obar(it), par3(it)) && ok;
+      if (it == 0) ok = tma::bar_wait(zbar(0), 0u) && ok;
+      if (k + 1 < nz) ok = tma::bar_wait(zbar(it + 1), par4(it + 1)) && ok;
+      const int buf = it & 1;
+      pl[buf][ty][tx] = uc;
+      const long long c = (long long)k * sz + off;
+      if (own && a.udf_out) a.udf_out[c] = uc;
+      if (__syncthreads_or(!ok)) {
+        ok = false;
+        break;
+      }
+      // every thread is past plane k - 1: its slots are free
+      if (tid == 0 && it >= 1) {
+        if (issued_u < nq) issue_u(issued_u++);
+        if (issued_o < n) issue_o(issued_o++);
+        if (issued_z < nv) issue_z(issued_z++);
+      }
+      float2 ul, ur;
+      ul.x = __shfl_up_sync(FULL, uc.x, 1);
+      ul.y = __shfl_up_sync(FULL, uc.y, 1);
+      ur.x = __shfl_down_sync(FULL, uc.x, 1);
+      ur.y = __shfl_down_sync(FULL, uc.y, 1);
+      if (own) {
+        const float2* os = reinterpret_cast<const float2*>(gbase + kFsU * kFsUSlot +
+                                                           (it % kFsO) * kFsOSlot);
+        const int o30 = (ty - 1) * 30 + (tx - 1);
+        const float2 bb = os[o30];
+        const float2 dg = reinterpret_cast<const float2*>(
+            reinterpret_cast<const unsigned char*>(os) + kFsBPad)[o30];
+        const float2* cxs =
+            reinterpret_cast<const float2*>(reinterpret_cast<const unsigned char*>(os) + 2 * kFsBPad);
+        const float2* cys = reinterpret_cast<const float2*>(
+            reinterpret_cast<const unsigned char*>(os) + 2 * kFsBPad + kFsX);
+        const float2* czs = reinterpret_cast<const float2*>(gbase + kFsU * kFsUSlot +
+                                                            kFsO * kFsOSlot);
+        float r = 0.0f;
+        if (!(dg.x < 0.0f)) {  // electrode cells (negative diagonal) keep r = 0
+          const bool zm = k > 0, zp = k < nz - 1;
+          DfAcc acc{bb.x, bb.y};
+          if (a.has_alpha) acc.add(a.nalpha, uc);
+          acc.add(make_float2(-dg.x, -dg.y), uc);
+          const float2 us = pl[buf][ty - 1][tx], un = pl[buf][ty + 1][tx];
+          const int o32 = (ty - 1) * 32 + (tx - 1);
+          if (xm) acc.add(cxs[o32], ul);
+          if (xp) acc.add(cxs[o32 + 1], ur);
+          if (ym) acc.add(cys[o30], us);
+          if (yp) acc.add(cys[o30 + 30], un);
+          if (zm) acc.add(czs[(it % kFsZ) * (kFsBPad / 8) + o30], um);
+          if (zp) acc.add(czs[((it + 1) % kFsZ) * (kFsBPad / 8) + o30], up);
+          r = acc.value();
+        }
+        if (a.r[0]) (((par0 + k) & 1) ? a.r[1] : a.r[0])[(long long)k * szW + eoff] = r;
+        ss = fmaf(r, r, ss);
+      }
+      um = uc;
+      uc = up;
+      if (it + 1 < n) {
+        const int q = it + 3;
+        ok = tma::bar_wait(ubar(q), par3(q)) && ok;
+        combine(q, q % kFsU, up);
+      }
+    }
+  } else {
+    ok = false;
+  }
+  if (!ok && tid == 0) {
+    atomicExch(&g_ir_timeout, 1u);
+    for (int q = max(0, issued_u - kFsU); q < issued_u; ++q) tma::bar_wait(ubar(q), par3(q));
+    for (int w = max(0, issued_o - kFsO); w < issued_o; ++w) tma::bar_wait(obar(w), par3(w));
+    for (int v = max(0, issued_z - kFsZ); v < issued_z; ++v) tma::bar_wait(zbar(v), par4(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
+  if (tx == 0) red[ty] = ss;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const long long cta = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    double v = threadIdx.x < NT / 32 ? (double)red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (threadIdx.x == 0) a.partial[cta] = v;
+  }
+}
+
 // 1.0 into *flag (mapped host memory) if any of u[0..n) is neither +0 nor -0
 // (a NaN counts as nonzero); at most one store per block.
 // The test is on the bits (all but the sign zero), on the integer pipe, 16
@@ -871,9 +1086,11 @@ static long long ir_ctas(const Box& b, int zchunk) {
 int ir_partials(const Box& b, int zchunk) { return (int)ir_ctas(b, zchunk); }
 
 bool ir_tma_ready() {
-  static const bool ok = cudaFuncSetAttribute(k_ir_df2_tma,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              kIrSmem) == cudaSuccess;
+  static const bool ok =
+      cudaFuncSetAttribute(k_ir_df2_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kIrSmem) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(k_ir_dff_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kFsSmem) ==
+          cudaSuccess;
   return ok;
 }
 
@@ -923,12 +1140,37 @@ static bool ir_tma(const IrArgs& a, dim3 g, cudaStream_t s) {
   return true;
 }
 
+// The staged face-array step (k_ir_dff_tma) where it applies: a
+// variable-coefficient refinement step (double-float iterate plus correction,
+// double-float b), nx a multiple of 8 and at least 64 x 16 cells per plane,
+// 16-byte aligned arrays and encodable tensor maps.  False: nothing launched.
+static bool ir_tma_faces(const IrArgs& a, dim3 g, cudaStream_t s) {
+  const Box& b = a.op.b;
+  if (b.nx % 8 != 0 || b.nx < 64 || b.ny < 16 || !a.udf_in || !a.bdf || !a.e[0] || !a.e[1] ||
+      !a.op.cxd || !a.op.cyd || !a.op.czd || !a.op.Dd || !ir_tma_ready())
+    return false;
+  FsMaps m;
+  const long long fx = 2LL * b.nx;
+  if (!tma_map_f32(&m.u, a.udf_in, fx, b.ny, b.nz, 68, TY) ||
+      !tma_map_f32(&m.e0, a.e[0], a.W, b.ny, b.nz, 24, TY) ||
+      !tma_map_f32(&m.e1, a.e[1], a.W, b.ny, b.nz, 24, TY) ||
+      !tma_map_f32(&m.b, a.bdf, fx, b.ny, b.nz, 2 * (TX - 2), TY - 2) ||
+      !tma_map_f32(&m.d, a.op.Dd, fx, b.ny, b.nz, 2 * (TX - 2), TY - 2) ||
+      !tma_map_f32(&m.cx, a.op.cxd, fx, b.ny, b.nz, 2 * TX, TY - 2) ||
+      !tma_map_f32(&m.cy, a.op.cyd, fx, b.ny, b.nz, 2 * (TX - 2), TY - 1) ||
+      !tma_map_f32(&m.cz, a.op.czd, fx, b.ny, b.nz, 2 * (TX - 2), TY - 2))
+    return false;
+  k_ir_dff_tma<<<g, NT, kFsSmem, s>>>(a, m);
+  return true;
+}
+
 template <bool P, bool F, bool E, bool U, int B, bool Z>
 static void go(const IrArgs& a, dim3 g, cudaStream_t s) {
   if (P && !Z) {
     if (E && !U && B == 0 && ir_tma(a, g, s)) return;
     k_ir_df2<E, U, B><<<g, NT, 0, s>>>(a);
   } else {
+    if (F && E && !U && B == 0 && !Z && ir_tma_faces(a, g, s)) return;
     k_ir_df<F, E, U, B, Z><<<g, NT, 0, s>>>(a);
   }
 }

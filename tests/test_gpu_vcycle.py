@@ -287,6 +287,38 @@ def test_staged_refinement_helmholtz_converges_to_oracle(mg, ir_zchunk):
         assert oracle.rel_l2(p.cpu().numpy(), ref) <= 1e-9
 
 
+@pytest.mark.parametrize("ir_zchunk", [0, 16, 128])
+def test_staged_refinement_poisson_converges_to_oracle(mg, ir_zchunk):
+    """The Poisson problem of the staged-sweep box (slab, electrode block in
+    the last x-tile, Neumann sides) solved to 1e-10: its refinement steps run
+    the one-cell face-array pass whose planes arrive by tensor copies (9 CTA
+    columns of 30 cells over 264, the last with 24; 2 row tiles of 14 over
+    20; chunks of 10, 16 with a ragged 8, or all 40 planes).  Within 1e-9 of
+    the oracle's answer."""
+    shape = TMA_SHAPE
+    nz, ny, nx = shape
+    h = 1.0 / nx
+    rho = blobs(shape, 36)
+    eps = W.dielectric_slab_box(shape, h, (0.0, 0.0, 0.0), z_top=0.07)
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[18:27, 6:13, 250:262] = 1
+    mv = np.where(mask != 0, 0.5, 0.0)
+    bc_kind = (1, 1, 1, 1, 0, 0)
+    bc_value = (0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+    s = mg.Solver(shape, h, eps_r=cuda(eps), mask=cuda(mask), mask_value=cuda(mv),
+                  bc_kind=bc_kind, bc_value=bc_value, precision=1, nu1=2, nu2=1,
+                  inner_cycles=2)
+    s.set_options(ir_zchunk=ir_zchunk)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st = s.solve_poisson(cuda(rho), u, 1e-10)
+    s.close()
+    assert st["converged"] and st["cycles"] >= 2
+    p = oracle.Problem(shape, h, 0.0, eps, mask, bc_kind, bc_value)
+    ref, _, rel, _ = p.solve(rho / oracle.EPS0, u0=mv, tol=1e-13)
+    assert rel < 1e-12
+    assert oracle.rel_l2(u.cpu().numpy(), ref) <= 1e-9
+
+
 @pytest.mark.parametrize("nu", [(2, 1), (1, 1)])
 def test_stacked_helmholtz_matches_oracle_and_unstacked(mg, nu):
     """The three Helmholtz problems of one context run their FP32 V-cycles
