@@ -155,6 +155,7 @@ def test_noalloc_binding_rejects_mismatched_shapes():
     ("sweep_zchunk", -2, b"sweep_zchunk"),
     ("coarse_visits", 3, b"coarse_visits"),
     ("fixed_cycles", 2, b"fixed_cycles"),
+    ("stack", 2, b"stack"),
 ])
 def test_create_rejects_bad_option_values(lib, field, value, msg):
     """Option values outside their documented sets are refused before any
