@@ -319,6 +319,51 @@ def test_staged_refinement_poisson_converges_to_oracle(mg, ir_zchunk):
     assert oracle.rel_l2(u.cpu().numpy(), ref) <= 1e-9
 
 
+@pytest.mark.parametrize("shape", [(24, 16, 64), (20, 24, 72)])
+def test_staged_poisson_refinement_smallest_boxes(mg, shape):
+    """The staged face-array refinement step at the smallest planes it takes
+    (64 x 16: three CTA columns of 30 cells, the last with 4; two row tiles
+    of 14, the last with 2) and at 72 x 24 (columns of 30, 30, 12; rows of
+    14 and 10), with the slab and Neumann sides: within 1e-9 of the oracle.
+    (Sizes whose halvings reach a coarsest level of at most 4096 cells.)"""
+    nz, ny, nx = shape
+    h = 1.0 / nx
+    rho = blobs(shape, 39)
+    eps = W.dielectric_slab_box(shape, h, (0.0, 0.0, 0.0), z_top=0.3 * nz * h)
+    bc_kind = (1, 1, 1, 1, 0, 0)
+    bc_value = (0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+    s = mg.Solver(shape, h, eps_r=cuda(eps), bc_kind=bc_kind, bc_value=bc_value,
+                  precision=1, nu1=2, nu2=1, inner_cycles=2)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    st = s.solve_poisson(cuda(rho), u, 1e-10)
+    s.close()
+    assert st["converged"] and st["cycles"] >= 2
+    p = oracle.Problem(shape, h, 0.0, eps, None, bc_kind, bc_value)
+    ref, _, rel, _ = p.solve(rho / oracle.EPS0, tol=1e-13)
+    assert rel < 1e-12
+    assert oracle.rel_l2(u.cpu().numpy(), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 128), (16, 20, 136)])
+def test_staged_helmholtz_refinement_smallest_boxes(mg, shape):
+    """The staged two-cell refinement step at the smallest planes it takes
+    (128 x 16: three CTA columns of 60 cells, the last with 8; two row tiles)
+    and at 136 x 20 (columns of 60, 60, 16; rows of 14 and 6): each of the
+    three Helmholtz answers within 1e-9 of the oracle's."""
+    h = 1.0 / shape[2]
+    S = np.abs(blobs(shape, 40)) / W.EPS0
+    kap = W.helmholtz_kappas()
+    s = mg.Solver(shape, h, precision=1, nu1=2, nu2=1, inner_cycles=2)
+    psi = [torch.zeros(shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    st = s.solve_helmholtz_batch(cuda(S), psi, kap, 1e-10)
+    s.close()
+    assert all(x["converged"] and x["cycles"] >= 2 for x in st)
+    for p, k in zip(psi, kap):
+        ref, _, rel, _ = oracle.helmholtz(shape, h, k).solve(S, tol=1e-13)
+        assert rel < 1e-12
+        assert oracle.rel_l2(p.cpu().numpy(), ref) <= 1e-9
+
+
 @pytest.mark.parametrize("nu", [(2, 1), (1, 1)])
 def test_stacked_helmholtz_matches_oracle_and_unstacked(mg, nu):
     """The three Helmholtz problems of one context run their FP32 V-cycles
