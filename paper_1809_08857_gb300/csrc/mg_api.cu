@@ -31,6 +31,7 @@
 
 #include "../../include/mg.h"
 #include "mg_diverge.h"
+#include "mg_trim.h"
 #include "mg_internal.h"
 
 namespace {
@@ -807,27 +808,10 @@ struct Stack {
   const StepGraph* g = nullptr;
 };
 
-// Inner V-cycles of p's next refinement step: the context's inner_cycles,
-// or fewer when the contraction per V-cycle measured over the last step
-// (from the second step on) says that fewer reach tol.  The measured rate is
-// taken 15 % weaker in its logarithm, so that a step that varies a little
-// from the last one still lands below tol; if it does not, the step after it
-// runs the full count again.  The fixed point and the tolerance test are
-// unchanged: only the number of V-cycles in the last step can shrink.  (An
-// answer that meets tol is as close to the exact discrete solution as its
-// problem's conditioning allows: the error of the 512^3 gap Poisson answer is
-// up to 30 times its relative residual, since the boundary lift dominates
-// ||b||; a stricter aim than tol removed every trimmed V-cycle of the
-// benchmark's set.)
+// Inner V-cycles of p's next refinement step (the trimming rule of mg_trim.h).
 int next_inner_cycles(const Prob& p) {
-  const int full = p.c->opt.inner_cycles;
-  if (p.c->opt.fixed_cycles || p.cyc < 2 || p.ic_last < 1 || !(p.rel_prev > 0.0) ||
-      !(p.rel > 0.0) || !(p.rel < p.rel_prev))
-    return full;
-  const double per_cycle = std::log(p.rel / p.rel_prev) / p.ic_last;  // < 0
-  const double need = std::log(p.tol / p.rel) / (0.85 * per_cycle);
-  if (!(need > 0.0) || need >= full) return full;
-  return std::max(1, (int)std::ceil(need));
+  return mg::trimmed_inner_cycles(p.c->opt.inner_cycles, p.c->opt.fixed_cycles != 0, p.cyc,
+                                  p.ic_last, p.rel_prev, p.rel, p.tol);
 }
 
 // kind Poisson with alpha = 0 is Eq. 2 (b = rho / eps0 + lifts); with
